@@ -1,0 +1,326 @@
+"""Benchmark of the qNEP force call on one GB300 (or N replicas under torchrun).
+
+Workload (default): BaTiO3 cubic perovskite 10x10x10 supercell, 5000 atoms,
+a = 4.0 A with N(0, 0.05 A) displacements, 3 species; NEP descriptor r_c 6/4 A,
+n_max 4/4, basis 8, l_max 4 + 4-body, 30 tanh units, two outputs; Ewald
+alpha = 0.3 1/A, real-space cutoff 6 A, k_max for 1e-6 relative error, mode 1;
+outputs energy, forces, virial, charges, BEC and polarization.
+
+A step is one full force call (neighbour build, descriptor + network,
+charges, Ewald, real space, backward, BEC).  Inputs are resident in HBM; the
+force call is replayed from a CUDA graph; L2 is flushed (a 512 MB write)
+between timed steps, outside the timed events.  The JSON line follows the
+repository's measurement contract ("Measurement").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "qNEP force-call atom-steps/s on 1 GB300 (mixed/batched vs FP32) at stated error"
+UNIT = "atom-steps/s"
+WORKLOAD = ("BaTiO3 10x10x10 perovskite, 5000 atoms, 3 species; NEP 6/4 A, n_max 4/4, basis 8, l_max 4 + 4-body, "
+            "30 tanh units x 2 outputs; Ewald alpha 0.3, r_c 6 A, k_max 2.230 (1e-6), mode 1; "
+            "forces + virial + BEC + polarization, FP32 path")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self, sm_max_default: float) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else sm_max_default,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _ewald_kcount(box, kmax):
+    """Half-space k vectors with |k| < kmax (for the algorithmic operation count)."""
+    lengths = np.diag(box)
+    nmax = [int(math.floor(kmax * ln / (2 * math.pi))) for ln in lengths]
+    g = np.meshgrid(*[np.arange(-m, m + 1) for m in nmax], indexing="ij")
+    n = np.stack([x.ravel() for x in g], 1)
+    k = 2 * math.pi * n / lengths
+    k2 = (k * k).sum(1)
+    return int(((k2 > 0) & (k2 < kmax * kmax)).sum()) // 2
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_19034_gb300 import workloads
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sysm, hp, params, elec = workloads.config_batio3()
+    n = sysm.n_atoms
+    model = QNEP(hp, params, elec)
+    pos = torch.tensor(sysm.positions, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    model.reserve(n, sysm.box)
+    # capacity check (and list growth) before capture
+    out = model.compute(pos, typ, sysm.box)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            model.compute_into(pos, typ, sysm.box, out, stream=stream.cuda_stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        model.compute_into(pos, typ, sysm.box, out, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    peaks, peak_kind = _peaks()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                graph.replay()
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3)
+
+    # parity spot-check of the timed graph's output (energy per atom, finite forces)
+    sc = parse_scalars(out["scalars"])
+    status = int(sc["status"])
+
+    # per-stage device times (events on the launching stream), eager launches
+    model.set_profiling(True)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            model.compute_into(pos, typ, sysm.box, out, stream=stream.cuda_stream)
+    stages, calls = model.stage_times()
+    model.set_profiling(False)
+    stage_avg = {k: v / max(calls, 1) for k, v in stages.items()}
+
+    # end to end: host buffers through the C ABI (copies in and out timed)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        model.compute_host(sysm.positions, sysm.types, sysm.box)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    h2d = n * 3 * 4 + n * 4
+    d2h = 20 * 8 + n * 3 * 4 + n * 9 * 4 + n * 4
+
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    line = None
+    if rank == 0:
+        roof = _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "l2": "flushed between steps (512 MB write)",
+                       "launch": "CUDA graph replay of one qnep_compute", "parallelism": "replicas" if world > 1
+                       else "single GPU", "wall_s": wall},
+            "stage_ms": stage_avg,
+            "roofline": roof,
+            "e2e": {"value": n / (statistics.median(e2e_ms) * 1e-3) * world, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.median(e2e_ms)},
+            "gpu_launches": KERNELS_PER_CALL * args.steps,
+            "clocks": clocks,
+            "device_status": status,
+            "energy_per_atom": sc["energy"] / n,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline(sysm, hp, params, elec, reps=1)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# kernels of one Ewald force call with forces + BEC: bin(4), neighbours, descriptor
+# forward, phases, S(k), S(k) finalize, field, backward, finalize atoms, finalize scalars
+KERNELS_PER_CALL = 13
+
+
+def _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind):
+    """Roofline of the dominant kernel from its live CUDA-event duration."""
+    name = max(stage_avg, key=stage_avg.get)
+    ms = stage_avg[name]
+    n = sysm.n_atoms
+    nk = _ewald_kcount(sysm.box, elec.kmax)
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    if name in ("field", "ewald_structure_factor"):
+        # algorithmic FP32 work: per (atom, half-space k) one complex multiply-accumulate
+        # for S(k) (8 flop) or potential + force (16 flop)
+        flop = n * nk * (16 if name == "field" else 8)
+        achieved = flop / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "ms": ms,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+                "work": f"{n} atoms x {nk} half-space k"}
+    flop = n * FLOP_PER_ATOM.get(name, 0)
+    achieved = flop / (ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None, "ms": ms,
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
+
+
+# algorithmic FP32 flop per atom of the descriptor kernels (BaTiO3 neighbour counts)
+FLOP_PER_ATOM = {"descriptor_forward": 18000, "descriptor_backward": 45000}
+
+
+def _cpu_baseline(sysm, hp, params, elec, reps=1):
+    import torch
+
+    from oracle import forcecall
+    cores = torch.get_num_threads()
+    t = time.perf_counter()
+    for _ in range(reps):
+        forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    dt = (time.perf_counter() - t) / reps
+    return {"value": sysm.n_atoms / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full force call(s) of the same workload (FP64 oracle, torch CPU threads={cores})"}
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores on this workload (rank 0 only)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import torch
+
+    from oracle import forcecall
+    from paper_2601_19034_gb300 import workloads
+    sysm, hp, params, elec = workloads.config_batio3()
+    cores = torch.get_num_threads()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sysm.n_atoms * len(times) / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "atoms": sysm.n_atoms},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step one full force call of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * qnep.h -- C ABI of the GB300 qNEP force call.
+ *
+ * qNEP (arXiv 2601.19034) is a neuroevolution potential whose single-hidden-
+ * layer network has two outputs per atom: a site energy U_i (Eq. U_i, Sec. II.A)
+ * and a partial charge q_i (Sec. II.B).  One force call computes, for one
+ * periodic structure (or a batch of structures under several parameter
+ * vectors):
+ *   - the NEP descriptor of every atom over its neighbour list (Sec. II.A),
+ *   - U_i and q_i from the network (Eq. U_i and the charge node, Sec. II.B),
+ *   - the charge scaling q~ = sqrt(eps_inf) q (Sec. II.D) and the total-charge
+ *     correction (Eq. charge-scaling),
+ *   - the electrostatic energy of the charges by Ewald summation (Eqs. U_ES,
+ *     U_k, S_k, Sec. II.B) or PPPM (Sec. II.F), mode 1 (real + k + self) or
+ *     mode 2 (k only, Eq. mode2),
+ *   - forces and virial including the dynamic-charge terms (Sec. II.C),
+ *   - the polarization (Eq. polarization) and the periodic Born effective
+ *     charges (Eq. bec_2).
+ *
+ * Units: Angstrom, e, eV; k_e = 14.3996454784 eV A / e^2.
+ * All entry points return a qnep_status; none aborts the process.
+ * Device pointers are CUDA global-memory addresses on the current device;
+ * host pointers are ordinary host memory.  Calls are asynchronous on the
+ * given stream unless stated otherwise.
+ */
+#ifndef QNEP_H
+#define QNEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QNEP_OK = 0,
+    QNEP_ERR_ARG = 1,           /* invalid argument (NULL, size, range, NaN box) */
+    QNEP_ERR_CUDA = 2,          /* a CUDA call failed; the model should be destroyed */
+    QNEP_ERR_NBR_OVERFLOW = 3,  /* an atom had more neighbours than the list capacity */
+    QNEP_ERR_UNSUPPORTED = 4,   /* shape / box / option not supported by this build */
+    QNEP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    QNEP_ERR_OOM = 6            /* device allocation failed */
+} qnep_status;
+
+/* Descriptor and network sizes (Sec. II.A).  This build supports
+ * n_radial = n_angular = 5, basis_radial = basis_angular = 9, l_max = 4,
+ * use_4body = 1, n_neurons = 30 (descriptor length 30) and 1..4 species;
+ * other sizes return QNEP_ERR_UNSUPPORTED. */
+typedef struct {
+    int   n_species;
+    float rc_radial;        /* radial descriptor cutoff (A) */
+    float rc_angular;       /* angular descriptor cutoff (A), <= rc_radial */
+    int   n_radial;         /* number of radial functions g_n (n_max + 1) */
+    int   n_angular;        /* number of angular radial functions */
+    int   basis_radial;     /* Chebyshev terms per radial function (basis size + 1) */
+    int   basis_angular;
+    int   l_max;            /* highest angular order of the 3-body terms */
+    int   use_4body;        /* 1: append the 4-body terms */
+    int   n_neurons;        /* hidden-layer width N_neu */
+} qnep_hparams;
+
+enum { QNEP_EWALD = 0, QNEP_PPPM = 1 };
+enum { QNEP_PREC_FP32 = 0, QNEP_PREC_MLP_BF16 = 1, QNEP_PREC_MLP_TF32 = 2 };
+
+/* Electrostatics settings (Sec. II.B, II.F). */
+typedef struct {
+    int    mode;       /* 1: U^r + U^k + U^s (Eq. U_ES); 2: U^k only (Eq. mode2) */
+    int    kind;       /* QNEP_EWALD or QNEP_PPPM */
+    double alpha;      /* Ewald splitting parameter (1/A) */
+    double rc_real;    /* real-space cutoff (A), mode 1; <= rc_radial */
+    double kmax;       /* Ewald: strict wave-vector cutoff |k| < kmax (1/A) */
+    int    mesh[3];    /* PPPM mesh (even sizes) */
+    int    order;      /* PPPM assignment order; this build supports 5 */
+    double q_total;    /* target total charge Q of the naked charges (Eq. charge-scaling) */
+} qnep_elec;
+
+/* Parameter blob of one candidate: n_params float32 values, laid out as
+ *   c_R[ti][tj][n][k]   n_species^2 * n_radial * basis_radial
+ *   c_A[ti][tj][n][k]   n_species^2 * n_angular * basis_angular
+ *   scaler[nu]          n_des
+ *   per species t:      W0[mu][nu] (n_neurons * n_des), b0[mu], w1E[mu], w1q[mu], b1E, b1q
+ *   sqrt_eps_inf        1
+ * where n_des = n_radial + l_max * n_angular + (use_4body ? n_angular : 0).
+ * The network weights are those of the central atom's species. */
+size_t qnep_param_count(const qnep_hparams* hp);
+
+typedef struct qnep_model qnep_model;
+
+/* Number and meaning of the FP64 scalar outputs (device array). */
+#define QNEP_NSCALARS 20
+enum {
+    QNEP_S_ENERGY = 0,      /* U^tot = U^NEP + U^ES (eV) */
+    QNEP_S_E_NEP = 1,       /* sum_i U_i */
+    QNEP_S_E_REAL = 2,      /* U^r (mode 1) */
+    QNEP_S_E_KSPACE = 3,    /* U^k (Ewald or PPPM) */
+    QNEP_S_E_SELF = 4,      /* U^s (mode 1) */
+    QNEP_S_VIRIAL = 5,      /* 9 values, row-major W_ab = sum_i r_ia F_ib convention (eV) */
+    QNEP_S_POLARIZATION = 14, /* 3 values, P = sum_i q~^c_i r_i (e A), positions as given */
+    QNEP_S_QTILDE_SUM = 17, /* sum of corrected naked charges (= q_total) */
+    QNEP_S_PHI_MEAN = 18,   /* mean electrostatic potential dU^ES/dq (V) */
+    QNEP_S_STATUS = 19      /* device-side status bits of this call (0 = fine) */
+};
+
+/* Outputs of one force call.  Every pointer may be NULL (not computed).
+ * Requesting forces or virial runs the backward pass; requesting bec adds
+ * the charge-derivative contraction. */
+typedef struct {
+    double* scalars;      /* device, QNEP_NSCALARS doubles (written every call) */
+    float*  forces;       /* device [N][3] (eV/A) */
+    float*  charges;      /* device [N] corrected screened charges q^c = q~^c / sqrt(eps_inf) */
+    float*  bec;          /* device [N][3][3] periodic Born effective charges Z_i,ab (Eq. bec_2) */
+    float*  site_energy;  /* device [N] U_i (optional) */
+    float*  potential;    /* device [N] phi_i = dU^ES/dq^c_i (optional) */
+    float*  descriptor;   /* device [N][n_des] (optional, for parity checks) */
+    int     want_virial;  /* 1: compute the virial into scalars (needs the backward pass) */
+} qnep_outputs;
+
+/* Create a model: copies n_candidates parameter blobs (host, candidate-major,
+ * n_candidates * qnep_param_count(hp) floats) to the device.  The model owns
+ * its device copies, neighbour lists, k-tables, meshes and FFT plans.
+ * precision: QNEP_PREC_*.  Fails with QNEP_ERR_UNSUPPORTED for shapes this
+ * build does not have kernels for. */
+qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* params_host,
+                        size_t n_params, int n_candidates, const qnep_elec* es, int precision);
+
+/* Pre-size every workspace for up to n_atoms atoms in this box (host double[9],
+ * rows = lattice vectors) so that later qnep_compute calls with the same box
+ * and at most n_atoms atoms allocate nothing (required before stream capture). */
+qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]);
+
+/* One force call on one structure with candidate 0.
+ *   positions: device [N][3] float32 (A); may lie outside the box (wrapped internally)
+ *   types:     device [N] int32 species index in [0, n_species)
+ *   box:       host double[9], rows = lattice vectors; orthorhombic only in this
+ *              build (QNEP_ERR_UNSUPPORTED otherwise), every edge >= the list cutoff
+ *   stream:    cudaStream_t (NULL = legacy default stream)
+ * Asynchronous: returns after enqueueing.  Device-side errors (neighbour
+ * overflow) are recorded in scalars[QNEP_S_STATUS] and returned by the next
+ * qnep_sync_status. */
+qnep_status qnep_compute(qnep_model* m, int n_atoms, const float* positions, const int* types,
+                         const double box[9], void* stream, const qnep_outputs* out);
+
+/* Same call on host buffers (positions [N][3], types [N]; outputs as in
+ * qnep_outputs but every pointer is HOST memory): copies in, computes, copies
+ * back and synchronizes.  This is the end-to-end path. */
+qnep_status qnep_compute_host(qnep_model* m, int n_atoms, const float* positions_host,
+                              const int* types_host, const double box[9], void* stream,
+                              const qnep_outputs* out_host);
+
+/* Synchronize the stream and return the device-side status of the last call. */
+qnep_status qnep_sync_status(qnep_model* m, void* stream);
+
+/* Change the neighbour-list capacities (entries per atom); 0 keeps the value. */
+qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
+
+/* Stage timers (tracing).  When enabled, every qnep_compute records CUDA events
+ * around each stage on its stream and accumulates the elapsed times.
+ * qnep_stage_times synchronizes, writes up to max_stages accumulated times (ms)
+ * and the number of timed calls, and resets the accumulators.  Stage names:
+ * qnep_stage_name(k) for k < QNEP_NSTAGES ("" beyond). */
+#define QNEP_NSTAGES 10
+qnep_status qnep_set_profiling(qnep_model* m, int enable);
+qnep_status qnep_stage_times(qnep_model* m, float* ms_out, int max_stages, int* n_calls);
+const char* qnep_stage_name(int stage);
+
+void        qnep_destroy(qnep_model* m);
+const char* qnep_status_string(qnep_status s);
+const char* qnep_last_error(qnep_model* m);   /* detail of the last failing call */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QNEP_H */

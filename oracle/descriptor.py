@@ -105,7 +105,7 @@ def descriptor(vec_r: torch.Tensor, i_r: np.ndarray, j_r: np.ndarray,
     cos = (u[e1] * u[e2]).sum(1).clamp(-1.0, 1.0)
     pl = legendre(cos, model.l_max)                                  # [P, l]
     gg = g_a[e1] * g_a[e2]                                           # [P, n]
-    contrib = (pl[:, :, None] * gg[:, None, :]).reshape(len(owner), -1)  # l-major, then n
+    contrib = (pl[:, :, None] * gg[:, None, :]).reshape(len(owner), model.l_max * n_a)  # l-major, then n
     d_ang = torch.zeros(n_loc, model.l_max * n_a, dtype=torch.float64).index_add(0, owner_t, contrib)
 
     parts = [d_rad, d_ang]

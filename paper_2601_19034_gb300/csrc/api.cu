@@ -1,0 +1,518 @@
+// C ABI of the qNEP force call: model lifetime, workspaces, k-tables and the
+// launch sequence of one force call (see include/qnep.h for the contract).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qnep.h"
+#include "qnep_internal.cuh"
+
+using namespace qnep;
+
+struct qnep_model {
+    qnep_hparams hp{};
+    qnep_elec es{};
+    int precision = 0;
+    int n_cand = 1;
+    ParamLayout lay{};
+    float* d_params = nullptr;
+    float sqrt_eps = 1.f;
+    int cap_list = 0, cap_ang = 0;          // 0: automatic from the density
+    // per-atom workspaces (grow only)
+    int n_alloc = 0, cl_alloc = 0, ca_alloc = 0, nph_alloc = 0;
+    float4* pos4 = nullptr;
+    int* cell_of = nullptr;
+    int* cell_atoms = nullptr;
+    int* nbr_list = nullptr;
+    int* cnt_list = nullptr;
+    int* nbr_ang = nullptr;
+    int* cnt_ang = nullptr;
+    float* ang = nullptr;
+    float* du = nullptr;
+    float* dq = nullptr;
+    float* u = nullptr;
+    float* q = nullptr;
+    float* phi = nullptr;
+    float* acc12 = nullptr;
+    float2* phase = nullptr;
+    // cells
+    int ncell_alloc = 0;
+    int* cell_count = nullptr;
+    int* cell_start = nullptr;
+    int* cell_fill = nullptr;
+    Accum* d_acc = nullptr;
+    unsigned int* h_status = nullptr;       // pinned mirror of the device status word
+    // geometry / Ewald tables, rebuilt when the box changes
+    bool have_box = false;
+    double box[9]{};
+    Geom geom{};
+    EwaldTab tab{};
+    int nk_alloc = 0, ncol_alloc = 0, nchunk_alloc = 0;
+    int4* d_col = nullptr;
+    int* d_chunk_col = nullptr;
+    float* d_kg = nullptr;
+    double2* d_S = nullptr;
+    float2* d_C = nullptr;
+    // device staging of the host-buffer entry point
+    int nio_alloc = 0;
+    float* io_pos = nullptr;
+    int* io_types = nullptr;
+    float* io_out[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* io_scalars = nullptr;
+    // stage timers
+    bool profiling = false;
+    cudaEvent_t ev[QNEP_NSTAGES + 1]{};
+    double stage_ms[QNEP_NSTAGES]{};
+    int timed_calls = 0;
+    bool pending = false;
+    std::string err;
+};
+
+namespace {
+
+qnep_status fail(qnep_model* m, qnep_status s, const std::string& msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(m, e_ == cudaErrorMemoryAllocation ? QNEP_ERR_OOM : QNEP_ERR_CUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+template <class T>
+cudaError_t grow(T** p, size_t count) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+bool supported_shape(const qnep_hparams* hp) {
+    return hp->n_radial == NR && hp->n_angular == NA && hp->basis_radial == KR && hp->basis_angular == KA &&
+           hp->l_max == LMAX && hp->use_4body == 1 && hp->n_neurons == NNEU && hp->n_species >= 1 &&
+           hp->n_species <= MAX_SPECIES;
+}
+
+float list_cutoff(const qnep_model* m) {
+    float rc = m->hp.rc_radial;
+    if (m->es.mode == 1 && (float)m->es.rc_real > rc) rc = (float)m->es.rc_real;
+    return rc;
+}
+
+// Half-space Ewald k-set in columns (n1, n2) with runs of n3, chunks of 8.
+qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
+    const double two_pi = 6.283185307179586;
+    const double kmax = m->es.kmax, alpha = m->es.alpha;
+    const double vol = L[0] * L[1] * L[2];
+    int nmax[3];
+    for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(kmax * L[d] / two_pi);
+    std::vector<int4> cols;
+    std::vector<float> kg;
+    std::vector<int> chunk_col;
+    for (int n1 = 0; n1 <= nmax[0]; ++n1) {
+        for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2) {
+            if (n1 == 0 && n2 < 0) continue;
+            double kx = two_pi * n1 / L[0], ky = two_pi * n2 / L[1];
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
+                if (n1 == 0 && n2 == 0 && n3 <= 0) continue;
+                double kz = two_pi * n3 / L[2];
+                double k2 = kx * kx + ky * ky + kz * kz;
+                if (k2 > 0 && k2 < kmax * kmax) {
+                    lo = std::min(lo, n3);
+                    hi = std::max(hi, n3);
+                }
+            }
+            if (hi < lo) continue;
+            int nchunk = (hi - lo + 1 + 7) / 8;
+            int c = (int)cols.size();
+            cols.push_back(make_int4(n1, n2, lo, (int)kg.size()));
+            for (int h = 0; h < nchunk; ++h) chunk_col.push_back(c);
+            for (int t = 0; t < 8 * nchunk; ++t) {
+                int n3 = lo + t;
+                double kz = two_pi * n3 / L[2];
+                double k2 = kx * kx + ky * ky + kz * kz;
+                bool ok = n3 <= hi && k2 > 0 && k2 < kmax * kmax && !(n1 == 0 && n2 == 0 && n3 <= 0);
+                kg.push_back(ok ? (float)(two_pi / vol * std::exp(-k2 / (4 * alpha * alpha)) / k2) : 0.f);
+            }
+        }
+    }
+    cols.push_back(make_int4(0, 0, 0, (int)kg.size()));
+    int ncol = (int)cols.size() - 1, nk = (int)kg.size(), nch = (int)chunk_col.size();
+    if (ncol + 1 > m->ncol_alloc) {
+        CK(grow(&m->d_col, ncol + 1));
+        m->ncol_alloc = ncol + 1;
+    }
+    if (nch > m->nchunk_alloc) {
+        CK(grow(&m->d_chunk_col, nch));
+        m->nchunk_alloc = nch;
+    }
+    if (nk > m->nk_alloc) {
+        CK(grow(&m->d_kg, nk));
+        CK(grow(&m->d_S, nk));
+        CK(grow(&m->d_C, nk));
+        m->nk_alloc = nk;
+    }
+    CK(cudaMemcpy(m->d_col, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice));
+    if (nch) CK(cudaMemcpy(m->d_chunk_col, chunk_col.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
+    if (nk) CK(cudaMemcpy(m->d_kg, kg.data(), sizeof(float) * nk, cudaMemcpyHostToDevice));
+    EwaldTab& t = m->tab;
+    t.n1max = nmax[0];
+    t.n2max = nmax[1];
+    t.n3max = nmax[2];
+    t.ncol = ncol;
+    t.nchunk = nch;
+    t.nk = nk;
+    t.yoff = nmax[0] + 1;
+    t.zoff = t.yoff + 2 * nmax[1] + 1;
+    t.nph = t.zoff + 2 * nmax[2] + 8;
+    if ((t.nph & 1) == 0) t.nph += 1;   // odd row stride: conflict-free strided shared-memory reads
+    for (int d = 0; d < 3; ++d) {
+        t.L[d] = (float)L[d];
+        double il = 1.0 / L[d];
+        t.invl_hi[d] = (float)il;
+        t.invl_lo[d] = (float)(il - (double)t.invl_hi[d]);
+    }
+    t.alpha = (float)alpha;
+    t.col = m->d_col;
+    t.chunk_col = m->d_chunk_col;
+    t.kg = m->d_kg;
+    t.S = m->d_S;
+    t.C = m->d_C;
+    return QNEP_OK;
+}
+
+qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
+    if (!box) return fail(m, QNEP_ERR_ARG, "box is NULL");
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(box[k])) return fail(m, QNEP_ERR_ARG, "box has a non-finite entry");
+    if (box[1] != 0 || box[2] != 0 || box[3] != 0 || box[5] != 0 || box[6] != 0 || box[7] != 0)
+        return fail(m, QNEP_ERR_UNSUPPORTED, "only orthorhombic boxes are supported");
+    double L[3] = {box[0], box[4], box[8]};
+    const float rcl = list_cutoff(m);
+    for (int d = 0; d < 3; ++d) {
+        if (!(L[d] > 0)) return fail(m, QNEP_ERR_ARG, "box edge must be positive");
+        if (L[d] < rcl) return fail(m, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff");
+    }
+    bool box_changed = !m->have_box || std::memcmp(m->box, box, sizeof(double) * 9) != 0;
+    if (box_changed) {
+        if (m->have_box) CK(cudaStreamSynchronize(st));   // in-flight kernels may read the old tables
+        Geom& g = m->geom;
+        g.ncells = 1;
+        for (int d = 0; d < 3; ++d) {
+            g.L[d] = (float)L[d];
+            g.invL[d] = (float)(1.0 / L[d]);
+            int nc = (int)std::floor(L[d] / rcl);
+            g.nc[d] = nc < 1 ? 1 : nc;
+            g.ncells *= g.nc[d];
+        }
+        g.rc_list = rcl;
+        g.rc_radial = m->hp.rc_radial;
+        g.rc_angular = m->hp.rc_angular;
+        g.rc_real = m->es.mode == 1 ? (float)m->es.rc_real : 0.f;
+        if (g.ncells + 1 > m->ncell_alloc) {
+            CK(grow(&m->cell_count, g.ncells + 1));
+            CK(grow(&m->cell_start, g.ncells + 1));
+            CK(grow(&m->cell_fill, g.ncells + 1));
+            m->ncell_alloc = g.ncells + 1;
+        }
+        if (m->es.mode != 0 && m->es.kind == QNEP_EWALD) {
+            qnep_status s = build_ewald_table(m, L);
+            if (s != QNEP_OK) return s;
+        }
+        std::memcpy(m->box, box, sizeof(double) * 9);
+        m->have_box = true;
+    }
+    // neighbour capacities from the mean density (2x the mean count + margin)
+    const double vol = L[0] * L[1] * L[2];
+    const double dens = n / vol;
+    const double pi43 = 4.18879020478639;
+    int cl = m->cap_list, ca = m->cap_ang;
+    if (cl <= 0) cl = ((int)(2.0 * pi43 * rcl * rcl * rcl * dens) + 32 + 31) / 32 * 32;
+    if (ca <= 0) {
+        double ra = m->hp.rc_angular;
+        ca = ((int)(2.0 * pi43 * ra * ra * ra * dens) + 16 + 15) / 16 * 16;
+    }
+    int nph = (m->es.mode != 0 && m->es.kind == QNEP_EWALD) ? m->tab.nph : 0;
+    bool need_atoms = n > m->n_alloc;
+    if (need_atoms || cl > m->cl_alloc || ca > m->ca_alloc || nph > m->nph_alloc) {
+        int na = std::max(n, m->n_alloc);
+        int ncl = std::max(cl, m->cl_alloc), nca = std::max(ca, m->ca_alloc), nnph = std::max(nph, m->nph_alloc);
+        CK(cudaStreamSynchronize(st));
+        CK(grow(&m->nbr_list, (size_t)ncl * na));
+        CK(grow(&m->nbr_ang, (size_t)nca * na));
+        if (need_atoms) {
+            CK(grow(&m->pos4, na));
+            CK(grow(&m->cell_of, na));
+            CK(grow(&m->cell_atoms, na));
+            CK(grow(&m->cnt_list, (size_t)MAX_SPECIES * na));
+            CK(grow(&m->cnt_ang, (size_t)MAX_SPECIES * na));
+            CK(grow(&m->ang, (size_t)NANG * na));
+            CK(grow(&m->du, (size_t)NDES * na));
+            CK(grow(&m->dq, (size_t)NDES * na));
+            CK(grow(&m->u, na));
+            CK(grow(&m->q, na));
+            CK(grow(&m->phi, na));
+            CK(grow(&m->acc12, (size_t)12 * na));
+        }
+        if (need_atoms || nnph > m->nph_alloc) CK(grow(&m->phase, (size_t)std::max(nnph, 1) * na));
+        m->n_alloc = na;
+        m->cl_alloc = ncl;
+        m->ca_alloc = nca;
+        m->nph_alloc = nnph;
+    }
+    m->tab.phase = m->phase;
+    return QNEP_OK;
+}
+
+const char* kStageNames[QNEP_NSTAGES] = {"cell_bin", "neighbors", "descriptor_forward", "ewald_phases",
+                                         "ewald_structure_factor", "ewald_sk_finalize", "field",
+                                         "descriptor_backward", "finalize", "pppm"};
+
+// Accumulate the event times of the previous profiled call (events are complete
+// once the stream has passed them; the caller synchronizes before reading).
+void harvest(qnep_model* m) {
+    if (!m->pending) return;
+    for (int k = 0; k < QNEP_NSTAGES; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m->ev[k], m->ev[k + 1]) == cudaSuccess) m->stage_ms[k] += ms;
+    }
+    m->timed_calls += 1;
+    m->pending = false;
+}
+
+struct StageMark {
+    qnep_model* m;
+    cudaStream_t st;
+    void operator()(int k) const {
+        if (m->profiling) cudaEventRecord(m->ev[k], st);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* qnep_stage_name(int stage) { return (stage >= 0 && stage < QNEP_NSTAGES) ? kStageNames[stage] : ""; }
+
+qnep_status qnep_set_profiling(qnep_model* m, int enable) {
+    if (!m) return QNEP_ERR_ARG;
+    if (enable && !m->ev[0]) {
+        for (int k = 0; k <= QNEP_NSTAGES; ++k) CK(cudaEventCreate(&m->ev[k]));
+    }
+    m->profiling = enable != 0;
+    return QNEP_OK;
+}
+
+qnep_status qnep_stage_times(qnep_model* m, float* ms_out, int max_stages, int* n_calls) {
+    if (!m) return QNEP_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    harvest(m);
+    for (int k = 0; k < max_stages && k < QNEP_NSTAGES; ++k) ms_out[k] = (float)m->stage_ms[k];
+    if (n_calls) *n_calls = m->timed_calls;
+    for (int k = 0; k < QNEP_NSTAGES; ++k) m->stage_ms[k] = 0.0;
+    m->timed_calls = 0;
+    return QNEP_OK;
+}
+
+size_t qnep_param_count(const qnep_hparams* hp) {
+    if (!hp) return 0;
+    int s = hp->n_species;
+    int ndes = hp->n_radial + hp->n_angular * hp->l_max + (hp->use_4body ? hp->n_angular : 0);
+    return (size_t)s * s * (hp->n_radial * hp->basis_radial + hp->n_angular * hp->basis_angular) + ndes +
+           (size_t)s * (hp->n_neurons * (ndes + 3) + 2) + 1;
+}
+
+const char* qnep_status_string(qnep_status s) {
+    switch (s) {
+        case QNEP_OK: return "ok";
+        case QNEP_ERR_ARG: return "invalid argument";
+        case QNEP_ERR_CUDA: return "CUDA error";
+        case QNEP_ERR_NBR_OVERFLOW: return "neighbour list overflow";
+        case QNEP_ERR_UNSUPPORTED: return "unsupported";
+        case QNEP_ERR_TIMEOUT: return "device wait timed out";
+        case QNEP_ERR_OOM: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char* qnep_last_error(qnep_model* m) { return m ? m->err.c_str() : ""; }
+
+qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* params_host, size_t n_params,
+                        int n_candidates, const qnep_elec* es, int precision) {
+    qnep_model* m = nullptr;
+    if (!out || !hp || !params_host || !es || n_candidates < 1) return QNEP_ERR_ARG;
+    *out = nullptr;
+    if (!supported_shape(hp)) return QNEP_ERR_UNSUPPORTED;
+    if (!(hp->rc_radial > 0) || !(hp->rc_angular > 0) || hp->rc_angular > hp->rc_radial) return QNEP_ERR_ARG;
+    size_t per = qnep_param_count(hp);
+    if (n_params != per * (size_t)n_candidates) return QNEP_ERR_ARG;
+    if (es->mode < 0 || es->mode > 2) return QNEP_ERR_ARG;
+    if (es->mode != 0) {
+        if (!(es->alpha > 0)) return QNEP_ERR_ARG;
+        if (es->kind != QNEP_EWALD && es->kind != QNEP_PPPM) return QNEP_ERR_ARG;
+        if (es->kind == QNEP_EWALD && !(es->kmax > 0)) return QNEP_ERR_ARG;
+        if (es->kind == QNEP_PPPM) return QNEP_ERR_UNSUPPORTED;
+        if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
+    }
+    if (precision != QNEP_PREC_FP32) return QNEP_ERR_UNSUPPORTED;
+    for (size_t k = 0; k < n_params; ++k)
+        if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
+    m = new qnep_model();
+    m->hp = *hp;
+    m->es = *es;
+    m->precision = precision;
+    m->n_cand = n_candidates;
+    m->lay = make_layout(hp->n_species);
+    m->sqrt_eps = params_host[m->lay.sqrt_eps];
+    CK(cudaMalloc((void**)&m->d_params, sizeof(float) * n_params));
+    CK(cudaMemcpy(m->d_params, params_host, sizeof(float) * n_params, cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void**)&m->d_acc, sizeof(Accum)));
+    CK(cudaMemset(m->d_acc, 0, sizeof(Accum)));
+    CK(cudaMallocHost((void**)&m->h_status, sizeof(unsigned int)));
+    *m->h_status = 0;
+    *out = m;
+    return QNEP_OK;
+}
+
+qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular) {
+    if (!m || cap_list < 0 || cap_angular < 0) return QNEP_ERR_ARG;
+    if (cap_list) m->cap_list = cap_list;
+    if (cap_angular) m->cap_ang = cap_angular;
+    return QNEP_OK;
+}
+
+qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]) {
+    if (!m || n_atoms < 0) return QNEP_ERR_ARG;
+    qnep_status s = prepare(m, n_atoms, box, 0);
+    if (s != QNEP_OK) return s;
+    CK(cudaDeviceSynchronize());
+    return QNEP_OK;
+}
+
+qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int* types, const double box[9],
+                         void* stream, const qnep_outputs* out) {
+    if (!m) return QNEP_ERR_ARG;
+    if (n < 1 || n > INDEX_MASK) return fail(m, QNEP_ERR_ARG, "atom count out of range");
+    if (!positions || !types || !out) return fail(m, QNEP_ERR_ARG, "NULL input or output struct");
+    cudaStream_t st = (cudaStream_t)stream;
+    qnep_status s = prepare(m, n, box, st);
+    if (s != QNEP_OK) return s;
+    const Geom& g = m->geom;
+    const bool ewald = m->es.mode != 0 && m->es.kind == QNEP_EWALD;
+    const bool backward = out->forces || out->bec || out->want_virial;
+    const bool want_bec = out->bec != nullptr;
+    const float q_target = (float)(m->es.q_total / (double)m->sqrt_eps);   // Q in screened-charge units
+    const int cl = m->cap_list > 0 ? m->cap_list : m->cl_alloc;
+    const int ca = m->cap_ang > 0 ? m->cap_ang : m->ca_alloc;
+    ElecConst ec{m->es.mode, m->es.kind, (float)m->es.alpha, (float)m->es.q_total};
+
+    if (m->profiling) {
+        CK(cudaStreamSynchronize(st));   // the previous call's events are complete
+        harvest(m);
+    }
+    StageMark mark{m, st};
+    mark(0);
+    CK(cudaMemsetAsync(m->d_acc, 0, sizeof(Accum), st));
+    launch_bin(positions, types, n, g, m->pos4, m->cell_of, m->cell_count, m->cell_start, m->cell_fill, m->cell_atoms,
+               st);
+    mark(1);
+    launch_neighbors(m->pos4, m->cell_start, m->cell_atoms, n, m->hp.n_species, g, cl, ca, m->nbr_list, m->cnt_list,
+                     m->nbr_ang, m->cnt_ang, m->d_acc, st);
+    mark(2);
+    launch_descriptor_forward(m->pos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params, m->lay,
+                              backward ? m->ang : nullptr, backward ? m->du : nullptr, backward ? m->dq : nullptr,
+                              m->u, m->q, out->descriptor, m->d_acc, st);
+    mark(3);
+    if (ewald) launch_ewald_phases(m->pos4, n, m->tab, st);
+    mark(4);
+    if (ewald) launch_ewald_sk(m->q, m->d_acc, n, q_target, m->tab, st);
+    mark(5);
+    if (ewald) launch_ewald_sk_finalize(m->tab, m->d_acc, st);
+    mark(6);
+    launch_field(m->pos4, positions, m->q, m->nbr_list, m->cnt_list, n, m->hp.n_species, g, ec, q_target, m->sqrt_eps,
+                 ewald, m->tab, nullptr, m->phi, m->acc12, out->charges, m->d_acc, st);
+    mark(7);
+    if (backward)
+        launch_descriptor_backward(m->pos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
+                                   m->lay, m->ang, m->du, m->dq, m->phi, m->d_acc, want_bec, m->acc12, m->d_acc, st);
+    mark(8);
+    launch_finalize_atoms(m->acc12, n, out->forces, out->bec, m->phi, out->potential, st);
+    if (out->site_energy) CK(cudaMemcpyAsync(out->site_energy, m->u, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    launch_finalize_scalars(m->d_acc, n, m->sqrt_eps, out->scalars, st);
+    mark(9);
+    mark(10);
+    if (m->profiling) m->pending = true;
+    CK(cudaMemcpyAsync(m->h_status, &m->d_acc->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaGetLastError());
+    return QNEP_OK;
+}
+
+qnep_status qnep_sync_status(qnep_model* m, void* stream) {
+    if (!m) return QNEP_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned st = *m->h_status;
+    if (st & 1u) return fail(m, QNEP_ERR_NBR_OVERFLOW, "an atom had more neighbours than the list capacity");
+    return QNEP_OK;
+}
+
+qnep_status qnep_compute_host(qnep_model* m, int n, const float* positions_host, const int* types_host,
+                              const double box[9], void* stream, const qnep_outputs* out_host) {
+    if (!m) return QNEP_ERR_ARG;
+    if (n < 1 || !positions_host || !types_host || !out_host) return fail(m, QNEP_ERR_ARG, "bad host arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > m->nio_alloc) {
+        CK(cudaStreamSynchronize(st));
+        CK(grow(&m->io_pos, (size_t)3 * n));
+        CK(grow(&m->io_types, n));
+        const size_t sizes[6] = {(size_t)3 * n, (size_t)n, (size_t)9 * n, (size_t)n, (size_t)n, (size_t)NDES * n};
+        for (int k = 0; k < 6; ++k) CK(grow(&m->io_out[k], sizes[k]));
+        if (!m->io_scalars) CK(cudaMalloc((void**)&m->io_scalars, sizeof(double) * QNEP_NSCALARS));
+        m->nio_alloc = n;
+    }
+    CK(cudaMemcpyAsync(m->io_pos, positions_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(m->io_types, types_host, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    qnep_outputs dev{};
+    dev.scalars = out_host->scalars ? m->io_scalars : nullptr;
+    dev.forces = out_host->forces ? m->io_out[0] : nullptr;
+    dev.charges = out_host->charges ? m->io_out[1] : nullptr;
+    dev.bec = out_host->bec ? m->io_out[2] : nullptr;
+    dev.site_energy = out_host->site_energy ? m->io_out[3] : nullptr;
+    dev.potential = out_host->potential ? m->io_out[4] : nullptr;
+    dev.descriptor = out_host->descriptor ? m->io_out[5] : nullptr;
+    dev.want_virial = out_host->want_virial;
+    qnep_status s = qnep_compute(m, n, m->io_pos, m->io_types, box, stream, &dev);
+    if (s != QNEP_OK) return s;
+    if (out_host->scalars)
+        CK(cudaMemcpyAsync(out_host->scalars, dev.scalars, sizeof(double) * QNEP_NSCALARS, cudaMemcpyDeviceToHost, st));
+    struct { float* h; float* d; size_t cnt; } cp[6] = {
+        {out_host->forces, dev.forces, (size_t)3 * n},    {out_host->charges, dev.charges, (size_t)n},
+        {out_host->bec, dev.bec, (size_t)9 * n},          {out_host->site_energy, dev.site_energy, (size_t)n},
+        {out_host->potential, dev.potential, (size_t)n},  {out_host->descriptor, dev.descriptor, (size_t)NDES * n}};
+    for (auto& c : cp)
+        if (c.h) CK(cudaMemcpyAsync(c.h, c.d, sizeof(float) * c.cnt, cudaMemcpyDeviceToHost, st));
+    return qnep_sync_status(m, stream);
+}
+
+void qnep_destroy(qnep_model* m) {
+    if (!m) return;
+    void* bufs[] = {m->d_params, m->pos4, m->cell_of, m->cell_atoms, m->nbr_list, m->cnt_list, m->nbr_ang,
+                    m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phi, m->acc12, m->phase, m->cell_count,
+                    m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_kg, m->d_S, m->d_C,
+                    m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
+                    m->io_out[4], m->io_out[5]};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (m->h_status) cudaFreeHost(m->h_status);
+    for (int k = 0; k <= QNEP_NSTAGES; ++k)
+        if (m->ev[k]) cudaEventDestroy(m->ev[k]);
+    delete m;
+}
+
+}  // extern "C"

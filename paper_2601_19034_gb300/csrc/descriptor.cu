@@ -1,0 +1,654 @@
+// NEP descriptor, two-output network and the chain-rule backward.
+//
+// Descriptor (the NEP3/NEP4 form the paper defers to, Sec. II.A):
+//   f_c(r) = (1 + cos(pi r / r_c)) / 2,  x = 2 (r/r_c - 1)^2 - 1,  f_k = (T_k(x) + 1) f_c / 2
+//   g_n(r) = sum_k c[t_i][t_j][n][k] f_k(r)
+//   D^R_n = sum_j g^R_n(r_ij)
+//   D^A_{nl} = sum_{j,k} g^A_n(r_ij) g^A_n(r_ik) P_l(cos theta_ijk) = sum_m w_lm A_{n,lm}^2,
+//              A_{n,lm} = sum_j g^A_n(r_ij) Y_lm(u_ij)           (addition theorem)
+//   D^4b_n = tr(T_n^3),  T_n = sum_j g^A_n(r_ij) (u u^T - I/3)   (built from the l = 2 A's)
+// Y_lm are real harmonic polynomials of the unit vector with weights w_lm such
+// that sum_m w_lm Y_lm(a) Y_lm(b) = P_l(a.b).
+// Network (Eq. U_i and the charge node of Sec. II.B), weights of the central
+// species: h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q.  The forward
+// kernel also stores dU/dD and dq/dD; the backward forms the adjoints
+//   lambda = dU/dD + (phi_i - mean phi) dq/dD,   kappa = sqrt(eps_inf) dq/dD
+// (partial forces of Sec. II.C: F^NEP_ij plus the real / reciprocal / self
+// dynamic-charge terms, and a_ij = dq~_i/dr_ij for Eq. bec_2), recomputes
+// dD/dr_ij per neighbour entry and scatters the partial forces.
+#include "qnep_internal.cuh"
+
+namespace qnep {
+
+namespace {
+
+__constant__ float c_wlm[NLM] = {1.f, 1.f, 1.f,
+                                 0.25f, 3.f, 3.f, 0.75f, 3.f,
+                                 0.25f, 0.375f, 0.375f, 3.75f, 15.f, 0.625f, 0.625f,
+                                 1.f / 64.f, 0.625f, 0.625f, 0.3125f, 1.25f, 4.375f, 4.375f, 35.f / 64.f, 8.75f};
+
+__device__ __forceinline__ void harmonics(float x, float y, float z, float Y[NLM]) {
+    float x2 = x * x, y2 = y * y, z2 = z * z;
+    Y[0] = z; Y[1] = x; Y[2] = y;
+    Y[3] = 3.f * z2 - 1.f; Y[4] = x * z; Y[5] = y * z; Y[6] = x2 - y2; Y[7] = x * y;
+    float a5 = 5.f * z2 - 1.f;
+    Y[8] = z * (5.f * z2 - 3.f); Y[9] = x * a5; Y[10] = y * a5; Y[11] = z * (x2 - y2); Y[12] = x * y * z;
+    Y[13] = x * (x2 - 3.f * y2); Y[14] = y * (3.f * x2 - y2);
+    float a7 = 7.f * z2 - 3.f, b7 = 7.f * z2 - 1.f;
+    Y[15] = (35.f * z2 - 30.f) * z2 + 3.f; Y[16] = x * z * a7; Y[17] = y * z * a7; Y[18] = (x2 - y2) * b7;
+    Y[19] = x * y * b7; Y[20] = z * x * (x2 - 3.f * y2); Y[21] = z * y * (3.f * x2 - y2);
+    Y[22] = x2 * x2 - 6.f * x2 * y2 + y2 * y2; Y[23] = x * y * (x2 - y2);
+}
+
+// g = sum_lm psi_lm grad_u Y_lm(u) (gradient of the polynomials, not yet projected)
+__device__ __forceinline__ void harmonics_grad(float x, float y, float z, const float p[NLM], float& gx,
+                                               float& gy, float& gz) {
+    float x2 = x * x, y2 = y * y, z2 = z * z;
+    gx = p[1] + p[4] * z + p[6] * 2.f * x + p[7] * y;
+    gy = p[2] + p[5] * z - p[6] * 2.f * y + p[7] * x;
+    gz = p[0] + p[3] * 6.f * z + p[4] * x + p[5] * y;
+    float a5 = 5.f * z2 - 1.f;
+    gx += p[9] * a5 + p[11] * 2.f * x * z + p[12] * y * z + p[13] * 3.f * (x2 - y2) + p[14] * 6.f * x * y;
+    gy += p[10] * a5 - p[11] * 2.f * y * z + p[12] * x * z - p[13] * 6.f * x * y + p[14] * 3.f * (x2 - y2);
+    gz += p[8] * (15.f * z2 - 3.f) + p[9] * 10.f * x * z + p[10] * 10.f * y * z + p[11] * (x2 - y2) + p[12] * x * y;
+    float a7 = 7.f * z2 - 3.f, b7 = 7.f * z2 - 1.f, zc = z * a7;
+    gx += p[16] * zc + p[18] * 2.f * x * b7 + p[19] * y * b7 + p[20] * 3.f * z * (x2 - y2) + p[21] * 6.f * x * y * z +
+          p[22] * (4.f * x2 * x - 12.f * x * y2) + p[23] * (3.f * x2 * y - y2 * y);
+    gy += p[17] * zc - p[18] * 2.f * y * b7 + p[19] * x * b7 - p[20] * 6.f * x * y * z + p[21] * 3.f * z * (x2 - y2) +
+          p[22] * (4.f * y2 * y - 12.f * x2 * y) + p[23] * (x2 * x - 3.f * x * y2);
+    gz += p[15] * (140.f * z2 - 60.f) * z + p[16] * x * (21.f * z2 - 3.f) + p[17] * y * (21.f * z2 - 3.f) +
+          p[18] * 14.f * z * (x2 - y2) + p[19] * 14.f * x * y * z + p[20] * x * (x2 - 3.f * y2) +
+          p[21] * y * (3.f * x2 - y2);
+}
+
+template <int K>
+__device__ __forceinline__ void basis(float r, float rc, float f[K]) {
+    float rr = r / rc;
+    float fc = 0.5f * (1.f + cospif(rr));
+    float x = 2.f * (rr - 1.f) * (rr - 1.f) - 1.f;
+    float t0 = 1.f, t1 = x;
+    f[0] = fc;
+    if (K > 1) f[1] = 0.5f * (x + 1.f) * fc;
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        float t2 = 2.f * x * t1 - t0;
+        f[k] = 0.5f * (t2 + 1.f) * fc;
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void basis_d(float r, float rc, float f[K], float df[K]) {
+    float rr = r / rc;
+    float s, c;
+    sincospif(rr, &s, &c);
+    float fc = 0.5f * (1.f + c);
+    float dfc = -0.5f * 3.14159265358979f / rc * s;
+    float x = 2.f * (rr - 1.f) * (rr - 1.f) - 1.f;
+    float dx = 4.f * (rr - 1.f) / rc;
+    float t0 = 1.f, t1 = x, d0 = 0.f, d1 = 1.f;
+    f[0] = fc;
+    df[0] = dfc;
+    if (K > 1) {
+        f[1] = 0.5f * (x + 1.f) * fc;
+        df[1] = 0.5f * (dx * fc + (x + 1.f) * dfc);
+    }
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        float t2 = 2.f * x * t1 - t0;
+        float d2 = 2.f * t1 + 2.f * x * d1 - d0;   // T_k' by differentiating the recurrence
+        f[k] = 0.5f * (t2 + 1.f) * fc;
+        df[k] = 0.5f * (d2 * dx * fc + (t2 + 1.f) * dfc);
+        t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+    }
+}
+
+template <int TPA>
+__device__ __forceinline__ float group_sum(float v, unsigned mask) {
+#pragma unroll
+    for (int o = TPA / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, TPA);
+    return v;
+}
+
+template <int TPA>
+__device__ __forceinline__ unsigned group_mask() {
+    if (TPA == 32) return 0xffffffffu;
+    unsigned lane = threadIdx.x & 31;
+    return ((1u << TPA) - 1u) << (lane & ~(unsigned)(TPA - 1));
+}
+
+__device__ __forceinline__ void entry_vector(const float4* __restrict__ pos4, int e, const float4& pi,
+                                             const Geom& g, float& vx, float& vy, float& vz) {
+    int j = entry_index(e);
+    float tx, ty, tz;
+    entry_shift(e, tx, ty, tz);
+    float4 pj = __ldg(&pos4[j]);
+    vx = (pj.x - pi.x) + tx * g.L[0];
+    vy = (pj.y - pi.y) + ty * g.L[1];
+    vz = (pj.z - pi.z) + tz * g.L[2];
+}
+
+// 4-body: T_n from the l = 2 expansion coefficients (unnormalised harmonics 3..7)
+__device__ __forceinline__ void tensor_from_a(const float a[5], float t[6]) {
+    // a: (3z^2-1, xz, yz, x^2-y^2, xy) sums; t: xx, yy, zz, xy, xz, yz
+    float zz = a[0] * (1.f / 3.f);
+    t[0] = 0.5f * (a[3] - zz);
+    t[1] = 0.5f * (-a[3] - zz);
+    t[2] = zz;
+    t[3] = a[4];
+    t[4] = a[1];
+    t[5] = a[2];
+}
+
+__device__ __forceinline__ void tensor_square(const float t[6], float s[6]) {
+    s[0] = t[0] * t[0] + t[3] * t[3] + t[4] * t[4];
+    s[1] = t[3] * t[3] + t[1] * t[1] + t[5] * t[5];
+    s[2] = t[4] * t[4] + t[5] * t[5] + t[2] * t[2];
+    s[3] = t[0] * t[3] + t[3] * t[1] + t[4] * t[5];
+    s[4] = t[0] * t[4] + t[3] * t[5] + t[4] * t[2];
+    s[5] = t[3] * t[4] + t[1] * t[5] + t[5] * t[2];
+}
+
+template <int TPA>
+__global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos4, const int* __restrict__ nbr_list,
+                                                  const int* __restrict__ cnt_list, const int* __restrict__ nbr_ang,
+                                                  const int* __restrict__ cnt_ang, int n, Geom g,
+                                                  const float* __restrict__ params, ParamLayout lay,
+                                                  float* __restrict__ ang_coef, float* __restrict__ du,
+                                                  float* __restrict__ dq, float* __restrict__ u_out,
+                                                  float* __restrict__ q_out, float* __restrict__ des_out,
+                                                  Accum* __restrict__ acc) {
+    extern __shared__ float sp[];
+    for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
+    __syncthreads();
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / TPA;
+    const int lane = gt % TPA;
+    double su = 0.0, sq = 0.0;
+    if (i < n) {
+        const unsigned gm = group_mask<TPA>();
+        const int S = lay.n_species;
+        const float4 pi = __ldg(&pos4[i]);
+        const int ti = __float_as_int(pi.w);
+        const float rcr2 = g.rc_radial * g.rc_radial;
+
+        // radial: per neighbour-species basis sums contracted with c_R
+        float dr[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) dr[q] = 0.f;
+        int off = 0;
+        for (int s = 0; s < S; ++s) {
+            const int cnt = __ldg(&cnt_list[(size_t)s * n + i]);
+            float b[KR];
+#pragma unroll
+            for (int k = 0; k < KR; ++k) b[k] = 0.f;
+            for (int e = lane; e < cnt; e += TPA) {
+                int ent = __ldg(&nbr_list[(size_t)(off + e) * n + i]);
+                float vx, vy, vz;
+                entry_vector(pos4, ent, pi, g, vx, vy, vz);
+                float r2 = vx * vx + vy * vy + vz * vz;
+                if (r2 < rcr2) {
+                    float f[KR];
+                    basis<KR>(sqrtf(r2), g.rc_radial, f);
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) b[k] += f[k];
+                }
+            }
+            off += cnt;
+            const float* c = sp + lay.c_radial + ((ti * S + s) * NR) * KR;
+#pragma unroll
+            for (int q = 0; q < NR; ++q)
+#pragma unroll
+                for (int k = 0; k < KR; ++k) dr[q] = fmaf(c[q * KR + k], b[k], dr[q]);
+        }
+
+        // angular expansion coefficients A_{n,lm}
+        float a[NA][NLM];
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+#pragma unroll
+            for (int m = 0; m < NLM; ++m) a[q][m] = 0.f;
+        off = 0;
+        for (int s = 0; s < S; ++s) {
+            const int cnt = __ldg(&cnt_ang[(size_t)s * n + i]);
+            const float* c = sp + lay.c_angular + ((ti * S + s) * NA) * KA;
+            for (int e = lane; e < cnt; e += TPA) {
+                int ent = __ldg(&nbr_ang[(size_t)(off + e) * n + i]);
+                float vx, vy, vz;
+                entry_vector(pos4, ent, pi, g, vx, vy, vz);
+                float r = sqrtf(vx * vx + vy * vy + vz * vz);
+                float f[KA];
+                basis<KA>(r, g.rc_angular, f);
+                float gn[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) {
+                    float acc_g = 0.f;
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) acc_g = fmaf(c[q * KA + k], f[k], acc_g);
+                    gn[q] = acc_g;
+                }
+                float ir = 1.f / r;
+                float Y[NLM];
+                harmonics(vx * ir, vy * ir, vz * ir, Y);
+#pragma unroll
+                for (int q = 0; q < NA; ++q)
+#pragma unroll
+                    for (int m = 0; m < NLM; ++m) a[q][m] = fmaf(gn[q], Y[m], a[q][m]);
+            }
+            off += cnt;
+        }
+        if (TPA > 1) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) dr[q] = group_sum<TPA>(dr[q], gm);
+#pragma unroll
+            for (int q = 0; q < NA; ++q)
+#pragma unroll
+                for (int m = 0; m < NLM; ++m) a[q][m] = group_sum<TPA>(a[q][m], gm);
+        }
+        if (ang_coef) {
+#pragma unroll
+            for (int q = 0; q < NA; ++q)
+#pragma unroll
+                for (int m = 0; m < NLM; ++m)
+                    if (((q * NLM + m) % TPA) == lane) ang_coef[(size_t)(q * NLM + m) * n + i] = a[q][m];
+        }
+
+        // descriptor vector
+        float d[NDES];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) d[q] = dr[q];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            float s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) s1 = fmaf(c_wlm[m], a[q][m] * a[q][m], s1);
+#pragma unroll
+            for (int m = 3; m < 8; ++m) s2 = fmaf(c_wlm[m], a[q][m] * a[q][m], s2);
+#pragma unroll
+            for (int m = 8; m < 15; ++m) s3 = fmaf(c_wlm[m], a[q][m] * a[q][m], s3);
+#pragma unroll
+            for (int m = 15; m < 24; ++m) s4 = fmaf(c_wlm[m], a[q][m] * a[q][m], s4);
+            d[NR + 0 * NA + q] = s1;
+            d[NR + 1 * NA + q] = s2;
+            d[NR + 2 * NA + q] = s3;
+            d[NR + 3 * NA + q] = s4;
+            float t[6], t2[6];
+            float a2[5] = {a[q][3], a[q][4], a[q][5], a[q][6], a[q][7]};
+            tensor_from_a(a2, t);
+            tensor_square(t, t2);
+            // tr(T^3) = sum_ab (T^2)_ab T_ab (T symmetric)
+            d[NR + 4 * NA + q] = t2[0] * t[0] + t2[1] * t[1] + t2[2] * t[2] +
+                                 2.f * (t2[3] * t[3] + t2[4] * t[4] + t2[5] * t[5]);
+        }
+        const float* scaler = sp + lay.scaler;
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) d[v] *= scaler[v];
+        if (des_out && lane == 0) {
+#pragma unroll
+            for (int v = 0; v < NDES; ++v) des_out[(size_t)i * NDES + v] = d[v];
+        }
+
+        // network and its input gradients (hidden units split over the TPA lanes)
+        const float* net = sp + lay.mlp + ti * lay.mlp_stride;
+        float uu = 0.f, qq = 0.f, gu[NDES], gq[NDES];
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) { gu[v] = 0.f; gq[v] = 0.f; }
+        for (int mu = lane; mu < NNEU; mu += TPA) {
+            const float* w0 = net + ParamLayout::W0 + mu * NDES;
+            float pre = -net[ParamLayout::B0 + mu];
+#pragma unroll
+            for (int v = 0; v < NDES; ++v) pre = fmaf(w0[v], d[v], pre);
+            float h = tanhf(pre);
+            float we = net[ParamLayout::W1E + mu], wq = net[ParamLayout::W1Q + mu];
+            uu = fmaf(we, h, uu);
+            qq = fmaf(wq, h, qq);
+            float dh = 1.f - h * h;
+            float ae = we * dh, aq = wq * dh;
+#pragma unroll
+            for (int v = 0; v < NDES; ++v) {
+                gu[v] = fmaf(ae, w0[v], gu[v]);
+                gq[v] = fmaf(aq, w0[v], gq[v]);
+            }
+        }
+        if (TPA > 1) {
+            uu = group_sum<TPA>(uu, gm);
+            qq = group_sum<TPA>(qq, gm);
+#pragma unroll
+            for (int v = 0; v < NDES; ++v) {
+                gu[v] = group_sum<TPA>(gu[v], gm);
+                gq[v] = group_sum<TPA>(gq[v], gm);
+            }
+        }
+        uu -= net[ParamLayout::B1E];
+        qq -= net[ParamLayout::B1Q];
+        if (du) {
+#pragma unroll
+            for (int v = 0; v < NDES; ++v)
+                if ((v % TPA) == lane) {
+                    du[(size_t)v * n + i] = gu[v] * scaler[v];
+                    dq[(size_t)v * n + i] = gq[v] * scaler[v];
+                }
+        }
+        if (lane == 0) {
+            u_out[i] = uu;
+            q_out[i] = qq;
+            su = (double)uu;
+            sq = (double)qq;
+        }
+    }
+    // warp reduction of the FP64 energy / charge sums, one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc->sum_u, su);
+        atomicAdd(&acc->sum_q, sq);
+    }
+}
+
+// Scatter one partial force F_ij (and a_ij) of entry (i -> j, vector v).
+template <bool BEC>
+__device__ __forceinline__ void scatter(float4* __restrict__ acc12, int j, float vx, float vy, float vz, float fx,
+                                        float fy, float fz, float ax, float ay, float az, float fi[3], float zi[9],
+                                        float w[9]) {
+    fi[0] += fx; fi[1] += fy; fi[2] += fz;
+    w[0] -= vx * fx; w[1] -= vx * fy; w[2] -= vx * fz;
+    w[3] -= vy * fx; w[4] -= vy * fy; w[5] -= vy * fz;
+    w[6] -= vz * fx; w[7] -= vz * fy; w[8] -= vz * fz;
+    if (BEC) {
+        float hx = 0.5f * vx, hy = 0.5f * vy, hz = 0.5f * vz;
+        float z0 = hx * ax, z1 = hx * ay, z2 = hx * az, z3 = hy * ax, z4 = hy * ay, z5 = hy * az, z6 = hz * ax,
+              z7 = hz * ay, z8 = hz * az;
+        zi[0] += z0; zi[1] += z1; zi[2] += z2; zi[3] += z3; zi[4] += z4;
+        zi[5] += z5; zi[6] += z6; zi[7] += z7; zi[8] += z8;
+        atomicAdd(&acc12[3 * j + 0], make_float4(-fx, -fy, -fz, -z0));
+        atomicAdd(&acc12[3 * j + 1], make_float4(-z1, -z2, -z3, -z4));
+        atomicAdd(&acc12[3 * j + 2], make_float4(-z5, -z6, -z7, -z8));
+    } else {
+        atomicAdd(&acc12[3 * j + 0], make_float4(-fx, -fy, -fz, 0.f));
+    }
+}
+
+constexpr int PHI_STRIDE = 2 * NANG + 1;   // adjoint-weighted A's of one atom (odd stride)
+
+template <int TPA, bool BEC>
+__global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos4, const int* __restrict__ nbr_list,
+                                                  const int* __restrict__ cnt_list, const int* __restrict__ nbr_ang,
+                                                  const int* __restrict__ cnt_ang, int n, Geom g,
+                                                  const float* __restrict__ params, ParamLayout lay,
+                                                  const float* __restrict__ ang_coef, const float* __restrict__ du,
+                                                  const float* __restrict__ dqp, const float* __restrict__ phi,
+                                                  const Accum* __restrict__ acc_in, float4* __restrict__ acc12,
+                                                  Accum* __restrict__ acc) {
+    extern __shared__ float sm[];
+    float* sp = sm;
+    float* sphi = sm + ((lay.total + 3) & ~3);
+    for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
+    __syncthreads();
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / TPA;
+    const int lane = gt % TPA;
+    float w[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = 0.f;
+    if (i < n) {
+        const unsigned gm = group_mask<TPA>();
+        const int S = lay.n_species;
+        const float4 pi = __ldg(&pos4[i]);
+        const int ti = __float_as_int(pi.w);
+        const float seps = sp[lay.sqrt_eps];
+        const float phibar = (float)(acc_in->sum_phi / (double)n);
+        const float dphi = phi[i] - phibar;
+        float lam[NDES], kap[NDES];
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) {
+            float gq = __ldg(&dqp[(size_t)v * n + i]);
+            lam[v] = fmaf(dphi, gq, __ldg(&du[(size_t)v * n + i]));
+            kap[v] = seps * gq;
+        }
+        // adjoint-weighted angular coefficients: Phi_{n,lm} = dE/dA_{n,lm}
+        float* my = sphi + (threadIdx.x / TPA) * PHI_STRIDE;
+        for (int e = lane; e < NANG; e += TPA) {
+            int q = e / NLM, m = e % NLM;
+            int l = m < 3 ? 1 : (m < 8 ? 2 : (m < 15 ? 3 : 4));
+            float av = __ldg(&ang_coef[(size_t)e * n + i]);
+            float pl = 2.f * c_wlm[m] * av * lam[NR + (l - 1) * NA + q];
+            float pk = 2.f * c_wlm[m] * av * kap[NR + (l - 1) * NA + q];
+            if (l == 2) {
+                float a2[5], t[6], t2[6];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) a2[k] = __ldg(&ang_coef[(size_t)(q * NLM + 3 + k) * n + i]);
+                tensor_from_a(a2, t);
+                tensor_square(t, t2);
+                float dd;   // d tr(T^3) / d A_{n,lm} = 3 sum_ab (T^2)_ab dT_ab/dA
+                if (m == 3) dd = 3.f * (t2[2] * (1.f / 3.f) - (t2[0] + t2[1]) * (1.f / 6.f));
+                else if (m == 4) dd = 6.f * t2[4];
+                else if (m == 5) dd = 6.f * t2[5];
+                else if (m == 6) dd = 1.5f * (t2[0] - t2[1]);
+                else dd = 6.f * t2[3];
+                pl = fmaf(lam[NR + 4 * NA + q], dd, pl);
+                pk = fmaf(kap[NR + 4 * NA + q], dd, pk);
+            }
+            my[e] = pl;
+            my[NANG + e] = pk;
+        }
+        __syncwarp(gm);
+
+        float fi[3] = {0.f, 0.f, 0.f}, zi[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) zi[k] = 0.f;
+        const float rcr2 = g.rc_radial * g.rc_radial;
+        // radial entries
+        int off = 0;
+        for (int s = 0; s < S; ++s) {
+            const int cnt = __ldg(&cnt_list[(size_t)s * n + i]);
+            const float* c = sp + lay.c_radial + ((ti * S + s) * NR) * KR;
+            float ml[KR], mk[KR];
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                float x = 0.f, y = 0.f;
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    x = fmaf(lam[q], c[q * KR + k], x);
+                    y = fmaf(kap[q], c[q * KR + k], y);
+                }
+                ml[k] = x;
+                mk[k] = y;
+            }
+            for (int e = lane; e < cnt; e += TPA) {
+                int ent = __ldg(&nbr_list[(size_t)(off + e) * n + i]);
+                float vx, vy, vz;
+                entry_vector(pos4, ent, pi, g, vx, vy, vz);
+                float r2 = vx * vx + vy * vy + vz * vz;
+                if (r2 < rcr2) {
+                    float r = sqrtf(r2);
+                    float f[KR], df[KR];
+                    basis_d<KR>(r, g.rc_radial, f, df);
+                    float sl = 0.f, sk = 0.f;
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) {
+                        sl = fmaf(ml[k], df[k], sl);
+                        sk = fmaf(mk[k], df[k], sk);
+                    }
+                    float ir = 1.f / r;
+                    float ux = vx * ir, uy = vy * ir, uz = vz * ir;
+                    scatter<BEC>(acc12, entry_index(ent), vx, vy, vz, sl * ux, sl * uy, sl * uz, sk * ux, sk * uy,
+                                 sk * uz, fi, zi, w);
+                }
+            }
+            off += cnt;
+        }
+        // angular entries
+        off = 0;
+        for (int s = 0; s < S; ++s) {
+            const int cnt = __ldg(&cnt_ang[(size_t)s * n + i]);
+            const float* c = sp + lay.c_angular + ((ti * S + s) * NA) * KA;
+            for (int e = lane; e < cnt; e += TPA) {
+                int ent = __ldg(&nbr_ang[(size_t)(off + e) * n + i]);
+                float vx, vy, vz;
+                entry_vector(pos4, ent, pi, g, vx, vy, vz);
+                float r = sqrtf(vx * vx + vy * vy + vz * vz);
+                float f[KA], df[KA];
+                basis_d<KA>(r, g.rc_angular, f, df);
+                float gn[NA], dgn[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) {
+                    float x = 0.f, y = 0.f;
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) {
+                        x = fmaf(c[q * KA + k], f[k], x);
+                        y = fmaf(c[q * KA + k], df[k], y);
+                    }
+                    gn[q] = x;
+                    dgn[q] = y;
+                }
+                float ir = 1.f / r;
+                float ux = vx * ir, uy = vy * ir, uz = vz * ir;
+                float Y[NLM];
+                harmonics(ux, uy, uz, Y);
+                float out[2][3];
+#pragma unroll
+                for (int pass = 0; pass < (BEC ? 2 : 1); ++pass) {
+                    const float* ph = my + pass * NANG;
+                    float psi[NLM];
+#pragma unroll
+                    for (int m = 0; m < NLM; ++m) psi[m] = 0.f;
+                    float rho = 0.f;
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) {
+                        float pq = 0.f;
+#pragma unroll
+                        for (int m = 0; m < NLM; ++m) {
+                            float pv = ph[q * NLM + m];
+                            pq = fmaf(pv, Y[m], pq);
+                            psi[m] = fmaf(gn[q], pv, psi[m]);
+                        }
+                        rho = fmaf(dgn[q], pq, rho);
+                    }
+                    float gx, gy, gz;
+                    harmonics_grad(ux, uy, uz, psi, gx, gy, gz);
+                    float gu = gx * ux + gy * uy + gz * uz;
+                    out[pass][0] = rho * ux + (gx - gu * ux) * ir;
+                    out[pass][1] = rho * uy + (gy - gu * uy) * ir;
+                    out[pass][2] = rho * uz + (gz - gu * uz) * ir;
+                }
+                if (!BEC) { out[1][0] = out[1][1] = out[1][2] = 0.f; }
+                scatter<BEC>(acc12, entry_index(ent), vx, vy, vz, out[0][0], out[0][1], out[0][2], out[1][0],
+                             out[1][1], out[1][2], fi, zi, w);
+            }
+            off += cnt;
+        }
+        if (TPA > 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fi[k] = group_sum<TPA>(fi[k], gm);
+            if (BEC) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) zi[k] = group_sum<TPA>(zi[k], gm);
+            }
+        }
+        if (lane == 0) {
+            atomicAdd(&acc12[3 * i + 0], make_float4(fi[0], fi[1], fi[2], zi[0]));
+            if (BEC) {
+                atomicAdd(&acc12[3 * i + 1], make_float4(zi[1], zi[2], zi[3], zi[4]));
+                atomicAdd(&acc12[3 * i + 2], make_float4(zi[5], zi[6], zi[7], zi[8]));
+            }
+        }
+    }
+    // block reduction of the virial, FP64 atomics
+    __shared__ float red[9][4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float v = w[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += (double)red[threadIdx.x][q];
+        atomicAdd(&acc->virial[threadIdx.x], t);
+    }
+}
+
+template <int TPA>
+void fwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
+                const float* params, const ParamLayout& lay, float* ang, float* du, float* dq, float* u, float* q,
+                float* des, Accum* acc, cudaStream_t st) {
+    const int threads = 128;
+    long long blocks = ((long long)n * TPA + threads - 1) / threads;
+    size_t smem = sizeof(float) * lay.total;
+    k_desc_fwd<TPA><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq, u,
+                                                             q, des, acc);
+}
+
+template <int TPA, bool BEC>
+void bwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
+                const float* params, const ParamLayout& lay, const float* ang, const float* du, const float* dq,
+                const float* phi, const Accum* acc_in, float4* acc12, Accum* acc, cudaStream_t st) {
+    const int threads = 128;
+    long long blocks = ((long long)n * TPA + threads - 1) / threads;
+    size_t smem = sizeof(float) * (((lay.total + 3) & ~3) + (threads / TPA) * PHI_STRIDE);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_desc_bwd<TPA, BEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    k_desc_bwd<TPA, BEC><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq,
+                                                                  phi, acc_in, acc12, acc);
+}
+
+}  // namespace
+
+int choose_tpa(int n) {
+    // lanes per atom: enough threads to fill 152 SMs x 4 warps for small systems
+    if (n <= 8192) return 4;
+    if (n <= 65536) return 2;
+    return 1;
+}
+
+void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
+                               const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
+                               float* ang_coef, float* du, float* dq, float* u_out, float* q_out, float* des_out,
+                               Accum* acc, cudaStream_t st) {
+    if (n == 0) return;
+    int tpa = choose_tpa(n);
+    if (tpa == 4)
+        fwd_launch<4>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
+                      des_out, acc, st);
+    else if (tpa == 2)
+        fwd_launch<2>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
+                      des_out, acc, st);
+    else
+        fwd_launch<1>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
+                      des_out, acc, st);
+}
+
+void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
+                                const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
+                                const float* ang_coef, const float* du, const float* dq, const float* phi,
+                                const Accum* acc_in, bool want_bec, float* acc12, Accum* acc, cudaStream_t st) {
+    if (n == 0) return;
+    float4* a4 = reinterpret_cast<float4*>(acc12);
+    int tpa = choose_tpa(n) >= 2 ? choose_tpa(n) : 2;
+    if (want_bec) {
+        if (tpa == 4)
+            bwd_launch<4, true>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
+                                acc_in, a4, acc, st);
+        else
+            bwd_launch<2, true>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
+                                acc_in, a4, acc, st);
+    } else {
+        if (tpa == 4)
+            bwd_launch<4, false>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
+                                 acc_in, a4, acc, st);
+        else
+            bwd_launch<2, false>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
+                                 acc_in, a4, acc, st);
+    }
+}
+
+}  // namespace qnep

@@ -1,0 +1,168 @@
+// Internal declarations of the GB300 qNEP force call (not part of the C ABI).
+//
+// Layout conventions (device):
+//   pos4[i]            float4 (x, y, z wrapped into the box, species as int bits)
+//   list entries       int32: neighbour index j in bits 0..25, image code in bits 26..30,
+//                      code = (Tx+1) + 3 (Ty+1) + 9 (Tz+1), r_ij = pos4[j] + T.L - pos4[i];
+//                      column-major [cap][N]; entries of an atom grouped by neighbour
+//                      species (count per species in cnt[s][N])
+//   per-atom vectors   column-major [component][N] for coalesced access
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qnep {
+
+// Descriptor / network shape supported by the kernels of this build.
+constexpr int NR = 5;      // radial functions
+constexpr int KR = 9;      // Chebyshev terms (radial)
+constexpr int NA = 5;      // angular radial functions
+constexpr int KA = 9;      // Chebyshev terms (angular)
+constexpr int LMAX = 4;
+constexpr int NLM = 24;    // (l, m) pairs for l = 1..4
+constexpr int NDES = NR + NA * LMAX + NA;   // 30
+constexpr int NNEU = 30;
+constexpr int MAX_SPECIES = 4;
+constexpr int NANG = NA * NLM;              // 120 angular expansion coefficients per atom
+constexpr float KE = 14.3996454784f;        // k_e = 1/(4 pi eps0), eV A / e^2
+constexpr double KE_D = 14.3996454784;
+
+constexpr int CODE_SHIFT = 26;
+constexpr int INDEX_MASK = (1 << CODE_SHIFT) - 1;
+
+// Offsets (floats) into one candidate's parameter blob.
+struct ParamLayout {
+    int n_species;
+    int c_radial;      // [S][S][NR][KR]
+    int c_angular;     // [S][S][NA][KA]
+    int scaler;        // [NDES]
+    int mlp;           // start of species 0 network block
+    int mlp_stride;    // floats per species block
+    int sqrt_eps;      // 1 float
+    int total;
+    // inside a species block
+    static constexpr int W0 = 0;                  // [NNEU][NDES]
+    static constexpr int B0 = NNEU * NDES;        // [NNEU]
+    static constexpr int W1E = B0 + NNEU;
+    static constexpr int W1Q = W1E + NNEU;
+    static constexpr int B1E = W1Q + NNEU;
+    static constexpr int B1Q = B1E + 1;
+    static constexpr int BLOCK = B1Q + 1;
+};
+
+inline ParamLayout make_layout(int s) {
+    ParamLayout p;
+    p.n_species = s;
+    p.c_radial = 0;
+    p.c_angular = s * s * NR * KR;
+    p.scaler = p.c_angular + s * s * NA * KA;
+    p.mlp = p.scaler + NDES;
+    p.mlp_stride = ParamLayout::BLOCK;
+    p.sqrt_eps = p.mlp + s * ParamLayout::BLOCK;
+    p.total = p.sqrt_eps + 1;
+    return p;
+}
+
+// Orthorhombic box and cell grid, passed by value to kernels.
+struct Geom {
+    float L[3];        // edge lengths
+    float invL[3];
+    int nc[3];         // cells per dimension
+    int ncells;
+    float rc_list;     // list cutoff (max of radial descriptor and real-space cutoffs)
+    float rc_radial;
+    float rc_angular;
+    float rc_real;     // 0 when there is no real-space term
+};
+
+// FP64 accumulators of one force call (zeroed at the start of every call).
+struct Accum {
+    double sum_q;        // sum of raw network charges q_i
+    double sum_u;        // sum of site energies
+    double sum_phi;      // sum of phi_i
+    double e_real;
+    double e_self;
+    double e_kspace;
+    double virial[9];
+    double polar[3];
+    double sum_qc;       // sum of corrected naked charges q~^c
+    unsigned int status; // bit 0: neighbour overflow
+    unsigned int pad;
+};
+
+// Electrostatics constants for the kernels.
+struct ElecConst {
+    int mode;            // 0: none, 1: real + k + self, 2: k only
+    int kind;            // 0 Ewald, 1 PPPM
+    float alpha;
+    float q_total;
+};
+
+// Ewald k-space description (host-built, uploaded when the box changes).
+//  Half space of wave vectors k = 2 pi (n1/Lx, n2/Ly, n3/Lz), |k| < kmax, grouped
+//  in columns (n1, n2) holding the contiguous run n3 in [lo, hi].  Each column is
+//  stored as chunks of 8 consecutive n3 (padded past hi with G = 0), so the
+//  padded index of (column c, chunk h, t) is col[c].w + 8 h + t.
+struct EwaldTab {
+    int n1max, n2max, n3max;
+    int ncol;             // columns
+    int nchunk;           // 8-wide chunks over all columns
+    int nk;               // padded k count = 8 nchunk
+    int nph;              // complex phase factors per atom
+    int yoff, zoff;       // offsets of the Y and Z tables in an atom's row
+    float L[3];
+    float invl_hi[3], invl_lo[3];   // 1/L as a float pair (phase reduction)
+    float alpha;
+    const int4* col;      // [ncol + 1] (n1, n2, lo, padded offset); last entry: (0, 0, 0, nk)
+    const int* chunk_col; // [nchunk] column of each chunk
+    const float* kg;      // [nk] G(k) = (2 pi / V) exp(-k^2 / 4 alpha^2) / k^2, 0 on padding
+    double2* S;           // [nk] structure factor sum_i q_i exp(-i k.r_i) (FP64)
+    float2* C;            // [nk] 4 k_e G(k) S(k) (FP32) for the force / potential pass
+    float2* phase;        // [N][nph]: X[0..n1max], Y[-n2max..n2max], Z[-n3max..n3max+7]
+};
+
+__device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }
+__device__ __forceinline__ void entry_shift(int e, float& tx, float& ty, float& tz) {
+    int code = (unsigned)e >> CODE_SHIFT;
+    int cz = code / 9;
+    int cy = (code - 9 * cz) / 3;
+    int cx = code - 9 * cz - 3 * cy;
+    tx = (float)(cx - 1);
+    ty = (float)(cy - 1);
+    tz = (float)(cz - 1);
+}
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// ---- host-side launchers (defined in the .cu files) ---------------------------------
+
+struct Workspace;   // defined in api.cu
+
+void launch_bin(const float* pos, const int* types, int n, const Geom& g, float4* pos4, int* cell_of,
+                int* cell_count, int* cell_start, int* cell_fill, int* cell_atoms, cudaStream_t st);
+void launch_neighbors(const float4* pos4, const int* cell_start, const int* cell_atoms, int n,
+                      int n_species, const Geom& g, int cap_list, int cap_ang, int* nbr_list,
+                      int* cnt_list, int* nbr_ang, int* cnt_ang, Accum* acc, cudaStream_t st);
+void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list,
+                               const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
+                               const float* params, const ParamLayout& lay, float* ang_coef,
+                               float* du, float* dq, float* u_out, float* q_out, float* des_out,
+                               Accum* acc, cudaStream_t st);
+void launch_ewald_phases(const float4* pos4, int n, EwaldTab tab, cudaStream_t st);
+void launch_ewald_sk(const float* q_raw, const Accum* acc, int n, float q_target, EwaldTab tab, cudaStream_t st);
+void launch_ewald_sk_finalize(EwaldTab tab, Accum* acc, cudaStream_t st);
+void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, const int* nbr_list,
+                  const int* cnt_list, int n, int n_species, const Geom& g, ElecConst ec, float q_target,
+                  float sqrt_eps, bool ewald, EwaldTab tab, const float* pppm_field, float* phi,
+                  float* acc12, float* charges_out, Accum* acc, cudaStream_t st);
+void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list,
+                                const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
+                                const float* params, const ParamLayout& lay, const float* ang_coef,
+                                const float* du, const float* dq, const float* phi, const Accum* acc_in,
+                                bool want_bec, float* acc12, Accum* acc, cudaStream_t st);
+void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi,
+                           float* potential, cudaStream_t st);
+void launch_finalize_scalars(const Accum* acc, int n, float sqrt_eps, double* scalars, cudaStream_t st);
+
+}  // namespace qnep

@@ -1,0 +1,181 @@
+"""PyTorch-facing wrapper of the qNEP force call.
+
+``QNEP`` owns one model handle of the C library; ``compute`` takes CUDA
+tensors and returns CUDA tensors, launching on torch's current stream.  Every
+step of the force call runs in the library's kernels; this module only
+allocates output tensors and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from .workloads import Elec, HParams
+
+
+def _hp_c(hp: HParams) -> _lib.HParamsC:
+    return _lib.HParamsC(hp.n_species, hp.rc_radial, hp.rc_angular, hp.n_radial, hp.n_angular,
+                         hp.basis_radial, hp.basis_angular, hp.l_max, hp.use_4body, hp.n_neurons)
+
+
+def _elec_c(es: Elec) -> _lib.ElecC:
+    kind = _lib.QNEP_EWALD if es.kind == "ewald" else _lib.QNEP_PPPM
+    return _lib.ElecC(es.mode, kind, es.alpha, es.rc_real, es.kmax, (ctypes.c_int * 3)(*es.mesh),
+                      es.order, es.q_total)
+
+
+_PREC = {"fp32": _lib.QNEP_PREC_FP32, "bf16": _lib.QNEP_PREC_MLP_BF16, "tf32": _lib.QNEP_PREC_MLP_TF32}
+
+
+def parse_scalars(s) -> dict:
+    """Split the FP64 scalar output vector into named values (host numpy)."""
+    s = s.detach().cpu().numpy() if isinstance(s, torch.Tensor) else np.asarray(s)
+    out = {}
+    for k, v in _lib.SCALAR_NAMES.items():
+        out[k] = s[v].copy() if isinstance(v, slice) else float(s[v])
+    out["virial"] = out["virial"].reshape(3, 3)
+    return out
+
+
+class QNEP:
+    """One qNEP model (descriptor + network parameters, electrostatics settings)."""
+
+    def __init__(self, hp: HParams, params, elec: Elec, precision: str = "fp32"):
+        self.lib = _lib.load()
+        blob = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        n_cand = blob.size // hp.n_params
+        self.hp, self.elec = hp, elec
+        handle = ctypes.c_void_p()
+        hpc, esc = _hp_c(hp), _elec_c(elec)
+        st = self.lib.qnep_create(ctypes.byref(handle), ctypes.byref(hpc), blob.ctypes.data, blob.size,
+                                  n_cand, ctypes.byref(esc), _PREC[precision])
+        _lib.check(st)
+        self.handle = handle
+        self._box = (ctypes.c_double * 9)()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.qnep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_capacity(self, cap_list: int = 0, cap_angular: int = 0):
+        _lib.check(self.lib.qnep_set_capacity(self.handle, int(cap_list), int(cap_angular)), self.handle)
+
+    def _set_box(self, box):
+        b = np.asarray(box, dtype=np.float64).reshape(9)
+        for k in range(9):
+            self._box[k] = float(b[k])
+
+    def reserve(self, n_atoms: int, box):
+        self._set_box(box)
+        _lib.check(self.lib.qnep_reserve(self.handle, int(n_atoms), self._box), self.handle)
+
+    def outputs(self, n: int, device, forces=True, bec=True, charges=True, virial=True,
+                descriptor=False, potential=False, site_energy=False) -> dict:
+        """Allocate an output dict of CUDA tensors for ``compute_into``."""
+        out = {"scalars": torch.zeros(_lib.QNEP_NSCALARS, dtype=torch.float64, device=device)}
+        if forces:
+            out["forces"] = torch.empty(n, 3, dtype=torch.float32, device=device)
+        if bec:
+            out["bec"] = torch.empty(n, 3, 3, dtype=torch.float32, device=device)
+        if charges:
+            out["charges"] = torch.empty(n, dtype=torch.float32, device=device)
+        if descriptor:
+            out["descriptor"] = torch.empty(n, self.hp.n_des, dtype=torch.float32, device=device)
+        if potential:
+            out["potential"] = torch.empty(n, dtype=torch.float32, device=device)
+        if site_energy:
+            out["site_energy"] = torch.empty(n, dtype=torch.float32, device=device)
+        out["_virial"] = bool(virial)
+        return out
+
+    def compute_into(self, positions: torch.Tensor, types: torch.Tensor, box, out: dict, stream=None):
+        """Enqueue one force call writing into ``out`` (from ``outputs``); no synchronisation."""
+        assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
+        assert types.is_cuda and types.dtype == torch.int32 and types.is_contiguous()
+        n = positions.shape[0]
+        self._set_box(box)
+
+        def ptr(name):
+            t = out.get(name)
+            return t.data_ptr() if t is not None else None
+
+        oc = _lib.OutputsC(ptr("scalars"), ptr("forces"), ptr("charges"), ptr("bec"), ptr("site_energy"),
+                           ptr("potential"), ptr("descriptor"), 1 if out.get("_virial") else 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(positions.device).cuda_stream
+        st = self.lib.qnep_compute(self.handle, n, positions.data_ptr(), types.data_ptr(), self._box,
+                                   ctypes.c_void_p(stream), ctypes.byref(oc))
+        _lib.check(st, self.handle)
+
+    def set_profiling(self, enable: bool = True):
+        _lib.check(self.lib.qnep_set_profiling(self.handle, 1 if enable else 0), self.handle)
+
+    def stage_times(self) -> tuple:
+        """Accumulated per-stage device times (ms) since the last read, and the call count."""
+        buf = (ctypes.c_float * _lib.QNEP_NSTAGES)()
+        calls = ctypes.c_int()
+        _lib.check(self.lib.qnep_stage_times(self.handle, buf, _lib.QNEP_NSTAGES, ctypes.byref(calls)),
+                   self.handle)
+        names = [self.lib.qnep_stage_name(k).decode() for k in range(_lib.QNEP_NSTAGES)]
+        return dict(zip(names, list(buf))), calls.value
+
+    def sync_status(self, stream=None) -> int:
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        return self.lib.qnep_sync_status(self.handle, ctypes.c_void_p(stream))
+
+    def compute(self, positions: torch.Tensor, types: torch.Tensor, box, retries: int = 3, **want) -> dict:
+        """Force call with a status check; grows the neighbour lists and retries on overflow."""
+        out = self.outputs(positions.shape[0], positions.device, **want)
+        for _ in range(retries + 1):
+            self.compute_into(positions, types, box, out)
+            st = self.sync_status()
+            if st != _lib.QNEP_ERR_NBR_OVERFLOW:
+                _lib.check(st, self.handle)
+                return out
+            self._grow_capacity()
+        raise _lib.QnepError(_lib.QNEP_ERR_NBR_OVERFLOW, "neighbour list overflow after retries")
+
+    def _grow_capacity(self):
+        cur = getattr(self, "_caps", (0, 0))
+        cl = max(64, int(cur[0] * 1.5) if cur[0] else 256)
+        ca = max(32, int(cur[1] * 1.5) if cur[1] else 96)
+        self._caps = (cl, ca)
+        self.set_capacity(cl, ca)
+
+    def compute_host(self, positions: np.ndarray, types: np.ndarray, box, forces=True, bec=True,
+                     charges=True, virial=True) -> dict:
+        """End-to-end call on host arrays through ``qnep_compute_host`` (copies inside)."""
+        pos = np.ascontiguousarray(positions, dtype=np.float32)
+        typ = np.ascontiguousarray(types, dtype=np.int32)
+        n = len(pos)
+        res = {"scalars": np.zeros(_lib.QNEP_NSCALARS)}
+        if forces:
+            res["forces"] = np.empty((n, 3), np.float32)
+        if bec:
+            res["bec"] = np.empty((n, 3, 3), np.float32)
+        if charges:
+            res["charges"] = np.empty(n, np.float32)
+
+        def ptr(name):
+            a = res.get(name)
+            return a.ctypes.data if a is not None else None
+
+        oc = _lib.OutputsC(ptr("scalars"), ptr("forces"), ptr("charges"), ptr("bec"), None, None, None,
+                           1 if virial else 0)
+        self._set_box(box)
+        st = self.lib.qnep_compute_host(self.handle, n, pos.ctypes.data, typ.ctypes.data, self._box,
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                        ctypes.byref(oc))
+        _lib.check(st, self.handle)
+        return res
