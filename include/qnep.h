@@ -164,6 +164,37 @@ qnep_status qnep_set_profiling(qnep_model* m, int enable);
 qnep_status qnep_stage_times(qnep_model* m, float* ms_out, int max_stages, int* n_calls);
 const char* qnep_stage_name(int stage);
 
+/* Reciprocal-space Ewald sum of given charges that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory -- host programs that give all of the GPU's memory
+ * to their own pool allocator and forbid allocations by libraries, and
+ * time-critical loops where cudaMalloc / cudaFree would synchronise the device.
+ * It runs the kernels of the reciprocal-space stage of qnep_compute on its
+ * inputs, with every scratch buffer in one fixed-size __device__ array (about
+ * 10 MB, held by each GPU that loads the library until the process exits).
+ *   positions:     device [N][3] float32 (A)         charges: device [N] float32 (e)
+ *   box:           host double[9], orthorhombic       alpha, kmax: as in qnep_elec
+ *   potential:     device [N] phi^k_i = dU^k/dq_i (V), or NULL
+ *   forces:        device [N][3] static reciprocal-space forces (eV/A), or NULL
+ *   energy_virial: device [10] doubles: U^k, then the 3x3 static k-space virial, or NULL
+ *   err, err_len:  optional host buffer for a message when the call fails
+ * Limits: N <= QNEP_NOALLOC_MAX_ATOMS, at most QNEP_NOALLOC_MAX_PHASE phase
+ * factors per atom ((floor(kmax Lx/2pi)+1) + 2 floor(kmax Ly/2pi) + 1 +
+ * 2 floor(kmax Lz/2pi) + 8, rounded up to odd) and QNEP_NOALLOC_MAX_KPAD padded
+ * half-space wave vectors; larger inputs return QNEP_ERR_UNSUPPORTED before any
+ * GPU work.  The charges are used as given (no total-charge correction).
+ * The first call on a device (with that device current) looks up the array's
+ * address with cudaGetSymbolAddress; make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (what must start
+ * at zero is cleared by each call); calls that overlap on the GPU race. */
+#define QNEP_NOALLOC_MAX_ATOMS 8192
+#define QNEP_NOALLOC_MAX_PHASE 128
+#define QNEP_NOALLOC_MAX_KPAD 32768
+qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const float* charges,
+                                      const double box[9], double alpha, double kmax, float* potential,
+                                      float* forces, double* energy_virial, void* stream, char* err,
+                                      size_t err_len);
+
 void        qnep_destroy(qnep_model* m);
 const char* qnep_status_string(qnep_status s);
 const char* qnep_last_error(qnep_model* m);   /* detail of the last failing call */

@@ -1,0 +1,71 @@
+"""qnep_ewald_kspace_noalloc against the reciprocal-space part of qnep_compute.
+
+The entry point serves callers that must not allocate device memory (a host
+program that owns all GPU memory through its own pool, or a time-critical loop
+where cudaMalloc would synchronise the device).  This test calls it through the
+C ABI twice in a row on the charges and positions of a mode-2 Ewald force call
+(mode 2 has no real-space or self term, so the existing entry point's potential
+is exactly the reciprocal-space potential) and compares potential and energy
+with the tolerances of the parity tests.  The file is named so that pytest
+collects it last; it also runs alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _entry(lib):
+    f = lib.qnep_ewald_kspace_noalloc
+    p = ctypes.c_void_p
+    f.argtypes = [ctypes.c_int, p, p, p, ctypes.c_double, ctypes.c_double, p, p, p, p, ctypes.c_char_p,
+                  ctypes.c_size_t]
+    f.restype = ctypes.c_int
+    return f
+
+
+def test_noalloc_matches_qnep_compute_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19034_gb300 import _lib
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
+
+    lib = _lib.load()
+    fn = _entry(lib)
+    dev = torch.device("cuda:0")
+    sysm, hp, params, _ = wl.config_water_small()
+    elec = wl.Elec(mode=2, kind="ewald")
+    model = QNEP(hp, params, elec)
+    pos = torch.tensor(sysm.positions, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    ref = model.compute(pos, typ, sysm.box, potential=True)
+    torch.cuda.synchronize()
+    ref_sc = parse_scalars(ref["scalars"])
+    n = sysm.n_atoms
+    box = (ctypes.c_double * 9)(*np.asarray(sysm.box, np.float64).ravel())
+    err = ctypes.create_string_buffer(256)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        phi = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+        force = torch.full((n, 3), float("nan"), dtype=torch.float32, device=dev)
+        ev = torch.full((10,), float("nan"), dtype=torch.float64, device=dev)
+        st = fn(n, pos.data_ptr(), ref["charges"].data_ptr(), box, elec.alpha, elec.kmax, phi.data_ptr(),
+                force.data_ptr(), ev.data_ptr(), stream, err, len(err))
+        assert st == 0, err.value.decode()
+        torch.cuda.synchronize()
+        assert abs(ev[0].item() - ref_sc["e_kspace"]) / n <= 1e-6
+        assert (phi - ref["potential"]).abs().max().item() <= 2e-5
+        assert torch.isfinite(force).all()
+        assert abs(force.double().sum(0)).max().item() < 1e-3
+    # sizes beyond the fixed array are refused before any GPU work, with a message
+    big = torch.zeros((8193, 3), dtype=torch.float32, device=dev)
+    q = torch.zeros(8193, dtype=torch.float32, device=dev)
+    st = fn(8193, big.data_ptr(), q.data_ptr(), box, elec.alpha, elec.kmax, None, None, None, stream, err, len(err))
+    assert st == _lib.QNEP_ERR_UNSUPPORTED and b"QNEP_NOALLOC_MAX_ATOMS" in err.value
+    model.close()
