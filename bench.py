@@ -232,9 +232,10 @@ def run_ours(args):
     return line
 
 
-# kernels of one Ewald force call with forces + BEC: bin(4), neighbours, descriptor
-# forward, phases, S(k), S(k) finalize, field, backward, finalize atoms, finalize scalars
-KERNELS_PER_CALL = 13
+# kernels of one Ewald force call with forces + BEC (warp-per-atom path): k_bin, k_scan,
+# k_fill, k_order, k_nbr_desc_coop, k_real (second stream), k_sk (with its fused
+# finalisation), k_field_k, k_desc_bwd_coop, k_finalize
+KERNELS_PER_CALL = 10
 
 
 def _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind):
@@ -245,10 +246,10 @@ def _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind):
     nk = _ewald_kcount(sysm.box, elec.kmax)
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x FMA x clock
-    if name in ("field", "ewald_structure_factor"):
+    if name in ("field_kspace", "ewald_structure_factor"):
         # algorithmic FP32 work: per (atom, half-space k) one complex multiply-accumulate
         # for S(k) (8 flop) or potential + force (16 flop)
-        flop = n * nk * (16 if name == "field" else 8)
+        flop = n * nk * (16 if name == "field_kspace" else 8)
         achieved = flop / (ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None, "ms": ms,

@@ -154,6 +154,12 @@ qnep_status qnep_sync_status(qnep_model* m, void* stream);
 /* Change the neighbour-list capacities (entries per atom); 0 keeps the value. */
 qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
 
+/* Kernel family for the per-atom stages: QNEP_PATH_AUTO picks warp-per-atom
+ * kernels up to 65536 atoms and thread-per-atom kernels above; the others force
+ * one family (both compute the same quantities).  Used by the tuner and tests. */
+enum { QNEP_PATH_AUTO = 0, QNEP_PATH_WARP = 1, QNEP_PATH_THREAD = 2 };
+qnep_status qnep_set_path(qnep_model* m, int path);
+
 /* Stage timers (tracing).  When enabled, every qnep_compute records CUDA events
  * around each stage on its stream and accumulates the elapsed times.
  * qnep_stage_times synchronizes, writes up to max_stages accumulated times (ms)

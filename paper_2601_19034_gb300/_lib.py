@@ -26,6 +26,9 @@ QNEP_PREC_MLP_BF16 = 1
 QNEP_PREC_MLP_TF32 = 2
 QNEP_NSCALARS = 20
 QNEP_NSTAGES = 10
+QNEP_PATH_AUTO = 0
+QNEP_PATH_WARP = 1
+QNEP_PATH_THREAD = 2
 SCALAR_NAMES = {
     "energy": 0, "e_nep": 1, "e_real": 2, "e_kspace": 3, "e_self": 4,
     "virial": slice(5, 14), "polarization": slice(14, 17), "qtilde_sum": 17, "phi_mean": 18, "status": 19,
@@ -71,6 +74,8 @@ def _declare(lib):
     lib.qnep_compute_host.restype = i
     lib.qnep_sync_status.argtypes = [p, p]
     lib.qnep_sync_status.restype = i
+    lib.qnep_set_path.argtypes = [p, i]
+    lib.qnep_set_path.restype = i
     lib.qnep_set_capacity.argtypes = [p, i, i]
     lib.qnep_set_capacity.restype = i
     lib.qnep_destroy.argtypes = [p]

@@ -2,6 +2,7 @@
 // launch sequence of one force call (see include/qnep.h for the contract).
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,9 +21,12 @@ struct qnep_model {
     float* d_params = nullptr;
     float sqrt_eps = 1.f;
     int cap_list = 0, cap_ang = 0;          // 0: automatic from the density
+    int path = QNEP_PATH_AUTO;
     // per-atom workspaces (grow only)
     int n_alloc = 0, cl_alloc = 0, ca_alloc = 0, nph_alloc = 0;
-    float4* pos4 = nullptr;
+    float4* pos4 = nullptr;        // wrapped positions, input order
+    float4* spos4 = nullptr;       // wrapped positions sorted by cell (working order)
+    int* sidx = nullptr;           // input index of each sorted slot
     int* cell_of = nullptr;
     int* cell_atoms = nullptr;
     int* nbr_list = nullptr;
@@ -34,8 +38,7 @@ struct qnep_model {
     float* dq = nullptr;
     float* u = nullptr;
     float* q = nullptr;
-    float* phi = nullptr;
-    float* acc12 = nullptr;
+    float4* fields = nullptr;      // kfield [n] | rfield [n] | acc12 [3n] (see desc_math.cuh)
     float2* phase = nullptr;
     // cells
     int ncell_alloc = 0;
@@ -43,7 +46,11 @@ struct qnep_model {
     int* cell_start = nullptr;
     int* cell_fill = nullptr;
     Accum* d_acc = nullptr;
-    unsigned int* h_status = nullptr;       // pinned mirror of the device status word
+    unsigned int* h_status = nullptr;       // mapped pinned word written by the last kernel
+    unsigned int* d_status = nullptr;       // its device alias
+    unsigned int* fin_done = nullptr;       // last-block counter of the finalize kernel
+    unsigned int* sk_done = nullptr;        // last-block counters of the structure-factor kernel
+    int sk_done_alloc = 0;
     // geometry / Ewald tables, rebuilt when the box changes
     bool have_box = false;
     double box[9]{};
@@ -52,6 +59,7 @@ struct qnep_model {
     int nk_alloc = 0, ncol_alloc = 0, nchunk_alloc = 0;
     int4* d_col = nullptr;
     int* d_chunk_col = nullptr;
+    int* d_chunk_order = nullptr;
     float* d_kg = nullptr;
     double2* d_S = nullptr;
     float2* d_C = nullptr;
@@ -61,9 +69,13 @@ struct qnep_model {
     int* io_types = nullptr;
     float* io_out[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double* io_scalars = nullptr;
+    // second stream for the real-space kernel (runs beside the structure factor)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // stage timers
     bool profiling = false;
-    cudaEvent_t ev[QNEP_NSTAGES + 1]{};
+    cudaEvent_t ev_start[QNEP_NSTAGES]{}, ev_end[QNEP_NSTAGES]{};
+    bool recorded[QNEP_NSTAGES]{};
     double stage_ms[QNEP_NSTAGES]{};
     int timed_calls = 0;
     bool pending = false;
@@ -151,8 +163,19 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
     }
     if (nch > m->nchunk_alloc) {
         CK(grow(&m->d_chunk_col, nch));
+        CK(grow(&m->d_chunk_order, nch));
         m->nchunk_alloc = nch;
     }
+    // processing order of the chunks: by the n3 window they cover (stable), so the
+    // lanes of a warp in the structure-factor kernel mostly read the same Z factors
+    std::vector<int> order(nch);
+    for (int gi = 0; gi < nch; ++gi) order[gi] = gi;
+    auto zstart = [&](int gi) {
+        const int4& c = cols[chunk_col[gi]];
+        return c.z + (8 * gi - c.w);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return zstart(a) < zstart(b); });
+    if (nch) CK(cudaMemcpy(m->d_chunk_order, order.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
     if (nk > m->nk_alloc) {
         CK(grow(&m->d_kg, nk));
         CK(grow(&m->d_S, nk));
@@ -182,6 +205,7 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
     t.alpha = (float)alpha;
     t.col = m->d_col;
     t.chunk_col = m->d_chunk_col;
+    t.chunk_order = m->d_chunk_order;
     t.kg = m->d_kg;
     t.S = m->d_S;
     t.C = m->d_C;
@@ -220,11 +244,18 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             CK(grow(&m->cell_count, g.ncells + 1));
             CK(grow(&m->cell_start, g.ncells + 1));
             CK(grow(&m->cell_fill, g.ncells + 1));
+            CK(cudaMemset(m->cell_count, 0, sizeof(int) * (g.ncells + 1)));
             m->ncell_alloc = g.ncells + 1;
         }
         if (m->es.mode != 0 && m->es.kind == QNEP_EWALD) {
             qnep_status s = build_ewald_table(m, L);
             if (s != QNEP_OK) return s;
+            int groups = (m->tab.nchunk + 31) / 32 + 1;
+            if (groups > m->sk_done_alloc) {
+                CK(grow(&m->sk_done, groups));
+                CK(cudaMemset(m->sk_done, 0, sizeof(unsigned int) * groups));
+                m->sk_done_alloc = groups;
+            }
         }
         std::memcpy(m->box, box, sizeof(double) * 9);
         m->have_box = true;
@@ -249,6 +280,8 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
         CK(grow(&m->nbr_ang, (size_t)nca * na));
         if (need_atoms) {
             CK(grow(&m->pos4, na));
+            CK(grow(&m->spos4, na));
+            CK(grow(&m->sidx, na));
             CK(grow(&m->cell_of, na));
             CK(grow(&m->cell_atoms, na));
             CK(grow(&m->cnt_list, (size_t)MAX_SPECIES * na));
@@ -258,10 +291,10 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             CK(grow(&m->dq, (size_t)NDES * na));
             CK(grow(&m->u, na));
             CK(grow(&m->q, na));
-            CK(grow(&m->phi, na));
-            CK(grow(&m->acc12, (size_t)12 * na));
+            CK(grow(&m->fields, (size_t)5 * na));
         }
-        if (need_atoms || nnph > m->nph_alloc) CK(grow(&m->phase, (size_t)std::max(nnph, 1) * na));
+        // +2 entries: bulk copies round the last tile up to 16 bytes
+        if (need_atoms || nnph > m->nph_alloc) CK(grow(&m->phase, (size_t)std::max(nnph, 1) * na + 2));
         m->n_alloc = na;
         m->cl_alloc = ncl;
         m->ca_alloc = nca;
@@ -272,26 +305,36 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
 }
 
 const char* kStageNames[QNEP_NSTAGES] = {"cell_bin", "neighbors", "descriptor_forward", "ewald_phases",
-                                         "ewald_structure_factor", "ewald_sk_finalize", "field",
+                                         "ewald_structure_factor", "field_kspace", "real_space",
                                          "descriptor_backward", "finalize", "pppm"};
 
-// Accumulate the event times of the previous profiled call (events are complete
-// once the stream has passed them; the caller synchronizes before reading).
+// Systems up to this size use the warp-per-atom kernels (descriptor_coop.cu).
+constexpr int kCoopMaxAtoms = 65536;
+
+// Accumulate the event times of the previous profiled call (its events are
+// complete once the stream has been synchronized).
 void harvest(qnep_model* m) {
     if (!m->pending) return;
     for (int k = 0; k < QNEP_NSTAGES; ++k) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, m->ev[k], m->ev[k + 1]) == cudaSuccess) m->stage_ms[k] += ms;
+        if (m->recorded[k] && cudaEventElapsedTime(&ms, m->ev_start[k], m->ev_end[k]) == cudaSuccess)
+            m->stage_ms[k] += ms;
+        m->recorded[k] = false;
     }
     m->timed_calls += 1;
     m->pending = false;
 }
 
-struct StageMark {
+struct StageTimer {
     qnep_model* m;
-    cudaStream_t st;
-    void operator()(int k) const {
-        if (m->profiling) cudaEventRecord(m->ev[k], st);
+    void begin(int k, cudaStream_t s) const {
+        if (m->profiling) cudaEventRecord(m->ev_start[k], s);
+    }
+    void end(int k, cudaStream_t s) const {
+        if (m->profiling) {
+            cudaEventRecord(m->ev_end[k], s);
+            m->recorded[k] = true;
+        }
     }
 };
 
@@ -303,8 +346,11 @@ const char* qnep_stage_name(int stage) { return (stage >= 0 && stage < QNEP_NSTA
 
 qnep_status qnep_set_profiling(qnep_model* m, int enable) {
     if (!m) return QNEP_ERR_ARG;
-    if (enable && !m->ev[0]) {
-        for (int k = 0; k <= QNEP_NSTAGES; ++k) CK(cudaEventCreate(&m->ev[k]));
+    if (enable && !m->ev_start[0]) {
+        for (int k = 0; k < QNEP_NSTAGES; ++k) {
+            CK(cudaEventCreate(&m->ev_start[k]));
+            CK(cudaEventCreate(&m->ev_end[k]));
+        }
     }
     m->profiling = enable != 0;
     return QNEP_OK;
@@ -375,9 +421,27 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
     CK(cudaMemcpy(m->d_params, params_host, sizeof(float) * n_params, cudaMemcpyHostToDevice));
     CK(cudaMalloc((void**)&m->d_acc, sizeof(Accum)));
     CK(cudaMemset(m->d_acc, 0, sizeof(Accum)));
-    CK(cudaMallocHost((void**)&m->h_status, sizeof(unsigned int)));
+    CK(cudaHostAlloc((void**)&m->h_status, sizeof(unsigned int), cudaHostAllocMapped));
     *m->h_status = 0;
+    CK(cudaHostGetDevicePointer((void**)&m->d_status, m->h_status, 0));
+    CK(cudaMalloc((void**)&m->fin_done, sizeof(unsigned int)));
+    CK(cudaMemset(m->fin_done, 0, sizeof(unsigned int)));
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            set_num_sms(sms);
+    }
+    CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
     *out = m;
+    return QNEP_OK;
+}
+
+qnep_status qnep_set_path(qnep_model* m, int path) {
+    if (!m || path < QNEP_PATH_AUTO || path > QNEP_PATH_THREAD) return QNEP_ERR_ARG;
+    m->path = path;
     return QNEP_OK;
 }
 
@@ -404,7 +468,6 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
     cudaStream_t st = (cudaStream_t)stream;
     qnep_status s = prepare(m, n, box, st);
     if (s != QNEP_OK) return s;
-    const Geom& g = m->geom;
     const bool ewald = m->es.mode != 0 && m->es.kind == QNEP_EWALD;
     const bool backward = out->forces || out->bec || out->want_virial;
     const bool want_bec = out->bec != nullptr;
@@ -414,42 +477,89 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
     ElecConst ec{m->es.mode, m->es.kind, (float)m->es.alpha, (float)m->es.q_total};
 
     if (m->profiling) {
-        CK(cudaStreamSynchronize(st));   // the previous call's events are complete
+        CK(cudaDeviceSynchronize());   // the previous call's events (both streams) are complete
         harvest(m);
     }
-    StageMark mark{m, st};
-    mark(0);
-    CK(cudaMemsetAsync(m->d_acc, 0, sizeof(Accum), st));
+    Geom g = m->geom;
+    const bool coop = m->path == QNEP_PATH_WARP || (m->path == QNEP_PATH_AUTO && n <= kCoopMaxAtoms);
+    if (coop) {   // atom-major lists for the warp-per-atom kernels
+        g.list_sa = cl;
+        g.list_se = 1;
+        g.ang_sa = ca;
+        g.ang_se = 1;
+    } else {      // entry-major lists for the thread-per-atom kernels
+        g.list_sa = 1;
+        g.list_se = n;
+        g.ang_sa = 1;
+        g.ang_se = n;
+    }
+    const FieldIn fin{m->fields, m->fields + n, m->es.mode, (float)m->es.alpha, q_target};
+    float* acc12 = reinterpret_cast<float*>(m->fields + 2 * (size_t)n);
+    float4* kfield = m->fields;
+    float4* rfield = m->fields + n;
+    StageTimer tm{m};
+    tm.begin(0, st);
     launch_bin(positions, types, n, g, m->pos4, m->cell_of, m->cell_count, m->cell_start, m->cell_fill, m->cell_atoms,
-               st);
-    mark(1);
-    launch_neighbors(m->pos4, m->cell_start, m->cell_atoms, n, m->hp.n_species, g, cl, ca, m->nbr_list, m->cnt_list,
-                     m->nbr_ang, m->cnt_ang, m->d_acc, st);
-    mark(2);
-    launch_descriptor_forward(m->pos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params, m->lay,
-                              backward ? m->ang : nullptr, backward ? m->du : nullptr, backward ? m->dq : nullptr,
-                              m->u, m->q, out->descriptor, m->d_acc, st);
-    mark(3);
-    if (ewald) launch_ewald_phases(m->pos4, n, m->tab, st);
-    mark(4);
-    if (ewald) launch_ewald_sk(m->q, m->d_acc, n, q_target, m->tab, st);
-    mark(5);
-    if (ewald) launch_ewald_sk_finalize(m->tab, m->d_acc, st);
-    mark(6);
-    launch_field(m->pos4, positions, m->q, m->nbr_list, m->cnt_list, n, m->hp.n_species, g, ec, q_target, m->sqrt_eps,
-                 ewald, m->tab, nullptr, m->phi, m->acc12, out->charges, m->d_acc, st);
-    mark(7);
-    if (backward)
-        launch_descriptor_backward(m->pos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
-                                   m->lay, m->ang, m->du, m->dq, m->phi, m->d_acc, want_bec, m->acc12, m->d_acc, st);
-    mark(8);
-    launch_finalize_atoms(m->acc12, n, out->forces, out->bec, m->phi, out->potential, st);
-    if (out->site_energy) CK(cudaMemcpyAsync(out->site_energy, m->u, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-    launch_finalize_scalars(m->d_acc, n, m->sqrt_eps, out->scalars, st);
-    mark(9);
-    mark(10);
+               m->spos4, m->sidx, m->d_acc, ewald ? m->tab.S : nullptr, ewald ? m->tab.nk : 0, st);
+    tm.end(0, st);
+    if (coop) {
+        tm.begin(2, st);
+        launch_nbr_desc_coop(m->spos4, m->cell_start, m->sidx, n, g, m->d_params, m->lay, cl, ca, m->nbr_list,
+                             m->cnt_list, m->nbr_ang, m->cnt_ang, backward ? m->ang : nullptr,
+                             backward ? m->du : nullptr, m->dq, m->u, m->q, out->descriptor, m->tab, ewald, m->fields,
+                             m->d_acc, st);
+        tm.end(2, st);
+    } else {
+        tm.begin(1, st);
+        launch_neighbors(m->spos4, m->cell_start, n, m->hp.n_species, g, cl, ca, m->nbr_list, m->cnt_list, m->nbr_ang,
+                         m->cnt_ang, m->d_acc, st);
+        tm.end(1, st);
+        tm.begin(2, st);
+        launch_descriptor_forward(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
+                                  m->lay, backward ? m->ang : nullptr, backward ? m->du : nullptr,
+                                  backward ? m->dq : nullptr, m->u, m->q, out->descriptor, m->sidx, m->fields,
+                                  m->d_acc, st);
+        tm.end(2, st);
+        tm.begin(3, st);
+        if (ewald) launch_ewald_phases(m->spos4, n, m->tab, st);
+        tm.end(3, st);
+    }
+    const bool real = m->es.mode == 1;
+    if (real) {   // real space on the second stream, beside the reciprocal-space kernels
+        CK(cudaEventRecord(m->ev_fork, st));
+        CK(cudaStreamWaitEvent(m->aux, m->ev_fork, 0));
+        tm.begin(6, m->aux);
+        launch_real(m->spos4, m->q, m->nbr_list, m->cnt_list, n, m->hp.n_species, g, (float)m->es.alpha, q_target,
+                    m->d_acc, rfield, m->d_acc, m->aux);
+        tm.end(6, m->aux);
+        CK(cudaEventRecord(m->ev_join, m->aux));
+    }
+    if (ewald) {
+        tm.begin(4, st);
+        launch_ewald_sk_fused(m->q, m->d_acc, n, q_target, m->tab, m->sk_done, st);
+        tm.end(4, st);
+        tm.begin(5, st);
+        launch_field_k(n, m->tab, kfield, m->d_acc, st);
+        tm.end(5, st);
+    }
+    if (real) CK(cudaStreamWaitEvent(st, m->ev_join, 0));
+    if (backward) {
+        tm.begin(7, st);
+        if (coop)
+            launch_desc_bwd_coop(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params, m->lay,
+                                 m->ang, m->du, m->dq, m->q, fin, m->d_acc, want_bec, acc12, m->d_acc, st);
+        else
+            launch_descriptor_backward(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
+                                       m->lay, m->ang, m->du, m->dq, m->q, fin, m->d_acc, want_bec, acc12, m->d_acc,
+                                       st);
+        tm.end(7, st);
+    }
+    tm.begin(8, st);
+    launch_finalize(acc12, n, m->sidx, positions, m->q, q_target, m->sqrt_eps, ec, kfield, rfield, out->forces,
+                    out->bec, out->charges, out->potential, m->u, out->site_energy, m->d_acc, out->scalars,
+                    m->d_status, m->fin_done, st);
+    tm.end(8, st);
     if (m->profiling) m->pending = true;
-    CK(cudaMemcpyAsync(m->h_status, &m->d_acc->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
     return QNEP_OK;
 }
@@ -502,16 +612,21 @@ qnep_status qnep_compute_host(qnep_model* m, int n, const float* positions_host,
 
 void qnep_destroy(qnep_model* m) {
     if (!m) return;
-    void* bufs[] = {m->d_params, m->pos4, m->cell_of, m->cell_atoms, m->nbr_list, m->cnt_list, m->nbr_ang,
-                    m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phi, m->acc12, m->phase, m->cell_count,
-                    m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_kg, m->d_S, m->d_C,
+    void* bufs[] = {m->d_params, m->pos4, m->spos4, m->sidx, m->fin_done, m->sk_done, m->fields, m->cell_of, m->cell_atoms, m->nbr_list, m->cnt_list, m->nbr_ang,
+                    m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phase, m->cell_count,
+                    m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_chunk_order, m->d_kg, m->d_S, m->d_C,
                     m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
                     m->io_out[4], m->io_out[5]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->h_status) cudaFreeHost(m->h_status);
-    for (int k = 0; k <= QNEP_NSTAGES; ++k)
-        if (m->ev[k]) cudaEventDestroy(m->ev[k]);
+    for (int k = 0; k < QNEP_NSTAGES; ++k) {
+        if (m->ev_start[k]) cudaEventDestroy(m->ev_start[k]);
+        if (m->ev_end[k]) cudaEventDestroy(m->ev_end[k]);
+    }
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_join) cudaEventDestroy(m->ev_join);
+    if (m->aux) cudaStreamDestroy(m->aux);
     delete m;
 }
 

@@ -16,139 +16,11 @@
 // (partial forces of Sec. II.C: F^NEP_ij plus the real / reciprocal / self
 // dynamic-charge terms, and a_ij = dq~_i/dr_ij for Eq. bec_2), recomputes
 // dD/dr_ij per neighbour entry and scatters the partial forces.
-#include "qnep_internal.cuh"
+#include "desc_math.cuh"
 
 namespace qnep {
 
 namespace {
-
-__constant__ float c_wlm[NLM] = {1.f, 1.f, 1.f,
-                                 0.25f, 3.f, 3.f, 0.75f, 3.f,
-                                 0.25f, 0.375f, 0.375f, 3.75f, 15.f, 0.625f, 0.625f,
-                                 1.f / 64.f, 0.625f, 0.625f, 0.3125f, 1.25f, 4.375f, 4.375f, 35.f / 64.f, 8.75f};
-
-__device__ __forceinline__ void harmonics(float x, float y, float z, float Y[NLM]) {
-    float x2 = x * x, y2 = y * y, z2 = z * z;
-    Y[0] = z; Y[1] = x; Y[2] = y;
-    Y[3] = 3.f * z2 - 1.f; Y[4] = x * z; Y[5] = y * z; Y[6] = x2 - y2; Y[7] = x * y;
-    float a5 = 5.f * z2 - 1.f;
-    Y[8] = z * (5.f * z2 - 3.f); Y[9] = x * a5; Y[10] = y * a5; Y[11] = z * (x2 - y2); Y[12] = x * y * z;
-    Y[13] = x * (x2 - 3.f * y2); Y[14] = y * (3.f * x2 - y2);
-    float a7 = 7.f * z2 - 3.f, b7 = 7.f * z2 - 1.f;
-    Y[15] = (35.f * z2 - 30.f) * z2 + 3.f; Y[16] = x * z * a7; Y[17] = y * z * a7; Y[18] = (x2 - y2) * b7;
-    Y[19] = x * y * b7; Y[20] = z * x * (x2 - 3.f * y2); Y[21] = z * y * (3.f * x2 - y2);
-    Y[22] = x2 * x2 - 6.f * x2 * y2 + y2 * y2; Y[23] = x * y * (x2 - y2);
-}
-
-// g = sum_lm psi_lm grad_u Y_lm(u) (gradient of the polynomials, not yet projected)
-__device__ __forceinline__ void harmonics_grad(float x, float y, float z, const float p[NLM], float& gx,
-                                               float& gy, float& gz) {
-    float x2 = x * x, y2 = y * y, z2 = z * z;
-    gx = p[1] + p[4] * z + p[6] * 2.f * x + p[7] * y;
-    gy = p[2] + p[5] * z - p[6] * 2.f * y + p[7] * x;
-    gz = p[0] + p[3] * 6.f * z + p[4] * x + p[5] * y;
-    float a5 = 5.f * z2 - 1.f;
-    gx += p[9] * a5 + p[11] * 2.f * x * z + p[12] * y * z + p[13] * 3.f * (x2 - y2) + p[14] * 6.f * x * y;
-    gy += p[10] * a5 - p[11] * 2.f * y * z + p[12] * x * z - p[13] * 6.f * x * y + p[14] * 3.f * (x2 - y2);
-    gz += p[8] * (15.f * z2 - 3.f) + p[9] * 10.f * x * z + p[10] * 10.f * y * z + p[11] * (x2 - y2) + p[12] * x * y;
-    float a7 = 7.f * z2 - 3.f, b7 = 7.f * z2 - 1.f, zc = z * a7;
-    gx += p[16] * zc + p[18] * 2.f * x * b7 + p[19] * y * b7 + p[20] * 3.f * z * (x2 - y2) + p[21] * 6.f * x * y * z +
-          p[22] * (4.f * x2 * x - 12.f * x * y2) + p[23] * (3.f * x2 * y - y2 * y);
-    gy += p[17] * zc - p[18] * 2.f * y * b7 + p[19] * x * b7 - p[20] * 6.f * x * y * z + p[21] * 3.f * z * (x2 - y2) +
-          p[22] * (4.f * y2 * y - 12.f * x2 * y) + p[23] * (x2 * x - 3.f * x * y2);
-    gz += p[15] * (140.f * z2 - 60.f) * z + p[16] * x * (21.f * z2 - 3.f) + p[17] * y * (21.f * z2 - 3.f) +
-          p[18] * 14.f * z * (x2 - y2) + p[19] * 14.f * x * y * z + p[20] * x * (x2 - 3.f * y2) +
-          p[21] * y * (3.f * x2 - y2);
-}
-
-template <int K>
-__device__ __forceinline__ void basis(float r, float rc, float f[K]) {
-    float rr = r / rc;
-    float fc = 0.5f * (1.f + cospif(rr));
-    float x = 2.f * (rr - 1.f) * (rr - 1.f) - 1.f;
-    float t0 = 1.f, t1 = x;
-    f[0] = fc;
-    if (K > 1) f[1] = 0.5f * (x + 1.f) * fc;
-#pragma unroll
-    for (int k = 2; k < K; ++k) {
-        float t2 = 2.f * x * t1 - t0;
-        f[k] = 0.5f * (t2 + 1.f) * fc;
-        t0 = t1;
-        t1 = t2;
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void basis_d(float r, float rc, float f[K], float df[K]) {
-    float rr = r / rc;
-    float s, c;
-    sincospif(rr, &s, &c);
-    float fc = 0.5f * (1.f + c);
-    float dfc = -0.5f * 3.14159265358979f / rc * s;
-    float x = 2.f * (rr - 1.f) * (rr - 1.f) - 1.f;
-    float dx = 4.f * (rr - 1.f) / rc;
-    float t0 = 1.f, t1 = x, d0 = 0.f, d1 = 1.f;
-    f[0] = fc;
-    df[0] = dfc;
-    if (K > 1) {
-        f[1] = 0.5f * (x + 1.f) * fc;
-        df[1] = 0.5f * (dx * fc + (x + 1.f) * dfc);
-    }
-#pragma unroll
-    for (int k = 2; k < K; ++k) {
-        float t2 = 2.f * x * t1 - t0;
-        float d2 = 2.f * t1 + 2.f * x * d1 - d0;   // T_k' by differentiating the recurrence
-        f[k] = 0.5f * (t2 + 1.f) * fc;
-        df[k] = 0.5f * (d2 * dx * fc + (t2 + 1.f) * dfc);
-        t0 = t1; t1 = t2; d0 = d1; d1 = d2;
-    }
-}
-
-template <int TPA>
-__device__ __forceinline__ float group_sum(float v, unsigned mask) {
-#pragma unroll
-    for (int o = TPA / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, TPA);
-    return v;
-}
-
-template <int TPA>
-__device__ __forceinline__ unsigned group_mask() {
-    if (TPA == 32) return 0xffffffffu;
-    unsigned lane = threadIdx.x & 31;
-    return ((1u << TPA) - 1u) << (lane & ~(unsigned)(TPA - 1));
-}
-
-__device__ __forceinline__ void entry_vector(const float4* __restrict__ pos4, int e, const float4& pi,
-                                             const Geom& g, float& vx, float& vy, float& vz) {
-    int j = entry_index(e);
-    float tx, ty, tz;
-    entry_shift(e, tx, ty, tz);
-    float4 pj = __ldg(&pos4[j]);
-    vx = (pj.x - pi.x) + tx * g.L[0];
-    vy = (pj.y - pi.y) + ty * g.L[1];
-    vz = (pj.z - pi.z) + tz * g.L[2];
-}
-
-// 4-body: T_n from the l = 2 expansion coefficients (unnormalised harmonics 3..7)
-__device__ __forceinline__ void tensor_from_a(const float a[5], float t[6]) {
-    // a: (3z^2-1, xz, yz, x^2-y^2, xy) sums; t: xx, yy, zz, xy, xz, yz
-    float zz = a[0] * (1.f / 3.f);
-    t[0] = 0.5f * (a[3] - zz);
-    t[1] = 0.5f * (-a[3] - zz);
-    t[2] = zz;
-    t[3] = a[4];
-    t[4] = a[1];
-    t[5] = a[2];
-}
-
-__device__ __forceinline__ void tensor_square(const float t[6], float s[6]) {
-    s[0] = t[0] * t[0] + t[3] * t[3] + t[4] * t[4];
-    s[1] = t[3] * t[3] + t[1] * t[1] + t[5] * t[5];
-    s[2] = t[4] * t[4] + t[5] * t[5] + t[2] * t[2];
-    s[3] = t[0] * t[3] + t[3] * t[1] + t[4] * t[5];
-    s[4] = t[0] * t[4] + t[3] * t[5] + t[4] * t[2];
-    s[5] = t[3] * t[4] + t[1] * t[5] + t[5] * t[2];
-}
 
 template <int TPA>
 __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos4, const int* __restrict__ nbr_list,
@@ -158,6 +30,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
                                                   float* __restrict__ ang_coef, float* __restrict__ du,
                                                   float* __restrict__ dq, float* __restrict__ u_out,
                                                   float* __restrict__ q_out, float* __restrict__ des_out,
+                                                  const int* __restrict__ sidx, float4* __restrict__ fields,
                                                   Accum* __restrict__ acc) {
     extern __shared__ float sp[];
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
@@ -184,7 +57,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
 #pragma unroll
             for (int k = 0; k < KR; ++k) b[k] = 0.f;
             for (int e = lane; e < cnt; e += TPA) {
-                int ent = __ldg(&nbr_list[(size_t)(off + e) * n + i]);
+                int ent = list_entry(nbr_list, i, off + e, g.list_sa, g.list_se);
                 float vx, vy, vz;
                 entry_vector(pos4, ent, pi, g, vx, vy, vz);
                 float r2 = vx * vx + vy * vy + vz * vz;
@@ -214,7 +87,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
             const int cnt = __ldg(&cnt_ang[(size_t)s * n + i]);
             const float* c = sp + lay.c_angular + ((ti * S + s) * NA) * KA;
             for (int e = lane; e < cnt; e += TPA) {
-                int ent = __ldg(&nbr_ang[(size_t)(off + e) * n + i]);
+                int ent = list_entry(nbr_ang, i, off + e, g.ang_sa, g.ang_se);
                 float vx, vy, vz;
                 entry_vector(pos4, ent, pi, g, vx, vy, vz);
                 float r = sqrtf(vx * vx + vy * vy + vz * vz);
@@ -286,7 +159,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
         for (int v = 0; v < NDES; ++v) d[v] *= scaler[v];
         if (des_out && lane == 0) {
 #pragma unroll
-            for (int v = 0; v < NDES; ++v) des_out[(size_t)i * NDES + v] = d[v];
+            for (int v = 0; v < NDES; ++v) des_out[(size_t)sidx[i] * NDES + v] = d[v];
         }
 
         // network and its input gradients (hidden units split over the TPA lanes)
@@ -336,6 +209,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
             su = (double)uu;
             sq = (double)qq;
         }
+        for (int part = lane; part < 5; part += TPA) zero_atom_fields(fields, n, i, part);
     }
     // warp reduction of the FP64 energy / charge sums, one atomic per warp
 #pragma unroll
@@ -380,9 +254,9 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
                                                   const int* __restrict__ cnt_ang, int n, Geom g,
                                                   const float* __restrict__ params, ParamLayout lay,
                                                   const float* __restrict__ ang_coef, const float* __restrict__ du,
-                                                  const float* __restrict__ dqp, const float* __restrict__ phi,
-                                                  const Accum* __restrict__ acc_in, float4* __restrict__ acc12,
-                                                  Accum* __restrict__ acc) {
+                                                  const float* __restrict__ dqp, const float* __restrict__ q_raw,
+                                                  FieldIn fin, const Accum* __restrict__ acc_in,
+                                                  float4* __restrict__ acc12, Accum* __restrict__ acc) {
     extern __shared__ float sm[];
     float* sp = sm;
     float* sphi = sm + ((lay.total + 3) & ~3);
@@ -400,8 +274,9 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
         const float4 pi = __ldg(&pos4[i]);
         const int ti = __float_as_int(pi.w);
         const float seps = sp[lay.sqrt_eps];
-        const float phibar = (float)(acc_in->sum_phi / (double)n);
-        const float dphi = phi[i] - phibar;
+        float qc, phi_i, phibar;
+        assemble_potential(fin, acc_in, q_raw, i, n, qc, phi_i, phibar);
+        const float dphi = phi_i - phibar;
         float lam[NDES], kap[NDES];
 #pragma unroll
         for (int v = 0; v < NDES; ++v) {
@@ -459,7 +334,7 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
                 mk[k] = y;
             }
             for (int e = lane; e < cnt; e += TPA) {
-                int ent = __ldg(&nbr_list[(size_t)(off + e) * n + i]);
+                int ent = list_entry(nbr_list, i, off + e, g.list_sa, g.list_se);
                 float vx, vy, vz;
                 entry_vector(pos4, ent, pi, g, vx, vy, vz);
                 float r2 = vx * vx + vy * vy + vz * vz;
@@ -487,7 +362,7 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
             const int cnt = __ldg(&cnt_ang[(size_t)s * n + i]);
             const float* c = sp + lay.c_angular + ((ti * S + s) * NA) * KA;
             for (int e = lane; e < cnt; e += TPA) {
-                int ent = __ldg(&nbr_ang[(size_t)(off + e) * n + i]);
+                int ent = list_entry(nbr_ang, i, off + e, g.ang_sa, g.ang_se);
                 float vx, vy, vz;
                 entry_vector(pos4, ent, pi, g, vx, vy, vz);
                 float r = sqrtf(vx * vx + vy * vy + vz * vz);
@@ -550,11 +425,13 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
             }
         }
         if (lane == 0) {
-            atomicAdd(&acc12[3 * i + 0], make_float4(fi[0], fi[1], fi[2], zi[0]));
-            if (BEC) {
-                atomicAdd(&acc12[3 * i + 1], make_float4(zi[1], zi[2], zi[3], zi[4]));
-                atomicAdd(&acc12[3 * i + 2], make_float4(zi[5], zi[6], zi[7], zi[8]));
-            }
+            // static electrostatic force q_i F^k / q + F^r and the BEC diagonal q~^c
+            const float4 kf = fin.kfield[i], rf = fin.rfield[i];
+            const float qt = seps * qc;
+            atomicAdd(&acc12[3 * i + 0], make_float4(fi[0] + fmaf(qc, kf.x, rf.x), fi[1] + fmaf(qc, kf.y, rf.y),
+                                                     fi[2] + fmaf(qc, kf.z, rf.z), zi[0] + qt));
+            atomicAdd(&acc12[3 * i + 1], make_float4(zi[1], zi[2], zi[3], zi[4] + qt));
+            atomicAdd(&acc12[3 * i + 2], make_float4(zi[5], zi[6], zi[7], zi[8] + qt));
         }
     }
     // block reduction of the virial, FP64 atomics
@@ -577,18 +454,19 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
 template <int TPA>
 void fwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
                 const float* params, const ParamLayout& lay, float* ang, float* du, float* dq, float* u, float* q,
-                float* des, Accum* acc, cudaStream_t st) {
+                float* des, const int* sidx, float4* fields, Accum* acc, cudaStream_t st) {
     const int threads = 128;
     long long blocks = ((long long)n * TPA + threads - 1) / threads;
     size_t smem = sizeof(float) * lay.total;
     k_desc_fwd<TPA><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq, u,
-                                                             q, des, acc);
+                                                             q, des, sidx, fields, acc);
 }
 
 template <int TPA, bool BEC>
 void bwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
                 const float* params, const ParamLayout& lay, const float* ang, const float* du, const float* dq,
-                const float* phi, const Accum* acc_in, float4* acc12, Accum* acc, cudaStream_t st) {
+                const float* q_raw, const FieldIn& fin, const Accum* acc_in, float4* acc12, Accum* acc,
+                cudaStream_t st) {
     const int threads = 128;
     long long blocks = ((long long)n * TPA + threads - 1) / threads;
     size_t smem = sizeof(float) * (((lay.total + 3) & ~3) + (threads / TPA) * PHI_STRIDE);
@@ -598,14 +476,13 @@ void bwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na,
         attr_set = true;
     }
     k_desc_bwd<TPA, BEC><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq,
-                                                                  phi, acc_in, acc12, acc);
+                                                                  q_raw, fin, acc_in, acc12, acc);
 }
 
 }  // namespace
 
 int choose_tpa(int n) {
-    // lanes per atom: enough threads to fill 152 SMs x 4 warps for small systems
-    if (n <= 8192) return 4;
+    // lanes per atom of the per-thread kernels (used for large systems)
     if (n <= 65536) return 2;
     return 1;
 }
@@ -613,42 +490,29 @@ int choose_tpa(int n) {
 void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                                const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                                float* ang_coef, float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               Accum* acc, cudaStream_t st) {
+                               const int* sidx, float4* fields, Accum* acc, cudaStream_t st) {
     if (n == 0) return;
-    int tpa = choose_tpa(n);
-    if (tpa == 4)
-        fwd_launch<4>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, acc, st);
-    else if (tpa == 2)
+    if (choose_tpa(n) == 2)
         fwd_launch<2>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, acc, st);
+                      des_out, sidx, fields, acc, st);
     else
         fwd_launch<1>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, acc, st);
+                      des_out, sidx, fields, acc, st);
 }
 
 void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                                 const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
-                                const float* ang_coef, const float* du, const float* dq, const float* phi,
-                                const Accum* acc_in, bool want_bec, float* acc12, Accum* acc, cudaStream_t st) {
+                                const float* ang_coef, const float* du, const float* dq, const float* q_raw,
+                                const FieldIn& fin, const Accum* acc_in, bool want_bec, float* acc12, Accum* acc,
+                                cudaStream_t st) {
     if (n == 0) return;
     float4* a4 = reinterpret_cast<float4*>(acc12);
-    int tpa = choose_tpa(n) >= 2 ? choose_tpa(n) : 2;
-    if (want_bec) {
-        if (tpa == 4)
-            bwd_launch<4, true>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
-                                acc_in, a4, acc, st);
-        else
-            bwd_launch<2, true>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
-                                acc_in, a4, acc, st);
-    } else {
-        if (tpa == 4)
-            bwd_launch<4, false>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
-                                 acc_in, a4, acc, st);
-        else
-            bwd_launch<2, false>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, phi,
-                                 acc_in, a4, acc, st);
-    }
+    if (want_bec)
+        bwd_launch<2, true>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, q_raw,
+                            fin, acc_in, a4, acc, st);
+    else
+        bwd_launch<2, false>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, q_raw,
+                             fin, acc_in, a4, acc, st);
 }
 
 }  // namespace qnep

@@ -13,7 +13,8 @@
 // through the adjoint of the backward kernel.  The kernel also initialises the
 // force / BEC accumulator of each atom (static force; q~^c_i on the BEC diagonal)
 // and adds the FP64 sums: sum phi, U^r = 1/2 sum q phi^r, U^s, P = sum q~^c r.
-#include "qnep_internal.cuh"
+#include "desc_math.cuh"
+#include "tma.cuh"
 
 namespace qnep {
 
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
                                                   ElecConst ec, float q_target, float seps, int ewald, EwaldTab tab,
                                                   const float* __restrict__ pppm_field, float* __restrict__ phi,
                                                   float4* __restrict__ acc12, float* __restrict__ charges_out,
-                                                  Accum* __restrict__ acc) {
+                                                  const int* __restrict__ sidx, Accum* __restrict__ acc) {
     extern __shared__ float2 stab[];
     __shared__ float red[W][8][33];
     __shared__ float wred[9][W];
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
         const float rc2 = g.rc_real * g.rc_real;
         const float al = ec.alpha;
         for (int e = w; e < total; e += W) {
-            int ent = __ldg(&nbr_list[(size_t)e * n + i]);
+            int ent = list_entry(nbr_list, i, e, g.list_sa, g.list_se);
             int j = entry_index(ent);
             float tx, ty, tz;
             entry_shift(ent, tx, ty, tz);
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
             float ph = t[0] + t[1] + phs;
             float fx = fmaf(qc, t[2], t[5]), fy = fmaf(qc, t[3], t[6]), fz = fmaf(qc, t[4], t[7]);
             phi[i] = ph;
-            if (charges_out) charges_out[i] = qc;
+            const int io = sidx ? __ldg(&sidx[i]) : i;
+            if (charges_out) charges_out[io] = qc;
             float qt = seps * qc;
             acc12[3 * i + 0] = make_float4(fx, fy, fz, qt);
             acc12[3 * i + 1] = make_float4(0.f, 0.f, 0.f, qt);
@@ -164,9 +166,9 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
             s_er = 0.5 * (double)qc * (double)t[1];
             s_es = ec.mode == 1 ? -(double)KE * ec.alpha * INV_SQRT_PI * (double)qc * (double)qc : 0.0;
             s_qc = (double)qt;
-            px = (double)qt * (double)pos_in[3 * i + 0];
-            py = (double)qt * (double)pos_in[3 * i + 1];
-            pz = (double)qt * (double)pos_in[3 * i + 2];
+            px = (double)qt * (double)pos_in[3 * io + 0];
+            py = (double)qt * (double)pos_in[3 * io + 1];
+            pz = (double)qt * (double)pos_in[3 * io + 2];
         }
         double v[7] = {s_phi, s_er, s_es, s_qc, px, py, pz};
 #pragma unroll
@@ -192,6 +194,266 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
     }
 }
 
+// Real space (mode 1) for sorted atom k, one warp per atom, lanes over list entries:
+//   phi^r_k = k_e sum_j q_j erfc(alpha r)/r,  F^r_k = sum_j 2 F^{r,static}_kj,
+//   W^r -= r_kj (x) F^{r,static}_kj,  U^r = 1/2 sum_k q_k phi^r_k.
+// rfield[k] = (F^r, phi^r); the sums go to the FP64 accumulators once per block.
+__global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, const float* __restrict__ q_raw,
+                                              const int* __restrict__ nbr_list, const int* __restrict__ cnt_list, int n,
+                                              int n_species, Geom g, float alpha, float q_target,
+                                              const Accum* __restrict__ acc_in, float4* __restrict__ rfield,
+                                              Accum* __restrict__ acc) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int k = blockIdx.x * (blockDim.x >> 5) + wib;
+    float wv[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wv[q] = 0.f;
+    float phr = 0.f, ereal = 0.f;
+    if (k < n) {
+        const float delta = (float)(((double)q_target - acc_in->sum_q) / (double)n);
+        const float4 pk = __ldg(&spos4[k]);
+        const float qk = __ldg(&q_raw[k]) + delta;
+        int total = 0;
+        for (int s = 0; s < n_species; ++s) total += __ldg(&cnt_list[(size_t)s * n + k]);
+        const float rc2 = g.rc_real * g.rc_real;
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int e = lane; e < total; e += 32) {
+            const int ent = list_entry(nbr_list, k, e, g.list_sa, g.list_se);
+            const int j = entry_index(ent);
+            float vx, vy, vz;
+            entry_vector(spos4, ent, pk, g, vx, vy, vz);
+            const float r2 = vx * vx + vy * vy + vz * vz;
+            if (r2 < rc2) {
+                const float r = sqrtf(r2), ir = 1.f / r;
+                const float qj = __ldg(&q_raw[j]) + delta;
+                const float ec = erfcf(alpha * r);
+                phr = fmaf(KE * qj, ec * ir, phr);
+                const float bracket = 2.f * alpha * r * INV_SQRT_PI * expf(-alpha * alpha * r2) + ec;
+                const float coef = -0.5f * KE * qk * qj * bracket * ir * ir * ir;
+                const float ax = coef * vx, ay = coef * vy, az = coef * vz;
+                fx = fmaf(2.f, ax, fx);
+                fy = fmaf(2.f, ay, fy);
+                fz = fmaf(2.f, az, fz);
+                wv[0] -= vx * ax; wv[1] -= vx * ay; wv[2] -= vx * az;
+                wv[3] -= vy * ax; wv[4] -= vy * ay; wv[5] -= vy * az;
+                wv[6] -= vz * ax; wv[7] -= vz * ay; wv[8] -= vz * az;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            phr += __shfl_xor_sync(0xffffffffu, phr, o);
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) rfield[k] = make_float4(fx, fy, fz, phr);
+        ereal = 0.5f * qk * phr;
+    }
+    __shared__ double red[11][8];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        float v = wv[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][wib] = (double)v;
+    }
+    if (lane == 0) {
+        red[9][wib] = (double)phr;     // every lane holds the reduced phi^r
+        red[10][wib] = (double)ereal;
+    }
+    __syncthreads();
+    if (threadIdx.x < 11) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x][q];
+        if (threadIdx.x < 9) atomicAdd(&acc->virial[threadIdx.x], t);
+        else if (threadIdx.x == 9) atomicAdd(&acc->sum_phi, t);
+        else atomicAdd(&acc->e_real, t);
+    }
+}
+
+// Reciprocal-space potential and field of 32 atoms (lanes) over one split of the
+// k columns (warps take every W-th column of the split).  With C = 4 k_e G S:
+//   phi^k_i = sum_half Re[C e^{i k.r_i}],  F^k_i = q_i sum_half k Im[C e^{i k.r_i}]
+// per column (n1, n2): T = sum_n3 C conj(Z(n3)), then conj(X Y) T.  Partial
+// results of the splits are added with float4 atomics to kfield = (F^k / q, phi^k).
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csplit, float4* __restrict__ kfield,
+                                                    Accum* __restrict__ acc) {
+    extern __shared__ __align__(16) float2 stab[];
+    __shared__ float red[W][4][33];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int failed;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int group = blockIdx.x / csplit, split = blockIdx.x - group * csplit;
+    const int i0 = group * 32;
+    const int i = i0 + lane;
+    const int cnt = min(32, n - i0);
+    // the 32 atoms' phase rows are contiguous: one TMA bulk copy into shared memory
+    if (threadIdx.x == 0) {
+        failed = 0;
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        const uint32_t bytes = round_up16((uint32_t)(cnt * tab.nph) * (uint32_t)sizeof(float2));
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(stab, tab.phase + (size_t)i0 * tab.nph, bytes, &bar);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0u)) failed = 1;
+    __syncthreads();
+    if (failed) {   // same decision in every thread of the block
+        mbar_wait_bounded(&bar, 0u);   // one more bounded chance for the copy in flight
+        if (threadIdx.x == 0) atomicOr(&acc->status, kStatusTimeout);
+        return;
+    }
+    float phk = 0.f, fk0 = 0.f, fk1 = 0.f, fk2 = 0.f;
+    if (lane < cnt) {
+        const float2* row = stab + lane * tab.nph;
+        const float kxs = TWO_PI / tab.L[0], kys = TWO_PI / tab.L[1], kzs = TWO_PI / tab.L[2];
+        for (int c = split + csplit * w; c < tab.ncol; c += csplit * W) {
+            const int4 ci = __ldg(&tab.col[c]);
+            const int kend = __ldg(&tab.col[c + 1].w);
+            const float2 x = row[ci.x], y = row[tab.yoff + ci.y + tab.n2max];
+            const float2 xy = make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
+            float tr = 0.f, ti = 0.f, tzr = 0.f, tzi = 0.f;
+            const float2* zr = row + tab.zoff + ci.z + tab.n3max - ci.w;   // zr[k] = Z(n3(k))
+            const float4* c4 = reinterpret_cast<const float4*>(tab.C);
+            for (int k = ci.w; k < kend; k += 8) {
+                const float n3b = (float)(ci.z + (k - ci.w));
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    const float4 cc = __ldg(&c4[(k + t) >> 1]);
+                    const float2 z0 = zr[k + t], z1 = zr[k + t + 1];
+                    float pr = fmaf(cc.x, z0.x, cc.y * z0.y);    // C conj(Z)
+                    float pim = fmaf(cc.y, z0.x, -cc.x * z0.y);
+                    tr += pr;
+                    ti += pim;
+                    tzr = fmaf(n3b + (float)t, pr, tzr);
+                    tzi = fmaf(n3b + (float)t, pim, tzi);
+                    pr = fmaf(cc.z, z1.x, cc.w * z1.y);
+                    pim = fmaf(cc.w, z1.x, -cc.z * z1.y);
+                    tr += pr;
+                    ti += pim;
+                    tzr = fmaf(n3b + (float)(t + 1), pr, tzr);
+                    tzi = fmaf(n3b + (float)(t + 1), pim, tzi);
+                }
+            }
+            const float zre = fmaf(xy.x, tr, xy.y * ti);
+            const float zim = fmaf(xy.x, ti, -xy.y * tr);
+            const float zzi = fmaf(xy.x, tzi, -xy.y * tzr);
+            phk += zre;
+            fk0 = fmaf(kxs * ci.x, zim, fk0);
+            fk1 = fmaf(kys * ci.y, zim, fk1);
+            fk2 = fmaf(kzs, zzi, fk2);
+        }
+    }
+    red[w][0][lane] = phk;
+    red[w][1][lane] = fk0;
+    red[w][2][lane] = fk1;
+    red[w][3][lane] = fk2;
+    __syncthreads();
+    if (w == 0) {
+        float t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v = 0.f;
+#pragma unroll
+            for (int u = 0; u < W; ++u) v += red[u][q][lane];
+            t[q] = v;
+        }
+        if (lane < cnt) atomicAdd(&kfield[i], make_float4(t[1], t[2], t[3], t[0]));
+        float sp = lane < cnt ? t[0] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        if (lane == 0) atomicAdd(&acc->sum_phi, (double)sp);
+    }
+}
+
+__device__ __forceinline__ void write_scalars(const Accum* __restrict__ acc, int n, double* __restrict__ out,
+                                              unsigned int* __restrict__ status_host) {
+    double e = acc->sum_u + acc->e_real + acc->e_kspace + acc->e_self;
+    out[0] = e;
+    out[1] = acc->sum_u;
+    out[2] = acc->e_real;
+    out[3] = acc->e_kspace;
+    out[4] = acc->e_self;
+    for (int k = 0; k < 9; ++k) out[5 + k] = acc->virial[k];
+    for (int k = 0; k < 3; ++k) out[14 + k] = acc->polar[k];
+    out[17] = acc->sum_qc;
+    out[18] = n > 0 ? acc->sum_phi / (double)n : 0.0;
+    out[19] = (double)acc->status;
+    if (status_host) *status_host = acc->status;
+}
+
+// Per-atom outputs back in input order (forces, BEC, charges q^c, potential
+// phi = phi^k + phi^r + phi^s, site energies), the block sums of P = sum q~^c r,
+// U^s = -k_e alpha/sqrt(pi) sum q^c^2 and sum q~^c; the last block writes the scalars.
+__global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __restrict__ sidx,
+                           const float* __restrict__ pos_in, const float* __restrict__ q_raw, float q_target,
+                           float seps, ElecConst ec, const float4* __restrict__ kfield,
+                           const float4* __restrict__ rfield, float* __restrict__ forces, float* __restrict__ bec,
+                           float* __restrict__ charges, float* __restrict__ potential, const float* __restrict__ u,
+                           float* __restrict__ site_energy, Accum* __restrict__ acc, double* __restrict__ scalars,
+                           unsigned int* __restrict__ status_host, unsigned int* __restrict__ done) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    // FP32 terms summed over a warp (32 atoms), then FP64 across warps and blocks
+    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // P (3), U^s, sum q~^c
+    if (k < n) {
+        const int io = sidx ? __ldg(&sidx[k]) : k;
+        const float delta = (float)(((double)q_target - acc->sum_q) / (double)n);
+        const float qc = __ldg(&q_raw[k]) + delta;
+        const float qt = seps * qc;
+        const float* a = acc12 + 12 * (size_t)k;
+        if (forces) {
+            forces[3 * (size_t)io + 0] = a[0];
+            forces[3 * (size_t)io + 1] = a[1];
+            forces[3 * (size_t)io + 2] = a[2];
+        }
+        if (bec) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) bec[9 * (size_t)io + q] = a[3 + q];
+        }
+        if (charges) charges[io] = qc;
+        const float phs = ec.mode == 1 ? -2.f * KE * ec.alpha * INV_SQRT_PI * qc : 0.f;
+        if (potential) potential[io] = kfield[k].w + rfield[k].w + phs;
+        if (site_energy) site_energy[io] = u[k];
+        v[0] = qt * pos_in[3 * (size_t)io + 0];
+        v[1] = qt * pos_in[3 * (size_t)io + 1];
+        v[2] = qt * pos_in[3 * (size_t)io + 2];
+        v[3] = ec.mode == 1 ? -KE * ec.alpha * INV_SQRT_PI * qc * qc : 0.f;
+        v[4] = qt;
+    }
+    __shared__ double red[5][8];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        float x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[q][wib] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x][q];
+        double* dst = threadIdx.x < 3 ? &acc->polar[threadIdx.x] : (threadIdx.x == 3 ? &acc->e_self : &acc->sum_qc);
+        atomicAdd(dst, t);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(done, 1u);
+        last = t == gridDim.x - 1;
+        if (last) *done = 0u;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        if (scalars) write_scalars(acc, n, scalars, status_host);
+        else if (status_host) *status_host = acc->status;
+    }
+}
+
 __global__ void k_finalize_atoms(const float* __restrict__ acc12, int n, float* __restrict__ forces,
                                  float* __restrict__ bec, const float* __restrict__ phi,
                                  float* __restrict__ potential) {
@@ -212,17 +474,7 @@ __global__ void k_finalize_atoms(const float* __restrict__ acc12, int n, float* 
 
 __global__ void k_finalize_scalars(const Accum* __restrict__ acc, int n, double* __restrict__ out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double e = acc->sum_u + acc->e_real + acc->e_kspace + acc->e_self;
-    out[0] = e;
-    out[1] = acc->sum_u;
-    out[2] = acc->e_real;
-    out[3] = acc->e_kspace;
-    out[4] = acc->e_self;
-    for (int k = 0; k < 9; ++k) out[5 + k] = acc->virial[k];
-    for (int k = 0; k < 3; ++k) out[14 + k] = acc->polar[k];
-    out[17] = acc->sum_qc;
-    out[18] = n > 0 ? acc->sum_phi / (double)n : 0.0;
-    out[19] = (double)acc->status;
+    write_scalars(acc, n, out, nullptr);
 }
 
 }  // namespace
@@ -230,9 +482,9 @@ __global__ void k_finalize_scalars(const Accum* __restrict__ acc, int n, double*
 void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, const int* nbr_list, const int* cnt_list,
                   int n, int n_species, const Geom& g, ElecConst ec, float q_target, float sqrt_eps, bool ewald,
                   EwaldTab tab, const float* pppm_field, float* phi, float* acc12, float* charges_out, Accum* acc,
-                  cudaStream_t st) {
+                  cudaStream_t st, const int* sidx) {
     if (n == 0) return;
-    constexpr int W = 8;
+    constexpr int W = 32;
     size_t smem = ewald ? sizeof(float2) * 32 * tab.nph : 0;
     static bool attr = false;
     if (!attr) {
@@ -241,7 +493,42 @@ void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, c
     }
     k_field<W><<<(n + 31) / 32, 32 * W, smem, st>>>(pos4, pos_in, q_raw, nbr_list, cnt_list, n, n_species, g, ec,
                                                     q_target, sqrt_eps, ewald ? 1 : 0, tab, pppm_field, phi,
-                                                    reinterpret_cast<float4*>(acc12), charges_out, acc);
+                                                    reinterpret_cast<float4*>(acc12), charges_out, sidx, acc);
+}
+
+void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, const int* cnt_list, int n,
+                 int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
+                 Accum* acc, cudaStream_t st) {
+    if (n == 0) return;
+    k_real<<<(n + 7) / 8, 256, 0, st>>>(spos4, q_raw, nbr_list, cnt_list, n, n_species, g, alpha, q_target, acc_in,
+                                        rfield, acc);
+}
+
+void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st) {
+    if (n == 0 || tab.ncol == 0) return;
+    constexpr int W = 8;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_field_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr = true;
+    }
+    const int groups = (n + 31) / 32;
+    // column splits: fill the 152 SMs x 8 resident blocks of 8 warps in one wave
+    int csplit = (152 * 8) / groups;
+    if (csplit < 1) csplit = 1;
+    if (csplit > tab.ncol) csplit = tab.ncol;
+    size_t smem = sizeof(float2) * 32 * tab.nph;
+    k_field_k<W><<<groups * csplit, 32 * W, smem, st>>>(n, tab, csplit, kfield, acc);
+}
+
+void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
+                     float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
+                     float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
+                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st) {
+    int blocks = (n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    k_finalize<<<blocks, 256, 0, st>>>(acc12, n, sidx, pos_in, q_raw, q_target, seps, ec, kfield, rfield, forces, bec,
+                                       charges, potential, u, site_energy, acc, scalars, status_host, done);
 }
 
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi, float* potential,

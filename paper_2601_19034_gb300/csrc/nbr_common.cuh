@@ -1,0 +1,115 @@
+// Warp-level neighbour-list construction shared by the list kernel and the
+// fused neighbour + descriptor kernel.
+#pragma once
+
+#include "qnep_internal.cuh"
+
+namespace qnep {
+
+__device__ __forceinline__ int nbr_cell_coord(float x, float invL, int nc) {
+    int c = (int)(x * invL * (float)nc);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Build the lists of sorted atom k (position pk) into shared memory.
+//   sl / slt: list entries (index | image code << 26) and neighbour species, capacity cap_l
+//   sa / sat: angular entries and species, capacity cap_a
+// The 27 stencil cells are visited in order; lanes test the atoms of one cell
+// (32 at a time) and a ballot compacts the accepted ones.  nl / na return the
+// number of entries stored (clamped to the capacities); the return value is true
+// when a capacity was exceeded.  Whole warp only.
+__device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos4, const int* __restrict__ cell_start,
+                                                 int k, float4 pk, const Geom& g, int cap_l, int cap_a, int* sl,
+                                                 int* slt, int* sa, int* sat, int& nl, int& na) {
+    const int lane = threadIdx.x & 31;
+    // lane s < 27 describes stencil cell s: first atom, atom count, image shift code and vector
+    int cstart = 0, ccnt = 0, code = CODE_SELF;
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    if (lane < 27) {
+        int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        float p[3] = {pk.x, pk.y, pk.z};
+        int cc[3], tt[3];
+        for (int q = 0; q < 3; ++q) {
+            int c = nbr_cell_coord(p[q], g.invL[q], g.nc[q]) + d[q];
+            int t = c < 0 ? -1 : (c >= g.nc[q] ? 1 : 0);
+            cc[q] = c - t * g.nc[q];
+            tt[q] = t;
+        }
+        int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+        cstart = cell_start[c];
+        ccnt = cell_start[c + 1] - cstart;
+        code = (tt[0] + 1) | ((tt[1] + 1) << 2) | ((tt[2] + 1) << 4);
+        tx = tt[0] * g.L[0];
+        ty = tt[1] * g.L[1];
+        tz = tt[2] * g.L[2];
+    }
+    const float rl2 = g.rc_list * g.rc_list;
+    const float ra2 = g.rc_angular * g.rc_angular;
+    const unsigned below = (1u << lane) - 1u;
+    int cl = 0, ca = 0;
+    for (int s = 0; s < 27; ++s) {
+        const int c0 = __shfl_sync(0xffffffffu, cstart, s);
+        const int cn = __shfl_sync(0xffffffffu, ccnt, s);
+        const int cd = __shfl_sync(0xffffffffu, code, s);
+        const float sx = __shfl_sync(0xffffffffu, tx, s), sy = __shfl_sync(0xffffffffu, ty, s),
+                    sz = __shfl_sync(0xffffffffu, tz, s);
+        for (int base = 0; base < cn; base += 32) {
+            const int m = c0 + base + lane;
+            bool inl = false, ina = false;
+            int typ = 0;
+            if (base + lane < cn) {
+                float4 pj = __ldg(&spos4[m]);
+                float vx = (pj.x - pk.x) + sx, vy = (pj.y - pk.y) + sy, vz = (pj.z - pk.z) + sz;
+                float r2 = vx * vx + vy * vy + vz * vz;
+                inl = r2 < rl2 && !(m == k && cd == CODE_SELF);
+                ina = inl && r2 < ra2;
+                typ = __float_as_int(pj.w);
+            }
+            const unsigned ml = __ballot_sync(0xffffffffu, inl);
+            const unsigned ma = __ballot_sync(0xffffffffu, ina);
+            const int ent = (int)((unsigned)m | ((unsigned)cd << CODE_SHIFT));
+            if (inl) {
+                int slot = cl + __popc(ml & below);
+                if (slot < cap_l) {
+                    sl[slot] = ent;
+                    slt[slot] = typ;
+                }
+            }
+            if (ina) {
+                int slot = ca + __popc(ma & below);
+                if (slot < cap_a) {
+                    sa[slot] = ent;
+                    sat[slot] = typ;
+                }
+            }
+            cl += __popc(ml);
+            ca += __popc(ma);
+        }
+    }
+    __syncwarp();
+    nl = cl < cap_l ? cl : cap_l;
+    na = ca < cap_a ? ca : cap_a;
+    return cl > cap_l || ca > cap_a;
+}
+
+// Write staged entries grouped by neighbour species: out[k * sa + slot * se], counts cnt[s][n].
+__device__ __forceinline__ void warp_write_grouped(const int* se_buf, const int* st_buf, int cnt, int n_species, int n,
+                                                   int k, int* __restrict__ out, size_t stride_atom,
+                                                   size_t stride_entry, int* __restrict__ out_cnt) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int off = 0;
+    for (int s = 0; s < n_species; ++s) {
+        const int c0 = off;
+        for (int base = 0; base < cnt; base += 32) {
+            const int e = base + lane;
+            const bool take = e < cnt && st_buf[e] == s;
+            const unsigned mk = __ballot_sync(0xffffffffu, take);
+            if (take) out[(size_t)k * stride_atom + (size_t)(off + __popc(mk & below)) * stride_entry] = se_buf[e];
+            off += __popc(mk);
+        }
+        if (lane == 0) out_cnt[(size_t)s * n + k] = off - c0;
+    }
+}
+
+}  // namespace qnep

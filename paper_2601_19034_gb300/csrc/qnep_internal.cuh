@@ -2,8 +2,8 @@
 //
 // Layout conventions (device):
 //   pos4[i]            float4 (x, y, z wrapped into the box, species as int bits)
-//   list entries       int32: neighbour index j in bits 0..25, image code in bits 26..30,
-//                      code = (Tx+1) + 3 (Ty+1) + 9 (Tz+1), r_ij = pos4[j] + T.L - pos4[i];
+//   list entries       32 bits: neighbour index j in bits 0..25, image shift T in bits 26..31,
+//                      two bits per axis holding T_d + 1; r_ij = pos4[j] + T.L - pos4[i];
 //                      column-major [cap][N]; entries of an atom grouped by neighbour
 //                      species (count per species in cnt[s][N])
 //   per-atom vectors   column-major [component][N] for coalesced access
@@ -30,6 +30,7 @@ constexpr double KE_D = 14.3996454784;
 
 constexpr int CODE_SHIFT = 26;
 constexpr int INDEX_MASK = (1 << CODE_SHIFT) - 1;
+constexpr int CODE_SELF = 1 | (1 << 2) | (1 << 4);   // image shift (0, 0, 0)
 
 // Offsets (floats) into one candidate's parameter blob.
 struct ParamLayout {
@@ -74,6 +75,8 @@ struct Geom {
     float rc_radial;
     float rc_angular;
     float rc_real;     // 0 when there is no real-space term
+    int list_sa, list_se;   // list entry e of sorted atom k at k * list_sa + e * list_se
+    int ang_sa, ang_se;     // same for the angular list
 };
 
 // FP64 accumulators of one force call (zeroed at the start of every call).
@@ -87,7 +90,9 @@ struct Accum {
     double virial[9];
     double polar[3];
     double sum_qc;       // sum of corrected naked charges q~^c
-    unsigned int status; // bit 0: neighbour overflow
+    unsigned int status; // bit 0: neighbour overflow, bit 1: a bounded wait gave up
+    unsigned int work_fwd;   // atom counters of the dynamically scheduled warp-per-atom kernels
+    unsigned int work_bwd;
     unsigned int pad;
 };
 
@@ -97,6 +102,15 @@ struct ElecConst {
     int kind;            // 0 Ewald, 1 PPPM
     float alpha;
     float q_total;
+};
+
+// Per-atom electrostatic fields consumed by the backward kernels.
+struct FieldIn {
+    const float4* kfield;   // (F^k / q, phi^k) per sorted atom (zero without k-space)
+    const float4* rfield;   // (F^r, phi^r) per sorted atom (zero without real space)
+    int mode;
+    float alpha;
+    float q_target;         // Q in screened-charge units (Q / sqrt(eps_inf))
 };
 
 // Ewald k-space description (host-built, uploaded when the box changes).
@@ -116,6 +130,8 @@ struct EwaldTab {
     float alpha;
     const int4* col;      // [ncol + 1] (n1, n2, lo, padded offset); last entry: (0, 0, 0, nk)
     const int* chunk_col; // [nchunk] column of each chunk
+    const int* chunk_order; // [nchunk] processing order of the chunks in the structure-factor kernel
+                            // (sorted by n3 window so a warp's lanes share Z loads); NULL = identity
     const float* kg;      // [nk] G(k) = (2 pi / V) exp(-k^2 / 4 alpha^2) / k^2, 0 on padding
     double2* S;           // [nk] structure factor sum_i q_i exp(-i k.r_i) (FP64)
     float2* C;            // [nk] 4 k_e G(k) S(k) (FP32) for the force / potential pass
@@ -124,43 +140,59 @@ struct EwaldTab {
 
 __device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }
 __device__ __forceinline__ void entry_shift(int e, float& tx, float& ty, float& tz) {
-    int code = (unsigned)e >> CODE_SHIFT;
-    int cz = code / 9;
-    int cy = (code - 9 * cz) / 3;
-    int cx = code - 9 * cz - 3 * cy;
-    tx = (float)(cx - 1);
-    ty = (float)(cy - 1);
-    tz = (float)(cz - 1);
+    const unsigned code = (unsigned)e >> CODE_SHIFT;
+    tx = (float)((int)(code & 3u) - 1);
+    ty = (float)((int)((code >> 2) & 3u) - 1);
+    tz = (float)((int)(code >> 4) - 1);
 }
-
-__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
 // ---- host-side launchers (defined in the .cu files) ---------------------------------
 
-struct Workspace;   // defined in api.cu
-
 void launch_bin(const float* pos, const int* types, int n, const Geom& g, float4* pos4, int* cell_of,
-                int* cell_count, int* cell_start, int* cell_fill, int* cell_atoms, cudaStream_t st);
-void launch_neighbors(const float4* pos4, const int* cell_start, const int* cell_atoms, int n,
-                      int n_species, const Geom& g, int cap_list, int cap_ang, int* nbr_list,
-                      int* cnt_list, int* nbr_ang, int* cnt_ang, Accum* acc, cudaStream_t st);
+                int* cell_count, int* cell_start, int* cell_fill, int* slot_atoms, float4* spos4, int* sidx,
+                Accum* acc, double2* zero_buf, int zero_count, cudaStream_t st);
+void launch_neighbors(const float4* spos4, const int* cell_start, int n, int n_species, const Geom& g,
+                      int cap_list, int cap_ang, int* nbr_list, int* cnt_list, int* nbr_ang, int* cnt_ang,
+                      Accum* acc, cudaStream_t st);
 void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list,
                                const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
                                const float* params, const ParamLayout& lay, float* ang_coef,
                                float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               Accum* acc, cudaStream_t st);
+                               const int* sidx, float4* fields, Accum* acc, cudaStream_t st);
+size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a);
+void set_num_sms(int n);
+void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
+                          const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
+                          int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,
+                          float* u, float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
+                          Accum* acc, cudaStream_t st);
+void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
+                          const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
+                          const float* ang_coef, const float* du, const float* dq, const float* q_raw,
+                          const FieldIn& fin, const Accum* acc_in, bool want_bec, float* acc12, Accum* acc,
+                          cudaStream_t st);
 void launch_ewald_phases(const float4* pos4, int n, EwaldTab tab, cudaStream_t st);
 void launch_ewald_sk(const float* q_raw, const Accum* acc, int n, float q_target, EwaldTab tab, cudaStream_t st);
+void launch_ewald_sk_fused(const float* q_raw, Accum* acc, int n, float q_target, EwaldTab tab,
+                           unsigned int* group_done, cudaStream_t st);
 void launch_ewald_sk_finalize(EwaldTab tab, Accum* acc, cudaStream_t st);
 void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, const int* nbr_list,
                   const int* cnt_list, int n, int n_species, const Geom& g, ElecConst ec, float q_target,
                   float sqrt_eps, bool ewald, EwaldTab tab, const float* pppm_field, float* phi,
-                  float* acc12, float* charges_out, Accum* acc, cudaStream_t st);
+                  float* acc12, float* charges_out, Accum* acc, cudaStream_t st, const int* sidx = nullptr);
 void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list,
                                 const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
                                 const float* params, const ParamLayout& lay, const float* ang_coef,
-                                const float* du, const float* dq, const float* phi, const Accum* acc_in,
-                                bool want_bec, float* acc12, Accum* acc, cudaStream_t st);
+                                const float* du, const float* dq, const float* q_raw, const FieldIn& fin,
+                                const Accum* acc_in, bool want_bec, float* acc12, Accum* acc, cudaStream_t st);
+void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, const int* cnt_list, int n,
+                 int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
+                 Accum* acc, cudaStream_t st);
+void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st);
+void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
+                     float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
+                     float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
+                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st);
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi,
                            float* potential, cudaStream_t st);
 void launch_finalize_scalars(const Accum* acc, int n, float sqrt_eps, double* scalars, cudaStream_t st);

@@ -67,6 +67,10 @@ class QNEP:
         except Exception:
             pass
 
+    def set_path(self, path: str = "auto"):
+        code = {"auto": _lib.QNEP_PATH_AUTO, "warp": _lib.QNEP_PATH_WARP, "thread": _lib.QNEP_PATH_THREAD}[path]
+        _lib.check(self.lib.qnep_set_path(self.handle, code), self.handle)
+
     def set_capacity(self, cap_list: int = 0, cap_angular: int = 0):
         _lib.check(self.lib.qnep_set_capacity(self.handle, int(cap_list), int(cap_angular)), self.handle)
 

@@ -35,9 +35,10 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _gpu(sysm, hp, params, elec, dev, **want):
+def _gpu(sysm, hp, params, elec, dev, path="auto", **want):
     from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
     model = QNEP(hp, params, elec)
+    model.set_path(path)
     pos = torch.tensor(sysm.positions, device=dev)
     typ = torch.tensor(sysm.types, device=dev)
     want.setdefault("descriptor", True)
@@ -83,9 +84,10 @@ def _compare(g, ref, sysm, elec, bec=True):
     return ok
 
 
-def test_water_64_ewald_mode1(dev):
+@pytest.mark.parametrize("path", ["warp", "thread"])
+def test_water_64_ewald_mode1(dev, path):
     sysm, hp, params, elec = wl.config_water_small()
-    g = _gpu(sysm, hp, params, elec, dev)
+    g = _gpu(sysm, hp, params, elec, dev, path=path)
     ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
     _compare(g, ref, sysm, elec)
     assert abs(g["qtilde_sum"]) < 1e-5
@@ -99,20 +101,22 @@ def test_water_64_ewald_mode2(dev):
     _compare(g, ref, sysm, elec)
 
 
-def test_batio3_40_small_box_images_and_charge_target(dev):
+@pytest.mark.parametrize("path", ["warp", "thread"])
+def test_batio3_40_small_box_images_and_charge_target(dev, path):
     s = wl.batio3_supercell(2, seed=31)
     hp = wl.HParams(n_species=3)
     params = wl.random_params(hp, np.random.default_rng(32))[0]
     elec = wl.Elec(mode=1, kind="ewald", q_total=0.3)
-    g = _gpu(s, hp, params, elec, dev)
+    g = _gpu(s, hp, params, elec, dev, path=path)
     ref = forcecall.force_call(s.positions.astype(np.float64), s.box, s.types, hp, params, elec)
     _compare(g, ref, s, elec)
     assert abs(g["qtilde_sum"] - 0.3) < 1e-5
 
 
-def test_batio3_5000_full_size(dev):
+@pytest.mark.parametrize("path", ["warp", "thread"])
+def test_batio3_5000_full_size(dev, path):
     sysm, hp, params, elec = wl.config_batio3()
-    g = _gpu(sysm, hp, params, elec, dev)
+    g = _gpu(sysm, hp, params, elec, dev, path=path)
     ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
     _compare(g, ref, sysm, elec)
     assert abs(g["forces"].astype(np.float64).sum(0)).max() < 1e-3   # weak Newton's third law
