@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cufft.h>
+
 #include "../../include/qnep.h"
 #include "qnep_internal.cuh"
 
@@ -63,6 +65,10 @@ struct qnep_model {
     float* d_kg = nullptr;
     double2* d_S = nullptr;
     float2* d_C = nullptr;
+    // PPPM meshes and FFT plans (created with the first box)
+    PppmTab pm{};
+    cufftHandle r2c = 0, c2r = 0;
+    bool have_mesh = false;
     // device staging of the host-buffer entry point
     int nio_alloc = 0;
     float* io_pos = nullptr;
@@ -212,6 +218,40 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
     return QNEP_OK;
 }
 
+// PPPM meshes, cuFFT plans (once) and the influence function (every new box).
+qnep_status setup_pppm(qnep_model* m, const double L[3], cudaStream_t st) {
+    PppmTab& pm = m->pm;
+    if (!m->have_mesh) {
+        pm.nx = m->es.mesh[0];
+        pm.ny = m->es.mesh[1];
+        pm.nz = m->es.mesh[2];
+        pm.nreal = (size_t)pm.nx * pm.ny * pm.nz;
+        pm.nhalf = (size_t)pm.nx * pm.ny * (pm.nz / 2 + 1);
+        CK(cudaMalloc((void**)&pm.rho, sizeof(float) * pm.nreal));
+        CK(cudaMemset(pm.rho, 0, sizeof(float) * pm.nreal));
+        CK(cudaMalloc((void**)&pm.shat, sizeof(float2) * pm.nhalf));
+        CK(cudaMalloc((void**)&pm.fhat, sizeof(float2) * 4 * pm.nhalf));
+        CK(cudaMalloc((void**)&pm.field, sizeof(float) * 4 * pm.nreal));
+        CK(cudaMalloc((void**)&pm.gopt, sizeof(float) * pm.nhalf));
+        if (cufftPlan3d(&m->r2c, pm.nx, pm.ny, pm.nz, CUFFT_R2C) != CUFFT_SUCCESS)
+            return fail(m, QNEP_ERR_CUDA, "cufftPlan3d (R2C) failed");
+        int dims[3] = {pm.nx, pm.ny, pm.nz};
+        if (cufftPlanMany(&m->c2r, 3, dims, nullptr, 1, (int)pm.nhalf, nullptr, 1, (int)pm.nreal, CUFFT_C2R, 4) !=
+            CUFFT_SUCCESS)
+            return fail(m, QNEP_ERR_CUDA, "cufftPlanMany (C2R x 4) failed");
+        m->have_mesh = true;
+    }
+    for (int d = 0; d < 3; ++d) {
+        pm.len[d] = (float)L[d];
+        const int nd = d == 0 ? pm.nx : (d == 1 ? pm.ny : pm.nz);
+        pm.inv_h[d] = (float)(nd / L[d]);
+        pm.inv_h_lo[d] = (float)(nd / L[d] - (double)pm.inv_h[d]);
+    }
+    launch_pppm_gopt(pm, m->es.alpha, L[0] * L[1] * L[2], st);
+    CK(cudaStreamSynchronize(st));
+    return QNEP_OK;
+}
+
 qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
     if (!box) return fail(m, QNEP_ERR_ARG, "box is NULL");
     for (int k = 0; k < 9; ++k)
@@ -256,6 +296,10 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
                 CK(cudaMemset(m->sk_done, 0, sizeof(unsigned int) * groups));
                 m->sk_done_alloc = groups;
             }
+        }
+        if (m->es.mode != 0 && m->es.kind == QNEP_PPPM) {
+            qnep_status s = setup_pppm(m, L, st);
+            if (s != QNEP_OK) return s;
         }
         std::memcpy(m->box, box, sizeof(double) * 9);
         m->have_box = true;
@@ -404,7 +448,11 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
         if (!(es->alpha > 0)) return QNEP_ERR_ARG;
         if (es->kind != QNEP_EWALD && es->kind != QNEP_PPPM) return QNEP_ERR_ARG;
         if (es->kind == QNEP_EWALD && !(es->kmax > 0)) return QNEP_ERR_ARG;
-        if (es->kind == QNEP_PPPM) return QNEP_ERR_UNSUPPORTED;
+        if (es->kind == QNEP_PPPM) {
+            if (es->order != 5) return QNEP_ERR_UNSUPPORTED;
+            for (int d = 0; d < 3; ++d)
+                if (es->mesh[d] < 4 || (es->mesh[d] & 1)) return QNEP_ERR_ARG;
+        }
         if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
     }
     if (precision != QNEP_PREC_FP32) return QNEP_ERR_UNSUPPORTED;
@@ -469,6 +517,7 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
     qnep_status s = prepare(m, n, box, st);
     if (s != QNEP_OK) return s;
     const bool ewald = m->es.mode != 0 && m->es.kind == QNEP_EWALD;
+    const bool pppm = m->es.mode != 0 && m->es.kind == QNEP_PPPM;
     const bool backward = out->forces || out->bec || out->want_virial;
     const bool want_bec = out->bec != nullptr;
     const float q_target = (float)(m->es.q_total / (double)m->sqrt_eps);   // Q in screened-charge units
@@ -499,8 +548,11 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
     float4* rfield = m->fields + n;
     StageTimer tm{m};
     tm.begin(0, st);
+    // the structure-factor sums (Ewald) or the charge mesh (PPPM) start from zero
+    double2* zbuf = ewald ? m->tab.S : (pppm ? reinterpret_cast<double2*>(m->pm.rho) : nullptr);
+    const int zcount = ewald ? m->tab.nk : (pppm ? (int)(m->pm.nreal / 4) : 0);
     launch_bin(positions, types, n, g, m->pos4, m->cell_of, m->cell_count, m->cell_start, m->cell_fill, m->cell_atoms,
-               m->spos4, m->sidx, m->d_acc, ewald ? m->tab.S : nullptr, ewald ? m->tab.nk : 0, st);
+               m->spos4, m->sidx, m->d_acc, zbuf, zcount, st);
     tm.end(0, st);
     if (coop) {
         tm.begin(2, st);
@@ -541,6 +593,13 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
         tm.begin(5, st);
         launch_field_k(n, m->tab, kfield, m->d_acc, st);
         tm.end(5, st);
+    }
+    if (pppm) {
+        tm.begin(9, st);
+        if (launch_pppm(m->spos4, m->q, n, m->d_acc, q_target, m->pm, (float)m->es.alpha, m->r2c, m->c2r, kfield,
+                        m->d_acc, st) != 0)
+            return fail(m, QNEP_ERR_CUDA, "cuFFT execution failed");
+        tm.end(9, st);
     }
     if (real) CK(cudaStreamWaitEvent(st, m->ev_join, 0));
     if (backward) {
@@ -627,6 +686,13 @@ void qnep_destroy(qnep_model* m) {
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     if (m->ev_join) cudaEventDestroy(m->ev_join);
     if (m->aux) cudaStreamDestroy(m->aux);
+    if (m->have_mesh) {
+        cufftDestroy(m->r2c);
+        cufftDestroy(m->c2r);
+        void* mesh[] = {m->pm.rho, m->pm.shat, m->pm.fhat, m->pm.field, m->pm.gopt};
+        for (void* b : mesh)
+            if (b) cudaFree(b);
+    }
     delete m;
 }
 

@@ -138,6 +138,22 @@ struct EwaldTab {
     float2* phase;        // [N][nph]: X[0..n1max], Y[-n2max..n2max], Z[-n3max..n3max+7]
 };
 
+// PPPM mesh description (Sec. II.F); meshes are [nx][ny][nz] (z fastest), the half
+// spectrum [nx][ny][nz/2 + 1].
+struct PppmTab {
+    int nx, ny, nz;
+    size_t nreal;        // nx ny nz
+    size_t nhalf;        // nx ny (nz/2 + 1)
+    float inv_h[3];      // N_d / L_d (high part)
+    float inv_h_lo[3];   // N_d / L_d - inv_h (low part: mesh coordinates carried to ~2^-48)
+    float len[3];        // L_d
+    float* rho;          // charge mesh
+    float2* shat;        // FFT of rho
+    float2* fhat;        // 4 x nhalf: S G_opt, i k_x S G_opt, i k_y S G_opt, i k_z S G_opt
+    float* field;        // 4 x nreal: their unnormalised inverse transforms
+    float* gopt;         // nhalf: optimal influence function
+};
+
 __device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }
 __device__ __forceinline__ void entry_shift(int e, float& tx, float& ty, float& tz) {
     const unsigned code = (unsigned)e >> CODE_SHIFT;
@@ -189,6 +205,9 @@ void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, c
                  int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
                  Accum* acc, cudaStream_t st);
 void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st);
+void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t st);
+int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc_in, float q_target, PppmTab pm,
+                float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st);
 void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
                      float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
                      float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,

@@ -7,7 +7,8 @@ Tolerances (FP32 path; derivation in DESIGN.md, "Parity tolerances"):
   BEC           max |dZ|          <= 1e-4 e
   virial        max |dW| / N      <= 1e-5 eV/atom
   polarization  max |dP| / N      <= 1e-5 e A/atom
-  potential     max |dphi|        <= 2e-5 V
+  potential     max |dphi|        <= 1e-5 max|phi| (FP32 accumulation: O(100)-term sums and
+                                    the FFT, times 2 k_e for PPPM; 4-5 sigma tail over 1e4-1e5 atoms)
   descriptor    |dD| <= 2e-5 |D| + 2e-6
 Atoms that own a pair within 1e-5 A of the hard real-space cutoff are left out
 of the per-atom comparisons: there the FP32 and FP64 cutoff decisions may
@@ -23,7 +24,7 @@ from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = dict(e=1e-6, f=1e-4, q=2e-6, z=1e-4, w=1e-5, p=1e-5, phi=2e-5)
+TOL = dict(e=1e-6, f=1e-4, q=2e-6, z=1e-4, w=1e-5, p=1e-5, phi_rel=1e-5)
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +74,8 @@ def _compare(g, ref, sysm, elec, bec=True):
     assert np.abs(g["charges"] - ref["charges"]).max() <= TOL["q"]
     np.testing.assert_allclose(g["descriptor"], ref["descriptor"], rtol=2e-5, atol=2e-6)
     np.testing.assert_allclose(g["site_energy"], ref["site_energy"], rtol=0, atol=2e-6)
-    assert np.abs(g["potential"][ok] - ref["phi"][ok]).max() <= TOL["phi"]
+    phi_scale = max(1.0, float(np.abs(ref["phi"]).max()))
+    assert np.abs(g["potential"][ok] - ref["phi"][ok]).max() <= TOL["phi_rel"] * phi_scale
     df = np.abs(g["forces"][ok] - ref["forces"][ok]).max()
     assert df <= TOL["f"], df
     assert np.abs(g["virial"] - ref["virial"]).max() / n <= TOL["w"] + slack / n
@@ -193,3 +195,33 @@ def test_neighbour_overflow_is_reported_and_recovered(dev):
     ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec,
                                want_bec=False)
     assert abs(parse_scalars(res["scalars"])["energy"] - ref["energy"]) / sysm.n_atoms < 1e-6
+
+
+@pytest.mark.parametrize("path", ["warp", "thread"])
+def test_water_pppm_small_mesh(dev, path):
+    """PPPM (order 5) on 64 H2O with a 16^3 mesh, modes 1 and 2."""
+    sysm, hp, params, _ = wl.config_water_small()
+    for mode in (1, 2):
+        elec = wl.Elec(mode=mode, kind="pppm", mesh=(16, 16, 16), order=5)
+        g = _gpu(sysm, hp, params, elec, dev, path=path)
+        ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+        _compare(g, ref, sysm, elec)
+
+
+def test_water_pppm_uneven_mesh_and_box(dev):
+    s = wl.water_box(3, length=9.3, seed=17)
+    s.box = np.diag([9.3, 9.3, 9.3])
+    hp = wl.HParams(n_species=2)
+    params = wl.random_params(hp, np.random.default_rng(18))[0]
+    elec = wl.Elec(mode=1, kind="pppm", mesh=(12, 10, 14), order=5, q_total=-0.2)
+    g = _gpu(s, hp, params, elec, dev)
+    ref = forcecall.force_call(s.positions.astype(np.float64), s.box, s.types, hp, params, elec)
+    _compare(g, ref, s, elec)
+
+
+def test_water_24000_pppm_full_size(dev):
+    """8000 H2O at 1.0 g/cm^3, PPPM 64^3, order 5, alpha 0.3 (the PPPM workload, full size)."""
+    sysm, hp, params, elec = wl.config_water_pppm()
+    g = _gpu(sysm, hp, params, elec, dev)
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    _compare(g, ref, sysm, elec)
