@@ -148,6 +148,24 @@ qnep_status qnep_compute_host(qnep_model* m, int n_atoms, const float* positions
                               const int* types_host, const double box[9], void* stream,
                               const qnep_outputs* out_host);
 
+/* Vector-Jacobian product of the force call (the derivatives of Sec. II.C and II.D).
+ * For weights g_E (energy), g_q (per-atom corrected screened charges, optional) and
+ * g_P (polarization) writes, per atom i (input order),
+ *   grad[i][b] = g_E dU^tot/dr_ib + sum_j g_q,j dq^c_j/dr_ib + sum_a g_P,a Z_i,ab
+ * where the charge derivative includes the total-charge correction and the last term
+ * uses the periodic Born effective charges of Eq. bec_2 as dP/dr.  The descriptor
+ * derivatives are recomputed, nothing per pair is stored.  Other outputs in `out`
+ * behave as in qnep_compute except `forces`, which must be NULL; the virial in the
+ * scalars is then that of the weighted objective g_E U + sum g_q q^c. */
+typedef struct {
+    double       energy_weight;    /* g_E */
+    const float* charge_weight;    /* device [N] g_q in input order, or NULL */
+    double       polar_weight[3];  /* g_P */
+    float*       grad;             /* device [N][3] output */
+} qnep_vjp;
+qnep_status qnep_compute_vjp(qnep_model* m, int n_atoms, const float* positions, const int* types,
+                             const double box[9], void* stream, const qnep_outputs* out, const qnep_vjp* vjp);
+
 /* Synchronize the stream and return the device-side status of the last call. */
 qnep_status qnep_sync_status(qnep_model* m, void* stream);
 

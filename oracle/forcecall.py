@@ -237,3 +237,28 @@ def polarization_autograd(positions, box, types, hp, blob, elec):
     qt = s * q
     qt_c = qt + (elec.q_total - qt.sum()) / n
     return (qt_c[:, None] * pos).sum(0), pos
+
+
+def charges_autograd(positions, box, types, hp, blob, elec):
+    """Corrected screened charges q^c(r) as a differentiable function of the positions.
+
+    q~ = sqrt(eps_inf) q, q~^c = q~ + (Q - sum q~)/N (Eq. charge-scaling, reading of
+    the stage-3 docstring), q^c = q~^c / sqrt(eps_inf).  Returns (q^c, positions leaf).
+    """
+    pos0 = np.asarray(positions, dtype=np.float64)
+    box0 = np.asarray(box, dtype=np.float64)
+    types = np.asarray(types, dtype=np.int64)
+    n = len(pos0)
+    model = unpack(blob, hp)
+    ent_r, ent_a, _ = _entry_sets(pos0, box0, hp, elec)
+    pos = torch.tensor(pos0, requires_grad=True)
+
+    def vecs(ent):
+        return pos[ent.j] + torch.as_tensor(ent.shift @ box0) - pos[ent.i]
+
+    d = desc_mod.descriptor(vecs(ent_r), ent_r.i, ent_r.j, vecs(ent_a), ent_a.i, ent_a.j, types,
+                            np.arange(n), model)
+    _, q = network.site_energy_and_charge(d, types, model)
+    s = model.sqrt_eps_inf
+    qt = s * q
+    return (qt + (elec.q_total - qt.sum()) / n) / s, pos

@@ -54,6 +54,11 @@ class OutputsC(ctypes.Structure):
                 ("descriptor", ctypes.c_void_p), ("want_virial", ctypes.c_int)]
 
 
+class VjpC(ctypes.Structure):
+    _fields_ = [("energy_weight", ctypes.c_double), ("charge_weight", ctypes.c_void_p),
+                ("polar_weight", ctypes.c_double * 3), ("grad", ctypes.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -70,6 +75,8 @@ def _declare(lib):
     lib.qnep_reserve.restype = i
     lib.qnep_compute.argtypes = [p, i, p, p, p, p, ctypes.POINTER(OutputsC)]
     lib.qnep_compute.restype = i
+    lib.qnep_compute_vjp.argtypes = [p, i, p, p, p, p, ctypes.POINTER(OutputsC), ctypes.POINTER(VjpC)]
+    lib.qnep_compute_vjp.restype = i
     lib.qnep_compute_host.argtypes = [p, i, p, p, p, p, ctypes.POINTER(OutputsC)]
     lib.qnep_compute_host.restype = i
     lib.qnep_sync_status.argtypes = [p, p]

@@ -508,8 +508,14 @@ qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]) {
     return QNEP_OK;
 }
 
-qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int* types, const double box[9],
-                         void* stream, const qnep_outputs* out) {
+}  // extern "C"
+
+namespace {
+
+// One force call; with a vector-Jacobian product request the backward runs with
+// the weighted adjoints and the gradient replaces the force output.
+qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int* types, const double box[9],
+                         void* stream, const qnep_outputs* out, const qnep_vjp* vjp) {
     if (!m) return QNEP_ERR_ARG;
     if (n < 1 || n > INDEX_MASK) return fail(m, QNEP_ERR_ARG, "atom count out of range");
     if (!positions || !types || !out) return fail(m, QNEP_ERR_ARG, "NULL input or output struct");
@@ -518,8 +524,9 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
     if (s != QNEP_OK) return s;
     const bool ewald = m->es.mode != 0 && m->es.kind == QNEP_EWALD;
     const bool pppm = m->es.mode != 0 && m->es.kind == QNEP_PPPM;
-    const bool backward = out->forces || out->bec || out->want_virial;
-    const bool want_bec = out->bec != nullptr;
+    const bool gp_nonzero = vjp && (vjp->polar_weight[0] != 0 || vjp->polar_weight[1] != 0 || vjp->polar_weight[2] != 0);
+    const bool backward = out->forces || out->bec || out->want_virial || vjp;
+    const bool want_bec = out->bec != nullptr || gp_nonzero;
     const float q_target = (float)(m->es.q_total / (double)m->sqrt_eps);   // Q in screened-charge units
     const int cl = m->cap_list > 0 ? m->cap_list : m->cl_alloc;
     const int ca = m->cap_ang > 0 ? m->cap_ang : m->ca_alloc;
@@ -542,7 +549,8 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
         g.ang_sa = 1;
         g.ang_se = n;
     }
-    const FieldIn fin{m->fields, m->fields + n, m->es.mode, (float)m->es.alpha, q_target};
+    const FieldIn fin{m->fields, m->fields + n, m->es.mode, (float)m->es.alpha, q_target,
+                      vjp ? (float)vjp->energy_weight : 1.f, vjp ? vjp->charge_weight : nullptr, m->sidx};
     float* acc12 = reinterpret_cast<float*>(m->fields + 2 * (size_t)n);
     float4* kfield = m->fields;
     float4* rfield = m->fields + n;
@@ -559,7 +567,7 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
         launch_nbr_desc_coop(m->spos4, m->cell_start, m->sidx, n, g, m->d_params, m->lay, cl, ca, m->nbr_list,
                              m->cnt_list, m->nbr_ang, m->cnt_ang, backward ? m->ang : nullptr,
                              backward ? m->du : nullptr, m->dq, m->u, m->q, out->descriptor, m->tab, ewald, m->fields,
-                             m->d_acc, st);
+                             vjp ? vjp->charge_weight : nullptr, m->d_acc, st);
         tm.end(2, st);
     } else {
         tm.begin(1, st);
@@ -570,7 +578,7 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
         launch_descriptor_forward(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
                                   m->lay, backward ? m->ang : nullptr, backward ? m->du : nullptr,
                                   backward ? m->dq : nullptr, m->u, m->q, out->descriptor, m->sidx, m->fields,
-                                  m->d_acc, st);
+                                  vjp ? vjp->charge_weight : nullptr, m->d_acc, st);
         tm.end(2, st);
         tm.begin(3, st);
         if (ewald) launch_ewald_phases(m->spos4, n, m->tab, st);
@@ -614,13 +622,34 @@ qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int
         tm.end(7, st);
     }
     tm.begin(8, st);
+    float gp[3] = {0.f, 0.f, 0.f};
+    if (vjp)
+        for (int d = 0; d < 3; ++d) gp[d] = (float)vjp->polar_weight[d];
     launch_finalize(acc12, n, m->sidx, positions, m->q, q_target, m->sqrt_eps, ec, kfield, rfield, out->forces,
                     out->bec, out->charges, out->potential, m->u, out->site_energy, m->d_acc, out->scalars,
-                    m->d_status, m->fin_done, st);
+                    m->d_status, m->fin_done, st, vjp ? vjp->grad : nullptr, gp);
     tm.end(8, st);
     if (m->profiling) m->pending = true;
     CK(cudaGetLastError());
     return QNEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qnep_status qnep_compute(qnep_model* m, int n, const float* positions, const int* types, const double box[9],
+                         void* stream, const qnep_outputs* out) {
+    return compute_impl(m, n, positions, types, box, stream, out, nullptr);
+}
+
+qnep_status qnep_compute_vjp(qnep_model* m, int n, const float* positions, const int* types, const double box[9],
+                             void* stream, const qnep_outputs* out, const qnep_vjp* vjp) {
+    if (!m) return QNEP_ERR_ARG;
+    if (!vjp || !vjp->grad || !out) return fail(m, QNEP_ERR_ARG, "vector-Jacobian product needs vjp->grad");
+    if (out->forces) return fail(m, QNEP_ERR_ARG, "forces output must be NULL in a vector-Jacobian product");
+    if (!std::isfinite(vjp->energy_weight)) return fail(m, QNEP_ERR_ARG, "non-finite energy weight");
+    return compute_impl(m, n, positions, types, box, stream, out, vjp);
 }
 
 qnep_status qnep_sync_status(qnep_model* m, void* stream) {

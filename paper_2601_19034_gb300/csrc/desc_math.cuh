@@ -176,6 +176,15 @@ __device__ __forceinline__ void zero_atom_fields(float4* __restrict__ base, int 
 // Corrected charge q^c_k, total potential phi_k = phi^k + phi^r + phi^s and its
 // mean over atoms (sum phi^k and sum phi^r are accumulated by the field kernels;
 // sum_k phi^s_k = -2 k_e alpha / sqrt(pi) sum q^c = -2 k_e alpha / sqrt(pi) Q / sqrt(eps_inf)).
+// Weight of dq_k/dD in the adjoint: g_E (phi_k - mean phi) + (g_q,k - mean g_q)
+// (the charge correction makes dq^c_j/dq_l = delta_jl - 1/N).
+__device__ __forceinline__ float charge_adjoint_weight(const FieldIn& fin, const Accum* __restrict__ acc_in, int k,
+                                                       int n, float dphi) {
+    float w = fin.e_weight * dphi;
+    if (fin.gq) w += __ldg(&fin.gq[__ldg(&fin.sidx[k])]) - (float)(acc_in->sum_gq / (double)n);
+    return w;
+}
+
 __device__ __forceinline__ void assemble_potential(const FieldIn& fin, const Accum* __restrict__ acc_in,
                                                    const float* __restrict__ q_raw, int k, int n, float& qc,
                                                    float& phi_k, float& phibar) {

@@ -31,14 +31,14 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
                                                   float* __restrict__ dq, float* __restrict__ u_out,
                                                   float* __restrict__ q_out, float* __restrict__ des_out,
                                                   const int* __restrict__ sidx, float4* __restrict__ fields,
-                                                  Accum* __restrict__ acc) {
+                                                  const float* __restrict__ gq_in, Accum* __restrict__ acc) {
     extern __shared__ float sp[];
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / TPA;
     const int lane = gt % TPA;
-    double su = 0.0, sq = 0.0;
+    double su = 0.0, sq = 0.0, sg = 0.0;
     if (i < n) {
         const unsigned gm = group_mask<TPA>();
         const int S = lay.n_species;
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
             q_out[i] = qq;
             su = (double)uu;
             sq = (double)qq;
+            if (gq_in) sg = (double)__ldg(&gq_in[__ldg(&sidx[i])]);
         }
         for (int part = lane; part < 5; part += TPA) zero_atom_fields(fields, n, i, part);
     }
@@ -216,10 +217,12 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
     for (int o = 16; o > 0; o >>= 1) {
         su += __shfl_xor_sync(0xffffffffu, su, o);
         sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&acc->sum_u, su);
         atomicAdd(&acc->sum_q, sq);
+        if (gq_in) atomicAdd(&acc->sum_gq, sg);
     }
 }
 
@@ -276,12 +279,12 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
         const float seps = sp[lay.sqrt_eps];
         float qc, phi_i, phibar;
         assemble_potential(fin, acc_in, q_raw, i, n, qc, phi_i, phibar);
-        const float dphi = phi_i - phibar;
+        const float wq = charge_adjoint_weight(fin, acc_in, i, n, phi_i - phibar);
         float lam[NDES], kap[NDES];
 #pragma unroll
         for (int v = 0; v < NDES; ++v) {
             float gq = __ldg(&dqp[(size_t)v * n + i]);
-            lam[v] = fmaf(dphi, gq, __ldg(&du[(size_t)v * n + i]));
+            lam[v] = fmaf(wq, gq, fin.e_weight * __ldg(&du[(size_t)v * n + i]));
             kap[v] = seps * gq;
         }
         // adjoint-weighted angular coefficients: Phi_{n,lm} = dE/dA_{n,lm}
@@ -427,9 +430,9 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
         if (lane == 0) {
             // static electrostatic force q_i F^k / q + F^r and the BEC diagonal q~^c
             const float4 kf = fin.kfield[i], rf = fin.rfield[i];
-            const float qt = seps * qc;
-            atomicAdd(&acc12[3 * i + 0], make_float4(fi[0] + fmaf(qc, kf.x, rf.x), fi[1] + fmaf(qc, kf.y, rf.y),
-                                                     fi[2] + fmaf(qc, kf.z, rf.z), zi[0] + qt));
+            const float qt = seps * qc, ew = fin.e_weight;
+            atomicAdd(&acc12[3 * i + 0], make_float4(fi[0] + ew * fmaf(qc, kf.x, rf.x), fi[1] + ew * fmaf(qc, kf.y, rf.y),
+                                                     fi[2] + ew * fmaf(qc, kf.z, rf.z), zi[0] + qt));
             atomicAdd(&acc12[3 * i + 1], make_float4(zi[1], zi[2], zi[3], zi[4] + qt));
             atomicAdd(&acc12[3 * i + 2], make_float4(zi[5], zi[6], zi[7], zi[8] + qt));
         }
@@ -454,12 +457,12 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
 template <int TPA>
 void fwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
                 const float* params, const ParamLayout& lay, float* ang, float* du, float* dq, float* u, float* q,
-                float* des, const int* sidx, float4* fields, Accum* acc, cudaStream_t st) {
+                float* des, const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st) {
     const int threads = 128;
     long long blocks = ((long long)n * TPA + threads - 1) / threads;
     size_t smem = sizeof(float) * lay.total;
     k_desc_fwd<TPA><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq, u,
-                                                             q, des, sidx, fields, acc);
+                                                             q, des, sidx, fields, gq, acc);
 }
 
 template <int TPA, bool BEC>
@@ -490,14 +493,14 @@ int choose_tpa(int n) {
 void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                                const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                                float* ang_coef, float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               const int* sidx, float4* fields, Accum* acc, cudaStream_t st) {
+                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st) {
     if (n == 0) return;
     if (choose_tpa(n) == 2)
         fwd_launch<2>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, sidx, fields, acc, st);
+                      des_out, sidx, fields, gq, acc, st);
     else
         fwd_launch<1>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, sidx, fields, acc, st);
+                      des_out, sidx, fields, gq, acc, st);
 }
 
 void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     const float* __restrict__ params, ParamLayout lay, int cap_l, int cap_a, int* __restrict__ nbr_list,
     int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang, float* __restrict__ ang_coef,
     float* __restrict__ du, float* __restrict__ dq, float* __restrict__ u_out, float* __restrict__ q_out,
-    float* __restrict__ des_out, EwaldTab tab, int do_phase, float4* __restrict__ fields, Accum* __restrict__ acc) {
+    float* __restrict__ des_out, EwaldTab tab, int do_phase, float4* __restrict__ fields,
+    const float* __restrict__ gq_in, Accum* __restrict__ acc) {
     extern __shared__ float csm[];
     float* sp = csm;
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     float* dbuf = abuf + NANG;
     float* hb = dbuf + 32;
     __syncthreads();
-    double su = 0.0, sq = 0.0;
+    double su = 0.0, sq = 0.0, sg = 0.0;
     // dynamic scheduling: each warp takes the next atom until all are done
     for (;;) {
         int k = 0;
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
             q_out[k] = qq;
             su += (double)uu;   // a warp handles several atoms
             sq += (double)qq;
+            if (gq_in) sg += (double)__ldg(&gq_in[__ldg(&sidx[k])]);
         }
         if (do_phase) {
             for (int e = lane; e < tab.nph; e += 32) tab.phase[(size_t)k * tab.nph + e] = phase_entry(pk, e, tab);
@@ -218,20 +220,23 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
         __syncwarp();   // shared buffers are reused by the warp's next atom
     }
     // block sums of U and q (FP64), one atomic per block
-    __shared__ double red[2][CW];
+    __shared__ double red[3][CW];
     if (lane == 0) {
         red[0][wib] = su;
         red[1][wib] = sq;
+        red[2][wib] = sg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        double a = 0.0, b = 0.0, cg = 0.0;
         for (int w = 0; w < CW; ++w) {
             a += red[0][w];
             b += red[1][w];
+            cg += red[2][w];
         }
         atomicAdd(&acc->sum_u, a);
         atomicAdd(&acc->sum_q, b);
+        if (gq_in) atomicAdd(&acc->sum_gq, cg);
     }
 }
 
@@ -292,10 +297,10 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
         const float seps = sp[lay.sqrt_eps];
         float qc, phi_k, phibar;
         assemble_potential(fin, acc_in, q_raw, k, n, qc, phi_k, phibar);
-        const float dphi = phi_k - phibar;
+        const float wq = charge_adjoint_weight(fin, acc_in, k, n, phi_k - phibar);
         if (lane < NDES) {
             float gq = __ldg(&dqp[(size_t)k * NDES + lane]);
-            lk[lane] = fmaf(dphi, gq, __ldg(&du[(size_t)k * NDES + lane]));
+            lk[lane] = fmaf(wq, gq, fin.e_weight * __ldg(&du[(size_t)k * NDES + lane]));
             lk[32 + lane] = seps * gq;
         }
         __syncwarp();
@@ -439,9 +444,9 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
         if (lane == 0) {
             // static electrostatic force q_k F^k / q + F^r and the BEC diagonal q~^c
             const float4 kf = fin.kfield[k], rf = fin.rfield[k];
-            const float qt = seps * qc;
-            atomicAdd(&acc12[3 * k + 0], make_float4(fi[0] + fmaf(qc, kf.x, rf.x), fi[1] + fmaf(qc, kf.y, rf.y),
-                                                     fi[2] + fmaf(qc, kf.z, rf.z), zi[0] + qt));
+            const float qt = seps * qc, ew = fin.e_weight;
+            atomicAdd(&acc12[3 * k + 0], make_float4(fi[0] + ew * fmaf(qc, kf.x, rf.x), fi[1] + ew * fmaf(qc, kf.y, rf.y),
+                                                     fi[2] + ew * fmaf(qc, kf.z, rf.z), zi[0] + qt));
             atomicAdd(&acc12[3 * k + 1], make_float4(zi[1], zi[2], zi[3], zi[4] + qt));
             atomicAdd(&acc12[3 * k + 2], make_float4(zi[5], zi[6], zi[7], zi[8] + qt));
         }
@@ -477,8 +482,8 @@ size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a) {
 void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq, float* u,
-                          float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields, Accum* acc,
-                          cudaStream_t st) {
+                          float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
+                          const float* gq, Accum* acc, cudaStream_t st) {
     if (n == 0) return;
     static bool attr = false;
     if (!attr) {
@@ -492,7 +497,7 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
     if (per_sm > 0 && blocks > per_sm * g_num_sms) blocks = per_sm * g_num_sms;
     k_nbr_desc_coop<<<blocks, 32 * CW, smem, st>>>(
         spos4, cell_start, sidx, n, g, params, lay, cap_l, cap_a, nbr_list, cnt_list, nbr_ang, cnt_ang, ang_coef, du,
-        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, acc);
+        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc);
 }
 
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,

@@ -393,7 +393,8 @@ __global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __
                            const float4* __restrict__ rfield, float* __restrict__ forces, float* __restrict__ bec,
                            float* __restrict__ charges, float* __restrict__ potential, const float* __restrict__ u,
                            float* __restrict__ site_energy, Accum* __restrict__ acc, double* __restrict__ scalars,
-                           unsigned int* __restrict__ status_host, unsigned int* __restrict__ done) {
+                           unsigned int* __restrict__ status_host, unsigned int* __restrict__ done,
+                           float* __restrict__ grad, float gpx, float gpy, float gpz) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     // FP32 terms summed over a warp (32 atoms), then FP64 across warps and blocks
     float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // P (3), U^s, sum q~^c
@@ -411,6 +412,11 @@ __global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __
         if (bec) {
 #pragma unroll
             for (int q = 0; q < 9; ++q) bec[9 * (size_t)io + q] = a[3 + q];
+        }
+        if (grad) {   // -F of the weighted objective plus g_P . Z (Z_ab = a[3 + 3a + b])
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                grad[3 * (size_t)io + b] = -a[b] + gpx * a[3 + b] + gpy * a[6 + b] + gpz * a[9 + b];
         }
         if (charges) charges[io] = qc;
         const float phs = ec.mode == 1 ? -2.f * KE * ec.alpha * INV_SQRT_PI * qc : 0.f;
@@ -524,11 +530,13 @@ void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cuda
 void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
                      float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
                      float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
-                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st) {
+                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st,
+                     float* grad, const float* gp) {
     int blocks = (n + 255) / 256;
     if (blocks < 1) blocks = 1;
     k_finalize<<<blocks, 256, 0, st>>>(acc12, n, sidx, pos_in, q_raw, q_target, seps, ec, kfield, rfield, forces, bec,
-                                       charges, potential, u, site_energy, acc, scalars, status_host, done);
+                                       charges, potential, u, site_energy, acc, scalars, status_host, done, grad,
+                                       gp ? gp[0] : 0.f, gp ? gp[1] : 0.f, gp ? gp[2] : 0.f);
 }
 
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi, float* potential,

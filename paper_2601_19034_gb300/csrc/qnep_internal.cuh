@@ -90,6 +90,7 @@ struct Accum {
     double virial[9];
     double polar[3];
     double sum_qc;       // sum of corrected naked charges q~^c
+    double sum_gq;       // sum of the charge weights of a vector-Jacobian product
     unsigned int status; // bit 0: neighbour overflow, bit 1: a bounded wait gave up
     unsigned int work_fwd;   // atom counters of the dynamically scheduled warp-per-atom kernels
     unsigned int work_bwd;
@@ -111,6 +112,9 @@ struct FieldIn {
     int mode;
     float alpha;
     float q_target;         // Q in screened-charge units (Q / sqrt(eps_inf))
+    float e_weight;         // weight of the energy (1 for forces)
+    const float* gq;        // per-atom charge weights in input order (NULL: none)
+    const int* sidx;        // input index of each sorted atom (for gq)
 };
 
 // Ewald k-space description (host-built, uploaded when the box changes).
@@ -174,14 +178,14 @@ void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const in
                                const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
                                const float* params, const ParamLayout& lay, float* ang_coef,
                                float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               const int* sidx, float4* fields, Accum* acc, cudaStream_t st);
+                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st);
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a);
 void set_num_sms(int n);
 void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,
                           float* u, float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
-                          Accum* acc, cudaStream_t st);
+                          const float* gq, Accum* acc, cudaStream_t st);
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                           const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                           const float* ang_coef, const float* du, const float* dq, const float* q_raw,
@@ -211,7 +215,8 @@ int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc
 void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
                      float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
                      float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
-                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st);
+                     Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st,
+                     float* grad = nullptr, const float* gp = nullptr);
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi,
                            float* potential, cudaStream_t st);
 void launch_finalize_scalars(const Accum* acc, int n, float sqrt_eps, double* scalars, cudaStream_t st);

@@ -157,6 +157,27 @@ class QNEP:
         self._caps = (cl, ca)
         self.set_capacity(cl, ca)
 
+    def vjp(self, positions: torch.Tensor, types: torch.Tensor, box, g_energy: float, g_charges=None,
+            g_polar=(0.0, 0.0, 0.0), stream=None) -> torch.Tensor:
+        """g_E dU/dr + sum_j g_q,j dq^c_j/dr + g_P . Z (Z: periodic Born effective charges), [N, 3]."""
+        n = positions.shape[0]
+        grad = torch.empty(n, 3, dtype=torch.float32, device=positions.device)
+        scal = torch.zeros(_lib.QNEP_NSCALARS, dtype=torch.float64, device=positions.device)
+        oc = _lib.OutputsC(scal.data_ptr(), None, None, None, None, None, None, 0)
+        gq = None
+        if g_charges is not None:
+            gq = g_charges.detach().to(device=positions.device, dtype=torch.float32).contiguous()
+        vc = _lib.VjpC(float(g_energy), gq.data_ptr() if gq is not None else None,
+                       (ctypes.c_double * 3)(*[float(x) for x in g_polar]), grad.data_ptr())
+        self._set_box(box)
+        if stream is None:
+            stream = torch.cuda.current_stream(positions.device).cuda_stream
+        st = self.lib.qnep_compute_vjp(self.handle, n, positions.data_ptr(), types.data_ptr(), self._box,
+                                       ctypes.c_void_p(stream), ctypes.byref(oc), ctypes.byref(vc))
+        _lib.check(st, self.handle)
+        _lib.check(self.sync_status(), self.handle)
+        return grad
+
     def compute_host(self, positions: np.ndarray, types: np.ndarray, box, forces=True, bec=True,
                      charges=True, virial=True) -> dict:
         """End-to-end call on host arrays through ``qnep_compute_host`` (copies inside)."""
@@ -183,3 +204,38 @@ class QNEP:
                                         ctypes.byref(oc))
         _lib.check(st, self.handle)
         return res
+
+
+class QNEPFunction(torch.autograd.Function):
+    """Differentiable qNEP force call: positions [N, 3] -> (U^tot, q^c [N], P [3]).
+
+    forward runs the force call (energy, corrected screened charges, polarization);
+    backward runs the library's hand-written backward once with the incoming
+    weights (qnep_compute_vjp): g_E dU/dr + sum g_q dq^c/dr + g_P . Z, where the
+    polarization derivative is the periodic Born effective charge of Eq. bec_2.
+    No per-pair derivative is stored between the two calls.
+    """
+
+    @staticmethod
+    def forward(ctx, positions, model, types, box):
+        pos = positions.detach().contiguous()
+        out = model.outputs(pos.shape[0], pos.device, forces=False, bec=False, charges=True, virial=False)
+        model.compute_into(pos, types, box, out)
+        _lib.check(model.sync_status(), model.handle)
+        s = out["scalars"]
+        ctx.model, ctx.types, ctx.box = model, types, box
+        ctx.save_for_backward(pos)
+        return s[0].clone(), out["charges"].to(torch.float64), s[14:17].clone()
+
+    @staticmethod
+    def backward(ctx, g_energy, g_charges, g_polar):
+        (pos,) = ctx.saved_tensors
+        ge = float(g_energy) if g_energy is not None else 0.0
+        gp = [float(x) for x in g_polar] if g_polar is not None else [0.0, 0.0, 0.0]
+        grad = ctx.model.vjp(pos, ctx.types, ctx.box, ge, g_charges, gp)
+        return grad.to(pos.dtype), None, None, None
+
+
+def qnep_energy(model: QNEP, positions: torch.Tensor, types: torch.Tensor, box):
+    """(U^tot, q^c, P) with autograd support (QNEPFunction)."""
+    return QNEPFunction.apply(positions, model, types, box)

@@ -183,3 +183,24 @@ def test_cluster_bec_relative_form_matches_dp_dr():
                 p_plus = fc.polarization_autograd(pp, box, types, hp, blob, elec)[0].numpy()
                 p_minus = fc.polarization_autograd(pm, box, types, hp, blob, elec)[0].numpy()
             np.testing.assert_allclose((p_plus - p_minus) / (2 * h), z[i][:, b], atol=1e-8)
+
+
+def test_charge_gradient_matches_finite_differences(batio3_subcell):
+    """d(sum_i c_i q^c_i)/dr by autograd against central differences (charge correction included)."""
+    pos, box, types, hp, blob, elec = batio3_subcell
+    c = np.random.default_rng(3).normal(size=len(pos))
+    qc, leaf = fc.charges_autograd(pos, box, types, hp, blob, elec)
+    (torch.as_tensor(c) * qc).sum().backward()
+    grad = leaf.grad.numpy()
+    h = 1e-5
+    for i, d in ((1, 0), (22, 2), (35, 1)):
+        pp, pm = pos.copy(), pos.copy()
+        pp[i, d] += h
+        pm[i, d] -= h
+        with torch.no_grad():
+            fp = float((torch.as_tensor(c) * fc.charges_autograd(pp, box, types, hp, blob, elec)[0]).sum())
+            fm = float((torch.as_tensor(c) * fc.charges_autograd(pm, box, types, hp, blob, elec)[0]).sum())
+        assert abs((fp - fm) / (2 * h) - grad[i, d]) < 1e-7
+    # and it agrees with the staged force call's charges
+    out = fc.force_call(pos, box, types, hp, blob, elec, want_bec=False)
+    np.testing.assert_allclose(qc.detach().numpy(), out["charges"], atol=1e-12)
