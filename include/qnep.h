@@ -219,6 +219,60 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
                                       float* forces, double* energy_virial, void* stream, char* err,
                                       size_t err_len);
 
+/* ---- Batched evaluation -----------------------------------------------------
+ * Many structures of uneven size, each under many candidate parameter vectors:
+ * the shape of a separable natural-evolution-strategy fitness evaluation, where
+ * every candidate of the population is scored on every training structure
+ * (Sec. II.E; the training loss weighs energies, forces and charges).  One call
+ * returns, for every (candidate c, structure s), the total energy U^tot
+ * (Eq. U_i, Eq. U_ES with the charges of Sec. II.D), the forces including the
+ * charge-derivative terms (Sec. II.C) and the corrected charges q^c.
+ * Electrostatics: Ewald (mode 1 or 2) per structure; PPPM is not offered here.
+ * Virial, BEC and polarization are not computed by the batched call.
+ *
+ * qnep_batch_create: hp and es as for qnep_create (es->kind must be QNEP_EWALD);
+ *   params_host = n_candidates blobs of qnep_param_count(hp) floats, candidate-major.
+ * qnep_batch_compute (asynchronous on `stream`, no host synchronisation once the
+ *   batch description is known, so it can be captured in a CUDA graph):
+ *   atom_offsets: host [n_struct + 1], atom_offsets[0] = 0, non-decreasing;
+ *                 structure s holds atoms atom_offsets[s] .. atom_offsets[s+1]-1
+ *   positions:    device [N_total][3] float32 (A), types: device [N_total] int32
+ *   boxes:        host [n_struct][9] doubles, orthorhombic, every edge >= the
+ *                 neighbour-list cutoff; at most 32768 atoms per structure
+ *   energy:       device [n_candidates][n_struct] doubles (eV)
+ *   forces:       device [n_candidates][N_total][3] float32 (eV/A), or NULL
+ *   charges:      device [n_candidates][N_total] float32 (e), or NULL
+ * The first call with a new (atom_offsets, boxes) builds the k-tables and work
+ * list on the host and (re)allocates workspaces; later identical calls only
+ * launch.  Errors in the arguments return before any GPU work; device-side
+ * conditions (list overflow, a species index out of range) are reported by
+ * qnep_batch_sync_status (QNEP_ERR_NBR_OVERFLOW: raise the capacity with
+ * qnep_batch_set_capacity and call again; outputs of that call are invalid).
+ * Caller owns every buffer; the batch owns its device copies and workspaces. */
+typedef struct qnep_batch qnep_batch;
+enum { QNEP_BATCH_ORDER_LARGEST_FIRST = 0, QNEP_BATCH_ORDER_STRUCTURE = 1 };
+qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const float* params_host,
+                              size_t n_params, int n_candidates, const qnep_elec* es);
+qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                               const int* types, const double* boxes, void* stream, double* energy,
+                               float* forces, float* charges);
+qnep_status qnep_batch_sync_status(qnep_batch* b);
+/* Neighbour capacities (entries per atom; 0 = from the densest structure) and their current values. */
+qnep_status qnep_batch_set_capacity(qnep_batch* b, int cap_list, int cap_angular);
+qnep_status qnep_batch_capacity(const qnep_batch* b, int* cap_list, int* cap_angular);
+/* Launch configuration: warps per block of the item kernel (4 or 8) and the order
+ * in which blocks take the (structure, candidate-group) items. */
+qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order);
+qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
+/* Autotuner: times every launch configuration on this batch (`reps` calls each,
+ * median, CUDA events on `stream`), keeps the fastest and returns its time (ms).
+ * Writes the same outputs as qnep_batch_compute. Synchronizes the stream. */
+qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                                const int* types, const double* boxes, void* stream, double* energy,
+                                float* forces, float* charges, int reps, double* best_ms);
+const char* qnep_batch_last_error(const qnep_batch* b);
+void        qnep_batch_destroy(qnep_batch* b);
+
 void        qnep_destroy(qnep_model* m);
 const char* qnep_status_string(qnep_status s);
 const char* qnep_last_error(qnep_model* m);   /* detail of the last failing call */

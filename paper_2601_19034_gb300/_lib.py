@@ -26,6 +26,7 @@ QNEP_PREC_MLP_BF16 = 1
 QNEP_PREC_MLP_TF32 = 2
 QNEP_NSCALARS = 20
 QNEP_NSTAGES = 10
+QNEP_BATCH_ORDER_LARGEST_FIRST, QNEP_BATCH_ORDER_STRUCTURE = 0, 1
 QNEP_PATH_AUTO = 0
 QNEP_PATH_WARP = 1
 QNEP_PATH_THREAD = 2
@@ -97,6 +98,28 @@ def _declare(lib):
     lib.qnep_stage_times.restype = i
     lib.qnep_stage_name.argtypes = [i]
     lib.qnep_stage_name.restype = ctypes.c_char_p
+    # batched evaluation
+    lib.qnep_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(HParamsC), p, ctypes.c_size_t, i,
+                                      ctypes.POINTER(ElecC)]
+    lib.qnep_batch_create.restype = i
+    lib.qnep_batch_compute.argtypes = [p, i, p, p, p, p, p, p, p, p]
+    lib.qnep_batch_compute.restype = i
+    lib.qnep_batch_sync_status.argtypes = [p]
+    lib.qnep_batch_sync_status.restype = i
+    lib.qnep_batch_set_capacity.argtypes = [p, i, i]
+    lib.qnep_batch_set_capacity.restype = i
+    lib.qnep_batch_capacity.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.qnep_batch_capacity.restype = i
+    lib.qnep_batch_set_config.argtypes = [p, i, i]
+    lib.qnep_batch_set_config.restype = i
+    lib.qnep_batch_get_config.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.qnep_batch_get_config.restype = i
+    lib.qnep_batch_autotune.argtypes = [p, i, p, p, p, p, p, p, p, p, i, ctypes.POINTER(ctypes.c_double)]
+    lib.qnep_batch_autotune.restype = i
+    lib.qnep_batch_last_error.argtypes = [p]
+    lib.qnep_batch_last_error.restype = ctypes.c_char_p
+    lib.qnep_batch_destroy.argtypes = [p]
+    lib.qnep_batch_destroy.restype = None
     return lib
 
 
@@ -118,8 +141,11 @@ class QnepError(RuntimeError):
         self.status = status
 
 
-def check(status: int, model=None):
+def check(status: int, model=None, batch=None):
     if status != QNEP_OK:
         lib = load()
-        detail = lib.qnep_last_error(model).decode() if model else ""
+        if batch:
+            detail = lib.qnep_batch_last_error(batch).decode()
+        else:
+            detail = lib.qnep_last_error(model).decode() if model else ""
         raise QnepError(status, detail)

@@ -11,6 +11,7 @@
 
 #include "../../include/qnep.h"
 #include "qnep_internal.cuh"
+#include "kset_host.h"
 
 using namespace qnep;
 
@@ -125,43 +126,12 @@ float list_cutoff(const qnep_model* m) {
 
 // Half-space Ewald k-set in columns (n1, n2) with runs of n3, chunks of 8.
 qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
-    const double two_pi = 6.283185307179586;
-    const double kmax = m->es.kmax, alpha = m->es.alpha;
-    const double vol = L[0] * L[1] * L[2];
-    int nmax[3];
-    for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(kmax * L[d] / two_pi);
-    std::vector<int4> cols;
-    std::vector<float> kg;
-    std::vector<int> chunk_col;
-    for (int n1 = 0; n1 <= nmax[0]; ++n1) {
-        for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2) {
-            if (n1 == 0 && n2 < 0) continue;
-            double kx = two_pi * n1 / L[0], ky = two_pi * n2 / L[1];
-            int lo = 1 << 30, hi = -(1 << 30);
-            for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
-                if (n1 == 0 && n2 == 0 && n3 <= 0) continue;
-                double kz = two_pi * n3 / L[2];
-                double k2 = kx * kx + ky * ky + kz * kz;
-                if (k2 > 0 && k2 < kmax * kmax) {
-                    lo = std::min(lo, n3);
-                    hi = std::max(hi, n3);
-                }
-            }
-            if (hi < lo) continue;
-            int nchunk = (hi - lo + 1 + 7) / 8;
-            int c = (int)cols.size();
-            cols.push_back(make_int4(n1, n2, lo, (int)kg.size()));
-            for (int h = 0; h < nchunk; ++h) chunk_col.push_back(c);
-            for (int t = 0; t < 8 * nchunk; ++t) {
-                int n3 = lo + t;
-                double kz = two_pi * n3 / L[2];
-                double k2 = kx * kx + ky * ky + kz * kz;
-                bool ok = n3 <= hi && k2 > 0 && k2 < kmax * kmax && !(n1 == 0 && n2 == 0 && n3 <= 0);
-                kg.push_back(ok ? (float)(two_pi / vol * std::exp(-k2 / (4 * alpha * alpha)) / k2) : 0.f);
-            }
-        }
-    }
-    cols.push_back(make_int4(0, 0, 0, (int)kg.size()));
+    KSet ks = build_kset(L, m->es.kmax, m->es.alpha);
+    const int* nmax = ks.nmax;
+    const std::vector<int4>& cols = ks.cols;
+    const std::vector<int>& chunk_col = ks.chunk_col;
+    const std::vector<float>& kg = ks.kg;
+    const double alpha = m->es.alpha;
     int ncol = (int)cols.size() - 1, nk = (int)kg.size(), nch = (int)chunk_col.size();
     if (ncol + 1 > m->ncol_alloc) {
         CK(grow(&m->d_col, ncol + 1));

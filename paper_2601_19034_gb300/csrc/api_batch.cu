@@ -1,0 +1,533 @@
+// C ABI of the batched force call (include/qnep.h, "Batched evaluation"): the batch
+// description (structures, boxes, k-tables, work items), its workspaces, the launch
+// sequence and the autotuner that picks the block shape and the item order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/qnep.h"
+#include "batch_internal.cuh"
+#include "kset_host.h"
+
+using namespace qnep;
+
+struct qnep_batch {
+    qnep_hparams hp{};
+    qnep_elec es{};
+    ParamLayout lay{};
+    int n_cand = 0, n_groups = 0;
+    float* d_pt = nullptr;                  // [group][p][CG]
+    int cap_l_user = 0, cap_a_user = 0;
+    int warps = 8;                          // warps per block of the item kernel (4 or 8)
+    int order_policy = QNEP_BATCH_ORDER_LARGEST_FIRST;
+    int num_sms = 152;
+    // batch description (rebuilt when the structures or boxes change)
+    bool have_desc = false;
+    int n_struct = 0, n_total = 0, nmax = 0, nph_max = 0, nk_max = 0;
+    std::vector<int> h_off;
+    std::vector<double> h_box;
+    int cap_l = 0, cap_a = 0;
+    std::vector<int2> items_lpt, items_nat;
+    BatchStruct* d_st = nullptr;
+    BatchKTab* d_kt = nullptr;
+    int4* d_chunk = nullptr;
+    float4* d_kvec = nullptr;
+    int2* d_items_lpt = nullptr;
+    int2* d_items_nat = nullptr;
+    int n_items = 0;
+    // pre-pass outputs (element counts allocated)
+    struct {
+        size_t spos4 = 0, sidx = 0, order = 0, spec = 0, cells = 0, list = 0, ang = 0, cnt_list = 0, cnt_ang = 0,
+               phase = 0;
+    } alloc;
+    float4* spos4 = nullptr;
+    int* sidx = nullptr;
+    int* order = nullptr;
+    int* spec_off = nullptr;
+    int* cell_start = nullptr;
+    int* nbr_list = nullptr;
+    int* cnt_list = nullptr;
+    int* nbr_ang = nullptr;
+    int* cnt_ang = nullptr;
+    float2* phase = nullptr;
+    // per-slot scratch
+    size_t slot_bytes_alloc = 0;
+    int slots_alloc = 0;
+    BatchScratch sc{};
+    float* scratch = nullptr;
+    unsigned int* d_work = nullptr;
+    unsigned int* d_status = nullptr;
+    cudaStream_t last_stream = nullptr;
+    std::map<std::pair<int, int>, int> per_sm_cache;   // (warps, nph_max) -> resident blocks per SM
+    std::string err;
+};
+
+namespace {
+
+qnep_status failb(qnep_batch* b, qnep_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    return s;
+}
+
+#define CKB(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return failb(b, e_ == cudaErrorMemoryAllocation ? QNEP_ERR_OOM : QNEP_ERR_CUDA,        \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+template <class T>
+cudaError_t regrow(T** p, size_t count, size_t* have) {
+    if (count <= *have && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+    if (e == cudaSuccess) *have = count;
+    return e;
+}
+
+template <class T>
+cudaError_t upload(T** p, const std::vector<T>& v) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+float list_cutoff_b(const qnep_batch* b) {
+    float rc = b->hp.rc_radial;
+    if (b->es.mode == 1 && (float)b->es.rc_real > rc) rc = (float)b->es.rc_real;
+    return rc;
+}
+
+// Structures, boxes, k-tables and work items of a new batch description.
+qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* boxes, cudaStream_t st) {
+    const float rcl = list_cutoff_b(b);
+    std::vector<BatchStruct> sts(n_struct);
+    std::vector<BatchKTab> kts;
+    std::vector<int4> chunks;
+    std::vector<float4> kvec;
+    std::map<std::tuple<double, double, double>, int> tab_of;
+    std::vector<int> nk_of;   // padded k count per table
+    int cell_total = 0, nmax = 0, nph_max = 0, nk_max = 0;
+    double dens_max = 0.0;
+    const double two_pi = 6.283185307179586, ke = 14.3996454784;
+    for (int s = 0; s < n_struct; ++s) {
+        const double* bx = boxes + 9 * (size_t)s;
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(bx[k])) return failb(b, QNEP_ERR_ARG, "box has a non-finite entry");
+        if (bx[1] != 0 || bx[2] != 0 || bx[3] != 0 || bx[5] != 0 || bx[6] != 0 || bx[7] != 0)
+            return failb(b, QNEP_ERR_UNSUPPORTED, "only orthorhombic boxes are supported");
+        const double L[3] = {bx[0], bx[4], bx[8]};
+        BatchStruct& t = sts[s];
+        t.atom_off = off[s];
+        t.n = off[s + 1] - off[s];
+        if (t.n < 0) return failb(b, QNEP_ERR_ARG, "atom offsets must be non-decreasing");
+        if (t.n > 32768) return failb(b, QNEP_ERR_UNSUPPORTED, "batched structures hold at most 32768 atoms");
+        nmax = std::max(nmax, t.n);
+        Geom& g = t.g;
+        g.ncells = 1;
+        for (int d = 0; d < 3; ++d) {
+            if (!(L[d] > 0)) return failb(b, QNEP_ERR_ARG, "box edge must be positive");
+            if (L[d] < rcl) return failb(b, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff");
+            g.L[d] = (float)L[d];
+            g.invL[d] = (float)(1.0 / L[d]);
+            int nc = (int)std::floor(L[d] / rcl);
+            g.nc[d] = std::min(std::max(nc, 1), 8);
+            g.ncells *= g.nc[d];
+        }
+        g.rc_list = rcl;
+        g.rc_radial = b->hp.rc_radial;
+        g.rc_angular = b->hp.rc_angular;
+        g.rc_real = b->es.mode == 1 ? (float)b->es.rc_real : 0.f;
+        g.list_sa = g.list_se = g.ang_sa = g.ang_se = 0;
+        t.cell_off = cell_total;
+        cell_total += g.ncells + 1;
+        dens_max = std::max(dens_max, t.n / (L[0] * L[1] * L[2]));
+        auto key = std::make_tuple(L[0], L[1], L[2]);
+        auto it = tab_of.find(key);
+        if (it == tab_of.end()) {
+            KSet ks = build_kset(L, b->es.kmax, b->es.alpha);
+            BatchKTab kt{};
+            kt.n1max = ks.nmax[0];
+            kt.n2max = ks.nmax[1];
+            kt.n3max = ks.nmax[2];
+            kt.yoff = kt.n1max + 1;
+            kt.zoff = kt.yoff + 2 * kt.n2max + 1;
+            kt.nph = kt.zoff + 2 * kt.n3max + 8;
+            if (kt.nph > BATCH_MAX_NPH)
+                return failb(b, QNEP_ERR_UNSUPPORTED, "box too large for the batched k-space tables");
+            kt.nchunk = (int)ks.chunk_col.size();
+            kt.chunk_off = (int)chunks.size();
+            for (int d = 0; d < 3; ++d) {
+                double il = 1.0 / L[d];
+                kt.invl_hi[d] = (float)il;
+                kt.invl_lo[d] = (float)(il - (double)kt.invl_hi[d]);
+            }
+            for (int h = 0; h < kt.nchunk; ++h) {
+                const int4& c = ks.cols[ks.chunk_col[h]];
+                const int n3 = c.z + (8 * h - c.w);
+                chunks.push_back(make_int4(c.x, c.y, n3, 0));
+                for (int q = 0; q < 8; ++q) {
+                    const float gk = ks.kg[8 * h + q];
+                    kvec.push_back(make_float4((float)(two_pi * c.x / L[0]), (float)(two_pi * c.y / L[1]),
+                                               (float)(two_pi * (n3 + q) / L[2]), (float)(4.0 * ke * gk)));
+                }
+            }
+            nph_max = std::max(nph_max, kt.nph);
+            nk_max = std::max(nk_max, 8 * kt.nchunk);
+            it = tab_of.emplace(key, (int)kts.size()).first;
+            kts.push_back(kt);
+            nk_of.push_back(8 * kt.nchunk);
+        }
+        t.ktab = it->second;
+    }
+    if (nph_max % 2 == 0) nph_max += 1;
+    // neighbour capacities from the densest structure (2x the mean count + margin)
+    const double pi43 = 4.18879020478639;
+    int cl = b->cap_l_user, ca = b->cap_a_user;
+    if (cl <= 0) cl = ((int)(2.0 * pi43 * rcl * rcl * rcl * dens_max) + 32 + 31) / 32 * 32;
+    if (ca <= 0) {
+        double ra = b->hp.rc_angular;
+        ca = ((int)(2.0 * pi43 * ra * ra * ra * dens_max) + 16 + 15) / 16 * 16;
+    }
+    // work items: (structure, group); cost ~ atoms x (descriptor work + wave vectors)
+    std::vector<std::pair<double, int2>> it;
+    for (int s = 0; s < n_struct; ++s) {
+        if (sts[s].n == 0) continue;
+        const double cost = (double)sts[s].n * (2800.0 + nk_of[sts[s].ktab]);
+        for (int gi = 0; gi < b->n_groups; ++gi) it.push_back({cost, make_int2(s, gi)});
+    }
+    b->items_nat.clear();
+    for (auto& x : it) b->items_nat.push_back(x.second);
+    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+        return x.first > y.first;
+    });
+    b->items_lpt.clear();
+    for (auto& x : it) b->items_lpt.push_back(x.second);
+    // uploads (in-flight work of the previous description may still read the old tables)
+    if (b->have_desc && b->last_stream) CKB(cudaStreamSynchronize(b->last_stream));
+    CKB(cudaStreamSynchronize(st));
+    CKB(upload(&b->d_st, sts));
+    CKB(upload(&b->d_kt, kts));
+    CKB(upload(&b->d_chunk, chunks));
+    CKB(upload(&b->d_kvec, kvec));
+    CKB(upload(&b->d_items_lpt, b->items_lpt));
+    CKB(upload(&b->d_items_nat, b->items_nat));
+    b->n_items = (int)b->items_lpt.size();
+    b->n_struct = n_struct;
+    b->n_total = off[n_struct];
+    b->nmax = nmax;
+    b->nph_max = nph_max;
+    b->nk_max = nk_max;
+    b->cap_l = cl;
+    b->cap_a = ca;
+    const size_t N = (size_t)b->n_total, S = (size_t)b->hp.n_species;
+    CKB(regrow(&b->spos4, N, &b->alloc.spos4));
+    CKB(regrow(&b->sidx, N, &b->alloc.sidx));
+    CKB(regrow(&b->order, N, &b->alloc.order));
+    CKB(regrow(&b->spec_off, (size_t)n_struct * (MAX_SPECIES + 1), &b->alloc.spec));
+    CKB(regrow(&b->cell_start, (size_t)cell_total, &b->alloc.cells));
+    CKB(regrow(&b->nbr_list, N * (size_t)cl, &b->alloc.list));
+    CKB(regrow(&b->nbr_ang, N * (size_t)ca, &b->alloc.ang));
+    CKB(regrow(&b->cnt_list, N * S, &b->alloc.cnt_list));
+    CKB(regrow(&b->cnt_ang, N * S, &b->alloc.cnt_ang));
+    CKB(regrow(&b->phase, N * (size_t)nph_max, &b->alloc.phase));
+    b->h_off.assign(off, off + n_struct + 1);
+    b->h_box.assign(boxes, boxes + 9 * (size_t)n_struct);
+    b->have_desc = true;
+    return QNEP_OK;
+}
+
+// Per-slot scratch for the current description and block shape.
+qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
+    const size_t nm = (size_t)std::max(b->nmax, 1), nk = (size_t)std::max(b->nk_max, 8);
+    BatchScratch& sc = b->sc;
+    const size_t sA = nm * NANG * CG, sD = nm * 2 * NDES * CG, sN = nm * CG, sK = nk * CG;
+    // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2)
+    const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 64;
+    const size_t bytes = per * sizeof(float) * (size_t)slots;
+    if (bytes > b->slot_bytes_alloc || !b->scratch) {
+        CKB(cudaStreamSynchronize(st));
+        if (b->last_stream) CKB(cudaStreamSynchronize(b->last_stream));
+        if (b->scratch) cudaFree(b->scratch);
+        b->scratch = nullptr;
+        b->slot_bytes_alloc = 0;
+        CKB(cudaMalloc((void**)&b->scratch, bytes));
+        b->slot_bytes_alloc = bytes;
+    }
+    // carve: arrays of all slots back to back (each 16-byte aligned)
+    float* p = b->scratch;
+    auto take = [&](size_t floats) {
+        float* q = p;
+        p += (floats + 3) & ~(size_t)3;
+        return q;
+    };
+    sc.stride_A = sA;
+    sc.stride_duq = sD;
+    sc.stride_n = sN;
+    sc.stride_k = sK;
+    sc.A = take(sA * slots);
+    sc.duq = take(sD * slots);
+    sc.uq = reinterpret_cast<float2*>(take(2 * sN * slots));
+    sc.qc = take(sN * slots);
+    sc.fk = reinterpret_cast<float4*>(take(4 * sN * slots));
+    sc.fr = reinterpret_cast<float4*>(take(4 * sN * slots));
+    sc.fsum = reinterpret_cast<float4*>(take(4 * sN * slots));
+    sc.sk = reinterpret_cast<float2*>(take(2 * sK * slots));
+    b->slots_alloc = slots;
+    return QNEP_OK;
+}
+
+bool same_desc(const qnep_batch* b, int n_struct, const int* off, const double* boxes) {
+    if (!b->have_desc || b->n_struct != n_struct) return false;
+    if (std::memcmp(b->h_off.data(), off, sizeof(int) * (n_struct + 1)) != 0) return false;
+    return std::memcmp(b->h_box.data(), boxes, sizeof(double) * 9 * (size_t)n_struct) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const float* params_host, size_t n_params,
+                              int n_candidates, const qnep_elec* es) {
+    qnep_batch* b = nullptr;
+    if (!out || !hp || !params_host || !es || n_candidates < 1) return QNEP_ERR_ARG;
+    *out = nullptr;
+    if (hp->n_radial != NR || hp->n_angular != NA || hp->basis_radial != KR || hp->basis_angular != KA ||
+        hp->l_max != LMAX || hp->use_4body != 1 || hp->n_neurons != NNEU || hp->n_species < 1 ||
+        hp->n_species > MAX_SPECIES)
+        return QNEP_ERR_UNSUPPORTED;
+    if (!(hp->rc_radial > 0) || !(hp->rc_angular > 0) || hp->rc_angular > hp->rc_radial) return QNEP_ERR_ARG;
+    const size_t per = qnep_param_count(hp);
+    if (n_params != per * (size_t)n_candidates) return QNEP_ERR_ARG;
+    if (es->mode != 1 && es->mode != 2) return QNEP_ERR_UNSUPPORTED;
+    if (es->kind != QNEP_EWALD) return QNEP_ERR_UNSUPPORTED;
+    if (!(es->alpha > 0) || !(es->kmax > 0)) return QNEP_ERR_ARG;
+    if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
+    for (size_t k = 0; k < n_params; ++k)
+        if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
+    b = new qnep_batch();
+    b->hp = *hp;
+    b->es = *es;
+    b->lay = make_layout(hp->n_species);
+    b->n_cand = n_candidates;
+    b->n_groups = (n_candidates + CG - 1) / CG;
+    const size_t P = (size_t)b->lay.total;
+    std::vector<float> pt((size_t)b->n_groups * P * CG, 0.f);
+    for (int gi = 0; gi < b->n_groups; ++gi)
+        for (int l = 0; l < CG; ++l) {
+            const int c = gi * CG + l;
+            float* dst = pt.data() + (size_t)gi * P * CG + l;
+            if (c < n_candidates) {
+                for (size_t p = 0; p < P; ++p) dst[p * CG] = params_host[(size_t)c * P + p];
+            } else {
+                dst[(size_t)b->lay.sqrt_eps * CG] = 1.f;   // padding lanes: zero network, finite charges
+            }
+        }
+    if (cudaMalloc((void**)&b->d_pt, sizeof(float) * pt.size()) != cudaSuccess ||
+        cudaMemcpy(b->d_pt, pt.data(), sizeof(float) * pt.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_work, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_status, sizeof(unsigned int)) != cudaSuccess) {
+        qnep_batch_destroy(b);
+        return QNEP_ERR_CUDA;
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        b->num_sms = sms;
+    *out = b;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_set_capacity(qnep_batch* b, int cap_list, int cap_angular) {
+    if (!b || cap_list < 0 || cap_angular < 0) return QNEP_ERR_ARG;
+    b->cap_l_user = cap_list;
+    b->cap_a_user = cap_angular;
+    b->have_desc = false;   // rebuilt (and lists re-sized) by the next call
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_capacity(const qnep_batch* b, int* cap_list, int* cap_angular) {
+    if (!b || !cap_list || !cap_angular) return QNEP_ERR_ARG;
+    *cap_list = b->cap_l;
+    *cap_angular = b->cap_a;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order) {
+    if (!b || (warps != 4 && warps != 8) ||
+        (order != QNEP_BATCH_ORDER_LARGEST_FIRST && order != QNEP_BATCH_ORDER_STRUCTURE))
+        return QNEP_ERR_ARG;
+    b->warps = warps;
+    b->order_policy = order;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order) {
+    if (!b || !warps || !order) return QNEP_ERR_ARG;
+    *warps = b->warps;
+    *order = b->order_policy;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                               const int* types, const double* boxes, void* stream, double* energy, float* forces,
+                               float* charges) {
+    if (!b) return QNEP_ERR_ARG;
+    if (n_struct < 1 || !atom_offsets || !boxes || !energy) return failb(b, QNEP_ERR_ARG, "bad batch arguments");
+    if (atom_offsets[0] != 0) return failb(b, QNEP_ERR_ARG, "atom_offsets[0] must be 0");
+    if (atom_offsets[n_struct] > 0 && (!positions || !types))
+        return failb(b, QNEP_ERR_ARG, "positions and types are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!same_desc(b, n_struct, atom_offsets, boxes)) {
+        qnep_status s = describe(b, n_struct, atom_offsets, boxes, st);
+        if (s != QNEP_OK) {
+            b->have_desc = false;
+            return s;
+        }
+    }
+    // blocks per SM of this shape (cached: no CUDA calls beyond launches once the batch is known,
+    // so the call can be captured in a graph)
+    const auto key = std::make_pair(b->warps, b->nph_max);
+    auto hit = b->per_sm_cache.find(key);
+    if (hit == b->per_sm_cache.end())
+        hit = b->per_sm_cache.emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max)).first;
+    const int per_sm = hit->second;
+    if (per_sm <= 0) return failb(b, QNEP_ERR_UNSUPPORTED, "item kernel does not fit on an SM");
+    const int slots = per_sm * b->num_sms;
+    qnep_status s = ensure_scratch(b, slots, st);
+    if (s != QNEP_OK) return s;
+    CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
+    CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
+    launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
+                      b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
+                      b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->d_status, st);
+    BatchArgs a{};
+    a.spos4 = b->spos4;
+    a.sidx = b->sidx;
+    a.order = b->order;
+    a.spec_off = b->spec_off;
+    a.nbr_list = b->nbr_list;
+    a.cnt_list = b->cnt_list;
+    a.nbr_ang = b->nbr_ang;
+    a.cnt_ang = b->cnt_ang;
+    a.cap_l = b->cap_l;
+    a.cap_a = b->cap_a;
+    a.phase = b->phase;
+    a.nph_stride = b->nph_max;
+    a.st = b->d_st;
+    a.kt = b->d_kt;
+    a.chunk = b->d_chunk;
+    a.kvec = b->d_kvec;
+    a.pt = b->d_pt;
+    a.lay = b->lay;
+    a.n_cand = b->n_cand;
+    a.items = b->order_policy == QNEP_BATCH_ORDER_STRUCTURE ? b->d_items_nat : b->d_items_lpt;
+    a.n_items = b->n_items;
+    a.work = b->d_work;
+    a.sc = b->sc;
+    a.mode = b->es.mode;
+    a.alpha = (float)b->es.alpha;
+    a.q_total = (float)b->es.q_total;
+    a.energy = energy;
+    a.forces = forces;
+    a.charges = charges;
+    a.n_struct = n_struct;
+    a.n_total = b->n_total;
+    a.status = b->d_status;
+    launch_batch_items(a, b->warps, b->nph_max, std::min(slots, std::max(b->n_items, 1)), st);
+    CKB(cudaGetLastError());
+    b->last_stream = st;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_sync_status(qnep_batch* b) {
+    if (!b) return QNEP_ERR_ARG;
+    CKB(cudaStreamSynchronize(b->last_stream));
+    unsigned int h = 0;
+    CKB(cudaMemcpy(&h, b->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    if (h & 4u) return failb(b, QNEP_ERR_ARG, "a species index is outside [0, n_species)");
+    if (h & 1u) return failb(b, QNEP_ERR_NBR_OVERFLOW, "neighbour list capacity exceeded");
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                                const int* types, const double* boxes, void* stream, double* energy, float* forces,
+                                float* charges, int reps, double* best_ms) {
+    if (!b || reps < 1) return QNEP_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    CKB(cudaEventCreate(&e0));
+    CKB(cudaEventCreate(&e1));
+    const int shapes[2] = {8, 4};
+    const int orders[2] = {QNEP_BATCH_ORDER_LARGEST_FIRST, QNEP_BATCH_ORDER_STRUCTURE};
+    double best = 1e300;
+    int bw = b->warps, bo = b->order_policy;
+    qnep_status result = QNEP_OK;
+    for (int w : shapes) {
+        for (int o : orders) {
+            b->warps = w;
+            b->order_policy = o;
+            qnep_status s = qnep_batch_compute(b, n_struct, atom_offsets, positions, types, boxes, stream, energy,
+                                               forces, charges);
+            if (s == QNEP_OK) s = qnep_batch_sync_status(b);
+            if (s != QNEP_OK) {
+                if (s == QNEP_ERR_UNSUPPORTED) continue;   // this block shape does not fit
+                result = s;
+                break;
+            }
+            std::vector<float> t(reps);
+            for (int r = 0; r < reps && s == QNEP_OK; ++r) {
+                cudaEventRecord(e0, st);
+                s = qnep_batch_compute(b, n_struct, atom_offsets, positions, types, boxes, stream, energy, forces,
+                                       charges);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t[r], e0, e1);
+            }
+            if (s != QNEP_OK) {
+                result = s;
+                break;
+            }
+            std::sort(t.begin(), t.end());
+            const double med = t[reps / 2];
+            if (med < best) {
+                best = med;
+                bw = w;
+                bo = o;
+            }
+        }
+        if (result != QNEP_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->warps = bw;
+    b->order_policy = bo;
+    if (best_ms) *best_ms = best < 1e299 ? best : -1.0;
+    return result;
+}
+
+const char* qnep_batch_last_error(const qnep_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void qnep_batch_destroy(qnep_batch* b) {
+    if (!b) return;
+    if (b->last_stream) cudaStreamSynchronize(b->last_stream);
+    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,     b->d_items_lpt,
+                    b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
+                    b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
+                    b->d_work,    b->d_status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+}  // extern "C"

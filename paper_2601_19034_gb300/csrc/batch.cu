@@ -1,0 +1,1051 @@
+// Batched force call: structures of uneven size under groups of 32 candidate
+// parameter vectors (one candidate per lane), one item per thread block.
+//
+// Pre-pass (candidate independent, one block per structure):
+//   k_batch_sort   wrap, bin into cells, stable cell order, species order
+//   k_batch_lists  neighbour lists (grouped by neighbour species) and the Ewald
+//                  phase-factor rows of every atom
+// Item kernel (persistent, items taken largest first), per (structure, group):
+//   1 forward    per species block: candidate-independent basis sums per atom
+//                  B^R[t_j][k] = sum_j f_k(r_ij),  B^A[t_j][k][lm] = sum_j f_k(r_ij) Y_lm(u_ij)
+//                then per lane: D^R_n = sum c^R[t_i][t_j][n][k] B^R,
+//                A_{n,lm} = sum c^A[t_i][t_j][n][k] B^A (Sec. II.A), descriptor,
+//                network U_i, q_i and dU/dD, dq/dD (Eq. U_i, Sec. II.B)
+//   2 charges    total-charge correction (block sum, FP64)
+//   3 S(k)       lanes over 32 wave vectors, FP32 terms over 64-atom tiles flushed
+//                to FP64 every 512 atoms; U^k per candidate (FP64)
+//   4 fields     lanes over atoms: phi^k_i and the k-space field (Sec. II.C);
+//                lanes over candidates: real-space phi^r_i and F^r_i
+//   5 backward   per species block: lambda = dU/dD + (phi_i - mean phi) dq/dD; radial
+//                and angular partial forces per pair (Sec. II.C), float4 atomics
+//   6 outputs    forces, corrected charges (input order), energy per candidate
+#include <algorithm>
+#include <cstdint>
+
+#include "batch_internal.cuh"
+#include "desc_math.cuh"
+#include "nbr_common.cuh"
+
+namespace qnep {
+
+namespace {
+
+constexpr int PREP_THREADS = 256;
+
+// shared-memory rows staged by the lanes of a warp (odd strides: conflict-free row writes)
+constexpr int TAB_R1 = KR;                     // forward radial: f_k
+constexpr int TAB_A1 = KA + NLM;               // forward angular: f_k, Y_lm
+constexpr int TAB_R4 = KR + 4;                 // backward radial: f'_k, u, j
+constexpr int TAB_A4 = 2 * KA + NLM + 5;       // backward angular: f_k, f'_k, Y_lm, u, 1/r, j
+constexpr int TAB_RS = 5;                      // real space: B, B' u, j
+constexpr int WT_FLOATS = 32 * TAB_A4;         // 1504
+constexpr int WBR = WT_FLOATS;                 // B^R [S][KR]
+constexpr int WBA = WBR + MAX_SPECIES * KR;    // B^A [S][KA][NLM] (16-byte aligned)
+constexpr int WCUM = WBA + MAX_SPECIES * KA * NLM;   // cumulative species counts (ints)
+constexpr int WARP_FLOATS = WCUM + 16;
+constexpr int PR_R = 0;                                  // c^R[t_i] staged [S][NR][KR][CG]
+constexpr int PR_A = MAX_SPECIES * NR * KR * CG;         // c^A[t_i] staged [S][NA][KA][CG]
+constexpr int PR_S = PR_A + MAX_SPECIES * NA * KA * CG;  // descriptor scaler [NDES][CG]
+constexpr int PARAM_FLOATS = PR_S + NDES * CG;
+constexpr int QT = 64;                         // atoms per charge tile of the S(k) phase
+constexpr int FLUSH_TILES = 8;                 // FP32 partial sums cover 512 atoms
+constexpr int ACCD = CG * 33 * 2;              // FP64 S(k) accumulators per warp [CG][33][2]
+constexpr int NSUMS = 6;                       // per-candidate FP64 sums
+
+static_assert(WBA % 4 == 0 && WARP_FLOATS % 4 == 0 && PARAM_FLOATS % 4 == 0, "float4 alignment");
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 batch_phase(const float4& p, int e, const BatchKTab& kt) {
+    if (e < kt.yoff) return phase_factor(p.x, e, kt.invl_hi[0], kt.invl_lo[0]);
+    if (e < kt.zoff) return phase_factor(p.y, e - kt.yoff - kt.n2max, kt.invl_hi[1], kt.invl_lo[1]);
+    return phase_factor(p.z, e - kt.zoff - kt.n3max, kt.invl_hi[2], kt.invl_lo[2]);
+}
+
+// Species of input atom i; an out-of-range type sets status bit 2 and counts as species 0.
+__device__ __forceinline__ int species_of(const int* __restrict__ types, int i, int n_species,
+                                         unsigned int* status) {
+    const int t = types[i];
+    if (t >= 0 && t < n_species) return t;
+    if (status) atomicOr(status, 4u);
+    return 0;
+}
+
+__device__ __forceinline__ float wrap_coord(float x, float L, float invL) {
+    float f = floorf(x * invL);
+    float y = fmaf(-f, L, x);
+    if (y >= L) y -= L;
+    if (y < 0.f) y += L;
+    if (y >= L) y = 0.f;
+    return y;
+}
+
+// ---------------------------------------------------------------------------------
+// pre-pass 1: cells, stable cell order, species order
+__global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __restrict__ pos,
+                                                             const int* __restrict__ types, int nmax, int n_species,
+                                                             const BatchStruct* __restrict__ sts,
+                                                             int* __restrict__ cell_start_all,
+                                                             float4* __restrict__ spos4, int* __restrict__ sidx,
+                                                             int* __restrict__ order, int* __restrict__ spec_off,
+                                                             unsigned int* __restrict__ status) {
+    extern __shared__ int psm[];
+    const BatchStruct bs = sts[blockIdx.x];
+    const int n = bs.n, off = bs.atom_off;
+    const Geom g = bs.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    int* cell_of = psm;                          // [nmax]
+    int* ccnt = cell_of + nmax;                  // [BATCH_MAX_CELLS + 1]
+    int* scnt = ccnt + BATCH_MAX_CELLS + 1;      // [MAX_SPECIES + 1]
+    for (int i = threadIdx.x; i <= g.ncells; i += blockDim.x) ccnt[i] = 0;
+    if (threadIdx.x <= MAX_SPECIES) scnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int cc[3];
+        for (int d = 0; d < 3; ++d) {
+            float y = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
+            int c = (int)(y * g.invL[d] * (float)g.nc[d]);
+            cc[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+        }
+        const int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+        cell_of[i] = c;
+        atomicAdd(&ccnt[c], 1);
+        atomicAdd(&scnt[species_of(types, off + i, n_species, status)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < g.ncells; ++c) {
+            int v = ccnt[c];
+            ccnt[c] = acc;
+            acc += v;
+        }
+        ccnt[g.ncells] = acc;
+        acc = 0;
+        for (int t = 0; t < n_species; ++t) {
+            int v = scnt[t];
+            scnt[t] = acc;
+            acc += v;
+        }
+        scnt[n_species] = acc;
+    }
+    __syncthreads();
+    int* cs = cell_start_all + bs.cell_off;
+    for (int i = threadIdx.x; i <= g.ncells; i += blockDim.x) cs[i] = ccnt[i];
+    if (threadIdx.x <= n_species) spec_off[blockIdx.x * (MAX_SPECIES + 1) + threadIdx.x] = scnt[threadIdx.x];
+    // stable placement by cell (ascending input index inside a cell), one warp per cell
+    for (int c = warp; c < g.ncells; c += nw) {
+        int base = ccnt[c];
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool in = i < n && cell_of[i] == c;
+            const unsigned mk = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int slot = base + __popc(mk & below);
+                float w[3];
+                for (int d = 0; d < 3; ++d) w[d] = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
+                spos4[off + slot] = make_float4(w[0], w[1], w[2],
+                                                __int_as_float(species_of(types, off + i, n_species, nullptr)));
+                sidx[off + slot] = i;
+            }
+            base += __popc(mk);
+        }
+    }
+    __syncthreads();
+    // species order over the sorted atoms (stable), one warp per species
+    for (int t = warp; t < n_species; t += nw) {
+        int base = scnt[t];
+        for (int m0 = 0; m0 < n; m0 += 32) {
+            const int m = m0 + lane;
+            const bool in = m < n && species_of(types, off + sidx[off + m], n_species, nullptr) == t;
+            const unsigned mk = __ballot_sync(0xffffffffu, in);
+            if (in) order[off + base + __popc(mk & below)] = m;
+            base += __popc(mk);
+        }
+    }
+}
+
+// pre-pass 2: neighbour lists and phase rows
+__global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
+    int n_species, const BatchStruct* __restrict__ sts, const BatchKTab* __restrict__ kts,
+    const int* __restrict__ cell_start_all, const float4* __restrict__ spos4, int cap_l, int cap_a,
+    int* __restrict__ nbr_list, int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang,
+    float2* __restrict__ phase, int nph_stride, unsigned int* __restrict__ status) {
+    extern __shared__ int psm[];
+    const BatchStruct bs = sts[blockIdx.x];
+    const int n = bs.n, off = bs.atom_off;
+    const Geom g = bs.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int* sl = psm + warp * (2 * cap_l + 2 * cap_a);
+    int* slt = sl + cap_l;
+    int* sa = slt + cap_l;
+    int* sat = sa + cap_a;
+    const float4* sp = spos4 + off;
+    const int* cs = cell_start_all + bs.cell_off;
+    for (int m = warp; m < n; m += nw) {
+        const float4 pk = sp[m];
+        int nl = 0, na = 0;
+        bool ovf = warp_build_lists(sp, cs, m, pk, g, cap_l, cap_a, sl, slt, sa, sat, nl, na);
+        warp_write_grouped(sl, slt, nl, n_species, n, m, nbr_list + (size_t)off * cap_l, (size_t)cap_l, 1,
+                           cnt_list + (size_t)off * n_species);
+        warp_write_grouped(sa, sat, na, n_species, n, m, nbr_ang + (size_t)off * cap_a, (size_t)cap_a, 1,
+                           cnt_ang + (size_t)off * n_species);
+        if (ovf && lane == 0) atomicOr(status, 1u);
+        __syncwarp();
+    }
+    const BatchKTab kt = kts[bs.ktab];
+    for (int idx = threadIdx.x; idx < n * kt.nph; idx += blockDim.x) {
+        const int m = idx / kt.nph, e = idx - m * kt.nph;
+        phase[(size_t)(off + m) * nph_stride + e] = batch_phase(sp[m], e, kt);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// item kernel
+
+// Stage c^R[t_i], c^A[t_i] (all neighbour species) and the scaler of the block's group.
+__device__ __forceinline__ void stage_params(const float* __restrict__ pg, const ParamLayout& lay, int ti,
+                                             float* __restrict__ prm) {
+    const int S = lay.n_species;
+    const int nr = S * NR * KR, na = S * NA * KA;
+    const int tot = (nr + na + NDES) * CG;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int p = idx >> 5, c = idx & 31;
+        int src, dst;
+        if (p < nr) {
+            src = lay.c_radial + ti * nr + p;
+            dst = PR_R + p * CG;
+        } else if (p < nr + na) {
+            src = lay.c_angular + ti * na + (p - nr);
+            dst = PR_A + (p - nr) * CG;
+        } else {
+            src = lay.scaler + (p - nr - na);
+            dst = PR_S + (p - nr - na) * CG;
+        }
+        prm[dst + c] = __ldg(&pg[(size_t)src * CG + c]);
+    }
+}
+
+// Cumulative neighbour counts of sorted atom m by species (lane 0 writes, warp reads).
+__device__ __forceinline__ void species_cum(const BatchArgs& a, int off, int n, int m, int S, int* cum) {
+    if ((threadIdx.x & 31) == 0) {
+        int tl = 0, ta = 0;
+        const int* cl = a.cnt_list + (size_t)off * S;
+        const int* ca = a.cnt_ang + (size_t)off * S;
+        for (int s = 0; s < S; ++s) {
+            cum[s] = tl;
+            cum[8 + s] = ta;
+            tl += cl[(size_t)s * n + m];
+            ta += ca[(size_t)s * n + m];
+        }
+        cum[S] = tl;
+        cum[8 + S] = ta;
+    }
+    __syncwarp();
+}
+
+template <int NW>
+__device__ __forceinline__ void block_sum(double v, double* red, double* dst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    red[warp * CG + lane] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += red[w * CG + lane];
+        dst[lane] = t;
+    }
+    __syncthreads();
+}
+
+// Forward of sorted atom m (species ti) for the 32 candidates of the group.
+__device__ __forceinline__ void forward_atom(const BatchArgs& a, const BatchStruct& bs, int m, int ti,
+                                             const float* __restrict__ prm, const float* __restrict__ pg,
+                                             float* __restrict__ wb, float* __restrict__ A,
+                                             float* __restrict__ duq, float2* __restrict__ uq, double& su,
+                                             double& sq) {
+    const int lane = threadIdx.x & 31;
+    const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
+    const Geom& g = bs.g;
+    const float4* sp = a.spos4 + off;
+    const float4 pk = sp[m];
+    float* tab = wb;
+    float* br = wb + WBR;
+    float* ba = wb + WBA;
+    int* cum = reinterpret_cast<int*>(wb + WCUM);
+    species_cum(a, off, n, m, S, cum);
+    for (int t = lane; t < S * KR; t += 32) br[t] = 0.f;
+    for (int t = lane; t < S * KA * NLM; t += 32) ba[t] = 0.f;
+    const int tot_l = cum[S], tot_a = cum[8 + S];
+    __syncwarp();
+
+    // candidate-independent radial basis sums: lanes over entries, then over (t_j, k)
+    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
+    const float rcr2 = g.rc_radial * g.rc_radial;
+    for (int base = 0; base < tot_l; base += 32) {
+        const int e = base + lane;
+        float f[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) f[k] = 0.f;
+        if (e < tot_l) {
+            float vx, vy, vz;
+            entry_vector(sp, __ldg(&lst[e]), pk, g, vx, vy, vz);
+            const float r2 = vx * vx + vy * vy + vz * vz;
+            if (r2 < rcr2) basis<KR>(sqrtf(r2), g.rc_radial, f);
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k) tab[lane * TAB_R1 + k] = f[k];
+        __syncwarp();
+        const int cntc = min(32, tot_l - base);
+        for (int idx = lane; idx < S * KR; idx += 32) {
+            const int tj = idx / KR, k = idx - tj * KR;
+            const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
+            float s = 0.f;
+            for (int r = lo; r < hi; ++r) s += tab[r * TAB_R1 + k];
+            br[idx] += s;
+        }
+        __syncwarp();
+    }
+    // candidate-independent angular basis sums B^A[t_j][k][lm]: lanes over entries
+    // (f_k, Y_lm to shared), then lane lm accumulates over the entries of each species
+    const int* lsa = a.nbr_ang + (size_t)(off + m) * a.cap_a;
+    for (int base = 0; base < tot_a; base += 32) {
+        const int e = base + lane;
+        if (e < tot_a) {
+            float vx, vy, vz;
+            entry_vector(sp, __ldg(&lsa[e]), pk, g, vx, vy, vz);
+            const float r = sqrtf(vx * vx + vy * vy + vz * vz);
+            float f[KA], Y[NLM];
+            basis<KA>(r, g.rc_angular, f);
+            const float ir = 1.f / r;
+            harmonics(vx * ir, vy * ir, vz * ir, Y);
+            float* row = tab + lane * TAB_A1;
+#pragma unroll
+            for (int k = 0; k < KA; ++k) row[k] = f[k];
+#pragma unroll
+            for (int q = 0; q < NLM; ++q) row[KA + q] = Y[q];
+        }
+        __syncwarp();
+        const int cntc = min(32, tot_a - base);
+        if (lane < NLM) {
+            for (int tj = 0; tj < S; ++tj) {
+                const int lo = max(cum[8 + tj] - base, 0), hi = min(cum[8 + tj + 1] - base, cntc);
+                if (lo >= hi) continue;
+                float b[KA];
+#pragma unroll
+                for (int k = 0; k < KA; ++k) b[k] = 0.f;
+                for (int r = lo; r < hi; ++r) {
+                    const float* row = tab + r * TAB_A1;
+                    const float y = row[KA + lane];
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) b[k] = fmaf(row[k], y, b[k]);
+                }
+                float* dst = ba + tj * KA * NLM + lane;
+#pragma unroll
+                for (int k = 0; k < KA; ++k) dst[k * NLM] += b[k];
+            }
+        }
+        __syncwarp();
+    }
+
+    // lane = candidate: contractions with this candidate's c^R, c^A
+    float d[NDES];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) d[q] = 0.f;
+    for (int tj = 0; tj < S; ++tj) {
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const float b = br[tj * KR + k];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) d[q] = fmaf(prm[PR_R + ((tj * NR + q) * KR + k) * CG + lane], b, d[q]);
+        }
+    }
+    float dA[NA][LMAX];
+#pragma unroll
+    for (int q = 0; q < NA; ++q)
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l) dA[q][l] = 0.f;
+    float d4[NA];
+    float* Ao = A + (size_t)m * NANG * CG + lane;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float acc[NA][12];
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+#pragma unroll
+            for (int mm = 0; mm < 12; ++mm) acc[q][mm] = 0.f;
+        for (int tj = 0; tj < S; ++tj) {
+#pragma unroll 3
+            for (int k = 0; k < KA; ++k) {
+                float cv[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) cv[q] = prm[PR_A + ((tj * NA + q) * KA + k) * CG + lane];
+                const float4* bp = reinterpret_cast<const float4*>(ba + (tj * KA + k) * NLM + 12 * h);
+                const float4 b0 = bp[0], b1 = bp[1], b2 = bp[2];
+                const float bv[12] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+#pragma unroll
+                for (int q = 0; q < NA; ++q)
+#pragma unroll
+                    for (int mm = 0; mm < 12; ++mm) acc[q][mm] = fmaf(cv[q], bv[mm], acc[q][mm]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+#pragma unroll
+            for (int mm = 0; mm < 12; ++mm) {
+                const int M = 12 * h + mm;
+                const int l = M < 3 ? 0 : (M < 8 ? 1 : (M < 15 ? 2 : 3));
+                Ao[(q * NLM + M) * CG] = acc[q][mm];
+                dA[q][l] = fmaf(c_wlm[M], acc[q][mm] * acc[q][mm], dA[q][l]);
+            }
+        }
+        if (h == 0) {
+#pragma unroll
+            for (int q = 0; q < NA; ++q) {
+                float a2[5], t[6], t2[6];
+#pragma unroll
+                for (int kk = 0; kk < 5; ++kk) a2[kk] = acc[q][3 + kk];
+                tensor_from_a(a2, t);
+                tensor_square(t, t2);
+                d4[q] = t2[0] * t[0] + t2[1] * t[1] + t2[2] * t[2] + 2.f * (t2[3] * t[3] + t2[4] * t[4] + t2[5] * t[5]);
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) d[NR + l * NA + q] = dA[q][l];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) d[NR + 4 * NA + q] = d4[q];
+#pragma unroll
+    for (int v = 0; v < NDES; ++v) d[v] *= prm[PR_S + v * CG + lane];
+
+    // network of species ti: h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q
+    const float* W = pg + (size_t)(a.lay.mlp + ti * a.lay.mlp_stride) * CG + lane;
+    float ge[NNEU], gq[NNEU];
+    float ue = 0.f, uqv = 0.f;
+#pragma unroll
+    for (int mu = 0; mu < NNEU; ++mu) {
+        float pre = -__ldg(&W[(ParamLayout::B0 + mu) * CG]);
+#pragma unroll
+        for (int v = 0; v < NDES; ++v) pre = fmaf(__ldg(&W[(ParamLayout::W0 + mu * NDES + v) * CG]), d[v], pre);
+        const float hh = tanhf(pre);
+        const float we = __ldg(&W[(ParamLayout::W1E + mu) * CG]), wq = __ldg(&W[(ParamLayout::W1Q + mu) * CG]);
+        ue = fmaf(we, hh, ue);
+        uqv = fmaf(wq, hh, uqv);
+        const float dh = 1.f - hh * hh;
+        ge[mu] = we * dh;
+        gq[mu] = wq * dh;
+    }
+    const float U = ue - __ldg(&W[ParamLayout::B1E * CG]);
+    const float Q = uqv - __ldg(&W[ParamLayout::B1Q * CG]);
+    // dU/dD_v = scaler_v sum_mu ge_mu W0[mu][v] (and dq/dD), one output pair at a time
+    float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+#pragma unroll 2
+    for (int v = 0; v < NDES; ++v) {
+        float du = 0.f, dq = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < NNEU; ++mu) {
+            const float w = __ldg(&W[(ParamLayout::W0 + mu * NDES + v) * CG]);
+            du = fmaf(ge[mu], w, du);
+            dq = fmaf(gq[mu], w, dq);
+        }
+        const float sv = prm[PR_S + v * CG + lane];
+        dd[v * CG] = du * sv;
+        dd[(NDES + v) * CG] = dq * sv;
+    }
+    uq[(size_t)m * CG + lane] = make_float2(U, Q);
+    su += (double)U;
+    sq += (double)Q;
+    __syncwarp();   // shared rows are reused by the warp's next atom
+}
+
+// Backward of sorted atom m (species ti): partial forces of every list entry.
+__device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStruct& bs, int m,
+                                              const float* __restrict__ prm, float* __restrict__ wb,
+                                              const float* __restrict__ A, const float* __restrict__ duq,
+                                              const float* __restrict__ qcs, const float4* __restrict__ fk,
+                                              const float4* __restrict__ fr, float4* __restrict__ fsum, int nmax,
+                                              float selfc, float phibar) {
+    const int lane = threadIdx.x & 31;
+    const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
+    const Geom& g = bs.g;
+    const float4* sp = a.spos4 + off;
+    const float4 pk = sp[m];
+    float* tab = wb;
+    int* cum = reinterpret_cast<int*>(wb + WCUM);
+    species_cum(a, off, n, m, S, cum);
+    const int tot_l = cum[S], tot_a = cum[8 + S];
+    const float qc = qcs[(size_t)m * CG + lane];
+    const float4 kf = fk[(size_t)lane * nmax + m];
+    const float4 rf = fr[(size_t)m * CG + lane];
+    const float wq = (kf.x + rf.x + selfc * qc) - phibar;
+    float lam[NDES];
+    const float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+#pragma unroll
+    for (int v = 0; v < NDES; ++v) lam[v] = fmaf(wq, dd[(NDES + v) * CG], dd[v * CG]);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+
+    // radial: F_ij = (sum_k mu_k f'_k(r)) u with mu_k = sum_n lambda_n c^R[t_i][t_j][n][k]
+    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
+    const float rcr2 = g.rc_radial * g.rc_radial;
+    for (int base = 0; base < tot_l; base += 32) {
+        const int e = base + lane;
+        float* row = tab + lane * TAB_R4;
+        float df[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) df[k] = 0.f;
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        int jj = -1;
+        if (e < tot_l) {
+            const int ent = __ldg(&lst[e]);
+            float vx, vy, vz;
+            entry_vector(sp, ent, pk, g, vx, vy, vz);
+            const float r2 = vx * vx + vy * vy + vz * vz;
+            if (r2 < rcr2) {
+                const float r = sqrtf(r2), ir = 1.f / r;
+                float f[KR];
+                basis_d<KR>(r, g.rc_radial, f, df);
+                ux = vx * ir;
+                uy = vy * ir;
+                uz = vz * ir;
+                jj = entry_index(ent);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k) row[k] = df[k];
+        row[KR] = ux;
+        row[KR + 1] = uy;
+        row[KR + 2] = uz;
+        row[KR + 3] = __int_as_float(jj);
+        __syncwarp();
+        const int cntc = min(32, tot_l - base);
+        for (int tj = 0; tj < S; ++tj) {
+            const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
+            if (lo >= hi) continue;
+            float mu[KR];
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                float x = 0.f;
+#pragma unroll
+                for (int q = 0; q < NR; ++q) x = fmaf(lam[q], prm[PR_R + ((tj * NR + q) * KR + k) * CG + lane], x);
+                mu[k] = x;
+            }
+            for (int r = lo; r < hi; ++r) {
+                const float* rw = tab + r * TAB_R4;
+                const int j = __float_as_int(rw[KR + 3]);
+                if (j < 0) continue;
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < KR; ++k) s = fmaf(mu[k], rw[k], s);
+                const float Fx = s * rw[KR], Fy = s * rw[KR + 1], Fz = s * rw[KR + 2];
+                fx += Fx;
+                fy += Fy;
+                fz += Fz;
+                atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
+            }
+        }
+        __syncwarp();
+    }
+
+    // angular: Phi_{n,lm} = d(lambda . D)/dA_{n,lm}
+    float Phi[NA][NLM];
+    const float* Ai = A + (size_t)m * NANG * CG + lane;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+#pragma unroll
+        for (int M = 0; M < NLM; ++M) {
+            const int l = M < 3 ? 0 : (M < 8 ? 1 : (M < 15 ? 2 : 3));
+            Phi[q][M] = 2.f * c_wlm[M] * Ai[(q * NLM + M) * CG] * lam[NR + l * NA + q];
+        }
+        float a2[5], t[6], t2[6];
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk) a2[kk] = Ai[(q * NLM + 3 + kk) * CG];
+        tensor_from_a(a2, t);
+        tensor_square(t, t2);
+        const float l4 = lam[NR + 4 * NA + q];
+        Phi[q][3] = fmaf(l4, 3.f * (t2[2] * (1.f / 3.f) - (t2[0] + t2[1]) * (1.f / 6.f)), Phi[q][3]);
+        Phi[q][4] = fmaf(l4, 6.f * t2[4], Phi[q][4]);
+        Phi[q][5] = fmaf(l4, 6.f * t2[5], Phi[q][5]);
+        Phi[q][6] = fmaf(l4, 1.5f * (t2[0] - t2[1]), Phi[q][6]);
+        Phi[q][7] = fmaf(l4, 6.f * t2[3], Phi[q][7]);
+    }
+    const int* lsa = a.nbr_ang + (size_t)(off + m) * a.cap_a;
+    for (int base = 0; base < tot_a; base += 32) {
+        const int e = base + lane;
+        if (e < tot_a) {
+            const int ent = __ldg(&lsa[e]);
+            float vx, vy, vz;
+            entry_vector(sp, ent, pk, g, vx, vy, vz);
+            const float r = sqrtf(vx * vx + vy * vy + vz * vz), ir = 1.f / r;
+            float f[KA], df[KA], Y[NLM];
+            basis_d<KA>(r, g.rc_angular, f, df);
+            const float ux = vx * ir, uy = vy * ir, uz = vz * ir;
+            harmonics(ux, uy, uz, Y);
+            float* row = tab + lane * TAB_A4;
+#pragma unroll
+            for (int k = 0; k < KA; ++k) {
+                row[k] = f[k];
+                row[KA + k] = df[k];
+            }
+#pragma unroll
+            for (int q = 0; q < NLM; ++q) row[2 * KA + q] = Y[q];
+            row[2 * KA + NLM] = ux;
+            row[2 * KA + NLM + 1] = uy;
+            row[2 * KA + NLM + 2] = uz;
+            row[2 * KA + NLM + 3] = ir;
+            row[2 * KA + NLM + 4] = __int_as_float(entry_index(ent));
+        }
+        __syncwarp();
+        const int cntc = min(32, tot_a - base);
+        for (int tj = 0; tj < S; ++tj) {
+            const int lo = max(cum[8 + tj] - base, 0), hi = min(cum[8 + tj + 1] - base, cntc);
+            const float* cA = prm + PR_A + tj * NA * KA * CG + lane;
+            for (int r = lo; r < hi; ++r) {
+                const float* rw = tab + r * TAB_A4;
+                float gn[NA], dgn[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) {
+                    float x = 0.f, y = 0.f;
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) {
+                        const float c = cA[(q * KA + k) * CG];
+                        x = fmaf(c, rw[k], x);
+                        y = fmaf(c, rw[KA + k], y);
+                    }
+                    gn[q] = x;
+                    dgn[q] = y;
+                }
+                float psi[NLM];
+#pragma unroll
+                for (int M = 0; M < NLM; ++M) psi[M] = 0.f;
+                float rho = 0.f;
+#pragma unroll
+                for (int q = 0; q < NA; ++q) {
+                    float pq = 0.f;
+#pragma unroll
+                    for (int M = 0; M < NLM; ++M) {
+                        pq = fmaf(Phi[q][M], rw[2 * KA + M], pq);
+                        psi[M] = fmaf(gn[q], Phi[q][M], psi[M]);
+                    }
+                    rho = fmaf(dgn[q], pq, rho);
+                }
+                const float ux = rw[2 * KA + NLM], uy = rw[2 * KA + NLM + 1], uz = rw[2 * KA + NLM + 2];
+                const float ir = rw[2 * KA + NLM + 3];
+                float gx, gy, gz;
+                harmonics_grad(ux, uy, uz, psi, gx, gy, gz);
+                const float gu = gx * ux + gy * uy + gz * uz;
+                const float Fx = rho * ux + (gx - gu * ux) * ir;
+                const float Fy = rho * uy + (gy - gu * uy) * ir;
+                const float Fz = rho * uz + (gz - gu * uz) * ir;
+                fx += Fx;
+                fy += Fy;
+                fz += Fz;
+                const int j = __float_as_int(rw[2 * KA + NLM + 4]);
+                atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
+            }
+        }
+        __syncwarp();
+    }
+    // own force: network part plus the static electrostatic forces q F^k/q + F^r
+    atomicAdd(&fsum[(size_t)m * CG + lane],
+              make_float4(fx + fmaf(qc, kf.y, rf.y), fy + fmaf(qc, kf.z, rf.z), fz + fmaf(qc, kf.w, rf.w), 0.f));
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* red = reinterpret_cast<double*>(bsm);     // [NW][CG]
+    double* sums = red + NW * CG;                      // [NSUMS][CG]
+    float* cst = reinterpret_cast<float*>(sums + NSUMS * CG);   // delta, phibar, q_target, pad [4][CG]
+    float* un = cst + 4 * CG;                          // union of the phases' working sets
+    const int S = a.lay.n_species;
+    const size_t slot = blockIdx.x;
+    float* A = a.sc.A + slot * a.sc.stride_A;
+    float* duq = a.sc.duq + slot * a.sc.stride_duq;
+    float2* uq = a.sc.uq + slot * a.sc.stride_n;
+    float* qcs = a.sc.qc + slot * a.sc.stride_n;
+    float4* fk = a.sc.fk + slot * a.sc.stride_n;
+    float4* fr = a.sc.fr + slot * a.sc.stride_n;
+    float4* fsum = a.sc.fsum + slot * a.sc.stride_n;
+    float2* sk = a.sc.sk + slot * a.sc.stride_k;
+    const int nmax = (int)(a.sc.stride_n / CG);
+    const float selfc = a.mode == 1 ? -2.f * KE * a.alpha * 0.564189583547756287f : 0.f;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= a.n_items) break;
+        const int2 item = a.items[it];
+        const BatchStruct bs = a.st[item.x];
+        const int grp = item.y, n = bs.n, off = bs.atom_off;
+        const int cand = grp * CG + lane;
+        const float* pg = a.pt + (size_t)grp * a.lay.total * CG;
+        const int* so = a.spec_off + item.x * (MAX_SPECIES + 1);
+        for (int i = threadIdx.x; i < n * CG; i += NW * 32) fsum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        // 1 forward, one species block at a time (its parameters staged in shared memory)
+        double su = 0.0, sq = 0.0;
+        for (int ti = 0; ti < S; ++ti) {
+            const int p0 = so[ti], p1 = so[ti + 1];
+            if (p1 == p0) continue;
+            __syncthreads();
+            stage_params(pg, a.lay, ti, un);
+            __syncthreads();
+            float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
+            for (int p = p0 + warp; p < p1; p += NW)
+                forward_atom(a, bs, a.order[off + p], ti, un, pg, wb, A, duq, uq, su, sq);
+        }
+        block_sum<NW>(su, red, sums + 0 * CG);
+        block_sum<NW>(sq, red, sums + 4 * CG);
+        if (warp == 0) {
+            const float seps = __ldg(&pg[(size_t)a.lay.sqrt_eps * CG + lane]);
+            const float qt = a.q_total / seps;
+            cst[lane] = (float)(((double)qt - sums[4 * CG + lane]) / (double)n);
+            cst[2 * CG + lane] = qt;
+        }
+        __syncthreads();
+        // 2 corrected charges q^c = q + (Q / sqrt(eps_inf) - sum q) / N
+        for (int i = threadIdx.x; i < n * CG; i += NW * 32) qcs[i] = uq[i].y + cst[i & 31];
+        __syncthreads();
+
+        // 3 structure factor: lanes over 32 wave vectors (4 chunks of 8), FP64 flushes
+        const BatchKTab kt = a.kt[bs.ktab];
+        const float2* phb = a.phase + (size_t)off * a.nph_stride;
+        double ek = 0.0;
+        {
+            float* qt = un;
+            double* accd = reinterpret_cast<double*>(un + QT * CG) + warp * ACCD;
+            const int ntask = (kt.nchunk + 3) >> 2;
+            for (int tb = 0; tb < ntask; tb += NW) {
+                const int task = tb + warp;
+                const bool act = task < ntask;
+                const int h = task * 4 + (lane >> 3), t = lane & 7;
+                int e1 = 0, e2 = kt.yoff, e3 = kt.zoff;
+                if (act && h < kt.nchunk) {
+                    const int4 ci = __ldg(&a.chunk[kt.chunk_off + h]);
+                    e1 = ci.x;
+                    e2 = kt.yoff + ci.y + kt.n2max;
+                    e3 = kt.zoff + ci.z + t + kt.n3max;
+                }
+                float sr[CG], si[CG];
+#pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    sr[c] = 0.f;
+                    si[c] = 0.f;
+                }
+                if (act)
+                    for (int i = lane; i < ACCD; i += 32) accd[i] = 0.0;
+                int tiles = 0;
+                for (int j0 = 0; j0 < n; j0 += QT) {
+                    const int cnt = min(QT, n - j0);
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < cnt * CG; i += NW * 32) qt[i] = qcs[(size_t)j0 * CG + i];
+                    __syncthreads();
+                    if (act) {
+                        for (int jj = 0; jj < cnt; ++jj) {
+                            const float2* row = phb + (size_t)(j0 + jj) * a.nph_stride;
+                            const float2 e = cmul(cmul(__ldg(&row[e1]), __ldg(&row[e2])), __ldg(&row[e3]));
+                            const float4* q4 = reinterpret_cast<const float4*>(qt + jj * CG);
+#pragma unroll
+                            for (int c4 = 0; c4 < CG / 4; ++c4) {
+                                const float4 q = q4[c4];
+                                sr[4 * c4 + 0] = fmaf(q.x, e.x, sr[4 * c4 + 0]);
+                                si[4 * c4 + 0] = fmaf(q.x, e.y, si[4 * c4 + 0]);
+                                sr[4 * c4 + 1] = fmaf(q.y, e.x, sr[4 * c4 + 1]);
+                                si[4 * c4 + 1] = fmaf(q.y, e.y, si[4 * c4 + 1]);
+                                sr[4 * c4 + 2] = fmaf(q.z, e.x, sr[4 * c4 + 2]);
+                                si[4 * c4 + 2] = fmaf(q.z, e.y, si[4 * c4 + 2]);
+                                sr[4 * c4 + 3] = fmaf(q.w, e.x, sr[4 * c4 + 3]);
+                                si[4 * c4 + 3] = fmaf(q.w, e.y, si[4 * c4 + 3]);
+                            }
+                        }
+                        if (++tiles == FLUSH_TILES || j0 + QT >= n) {
+                            tiles = 0;
+#pragma unroll
+                            for (int c = 0; c < CG; ++c) {
+                                double* p = accd + (c * 33 + lane) * 2;
+                                p[0] += (double)sr[c];
+                                p[1] += (double)si[c];
+                                sr[c] = 0.f;
+                                si[c] = 0.f;
+                            }
+                        }
+                    }
+                }
+                if (act) {
+                    __syncwarp();
+                    // lane = candidate: U^k += (w/2)|S|^2 and the FP32 copy w S, w = 4 k_e G
+                    for (int kk = 0; kk < 32; ++kk) {
+                        const int hk = task * 4 + (kk >> 3);
+                        if (hk >= kt.nchunk) break;
+                        const int kl = 8 * hk + (kk & 7);
+                        const float w = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]).w;
+                        const double* p = accd + (lane * 33 + kk) * 2;
+                        const double Sr = p[0], Si = p[1];
+                        ek += 0.5 * (double)w * (Sr * Sr + Si * Si);
+                        sk[(size_t)kl * CG + lane] = make_float2((float)((double)w * Sr), (float)((double)w * Si));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // 4a k-space potential and field: lanes over atoms, 16 candidates per pass
+        {
+            float2* ph = reinterpret_cast<float2*>(un) + (size_t)warp * kt.nph * 32;
+            for (int task = warp; task * 32 < n; task += NW) {
+                const int j = task * 32 + lane;
+                const int cnt = min(32, n - task * 32);
+                const float2* src = phb + (size_t)task * 32 * a.nph_stride;
+                for (int idx = lane; idx < cnt * kt.nph; idx += 32) {
+                    const int jj = idx / kt.nph, e = idx - jj * kt.nph;
+                    ph[e * 32 + jj] = src[(size_t)jj * a.nph_stride + e];
+                }
+                __syncwarp();
+                for (int c0 = 0; c0 < CG; c0 += 16) {
+                    float fphi[16], ex[16], ey[16], ez[16], tt[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        fphi[c] = 0.f;
+                        ex[c] = 0.f;
+                        ey[c] = 0.f;
+                        ez[c] = 0.f;
+                        tt[c] = 0.f;
+                    }
+                    float pkx = 0.f, pky = 0.f;
+                    int pn1 = -(1 << 30), pn2 = 0;
+                    for (int h = 0; h < kt.nchunk; ++h) {
+                        const int4 ci = __ldg(&a.chunk[kt.chunk_off + h]);
+                        const float4* kv = a.kvec + 8 * (size_t)(kt.chunk_off + h);
+                        if (ci.x != pn1 || ci.y != pn2) {
+                            // new column (n1, n2): fold the column's Im sums into E_x, E_y
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                ex[c] = fmaf(pkx, tt[c], ex[c]);
+                                ey[c] = fmaf(pky, tt[c], ey[c]);
+                                tt[c] = 0.f;
+                            }
+                            pn1 = ci.x;
+                            pn2 = ci.y;
+                            const float4 k0 = __ldg(&kv[0]);
+                            pkx = k0.x;
+                            pky = k0.y;
+                        }
+                        const float2 xy = cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
+                        for (int t = 0; t < 8; ++t) {
+                            const float4 k4 = __ldg(&kv[t]);
+                            if (k4.w == 0.f) continue;
+                            const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
+                            const float4* s4 = reinterpret_cast<const float4*>(sk + (size_t)(8 * h + t) * CG + c0);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const float4 v = s4[u];
+                                // z = C conj(e) for the two candidates of v
+                                float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
+                                fphi[2 * u] += zr;
+                                tt[2 * u] += zi;
+                                ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
+                                zr = fmaf(v.z, e.x, v.w * e.y);
+                                zi = fmaf(v.w, e.x, -v.z * e.y);
+                                fphi[2 * u + 1] += zr;
+                                tt[2 * u + 1] += zi;
+                                ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        ex[c] = fmaf(pkx, tt[c], ex[c]);
+                        ey[c] = fmaf(pky, tt[c], ey[c]);
+                    }
+                    if (j < n) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            fk[(size_t)(c0 + c) * nmax + j] = make_float4(fphi[c], ex[c], ey[c], ez[c]);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+
+        // 4b real space (lanes over candidates) and the potential sums
+        double er = 0.0, sphi = 0.0, sq2 = 0.0;
+        {
+            float* tab = un + PARAM_FLOATS + warp * WARP_FLOATS;
+            int* cum = reinterpret_cast<int*>(tab + WCUM);
+            const float4* sp = a.spos4 + off;
+            const Geom& g = bs.g;
+            const float rcs2 = g.rc_real * g.rc_real;
+            for (int m = warp; m < n; m += NW) {
+                const float qi = qcs[(size_t)m * CG + lane];
+                float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                if (a.mode == 1) {
+                    species_cum(a, off, n, m, S, cum);
+                    const int tot_l = cum[S];
+                    const float4 pk = sp[m];
+                    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
+                    for (int base = 0; base < tot_l; base += 32) {
+                        const int e = base + lane;
+                        float B = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+                        int jj = -1;
+                        if (e < tot_l) {
+                            const int ent = __ldg(&lst[e]);
+                            float vx, vy, vz;
+                            entry_vector(sp, ent, pk, g, vx, vy, vz);
+                            const float r2 = vx * vx + vy * vy + vz * vz;
+                            if (r2 < rcs2) {
+                                const float r = sqrtf(r2), ir = 1.f / r, ar = a.alpha * r;
+                                const float ec = erfcf(ar);
+                                B = KE * ec * ir;
+                                // dB/dr = -k_e (erfc(a r) / r + 2 a / sqrt(pi) exp(-a^2 r^2)) / r
+                                const float dB = -KE * (ec * ir + 1.12837916709551257f * a.alpha * expf(-ar * ar)) * ir;
+                                bx = dB * vx * ir;
+                                by = dB * vy * ir;
+                                bz = dB * vz * ir;
+                                jj = entry_index(ent);
+                            }
+                        }
+                        float* row = tab + lane * TAB_RS;
+                        row[0] = B;
+                        row[1] = bx;
+                        row[2] = by;
+                        row[3] = bz;
+                        row[4] = __int_as_float(jj);
+                        __syncwarp();
+                        const int cntc = min(32, tot_l - base);
+                        for (int r = 0; r < cntc; ++r) {
+                            const float* rw = tab + r * TAB_RS;
+                            const int j = __float_as_int(rw[4]);
+                            if (j < 0) continue;
+                            const float qj = qcs[(size_t)j * CG + lane];
+                            ph = fmaf(qj, rw[0], ph);
+                            gx = fmaf(qj, rw[1], gx);
+                            gy = fmaf(qj, rw[2], gy);
+                            gz = fmaf(qj, rw[3], gz);
+                        }
+                        __syncwarp();
+                    }
+                }
+                // F^r_i = sum_j q_i q_j B'(r) u_ij (u_ij from i to j)
+                fr[(size_t)m * CG + lane] = make_float4(ph, qi * gx, qi * gy, qi * gz);
+                const float4 kf = fk[(size_t)lane * nmax + m];
+                sphi += (double)ph + (double)kf.x;
+                er += 0.5 * (double)qi * (double)ph;
+                sq2 += (double)qi * (double)qi;
+            }
+        }
+        block_sum<NW>(ek, red, sums + 1 * CG);
+        block_sum<NW>(er, red, sums + 2 * CG);
+        block_sum<NW>(sq2, red, sums + 3 * CG);
+        block_sum<NW>(sphi, red, sums + 5 * CG);
+        if (warp == 0)
+            cst[CG + lane] = (float)((sums[5 * CG + lane] + (double)selfc * (double)cst[2 * CG + lane]) / (double)n);
+        __syncthreads();
+
+        // 5 backward, one species block at a time
+        for (int ti = 0; ti < S; ++ti) {
+            const int p0 = so[ti], p1 = so[ti + 1];
+            if (p1 == p0) continue;
+            __syncthreads();
+            stage_params(pg, a.lay, ti, un);
+            __syncthreads();
+            float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
+            const float phibar = cst[CG + lane];
+            for (int p = p0 + warp; p < p1; p += NW)
+                backward_atom(a, bs, a.order[off + p], un, wb, A, duq, qcs, fk, fr, fsum, nmax, selfc, phibar);
+        }
+        __syncthreads();
+
+        // 6 outputs in input order, candidate-major
+        if (a.forces || a.charges) {
+            for (int i = threadIdx.x; i < n * CG; i += NW * 32) {
+                const int m = i >> 5, c = grp * CG + (i & 31);
+                if (c >= a.n_cand) continue;
+                const size_t gi = (size_t)off + __ldg(&a.sidx[off + m]);
+                if (a.forces) {
+                    const float4 F = fsum[i];
+                    float* fo = a.forces + ((size_t)c * a.n_total + gi) * 3;
+                    fo[0] = F.x;
+                    fo[1] = F.y;
+                    fo[2] = F.z;
+                }
+                if (a.charges) a.charges[(size_t)c * a.n_total + gi] = qcs[i];
+            }
+        }
+        if (warp == 0 && cand < a.n_cand) {
+            double e = sums[lane] + sums[CG + lane];
+            if (a.mode == 1) e += sums[2 * CG + lane] - (double)KE * (double)a.alpha * 0.564189583547756287 * sums[3 * CG + lane];
+            a.energy[(size_t)cand * a.n_struct + item.x] = e;
+        }
+    }
+}
+
+template <int NW>
+size_t item_smem(int nph_max) {
+    const size_t head = sizeof(double) * (NW + NSUMS) * CG + sizeof(float) * 4 * CG;
+    const size_t p1 = sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
+    const size_t p3 = sizeof(float) * (size_t)QT * CG + sizeof(double) * (size_t)NW * ACCD;
+    const size_t p4 = sizeof(float2) * (size_t)NW * nph_max * 32;
+    return head + std::max(p1, std::max(p3, p4));
+}
+
+}  // namespace
+
+void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
+                       const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
+                       int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
+                       int* cnt_ang, float2* phase, int nph_stride, unsigned int* status, cudaStream_t st_) {
+    if (n_struct <= 0) return;
+    const size_t sm1 = sizeof(int) * ((size_t)nmax + BATCH_MAX_CELLS + 1 + MAX_SPECIES + 1);
+    const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a);
+    static size_t attr1 = 0, attr2 = 0;
+    if (sm1 > 48 * 1024 && sm1 > attr1) {
+        cudaFuncSetAttribute(k_batch_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+        attr1 = sm1;
+    }
+    if (sm2 > 48 * 1024 && sm2 > attr2) {
+        cudaFuncSetAttribute(k_batch_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        attr2 = sm2;
+    }
+    k_batch_sort<<<n_struct, PREP_THREADS, sm1, st_>>>(pos, types, nmax, n_species, st, cell_start, spos4, sidx,
+                                                        order, spec_off, status);
+    k_batch_lists<<<n_struct, PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
+                                                         cnt_list, nbr_ang, cnt_ang, phase, nph_stride, status);
+}
+
+size_t batch_item_smem(int warps, int nph_max) {
+    return warps == 4 ? item_smem<4>(nph_max) : item_smem<8>(nph_max);
+}
+
+int batch_item_blocks_per_sm(int warps, int nph_max) {
+    const size_t smem = batch_item_smem(warps, nph_max);
+    int nb = 0;
+    if (warps == 4) {
+        cudaFuncSetAttribute(k_batch_items<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<4>, 128, smem) != cudaSuccess) nb = 0;
+    } else {
+        cudaFuncSetAttribute(k_batch_items<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8>, 256, smem) != cudaSuccess) nb = 0;
+    }
+    return nb;
+}
+
+void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int grid, cudaStream_t st_) {
+    if (grid <= 0 || a.n_items <= 0) return;
+    const size_t smem = batch_item_smem(warps, nph_max);
+    if (warps == 4)
+        k_batch_items<4><<<grid, 128, smem, st_>>>(a);
+    else
+        k_batch_items<8><<<grid, 256, smem, st_>>>(a);
+}
+
+}  // namespace qnep

@@ -1,0 +1,109 @@
+// Internal declarations of the batched force call: many structures of uneven size,
+// each evaluated under many candidate parameter vectors (the shape of a separable
+// natural-evolution-strategy fitness evaluation, Sec. II.E).
+//
+// Work decomposition.  The unit of work ("item") is one structure under a group of
+// CG = 32 candidates.  One thread block owns an item from start to end, so every
+// per-structure synchronisation point of the force call (total charge, S(k), mean
+// potential) is a block barrier, and a persistent grid takes items from a queue
+// ordered largest first.  Inside an item lane c of every warp evaluates candidate
+// c of the group: geometry, basis functions, harmonics and Ewald phases do not
+// depend on the candidate, so they are computed once per pair or atom, staged in
+// shared memory and read by all 32 lanes as broadcasts, while each lane reads its
+// own candidate's parameters from a candidate-minor copy ([parameter][candidate]),
+// conflict-free.  Per-candidate results are laid out [atom][..][candidate] so the
+// lanes' loads, stores and float4 atomics are coalesced.
+#pragma once
+
+#include "qnep_internal.cuh"
+
+namespace qnep {
+
+constexpr int CG = 32;               // candidates per item (one per lane)
+constexpr int BATCH_MAX_NPH = 96;    // phase factors per atom (n_max <= 17 per axis: edges up to
+                                     // ~48 A at k_max = 2.23 1/A)
+constexpr int BATCH_MAX_CELLS = 512; // cell grid per structure (8 per axis at most)
+
+// One structure of the batch (host-built).
+struct BatchStruct {
+    int atom_off;    // first atom in the concatenated inputs
+    int n;           // atoms
+    int ktab;        // its k-space table
+    int cell_off;    // offset of its cell_start array (ncells + 1 entries)
+    Geom g;          // box and cell grid
+};
+
+// Half-space k-set of one box shape (see KSet): chunk h of the table is global chunk
+// chunk_off + h, whose 8 wave vectors are kvec[8 (chunk_off + h) + t].
+struct BatchKTab {
+    int n1max, n2max, n3max;
+    int nph;         // phase factors per atom: X[0..n1max] | Y[-n2max..n2max] | Z[-n3max..n3max+7]
+    int yoff, zoff;
+    int nchunk;
+    int chunk_off;
+    float invl_hi[3], invl_lo[3];
+};
+
+// Per-slot scratch (one slot per resident block), in floats, for nmax atoms.
+struct BatchScratch {
+    float* A;        // [nmax][NANG][CG] angular expansion coefficients A_{n,lm}
+    float* duq;      // [nmax][2 NDES][CG] dU/dD (scaled) then dq/dD (scaled)
+    float2* uq;      // [nmax][CG] (U_i, q_i) raw network outputs
+    float* qc;       // [nmax][CG] corrected charges q^c
+    float4* fk;      // [CG][nmax] (phi^k, E^k) k-space potential and field per unit charge
+    float4* fr;      // [nmax][CG] (phi^r, F^r) real space
+    float4* fsum;    // [nmax][CG] force accumulators (xyz, pad)
+    float2* sk;      // [nk_max][CG] 4 k_e G(k) S(k) (FP32)
+    size_t stride_A, stride_duq, stride_n, stride_k;   // per-slot strides (elements)
+};
+
+struct BatchArgs {
+    // pre-pass outputs (per structure, candidate independent)
+    const float4* spos4;     // [N] cell-sorted wrapped positions (species in w)
+    const int* sidx;         // [N] input index (within the structure) of each sorted atom
+    const int* order;        // [N] sorted atoms grouped by species
+    const int* spec_off;     // [n_struct][MAX_SPECIES + 1] species ranges of `order`
+    const int* nbr_list;     // [N][cap_l] grouped by neighbour species
+    const int* cnt_list;     // structure s: [S][n_s] at cnt_list + atom_off * S
+    const int* nbr_ang;
+    const int* cnt_ang;
+    int cap_l, cap_a;
+    const float2* phase;     // [N][nph_stride]
+    int nph_stride;
+    // tables
+    const BatchStruct* st;
+    const BatchKTab* kt;
+    const int4* chunk;       // [n_chunks] (n1, n2, first n3, 0)
+    const float4* kvec;      // [8 n_chunks] (kx, ky, kz, 4 k_e G) (G = 0 on padding)
+    // parameters by candidate group: [group][p][CG] (lane-minor)
+    const float* pt;
+    ParamLayout lay;
+    int n_cand;
+    // work queue
+    const int2* items;       // (structure, group), largest first
+    int n_items;
+    unsigned int* work;
+    BatchScratch sc;
+    // electrostatics
+    int mode;
+    float alpha;
+    float q_total;
+    // outputs
+    double* energy;          // [n_cand][n_struct]
+    float* forces;           // [n_cand][N_total][3] or NULL
+    float* charges;          // [n_cand][N_total] or NULL
+    int n_struct;
+    int n_total;
+    unsigned int* status;    // bit 0: neighbour overflow
+};
+
+void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
+                       const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
+                       int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
+                       int* cnt_ang, float2* phase, int nph_stride, unsigned int* status, cudaStream_t st_);
+// Dynamic shared memory of the item kernel and its resident blocks per SM (0: does not fit).
+size_t batch_item_smem(int warps, int nph_max);
+int batch_item_blocks_per_sm(int warps, int nph_max);
+void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int grid, cudaStream_t st_);
+
+}  // namespace qnep

@@ -1,0 +1,62 @@
+// Host construction of the half-space Ewald k-set (shared by the single-structure
+// and the batched force calls).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace qnep {
+
+// Wave vectors k = 2 pi (n1/Lx, n2/Ly, n3/Lz) with 0 < |k| < kmax in the half space
+// n1 > 0, or n1 = 0 and n2 > 0, or n1 = n2 = 0 and n3 > 0 (S(-k) = S(k)^*).  They
+// are grouped in columns (n1, n2) holding the contiguous run n3 in [lo, hi], and each
+// column is stored as 8-wide chunks of n3, padded past hi with G = 0.
+struct KSet {
+    int nmax[3];
+    std::vector<int4> cols;       // (n1, n2, lo, padded offset); last entry (0, 0, 0, nk)
+    std::vector<int> chunk_col;   // column of each chunk
+    std::vector<float> kg;        // G(k) = (2 pi / V) exp(-k^2 / 4 alpha^2) / k^2, 0 on padding
+};
+
+inline KSet build_kset(const double L[3], double kmax, double alpha) {
+    const double two_pi = 6.283185307179586;
+    const double vol = L[0] * L[1] * L[2];
+    KSet ks;
+    for (int d = 0; d < 3; ++d) ks.nmax[d] = (int)std::floor(kmax * L[d] / two_pi);
+    const int* nmax = ks.nmax;
+    for (int n1 = 0; n1 <= nmax[0]; ++n1) {
+        for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2) {
+            if (n1 == 0 && n2 < 0) continue;
+            double kx = two_pi * n1 / L[0], ky = two_pi * n2 / L[1];
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
+                if (n1 == 0 && n2 == 0 && n3 <= 0) continue;
+                double kz = two_pi * n3 / L[2];
+                double k2 = kx * kx + ky * ky + kz * kz;
+                if (k2 > 0 && k2 < kmax * kmax) {
+                    lo = std::min(lo, n3);
+                    hi = std::max(hi, n3);
+                }
+            }
+            if (hi < lo) continue;
+            int nchunk = (hi - lo + 1 + 7) / 8;
+            int c = (int)ks.cols.size();
+            ks.cols.push_back(make_int4(n1, n2, lo, (int)ks.kg.size()));
+            for (int h = 0; h < nchunk; ++h) ks.chunk_col.push_back(c);
+            for (int t = 0; t < 8 * nchunk; ++t) {
+                int n3 = lo + t;
+                double kz = two_pi * n3 / L[2];
+                double k2 = kx * kx + ky * ky + kz * kz;
+                bool ok = n3 <= hi && k2 > 0 && k2 < kmax * kmax && !(n1 == 0 && n2 == 0 && n3 <= 0);
+                ks.kg.push_back(ok ? (float)(two_pi / vol * std::exp(-k2 / (4 * alpha * alpha)) / k2) : 0.f);
+            }
+        }
+    }
+    ks.cols.push_back(make_int4(0, 0, 0, (int)ks.kg.size()));
+    return ks;
+}
+
+}  // namespace qnep

@@ -239,3 +239,126 @@ class QNEPFunction(torch.autograd.Function):
 def qnep_energy(model: QNEP, positions: torch.Tensor, types: torch.Tensor, box):
     """(U^tot, q^c, P) with autograd support (QNEPFunction)."""
     return QNEPFunction.apply(positions, model, types, box)
+
+
+class QNEPBatch:
+    """Batched force call: every (candidate parameter vector, structure) pair of a batch.
+
+    ``params`` is [n_candidates, n_params]; ``compute`` takes the concatenated
+    positions [N_total, 3] and types [N_total] as CUDA tensors, the host atom
+    offsets [n_struct + 1] and boxes [n_struct, 3, 3], and returns CUDA tensors
+    energy [C, S] (float64), forces [C, N_total, 3] and charges [C, N_total].
+    """
+
+    def __init__(self, hp: HParams, params, elec: Elec):
+        self.lib = _lib.load()
+        blob = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        self.n_cand = blob.size // hp.n_params
+        self.hp, self.elec = hp, elec
+        handle = ctypes.c_void_p()
+        hpc, esc = _hp_c(hp), _elec_c(elec)
+        _lib.check(self.lib.qnep_batch_create(ctypes.byref(handle), ctypes.byref(hpc), blob.ctypes.data,
+                                              blob.size, self.n_cand, ctypes.byref(esc)))
+        self.handle = handle
+        self._desc = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.qnep_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _describe(self, offsets, boxes):
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1))
+        bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 9))
+        self._desc = (off, bx)   # kept alive: the library reads them on every call
+        return off, bx
+
+    def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True) -> dict:
+        out = {"energy": torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)}
+        if forces:
+            out["forces"] = torch.empty(self.n_cand, n_total, 3, dtype=torch.float32, device=device)
+        if charges:
+            out["charges"] = torch.empty(self.n_cand, n_total, dtype=torch.float32, device=device)
+        return out
+
+    def _args(self, positions, types, offsets, boxes, out, stream):
+        assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
+        assert types.is_cuda and types.dtype == torch.int32 and types.is_contiguous()
+        off, bx = self._describe(offsets, boxes)
+        if stream is None:
+            stream = torch.cuda.current_stream(positions.device).cuda_stream
+
+        def ptr(name):
+            t = out.get(name)
+            return t.data_ptr() if t is not None else None
+
+        return (self.handle, len(off) - 1, off.ctypes.data, positions.data_ptr(), types.data_ptr(),
+                bx.ctypes.data, ctypes.c_void_p(stream), ptr("energy"), ptr("forces"), ptr("charges"))
+
+    def compute_into(self, positions, types, offsets, boxes, out: dict, stream=None):
+        """Enqueue one batched call writing into ``out`` (from ``outputs``); no synchronisation."""
+        _lib.check(self.lib.qnep_batch_compute(*self._args(positions, types, offsets, boxes, out, stream)),
+                   batch=self.handle)
+
+    def sync_status(self) -> int:
+        return self.lib.qnep_batch_sync_status(self.handle)
+
+    def compute(self, positions, types, offsets, boxes, retries: int = 3, forces=True, charges=True) -> dict:
+        """Batched call with a status check; grows the neighbour lists and retries on overflow."""
+        n_struct = len(offsets) - 1
+        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges)
+        for _ in range(retries + 1):
+            self.compute_into(positions, types, offsets, boxes, out)
+            st = self.sync_status()
+            if st != _lib.QNEP_ERR_NBR_OVERFLOW:
+                _lib.check(st, batch=self.handle)
+                return out
+            cl, ca = self.capacity()
+            self.set_capacity(int(cl * 1.5) + 32, int(ca * 1.5) + 16)
+        raise _lib.QnepError(_lib.QNEP_ERR_NBR_OVERFLOW, "neighbour list overflow after retries")
+
+    def set_capacity(self, cap_list: int = 0, cap_angular: int = 0):
+        _lib.check(self.lib.qnep_batch_set_capacity(self.handle, int(cap_list), int(cap_angular)),
+                   batch=self.handle)
+
+    def capacity(self) -> tuple:
+        cl, ca = ctypes.c_int(), ctypes.c_int()
+        _lib.check(self.lib.qnep_batch_capacity(self.handle, ctypes.byref(cl), ctypes.byref(ca)),
+                   batch=self.handle)
+        return cl.value, ca.value
+
+    def set_config(self, warps: int = 8, order: str = "largest_first"):
+        code = {"largest_first": _lib.QNEP_BATCH_ORDER_LARGEST_FIRST,
+                "structure": _lib.QNEP_BATCH_ORDER_STRUCTURE}[order]
+        _lib.check(self.lib.qnep_batch_set_config(self.handle, int(warps), code), batch=self.handle)
+
+    def config(self) -> tuple:
+        w, o = ctypes.c_int(), ctypes.c_int()
+        _lib.check(self.lib.qnep_batch_get_config(self.handle, ctypes.byref(w), ctypes.byref(o)),
+                   batch=self.handle)
+        return w.value, ("largest_first", "structure")[o.value]
+
+    def autotune(self, positions, types, offsets, boxes, reps: int = 3, out: dict | None = None) -> float:
+        """Time every launch configuration on this batch and keep the fastest; returns its ms."""
+        if out is None:
+            out = self.outputs(len(offsets) - 1, positions.shape[0], positions.device)
+        best = ctypes.c_double()
+        args = self._args(positions, types, offsets, boxes, out, None)
+        _lib.check(self.lib.qnep_batch_autotune(*args, int(reps), ctypes.byref(best)), batch=self.handle)
+        return best.value
+
+
+def stack_structures(systems) -> tuple:
+    """Concatenate structures: (positions [N, 3] f32, types [N] i32, offsets [S + 1], boxes [S, 3, 3])."""
+    pos = np.concatenate([np.asarray(s.positions, dtype=np.float32) for s in systems]).reshape(-1, 3)
+    typ = np.concatenate([np.asarray(s.types, dtype=np.int32) for s in systems])
+    off = np.zeros(len(systems) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([s.n_atoms for s in systems])
+    boxes = np.stack([np.asarray(s.box, dtype=np.float64).reshape(3, 3) for s in systems])
+    return pos, typ, off, boxes

@@ -1,0 +1,185 @@
+"""GPU parity of the batched force call (many structures x many candidate parameter vectors).
+
+Every (candidate, structure) pair of a small batch is compared with the FP64 oracle
+(energy |dE|/N <= 1e-6 eV/atom, forces <= 1e-4 eV/A, charges <= 2e-6 e, the
+tolerances of the single-structure path), and with the single-structure CUDA path.
+The full 512 x 64 LLZO batch is checked on sampled (candidate, structure) pairs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import forcecall  # noqa: E402
+from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = dict(e=1e-6, f=1e-4, q=2e-6)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19034_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def _llzo(reps, seed, sigma=0.1):
+    """Supercell reps of the random 192-atom LLZO cell with N(0, sigma) moves."""
+    base = wl.llzo_base_cell()
+    a = base.box[0, 0]
+    rng = np.random.default_rng(seed)
+    shifts = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3)
+    pos = (base.positions[None].astype(np.float64) + shifts[:, None, :] * a).reshape(-1, 3)
+    pos += rng.normal(0.0, sigma, size=pos.shape)
+    lengths = np.asarray(reps) * a
+    pos %= lengths
+    return wl.System(pos.astype(np.float32), np.tile(base.types, len(shifts)), np.diag(lengths.astype(np.float64)),
+                     wl.LLZO_SPECIES)
+
+
+def _run_batch(systems, hp, params, elec, dev, warps=8, order="largest_first"):
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    pos, typ, off, boxes = stack_structures(systems)
+    b = QNEPBatch(hp, params, elec)
+    b.set_config(warps, order)
+    out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    b.close()
+    return res, off
+
+
+def _check_pair(res, off, systems, s, c, hp, params, elec):
+    sysm = systems[s]
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params[c], elec,
+                               want_bec=False)
+    n = sysm.n_atoms
+    sl = slice(off[s], off[s + 1])
+    assert abs(res["energy"][c, s] - ref["energy"]) / n <= TOL["e"], (s, c, res["energy"][c, s], ref["energy"])
+    df = np.abs(res["forces"][c, sl] - ref["forces"]).max()
+    assert df <= TOL["f"], (s, c, df)
+    dq = np.abs(res["charges"][c, sl] - ref["charges"]).max()
+    assert dq <= TOL["q"], (s, c, dq)
+
+
+@pytest.mark.parametrize("warps", [8, 4])
+def test_small_batch_every_pair_against_oracle(dev, warps):
+    systems = [_llzo((1, 1, 1), 1), _llzo((2, 1, 1), 2), _llzo((1, 1, 2), 3)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(11), n_candidates=3)
+    elec = wl.Elec(mode=1, kind="ewald")
+    res, off = _run_batch(systems, hp, params, elec, dev, warps=warps)
+    for s in range(len(systems)):
+        for c in range(3):
+            _check_pair(res, off, systems, s, c, hp, params, elec)
+
+
+def test_two_groups_against_single_structure_path(dev):
+    """40 candidates (a full and a partial lane group) x 4 structures vs qnep_compute per pair."""
+    from paper_2601_19034_gb300.qnep import QNEP
+    systems = [_llzo((1, 1, 1), 4), _llzo((1, 2, 1), 5), _llzo((2, 2, 1), 6), _llzo((1, 1, 1), 7)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(12), n_candidates=40)
+    elec = wl.Elec(mode=1, kind="ewald")
+    res, off = _run_batch(systems, hp, params, elec, dev)
+    for c in range(40):
+        model = QNEP(hp, params[c], elec)
+        for s, sysm in enumerate(systems):
+            out = model.compute(torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev),
+                                sysm.box, bec=False, virial=False)
+            sl = slice(off[s], off[s + 1])
+            e1 = out["scalars"][0].item()
+            assert abs(res["energy"][c, s] - e1) / sysm.n_atoms <= 2 * TOL["e"], (s, c)
+            assert np.abs(res["forces"][c, sl] - out["forces"].cpu().numpy()).max() <= 2 * TOL["f"], (s, c)
+            assert np.abs(res["charges"][c, sl] - out["charges"].cpu().numpy()).max() <= 2 * TOL["q"], (s, c)
+        model.close()
+    # one pair of each group against the oracle as well
+    for s, c in ((2, 5), (1, 37)):
+        _check_pair(res, off, systems, s, c, hp, params, elec)
+
+
+def test_mode2_total_charge_and_one_species_water(dev):
+    """k-space-only electrostatics, a charged target and 2-species water boxes of uneven size."""
+    systems = [wl.water_box(4, seed=21), wl.water_box(5, seed=22)]
+    hp = wl.HParams(n_species=2)
+    params = wl.random_params(hp, np.random.default_rng(13), n_candidates=33)
+    elec = wl.Elec(mode=2, kind="ewald", q_total=0.5)
+    res, off = _run_batch(systems, hp, params, elec, dev)
+    for s, c in ((0, 0), (1, 32), (1, 7)):
+        _check_pair(res, off, systems, s, c, hp, params, elec)
+    # total corrected charge is Q / sqrt(eps_inf) per pair
+    for s in range(2):
+        tot = res["charges"][:, off[s]:off[s + 1]].astype(np.float64).sum(1)
+        np.testing.assert_allclose(tot, 0.5 / params[:, -1].astype(np.float64), atol=2e-4)
+
+
+def test_graph_replay_and_autotuner_agree(dev):
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    systems = [_llzo((1, 1, 1), 8), _llzo((2, 1, 1), 9), _llzo((1, 2, 2), 10)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(14), n_candidates=64)
+    elec = wl.Elec(mode=1, kind="ewald")
+    pos, typ, off, boxes = stack_structures(systems)
+    pos_d, typ_d = torch.tensor(pos, device=dev), torch.tensor(typ, device=dev)
+    b = QNEPBatch(hp, params, elec)
+    ref = {k: v.clone() for k, v in b.compute(pos_d, typ_d, off, boxes).items()}
+    ms = b.autotune(pos_d, typ_d, off, boxes, reps=2)
+    assert ms > 0
+    out = b.outputs(len(systems), pos.shape[0], dev)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        b.compute_into(pos_d, typ_d, off, boxes, out)   # description cached: launch only
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.compute_into(pos_d, typ_d, off, boxes, out)
+    for v in out.values():
+        v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.sync_status() == 0
+    n = np.diff(off)
+    de = (out["energy"] - ref["energy"]).abs().cpu().numpy() / n[None, :]
+    assert de.max() <= 1e-6
+    assert (out["forces"] - ref["forces"]).abs().max().item() <= 1e-4
+    assert (out["charges"] - ref["charges"]).abs().max().item() <= 1e-6
+    b.close()
+
+
+def test_argument_errors_before_gpu_work(dev):
+    from paper_2601_19034_gb300 import _lib
+    from paper_2601_19034_gb300.qnep import QNEPBatch
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(15), n_candidates=2)
+    b = QNEPBatch(hp, params, wl.Elec(mode=1, kind="ewald"))
+    pos = torch.zeros(10, 3, device=dev)
+    typ = torch.zeros(10, dtype=torch.int32, device=dev)
+    with pytest.raises(_lib.QnepError) as e:   # box edge below the 6 A list cutoff
+        b.compute(pos, typ, [0, 10], np.diag([5.0, 20.0, 20.0])[None])
+    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    with pytest.raises(_lib.QnepError) as e:   # offsets must not decrease
+        b.compute(pos, typ, [0, 10, 5], np.stack([np.eye(3) * 20.0] * 2))
+    assert e.value.status == _lib.QNEP_ERR_ARG
+    # a species index outside [0, n_species) is reported by the status check (no out-of-range access)
+    typ_bad = torch.tensor([0, 1, 2, 3, 7, 0, 1, 2, 3, 0], dtype=torch.int32, device=dev)
+    pos_ok = torch.rand(10, 3, device=dev) * 20.0
+    with pytest.raises(_lib.QnepError) as e:
+        b.compute(pos_ok, typ_bad, [0, 10], (np.eye(3) * 20.0)[None])
+    assert e.value.status == _lib.QNEP_ERR_ARG
+    b.close()
+
+
+def test_full_llzo_batch_sampled_pairs(dev):
+    """512 LLZO cells (192-1536 atoms) x 64 candidates in one call; sampled pairs vs the oracle."""
+    systems, hp, params, elec = wl.config_llzo_batch()
+    res, off = _run_batch(systems, hp, params, elec, dev)
+    assert np.isfinite(res["energy"]).all() and np.isfinite(res["forces"]).all()
+    sizes = np.diff(off)
+    big = int(np.argmax(sizes))
+    small = int(np.argmin(sizes))
+    for s, c in ((big, 63), (small, 0), (int(np.argsort(sizes)[len(sizes) // 2]), 33)):
+        _check_pair(res, off, systems, s, c, hp, params, elec)
