@@ -39,12 +39,18 @@ WORKLOADS = {
                    "PPPM mesh 64^3, order 5, alpha 0.3, r_c 6 A, mode 1; forces + virial + BEC + polarization, "
                    "FP32 path"),
 }
+WORKLOADS["llzo_batch"] = (
+    "512 LLZO-shaped cells (Li/La/Zr/O 7:3:2:12, 1x1x1..2x2x2 supercells of a random 12.97 A 192-atom cell, "
+    "192-1536 atoms, N(0, 0.1 A) moves) x 64 candidate parameter vectors N(0, 0.1), 4 species; same descriptor / "
+    "network; Ewald per cell alpha 0.3, r_c 6 A, k_max 2.230, mode 1; energy, forces and charges per "
+    "(structure, candidate), FP32 path, one persistent launch")
 WORKLOAD = WORKLOADS["batio3"]
 
 
 def _config(name):
     from paper_2601_19034_gb300 import workloads
-    return {"batio3": workloads.config_batio3, "water_pppm": workloads.config_water_pppm}[name]()
+    return {"batio3": workloads.config_batio3, "water_pppm": workloads.config_water_pppm,
+            "llzo_batch": workloads.config_llzo_batch}[name]()
 
 
 def _peaks():
@@ -312,8 +318,10 @@ def run_reference(args):
 
     from oracle import forcecall
     from paper_2601_19034_gb300 import workloads
-    sysm, hp, params, elec = _config(args.workload)
     cores = torch.get_num_threads()
+    if args.workload == "llzo_batch":
+        return _reference_batch(args, world, cores)
+    sysm, hp, params, elec = _config(args.workload)
     times = []
     for k in range(args.warmup + args.steps):
         t = time.perf_counter()
@@ -332,6 +340,211 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# kernels of one batched call: k_batch_sort, k_batch_lists, k_batch_items
+BATCH_KERNELS_PER_CALL = 3
+
+
+def _batch_flop(systems, hp, elec, n_cand):
+    """Algorithmic FP32 flop of one batched call (per (atom, candidate) counts).
+
+    Neighbour counts are the density estimates 4/3 pi r_c^3 rho of each structure.
+    Per (atom, candidate): descriptor contractions 2 S (K_R N_R + K_A N_A N_lm),
+    network 2 (N_neu N_des) x 3 (forward, dU/dD, dq/dD), radial backward 24 per pair,
+    angular backward 840 per pair, real space 8 per pair, Ewald 14 per half-space k.
+    """
+    S = hp.n_species
+    total = 0.0
+    for sy in systems:
+        vol = float(np.prod(np.diag(sy.box)))
+        rho = sy.n_atoms / vol
+        n_r = 4.0 / 3.0 * math.pi * hp.rc_radial ** 3 * rho
+        n_a = 4.0 / 3.0 * math.pi * hp.rc_angular ** 3 * rho
+        nk = _ewald_kcount(sy.box, elec.kmax)
+        per = (2 * S * (hp.basis_radial * hp.n_radial + hp.basis_angular * hp.n_angular * 24)
+               + 6 * hp.n_neurons * hp.n_des + 24 * n_r + 840 * n_a + 8 * n_r + 14 * nk)
+        total += sy.n_atoms * n_cand * per
+    return total
+
+
+def run_batch(args):
+    """Batched form: every (candidate, structure) pair of the LLZO batch in one persistent launch."""
+    import torch
+
+    from paper_2601_19034_gb300.qnep import QNEP, QNEPBatch, stack_structures
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems, hp, params, elec = _config("llzo_batch")
+    if args.structures:
+        systems = systems[:args.structures]
+    if args.candidates:
+        params = params[:args.candidates]
+    n_cand = params.shape[0]
+    pos, typ, off, boxes = stack_structures(systems)
+    n_total = int(off[-1])
+    pos_d, typ_d = torch.tensor(pos, device=dev), torch.tensor(typ, device=dev)
+    b = QNEPBatch(hp, params, elec)
+    out = b.compute(pos_d, typ_d, off, boxes)          # lists sized, status checked
+    tune_ms = b.autotune(pos_d, typ_d, off, boxes, reps=2, out=out)
+    warps, order = b.config()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            graph.replay()
+    torch.cuda.synchronize()
+    peaks, peak_kind = _peaks()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                graph.replay()
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    ms_per_step = float(sum(step_ms)) / args.steps
+    evals = n_total * n_cand
+    value = world * evals / (ms_per_step * 1e-3)
+    status = b.sync_status()
+
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    flop = _batch_flop(systems, hp, elec, n_cand)
+
+    # plain FP32 single-structure path on the same structures (candidate 0; one call per structure)
+    single = QNEP(hp, params[0], elec)
+    single_ms = 0.0
+    for sy in systems[:64]:
+        p1, t1 = torch.tensor(sy.positions, device=dev), torch.tensor(sy.types, device=dev)
+        o1 = single.compute(p1, t1, sy.box, bec=False, virial=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(3):
+            single.compute_into(p1, t1, sy.box, o1)
+        ev1.record()
+        ev1.synchronize()
+        single_ms += ev0.elapsed_time(ev1) / 3
+    n64 = int(sum(sy.n_atoms for sy in systems[:64]))
+    plain_value = n64 / (single_ms * 1e-3)
+    single.close()
+
+    # end to end: positions / types from pinned host memory, energies back, through the public API
+    pos_h = torch.tensor(pos).pin_memory()
+    typ_h = torch.tensor(typ).pin_memory()
+    e_h = torch.empty(n_cand, len(systems), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + min(args.steps, 10)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with torch.cuda.stream(stream):
+            pos_d.copy_(pos_h, non_blocking=True)
+            typ_d.copy_(typ_h, non_blocking=True)
+            b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+            e_h.copy_(out["energy"], non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    line = None
+    if rank == 0:
+        achieved = flop / (ms_per_step * 1e-3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["llzo_batch"], "structures": len(systems), "candidates": n_cand,
+                       "atoms": n_total, "atom_evaluations_per_step": evals,
+                       "l2": "flushed between steps (512 MB write); working set > L2",
+                       "launch": "CUDA graph replay of one qnep_batch_compute (pre-pass + persistent item kernel)",
+                       "autotuned": {"warps": warps, "order": order, "ms": tune_ms},
+                       "parallelism": "replicas" if world > 1 else "single GPU", "wall_s": wall},
+            "roofline": {"kernel": "k_batch_items (+ pre-pass, whole call)", "bound": "alu", "achieved": achieved,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "ms": ms_per_step,
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+                         "work": f"{flop:.4g} algorithmic flop per call"},
+            "plain_fp32": {"value": plain_value, "unit": UNIT,
+                           "what": "single-structure qnep_compute, forces + charges, one call per structure "
+                                   "(first 64 structures, candidate 0)",
+                           "speedup_batched_vs_plain": value / plain_value},
+            "e2e": {"value": evals / (statistics.median(e2e_ms) * 1e-3) * world, "unit": UNIT,
+                    "h2d_bytes_per_step": n_total * 16, "d2h_bytes_per_step": n_cand * len(systems) * 8,
+                    "ms_per_step": statistics.median(e2e_ms)},
+            "gpu_launches": BATCH_KERNELS_PER_CALL * args.steps,
+            "clocks": clocks,
+            "device_status": status,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline_batch(systems, hp, params, elec)
+    b.close()
+    return line
+
+
+def _cpu_baseline_batch(systems, hp, params, elec):
+    """Oracle on a bounded sample: the two smallest structures under one candidate."""
+    import torch
+
+    from oracle import forcecall
+    cores = torch.get_num_threads()
+    order = np.argsort([sy.n_atoms for sy in systems])[:2]
+    t = time.perf_counter()
+    atoms = 0
+    for s_ in order:
+        sy = systems[s_]
+        forcecall.force_call(sy.positions.astype(np.float64), sy.box, sy.types, hp, params[0], elec,
+                             want_bec=False)
+        atoms += sy.n_atoms
+    dt = time.perf_counter() - t
+    return {"value": atoms / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{atoms} atom-evaluations: the 2 smallest structures x 1 candidate (FP64 oracle, "
+                      f"torch CPU threads={cores})"}
+
+
+def _reference_batch(args, world, cores):
+    """Oracle steps on the batch workload: each step one (smallest structure, candidate) pair."""
+    from oracle import forcecall
+    systems, hp, params, elec = _config("llzo_batch")
+    small = [i for i in np.argsort([sy.n_atoms for sy in systems])]
+    times, atoms = [], 0
+    for k in range(args.warmup + args.steps):
+        sy = systems[small[k % 8]]
+        t = time.perf_counter()
+        forcecall.force_call(sy.positions.astype(np.float64), sy.box, sy.types, hp, params[k % params.shape[0]],
+                             elec, want_bec=False)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+            atoms += sy.n_atoms
+    total = sum(times)
+    value = atoms / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS["llzo_batch"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step one (structure, candidate) pair of the batch, the 8 smallest "
+                                       "structures in turn"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,10 +553,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="batio3", choices=sorted(WORKLOADS))
+    ap.add_argument("--structures", type=int, default=0, help="llzo_batch: first N structures only (profiling)")
+    ap.add_argument("--candidates", type=int, default=0, help="llzo_batch: first C candidates only (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "llzo_batch":
+        line = run_batch(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line))
 

@@ -252,8 +252,9 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     const size_t nm = (size_t)std::max(b->nmax, 1), nk = (size_t)std::max(b->nk_max, 8);
     BatchScratch& sc = b->sc;
     const size_t sA = nm * NANG * CG, sD = nm * 2 * NDES * CG, sN = nm * CG, sK = nk * CG;
-    // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2)
-    const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 64;
+    const size_t sP = (size_t)((nm + 511) / 512) * sK;   // partial structure factors per 512 atoms
+    // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2), skp (2)
+    const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 2 * sP + 64;
     const size_t bytes = per * sizeof(float) * (size_t)slots;
     if (bytes > b->slot_bytes_alloc || !b->scratch) {
         CKB(cudaStreamSynchronize(st));
@@ -283,6 +284,8 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     sc.fr = reinterpret_cast<float4*>(take(4 * sN * slots));
     sc.fsum = reinterpret_cast<float4*>(take(4 * sN * slots));
     sc.sk = reinterpret_cast<float2*>(take(2 * sK * slots));
+    sc.stride_p = sP;
+    sc.skp = reinterpret_cast<float2*>(take(2 * sP * slots));
     b->slots_alloc = slots;
     return QNEP_OK;
 }

@@ -49,7 +49,7 @@ constexpr int PR_S = PR_A + MAX_SPECIES * NA * KA * CG;  // descriptor scaler [N
 constexpr int PARAM_FLOATS = PR_S + NDES * CG;
 constexpr int QT = 64;                         // atoms per charge tile of the S(k) phase
 constexpr int FLUSH_TILES = 8;                 // FP32 partial sums cover 512 atoms
-constexpr int ACCD = CG * 33 * 2;              // FP64 S(k) accumulators per warp [CG][33][2]
+constexpr int KW = 64;                         // wave vectors per staged window of the field pass
 constexpr int NSUMS = 6;                       // per-candidate FP64 sums
 
 static_assert(WBA % 4 == 0 && WARP_FLOATS % 4 == 0 && PARAM_FLOATS % 4 == 0, "float4 alignment");
@@ -261,12 +261,12 @@ __device__ __forceinline__ void block_sum(double v, double* red, double* dst) {
     __syncthreads();
 }
 
-// Forward of sorted atom m (species ti) for the 32 candidates of the group.
-__device__ __forceinline__ void forward_atom(const BatchArgs& a, const BatchStruct& bs, int m, int ti,
-                                             const float* __restrict__ prm, const float* __restrict__ pg,
-                                             float* __restrict__ wb, float* __restrict__ A,
-                                             float* __restrict__ duq, float2* __restrict__ uq, double& su,
-                                             double& sq) {
+// Descriptor of sorted atom m for the 32 candidates of the group: A_{n,lm} to A, the
+// scaled descriptor to rows 0..NDES-1 of the atom's duq block (replaced by dU/dD in the
+// network pass).
+__device__ __forceinline__ void descriptor_atom(const BatchArgs& a, const BatchStruct& bs, int m,
+                                                const float* __restrict__ prm, float* __restrict__ wb,
+                                                float* __restrict__ A, float* __restrict__ duq) {
     const int lane = threadIdx.x & 31;
     const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
     const Geom& g = bs.g;
@@ -423,44 +423,98 @@ __device__ __forceinline__ void forward_atom(const BatchArgs& a, const BatchStru
 #pragma unroll
     for (int v = 0; v < NDES; ++v) d[v] *= prm[PR_S + v * CG + lane];
 
-    // network of species ti: h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q
-    const float* W = pg + (size_t)(a.lay.mlp + ti * a.lay.mlp_stride) * CG + lane;
-    float ge[NNEU], gq[NNEU];
-    float ue = 0.f, uqv = 0.f;
+    float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+#pragma unroll
+    for (int v = 0; v < NDES; ++v) dd[v * CG] = d[v];
+    __syncwarp();   // shared rows are reused by the warp's next atom
+}
+
+// Network of species t_i for two atoms (m1 < 0: one) and the 32 candidates, weights staged
+// in shared memory: net = [W0 (NNEU x NDES) | b0 | w1E | w1q | b1E | b1q | scaler (NDES)][CG].
+// h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q (Eq. U_i, Sec. II.B); writes
+// dU/dD and dq/dD (scaled) over D, and (U, q).
+constexpr int NET_SCALER = ParamLayout::BLOCK;
+constexpr int NET_FLOATS = (ParamLayout::BLOCK + NDES) * CG;
+
+__device__ __forceinline__ void network_pair(const float* __restrict__ net, int m0, int m1,
+                                             float* __restrict__ duq, float2* __restrict__ uq, double& su,
+                                             double& sq) {
+    const int lane = threadIdx.x & 31;
+    const bool two = m1 >= 0;
+    float* D0 = duq + (size_t)m0 * 2 * NDES * CG + lane;
+    float* D1 = duq + (size_t)(two ? m1 : m0) * 2 * NDES * CG + lane;
+    const float* nl = net + lane;
+    float d0[NDES], d1[NDES];
+#pragma unroll
+    for (int v = 0; v < NDES; ++v) {
+        d0[v] = D0[v * CG];
+        d1[v] = D1[v * CG];
+    }
+    float ge0[NNEU], gq0[NNEU], ge1[NNEU], gq1[NNEU];
+    float ue0 = 0.f, uq0 = 0.f, ue1 = 0.f, uq1 = 0.f;
 #pragma unroll
     for (int mu = 0; mu < NNEU; ++mu) {
-        float pre = -__ldg(&W[(ParamLayout::B0 + mu) * CG]);
+        float p0 = -nl[(ParamLayout::B0 + mu) * CG], p1 = p0;
 #pragma unroll
-        for (int v = 0; v < NDES; ++v) pre = fmaf(__ldg(&W[(ParamLayout::W0 + mu * NDES + v) * CG]), d[v], pre);
-        const float hh = tanhf(pre);
-        const float we = __ldg(&W[(ParamLayout::W1E + mu) * CG]), wq = __ldg(&W[(ParamLayout::W1Q + mu) * CG]);
-        ue = fmaf(we, hh, ue);
-        uqv = fmaf(wq, hh, uqv);
-        const float dh = 1.f - hh * hh;
-        ge[mu] = we * dh;
-        gq[mu] = wq * dh;
+        for (int v = 0; v < NDES; ++v) {
+            const float w = nl[(ParamLayout::W0 + mu * NDES + v) * CG];
+            p0 = fmaf(w, d0[v], p0);
+            p1 = fmaf(w, d1[v], p1);
+        }
+        const float h0 = tanhf(p0), h1 = tanhf(p1);
+        const float we = nl[(ParamLayout::W1E + mu) * CG], wq = nl[(ParamLayout::W1Q + mu) * CG];
+        ue0 = fmaf(we, h0, ue0);
+        uq0 = fmaf(wq, h0, uq0);
+        ue1 = fmaf(we, h1, ue1);
+        uq1 = fmaf(wq, h1, uq1);
+        const float dh0 = 1.f - h0 * h0, dh1 = 1.f - h1 * h1;
+        ge0[mu] = we * dh0;
+        gq0[mu] = wq * dh0;
+        ge1[mu] = we * dh1;
+        gq1[mu] = wq * dh1;
     }
-    const float U = ue - __ldg(&W[ParamLayout::B1E * CG]);
-    const float Q = uqv - __ldg(&W[ParamLayout::B1Q * CG]);
-    // dU/dD_v = scaler_v sum_mu ge_mu W0[mu][v] (and dq/dD), one output pair at a time
-    float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+    const float b1e = nl[ParamLayout::B1E * CG], b1q = nl[ParamLayout::B1Q * CG];
 #pragma unroll 2
     for (int v = 0; v < NDES; ++v) {
-        float du = 0.f, dq = 0.f;
+        float du0 = 0.f, dq0 = 0.f, du1 = 0.f, dq1 = 0.f;
 #pragma unroll
         for (int mu = 0; mu < NNEU; ++mu) {
-            const float w = __ldg(&W[(ParamLayout::W0 + mu * NDES + v) * CG]);
-            du = fmaf(ge[mu], w, du);
-            dq = fmaf(gq[mu], w, dq);
+            const float w = nl[(ParamLayout::W0 + mu * NDES + v) * CG];
+            du0 = fmaf(ge0[mu], w, du0);
+            dq0 = fmaf(gq0[mu], w, dq0);
+            du1 = fmaf(ge1[mu], w, du1);
+            dq1 = fmaf(gq1[mu], w, dq1);
         }
-        const float sv = prm[PR_S + v * CG + lane];
-        dd[v * CG] = du * sv;
-        dd[(NDES + v) * CG] = dq * sv;
+        const float sv = nl[(NET_SCALER + v) * CG];
+        D0[v * CG] = du0 * sv;
+        D0[(NDES + v) * CG] = dq0 * sv;
+        if (two) {
+            D1[v * CG] = du1 * sv;
+            D1[(NDES + v) * CG] = dq1 * sv;
+        }
     }
-    uq[(size_t)m * CG + lane] = make_float2(U, Q);
-    su += (double)U;
-    sq += (double)Q;
-    __syncwarp();   // shared rows are reused by the warp's next atom
+    const float U0 = ue0 - b1e, Q0 = uq0 - b1q;
+    uq[(size_t)m0 * CG + lane] = make_float2(U0, Q0);
+    su += (double)U0;
+    sq += (double)Q0;
+    if (two) {
+        const float U1 = ue1 - b1e, Q1 = uq1 - b1q;
+        uq[(size_t)m1 * CG + lane] = make_float2(U1, Q1);
+        su += (double)U1;
+        sq += (double)Q1;
+    }
+}
+
+// Stage the network block of species ti and the scaler (layout of network_pair).
+__device__ __forceinline__ void stage_network(const float* __restrict__ pg, const ParamLayout& lay, int ti,
+                                              float* __restrict__ net) {
+    const int tot = NET_FLOATS;
+    const float* src = pg + (size_t)(lay.mlp + ti * lay.mlp_stride) * CG;
+    const float* scl = pg + (size_t)lay.scaler * CG;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int p = idx >> 5;
+        net[idx] = p < ParamLayout::BLOCK ? __ldg(&src[idx]) : __ldg(&scl[idx - ParamLayout::BLOCK * CG]);
+    }
 }
 
 // Backward of sorted atom m (species ti): partial forces of every list entry.
@@ -674,6 +728,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     float4* fr = a.sc.fr + slot * a.sc.stride_n;
     float4* fsum = a.sc.fsum + slot * a.sc.stride_n;
     float2* sk = a.sc.sk + slot * a.sc.stride_k;
+    float2* skp = a.sc.skp + slot * a.sc.stride_p;
     const int nmax = (int)(a.sc.stride_n / CG);
     const float selfc = a.mode == 1 ? -2.f * KE * a.alpha * 0.564189583547756287f : 0.f;
 
@@ -691,7 +746,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         const int* so = a.spec_off + item.x * (MAX_SPECIES + 1);
         for (int i = threadIdx.x; i < n * CG; i += NW * 32) fsum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-        // 1 forward, one species block at a time (its parameters staged in shared memory)
+        // 1 forward, one species block at a time: descriptor with c^R, c^A staged, then the
+        // network with its weights staged (two atoms per weight load)
         double su = 0.0, sq = 0.0;
         for (int ti = 0; ti < S; ++ti) {
             const int p0 = so[ti], p1 = so[ti + 1];
@@ -700,8 +756,12 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             stage_params(pg, a.lay, ti, un);
             __syncthreads();
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
-            for (int p = p0 + warp; p < p1; p += NW)
-                forward_atom(a, bs, a.order[off + p], ti, un, pg, wb, A, duq, uq, su, sq);
+            for (int p = p0 + warp; p < p1; p += NW) descriptor_atom(a, bs, a.order[off + p], un, wb, A, duq);
+            __syncthreads();
+            stage_network(pg, a.lay, ti, un);
+            __syncthreads();
+            for (int p = p0 + 2 * warp; p < p1; p += 2 * NW)
+                network_pair(un, a.order[off + p], p + 1 < p1 ? a.order[off + p + 1] : -1, duq, uq, su, sq);
         }
         block_sum<NW>(su, red, sums + 0 * CG);
         block_sum<NW>(sq, red, sums + 4 * CG);
@@ -716,20 +776,26 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         for (int i = threadIdx.x; i < n * CG; i += NW * 32) qcs[i] = uq[i].y + cst[i & 31];
         __syncthreads();
 
-        // 3 structure factor: lanes over 32 wave vectors (4 chunks of 8), FP64 flushes
+        // 3 structure factor: lanes over 32 wave vectors (4 chunks of 8); the charges and phase
+        // rows of each 64-atom tile are staged in shared memory; FP32 partial sums over 512
+        // atoms go to the slot's partial buffer and are added in FP64 (lane = candidate)
         const BatchKTab kt = a.kt[bs.ktab];
         const float2* phb = a.phase + (size_t)off * a.nph_stride;
+        const int nkp = 8 * kt.nchunk;
         double ek = 0.0;
         {
-            float* qt = un;
-            double* accd = reinterpret_cast<double*>(un + QT * CG) + warp * ACCD;
+            float* qt = un;                                          // [QT][CG]
+            float2* pt2 = reinterpret_cast<float2*>(un + QT * CG);   // [QT][nph]
+            const int nph = kt.nph;
             const int ntask = (kt.nchunk + 3) >> 2;
+            const int nfl = (n + QT * FLUSH_TILES - 1) / (QT * FLUSH_TILES);
             for (int tb = 0; tb < ntask; tb += NW) {
                 const int task = tb + warp;
                 const bool act = task < ntask;
                 const int h = task * 4 + (lane >> 3), t = lane & 7;
+                const bool kval = act && h < kt.nchunk;
                 int e1 = 0, e2 = kt.yoff, e3 = kt.zoff;
-                if (act && h < kt.nchunk) {
+                if (kval) {
                     const int4 ci = __ldg(&a.chunk[kt.chunk_off + h]);
                     e1 = ci.x;
                     e2 = kt.yoff + ci.y + kt.n2max;
@@ -741,18 +807,20 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     sr[c] = 0.f;
                     si[c] = 0.f;
                 }
-                if (act)
-                    for (int i = lane; i < ACCD; i += 32) accd[i] = 0.0;
-                int tiles = 0;
+                int tiles = 0, fl = 0;
                 for (int j0 = 0; j0 < n; j0 += QT) {
                     const int cnt = min(QT, n - j0);
                     __syncthreads();
                     for (int i = threadIdx.x; i < cnt * CG; i += NW * 32) qt[i] = qcs[(size_t)j0 * CG + i];
+                    for (int i = threadIdx.x; i < cnt * nph; i += NW * 32) {
+                        const int jj = i / nph, e = i - jj * nph;
+                        pt2[i] = __ldg(&phb[(size_t)(j0 + jj) * a.nph_stride + e]);
+                    }
                     __syncthreads();
                     if (act) {
                         for (int jj = 0; jj < cnt; ++jj) {
-                            const float2* row = phb + (size_t)(j0 + jj) * a.nph_stride;
-                            const float2 e = cmul(cmul(__ldg(&row[e1]), __ldg(&row[e2])), __ldg(&row[e3]));
+                            const float2* row = pt2 + jj * nph;
+                            const float2 e = cmul(cmul(row[e1], row[e2]), row[e3]);
                             const float4* q4 = reinterpret_cast<const float4*>(qt + jj * CG);
 #pragma unroll
                             for (int c4 = 0; c4 < CG / 4; ++c4) {
@@ -769,27 +837,35 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         }
                         if (++tiles == FLUSH_TILES || j0 + QT >= n) {
                             tiles = 0;
+                            if (kval) {
+                                float4* dst = reinterpret_cast<float4*>(skp + ((size_t)fl * nkp + 8 * h + t) * CG);
+#pragma unroll
+                                for (int c = 0; c < CG; c += 2) dst[c >> 1] = make_float4(sr[c], si[c], sr[c + 1], si[c + 1]);
+                            }
 #pragma unroll
                             for (int c = 0; c < CG; ++c) {
-                                double* p = accd + (c * 33 + lane) * 2;
-                                p[0] += (double)sr[c];
-                                p[1] += (double)si[c];
                                 sr[c] = 0.f;
                                 si[c] = 0.f;
                             }
+                            ++fl;
                         }
                     }
                 }
                 if (act) {
                     __syncwarp();
-                    // lane = candidate: U^k += (w/2)|S|^2 and the FP32 copy w S, w = 4 k_e G
+                    // lane = candidate: S in FP64 over the partial sums, U^k += (w/2)|S|^2 and the
+                    // FP32 copy C = w S, w = 4 k_e G(k)
                     for (int kk = 0; kk < 32; ++kk) {
                         const int hk = task * 4 + (kk >> 3);
                         if (hk >= kt.nchunk) break;
                         const int kl = 8 * hk + (kk & 7);
                         const float w = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]).w;
-                        const double* p = accd + (lane * 33 + kk) * 2;
-                        const double Sr = p[0], Si = p[1];
+                        double Sr = 0.0, Si = 0.0;
+                        for (int f = 0; f < nfl; ++f) {
+                            const float2 v = skp[((size_t)f * nkp + kl) * CG + lane];
+                            Sr += (double)v.x;
+                            Si += (double)v.y;
+                        }
                         ek += 0.5 * (double)w * (Sr * Sr + Si * Si);
                         sk[(size_t)kl * CG + lane] = make_float2((float)((double)w * Sr), (float)((double)w * Si));
                     }
@@ -798,16 +874,26 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         }
         __syncthreads();
 
-        // 4a k-space potential and field: lanes over atoms, 16 candidates per pass
+        // 4a k-space potential and field: lanes over atoms (32 per warp task), 16 candidates per
+        // pass; C(k), the wave vectors and the chunk list staged in windows of KW wave vectors
         {
-            float2* ph = reinterpret_cast<float2*>(un) + (size_t)warp * kt.nph * 32;
-            for (int task = warp; task * 32 < n; task += NW) {
+            const int nph = kt.nph;
+            float2* ph = reinterpret_cast<float2*>(un) + (size_t)warp * nph * 32;   // [nph][32 atoms]
+            float2* sw = reinterpret_cast<float2*>(un) + (size_t)NW * nph * 32;     // [KW][CG]
+            float4* kw = reinterpret_cast<float4*>(sw + KW * CG);                   // [KW]
+            int4* cw = reinterpret_cast<int4*>(kw + KW);                             // [KW / 8]
+            const int ntask = (n + 31) >> 5;
+            for (int r0 = 0; r0 < ntask; r0 += NW) {
+                const int task = r0 + warp;
+                const bool act = task < ntask;
                 const int j = task * 32 + lane;
-                const int cnt = min(32, n - task * 32);
-                const float2* src = phb + (size_t)task * 32 * a.nph_stride;
-                for (int idx = lane; idx < cnt * kt.nph; idx += 32) {
-                    const int jj = idx / kt.nph, e = idx - jj * kt.nph;
-                    ph[e * 32 + jj] = src[(size_t)jj * a.nph_stride + e];
+                if (act) {
+                    const int cnt = min(32, n - task * 32);
+                    const float2* src = phb + (size_t)task * 32 * a.nph_stride;
+                    for (int idx = lane; idx < cnt * nph; idx += 32) {
+                        const int jj = idx / nph, e = idx - jj * nph;
+                        ph[e * 32 + jj] = __ldg(&src[(size_t)jj * a.nph_stride + e]);
+                    }
                 }
                 __syncwarp();
                 for (int c0 = 0; c0 < CG; c0 += 16) {
@@ -822,42 +908,56 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     }
                     float pkx = 0.f, pky = 0.f;
                     int pn1 = -(1 << 30), pn2 = 0;
-                    for (int h = 0; h < kt.nchunk; ++h) {
-                        const int4 ci = __ldg(&a.chunk[kt.chunk_off + h]);
-                        const float4* kv = a.kvec + 8 * (size_t)(kt.chunk_off + h);
-                        if (ci.x != pn1 || ci.y != pn2) {
-                            // new column (n1, n2): fold the column's Im sums into E_x, E_y
-#pragma unroll
-                            for (int c = 0; c < 16; ++c) {
-                                ex[c] = fmaf(pkx, tt[c], ex[c]);
-                                ey[c] = fmaf(pky, tt[c], ey[c]);
-                                tt[c] = 0.f;
-                            }
-                            pn1 = ci.x;
-                            pn2 = ci.y;
-                            const float4 k0 = __ldg(&kv[0]);
-                            pkx = k0.x;
-                            pky = k0.y;
+                    for (int k0 = 0; k0 < nkp; k0 += KW) {
+                        const int kc = min(KW, nkp - k0);
+                        __syncthreads();
+                        {
+                            const float4* s4 = reinterpret_cast<const float4*>(sk + (size_t)k0 * CG);
+                            float4* d4 = reinterpret_cast<float4*>(sw);
+                            for (int i = threadIdx.x; i < kc * CG / 2; i += NW * 32) d4[i] = s4[i];
+                            for (int i = threadIdx.x; i < kc; i += NW * 32)
+                                kw[i] = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + k0 + i]);
+                            for (int i = threadIdx.x; i < (kc >> 3); i += NW * 32)
+                                cw[i] = __ldg(&a.chunk[kt.chunk_off + (k0 >> 3) + i]);
                         }
-                        const float2 xy = cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
-                        for (int t = 0; t < 8; ++t) {
-                            const float4 k4 = __ldg(&kv[t]);
-                            if (k4.w == 0.f) continue;
-                            const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
-                            const float4* s4 = reinterpret_cast<const float4*>(sk + (size_t)(8 * h + t) * CG + c0);
+                        __syncthreads();
+                        if (!act) continue;
+                        for (int hh = 0; hh < (kc >> 3); ++hh) {
+                            const int4 ci = cw[hh];
+                            if (ci.x != pn1 || ci.y != pn2) {
+                                // new column (n1, n2): fold the column's Im sums into E_x, E_y
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const float4 v = s4[u];
-                                // z = C conj(e) for the two candidates of v
-                                float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
-                                fphi[2 * u] += zr;
-                                tt[2 * u] += zi;
-                                ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
-                                zr = fmaf(v.z, e.x, v.w * e.y);
-                                zi = fmaf(v.w, e.x, -v.z * e.y);
-                                fphi[2 * u + 1] += zr;
-                                tt[2 * u + 1] += zi;
-                                ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                                for (int c = 0; c < 16; ++c) {
+                                    ex[c] = fmaf(pkx, tt[c], ex[c]);
+                                    ey[c] = fmaf(pky, tt[c], ey[c]);
+                                    tt[c] = 0.f;
+                                }
+                                pn1 = ci.x;
+                                pn2 = ci.y;
+                                const float4 k0v = kw[hh * 8];
+                                pkx = k0v.x;
+                                pky = k0v.y;
+                            }
+                            const float2 xy = cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
+                            for (int t = 0; t < 8; ++t) {
+                                const float4 k4 = kw[hh * 8 + t];
+                                if (k4.w == 0.f) continue;
+                                const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
+                                const float4* s4 = reinterpret_cast<const float4*>(sw + (hh * 8 + t) * CG + c0);
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const float4 v = s4[u];
+                                    // z = C conj(e) for the two candidates of v
+                                    float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
+                                    fphi[2 * u] += zr;
+                                    tt[2 * u] += zi;
+                                    ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
+                                    zr = fmaf(v.z, e.x, v.w * e.y);
+                                    zi = fmaf(v.w, e.x, -v.z * e.y);
+                                    fphi[2 * u + 1] += zr;
+                                    tt[2 * u + 1] += zi;
+                                    ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                                }
                             }
                         }
                     }
@@ -866,7 +966,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         ex[c] = fmaf(pkx, tt[c], ex[c]);
                         ey[c] = fmaf(pky, tt[c], ey[c]);
                     }
-                    if (j < n) {
+                    if (act && j < n) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
                             fk[(size_t)(c0 + c) * nmax + j] = make_float4(fphi[c], ex[c], ey[c], ez[c]);
@@ -993,9 +1093,11 @@ template <int NW>
 size_t item_smem(int nph_max) {
     const size_t head = sizeof(double) * (NW + NSUMS) * CG + sizeof(float) * 4 * CG;
     const size_t p1 = sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
-    const size_t p3 = sizeof(float) * (size_t)QT * CG + sizeof(double) * (size_t)NW * ACCD;
-    const size_t p4 = sizeof(float2) * (size_t)NW * nph_max * 32;
-    return head + std::max(p1, std::max(p3, p4));
+    const size_t p1b = sizeof(float) * (size_t)NET_FLOATS;
+    const size_t p3 = sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max;
+    const size_t p4 = sizeof(float2) * ((size_t)NW * nph_max * 32 + (size_t)KW * CG) + sizeof(float4) * KW +
+                      sizeof(int4) * (KW / 8);
+    return head + std::max(std::max(p1, p1b), std::max(p3, p4));
 }
 
 }  // namespace

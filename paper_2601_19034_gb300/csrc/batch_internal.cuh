@@ -54,7 +54,8 @@ struct BatchScratch {
     float4* fr;      // [nmax][CG] (phi^r, F^r) real space
     float4* fsum;    // [nmax][CG] force accumulators (xyz, pad)
     float2* sk;      // [nk_max][CG] 4 k_e G(k) S(k) (FP32)
-    size_t stride_A, stride_duq, stride_n, stride_k;   // per-slot strides (elements)
+    float2* skp;     // [n_flush][nk_max][CG] FP32 partial structure factors (512-atom blocks)
+    size_t stride_A, stride_duq, stride_n, stride_k, stride_p;   // per-slot strides (elements)
 };
 
 struct BatchArgs {
