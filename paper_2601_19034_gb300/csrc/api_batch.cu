@@ -42,7 +42,7 @@ struct qnep_batch {
     // pre-pass outputs (element counts allocated)
     struct {
         size_t spos4 = 0, sidx = 0, order = 0, spec = 0, cells = 0, list = 0, ang = 0, cnt_list = 0, cnt_ang = 0,
-               phase = 0;
+               phase = 0, geo_rad = 0, geo_ang = 0, bsum = 0;
     } alloc;
     float4* spos4 = nullptr;
     int* sidx = nullptr;
@@ -54,6 +54,9 @@ struct qnep_batch {
     int* nbr_ang = nullptr;
     int* cnt_ang = nullptr;
     float2* phase = nullptr;
+    float* geo_rad = nullptr;
+    float* geo_ang = nullptr;
+    float* bsum = nullptr;
     // per-slot scratch
     size_t slot_bytes_alloc = 0;
     int slots_alloc = 0;
@@ -241,6 +244,9 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(regrow(&b->cnt_list, N * S, &b->alloc.cnt_list));
     CKB(regrow(&b->cnt_ang, N * S, &b->alloc.cnt_ang));
     CKB(regrow(&b->phase, N * (size_t)nph_max, &b->alloc.phase));
+    CKB(regrow(&b->geo_rad, N * (size_t)cl * BATCH_GR, &b->alloc.geo_rad));
+    CKB(regrow(&b->geo_ang, N * (size_t)ca * BATCH_GA, &b->alloc.geo_ang));
+    CKB(regrow(&b->bsum, N * (size_t)batch_bstride(b->hp.n_species), &b->alloc.bsum));
     b->h_off.assign(off, off + n_struct + 1);
     b->h_box.assign(boxes, boxes + 9 * (size_t)n_struct);
     b->have_desc = true;
@@ -413,7 +419,8 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
     launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
                       b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
-                      b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->d_status, st);
+                      b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->geo_rad, b->geo_ang, b->bsum,
+                      batch_bstride(b->hp.n_species), (float)b->es.alpha, b->d_status, st);
     BatchArgs a{};
     a.spos4 = b->spos4;
     a.sidx = b->sidx;
@@ -427,6 +434,10 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.cap_a = b->cap_a;
     a.phase = b->phase;
     a.nph_stride = b->nph_max;
+    a.geo_rad = b->geo_rad;
+    a.geo_ang = b->geo_ang;
+    a.bsum = b->bsum;
+    a.bstride = batch_bstride(b->hp.n_species);
     a.st = b->d_st;
     a.kt = b->d_kt;
     a.chunk = b->d_chunk;
@@ -527,6 +538,7 @@ void qnep_batch_destroy(qnep_batch* b) {
     void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,     b->d_items_lpt,
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
+                    b->geo_rad,   b->geo_ang,  b->bsum,
                     b->d_work,    b->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -3,17 +3,18 @@
 //
 // Pre-pass (candidate independent, one block per structure):
 //   k_batch_sort   wrap, bin into cells, stable cell order, species order
-//   k_batch_lists  neighbour lists (grouped by neighbour species) and the Ewald
-//                  phase-factor rows of every atom
+//   k_batch_lists  neighbour lists (grouped by neighbour species); per entry the pair
+//                  geometry rows (basis values and derivatives, harmonics, unit vector,
+//                  real-space kernel); per atom the basis sums
+//                  B^R[t_j][k] = sum_j f_k(r_ij),  B^A[t_j][k][lm] = sum_j f_k(r_ij) Y_lm(u_ij);
+//                  the Ewald phase-factor rows of every atom
 // Item kernel (persistent, items taken largest first), per (structure, group):
-//   1 forward    per species block: candidate-independent basis sums per atom
-//                  B^R[t_j][k] = sum_j f_k(r_ij),  B^A[t_j][k][lm] = sum_j f_k(r_ij) Y_lm(u_ij)
-//                then per lane: D^R_n = sum c^R[t_i][t_j][n][k] B^R,
-//                A_{n,lm} = sum c^A[t_i][t_j][n][k] B^A (Sec. II.A), descriptor,
-//                network U_i, q_i and dU/dD, dq/dD (Eq. U_i, Sec. II.B)
+//   1 forward    per species block, lane = candidate: D^R_n = sum c^R[t_i][t_j][n][k] B^R,
+//                A_{n,lm} = sum c^A[t_i][t_j][n][k] B^A (Sec. II.A), descriptor; then the
+//                network U_i, q_i and dU/dD, dq/dD (Eq. U_i, Sec. II.B), weights staged
 //   2 charges    total-charge correction (block sum, FP64)
-//   3 S(k)       lanes over 32 wave vectors, FP32 terms over 64-atom tiles flushed
-//                to FP64 every 512 atoms; U^k per candidate (FP64)
+//   3 S(k)       lanes over 32 wave vectors, FP32 terms over 512-atom blocks summed in
+//                FP64; U^k per candidate (FP64)
 //   4 fields     lanes over atoms: phi^k_i and the k-space field (Sec. II.C);
 //                lanes over candidates: real-space phi^r_i and F^r_i
 //   5 backward   per species block: lambda = dU/dD + (phi_i - mean phi) dq/dD; radial
@@ -32,14 +33,18 @@ namespace {
 
 constexpr int PREP_THREADS = 256;
 
-// shared-memory rows staged by the lanes of a warp (odd strides: conflict-free row writes)
-constexpr int TAB_R1 = KR;                     // forward radial: f_k
-constexpr int TAB_A1 = KA + NLM;               // forward angular: f_k, Y_lm
-constexpr int TAB_R4 = KR + 4;                 // backward radial: f'_k, u, j
-constexpr int TAB_A4 = 2 * KA + NLM + 5;       // backward angular: f_k, f'_k, Y_lm, u, 1/r, j
-constexpr int TAB_RS = 5;                      // real space: B, B' u, j
-constexpr int WT_FLOATS = 32 * TAB_A4;         // 1504
-constexpr int WBR = WT_FLOATS;                 // B^R [S][KR]
+// Candidate-independent pair geometry, written once per structure by the pre-pass:
+//   radial row  (GR floats per list entry):  f'_k (9) | u (3) | j if r < r_c^R else -1 |
+//                B(r) | B'(r) u (3) | j if r < r_c (real space) else -1 | pad
+//   angular row (GA floats per angular entry): f_k (9) | f'_k (9) | u (3) | 1/r | j | pad | Y_lm (24)
+//   basis sums  (per atom): B^R[t][k] (padded to MAX_SPECIES species) | B^A[t][k][lm]
+// with B(r) = k_e erfc(alpha r) / r.  Rows are copied into shared memory (float4) by the item kernel.
+constexpr int GR = 20, GR_DF = 0, GR_U = 9, GR_JD = 12, GR_B = 13, GR_BU = 14, GR_JR = 17;
+constexpr int GA = 48, GA_F = 0, GA_DF = 9, GA_U = 18, GA_IR = 21, GA_J = 22, GA_Y = 24;
+constexpr int TAB_P = KA + NLM;                // pre-pass staging row: f_k, Y_lm
+// per-warp shared memory of the item kernel
+constexpr int WT_FLOATS = 32 * GA;             // staged rows (32 angular or radial entries)
+constexpr int WBR = WT_FLOATS;                 // B^R [MAX_SPECIES][KR]
 constexpr int WBA = WBR + MAX_SPECIES * KR;    // B^A [S][KA][NLM] (16-byte aligned)
 constexpr int WCUM = WBA + MAX_SPECIES * KA * NLM;   // cumulative species counts (ints)
 constexpr int WARP_FLOATS = WCUM + 16;
@@ -168,33 +173,196 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __rest
     }
 }
 
-// pre-pass 2: neighbour lists and phase rows
+// Candidate-independent geometry of sorted atom m (whole warp): pair rows and basis sums.
+__device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, const Geom& g, float alpha, int m, int n,
+                                              int S, const int* __restrict__ lst, const int* __restrict__ cl,
+                                              const int* __restrict__ lsa, const int* __restrict__ ca,
+                                              float* __restrict__ grad_rows, float* __restrict__ gang_rows,
+                                              float* __restrict__ bs_out, float* __restrict__ tab,
+                                              int* __restrict__ cum) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        int tl = 0, ta = 0;
+        for (int s = 0; s < S; ++s) {
+            cum[s] = tl;
+            cum[8 + s] = ta;
+            tl += cl[(size_t)s * n + m];
+            ta += ca[(size_t)s * n + m];
+        }
+        cum[S] = tl;
+        cum[8 + S] = ta;
+    }
+    __syncwarp();
+    const int tot_l = cum[S], tot_a = cum[8 + S];
+    const float4 pk = sp[m];
+    const float rcr2 = g.rc_radial * g.rc_radial, rcs2 = g.rc_real * g.rc_real;
+    // radial rows and B^R: lanes over entries, then over (t_j, k)
+    float br0 = 0.f, br1 = 0.f;
+    for (int base = 0; base < tot_l; base += 32) {
+        const int e = base + lane;
+        float f[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) f[k] = 0.f;
+        if (e < tot_l) {
+            const int ent = lst[e];
+            float vx, vy, vz;
+            entry_vector(sp, ent, pk, g, vx, vy, vz);
+            const float r2 = vx * vx + vy * vy + vz * vz, r = sqrtf(r2), ir = 1.f / r;
+            float row[GR];
+#pragma unroll
+            for (int q = 0; q < GR; ++q) row[q] = 0.f;
+            row[GR_U] = vx * ir;
+            row[GR_U + 1] = vy * ir;
+            row[GR_U + 2] = vz * ir;
+            row[GR_JD] = __int_as_float(-1);
+            row[GR_JR] = __int_as_float(-1);
+            const int j = entry_index(ent);
+            if (r2 < rcr2) {
+                float df[KR];
+                basis_d<KR>(r, g.rc_radial, f, df);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) row[GR_DF + k] = df[k];
+                row[GR_JD] = __int_as_float(j);
+            }
+            if (r2 < rcs2) {
+                const float ar = alpha * r, ec = erfcf(ar);
+                const float B = KE * ec * ir;
+                // dB/dr = -k_e (erfc(a r) / r + 2 a / sqrt(pi) exp(-a^2 r^2)) / r
+                const float dB = -KE * (ec * ir + 1.12837916709551257f * alpha * expf(-ar * ar)) * ir;
+                row[GR_B] = B;
+                row[GR_BU] = dB * row[GR_U];
+                row[GR_BU + 1] = dB * row[GR_U + 1];
+                row[GR_BU + 2] = dB * row[GR_U + 2];
+                row[GR_JR] = __int_as_float(j);
+            }
+            float4* o = reinterpret_cast<float4*>(grad_rows + (size_t)e * GR);
+#pragma unroll
+            for (int q = 0; q < GR / 4; ++q) o[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k) tab[lane * KR + k] = f[k];
+        __syncwarp();
+        const int cntc = min(32, tot_l - base);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int idx = lane + 32 * h;
+            if (idx < S * KR) {
+                const int tj = idx / KR, k = idx - tj * KR;
+                const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
+                float x = 0.f;
+                for (int r = lo; r < hi; ++r) x += tab[r * KR + k];
+                if (h == 0) br0 += x;
+                else br1 += x;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane < MAX_SPECIES * KR) bs_out[lane] = lane < S * KR ? br0 : 0.f;
+    if (lane + 32 < MAX_SPECIES * KR) bs_out[lane + 32] = lane + 32 < S * KR ? br1 : 0.f;
+    // angular rows and B^A: lanes over entries, then lane lm accumulates per neighbour species
+    float ba[MAX_SPECIES][KA];
+#pragma unroll
+    for (int t = 0; t < MAX_SPECIES; ++t)
+#pragma unroll
+        for (int k = 0; k < KA; ++k) ba[t][k] = 0.f;
+    for (int base = 0; base < tot_a; base += 32) {
+        const int e = base + lane;
+        if (e < tot_a) {
+            const int ent = lsa[e];
+            float vx, vy, vz;
+            entry_vector(sp, ent, pk, g, vx, vy, vz);
+            const float r = sqrtf(vx * vx + vy * vy + vz * vz), ir = 1.f / r;
+            float row[GA];
+#pragma unroll
+            for (int q = 0; q < GA; ++q) row[q] = 0.f;
+            float f[KA], df[KA], Y[NLM];
+            basis_d<KA>(r, g.rc_angular, f, df);
+            const float ux = vx * ir, uy = vy * ir, uz = vz * ir;
+            harmonics(ux, uy, uz, Y);
+#pragma unroll
+            for (int k = 0; k < KA; ++k) {
+                row[GA_F + k] = f[k];
+                row[GA_DF + k] = df[k];
+                tab[lane * TAB_P + k] = f[k];
+            }
+            row[GA_U] = ux;
+            row[GA_U + 1] = uy;
+            row[GA_U + 2] = uz;
+            row[GA_IR] = ir;
+            row[GA_J] = __int_as_float(entry_index(ent));
+#pragma unroll
+            for (int q = 0; q < NLM; ++q) {
+                row[GA_Y + q] = Y[q];
+                tab[lane * TAB_P + KA + q] = Y[q];
+            }
+            float4* o = reinterpret_cast<float4*>(gang_rows + (size_t)e * GA);
+#pragma unroll
+            for (int q = 0; q < GA / 4; ++q) o[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+        }
+        __syncwarp();
+        const int cntc = min(32, tot_a - base);
+        if (lane < NLM) {
+#pragma unroll
+            for (int t = 0; t < MAX_SPECIES; ++t) {
+                if (t < S) {
+                    const int lo = max(cum[8 + t] - base, 0), hi = min(cum[8 + t + 1] - base, cntc);
+                    for (int r = lo; r < hi; ++r) {
+                        const float* row = tab + r * TAB_P;
+                        const float y = row[KA + lane];
+#pragma unroll
+                        for (int k = 0; k < KA; ++k) ba[t][k] = fmaf(row[k], y, ba[t][k]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (lane < NLM) {
+#pragma unroll
+        for (int t = 0; t < MAX_SPECIES; ++t)
+            if (t < S)
+#pragma unroll
+                for (int k = 0; k < KA; ++k) bs_out[MAX_SPECIES * KR + (t * KA + k) * NLM + lane] = ba[t][k];
+    }
+    __syncwarp();
+}
+
+// pre-pass 2: neighbour lists, pair geometry, basis sums and phase rows
 __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
     int n_species, const BatchStruct* __restrict__ sts, const BatchKTab* __restrict__ kts,
     const int* __restrict__ cell_start_all, const float4* __restrict__ spos4, int cap_l, int cap_a,
     int* __restrict__ nbr_list, int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang,
-    float2* __restrict__ phase, int nph_stride, unsigned int* __restrict__ status) {
+    float2* __restrict__ phase, int nph_stride, float* __restrict__ geo_rad, float* __restrict__ geo_ang,
+    float* __restrict__ bsum, int bstride, float alpha, unsigned int* __restrict__ status) {
     extern __shared__ int psm[];
     const BatchStruct bs = sts[blockIdx.x];
     const int n = bs.n, off = bs.atom_off;
     const Geom g = bs.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int* sl = psm + warp * (2 * cap_l + 2 * cap_a);
+    const int per_warp = 2 * cap_l + 2 * cap_a + 32 * TAB_P + 16;
+    int* sl = psm + warp * per_warp;
     int* slt = sl + cap_l;
     int* sa = slt + cap_l;
     int* sat = sa + cap_a;
+    float* tab = reinterpret_cast<float*>(sat + cap_a);
+    int* cum = reinterpret_cast<int*>(tab + 32 * TAB_P);
     const float4* sp = spos4 + off;
     const int* cs = cell_start_all + bs.cell_off;
+    int* lst_s = nbr_list + (size_t)off * cap_l;
+    int* lsa_s = nbr_ang + (size_t)off * cap_a;
+    int* cl_s = cnt_list + (size_t)off * n_species;
+    int* ca_s = cnt_ang + (size_t)off * n_species;
     for (int m = warp; m < n; m += nw) {
         const float4 pk = sp[m];
         int nl = 0, na = 0;
         bool ovf = warp_build_lists(sp, cs, m, pk, g, cap_l, cap_a, sl, slt, sa, sat, nl, na);
-        warp_write_grouped(sl, slt, nl, n_species, n, m, nbr_list + (size_t)off * cap_l, (size_t)cap_l, 1,
-                           cnt_list + (size_t)off * n_species);
-        warp_write_grouped(sa, sat, na, n_species, n, m, nbr_ang + (size_t)off * cap_a, (size_t)cap_a, 1,
-                           cnt_ang + (size_t)off * n_species);
+        warp_write_grouped(sl, slt, nl, n_species, n, m, lst_s, (size_t)cap_l, 1, cl_s);
+        warp_write_grouped(sa, sat, na, n_species, n, m, lsa_s, (size_t)cap_a, 1, ca_s);
         if (ovf && lane == 0) atomicOr(status, 1u);
-        __syncwarp();
+        __syncwarp();   // this warp's list writes are visible to its lanes
+        geometry_atom(sp, g, alpha, m, n, n_species, lst_s + (size_t)m * cap_l, cl_s, lsa_s + (size_t)m * cap_a, ca_s,
+                      geo_rad + (size_t)(off + m) * cap_l * GR, geo_ang + (size_t)(off + m) * cap_a * GA,
+                      bsum + (size_t)(off + m) * bstride, tab, cum);
     }
     const BatchKTab kt = kts[bs.ktab];
     for (int idx = threadIdx.x; idx < n * kt.nph; idx += blockDim.x) {
@@ -268,88 +436,15 @@ __device__ __forceinline__ void descriptor_atom(const BatchArgs& a, const BatchS
                                                 const float* __restrict__ prm, float* __restrict__ wb,
                                                 float* __restrict__ A, float* __restrict__ duq) {
     const int lane = threadIdx.x & 31;
-    const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
-    const Geom& g = bs.g;
-    const float4* sp = a.spos4 + off;
-    const float4 pk = sp[m];
-    float* tab = wb;
+    const int S = a.lay.n_species, off = bs.atom_off;
     float* br = wb + WBR;
     float* ba = wb + WBA;
-    int* cum = reinterpret_cast<int*>(wb + WCUM);
-    species_cum(a, off, n, m, S, cum);
-    for (int t = lane; t < S * KR; t += 32) br[t] = 0.f;
-    for (int t = lane; t < S * KA * NLM; t += 32) ba[t] = 0.f;
-    const int tot_l = cum[S], tot_a = cum[8 + S];
+    {
+        const float4* src = reinterpret_cast<const float4*>(a.bsum + (size_t)(off + m) * a.bstride);
+        float4* dst = reinterpret_cast<float4*>(br);
+        for (int i = lane; i < (a.bstride >> 2); i += 32) dst[i] = __ldg(&src[i]);
+    }
     __syncwarp();
-
-    // candidate-independent radial basis sums: lanes over entries, then over (t_j, k)
-    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
-    const float rcr2 = g.rc_radial * g.rc_radial;
-    for (int base = 0; base < tot_l; base += 32) {
-        const int e = base + lane;
-        float f[KR];
-#pragma unroll
-        for (int k = 0; k < KR; ++k) f[k] = 0.f;
-        if (e < tot_l) {
-            float vx, vy, vz;
-            entry_vector(sp, __ldg(&lst[e]), pk, g, vx, vy, vz);
-            const float r2 = vx * vx + vy * vy + vz * vz;
-            if (r2 < rcr2) basis<KR>(sqrtf(r2), g.rc_radial, f);
-        }
-#pragma unroll
-        for (int k = 0; k < KR; ++k) tab[lane * TAB_R1 + k] = f[k];
-        __syncwarp();
-        const int cntc = min(32, tot_l - base);
-        for (int idx = lane; idx < S * KR; idx += 32) {
-            const int tj = idx / KR, k = idx - tj * KR;
-            const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
-            float s = 0.f;
-            for (int r = lo; r < hi; ++r) s += tab[r * TAB_R1 + k];
-            br[idx] += s;
-        }
-        __syncwarp();
-    }
-    // candidate-independent angular basis sums B^A[t_j][k][lm]: lanes over entries
-    // (f_k, Y_lm to shared), then lane lm accumulates over the entries of each species
-    const int* lsa = a.nbr_ang + (size_t)(off + m) * a.cap_a;
-    for (int base = 0; base < tot_a; base += 32) {
-        const int e = base + lane;
-        if (e < tot_a) {
-            float vx, vy, vz;
-            entry_vector(sp, __ldg(&lsa[e]), pk, g, vx, vy, vz);
-            const float r = sqrtf(vx * vx + vy * vy + vz * vz);
-            float f[KA], Y[NLM];
-            basis<KA>(r, g.rc_angular, f);
-            const float ir = 1.f / r;
-            harmonics(vx * ir, vy * ir, vz * ir, Y);
-            float* row = tab + lane * TAB_A1;
-#pragma unroll
-            for (int k = 0; k < KA; ++k) row[k] = f[k];
-#pragma unroll
-            for (int q = 0; q < NLM; ++q) row[KA + q] = Y[q];
-        }
-        __syncwarp();
-        const int cntc = min(32, tot_a - base);
-        if (lane < NLM) {
-            for (int tj = 0; tj < S; ++tj) {
-                const int lo = max(cum[8 + tj] - base, 0), hi = min(cum[8 + tj + 1] - base, cntc);
-                if (lo >= hi) continue;
-                float b[KA];
-#pragma unroll
-                for (int k = 0; k < KA; ++k) b[k] = 0.f;
-                for (int r = lo; r < hi; ++r) {
-                    const float* row = tab + r * TAB_A1;
-                    const float y = row[KA + lane];
-#pragma unroll
-                    for (int k = 0; k < KA; ++k) b[k] = fmaf(row[k], y, b[k]);
-                }
-                float* dst = ba + tj * KA * NLM + lane;
-#pragma unroll
-                for (int k = 0; k < KA; ++k) dst[k * NLM] += b[k];
-            }
-        }
-        __syncwarp();
-    }
 
     // lane = candidate: contractions with this candidate's c^R, c^A
     float d[NDES];
@@ -526,9 +621,6 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
                                               float selfc, float phibar) {
     const int lane = threadIdx.x & 31;
     const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
-    const Geom& g = bs.g;
-    const float4* sp = a.spos4 + off;
-    const float4 pk = sp[m];
     float* tab = wb;
     int* cum = reinterpret_cast<int*>(wb + WCUM);
     species_cum(a, off, n, m, S, cum);
@@ -544,39 +636,15 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
     float fx = 0.f, fy = 0.f, fz = 0.f;
 
     // radial: F_ij = (sum_k mu_k f'_k(r)) u with mu_k = sum_n lambda_n c^R[t_i][t_j][n][k]
-    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
-    const float rcr2 = g.rc_radial * g.rc_radial;
+    const float4* grows = reinterpret_cast<const float4*>(a.geo_rad + (size_t)(off + m) * a.cap_l * GR);
     for (int base = 0; base < tot_l; base += 32) {
-        const int e = base + lane;
-        float* row = tab + lane * TAB_R4;
-        float df[KR];
-#pragma unroll
-        for (int k = 0; k < KR; ++k) df[k] = 0.f;
-        float ux = 0.f, uy = 0.f, uz = 0.f;
-        int jj = -1;
-        if (e < tot_l) {
-            const int ent = __ldg(&lst[e]);
-            float vx, vy, vz;
-            entry_vector(sp, ent, pk, g, vx, vy, vz);
-            const float r2 = vx * vx + vy * vy + vz * vz;
-            if (r2 < rcr2) {
-                const float r = sqrtf(r2), ir = 1.f / r;
-                float f[KR];
-                basis_d<KR>(r, g.rc_radial, f, df);
-                ux = vx * ir;
-                uy = vy * ir;
-                uz = vz * ir;
-                jj = entry_index(ent);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < KR; ++k) row[k] = df[k];
-        row[KR] = ux;
-        row[KR + 1] = uy;
-        row[KR + 2] = uz;
-        row[KR + 3] = __int_as_float(jj);
-        __syncwarp();
         const int cntc = min(32, tot_l - base);
+        {
+            float4* t4 = reinterpret_cast<float4*>(tab);
+            const float4* s4 = grows + (size_t)base * (GR / 4);
+            for (int i = lane; i < cntc * (GR / 4); i += 32) t4[i] = __ldg(&s4[i]);
+        }
+        __syncwarp();
         for (int tj = 0; tj < S; ++tj) {
             const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
             if (lo >= hi) continue;
@@ -589,13 +657,13 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
                 mu[k] = x;
             }
             for (int r = lo; r < hi; ++r) {
-                const float* rw = tab + r * TAB_R4;
-                const int j = __float_as_int(rw[KR + 3]);
+                const float* rw = tab + r * GR;
+                const int j = __float_as_int(rw[GR_JD]);
                 if (j < 0) continue;
-                float s = 0.f;
+                float sv = 0.f;
 #pragma unroll
-                for (int k = 0; k < KR; ++k) s = fmaf(mu[k], rw[k], s);
-                const float Fx = s * rw[KR], Fy = s * rw[KR + 1], Fz = s * rw[KR + 2];
+                for (int k = 0; k < KR; ++k) sv = fmaf(mu[k], rw[GR_DF + k], sv);
+                const float Fx = sv * rw[GR_U], Fy = sv * rw[GR_U + 1], Fz = sv * rw[GR_U + 2];
                 fx += Fx;
                 fy += Fy;
                 fz += Fz;
@@ -627,31 +695,13 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
         Phi[q][6] = fmaf(l4, 1.5f * (t2[0] - t2[1]), Phi[q][6]);
         Phi[q][7] = fmaf(l4, 6.f * t2[3], Phi[q][7]);
     }
-    const int* lsa = a.nbr_ang + (size_t)(off + m) * a.cap_a;
+    const float4* arows = reinterpret_cast<const float4*>(a.geo_ang + (size_t)(off + m) * a.cap_a * GA);
     for (int base = 0; base < tot_a; base += 32) {
-        const int e = base + lane;
-        if (e < tot_a) {
-            const int ent = __ldg(&lsa[e]);
-            float vx, vy, vz;
-            entry_vector(sp, ent, pk, g, vx, vy, vz);
-            const float r = sqrtf(vx * vx + vy * vy + vz * vz), ir = 1.f / r;
-            float f[KA], df[KA], Y[NLM];
-            basis_d<KA>(r, g.rc_angular, f, df);
-            const float ux = vx * ir, uy = vy * ir, uz = vz * ir;
-            harmonics(ux, uy, uz, Y);
-            float* row = tab + lane * TAB_A4;
-#pragma unroll
-            for (int k = 0; k < KA; ++k) {
-                row[k] = f[k];
-                row[KA + k] = df[k];
-            }
-#pragma unroll
-            for (int q = 0; q < NLM; ++q) row[2 * KA + q] = Y[q];
-            row[2 * KA + NLM] = ux;
-            row[2 * KA + NLM + 1] = uy;
-            row[2 * KA + NLM + 2] = uz;
-            row[2 * KA + NLM + 3] = ir;
-            row[2 * KA + NLM + 4] = __int_as_float(entry_index(ent));
+        {
+            const int cnt = min(32, tot_a - base);
+            float4* t4 = reinterpret_cast<float4*>(tab);
+            const float4* s4 = arows + (size_t)base * (GA / 4);
+            for (int i = lane; i < cnt * (GA / 4); i += 32) t4[i] = __ldg(&s4[i]);
         }
         __syncwarp();
         const int cntc = min(32, tot_a - base);
@@ -659,7 +709,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
             const int lo = max(cum[8 + tj] - base, 0), hi = min(cum[8 + tj + 1] - base, cntc);
             const float* cA = prm + PR_A + tj * NA * KA * CG + lane;
             for (int r = lo; r < hi; ++r) {
-                const float* rw = tab + r * TAB_A4;
+                const float* rw = tab + r * GA;
                 float gn[NA], dgn[NA];
 #pragma unroll
                 for (int q = 0; q < NA; ++q) {
@@ -667,8 +717,8 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
 #pragma unroll
                     for (int k = 0; k < KA; ++k) {
                         const float c = cA[(q * KA + k) * CG];
-                        x = fmaf(c, rw[k], x);
-                        y = fmaf(c, rw[KA + k], y);
+                        x = fmaf(c, rw[GA_F + k], x);
+                        y = fmaf(c, rw[GA_DF + k], y);
                     }
                     gn[q] = x;
                     dgn[q] = y;
@@ -682,13 +732,13 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
                     float pq = 0.f;
 #pragma unroll
                     for (int M = 0; M < NLM; ++M) {
-                        pq = fmaf(Phi[q][M], rw[2 * KA + M], pq);
+                        pq = fmaf(Phi[q][M], rw[GA_Y + M], pq);
                         psi[M] = fmaf(gn[q], Phi[q][M], psi[M]);
                     }
                     rho = fmaf(dgn[q], pq, rho);
                 }
-                const float ux = rw[2 * KA + NLM], uy = rw[2 * KA + NLM + 1], uz = rw[2 * KA + NLM + 2];
-                const float ir = rw[2 * KA + NLM + 3];
+                const float ux = rw[GA_U], uy = rw[GA_U + 1], uz = rw[GA_U + 2];
+                const float ir = rw[GA_IR];
                 float gx, gy, gz;
                 harmonics_grad(ux, uy, uz, psi, gx, gy, gz);
                 const float gu = gx * ux + gy * uy + gz * uz;
@@ -698,7 +748,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
                 fx += Fx;
                 fy += Fy;
                 fz += Fz;
-                const int j = __float_as_int(rw[2 * KA + NLM + 4]);
+                const int j = __float_as_int(rw[GA_J]);
                 atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
             }
         }
@@ -977,60 +1027,35 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         }
         __syncthreads();
 
-        // 4b real space (lanes over candidates) and the potential sums
+        // 4b real space (lanes over candidates, pair rows from the pre-pass) and the potential sums
         double er = 0.0, sphi = 0.0, sq2 = 0.0;
         {
             float* tab = un + PARAM_FLOATS + warp * WARP_FLOATS;
             int* cum = reinterpret_cast<int*>(tab + WCUM);
-            const float4* sp = a.spos4 + off;
-            const Geom& g = bs.g;
-            const float rcs2 = g.rc_real * g.rc_real;
             for (int m = warp; m < n; m += NW) {
                 const float qi = qcs[(size_t)m * CG + lane];
                 float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                 if (a.mode == 1) {
                     species_cum(a, off, n, m, S, cum);
                     const int tot_l = cum[S];
-                    const float4 pk = sp[m];
-                    const int* lst = a.nbr_list + (size_t)(off + m) * a.cap_l;
+                    const float4* grows = reinterpret_cast<const float4*>(a.geo_rad + (size_t)(off + m) * a.cap_l * GR);
                     for (int base = 0; base < tot_l; base += 32) {
-                        const int e = base + lane;
-                        float B = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-                        int jj = -1;
-                        if (e < tot_l) {
-                            const int ent = __ldg(&lst[e]);
-                            float vx, vy, vz;
-                            entry_vector(sp, ent, pk, g, vx, vy, vz);
-                            const float r2 = vx * vx + vy * vy + vz * vz;
-                            if (r2 < rcs2) {
-                                const float r = sqrtf(r2), ir = 1.f / r, ar = a.alpha * r;
-                                const float ec = erfcf(ar);
-                                B = KE * ec * ir;
-                                // dB/dr = -k_e (erfc(a r) / r + 2 a / sqrt(pi) exp(-a^2 r^2)) / r
-                                const float dB = -KE * (ec * ir + 1.12837916709551257f * a.alpha * expf(-ar * ar)) * ir;
-                                bx = dB * vx * ir;
-                                by = dB * vy * ir;
-                                bz = dB * vz * ir;
-                                jj = entry_index(ent);
-                            }
-                        }
-                        float* row = tab + lane * TAB_RS;
-                        row[0] = B;
-                        row[1] = bx;
-                        row[2] = by;
-                        row[3] = bz;
-                        row[4] = __int_as_float(jj);
-                        __syncwarp();
                         const int cntc = min(32, tot_l - base);
+                        {
+                            float4* t4 = reinterpret_cast<float4*>(tab);
+                            const float4* s4 = grows + (size_t)base * (GR / 4);
+                            for (int i = lane; i < cntc * (GR / 4); i += 32) t4[i] = __ldg(&s4[i]);
+                        }
+                        __syncwarp();
                         for (int r = 0; r < cntc; ++r) {
-                            const float* rw = tab + r * TAB_RS;
-                            const int j = __float_as_int(rw[4]);
+                            const float* rw = tab + r * GR;
+                            const int j = __float_as_int(rw[GR_JR]);
                             if (j < 0) continue;
                             const float qj = qcs[(size_t)j * CG + lane];
-                            ph = fmaf(qj, rw[0], ph);
-                            gx = fmaf(qj, rw[1], gx);
-                            gy = fmaf(qj, rw[2], gy);
-                            gz = fmaf(qj, rw[3], gz);
+                            ph = fmaf(qj, rw[GR_B], ph);
+                            gx = fmaf(qj, rw[GR_BU], gx);
+                            gy = fmaf(qj, rw[GR_BU + 1], gy);
+                            gz = fmaf(qj, rw[GR_BU + 2], gz);
                         }
                         __syncwarp();
                     }
@@ -1105,10 +1130,11 @@ size_t item_smem(int nph_max) {
 void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
                        const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
-                       int* cnt_ang, float2* phase, int nph_stride, unsigned int* status, cudaStream_t st_) {
+                       int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
+                       int bstride, float alpha, unsigned int* status, cudaStream_t st_) {
     if (n_struct <= 0) return;
     const size_t sm1 = sizeof(int) * ((size_t)nmax + BATCH_MAX_CELLS + 1 + MAX_SPECIES + 1);
-    const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a);
+    const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a + 32 * TAB_P + 16);
     static size_t attr1 = 0, attr2 = 0;
     if (sm1 > 48 * 1024 && sm1 > attr1) {
         cudaFuncSetAttribute(k_batch_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
@@ -1121,7 +1147,8 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
     k_batch_sort<<<n_struct, PREP_THREADS, sm1, st_>>>(pos, types, nmax, n_species, st, cell_start, spos4, sidx,
                                                         order, spec_off, status);
     k_batch_lists<<<n_struct, PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
-                                                         cnt_list, nbr_ang, cnt_ang, phase, nph_stride, status);
+                                                         cnt_list, nbr_ang, cnt_ang, phase, nph_stride, geo_rad,
+                                                         geo_ang, bsum, bstride, alpha, status);
 }
 
 size_t batch_item_smem(int warps, int nph_max) {

@@ -23,6 +23,7 @@ constexpr int CG = 32;               // candidates per item (one per lane)
 constexpr int BATCH_MAX_NPH = 96;    // phase factors per atom (n_max <= 17 per axis: edges up to
                                      // ~48 A at k_max = 2.23 1/A)
 constexpr int BATCH_MAX_CELLS = 512; // cell grid per structure (8 per axis at most)
+constexpr int BATCH_GR = 20, BATCH_GA = 48;   // floats per radial / angular pair row
 
 // One structure of the batch (host-built).
 struct BatchStruct {
@@ -71,6 +72,10 @@ struct BatchArgs {
     int cap_l, cap_a;
     const float2* phase;     // [N][nph_stride]
     int nph_stride;
+    const float* geo_rad;    // [N][cap_l][20] radial pair rows (see batch.cu)
+    const float* geo_ang;    // [N][cap_a][48] angular pair rows
+    const float* bsum;       // [N][bstride] basis sums B^R | B^A
+    int bstride;
     // tables
     const BatchStruct* st;
     const BatchKTab* kt;
@@ -101,7 +106,10 @@ struct BatchArgs {
 void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
                        const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
-                       int* cnt_ang, float2* phase, int nph_stride, unsigned int* status, cudaStream_t st_);
+                       int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
+                       int bstride, float alpha, unsigned int* status, cudaStream_t st_);
+// Floats per atom of the basis sums: B^R padded to MAX_SPECIES species, then B^A of n_species.
+inline int batch_bstride(int n_species) { return MAX_SPECIES * KR + n_species * KA * NLM; }
 // Dynamic shared memory of the item kernel and its resident blocks per SM (0: does not fit).
 size_t batch_item_smem(int warps, int nph_max);
 int batch_item_blocks_per_sm(int warps, int nph_max);
