@@ -19,6 +19,7 @@ struct qnep_model {
     qnep_hparams hp{};
     qnep_elec es{};
     int precision = 0;
+    int num_sms = 152;
     int n_cand = 1;
     ParamLayout lay{};
     float* d_params = nullptr;
@@ -41,6 +42,7 @@ struct qnep_model {
     float* dq = nullptr;
     float* u = nullptr;
     float* q = nullptr;
+    float* dtc = nullptr;          // scaled descriptors [n][32] handed to the tensor-core network
     float4* fields = nullptr;      // kfield [n] | rfield [n] | acc12 [3n] (see desc_math.cuh)
     float2* phase = nullptr;
     // cells
@@ -305,6 +307,7 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             CK(grow(&m->dq, (size_t)NDES * na));
             CK(grow(&m->u, na));
             CK(grow(&m->q, na));
+            if (m->precision != QNEP_PREC_FP32) CK(grow(&m->dtc, (size_t)32 * na));
             CK(grow(&m->fields, (size_t)5 * na));
         }
         // +2 entries: bulk copies round the last tile up to 16 bytes
@@ -425,7 +428,8 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
         }
         if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
     }
-    if (precision != QNEP_PREC_FP32) return QNEP_ERR_UNSUPPORTED;
+    if (precision != QNEP_PREC_FP32 && precision != QNEP_PREC_MLP_BF16 && precision != QNEP_PREC_MLP_TF32)
+        return QNEP_ERR_ARG;
     for (size_t k = 0; k < n_params; ++k)
         if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
     m = new qnep_model();
@@ -447,8 +451,10 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
             set_num_sms(sms);
+            m->num_sms = sms;
+        }
     }
     CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
@@ -497,6 +503,8 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
     const bool gp_nonzero = vjp && (vjp->polar_weight[0] != 0 || vjp->polar_weight[1] != 0 || vjp->polar_weight[2] != 0);
     const bool backward = out->forces || out->bec || out->want_virial || vjp;
     const bool want_bec = out->bec != nullptr || gp_nonzero;
+    if (vjp && m->precision != QNEP_PREC_FP32)
+        return fail(m, QNEP_ERR_UNSUPPORTED, "the vector-Jacobian product runs on the FP32 path only");
     const float q_target = (float)(m->es.q_total / (double)m->sqrt_eps);   // Q in screened-charge units
     const int cl = m->cap_list > 0 ? m->cap_list : m->cl_alloc;
     const int ca = m->cap_ang > 0 ? m->cap_ang : m->ca_alloc;
@@ -507,6 +515,7 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         harvest(m);
     }
     Geom g = m->geom;
+    const bool mixed = m->precision != QNEP_PREC_FP32;
     const bool coop = m->path == QNEP_PATH_WARP || (m->path == QNEP_PATH_AUTO && n <= kCoopMaxAtoms);
     if (coop) {   // atom-major lists for the warp-per-atom kernels
         g.list_sa = cl;
@@ -537,7 +546,10 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         launch_nbr_desc_coop(m->spos4, m->cell_start, m->sidx, n, g, m->d_params, m->lay, cl, ca, m->nbr_list,
                              m->cnt_list, m->nbr_ang, m->cnt_ang, backward ? m->ang : nullptr,
                              backward ? m->du : nullptr, m->dq, m->u, m->q, out->descriptor, m->tab, ewald, m->fields,
-                             vjp ? vjp->charge_weight : nullptr, m->d_acc, st);
+                             vjp ? vjp->charge_weight : nullptr, m->d_acc, st, mixed ? m->dtc : nullptr);
+        if (mixed)
+            launch_mlp_tc(m->precision, m->dtc, m->spos4, n, m->d_params, m->lay, backward ? m->du : nullptr, m->dq,
+                          NDES, 1, m->u, m->q, m->d_acc, m->num_sms, st);
         tm.end(2, st);
     } else {
         tm.begin(1, st);
@@ -548,7 +560,10 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         launch_descriptor_forward(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
                                   m->lay, backward ? m->ang : nullptr, backward ? m->du : nullptr,
                                   backward ? m->dq : nullptr, m->u, m->q, out->descriptor, m->sidx, m->fields,
-                                  vjp ? vjp->charge_weight : nullptr, m->d_acc, st);
+                                  vjp ? vjp->charge_weight : nullptr, m->d_acc, st, mixed ? m->dtc : nullptr);
+        if (mixed)
+            launch_mlp_tc(m->precision, m->dtc, m->spos4, n, m->d_params, m->lay, backward ? m->du : nullptr,
+                          backward ? m->dq : nullptr, 1, n, m->u, m->q, m->d_acc, m->num_sms, st);
         tm.end(2, st);
         tm.begin(3, st);
         if (ewald) launch_ewald_phases(m->spos4, n, m->tab, st);
@@ -674,7 +689,7 @@ void qnep_destroy(qnep_model* m) {
                     m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phase, m->cell_count,
                     m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_chunk_order, m->d_kg, m->d_S, m->d_C,
                     m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
-                    m->io_out[4], m->io_out[5]};
+                    m->io_out[4], m->io_out[5], m->dtc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->h_status) cudaFreeHost(m->h_status);

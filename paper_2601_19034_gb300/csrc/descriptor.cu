@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
                                                   float* __restrict__ dq, float* __restrict__ u_out,
                                                   float* __restrict__ q_out, float* __restrict__ des_out,
                                                   const int* __restrict__ sidx, float4* __restrict__ fields,
-                                                  const float* __restrict__ gq_in, Accum* __restrict__ acc) {
+                                                  const float* __restrict__ gq_in, Accum* __restrict__ acc,
+                                                  float* __restrict__ dtc) {
     extern __shared__ float sp[];
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
     __syncthreads();
@@ -161,7 +162,15 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
 #pragma unroll
             for (int v = 0; v < NDES; ++v) des_out[(size_t)sidx[i] * NDES + v] = d[v];
         }
+        if (dtc && lane == 0) {   // tensor-core network (precision form): hand the scaled descriptor over
+            float4* o = reinterpret_cast<float4*>(dtc + (size_t)i * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                o[q] = make_float4(d[4 * q], d[4 * q + 1], 4 * q + 2 < NDES ? d[4 * q + 2] : 0.f,
+                                   4 * q + 3 < NDES ? d[4 * q + 3] : 0.f);
+        }
 
+        if (!dtc) {
         // network and its input gradients (hidden units split over the TPA lanes)
         const float* net = sp + lay.mlp + ti * lay.mlp_stride;
         float uu = 0.f, qq = 0.f, gu[NDES], gq[NDES];
@@ -208,8 +217,9 @@ __global__ void __launch_bounds__(128) k_desc_fwd(const float4* __restrict__ pos
             q_out[i] = qq;
             su = (double)uu;
             sq = (double)qq;
-            if (gq_in) sg = (double)__ldg(&gq_in[__ldg(&sidx[i])]);
         }
+        }
+        if (lane == 0 && gq_in) sg = (double)__ldg(&gq_in[__ldg(&sidx[i])]);
         for (int part = lane; part < 5; part += TPA) zero_atom_fields(fields, n, i, part);
     }
     // warp reduction of the FP64 energy / charge sums, one atomic per warp
@@ -457,12 +467,13 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
 template <int TPA>
 void fwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na, const int* ca, int n, const Geom& g,
                 const float* params, const ParamLayout& lay, float* ang, float* du, float* dq, float* u, float* q,
-                float* des, const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st) {
+                float* des, const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st,
+                float* dtc) {
     const int threads = 128;
     long long blocks = ((long long)n * TPA + threads - 1) / threads;
     size_t smem = sizeof(float) * lay.total;
     k_desc_fwd<TPA><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq, u,
-                                                             q, des, sidx, fields, gq, acc);
+                                                             q, des, sidx, fields, gq, acc, dtc);
 }
 
 template <int TPA, bool BEC>
@@ -493,14 +504,15 @@ int choose_tpa(int n) {
 void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                                const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                                float* ang_coef, float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st) {
+                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st,
+                               float* dtc) {
     if (n == 0) return;
     if (choose_tpa(n) == 2)
         fwd_launch<2>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, sidx, fields, gq, acc, st);
+                      des_out, sidx, fields, gq, acc, st, dtc);
     else
         fwd_launch<1>(pos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef, du, dq, u_out, q_out,
-                      des_out, sidx, fields, gq, acc, st);
+                      des_out, sidx, fields, gq, acc, st, dtc);
 }
 
 void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,

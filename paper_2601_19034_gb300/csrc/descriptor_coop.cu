@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang, float* __restrict__ ang_coef,
     float* __restrict__ du, float* __restrict__ dq, float* __restrict__ u_out, float* __restrict__ q_out,
     float* __restrict__ des_out, EwaldTab tab, int do_phase, float4* __restrict__ fields,
-    const float* __restrict__ gq_in, Accum* __restrict__ acc) {
+    const float* __restrict__ gq_in, Accum* __restrict__ acc, float* __restrict__ dtc) {
     extern __shared__ float csm[];
     float* sp = csm;
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
@@ -168,8 +168,11 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
             dbuf[lane] = dv;
             if (des_out) des_out[(size_t)__ldg(&sidx[k]) * NDES + lane] = dv;
         }
+        // tensor-core network (precision form): hand the scaled descriptor (padded to 32) over
+        if (dtc) dtc[(size_t)k * 32 + lane] = dv;
         __syncwarp();
 
+        if (!dtc) {
         // network: lanes over hidden units, then over inputs for dU/dD and dq/dD
         const float* net = sp + lay.mlp + ti * lay.mlp_stride;
         float ue = 0.f, uq = 0.f;
@@ -210,8 +213,9 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
             q_out[k] = qq;
             su += (double)uu;   // a warp handles several atoms
             sq += (double)qq;
-            if (gq_in) sg += (double)__ldg(&gq_in[__ldg(&sidx[k])]);
         }
+        }
+        if (lane == 0 && gq_in) sg += (double)__ldg(&gq_in[__ldg(&sidx[k])]);
         if (do_phase) {
             for (int e = lane; e < tab.nph; e += 32) tab.phase[(size_t)k * tab.nph + e] = phase_entry(pk, e, tab);
         }
@@ -483,7 +487,7 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq, float* u,
                           float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
-                          const float* gq, Accum* acc, cudaStream_t st) {
+                          const float* gq, Accum* acc, cudaStream_t st, float* dtc) {
     if (n == 0) return;
     static bool attr = false;
     if (!attr) {
@@ -497,7 +501,7 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
     if (per_sm > 0 && blocks > per_sm * g_num_sms) blocks = per_sm * g_num_sms;
     k_nbr_desc_coop<<<blocks, 32 * CW, smem, st>>>(
         spos4, cell_start, sidx, n, g, params, lay, cap_l, cap_a, nbr_list, cnt_list, nbr_ang, cnt_ang, ang_coef, du,
-        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc);
+        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc, dtc);
 }
 
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,

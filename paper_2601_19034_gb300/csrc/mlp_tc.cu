@@ -1,0 +1,361 @@
+// Per-atom network on the 5th-generation tensor cores (precision form: BF16 or TF32
+// operands, FP32 accumulation in tensor memory).
+//
+// The network of Eq. U_i / Sec. II.B for a tile of 128 atoms is three small GEMMs:
+//   MMA1  P   = D W0^T          [128 x 32] x [32 x 32 S]   (all species' W0 stacked on N)
+//   epilogue  h = tanh(P_{t_i} - b0), U = w1E.h - b1E, q = w1q.h - b1q,
+//             gE = w1E (1 - h^2), gq = w1q (1 - h^2)      (FP32, one thread per atom)
+//   MMA2  dU/dD = GE W0         [128 x 32 S] x [32 S x 32]   GE block-diagonal by species
+//   MMA3  dq/dD = GQ W0         (same B operand)
+// N_des = 30 and N_neu = 30 are padded to 32 with zeros.  Operands live in shared
+// memory in the canonical K-major layout without swizzle (core matrices of 8 rows x
+// 16 bytes; K-adjacent cores 128 B apart, 8-row groups K/kpc x 128 B apart); one
+// thread issues the tcgen05.mma instructions, accumulators are in tensor memory and
+// are read back with tcgen05.ld (warp w owns lanes 32w..32w+31).  Every wait on an
+// mbarrier is bounded; a timeout sets a status bit and the block stops after
+// releasing its tensor memory.
+#include <stdint.h>
+
+#include <cuda_bf16.h>
+
+#include "qnep_internal.cuh"
+#include "tma.cuh"
+
+namespace qnep {
+
+namespace {
+
+constexpr int TM = 128;      // atoms per tile = MMA M = tensor-memory lanes
+constexpr int KP = 32;       // descriptor length padded
+constexpr int HP = 32;       // hidden width padded
+constexpr int TMEM_COLS = 256;
+constexpr int COL_P = 0;     // P: 32 S columns
+constexpr int COL_DU = 128;  // dU/dD: 32 columns
+constexpr int COL_DQ = 160;  // dq/dD: 32 columns
+
+// element size and per-instruction K of the two operand types
+template <int PREC> struct Op;
+template <> struct Op<PREC_BF16> { static constexpr int ES = 2, KSTEP = 16, FMT = 1; };
+template <> struct Op<PREC_TF32> { static constexpr int ES = 4, KSTEP = 8, FMT = 2; };
+
+// byte offset of element (row, k) of an R x K operand in the canonical K-major layout
+template <int ES>
+__host__ __device__ constexpr uint32_t kmaj(int row, int k, int K) {
+    return (uint32_t)((((row >> 3) * (K * ES / 16) + (k * ES) / 16) * 128) + (row & 7) * 16 + ((k * ES) % 16));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of tcgen05; base offset 0, no swizzle
+    return d;
+}
+
+// instruction descriptor: D F32, A/B format, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t instr_desc(int fmt, int M, int N) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    if (PREC == PREC_BF16) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// store one operand element (rounded to the operand type)
+template <int PREC>
+__device__ __forceinline__ void put(unsigned char* base, uint32_t off, float x) {
+    if (PREC == PREC_BF16) {
+        *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
+    } else {
+        uint32_t t;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+        *reinterpret_cast<uint32_t*>(base + off) = t;
+    }
+}
+
+struct MlpSmem {   // byte offsets of the operands and small parameters in dynamic shared memory
+    uint32_t a1, a2, a3, b1, b2, par, total;
+};
+
+template <int PREC>
+__host__ __device__ constexpr MlpSmem mlp_layout(int S) {
+    constexpr int ES = Op<PREC>::ES;
+    MlpSmem L{};
+    L.a1 = 0;
+    L.a2 = L.a1 + TM * KP * ES;
+    L.a3 = L.a2 + TM * HP * S * ES;
+    L.b1 = L.a3 + TM * HP * S * ES;
+    L.b2 = L.b1 + HP * S * KP * ES;
+    L.par = L.b2 + KP * HP * S * ES;
+    // b0, w1E, w1q [S][HP], b1E, b1Q [S], scaler [KP] (FP32)
+    L.total = L.par + (uint32_t)sizeof(float) * (3 * S * HP + 2 * S + KP);
+    return L;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, const float4* __restrict__ spos4,
+                                               int n, const float* __restrict__ params, ParamLayout lay,
+                                               float* __restrict__ du, float* __restrict__ dq, int d_sa, int d_sv,
+                                               float* __restrict__ u_out, float* __restrict__ q_out,
+                                               Accum* __restrict__ acc) {
+    using O = Op<PREC>;
+    constexpr int ES = O::ES;
+    extern __shared__ __align__(128) unsigned char msm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ double red[2][TM / 32];
+    __shared__ int failed;
+    const int S = lay.n_species;
+    const MlpSmem L = mlp_layout<PREC>(S);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char* A1 = msm + L.a1;
+    unsigned char* A2 = msm + L.a2;
+    unsigned char* A3 = msm + L.a3;
+    unsigned char* B1 = msm + L.b1;
+    unsigned char* B2 = msm + L.b2;
+    float* par = reinterpret_cast<float*>(msm + L.par);
+    float* pb0 = par;                   // [S][HP]
+    float* pwe = par + S * HP;
+    float* pwq = par + 2 * S * HP;
+    float* pb1 = par + 3 * S * HP;      // [S][2]
+    float* psc = pb1 + 2 * S;           // [KP]
+
+    // weights of every species: B1 [32 S rows (s, mu)][32 K (v)] and B2 [32 rows (v)][32 S K (s, mu)]
+    for (int idx = tid; idx < S * HP * KP; idx += TM) {
+        const int s = idx / (HP * KP), rem = idx - s * HP * KP, mu = rem / KP, v = rem - mu * KP;
+        const float w = (mu < NNEU && v < NDES) ? params[lay.mlp + s * lay.mlp_stride + ParamLayout::W0 + mu * NDES + v]
+                                                : 0.f;
+        put<PREC>(B1, kmaj<ES>(s * HP + mu, v, KP), w);
+        put<PREC>(B2, kmaj<ES>(v, s * HP + mu, HP * S), w);
+    }
+    for (int idx = tid; idx < S * HP; idx += TM) {
+        const int s = idx / HP, mu = idx - s * HP;
+        const float* net = params + lay.mlp + s * lay.mlp_stride;
+        pb0[idx] = mu < NNEU ? net[ParamLayout::B0 + mu] : 0.f;
+        pwe[idx] = mu < NNEU ? net[ParamLayout::W1E + mu] : 0.f;
+        pwq[idx] = mu < NNEU ? net[ParamLayout::W1Q + mu] : 0.f;
+    }
+    for (int s = tid; s < S; s += TM) {
+        pb1[2 * s] = params[lay.mlp + s * lay.mlp_stride + ParamLayout::B1E];
+        pb1[2 * s + 1] = params[lay.mlp + s * lay.mlp_stride + ParamLayout::B1Q];
+    }
+    for (int v = tid; v < KP; v += TM) psc[v] = v < NDES ? params[lay.scaler + v] : 0.f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        failed = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // canonical layout strides: K-adjacent core matrices 128 B apart, 8-row groups (K ES / 16) x 128 B
+    const uint32_t sA1 = (uint32_t)(KP * ES / 16) * 128, sA2 = (uint32_t)(HP * S * ES / 16) * 128;
+    const uint32_t kstep_bytes = (uint32_t)(O::KSTEP * ES / 16) * 128;
+    const uint32_t id1 = instr_desc(O::FMT, TM, HP * S), id2 = instr_desc(O::FMT, TM, KP);
+    uint32_t phase = 0;
+    double su = 0.0, sq = 0.0;
+
+    const int ntiles = (n + TM - 1) / TM;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile * TM + tid;
+        const bool valid = k < n;
+        int ti = 0;
+        // operand A1: this atom's scaled descriptor; A2 / A3 cleared (block-diagonal fill below)
+        {
+            float dv[KP];
+            if (valid) {
+                const float4* src = reinterpret_cast<const float4*>(dtc + (size_t)k * KP);
+#pragma unroll
+                for (int q = 0; q < KP / 4; ++q) {
+                    const float4 x = __ldg(&src[q]);
+                    dv[4 * q] = x.x;
+                    dv[4 * q + 1] = x.y;
+                    dv[4 * q + 2] = x.z;
+                    dv[4 * q + 3] = x.w;
+                }
+                ti = __float_as_int(__ldg(&spos4[k]).w);
+            } else {
+#pragma unroll
+                for (int q = 0; q < KP; ++q) dv[q] = 0.f;
+            }
+#pragma unroll
+            for (int v = 0; v < KP; ++v) put<PREC>(A1, kmaj<ES>(tid, v, KP), dv[v]);
+            for (int c = 0; c < HP * S; ++c) {
+                put<PREC>(A2, kmaj<ES>(tid, c, HP * S), 0.f);
+                put<PREC>(A3, kmaj<ES>(tid, c, HP * S), 0.f);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < KP / O::KSTEP; ++kk)
+                mma<PREC>(tmem + COL_P, smem_desc(smem_u32(A1) + kk * kstep_bytes, 128, sA1),
+                          smem_desc(smem_u32(B1) + kk * kstep_bytes, 128, sA1), id1, kk > 0);
+            mma_commit(&bar);
+        }
+        if (!mbar_wait_bounded(&bar, phase)) failed = 1;
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 1: P of the atom's species block (every block is read: the load is warp-wide)
+        float pre[HP];
+        for (int s = 0; s < S; ++s) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + COL_P + s * HP, v);
+            if (s == ti) {
+#pragma unroll
+                for (int c = 0; c < HP; ++c) pre[c] = v[c];
+            }
+        }
+        float ue = 0.f, uqv = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < HP; ++mu) {
+            const float h = tanhf(pre[mu] - pb0[ti * HP + mu]);
+            const float we = pwe[ti * HP + mu], wq = pwq[ti * HP + mu];
+            ue = fmaf(we, h, ue);
+            uqv = fmaf(wq, h, uqv);
+            const float dh = 1.f - h * h;
+            put<PREC>(A2, kmaj<ES>(tid, ti * HP + mu, HP * S), we * dh);
+            put<PREC>(A3, kmaj<ES>(tid, ti * HP + mu, HP * S), wq * dh);
+        }
+        const float U = ue - pb1[2 * ti], Q = uqv - pb1[2 * ti + 1];
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0 && !failed) {
+            for (int kk = 0; kk < HP * S / O::KSTEP; ++kk) {
+                const uint64_t b = smem_desc(smem_u32(B2) + kk * kstep_bytes, 128, sA2);
+                mma<PREC>(tmem + COL_DU, smem_desc(smem_u32(A2) + kk * kstep_bytes, 128, sA2), b, id2, kk > 0);
+                mma<PREC>(tmem + COL_DQ, smem_desc(smem_u32(A3) + kk * kstep_bytes, 128, sA2), b, id2, kk > 0);
+            }
+            mma_commit(&bar);
+        }
+        __syncthreads();
+        if (!failed && !mbar_wait_bounded(&bar, phase)) failed = 1;
+        phase ^= 1u;
+        tc_fence_after();
+        float gu[KP], gq[KP];
+        tmem_ld32(tmem + lane_base + COL_DU, gu);
+        tmem_ld32(tmem + lane_base + COL_DQ, gq);
+        if (valid) {
+            if (du) {
+#pragma unroll
+                for (int v = 0; v < NDES; ++v) {
+                    du[(size_t)k * d_sa + (size_t)v * d_sv] = gu[v] * psc[v];
+                    dq[(size_t)k * d_sa + (size_t)v * d_sv] = gq[v] * psc[v];
+                }
+            }
+            u_out[k] = U;
+            q_out[k] = Q;
+            su += (double)U;
+            sq += (double)Q;
+        }
+        tc_fence_before();
+        __syncthreads();   // operands and accumulators are reused by the next tile
+        tc_fence_after();
+        if (failed) break;
+    }
+    // block sums of U and q (FP64), one atomic each
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = su;
+        red[1][warp] = sq;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < TM / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        atomicAdd(&acc->sum_u, a);
+        atomicAdd(&acc->sum_q, b);
+        if (failed) atomicOr(&acc->status, kStatusTimeout);
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace
+
+size_t mlp_tc_smem(int precision, int n_species) {
+    const size_t need = precision == PREC_BF16 ? mlp_layout<PREC_BF16>(n_species).total
+                                               : mlp_layout<PREC_TF32>(n_species).total;
+    // at least 80 KB so that at most two blocks (2 x 256 tensor-memory columns) share an SM
+    return need > 80 * 1024 ? need : 80 * 1024;
+}
+
+void launch_mlp_tc(int precision, const float* dtc, const float4* spos4, int n, const float* params,
+                   const ParamLayout& lay, float* du, float* dq, int d_sa, int d_sv, float* u, float* q, Accum* acc,
+                   int num_sms, cudaStream_t st) {
+    if (n <= 0) return;
+    const size_t smem = mlp_tc_smem(precision, lay.n_species);
+    const int ntiles = (n + TM - 1) / TM;
+    // two blocks per SM at most (256 tensor-memory columns each)
+    const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
+    if (precision == PREC_BF16) {
+        cudaFuncSetAttribute(k_mlp_tc<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mlp_tc<PREC_BF16><<<grid, TM, smem, st>>>(dtc, spos4, n, params, lay, du, dq, d_sa, d_sv, u, q, acc);
+    } else {
+        cudaFuncSetAttribute(k_mlp_tc<PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_mlp_tc<PREC_TF32><<<grid, TM, smem, st>>>(dtc, spos4, n, params, lay, du, dq, d_sa, d_sv, u, q, acc);
+    }
+}
+
+}  // namespace qnep

@@ -28,6 +28,9 @@ constexpr int NANG = NA * NLM;              // 120 angular expansion coefficient
 constexpr float KE = 14.3996454784f;        // k_e = 1/(4 pi eps0), eV A / e^2
 constexpr double KE_D = 14.3996454784;
 
+constexpr int PREC_BF16 = 1;    // network operands on the tensor cores (precision form)
+constexpr int PREC_TF32 = 2;
+
 constexpr int CODE_SHIFT = 26;
 constexpr int INDEX_MASK = (1 << CODE_SHIFT) - 1;
 constexpr int CODE_SELF = 1 | (1 << 2) | (1 << 4);   // image shift (0, 0, 0)
@@ -178,14 +181,15 @@ void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const in
                                const int* nbr_ang, const int* cnt_ang, int n, const Geom& g,
                                const float* params, const ParamLayout& lay, float* ang_coef,
                                float* du, float* dq, float* u_out, float* q_out, float* des_out,
-                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st);
+                               const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st,
+                               float* dtc = nullptr);
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a);
 void set_num_sms(int n);
 void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,
                           float* u, float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
-                          const float* gq, Accum* acc, cudaStream_t st);
+                          const float* gq, Accum* acc, cudaStream_t st, float* dtc = nullptr);
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                           const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                           const float* ang_coef, const float* du, const float* dq, const float* q_raw,
@@ -209,6 +213,13 @@ void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, c
                  int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
                  Accum* acc, cudaStream_t st);
 void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st);
+// Network on the tensor cores for n atoms (precision PREC_BF16 or PREC_TF32): scaled
+// descriptors dtc [n][32] (sorted order) -> u, q, du / dq (element k, v at k d_sa + v d_sv),
+// FP64 sums of u and q into acc.
+size_t mlp_tc_smem(int precision, int n_species);
+void launch_mlp_tc(int precision, const float* dtc, const float4* spos4, int n, const float* params,
+                   const ParamLayout& lay, float* du, float* dq, int d_sa, int d_sv, float* u, float* q, Accum* acc,
+                   int num_sms, cudaStream_t st);
 void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t st);
 int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc_in, float q_target, PppmTab pm,
                 float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st);
