@@ -1,16 +1,17 @@
 """Benchmark of the qNEP force call on one GB300 (or N replicas under torchrun).
 
-Workload (default): BaTiO3 cubic perovskite 10x10x10 supercell, 5000 atoms,
-a = 4.0 A with N(0, 0.05 A) displacements, 3 species; NEP descriptor r_c 6/4 A,
-n_max 4/4, basis 8, l_max 4 + 4-body, 30 tanh units, two outputs; Ewald
-alpha = 0.3 1/A, real-space cutoff 6 A, k_max for 1e-6 relative error, mode 1;
-outputs energy, forces, virial, charges, BEC and polarization.
+Default workload (the batched form): 512 LLZO-shaped cells of 192-1536 atoms under
+64 candidate parameter vectors, every (structure, candidate) force call (energy,
+forces, charges; Ewald per cell) in one persistent launch replayed from a CUDA
+graph.  value = atom-evaluations per second.  The line also carries the plain
+FP32 single-structure path on the same structures, the precision form (BF16 /
+TF32 network on the tensor cores) against FP32 on 8000 waters with PPPM, the
+item kernel's roofline (CUDA events around it) and the FP64 oracle on the host.
 
-A step is one full force call (neighbour build, descriptor + network,
-charges, Ewald, real space, backward, BEC).  Inputs are resident in HBM; the
-force call is replayed from a CUDA graph; L2 is flushed (a 512 MB write)
-between timed steps, outside the timed events.  The JSON line follows the
-repository's measurement contract ("Measurement").
+Single-structure workloads (--workload batio3 | water_pppm, --precision): one full
+force call per step (forces, virial, BEC, polarization).  Inputs are resident in
+HBM; L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
+The JSON line follows the repository's measurement contract ("Measurement").
 """
 from __future__ import annotations
 
@@ -132,6 +133,41 @@ def _ewald_kcount(box, kmax):
     return int(((k2 > 0) & (k2 < kmax * kmax)).sum()) // 2
 
 
+def _time_single(model, sysm, dev, steps, warmup, flush, want=None):
+    """CUDA-graph replay of one force call; L2 flushed between calls; event-timed ms per call."""
+    import torch
+    want = want or {}
+    pos = torch.tensor(sysm.positions, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    model.reserve(sysm.n_atoms, sysm.box)
+    out = model.compute(pos, typ, sysm.box, **want)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            model.compute_into(pos, typ, sysm.box, out, stream=stream.cuda_stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        model.compute_into(pos, typ, sysm.box, out, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            graph.replay()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            graph.replay()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in zip(starts, ends)])), out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -146,7 +182,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sysm, hp, params, elec = _config(args.workload)
     n = sysm.n_atoms
-    model = QNEP(hp, params, elec)
+    model = QNEP(hp, params, elec, precision=args.precision)
     pos = torch.tensor(sysm.positions, device=dev)
     typ = torch.tensor(sysm.types, device=dev)
     model.reserve(n, sysm.box)
@@ -428,6 +464,29 @@ def run_batch(args):
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     flop = _batch_flop(systems, hp, elec, n_cand)
 
+    # the item kernel alone: CUDA events around it on the launching stream (eager calls)
+    b.set_profiling(True)
+    for _ in range(min(args.steps, 5) + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+    stage, calls = b.stage_times()
+    b.set_profiling(False)
+    item_ms = stage["items"] / max(calls, 1)
+    prep_ms = stage["prepass"] / max(calls, 1)
+
+    # precision form on liquid water (8000 H2O, PPPM 64^3): FP32 vs BF16 / TF32 network
+    mixed = {"workload": WORKLOADS["water_pppm"]}
+    sy_w, hp_w, par_w, el_w = _config("water_pppm")
+    for prec in ("fp32", "bf16", "tf32"):
+        mw = QNEP(hp_w, par_w, el_w, precision=prec)
+        ms_w, _ = _time_single(mw, sy_w, dev, min(args.steps, 20), 3, flush)
+        mixed[prec] = {"ms_per_call": ms_w, "value": sy_w.n_atoms / (ms_w * 1e-3), "unit": UNIT}
+        mw.close()
+    for prec in ("bf16", "tf32"):
+        mixed[f"speedup_{prec}_vs_fp32"] = mixed[prec]["value"] / mixed["fp32"]["value"]
+    mixed["errors_vs_oracle"] = "per-output table in DESIGN.md (tests/test_gpu_precision.py bounds)"
+
     # plain FP32 single-structure path on the same structures (candidate 0; one call per structure)
     single = QNEP(hp, params[0], elec)
     single_ms = 0.0
@@ -476,11 +535,13 @@ def run_batch(args):
                        "launch": "CUDA graph replay of one qnep_batch_compute (pre-pass + persistent item kernel)",
                        "autotuned": {"warps": warps, "order": order, "ms": tune_ms},
                        "parallelism": "replicas" if world > 1 else "single GPU", "wall_s": wall},
-            "roofline": {"kernel": "k_batch_items (+ pre-pass, whole call)", "bound": "alu", "achieved": achieved,
-                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                         "ms": ms_per_step,
+            "roofline": {"kernel": "k_batch_items", "bound": "alu", "achieved": flop / (item_ms * 1e-3) / 1e12,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / (item_ms * 1e-3) / 1e12 / fp32_peak,
+                         "traffic": None, "ms": item_ms, "prepass_ms": prep_ms,
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
-                         "work": f"{flop:.4g} algorithmic flop per call"},
+                         "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
+                         "whole_call_frac": achieved / fp32_peak},
+            "mixed": mixed,
             "plain_fp32": {"value": plain_value, "unit": UNIT,
                            "what": "single-structure qnep_compute, forces + charges, one call per structure "
                                    "(first 64 structures, candidate 0)",
@@ -552,7 +613,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="batio3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="llzo_batch", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32"],
+                    help="single-structure workloads: network precision")
     ap.add_argument("--structures", type=int, default=0, help="llzo_batch: first N structures only (profiling)")
     ap.add_argument("--candidates", type=int, default=0, help="llzo_batch: first C candidates only (profiling)")
     args = ap.parse_args()

@@ -270,6 +270,12 @@ qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
 qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
                                 const int* types, const double* boxes, void* stream, double* energy,
                                 float* forces, float* charges, int reps, double* best_ms);
+/* Stage timers: when enabled, each qnep_batch_compute records CUDA events around the
+ * candidate-independent pre-pass and around the item kernel on its stream;
+ * qnep_batch_stage_times synchronizes, writes the accumulated times (ms) of the
+ * two stages and the number of timed calls, and resets them. */
+qnep_status qnep_batch_set_profiling(qnep_batch* b, int enable);
+qnep_status qnep_batch_stage_times(qnep_batch* b, float* ms_out /* [2] */, int* n_calls);
 const char* qnep_batch_last_error(const qnep_batch* b);
 void        qnep_batch_destroy(qnep_batch* b);
 

@@ -116,6 +116,10 @@ def _declare(lib):
     lib.qnep_batch_get_config.restype = i
     lib.qnep_batch_autotune.argtypes = [p, i, p, p, p, p, p, p, p, p, i, ctypes.POINTER(ctypes.c_double)]
     lib.qnep_batch_autotune.restype = i
+    lib.qnep_batch_set_profiling.argtypes = [p, i]
+    lib.qnep_batch_set_profiling.restype = i
+    lib.qnep_batch_stage_times.argtypes = [p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i)]
+    lib.qnep_batch_stage_times.restype = i
     lib.qnep_batch_last_error.argtypes = [p]
     lib.qnep_batch_last_error.restype = ctypes.c_char_p
     lib.qnep_batch_destroy.argtypes = [p]

@@ -66,6 +66,11 @@ struct qnep_batch {
     unsigned int* d_status = nullptr;
     cudaStream_t last_stream = nullptr;
     std::map<std::pair<int, int>, int> per_sm_cache;   // (warps, nph_max) -> resident blocks per SM
+    // stage timers: events around the pre-pass and the item kernel of each profiled call
+    bool profiling = false, pending = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    double stage_ms[2] = {0.0, 0.0};
+    int timed_calls = 0;
     std::string err;
 };
 
@@ -417,6 +422,18 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     if (s != QNEP_OK) return s;
     CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
     CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
+    if (b->profiling) {
+        if (b->pending) {   // previous profiled call: harvest its events
+            CKB(cudaEventSynchronize(b->ev[2]));
+            float t0 = 0.f, t1 = 0.f;
+            cudaEventElapsedTime(&t0, b->ev[0], b->ev[1]);
+            cudaEventElapsedTime(&t1, b->ev[1], b->ev[2]);
+            b->stage_ms[0] += t0;
+            b->stage_ms[1] += t1;
+            ++b->timed_calls;
+        }
+        CKB(cudaEventRecord(b->ev[0], st));
+    }
     launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
                       b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
                       b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->geo_rad, b->geo_ang, b->bsum,
@@ -458,7 +475,12 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.n_struct = n_struct;
     a.n_total = b->n_total;
     a.status = b->d_status;
+    if (b->profiling) CKB(cudaEventRecord(b->ev[1], st));
     launch_batch_items(a, b->warps, b->nph_max, std::min(slots, std::max(b->n_items, 1)), st);
+    if (b->profiling) {
+        CKB(cudaEventRecord(b->ev[2], st));
+        b->pending = true;
+    }
     CKB(cudaGetLastError());
     b->last_stream = st;
     return QNEP_OK;
@@ -530,6 +552,35 @@ qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_off
     return result;
 }
 
+qnep_status qnep_batch_set_profiling(qnep_batch* b, int enable) {
+    if (!b) return QNEP_ERR_ARG;
+    if (enable && !b->ev[0])
+        for (auto& e : b->ev) CKB(cudaEventCreate(&e));
+    b->profiling = enable != 0;
+    b->pending = false;
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_stage_times(qnep_batch* b, float* ms_out, int* n_calls) {
+    if (!b || !ms_out || !n_calls) return QNEP_ERR_ARG;
+    if (b->pending) {
+        CKB(cudaEventSynchronize(b->ev[2]));
+        float t0 = 0.f, t1 = 0.f;
+        cudaEventElapsedTime(&t0, b->ev[0], b->ev[1]);
+        cudaEventElapsedTime(&t1, b->ev[1], b->ev[2]);
+        b->stage_ms[0] += t0;
+        b->stage_ms[1] += t1;
+        ++b->timed_calls;
+        b->pending = false;
+    }
+    ms_out[0] = (float)b->stage_ms[0];
+    ms_out[1] = (float)b->stage_ms[1];
+    *n_calls = b->timed_calls;
+    b->stage_ms[0] = b->stage_ms[1] = 0.0;
+    b->timed_calls = 0;
+    return QNEP_OK;
+}
+
 const char* qnep_batch_last_error(const qnep_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 void qnep_batch_destroy(qnep_batch* b) {
@@ -542,6 +593,8 @@ void qnep_batch_destroy(qnep_batch* b) {
                     b->d_work,    b->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto e : b->ev)
+        if (e) cudaEventDestroy(e);
     delete b;
 }
 

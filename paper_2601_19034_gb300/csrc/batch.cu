@@ -348,11 +348,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
     int* cum = reinterpret_cast<int*>(tab + 32 * TAB_P);
     const float4* sp = spos4 + off;
     const int* cs = cell_start_all + bs.cell_off;
+    // atoms of the structure are split over gridDim.y blocks (warp stride nw * gridDim.y)
+    const int wstride = nw * gridDim.y, wfirst = blockIdx.y * nw + warp;
     int* lst_s = nbr_list + (size_t)off * cap_l;
     int* lsa_s = nbr_ang + (size_t)off * cap_a;
     int* cl_s = cnt_list + (size_t)off * n_species;
     int* ca_s = cnt_ang + (size_t)off * n_species;
-    for (int m = warp; m < n; m += nw) {
+    for (int m = wfirst; m < n; m += wstride) {
         const float4 pk = sp[m];
         int nl = 0, na = 0;
         bool ovf = warp_build_lists(sp, cs, m, pk, g, cap_l, cap_a, sl, slt, sa, sat, nl, na);
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
                       bsum + (size_t)(off + m) * bstride, tab, cum);
     }
     const BatchKTab kt = kts[bs.ktab];
-    for (int idx = threadIdx.x; idx < n * kt.nph; idx += blockDim.x) {
+    for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < n * kt.nph; idx += blockDim.x * gridDim.y) {
         const int m = idx / kt.nph, e = idx - m * kt.nph;
         phase[(size_t)(off + m) * nph_stride + e] = batch_phase(sp[m], e, kt);
     }
@@ -1146,7 +1148,9 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
     }
     k_batch_sort<<<n_struct, PREP_THREADS, sm1, st_>>>(pos, types, nmax, n_species, st, cell_start, spos4, sidx,
                                                         order, spec_off, status);
-    k_batch_lists<<<n_struct, PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
+    // about one warp per 32 atoms of the largest structure
+    const int ysplit = std::max(1, std::min(64, (nmax + 32 * (PREP_THREADS / 32) - 1) / (32 * (PREP_THREADS / 32)) * 4));
+    k_batch_lists<<<dim3(n_struct, ysplit), PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
                                                          cnt_list, nbr_ang, cnt_ang, phase, nph_stride, geo_rad,
                                                          geo_ang, bsum, bstride, alpha, status);
 }

@@ -38,12 +38,6 @@ template <int PREC> struct Op;
 template <> struct Op<PREC_BF16> { static constexpr int ES = 2, KSTEP = 16, FMT = 1; };
 template <> struct Op<PREC_TF32> { static constexpr int ES = 4, KSTEP = 8, FMT = 2; };
 
-// byte offset of element (row, k) of an R x K operand in the canonical K-major layout
-template <int ES>
-__host__ __device__ constexpr uint32_t kmaj(int row, int k, int K) {
-    return (uint32_t)((((row >> 3) * (K * ES / 16) + (k * ES) / 16) * 128) + (row & 7) * 16 + ((k * ES) % 16));
-}
-
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -100,15 +94,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// store one operand element (rounded to the operand type)
+// 16 bytes of operand elements (8 BF16 or 4 TF32) from FP32 values, first element lowest
 template <int PREC>
-__device__ __forceinline__ void put(unsigned char* base, uint32_t off, float x) {
+__device__ __forceinline__ uint4 pack16(const float* v) {
+    uint32_t w[4];
     if (PREC == PREC_BF16) {
-        *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            w[q] = *reinterpret_cast<const uint32_t*>(&h);
+        }
     } else {
-        uint32_t t;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-        *reinterpret_cast<uint32_t*>(base + off) = t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[q]) : "f"(v[q]));
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Elements k0 .. k0 + NK - 1 of one row of an operand with K columns (k0, NK multiples of
+// the 16-byte core row), one 16-byte store per core matrix.
+template <int PREC, int NK>
+__device__ __forceinline__ void put_row(unsigned char* base, int row, int K, int k0, const float* v) {
+    constexpr int ES = Op<PREC>::ES, KPC = 16 / ES;
+    const int ncore = K * ES / 16;
+#pragma unroll
+    for (int c = 0; c < NK / KPC; ++c) {
+        const int kc = k0 / KPC + c;
+        *reinterpret_cast<uint4*>(base + ((row >> 3) * ncore + kc) * 128 + (row & 7) * 16) = pack16<PREC>(v + c * KPC);
     }
 }
 
@@ -160,12 +172,21 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
     float* psc = pb1 + 2 * S;           // [KP]
 
     // weights of every species: B1 [32 S rows (s, mu)][32 K (v)] and B2 [32 rows (v)][32 S K (s, mu)]
-    for (int idx = tid; idx < S * HP * KP; idx += TM) {
-        const int s = idx / (HP * KP), rem = idx - s * HP * KP, mu = rem / KP, v = rem - mu * KP;
-        const float w = (mu < NNEU && v < NDES) ? params[lay.mlp + s * lay.mlp_stride + ParamLayout::W0 + mu * NDES + v]
-                                                : 0.f;
-        put<PREC>(B1, kmaj<ES>(s * HP + mu, v, KP), w);
-        put<PREC>(B2, kmaj<ES>(v, s * HP + mu, HP * S), w);
+    for (int row = tid; row < S * HP; row += TM) {   // B1 row (s, mu): W0_s[mu][0..31]
+        const int s = row / HP, mu = row - s * HP;
+        float w[KP];
+#pragma unroll
+        for (int v = 0; v < KP; ++v)
+            w[v] = (mu < NNEU && v < NDES) ? params[lay.mlp + s * lay.mlp_stride + ParamLayout::W0 + mu * NDES + v] : 0.f;
+        put_row<PREC, KP>(B1, row, KP, 0, w);
+    }
+    for (int idx = tid; idx < KP * S; idx += TM) {    // B2 row v, block s: W0_s[0..31][v]
+        const int v = idx / S, s = idx - v * S;
+        float w[HP];
+#pragma unroll
+        for (int mu = 0; mu < HP; ++mu)
+            w[mu] = (mu < NNEU && v < NDES) ? params[lay.mlp + s * lay.mlp_stride + ParamLayout::W0 + mu * NDES + v] : 0.f;
+        put_row<PREC, HP>(B2, v, HP * S, s * HP, w);
     }
     for (int idx = tid; idx < S * HP; idx += TM) {
         const int s = idx / HP, mu = idx - s * HP;
@@ -225,11 +246,15 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
 #pragma unroll
                 for (int q = 0; q < KP; ++q) dv[q] = 0.f;
             }
+            put_row<PREC, KP>(A1, tid, KP, 0, dv);
+            // A2 / A3 are block-diagonal: clear the other species' blocks of this row
+            float z[HP];
 #pragma unroll
-            for (int v = 0; v < KP; ++v) put<PREC>(A1, kmaj<ES>(tid, v, KP), dv[v]);
-            for (int c = 0; c < HP * S; ++c) {
-                put<PREC>(A2, kmaj<ES>(tid, c, HP * S), 0.f);
-                put<PREC>(A3, kmaj<ES>(tid, c, HP * S), 0.f);
+            for (int c = 0; c < HP; ++c) z[c] = 0.f;
+            for (int s = 0; s < S; ++s) {
+                if (s == ti) continue;
+                put_row<PREC, HP>(A2, tid, HP * S, s * HP, z);
+                put_row<PREC, HP>(A3, tid, HP * S, s * HP, z);
             }
         }
         fence_proxy_async_smem();
@@ -256,7 +281,7 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
                 for (int c = 0; c < HP; ++c) pre[c] = v[c];
             }
         }
-        float ue = 0.f, uqv = 0.f;
+        float ue = 0.f, uqv = 0.f, ge[HP], gqv[HP];
 #pragma unroll
         for (int mu = 0; mu < HP; ++mu) {
             const float h = tanhf(pre[mu] - pb0[ti * HP + mu]);
@@ -264,9 +289,11 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
             ue = fmaf(we, h, ue);
             uqv = fmaf(wq, h, uqv);
             const float dh = 1.f - h * h;
-            put<PREC>(A2, kmaj<ES>(tid, ti * HP + mu, HP * S), we * dh);
-            put<PREC>(A3, kmaj<ES>(tid, ti * HP + mu, HP * S), wq * dh);
+            ge[mu] = we * dh;
+            gqv[mu] = wq * dh;
         }
+        put_row<PREC, HP>(A2, tid, HP * S, ti * HP, ge);
+        put_row<PREC, HP>(A3, tid, HP * S, ti * HP, gqv);
         const float U = ue - pb1[2 * ti], Q = uqv - pb1[2 * ti + 1];
         fence_proxy_async_smem();
         tc_fence_before();

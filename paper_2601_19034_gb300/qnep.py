@@ -344,6 +344,16 @@ class QNEPBatch:
                    batch=self.handle)
         return w.value, ("largest_first", "structure")[o.value]
 
+    def set_profiling(self, enable: bool = True):
+        _lib.check(self.lib.qnep_batch_set_profiling(self.handle, 1 if enable else 0), batch=self.handle)
+
+    def stage_times(self) -> tuple:
+        """Accumulated device times (ms) of the pre-pass and the item kernel, and the call count."""
+        buf = (ctypes.c_float * 2)()
+        calls = ctypes.c_int()
+        _lib.check(self.lib.qnep_batch_stage_times(self.handle, buf, ctypes.byref(calls)), batch=self.handle)
+        return {"prepass": buf[0], "items": buf[1]}, calls.value
+
     def autotune(self, positions, types, offsets, boxes, reps: int = 3, out: dict | None = None) -> float:
         """Time every launch configuration on this batch and keep the fastest; returns its ms."""
         if out is None:
