@@ -45,6 +45,11 @@ WORKLOADS["llzo_batch"] = (
     "192-1536 atoms, N(0, 0.1 A) moves) x 64 candidate parameter vectors N(0, 0.1), 4 species; same descriptor / "
     "network; Ewald per cell alpha 0.3, r_c 6 A, k_max 2.230, mode 1; energy, forces and charges per "
     "(structure, candidate), FP32 path, one persistent launch")
+WORKLOADS["mgwater_nve"] = (
+    "Mg-water interface: hcp Mg slab (a 3.21, c 5.21 A, 15 layers) under 60 A of water at 1.0 g/cm3, "
+    "112 x 65 orthohexagonal cells, ~1.0 M atoms, 3 species; same descriptor; network BF16 on the tensor "
+    "cores; PPPM mesh 256 x 256 x 384, order 5, alpha 0.3, r_c 6 A, mode 1; NVE velocity Verlet 0.5 fs "
+    "from 300 K Maxwell-Boltzmann; a step = one MD step (force call + two half kicks + drift)")
 WORKLOAD = WORKLOADS["batio3"]
 
 
@@ -357,6 +362,26 @@ def run_reference(args):
     cores = torch.get_num_threads()
     if args.workload == "llzo_batch":
         return _reference_batch(args, world, cores)
+    if args.workload == "mgwater_nve":
+        # bounded sample: each step one force call of a 3297-atom slab of the same construction
+        sy0, hp, params, _ = workloads.config_mg_water(nx=6, ny=4)
+        sysm = workloads.mg_water_interface(6, 4, seed=77)
+        elec = workloads.Elec(mode=1, kind="pppm", mesh=(20, 24, 100), order=5)
+        times = []
+        for k in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec,
+                                 want_bec=False)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t)
+        value = sysm.n_atoms * len(times) / sum(times)
+        return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOADS["mgwater_nve"]},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"each step one force call of a {sysm.n_atoms}-atom slab"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     sysm, hp, params, elec = _config(args.workload)
     times = []
     for k in range(args.warmup + args.steps):
@@ -606,6 +631,100 @@ def _reference_batch(args, world, cores):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_nve(args):
+    """Large-scale form: NVE velocity Verlet on the ~1 M-atom Mg-water interface."""
+    import torch
+
+    from paper_2601_19034_gb300 import workloads
+    from paper_2601_19034_gb300.qnep import QNEP, nve
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sysm, hp, params, elec = workloads.config_mg_water()
+    n = sysm.n_atoms
+    masses = workloads.species_masses(workloads.MGWATER_SPECIES)
+    v0 = workloads.maxwell_boltzmann(masses[sysm.types], 300.0).astype(np.float32)
+    model = QNEP(hp, params, elec, precision=args.precision if args.precision != "fp32" else "bf16")
+    pos = torch.tensor(sysm.positions, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    model.compute(pos, typ, sysm.box, bec=False)          # lists sized, status checked
+    nve(model, pos, vel, typ, masses, sysm.box, 0.5, args.warmup)
+    torch.cuda.synchronize()
+    peaks, peak_kind = _peaks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record()
+        _, en = nve(model, pos, vel, typ, masses, sysm.box, 0.5, args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    status = model.sync_status()
+    ms = e0.elapsed_time(e1)
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms * 1e-3)
+    e = en.cpu().numpy()
+    etot = e.sum(1)
+    tps = np.arange(len(etot)) * 0.5e-3
+    drift = float(np.polyfit(tps, (etot - etot[0]) / n, 1)[0] * 1e3) if len(etot) > 2 else None
+    # per-stage device times of one force call (library stage timers)
+    model.set_profiling(True)
+    for _ in range(3):
+        model.compute(pos, typ, sysm.box, bec=False)
+    stages, calls = model.stage_times()
+    model.set_profiling(False)
+    stage_avg = {k: v / max(calls, 1) for k, v in stages.items()}
+    # end to end: state from pinned host memory, the run, energies back
+    pos_h = torch.tensor(sysm.positions).pin_memory()
+    vel_h = torch.tensor(v0).pin_memory()
+    ksteps = min(args.steps, 10)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    pos.copy_(pos_h, non_blocking=True)
+    vel.copy_(vel_h, non_blocking=True)
+    _, en2 = nve(model, pos, vel, typ, masses, sysm.box, 0.5, ksteps)
+    en_h = en2.cpu()
+    e2e_s = time.perf_counter() - t
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (network bf16 on tensor cores, FP64 reductions)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["mgwater_nve"], "atoms": n, "dt_fs": 0.5,
+                       "l2": "inputs larger than L2 (1 M atoms, 25 M-point meshes)",
+                       "launch": "qnep_nve_run: per step kick+drift, force call, kick+FP64 kinetic energy",
+                       "parallelism": "replicas" if world > 1 else "single GPU", "wall_s": wall},
+            "nve": {"drift_mev_per_atom_ps": drift, "steps": args.steps,
+                    "max_abs_dE_per_atom_eV": float(np.abs(etot - etot[0]).max() / n),
+                    "kinetic_per_atom_eV": float(e[0, 1] / n)},
+            "stage_ms": stage_avg,
+            "roofline": _roofline_generic(stage_avg, sysm, clocks, peaks),
+            "e2e": {"value": n * ksteps / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": n * 24 // ksteps,
+                    "d2h_bytes_per_step": int(en_h.numel() * 8 // ksteps), "ms_per_step": e2e_s * 1e3 / ksteps},
+            "gpu_launches": None,
+            "clocks": clocks,
+            "device_status": status,
+        }
+        if not args.no_cpu_baseline:
+            from oracle import forcecall
+            small = workloads.mg_water_interface(6, 4, seed=77)
+            el_s = workloads.Elec(mode=1, kind="pppm", mesh=(20, 24, 100), order=5)
+            tc = time.perf_counter()
+            forcecall.force_call(small.positions.astype(np.float64), small.box, small.types, hp, params, el_s,
+                                 want_bec=False)
+            dtc = time.perf_counter() - tc
+            line["cpu_baseline"] = {"value": small.n_atoms / dtc, "unit": UNIT, "cores": torch.get_num_threads(),
+                                    "kind": "oracle", "sample": f"one force call of a {small.n_atoms}-atom "
+                                    "Mg-water slab of the same construction (FP64 oracle, PPPM)"}
+    model.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,6 +744,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "llzo_batch":
         line = run_batch(args)
+    elif args.workload == "mgwater_nve":
+        line = run_nve(args)
     else:
         line = run_ours(args)
     if line is not None:

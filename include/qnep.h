@@ -166,6 +166,19 @@ typedef struct {
 qnep_status qnep_compute_vjp(qnep_model* m, int n_atoms, const float* positions, const int* types,
                              const double box[9], void* stream, const qnep_outputs* out, const qnep_vjp* vjp);
 
+/* NVE molecular dynamics (velocity Verlet) around the force call.  Runs n_steps steps of
+ * dt_fs femtoseconds from the given state; the force call of this model (its
+ * precision and electrostatics) is evaluated at every step, neighbour lists rebuilt.
+ *   positions, velocities: device [N][3] float32 (A, A/fs), updated in place
+ *   types: device [N] int32; masses: host [n_species] doubles (amu)
+ *   forces: device [N][3] float32, left holding the forces of the final positions
+ *   energies: device [n_steps + 1][2] doubles: U_pot and the kinetic energy (eV) of the
+ *             initial state and after every step (kinetic energy reduced in FP64)
+ * Asynchronous on `stream`; qnep_sync_status reports the status of the last force call. */
+qnep_status qnep_nve_run(qnep_model* m, int n_atoms, float* positions, float* velocities, const int* types,
+                         const double* masses, const double box[9], double dt_fs, int n_steps, void* stream,
+                         float* forces, double* energies);
+
 /* Synchronize the stream and return the device-side status of the last call. */
 qnep_status qnep_sync_status(qnep_model* m, void* stream);
 

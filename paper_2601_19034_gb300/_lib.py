@@ -98,6 +98,8 @@ def _declare(lib):
     lib.qnep_stage_times.restype = i
     lib.qnep_stage_name.argtypes = [i]
     lib.qnep_stage_name.restype = ctypes.c_char_p
+    lib.qnep_nve_run.argtypes = [p, i, p, p, p, p, p, ctypes.c_double, i, p, p, p]
+    lib.qnep_nve_run.restype = i
     # batched evaluation
     lib.qnep_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(HParamsC), p, ctypes.c_size_t, i,
                                       ctypes.POINTER(ElecC)]

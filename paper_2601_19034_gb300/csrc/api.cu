@@ -43,6 +43,12 @@ struct qnep_model {
     float* u = nullptr;
     float* q = nullptr;
     float* dtc = nullptr;          // scaled descriptors [n][32] handed to the tensor-core network
+    // velocity-Verlet state: step counter, FP64 kinetic-energy accumulator, block counter,
+    // and the force call's scalars
+    int* md_step = nullptr;
+    double* md_ke = nullptr;
+    unsigned int* md_done = nullptr;
+    double* md_scalars = nullptr;
     float4* fields = nullptr;      // kfield [n] | rfield [n] | acc12 [3n] (see desc_math.cuh)
     float2* phase = nullptr;
     // cells
@@ -683,13 +689,55 @@ qnep_status qnep_compute_host(qnep_model* m, int n, const float* positions_host,
     return qnep_sync_status(m, stream);
 }
 
+qnep_status qnep_nve_run(qnep_model* m, int n, float* positions, float* velocities, const int* types,
+                         const double* masses, const double box[9], double dt_fs, int n_steps, void* stream,
+                         float* forces, double* energies) {
+    if (!m) return QNEP_ERR_ARG;
+    if (!positions || !velocities || !types || !masses || !forces || !energies || n_steps < 0 || !(dt_fs > 0))
+        return fail(m, QNEP_ERR_ARG, "bad NVE arguments");
+    float ms[MAX_SPECIES] = {1.f, 1.f, 1.f, 1.f};
+    for (int t = 0; t < m->hp.n_species; ++t) {
+        if (!(masses[t] > 0) || !std::isfinite(masses[t])) return fail(m, QNEP_ERR_ARG, "masses must be positive");
+        ms[t] = (float)masses[t];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!m->md_step) {
+        CK(cudaMalloc((void**)&m->md_step, sizeof(int)));
+        CK(cudaMalloc((void**)&m->md_ke, sizeof(double)));
+        CK(cudaMalloc((void**)&m->md_done, sizeof(unsigned int)));
+        CK(cudaMalloc((void**)&m->md_scalars, sizeof(double) * QNEP_NSCALARS));
+    }
+    CK(cudaMemsetAsync(m->md_step, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(m->md_ke, 0, sizeof(double), st));
+    CK(cudaMemsetAsync(m->md_done, 0, sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(energies, 0, sizeof(double) * 2 * (size_t)(n_steps + 1), st));
+    qnep_outputs o{};
+    o.scalars = m->md_scalars;
+    o.forces = forces;
+    o.want_virial = 0;
+    const float dt = (float)dt_fs;
+    qnep_status s = compute_impl(m, n, positions, types, box, stream, &o, nullptr);
+    if (s != QNEP_OK) return s;
+    launch_vv_kick_energy(n, velocities, forces, types, ms, m->hp.n_species, dt, false, m->md_scalars, energies,
+                          m->md_step, m->md_ke, m->md_done, st);
+    for (int k = 0; k < n_steps; ++k) {
+        launch_vv_kick_drift(n, positions, velocities, forces, types, ms, m->hp.n_species, dt, st);
+        s = compute_impl(m, n, positions, types, box, stream, &o, nullptr);
+        if (s != QNEP_OK) return s;
+        launch_vv_kick_energy(n, velocities, forces, types, ms, m->hp.n_species, dt, true, m->md_scalars, energies,
+                              m->md_step, m->md_ke, m->md_done, st);
+    }
+    CK(cudaGetLastError());
+    return QNEP_OK;
+}
+
 void qnep_destroy(qnep_model* m) {
     if (!m) return;
     void* bufs[] = {m->d_params, m->pos4, m->spos4, m->sidx, m->fin_done, m->sk_done, m->fields, m->cell_of, m->cell_atoms, m->nbr_list, m->cnt_list, m->nbr_ang,
                     m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phase, m->cell_count,
                     m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_chunk_order, m->d_kg, m->d_S, m->d_C,
                     m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
-                    m->io_out[4], m->io_out[5], m->dtc};
+                    m->io_out[4], m->io_out[5], m->dtc, m->md_step, m->md_ke, m->md_done, m->md_scalars};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->h_status) cudaFreeHost(m->h_status);

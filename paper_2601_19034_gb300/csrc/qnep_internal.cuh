@@ -220,6 +220,12 @@ size_t mlp_tc_smem(int precision, int n_species);
 void launch_mlp_tc(int precision, const float* dtc, const float4* spos4, int n, const float* params,
                    const ParamLayout& lay, float* du, float* dq, int d_sa, int d_sv, float* u, float* q, Accum* acc,
                    int num_sms, cudaStream_t st);
+// Velocity-Verlet halves (md.cu); masses in amu per species.
+void launch_vv_kick_drift(int n, float* pos, float* vel, const float* f, const int* types, const float* masses,
+                          int n_species, float dt, cudaStream_t st);
+void launch_vv_kick_energy(int n, float* vel, const float* f, const int* types, const float* masses, int n_species,
+                           float dt, bool kick, const double* scalars, double* energies, int* step, double* ke_acc,
+                           unsigned int* done, cudaStream_t st);
 void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t st);
 int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc_in, float q_target, PppmTab pm,
                 float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st);

@@ -206,6 +206,28 @@ class QNEP:
         return res
 
 
+def nve(model: "QNEP", positions: torch.Tensor, velocities: torch.Tensor, types: torch.Tensor, masses, box,
+        dt_fs: float, n_steps: int, stream=None):
+    """Velocity-Verlet NVE run (positions and velocities updated in place on the device).
+
+    Returns (forces [N, 3] of the final positions, energies [n_steps + 1, 2] = (U_pot, K) in eV).
+    """
+    assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
+    assert velocities.is_cuda and velocities.dtype == torch.float32 and velocities.is_contiguous()
+    n = positions.shape[0]
+    forces = torch.empty(n, 3, dtype=torch.float32, device=positions.device)
+    energies = torch.zeros(n_steps + 1, 2, dtype=torch.float64, device=positions.device)
+    ms = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    model._set_box(box)
+    if stream is None:
+        stream = torch.cuda.current_stream(positions.device).cuda_stream
+    st = model.lib.qnep_nve_run(model.handle, n, positions.data_ptr(), velocities.data_ptr(), types.data_ptr(),
+                                ms.ctypes.data, model._box, float(dt_fs), int(n_steps), ctypes.c_void_p(stream),
+                                forces.data_ptr(), energies.data_ptr())
+    _lib.check(st, model.handle)
+    return forces, energies
+
+
 class QNEPFunction(torch.autograd.Function):
     """Differentiable qNEP force call: positions [N, 3] -> (U^tot, q^c [N], P [3]).
 

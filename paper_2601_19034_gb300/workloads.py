@@ -23,6 +23,8 @@ WATER_SPECIES = ("O", "H")
 BATIO3_SPECIES = ("Ba", "Ti", "O")
 LLZO_SPECIES = ("Li", "La", "Zr", "O")
 MGWATER_SPECIES = ("Mg", "O", "H")
+MASSES = {"H": 1.008, "O": 15.999, "Mg": 24.305, "Li": 6.94, "La": 138.905, "Zr": 91.224, "Ba": 137.327,
+          "Ti": 47.867}   # amu
 
 AVOGADRO = 6.02214076e23
 M_H2O = 18.01528  # g/mol
@@ -277,3 +279,33 @@ def config_llzo_batch(seed: int = 1003, n_struct: int = 512, n_candidates: int =
     hp = HParams(n_species=4)
     params = random_params(hp, np.random.default_rng(seed + 100), n_candidates=n_candidates)
     return systems, hp, params, Elec(mode=1, kind="ewald")
+
+
+def scale_charge_head(params: np.ndarray, hp: HParams, factor: float) -> np.ndarray:
+    """Multiply the charge output layer (w1_q and b1_q of every species) by ``factor``."""
+    p = np.array(params, dtype=np.float32, copy=True)
+    s = hp.n_species
+    mlp = s * s * (hp.n_radial * hp.basis_radial + hp.n_angular * hp.basis_angular) + hp.n_des
+    block = hp.n_neurons * hp.n_des + 3 * hp.n_neurons + 2
+    for t in range(s):
+        w1q = mlp + t * block + hp.n_neurons * hp.n_des + 2 * hp.n_neurons
+        p[..., w1q:w1q + hp.n_neurons] *= factor
+        p[..., mlp + t * block + block - 1] *= factor        # b1_q
+    return p
+
+
+def config_mg_water(seed: int = 1004, nx: int = 112, ny: int = 65, mesh=(256, 256, 384)):
+    """Mg-water interface (~1.0 M atoms at the default size), PPPM, mode 1, 3 species.
+
+    Weights N(0, 0.1) except the charge output layer, N(0, 0.01): with a full-size random
+    charge head the per-species offsets charge the slab against the water layer (about
+    100 V/A across the interface) and the NVE run is not integrable at 0.5 fs.
+    """
+    sysm = mg_water_interface(nx, ny, seed=seed)
+    hp = HParams(n_species=3)
+    params = scale_charge_head(random_params(hp, np.random.default_rng(seed + 100)), hp, 0.1)
+    return sysm, hp, params[0], Elec(mode=1, kind="pppm", mesh=tuple(mesh), order=5)
+
+
+def species_masses(species) -> np.ndarray:
+    return np.array([MASSES[s] for s in species], dtype=np.float64)

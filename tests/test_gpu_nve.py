@@ -1,0 +1,147 @@
+"""Large-scale form: velocity-Verlet NVE around the force call, Mg-water interface with PPPM.
+
+* a 3297-atom Mg-water slab (same construction as the 1 M-atom system) against the FP64
+  oracle, FP32 and BF16 network;
+* one velocity-Verlet step against the update written out in numpy;
+* energy conservation of a short NVE run;
+* the full ~1.0 M-atom system (PPPM 256 x 256 x 384): BF16 against the FP32 path
+  (force RMSE <= 5e-3 eV/A), the charge constraint, and an NVE segment.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import forcecall  # noqa: E402
+from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+ACC_UNIT = 9.6485332e-3   # (eV/A)/amu in A/fs^2
+KE_UNIT = 103.6427        # amu A^2/fs^2 in eV
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19034_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def _small():
+    """3297-atom slab of the large system's construction and parameter recipe (PPPM h ~ 1 A)."""
+    sysm = wl.mg_water_interface(6, 4, seed=77)
+    _, hp, params, _ = wl.config_mg_water(nx=6, ny=4)
+    elec = wl.Elec(mode=1, kind="pppm", mesh=(20, 24, 100), order=5)
+    return sysm, hp, params, elec
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_small_mg_water_against_oracle(dev, precision):
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
+    sysm, hp, params, elec = _small()
+    model = QNEP(hp, params, elec, precision=precision)
+    out = model.compute(torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev), sysm.box,
+                        bec=False)
+    torch.cuda.synchronize()
+    sc = parse_scalars(out["scalars"])
+    f = out["forces"].cpu().numpy()
+    q = out["charges"].cpu().numpy()
+    model.close()
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec,
+                               want_bec=False)
+    n = sysm.n_atoms
+    de = abs(sc["energy"] - ref["energy"]) / n
+    rmse = np.sqrt(((f - ref["forces"]) ** 2).mean())
+    dfmax = np.abs(f - ref["forces"]).max()
+    fmax = np.abs(ref["forces"]).max()
+    print(f"\n{precision}: dE/N {de:.3g}, U^k/N {ref['e_kspace'] / n:.3g} eV, F max diff {dfmax:.3g}, "
+          f"max|F| {fmax:.3g}, F RMSE {rmse:.3g}")
+    if precision == "fp32":
+        assert de <= 1e-6 and dfmax <= 1e-4 and np.abs(q - ref["charges"]).max() <= 2e-6, (de, dfmax)
+    else:
+        assert rmse <= 5e-3 and de <= 2e-3, (rmse, de)
+
+
+def test_velocity_verlet_step_is_the_textbook_update(dev):
+    from paper_2601_19034_gb300.qnep import QNEP, nve
+    sysm, hp, params, elec = _small()
+    masses = wl.species_masses(wl.MGWATER_SPECIES)
+    m_atom = masses[sysm.types]
+    v0 = wl.maxwell_boltzmann(m_atom, 300.0, seed=5).astype(np.float32)
+    model = QNEP(hp, params, elec)
+    pos = torch.tensor(sysm.positions, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    f0 = model.compute(pos, typ, sysm.box, bec=False)["forces"].cpu().numpy().astype(np.float64)
+    vel = torch.tensor(v0, device=dev)
+    dt = 0.5
+    f1, en = nve(model, pos, vel, typ, masses, sysm.box, dt, 1)
+    torch.cuda.synchronize()
+    a0 = f0 * ACC_UNIT / m_atom[:, None]
+    x1 = sysm.positions.astype(np.float64) + dt * (v0 + 0.5 * dt * a0)
+    np.testing.assert_allclose(pos.cpu().numpy(), x1, atol=2e-5)
+    a1 = f1.cpu().numpy().astype(np.float64) * ACC_UNIT / m_atom[:, None]
+    v1 = v0 + 0.5 * dt * (a0 + a1)
+    np.testing.assert_allclose(vel.cpu().numpy(), v1, atol=1e-6)
+    e = en.cpu().numpy()
+    k0 = 0.5 * (m_atom[:, None] * v0.astype(np.float64) ** 2).sum() * KE_UNIT
+    k1 = 0.5 * (m_atom[:, None] * v1 ** 2).sum() * KE_UNIT
+    assert abs(e[0, 1] - k0) <= 1e-5 * k0 and abs(e[1, 1] - k1) <= 1e-5 * k1
+    model.close()
+
+
+def test_nve_energy_conservation_small(dev):
+    from paper_2601_19034_gb300.qnep import QNEP, nve
+    sysm, hp, params, elec = _small()
+    masses = wl.species_masses(wl.MGWATER_SPECIES)
+    v0 = wl.maxwell_boltzmann(masses[sysm.types], 300.0, seed=6).astype(np.float32)
+    model = QNEP(hp, params, elec, precision="bf16")
+    pos = torch.tensor(sysm.positions, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    _, en = nve(model, pos, vel, typ, masses, sysm.box, 0.5, 200)
+    assert model.sync_status() == 0
+    e = en.cpu().numpy()
+    etot = e.sum(1)
+    assert np.isfinite(etot).all()
+    n = sysm.n_atoms
+    t = np.arange(len(etot)) * 0.5e-3                       # ps
+    slope = np.polyfit(t, (etot - etot[0]) / n, 1)[0] * 1e3  # meV/atom/ps
+    print(f"\nNVE 3297 atoms, 200 x 0.5 fs: drift {slope:.3g} meV/atom/ps, "
+          f"max |dE|/N {np.abs(etot - etot[0]).max() / n:.3g} eV, K0/N {e[0, 1] / n:.4f} eV")
+    assert np.abs(etot - etot[0]).max() / n <= 2e-3
+    model.close()
+
+
+def test_full_size_mg_water(dev):
+    """~1.0 M atoms, PPPM 256 x 256 x 384: mixed vs FP32 forces, charge constraint, NVE segment."""
+    from paper_2601_19034_gb300.qnep import QNEP, nve, parse_scalars
+    sysm, hp, params, elec = wl.config_mg_water()
+    assert 0.98e6 <= sysm.n_atoms <= 1.02e6
+    pos = torch.tensor(sysm.positions, device=dev)
+    typ = torch.tensor(sysm.types, device=dev)
+    res = {}
+    for prec in ("fp32", "bf16"):
+        model = QNEP(hp, params, elec, precision=prec)
+        out = model.compute(pos, typ, sysm.box, bec=False)
+        torch.cuda.synchronize()
+        res[prec] = (out["forces"].clone(), parse_scalars(out["scalars"]), out["charges"].clone())
+        model.close()
+    f32, s32, q32 = res["fp32"]
+    fbf, sbf, _ = res["bf16"]
+    rmse = torch.sqrt(((fbf - f32) ** 2).mean()).item()
+    assert rmse <= 5e-3, rmse
+    assert abs(sbf["energy"] - s32["energy"]) / sysm.n_atoms <= 2e-3
+    assert abs(q32.double().sum().item() - 0.0) <= 1e-3                # Q = 0
+    assert torch.isfinite(f32).all()
+    masses = wl.species_masses(wl.MGWATER_SPECIES)
+    vel = torch.tensor(wl.maxwell_boltzmann(masses[sysm.types], 300.0).astype(np.float32), device=dev)
+    model = QNEP(hp, params, elec, precision="bf16")
+    _, en = nve(model, pos, vel, typ, masses, sysm.box, 0.5, 10)
+    assert model.sync_status() == 0
+    e = en.cpu().numpy()
+    assert np.isfinite(e).all()
+    assert np.abs(e.sum(1) - e[0].sum()).max() / sysm.n_atoms <= 1e-3
+    model.close()
