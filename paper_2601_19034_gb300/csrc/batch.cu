@@ -26,6 +26,7 @@
 #include "batch_internal.cuh"
 #include "desc_math.cuh"
 #include "nbr_common.cuh"
+#include "tma.cuh"
 
 namespace qnep {
 
@@ -40,14 +41,17 @@ constexpr int PREP_THREADS = 256;
 //   basis sums  (per atom): B^R[t][k] (padded to MAX_SPECIES species) | B^A[t][k][lm]
 // with B(r) = k_e erfc(alpha r) / r.  Rows are copied into shared memory (float4) by the item kernel.
 constexpr int GR = 20, GR_DF = 0, GR_U = 9, GR_JD = 12, GR_B = 13, GR_BU = 14, GR_JR = 17;
+static_assert(GR_JD == 12 && GR_B == 13 && GR_BU == 14 && GR_JR == 17, "float4 row reads assume this layout");
 constexpr int GA = 48, GA_F = 0, GA_DF = 9, GA_U = 18, GA_IR = 21, GA_J = 22, GA_Y = 24;
+static_assert(GA_DF == 9 && GA_U == 18 && GA_Y == 24, "float4 row reads assume this layout");
 constexpr int TAB_P = KA + NLM;                // pre-pass staging row: f_k, Y_lm
-// per-warp shared memory of the item kernel
-constexpr int WT_FLOATS = 32 * GA;             // staged rows (32 angular or radial entries)
-constexpr int WBR = WT_FLOATS;                 // B^R [MAX_SPECIES][KR]
-constexpr int WBA = WBR + MAX_SPECIES * KR;    // B^A [S][KA][NLM] (16-byte aligned)
-constexpr int WCUM = WBA + MAX_SPECIES * KA * NLM;   // cumulative species counts (ints)
+// per-warp shared memory of the item kernel: two row buffers (double-buffered bulk copies of
+// 32 pair rows, or of one atom's basis sums) and the cumulative species counts
+constexpr int WBUF = 32 * GA;                  // floats per buffer
+constexpr int WCUM = 2 * WBUF;                 // ints
 constexpr int WARP_FLOATS = WCUM + 16;
+constexpr int BS_MAX = MAX_SPECIES * KR + MAX_SPECIES * KA * NLM;   // basis-sum floats per atom
+static_assert(BS_MAX <= WBUF, "basis sums fit a row buffer");
 constexpr int PR_R = 0;                                  // c^R[t_i] staged [S][NR][KR][CG]
 constexpr int PR_A = MAX_SPECIES * NR * KR * CG;         // c^A[t_i] staged [S][NA][KA][CG]
 constexpr int PR_S = PR_A + MAX_SPECIES * NA * KA * CG;  // descriptor scaler [NDES][CG]
@@ -57,7 +61,7 @@ constexpr int FLUSH_TILES = 8;                 // FP32 partial sums cover 512 at
 constexpr int KW = 64;                         // wave vectors per staged window of the field pass
 constexpr int NSUMS = 6;                       // per-candidate FP64 sums
 
-static_assert(WBA % 4 == 0 && WARP_FLOATS % 4 == 0 && PARAM_FLOATS % 4 == 0, "float4 alignment");
+static_assert(WBUF % 4 == 0 && WARP_FLOATS % 4 == 0 && PARAM_FLOATS % 4 == 0, "float4 alignment");
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -417,6 +421,38 @@ __device__ __forceinline__ void species_cum(const BatchArgs& a, int off, int n, 
     __syncwarp();
 }
 
+// One bulk copy global -> shared of `bytes` (multiple of 16, both ends 16-byte aligned) into a
+// warp's buffer, completing on `bar` (issued by one lane, after the warp's last read of `dst`).
+__device__ __forceinline__ void warp_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(dst, src, bytes, bar);
+}
+
+// Wait for buffer b of a warp (parity bit b of par); false after the bounded wait gave up.
+__device__ __forceinline__ bool warp_wait(uint64_t* bars, int b, uint32_t& par, unsigned int* status) {
+    const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+    par ^= 1u << b;
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, kStatusTimeout);
+    return ok;
+}
+
+// Chunk jobs of an atom's backward: kind 0 = radial rows of neighbour species tj from row base
+// (at most 32), kind 1 = angular rows from base (at most 32), kind 2 = done.
+__device__ __forceinline__ void job_settle(const int* cum, int S, int& kind, int& tj, int& base) {
+    if (kind == 0) {
+        while (tj < S && base >= cum[tj + 1]) {
+            ++tj;
+            if (tj < S) base = cum[tj];
+        }
+        if (tj >= S) {
+            kind = 1;
+            base = 0;
+        }
+    }
+    if (kind == 1 && base >= cum[8 + S]) kind = 2;
+}
+
 template <int NW>
 __device__ __forceinline__ void block_sum(double v, double* red, double* dst) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -435,18 +471,12 @@ __device__ __forceinline__ void block_sum(double v, double* red, double* dst) {
 // scaled descriptor to rows 0..NDES-1 of the atom's duq block (replaced by dU/dD in the
 // network pass).
 __device__ __forceinline__ void descriptor_atom(const BatchArgs& a, const BatchStruct& bs, int m,
-                                                const float* __restrict__ prm, float* __restrict__ wb,
+                                                const float* __restrict__ prm, const float* __restrict__ bsb,
                                                 float* __restrict__ A, float* __restrict__ duq) {
     const int lane = threadIdx.x & 31;
-    const int S = a.lay.n_species, off = bs.atom_off;
-    float* br = wb + WBR;
-    float* ba = wb + WBA;
-    {
-        const float4* src = reinterpret_cast<const float4*>(a.bsum + (size_t)(off + m) * a.bstride);
-        float4* dst = reinterpret_cast<float4*>(br);
-        for (int i = lane; i < (a.bstride >> 2); i += 32) dst[i] = __ldg(&src[i]);
-    }
-    __syncwarp();
+    const int S = a.lay.n_species;
+    const float* br = bsb;                       // B^R [MAX_SPECIES][KR]
+    const float* ba = bsb + MAX_SPECIES * KR;    // B^A [S][KA][NLM]
 
     // lane = candidate: contractions with this candidate's c^R, c^A
     float d[NDES];
@@ -614,19 +644,32 @@ __device__ __forceinline__ void stage_network(const float* __restrict__ pg, cons
     }
 }
 
-// Backward of sorted atom m (species ti): partial forces of every list entry.
+// Backward of sorted atom m: partial forces of every list entry (Sec. II.C).  The atom's
+// pair rows arrive in 32-row pieces by double-buffered bulk copies: the copy of the next
+// piece is in flight while the current one is used.
 __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStruct& bs, int m,
                                               const float* __restrict__ prm, float* __restrict__ wb,
-                                              const float* __restrict__ A, const float* __restrict__ duq,
-                                              const float* __restrict__ qcs, const float4* __restrict__ fk,
-                                              const float4* __restrict__ fr, float4* __restrict__ fsum, int nmax,
-                                              float selfc, float phibar) {
+                                              uint64_t* bars, uint32_t& par, const float* __restrict__ A,
+                                              const float* __restrict__ duq, const float* __restrict__ qcs,
+                                              const float4* __restrict__ fk, const float4* __restrict__ fr,
+                                              float4* __restrict__ fsum, int nmax, float selfc, float phibar) {
     const int lane = threadIdx.x & 31;
     const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
-    float* tab = wb;
     int* cum = reinterpret_cast<int*>(wb + WCUM);
     species_cum(a, off, n, m, S, cum);
-    const int tot_l = cum[S], tot_a = cum[8 + S];
+    const int tot_a = cum[8 + S];
+    const float* rad_src = a.geo_rad + (size_t)(off + m) * a.cap_l * GR;
+    const float* ang_src = a.geo_ang + (size_t)(off + m) * a.cap_a * GA;
+    // first job and its copy
+    int kind = 0, tj = 0, base = 0;
+    job_settle(cum, S, kind, tj, base);
+    int b = 0;
+    if (kind != 2 && lane == 0) {
+        const int cnt = kind == 0 ? min(32, cum[tj + 1] - base) : min(32, tot_a - base);
+        warp_bulk(wb, kind == 0 ? rad_src + (size_t)base * GR : ang_src + (size_t)base * GA,
+                  (uint32_t)(cnt * (kind == 0 ? GR : GA) * 4), &bars[0]);
+    }
+
     const float qc = qcs[(size_t)m * CG + lane];
     const float4 kf = fk[(size_t)lane * nmax + m];
     const float4 rf = fr[(size_t)m * CG + lane];
@@ -635,47 +678,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
     const float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
 #pragma unroll
     for (int v = 0; v < NDES; ++v) lam[v] = fmaf(wq, dd[(NDES + v) * CG], dd[v * CG]);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-
-    // radial: F_ij = (sum_k mu_k f'_k(r)) u with mu_k = sum_n lambda_n c^R[t_i][t_j][n][k]
-    const float4* grows = reinterpret_cast<const float4*>(a.geo_rad + (size_t)(off + m) * a.cap_l * GR);
-    for (int base = 0; base < tot_l; base += 32) {
-        const int cntc = min(32, tot_l - base);
-        {
-            float4* t4 = reinterpret_cast<float4*>(tab);
-            const float4* s4 = grows + (size_t)base * (GR / 4);
-            for (int i = lane; i < cntc * (GR / 4); i += 32) t4[i] = __ldg(&s4[i]);
-        }
-        __syncwarp();
-        for (int tj = 0; tj < S; ++tj) {
-            const int lo = max(cum[tj] - base, 0), hi = min(cum[tj + 1] - base, cntc);
-            if (lo >= hi) continue;
-            float mu[KR];
-#pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                float x = 0.f;
-#pragma unroll
-                for (int q = 0; q < NR; ++q) x = fmaf(lam[q], prm[PR_R + ((tj * NR + q) * KR + k) * CG + lane], x);
-                mu[k] = x;
-            }
-            for (int r = lo; r < hi; ++r) {
-                const float* rw = tab + r * GR;
-                const int j = __float_as_int(rw[GR_JD]);
-                if (j < 0) continue;
-                float sv = 0.f;
-#pragma unroll
-                for (int k = 0; k < KR; ++k) sv = fmaf(mu[k], rw[GR_DF + k], sv);
-                const float Fx = sv * rw[GR_U], Fy = sv * rw[GR_U + 1], Fz = sv * rw[GR_U + 2];
-                fx += Fx;
-                fy += Fy;
-                fz += Fz;
-                atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
-            }
-        }
-        __syncwarp();
-    }
-
-    // angular: Phi_{n,lm} = d(lambda . D)/dA_{n,lm}
+    // Phi_{n,lm} = d(lambda . D)/dA_{n,lm}
     float Phi[NA][NLM];
     const float* Ai = A + (size_t)m * NANG * CG + lane;
 #pragma unroll
@@ -697,65 +700,121 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
         Phi[q][6] = fmaf(l4, 1.5f * (t2[0] - t2[1]), Phi[q][6]);
         Phi[q][7] = fmaf(l4, 6.f * t2[3], Phi[q][7]);
     }
-    const float4* arows = reinterpret_cast<const float4*>(a.geo_ang + (size_t)(off + m) * a.cap_a * GA);
-    for (int base = 0; base < tot_a; base += 32) {
-        {
-            const int cnt = min(32, tot_a - base);
-            float4* t4 = reinterpret_cast<float4*>(tab);
-            const float4* s4 = arows + (size_t)base * (GA / 4);
-            for (int i = lane; i < cnt * (GA / 4); i += 32) t4[i] = __ldg(&s4[i]);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float mu[KR];
+    int mu_tj = -1;
+    while (kind != 2) {
+        int k2 = kind, t2 = tj, b2 = base + 32;
+        job_settle(cum, S, k2, t2, b2);
+        __syncwarp();   // every lane is done with the other buffer (previous piece)
+        if (k2 != 2 && lane == 0) {
+            const int cnt = k2 == 0 ? min(32, cum[t2 + 1] - b2) : min(32, tot_a - b2);
+            warp_bulk(b ? wb : wb + WBUF, k2 == 0 ? rad_src + (size_t)b2 * GR : ang_src + (size_t)b2 * GA,
+                      (uint32_t)(cnt * (k2 == 0 ? GR : GA) * 4), &bars[b ^ 1]);
         }
-        __syncwarp();
-        const int cntc = min(32, tot_a - base);
-        for (int tj = 0; tj < S; ++tj) {
-            const int lo = max(cum[8 + tj] - base, 0), hi = min(cum[8 + tj + 1] - base, cntc);
-            const float* cA = prm + PR_A + tj * NA * KA * CG + lane;
-            for (int r = lo; r < hi; ++r) {
-                const float* rw = tab + r * GA;
-                float gn[NA], dgn[NA];
+        const bool ok = warp_wait(bars, b, par, a.status);
+        const float* rows = b ? wb + WBUF : wb;
+        if (ok && kind == 0) {
+            // radial: F_ij = (sum_k mu_k f'_k(r)) u, mu_k = sum_n lambda_n c^R[t_i][t_j][n][k]
+            if (tj != mu_tj) {
 #pragma unroll
-                for (int q = 0; q < NA; ++q) {
-                    float x = 0.f, y = 0.f;
+                for (int k = 0; k < KR; ++k) {
+                    float x = 0.f;
 #pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        const float c = cA[(q * KA + k) * CG];
-                        x = fmaf(c, rw[GA_F + k], x);
-                        y = fmaf(c, rw[GA_DF + k], y);
-                    }
-                    gn[q] = x;
-                    dgn[q] = y;
+                    for (int q = 0; q < NR; ++q) x = fmaf(lam[q], prm[PR_R + ((tj * NR + q) * KR + k) * CG + lane], x);
+                    mu[k] = x;
                 }
-                float psi[NLM];
-#pragma unroll
-                for (int M = 0; M < NLM; ++M) psi[M] = 0.f;
-                float rho = 0.f;
-#pragma unroll
-                for (int q = 0; q < NA; ++q) {
-                    float pq = 0.f;
-#pragma unroll
-                    for (int M = 0; M < NLM; ++M) {
-                        pq = fmaf(Phi[q][M], rw[GA_Y + M], pq);
-                        psi[M] = fmaf(gn[q], Phi[q][M], psi[M]);
-                    }
-                    rho = fmaf(dgn[q], pq, rho);
-                }
-                const float ux = rw[GA_U], uy = rw[GA_U + 1], uz = rw[GA_U + 2];
-                const float ir = rw[GA_IR];
-                float gx, gy, gz;
-                harmonics_grad(ux, uy, uz, psi, gx, gy, gz);
-                const float gu = gx * ux + gy * uy + gz * uz;
-                const float Fx = rho * ux + (gx - gu * ux) * ir;
-                const float Fy = rho * uy + (gy - gu * uy) * ir;
-                const float Fz = rho * uz + (gz - gu * uz) * ir;
+                mu_tj = tj;
+            }
+            const int cntc = min(32, cum[tj + 1] - base);
+            for (int r = 0; r < cntc; ++r) {
+                const float4* rw = reinterpret_cast<const float4*>(rows + r * GR);
+                const float4 d0 = rw[0], d1 = rw[1], d2 = rw[2], d3 = rw[3];   // f'_0..8 | u | j
+                const int j = __float_as_int(d3.x);
+                if (j < 0) continue;
+                float sv = mu[0] * d0.x;
+                sv = fmaf(mu[1], d0.y, sv);
+                sv = fmaf(mu[2], d0.z, sv);
+                sv = fmaf(mu[3], d0.w, sv);
+                sv = fmaf(mu[4], d1.x, sv);
+                sv = fmaf(mu[5], d1.y, sv);
+                sv = fmaf(mu[6], d1.z, sv);
+                sv = fmaf(mu[7], d1.w, sv);
+                sv = fmaf(mu[8], d2.x, sv);
+                const float Fx = sv * d2.y, Fy = sv * d2.z, Fz = sv * d2.w;
                 fx += Fx;
                 fy += Fy;
                 fz += Fz;
-                const int j = __float_as_int(rw[GA_J]);
                 atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
             }
+        } else if (ok) {
+            // angular: per entry the contraction of Phi with d(g_n Y_lm)/dr_ij
+            const int cntc = min(32, tot_a - base);
+            for (int t = 0; t < S; ++t) {
+                const int lo = max(cum[8 + t] - base, 0), hi = min(cum[8 + t + 1] - base, cntc);
+                const float* cA = prm + PR_A + t * NA * KA * CG + lane;
+                for (int r = lo; r < hi; ++r) {
+                    // row: f_0..8 | f'_0..8 | u | 1/r | j | pad | Y_lm (GA = 48 floats, 16-byte aligned)
+                    const float4* r4 = reinterpret_cast<const float4*>(rows + r * GA);
+                    const float4 a0 = r4[0], a1 = r4[1], a2 = r4[2], a3 = r4[3], a4 = r4[4], a5 = r4[5];
+                    const float fv[KA] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x};
+                    const float dfv[KA] = {a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w, a4.x, a4.y};
+                    float gn[NA], dgn[NA];
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) {
+                        float x = 0.f, y = 0.f;
+#pragma unroll
+                        for (int k = 0; k < KA; ++k) {
+                            const float c = cA[(q * KA + k) * CG];
+                            x = fmaf(c, fv[k], x);
+                            y = fmaf(c, dfv[k], y);
+                        }
+                        gn[q] = x;
+                        dgn[q] = y;
+                    }
+                    float Y[NLM];
+#pragma unroll
+                    for (int g4 = 0; g4 < NLM / 4; ++g4) {
+                        const float4 yv = r4[6 + g4];
+                        Y[4 * g4] = yv.x;
+                        Y[4 * g4 + 1] = yv.y;
+                        Y[4 * g4 + 2] = yv.z;
+                        Y[4 * g4 + 3] = yv.w;
+                    }
+                    float psi[NLM];
+#pragma unroll
+                    for (int M = 0; M < NLM; ++M) psi[M] = 0.f;
+                    float rho = 0.f;
+#pragma unroll
+                    for (int q = 0; q < NA; ++q) {
+                        float pq = 0.f;
+#pragma unroll
+                        for (int M = 0; M < NLM; ++M) {
+                            pq = fmaf(Phi[q][M], Y[M], pq);
+                            psi[M] = fmaf(gn[q], Phi[q][M], psi[M]);
+                        }
+                        rho = fmaf(dgn[q], pq, rho);
+                    }
+                    const float ux = a4.z, uy = a4.w, uz = a5.x, ir = a5.y;
+                    float gx, gy, gz;
+                    harmonics_grad(ux, uy, uz, psi, gx, gy, gz);
+                    const float gu = gx * ux + gy * uy + gz * uz;
+                    const float Fx = rho * ux + (gx - gu * ux) * ir;
+                    const float Fy = rho * uy + (gy - gu * uy) * ir;
+                    const float Fz = rho * uz + (gz - gu * uz) * ir;
+                    fx += Fx;
+                    fy += Fy;
+                    fz += Fz;
+                    atomicAdd(&fsum[(size_t)__float_as_int(a5.z) * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
+                }
+            }
         }
-        __syncwarp();
+        kind = k2;
+        tj = t2;
+        base = b2;
+        b ^= 1;
     }
+    __syncwarp();   // buffers and counts are reused by the warp's next atom
     // own force: network part plus the static electrostatic forces q F^k/q + F^r
     atomicAdd(&fsum[(size_t)m * CG + lane],
               make_float4(fx + fmaf(qc, kf.y, rf.y), fy + fmaf(qc, kf.z, rf.z), fz + fmaf(qc, kf.w, rf.w), 0.f));
@@ -765,7 +824,14 @@ template <int NW>
 __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ int s_item;
+    __shared__ __align__(8) uint64_t wbars[NW][2];   // per-warp barriers of the two row buffers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        mbar_init(&wbars[warp][0], 1);
+        mbar_init(&wbars[warp][1], 1);
+        mbar_init_fence();
+    }
+    uint32_t par = 0;   // phase bits of this warp's two buffers
     double* red = reinterpret_cast<double*>(bsm);     // [NW][CG]
     double* sums = red + NW * CG;                      // [NSUMS][CG]
     float* cst = reinterpret_cast<float*>(sums + NSUMS * CG);   // delta, phibar, q_target, pad [4][CG]
@@ -808,7 +874,20 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             stage_params(pg, a.lay, ti, un);
             __syncthreads();
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
-            for (int p = p0 + warp; p < p1; p += NW) descriptor_atom(a, bs, a.order[off + p], un, wb, A, duq);
+            // basis sums of the warp's atoms by double-buffered bulk copies
+            const uint32_t bs_bytes = (uint32_t)a.bstride * 4u;
+            int bsel = 0;
+            if (p0 + warp < p1 && lane == 0)
+                warp_bulk(wb, a.bsum + (size_t)(off + a.order[off + p0 + warp]) * a.bstride, bs_bytes, &wbars[warp][0]);
+            for (int p = p0 + warp; p < p1; p += NW) {
+                __syncwarp();
+                if (p + NW < p1 && lane == 0)
+                    warp_bulk(bsel ? wb : wb + WBUF, a.bsum + (size_t)(off + a.order[off + p + NW]) * a.bstride,
+                              bs_bytes, &wbars[warp][bsel ^ 1]);
+                warp_wait(wbars[warp], bsel, par, a.status);
+                descriptor_atom(a, bs, a.order[off + p], un, bsel ? wb + WBUF : wb, A, duq);
+                bsel ^= 1;
+            }
             __syncthreads();
             stage_network(pg, a.lay, ti, un);
             __syncthreads();
@@ -1050,14 +1129,15 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         }
                         __syncwarp();
                         for (int r = 0; r < cntc; ++r) {
-                            const float* rw = tab + r * GR;
-                            const int j = __float_as_int(rw[GR_JR]);
+                            const float4* rw = reinterpret_cast<const float4*>(tab + r * GR);
+                            const float4 d3 = rw[3], d4 = rw[4];   // (j_desc, B, B'u_x, B'u_y), (B'u_z, j_real, -, -)
+                            const int j = __float_as_int(d4.y);
                             if (j < 0) continue;
                             const float qj = qcs[(size_t)j * CG + lane];
-                            ph = fmaf(qj, rw[GR_B], ph);
-                            gx = fmaf(qj, rw[GR_BU], gx);
-                            gy = fmaf(qj, rw[GR_BU + 1], gy);
-                            gz = fmaf(qj, rw[GR_BU + 2], gz);
+                            ph = fmaf(qj, d3.y, ph);
+                            gx = fmaf(qj, d3.z, gx);
+                            gy = fmaf(qj, d3.w, gy);
+                            gz = fmaf(qj, d4.x, gz);
                         }
                         __syncwarp();
                     }
@@ -1088,7 +1168,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
             const float phibar = cst[CG + lane];
             for (int p = p0 + warp; p < p1; p += NW)
-                backward_atom(a, bs, a.order[off + p], un, wb, A, duq, qcs, fk, fr, fsum, nmax, selfc, phibar);
+                backward_atom(a, bs, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum, nmax,
+                              selfc, phibar);
         }
         __syncthreads();
 
