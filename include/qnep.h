@@ -185,9 +185,10 @@ qnep_status qnep_sync_status(qnep_model* m, void* stream);
 /* Change the neighbour-list capacities (entries per atom); 0 keeps the value. */
 qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
 
-/* Kernel family for the per-atom stages: QNEP_PATH_AUTO picks warp-per-atom
- * kernels up to 65536 atoms and thread-per-atom kernels above; the others force
- * one family (both compute the same quantities).  Used by the tuner and tests. */
+/* Kernel family for the per-atom stages: QNEP_PATH_AUTO picks the warp-per-atom
+ * kernels (the faster family at every size measured, 40 atoms to 1 M atoms);
+ * QNEP_PATH_WARP / QNEP_PATH_THREAD force one family (both compute the same
+ * quantities).  Used by the tests and for comparisons. */
 enum { QNEP_PATH_AUTO = 0, QNEP_PATH_WARP = 1, QNEP_PATH_THREAD = 2 };
 qnep_status qnep_set_path(qnep_model* m, int path);
 
