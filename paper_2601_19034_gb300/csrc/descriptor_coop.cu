@@ -299,53 +299,78 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
         const float4 pk = __ldg(&spos4[k]);
         const int ti = __float_as_int(pk.w);
         const float seps = sp[lay.sqrt_eps];
+        // every global load of the prologue is issued first (they are independent), then the
+        // arithmetic; adjoints travel between lanes by shuffles
+        const float duv = lane < NDES ? __ldg(&du[(size_t)k * NDES + lane]) : 0.f;
+        const float dqv = lane < NDES ? __ldg(&dqp[(size_t)k * NDES + lane]) : 0.f;
+        float av[4];
+#pragma unroll
+        for (int s4 = 0; s4 < 4; ++s4) {
+            const int el = lane + 32 * s4;
+            av[s4] = el < NANG ? __ldg(&ang_coef[(size_t)k * NANG + el]) : 0.f;
+        }
+        // lanes q < NA: the l = 2 coefficients of radial function q and the 4-body derivatives
+        float dd4[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (lane < NA) {
+            float a2[5], t[6], t2[6];
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) a2[kk] = __ldg(&ang_coef[(size_t)k * NANG + lane * NLM + 3 + kk]);
+            tensor_from_a(a2, t);
+            tensor_square(t, t2);
+            dd4[0] = 3.f * (t2[2] * (1.f / 3.f) - (t2[0] + t2[1]) * (1.f / 6.f));
+            dd4[1] = 6.f * t2[4];
+            dd4[2] = 6.f * t2[5];
+            dd4[3] = 1.5f * (t2[0] - t2[1]);
+            dd4[4] = 6.f * t2[3];
+        }
         float qc, phi_k, phibar;
         assemble_potential(fin, acc_in, q_raw, k, n, qc, phi_k, phibar);
         const float wq = charge_adjoint_weight(fin, acc_in, k, n, phi_k - phibar);
-        if (lane < NDES) {
-            float gq = __ldg(&dqp[(size_t)k * NDES + lane]);
-            lk[lane] = fmaf(wq, gq, fin.e_weight * __ldg(&du[(size_t)k * NDES + lane]));
-            lk[32 + lane] = seps * gq;
-        }
-        __syncwarp();
+        const float lkl = fmaf(wq, dqv, fin.e_weight * duv);   // lambda_v in lane v
+        const float lkk = seps * dqv;                         // kappa_v in lane v
         // dE/dA_{n,lm} for both adjoints
 #pragma unroll
         for (int s4 = 0; s4 < 4; ++s4) {
             const int el = lane + 32 * s4;
-            if (el < NANG) {
-                const int q = el / NLM, m = el - q * NLM;
-                const int l = m < 3 ? 1 : (m < 8 ? 2 : (m < 15 ? 3 : 4));
-                const float a = __ldg(&ang_coef[(size_t)k * NANG + el]);
-                const int dl = NR + (l - 1) * NA + q;
-                float pl = 2.f * c_wlm[m] * a * lk[dl];
-                float pkk = 2.f * c_wlm[m] * a * lk[32 + dl];
-                if (l == 2) {
-                    float a2[5], t[6], t2[6];
+            const int q = el / NLM, m = el - q * NLM;
+            const int l = m < 3 ? 1 : (m < 8 ? 2 : (m < 15 ? 3 : 4));
+            const int dl = min(NR + (l - 1) * NA + q, 31);
+            const float ldl = __shfl_sync(0xffffffffu, lkl, dl);
+            const float kdl = __shfl_sync(0xffffffffu, lkk, dl);
+            const int d4 = min(NR + 4 * NA + q, 31);
+            const float l4 = __shfl_sync(0xffffffffu, lkl, d4);
+            const float k4 = __shfl_sync(0xffffffffu, lkk, d4);
+            const int qs = min(q, NA - 1);
+            float dd = 0.f;
 #pragma unroll
-                    for (int kk = 0; kk < 5; ++kk) a2[kk] = __ldg(&ang_coef[(size_t)k * NANG + q * NLM + 3 + kk]);
-                    tensor_from_a(a2, t);
-                    tensor_square(t, t2);
-                    float dd;
-                    if (m == 3) dd = 3.f * (t2[2] * (1.f / 3.f) - (t2[0] + t2[1]) * (1.f / 6.f));
-                    else if (m == 4) dd = 6.f * t2[4];
-                    else if (m == 5) dd = 6.f * t2[5];
-                    else if (m == 6) dd = 1.5f * (t2[0] - t2[1]);
-                    else dd = 6.f * t2[3];
-                    const int d4 = NR + 4 * NA + q;
-                    pl = fmaf(lk[d4], dd, pl);
-                    pkk = fmaf(lk[32 + d4], dd, pkk);
+            for (int kk = 0; kk < 5; ++kk) {
+                const float v = __shfl_sync(0xffffffffu, dd4[kk], qs);
+                if (m == 3 + kk) dd = v;
+            }
+            if (el < NANG) {
+                float pl = 2.f * c_wlm[m] * av[s4] * ldl;
+                float pkk = 2.f * c_wlm[m] * av[s4] * kdl;
+                if (l == 2) {
+                    pl = fmaf(l4, dd, pl);
+                    pkk = fmaf(k4, dd, pkk);
                 }
                 ph[el] = pl;
                 ph[NANG + el] = pkk;
             }
         }
         // radial contractions mu[which][s][k] = sum_n adjoint_n c_R[ti][s][n][k]
+        float lr[NR], kr[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            lr[q] = __shfl_sync(0xffffffffu, lkl, q);
+            kr[q] = __shfl_sync(0xffffffffu, lkk, q);
+        }
         for (int idx = lane; idx < 2 * S * KR; idx += 32) {
             const int which = idx / (S * KR), rem = idx - which * S * KR, s = rem / KR, kk = rem - s * KR;
             const float* c = sp + lay.c_radial + ((ti * S + s) * NR) * KR;
             float x = 0.f;
 #pragma unroll
-            for (int q = 0; q < NR; ++q) x = fmaf(lk[which * 32 + q], c[q * KR + kk], x);
+            for (int q = 0; q < NR; ++q) x = fmaf(which ? kr[q] : lr[q], c[q * KR + kk], x);
             mu[(which * MAX_SPECIES + s) * KR + kk] = x;
         }
         __syncwarp();
