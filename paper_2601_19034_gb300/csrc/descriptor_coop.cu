@@ -384,14 +384,14 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
             tot_a += __ldg(&cnt_ang[(size_t)s * n + k]);
         }
         const float rcr2 = g.rc_radial * g.rc_radial;
-        for (int e = lane; e < tot_l; e += 32) {
-            const int ent = __ldg(&nbr_list[(size_t)k * g.list_sa + e]);
-            const int j = entry_index(ent);
-            float vx, vy, vz;
-            entry_vector(spos4, ent, pk, g, vx, vy, vz);
-            float r2 = vx * vx + vy * vy + vz * vz;
+        auto radial_entry = [&](int ent, const float4& pj) {
+            float tx, ty, tz;
+            entry_shift(ent, tx, ty, tz);
+            const float vx = (pj.x - pk.x) + tx * g.L[0], vy = (pj.y - pk.y) + ty * g.L[1],
+                        vz = (pj.z - pk.z) + tz * g.L[2];
+            const float r2 = vx * vx + vy * vy + vz * vz;
             if (r2 < rcr2) {
-                const int tj = __float_as_int(__ldg(&spos4[j]).w);
+                const int tj = __float_as_int(pj.w);
                 float r = sqrtf(r2), f[KR], df[KR];
                 basis_d<KR>(r, g.rc_radial, f, df);
                 const float* ml = mu + tj * KR;
@@ -403,9 +403,21 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
                     skk = fmaf(mk[kk], df[kk], skk);
                 }
                 float ir = 1.f / r, ux = vx * ir, uy = vy * ir, uz = vz * ir;
-                scatter_entry<BEC>(acc12, j, vx, vy, vz, sl * ux, sl * uy, sl * uz, skk * ux, skk * uy, skk * uz, fi,
-                                   zi, w);
+                scatter_entry<BEC>(acc12, entry_index(ent), vx, vy, vz, sl * ux, sl * uy, sl * uz, skk * ux,
+                                   skk * uy, skk * uz, fi, zi, w);
             }
+        };
+        // two rounds of entries per iteration: both entries and both positions are loaded
+        // before either is used
+        for (int e0 = lane; e0 < tot_l; e0 += 64) {
+            const int e1 = e0 + 32;
+            const bool has1 = e1 < tot_l;
+            const int ent0 = __ldg(&nbr_list[(size_t)k * g.list_sa + e0]);
+            const int ent1 = has1 ? __ldg(&nbr_list[(size_t)k * g.list_sa + e1]) : ent0;
+            const float4 p0 = __ldg(&spos4[entry_index(ent0)]);
+            const float4 p1 = __ldg(&spos4[entry_index(ent1)]);
+            radial_entry(ent0, p0);
+            if (has1) radial_entry(ent1, p1);
         }
         for (int e = lane; e < tot_a; e += 32) {
             const int ent = __ldg(&nbr_ang[(size_t)k * g.ang_sa + e]);

@@ -14,10 +14,11 @@ __device__ __forceinline__ int nbr_cell_coord(float x, float invL, int nc) {
 // Build the lists of sorted atom k (position pk) into shared memory.
 //   sl / slt: list entries (index | image code << 26) and neighbour species, capacity cap_l
 //   sa / sat: angular entries and species, capacity cap_a
-// The 27 stencil cells are visited in order; lanes test the atoms of one cell
-// (32 at a time) and a ballot compacts the accepted ones.  nl / na return the
-// number of entries stored (clamped to the capacities); the return value is true
-// when a capacity was exceeded.  Whole warp only.
+// The candidates of the 27 stencil cells (visited in order, atoms in cell order) form one
+// index space scanned 32 at a time: lane t finds its cell by a binary search over the
+// cells' prefix counts (shuffles), tests its candidate, and a ballot compacts the accepted
+// ones.  nl / na return the number of entries stored (clamped to the capacities); the return
+// value is true when a capacity was exceeded.  Whole warp only.
 __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos4, const int* __restrict__ cell_start,
                                                  int k, float4 pk, const Geom& g, int cap_l, int cap_a, int* sl,
                                                  int* slt, int* sa, int* sat, int& nl, int& na) {
@@ -43,48 +44,64 @@ __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos
         ty = tt[1] * g.L[1];
         tz = tt[2] * g.L[2];
     }
+    // inclusive prefix counts over the 27 cells (lanes 27..31 add nothing)
+    int incl = ccnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - ccnt;
     const float rl2 = g.rc_list * g.rc_list;
     const float ra2 = g.rc_angular * g.rc_angular;
     const unsigned below = (1u << lane) - 1u;
     int cl = 0, ca = 0;
-    for (int s = 0; s < 27; ++s) {
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        // cell of candidate t: the last cell s with excl[s] <= t (binary search over lanes 0..26)
+        int s = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = s + step;
+            const int ex = __shfl_sync(0xffffffffu, excl, probe < 27 ? probe : 26);
+            if (probe < 27 && ex <= t) s = probe;
+        }
         const int c0 = __shfl_sync(0xffffffffu, cstart, s);
-        const int cn = __shfl_sync(0xffffffffu, ccnt, s);
+        const int e0 = __shfl_sync(0xffffffffu, excl, s);
         const int cd = __shfl_sync(0xffffffffu, code, s);
         const float sx = __shfl_sync(0xffffffffu, tx, s), sy = __shfl_sync(0xffffffffu, ty, s),
                     sz = __shfl_sync(0xffffffffu, tz, s);
-        for (int base = 0; base < cn; base += 32) {
-            const int m = c0 + base + lane;
-            bool inl = false, ina = false;
-            int typ = 0;
-            if (base + lane < cn) {
-                float4 pj = __ldg(&spos4[m]);
-                float vx = (pj.x - pk.x) + sx, vy = (pj.y - pk.y) + sy, vz = (pj.z - pk.z) + sz;
-                float r2 = vx * vx + vy * vy + vz * vz;
-                inl = r2 < rl2 && !(m == k && cd == CODE_SELF);
-                ina = inl && r2 < ra2;
-                typ = __float_as_int(pj.w);
-            }
-            const unsigned ml = __ballot_sync(0xffffffffu, inl);
-            const unsigned ma = __ballot_sync(0xffffffffu, ina);
-            const int ent = (int)((unsigned)m | ((unsigned)cd << CODE_SHIFT));
-            if (inl) {
-                int slot = cl + __popc(ml & below);
-                if (slot < cap_l) {
-                    sl[slot] = ent;
-                    slt[slot] = typ;
-                }
-            }
-            if (ina) {
-                int slot = ca + __popc(ma & below);
-                if (slot < cap_a) {
-                    sa[slot] = ent;
-                    sat[slot] = typ;
-                }
-            }
-            cl += __popc(ml);
-            ca += __popc(ma);
+        const int m = c0 + (t - e0);
+        bool inl = false, ina = false;
+        int typ = 0;
+        if (t < total) {
+            float4 pj = __ldg(&spos4[m]);
+            float vx = (pj.x - pk.x) + sx, vy = (pj.y - pk.y) + sy, vz = (pj.z - pk.z) + sz;
+            float r2 = vx * vx + vy * vy + vz * vz;
+            inl = r2 < rl2 && !(m == k && cd == CODE_SELF);
+            ina = inl && r2 < ra2;
+            typ = __float_as_int(pj.w);
         }
+        const unsigned ml = __ballot_sync(0xffffffffu, inl);
+        const unsigned ma = __ballot_sync(0xffffffffu, ina);
+        const int ent = (int)((unsigned)m | ((unsigned)cd << CODE_SHIFT));
+        if (inl) {
+            int slot = cl + __popc(ml & below);
+            if (slot < cap_l) {
+                sl[slot] = ent;
+                slt[slot] = typ;
+            }
+        }
+        if (ina) {
+            int slot = ca + __popc(ma & below);
+            if (slot < cap_a) {
+                sa[slot] = ent;
+                sat[slot] = typ;
+            }
+        }
+        cl += __popc(ml);
+        ca += __popc(ma);
     }
     __syncwarp();
     nl = cl < cap_l ? cl : cap_l;
