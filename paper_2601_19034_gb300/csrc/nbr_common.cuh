@@ -15,7 +15,7 @@ __device__ __forceinline__ int nbr_cell_coord(float x, float invL, int nc) {
 //   sl / slt: list entries (index | image code << 26) and neighbour species, capacity cap_l
 //   sa / sat: angular entries and species, capacity cap_a
 // The candidates of the 27 stencil cells (visited in order, atoms in cell order) form one
-// index space scanned 32 at a time: lane t finds its cell by a binary search over the
+// index space scanned 4 x 32 at a time: lane t finds its cell by a binary search over the
 // cells' prefix counts (shuffles), tests its candidate, and a ballot compacts the accepted
 // ones.  nl / na return the number of entries stored (clamped to the capacities); the return
 // value is true when a capacity was exceeded.  Whole warp only.
@@ -57,51 +57,67 @@ __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos
     const float ra2 = g.rc_angular * g.rc_angular;
     const unsigned below = (1u << lane) - 1u;
     int cl = 0, ca = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        // cell of candidate t: the last cell s with excl[s] <= t (binary search over lanes 0..26)
-        int s = 0;
+    // four rounds of 32 candidates per iteration: the four position loads are in flight together
+    for (int base = 0; base < total; base += 128) {
+        int mm[4], cdd[4];
+        float sxx[4], syy[4], szz[4];
+        float4 pj[4];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int probe = s + step;
-            const int ex = __shfl_sync(0xffffffffu, excl, probe < 27 ? probe : 26);
-            if (probe < 27 && ex <= t) s = probe;
-        }
-        const int c0 = __shfl_sync(0xffffffffu, cstart, s);
-        const int e0 = __shfl_sync(0xffffffffu, excl, s);
-        const int cd = __shfl_sync(0xffffffffu, code, s);
-        const float sx = __shfl_sync(0xffffffffu, tx, s), sy = __shfl_sync(0xffffffffu, ty, s),
-                    sz = __shfl_sync(0xffffffffu, tz, s);
-        const int m = c0 + (t - e0);
-        bool inl = false, ina = false;
-        int typ = 0;
-        if (t < total) {
-            float4 pj = __ldg(&spos4[m]);
-            float vx = (pj.x - pk.x) + sx, vy = (pj.y - pk.y) + sy, vz = (pj.z - pk.z) + sz;
-            float r2 = vx * vx + vy * vy + vz * vz;
-            inl = r2 < rl2 && !(m == k && cd == CODE_SELF);
-            ina = inl && r2 < ra2;
-            typ = __float_as_int(pj.w);
-        }
-        const unsigned ml = __ballot_sync(0xffffffffu, inl);
-        const unsigned ma = __ballot_sync(0xffffffffu, ina);
-        const int ent = (int)((unsigned)m | ((unsigned)cd << CODE_SHIFT));
-        if (inl) {
-            int slot = cl + __popc(ml & below);
-            if (slot < cap_l) {
-                sl[slot] = ent;
-                slt[slot] = typ;
+        for (int u = 0; u < 4; ++u) {
+            const int t = base + 32 * u + lane;
+            // cell of candidate t: the last cell s with excl[s] <= t (binary search over lanes 0..26)
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int probe = s + step;
+                const int ex = __shfl_sync(0xffffffffu, excl, probe < 27 ? probe : 26);
+                if (probe < 27 && ex <= t) s = probe;
             }
+            const int c0 = __shfl_sync(0xffffffffu, cstart, s);
+            const int e0 = __shfl_sync(0xffffffffu, excl, s);
+            cdd[u] = __shfl_sync(0xffffffffu, code, s);
+            sxx[u] = __shfl_sync(0xffffffffu, tx, s);
+            syy[u] = __shfl_sync(0xffffffffu, ty, s);
+            szz[u] = __shfl_sync(0xffffffffu, tz, s);
+            mm[u] = c0 + (t - e0);
         }
-        if (ina) {
-            int slot = ca + __popc(ma & below);
-            if (slot < cap_a) {
-                sa[slot] = ent;
-                sat[slot] = typ;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            pj[u] = base + 32 * u + lane < total ? __ldg(&spos4[mm[u]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (base + 32 * u >= total) break;   // warp-uniform
+            const int t = base + 32 * u + lane;
+            const int m = mm[u], cd = cdd[u];
+            bool inl = false, ina = false;
+            int typ = 0;
+            if (t < total) {
+                float vx = (pj[u].x - pk.x) + sxx[u], vy = (pj[u].y - pk.y) + syy[u], vz = (pj[u].z - pk.z) + szz[u];
+                float r2 = vx * vx + vy * vy + vz * vz;
+                inl = r2 < rl2 && !(m == k && cd == CODE_SELF);
+                ina = inl && r2 < ra2;
+                typ = __float_as_int(pj[u].w);
             }
+            const unsigned ml = __ballot_sync(0xffffffffu, inl);
+            const unsigned ma = __ballot_sync(0xffffffffu, ina);
+            const int ent = (int)((unsigned)m | ((unsigned)cd << CODE_SHIFT));
+            if (inl) {
+                int slot = cl + __popc(ml & below);
+                if (slot < cap_l) {
+                    sl[slot] = ent;
+                    slt[slot] = typ;
+                }
+            }
+            if (ina) {
+                int slot = ca + __popc(ma & below);
+                if (slot < cap_a) {
+                    sa[slot] = ent;
+                    sat[slot] = typ;
+                }
+            }
+            cl += __popc(ml);
+            ca += __popc(ma);
         }
-        cl += __popc(ml);
-        ca += __popc(ma);
     }
     __syncwarp();
     nl = cl < cap_l ? cl : cap_l;
