@@ -28,6 +28,7 @@ struct qnep_batch {
     // batch description (rebuilt when the structures or boxes change)
     bool have_desc = false;
     int n_struct = 0, n_total = 0, nmax = 0, nph_max = 0, nk_max = 0;
+    bool has_empty = false;                 // a structure without atoms (its energy is written as 0)
     std::vector<int> h_off;
     std::vector<double> h_box;
     int cap_l = 0, cap_a = 0;
@@ -209,8 +210,12 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     }
     // work items: (structure, group); cost ~ atoms x (descriptor work + wave vectors)
     std::vector<std::pair<double, int2>> it;
+    b->has_empty = false;
     for (int s = 0; s < n_struct; ++s) {
-        if (sts[s].n == 0) continue;
+        if (sts[s].n == 0) {
+            b->has_empty = true;
+            continue;
+        }
         const double cost = (double)sts[s].n * (2800.0 + nk_of[sts[s].ktab]);
         for (int gi = 0; gi < b->n_groups; ++gi) it.push_back({cost, make_int2(s, gi)});
     }
@@ -422,6 +427,8 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     if (s != QNEP_OK) return s;
     CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
     CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
+    if (b->has_empty)   // structures without atoms have no item: their energies are zero
+        CKB(cudaMemsetAsync(energy, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
     if (b->profiling) {
         if (b->pending) {   // previous profiled call: harvest its events
             CKB(cudaEventSynchronize(b->ev[2]));

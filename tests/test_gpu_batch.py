@@ -183,3 +183,38 @@ def test_full_llzo_batch_sampled_pairs(dev):
     small = int(np.argmin(sizes))
     for s, c in ((big, 63), (small, 0), (int(np.argsort(sizes)[len(sizes) // 2]), 33)):
         _check_pair(res, off, systems, s, c, hp, params, elec)
+
+
+def test_edge_cases_empty_single_atom_and_one_candidate(dev):
+    """Empty and one-/two-atom structures next to a normal cell; one candidate (31 padded lanes)."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(16), n_candidates=1)
+    elec = wl.Elec(mode=1, kind="ewald")
+    one = wl.System(np.array([[1.0, 2.0, 3.0]], np.float32), np.array([2], np.int32), np.diag([9.0, 9.0, 9.0]),
+                    wl.LLZO_SPECIES)
+    two = wl.System(np.array([[1.0, 1.0, 1.0], [2.2, 1.1, 0.9]], np.float32), np.array([0, 3], np.int32),
+                    np.diag([8.0, 10.0, 12.0]), wl.LLZO_SPECIES)
+    empty = wl.System(np.zeros((0, 3), np.float32), np.zeros(0, np.int32), np.diag([10.0, 10.0, 10.0]),
+                      wl.LLZO_SPECIES)
+    systems = [one, _llzo((1, 1, 1), 17), empty, two]
+    pos, typ, off, boxes = stack_structures(systems)
+    b = QNEPBatch(hp, params, elec)
+    out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    b.close()
+    for s in (0, 1, 3):
+        _check_pair(res, off, systems, s, 0, hp, params, elec)
+    assert res["energy"][0, 2] == 0.0     # an empty structure contributes nothing
+
+
+def test_batched_three_species_perovskite_mix(dev):
+    """BaTiO3 cells of several sizes (cubic 8 A to 12 A) in one batch, mode 1 with a charge target."""
+    systems = [wl.batio3_supercell(2, seed=51), wl.batio3_supercell(3, seed=52), wl.batio3_supercell(2, seed=53)]
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(18), n_candidates=35)
+    elec = wl.Elec(mode=1, kind="ewald", q_total=-0.4)
+    res, off = _run_batch(systems, hp, params, elec, dev)
+    for s, c in ((0, 0), (1, 34), (2, 17)):
+        _check_pair(res, off, systems, s, c, hp, params, elec)
