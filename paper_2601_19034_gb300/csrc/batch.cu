@@ -727,25 +727,37 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
                 mu_tj = tj;
             }
             const int cntc = min(32, cum[tj + 1] - base);
-            for (int r = 0; r < cntc; ++r) {
-                const float4* rw = reinterpret_cast<const float4*>(rows + r * GR);
-                const float4 d0 = rw[0], d1 = rw[1], d2 = rw[2], d3 = rw[3];   // f'_0..8 | u | j
-                const int j = __float_as_int(d3.x);
-                if (j < 0) continue;
-                float sv = mu[0] * d0.x;
-                sv = fmaf(mu[1], d0.y, sv);
-                sv = fmaf(mu[2], d0.z, sv);
-                sv = fmaf(mu[3], d0.w, sv);
-                sv = fmaf(mu[4], d1.x, sv);
-                sv = fmaf(mu[5], d1.y, sv);
-                sv = fmaf(mu[6], d1.z, sv);
-                sv = fmaf(mu[7], d1.w, sv);
-                sv = fmaf(mu[8], d2.x, sv);
-                const float Fx = sv * d2.y, Fy = sv * d2.z, Fz = sv * d2.w;
-                fx += Fx;
-                fy += Fy;
-                fz += Fz;
-                atomicAdd(&fsum[(size_t)j * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
+            // four rows per iteration: independent chains (rows past the piece are skipped)
+            for (int r0 = 0; r0 < cntc; r0 += 4) {
+                float Fv[4][3];
+                int jv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = min(r0 + u, cntc - 1);
+                    const float4* rw = reinterpret_cast<const float4*>(rows + r * GR);
+                    const float4 d0 = rw[0], d1 = rw[1], d2 = rw[2], d3 = rw[3];   // f'_0..8 | u | j
+                    jv[u] = r0 + u < cntc ? __float_as_int(d3.x) : -1;
+                    float sv = mu[0] * d0.x;
+                    sv = fmaf(mu[1], d0.y, sv);
+                    sv = fmaf(mu[2], d0.z, sv);
+                    sv = fmaf(mu[3], d0.w, sv);
+                    sv = fmaf(mu[4], d1.x, sv);
+                    sv = fmaf(mu[5], d1.y, sv);
+                    sv = fmaf(mu[6], d1.z, sv);
+                    sv = fmaf(mu[7], d1.w, sv);
+                    sv = fmaf(mu[8], d2.x, sv);
+                    Fv[u][0] = sv * d2.y;
+                    Fv[u][1] = sv * d2.z;
+                    Fv[u][2] = sv * d2.w;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jv[u] < 0) continue;
+                    fx += Fv[u][0];
+                    fy += Fv[u][1];
+                    fz += Fv[u][2];
+                    atomicAdd(&fsum[(size_t)jv[u] * CG + lane], make_float4(-Fv[u][0], -Fv[u][1], -Fv[u][2], 0.f));
+                }
             }
         } else if (ok) {
             // angular: per entry the contraction of Phi with d(g_n Y_lm)/dr_ij
@@ -1128,16 +1140,28 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                             for (int i = lane; i < cntc * (GR / 4); i += 32) t4[i] = __ldg(&s4[i]);
                         }
                         __syncwarp();
-                        for (int r = 0; r < cntc; ++r) {
-                            const float4* rw = reinterpret_cast<const float4*>(tab + r * GR);
-                            const float4 d3 = rw[3], d4 = rw[4];   // (j_desc, B, B'u_x, B'u_y), (B'u_z, j_real, -, -)
-                            const int j = __float_as_int(d4.y);
-                            if (j < 0) continue;
-                            const float qj = qcs[(size_t)j * CG + lane];
-                            ph = fmaf(qj, d3.y, ph);
-                            gx = fmaf(qj, d3.z, gx);
-                            gy = fmaf(qj, d3.w, gy);
-                            gz = fmaf(qj, d4.x, gz);
+                        // four rows per iteration, their charge loads issued together; rows past
+                        // the piece and pairs beyond r_c contribute q_j = 0
+                        for (int r0 = 0; r0 < cntc; r0 += 4) {
+                            float4 d3[4];
+                            float bz[4], qj[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int r = min(r0 + u, cntc - 1);
+                                const float4* rw = reinterpret_cast<const float4*>(tab + r * GR);
+                                const float4 d4 = rw[4];   // (B'u_z, j_real, -, -)
+                                d3[u] = rw[3];             // (j_desc, B, B'u_x, B'u_y)
+                                bz[u] = d4.x;
+                                const int j = __float_as_int(d4.y);
+                                qj[u] = (j >= 0 && r0 + u < cntc) ? qcs[(size_t)j * CG + lane] : 0.f;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                ph = fmaf(qj[u], d3[u].y, ph);
+                                gx = fmaf(qj[u], d3[u].z, gx);
+                                gy = fmaf(qj[u], d3[u].w, gy);
+                                gz = fmaf(qj[u], bz[u], gz);
+                            }
                         }
                         __syncwarp();
                     }
