@@ -199,7 +199,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         }
         t.ktab = it->second;
     }
-    if (nph_max % 2 == 0) nph_max += 1;
+    nph_max += nph_max & 1;   // even: every atom's phase row starts on a 16-byte boundary (bulk copies)
     // neighbour capacities from the densest structure (2x the mean count + margin)
     const double pi43 = 4.18879020478639;
     int cl = b->cap_l_user, ca = b->cap_a_user;

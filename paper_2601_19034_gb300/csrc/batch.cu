@@ -58,8 +58,9 @@ constexpr int PR_S = PR_A + MAX_SPECIES * NA * KA * CG;  // descriptor scaler [N
 constexpr int PARAM_FLOATS = PR_S + NDES * CG;
 constexpr int QT = 64;                         // atoms per charge tile of the S(k) phase
 constexpr int FLUSH_TILES = 8;                 // FP32 partial sums cover 512 atoms
-constexpr int KW = 64;                         // wave vectors per staged window of the field pass
+constexpr int KW = 32;                         // wave vectors per staged window of the field pass
 constexpr int NSUMS = 6;                       // per-candidate FP64 sums
+constexpr int WIN_F2 = KW * CG + 2 * KW + KW / 4;   // float2 per field window: C(k) | k | chunks
 
 static_assert(WBUF % 4 == 0 && WARP_FLOATS % 4 == 0 && PARAM_FLOATS % 4 == 0, "float4 alignment");
 
@@ -403,21 +404,23 @@ __device__ __forceinline__ void stage_params(const float* __restrict__ pg, const
     }
 }
 
-// Cumulative neighbour counts of sorted atom m by species (lane 0 writes, warp reads).
+// Cumulative neighbour counts of sorted atom m by species: lanes 0..S-1 load the radial
+// counts and lanes 8..8+S-1 the angular ones (one round trip), scanned by shuffles within
+// each group of 8 lanes; cum[0..S] radial, cum[8..8+S] angular (the warp reads them after).
 __device__ __forceinline__ void species_cum(const BatchArgs& a, int off, int n, int m, int S, int* cum) {
-    if ((threadIdx.x & 31) == 0) {
-        int tl = 0, ta = 0;
-        const int* cl = a.cnt_list + (size_t)off * S;
-        const int* ca = a.cnt_ang + (size_t)off * S;
-        for (int s = 0; s < S; ++s) {
-            cum[s] = tl;
-            cum[8 + s] = ta;
-            tl += cl[(size_t)s * n + m];
-            ta += ca[(size_t)s * n + m];
-        }
-        cum[S] = tl;
-        cum[8 + S] = ta;
+    const int lane = threadIdx.x & 31, g = lane & 7;
+    __syncwarp();   // the warp is done with the previous atom's counts
+    int v = 0;
+    if (lane < 16 && g < S)
+        v = (lane < 8 ? a.cnt_list : a.cnt_ang)[(size_t)off * S + (size_t)g * n + m];
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, d, 8);
+        if (g >= d) v += t;
     }
+    // inclusive sums: lane g holds the count of species 0..g; cum[g + 1] = that
+    if (lane < 16 && g < S) cum[(lane & 8) + g + 1] = v;
+    if (lane == 0 || lane == 8) cum[lane] = 0;
     __syncwarp();
 }
 
@@ -559,11 +562,12 @@ __device__ __forceinline__ void descriptor_atom(const BatchArgs& a, const BatchS
 // Network of species t_i for two atoms (m1 < 0: one) and the 32 candidates, weights staged
 // in shared memory: net = [W0 (NNEU x NDES) | b0 | w1E | w1q | b1E | b1q | scaler (NDES)][CG].
 // h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q (Eq. U_i, Sec. II.B); writes
-// dU/dD and dq/dD (scaled) over D, and (U, q).
+// dU/dD and dq/dD (scaled) over D, and (U, q).  Not inlined: its own register allocation keeps
+// the item kernel free of spills.
 constexpr int NET_SCALER = ParamLayout::BLOCK;
 constexpr int NET_FLOATS = (ParamLayout::BLOCK + NDES) * CG;
 
-__device__ __forceinline__ void network_pair(const float* __restrict__ net, int m0, int m1,
+__device__ __noinline__ void network_pair(const float* __restrict__ net, int m0, int m1,
                                              float* __restrict__ duq, float2* __restrict__ uq, double& su,
                                              double& sq) {
     const int lane = threadIdx.x & 31;
@@ -837,13 +841,19 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ int s_item;
     __shared__ __align__(8) uint64_t wbars[NW][2];   // per-warp barriers of the two row buffers
+    __shared__ __align__(8) uint64_t tbars[2];       // block barriers of the two S(k) / field tiles
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         mbar_init(&wbars[warp][0], 1);
         mbar_init(&wbars[warp][1], 1);
+        if (warp == 0) {
+            mbar_init(&tbars[0], 1);
+            mbar_init(&tbars[1], 1);
+        }
         mbar_init_fence();
     }
-    uint32_t par = 0;   // phase bits of this warp's two buffers
+    uint32_t par = 0;    // phase bits of this warp's two buffers
+    uint32_t tpar = 0;   // phase bits of the two block tiles
     double* red = reinterpret_cast<double*>(bsm);     // [NW][CG]
     double* sums = red + NW * CG;                      // [NSUMS][CG]
     float* cst = reinterpret_cast<float*>(sums + NSUMS * CG);   // delta, phibar, q_target, pad [4][CG]
@@ -927,11 +937,25 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         const int nkp = 8 * kt.nchunk;
         double ek = 0.0;
         {
-            float* qt = un;                                          // [QT][CG]
-            float2* pt2 = reinterpret_cast<float2*>(un + QT * CG);   // [QT][nph]
-            const int nph = kt.nph;
+            // tile buffer b: charges [QT][CG] | phase rows [QT][nph_stride]; tile T of the
+            // (task round, atom tile) sequence is copied while tile T - 1 is summed
+            const int ps = a.nph_stride;
+            const int tile_f = QT * CG + 2 * QT * ps;
             const int ntask = (kt.nchunk + 3) >> 2;
             const int nfl = (n + QT * FLUSH_TILES - 1) / (QT * FLUSH_TILES);
+            const int ntile = (n + QT - 1) / QT;
+            const int total = ((ntask + NW - 1) / NW) * ntile;
+            auto issue = [&](int T) {
+                const int j0 = (T % ntile) * QT, cnt = min(QT, n - j0);
+                float* dst = un + (T & 1) * tile_f;
+                const uint32_t qb = (uint32_t)(cnt * CG * 4), rb = (uint32_t)(cnt * ps * 8);
+                fence_proxy_async_all();   // charges / C(k) were written by this block
+                mbar_expect_tx(&tbars[T & 1], qb + rb);
+                bulk_g2s(dst, qcs + (size_t)j0 * CG, qb, &tbars[T & 1]);
+                bulk_g2s(dst + QT * CG, phb + (size_t)j0 * ps, rb, &tbars[T & 1]);
+            };
+            if (threadIdx.x == 0 && total > 0) issue(0);
+            int T = 0;
             for (int tb = 0; tb < ntask; tb += NW) {
                 const int task = tb + warp;
                 const bool act = task < ntask;
@@ -951,18 +975,18 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     si[c] = 0.f;
                 }
                 int tiles = 0, fl = 0;
-                for (int j0 = 0; j0 < n; j0 += QT) {
+                for (int j0 = 0; j0 < n; j0 += QT, ++T) {
                     const int cnt = min(QT, n - j0);
-                    __syncthreads();
-                    for (int i = threadIdx.x; i < cnt * CG; i += NW * 32) qt[i] = qcs[(size_t)j0 * CG + i];
-                    for (int i = threadIdx.x; i < cnt * nph; i += NW * 32) {
-                        const int jj = i / nph, e = i - jj * nph;
-                        pt2[i] = __ldg(&phb[(size_t)(j0 + jj) * a.nph_stride + e]);
-                    }
-                    __syncthreads();
-                    if (act) {
+                    if (threadIdx.x == 0 && T + 1 < total) issue(T + 1);
+                    const int b = T & 1;
+                    const bool ok = mbar_wait_bounded(&tbars[b], (tpar >> b) & 1u);
+                    tpar ^= 1u << b;
+                    if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+                    const float* qt = un + b * tile_f;
+                    const float2* pt2 = reinterpret_cast<const float2*>(qt + QT * CG);
+                    if (act && ok) {
                         for (int jj = 0; jj < cnt; ++jj) {
-                            const float2* row = pt2 + jj * nph;
+                            const float2* row = pt2 + jj * ps;
                             const float2 e = cmul(cmul(row[e1], row[e2]), row[e3]);
                             const float4* q4 = reinterpret_cast<const float4*>(qt + jj * CG);
 #pragma unroll
@@ -978,21 +1002,22 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                                 si[4 * c4 + 3] = fmaf(q.w, e.y, si[4 * c4 + 3]);
                             }
                         }
-                        if (++tiles == FLUSH_TILES || j0 + QT >= n) {
-                            tiles = 0;
-                            if (kval) {
-                                float4* dst = reinterpret_cast<float4*>(skp + ((size_t)fl * nkp + 8 * h + t) * CG);
-#pragma unroll
-                                for (int c = 0; c < CG; c += 2) dst[c >> 1] = make_float4(sr[c], si[c], sr[c + 1], si[c + 1]);
-                            }
-#pragma unroll
-                            for (int c = 0; c < CG; ++c) {
-                                sr[c] = 0.f;
-                                si[c] = 0.f;
-                            }
-                            ++fl;
-                        }
                     }
+                    if (act && (++tiles == FLUSH_TILES || j0 + QT >= n)) {
+                        tiles = 0;
+                        if (kval) {
+                            float4* dst = reinterpret_cast<float4*>(skp + ((size_t)fl * nkp + 8 * h + t) * CG);
+#pragma unroll
+                            for (int c = 0; c < CG; c += 2) dst[c >> 1] = make_float4(sr[c], si[c], sr[c + 1], si[c + 1]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            sr[c] = 0.f;
+                            si[c] = 0.f;
+                        }
+                        ++fl;
+                    }
+                    __syncthreads();   // tile buffer b is refilled by the copy issued next iteration
                 }
                 if (act) {
                     __syncwarp();
@@ -1018,25 +1043,36 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         __syncthreads();
 
         // 4a k-space potential and field: lanes over atoms (32 per warp task), 16 candidates per
-        // pass; C(k), the wave vectors and the chunk list staged in windows of KW wave vectors
+        // pass; C(k), the wave vectors and the chunk list come in windows of KW wave vectors,
+        // window W + 1 copied while window W is used
         {
             const int nph = kt.nph;
             float2* ph = reinterpret_cast<float2*>(un) + (size_t)warp * nph * 32;   // [nph][32 atoms]
-            float2* sw = reinterpret_cast<float2*>(un) + (size_t)NW * nph * 32;     // [KW][CG]
-            float4* kw = reinterpret_cast<float4*>(sw + KW * CG);                   // [KW]
-            int4* cw = reinterpret_cast<int4*>(kw + KW);                             // [KW / 8]
+            float2* win = reinterpret_cast<float2*>(un) + (size_t)NW * nph * 32;    // 2 x window
             const int ntask = (n + 31) >> 5;
+            const int nwin = (nkp + KW - 1) / KW;
+            const int total = ((ntask + NW - 1) / NW) * 2 * nwin;
+            auto issue = [&](int W) {
+                const int k0 = (W % nwin) * KW, kc = min(KW, nkp - k0);
+                float2* sw = win + (W & 1) * WIN_F2;
+                const uint32_t sb = (uint32_t)(kc * CG * 8), kb = (uint32_t)(kc * 16), cb = (uint32_t)(kc / 8 * 16);
+                fence_proxy_async_all();   // charges / C(k) were written by this block
+                mbar_expect_tx(&tbars[W & 1], sb + kb + cb);
+                bulk_g2s(sw, sk + (size_t)k0 * CG, sb, &tbars[W & 1]);
+                bulk_g2s(sw + KW * CG, a.kvec + 8 * (size_t)kt.chunk_off + k0, kb, &tbars[W & 1]);
+                bulk_g2s(sw + KW * CG + 2 * KW, a.chunk + kt.chunk_off + k0 / 8, cb, &tbars[W & 1]);
+            };
+            if (threadIdx.x == 0 && total > 0) issue(0);
+            int W = 0;
             for (int r0 = 0; r0 < ntask; r0 += NW) {
                 const int task = r0 + warp;
                 const bool act = task < ntask;
                 const int j = task * 32 + lane;
-                if (act) {
-                    const int cnt = min(32, n - task * 32);
-                    const float2* src = phb + (size_t)task * 32 * a.nph_stride;
-                    for (int idx = lane; idx < cnt * nph; idx += 32) {
-                        const int jj = idx / nph, e = idx - jj * nph;
-                        ph[e * 32 + jj] = __ldg(&src[(size_t)jj * a.nph_stride + e]);
-                    }
+                if (act && j < n) {
+                    // lane = atom: its phase row, transposed
+                    const float2* src = phb + (size_t)j * a.nph_stride;
+#pragma unroll 4
+                    for (int e = 0; e < nph; ++e) ph[e * 32 + lane] = __ldg(&src[e]);
                 }
                 __syncwarp();
                 for (int c0 = 0; c0 < CG; c0 += 16) {
@@ -1051,58 +1087,59 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     }
                     float pkx = 0.f, pky = 0.f;
                     int pn1 = -(1 << 30), pn2 = 0;
-                    for (int k0 = 0; k0 < nkp; k0 += KW) {
+                    for (int k0 = 0; k0 < nkp; k0 += KW, ++W) {
                         const int kc = min(KW, nkp - k0);
-                        __syncthreads();
-                        {
-                            const float4* s4 = reinterpret_cast<const float4*>(sk + (size_t)k0 * CG);
-                            float4* d4 = reinterpret_cast<float4*>(sw);
-                            for (int i = threadIdx.x; i < kc * CG / 2; i += NW * 32) d4[i] = s4[i];
-                            for (int i = threadIdx.x; i < kc; i += NW * 32)
-                                kw[i] = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + k0 + i]);
-                            for (int i = threadIdx.x; i < (kc >> 3); i += NW * 32)
-                                cw[i] = __ldg(&a.chunk[kt.chunk_off + (k0 >> 3) + i]);
-                        }
-                        __syncthreads();
-                        if (!act) continue;
-                        for (int hh = 0; hh < (kc >> 3); ++hh) {
-                            const int4 ci = cw[hh];
-                            if (ci.x != pn1 || ci.y != pn2) {
-                                // new column (n1, n2): fold the column's Im sums into E_x, E_y
+                        if (threadIdx.x == 0 && W + 1 < total) issue(W + 1);
+                        const int b = W & 1;
+                        const bool ok = mbar_wait_bounded(&tbars[b], (tpar >> b) & 1u);
+                        tpar ^= 1u << b;
+                        if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+                        const float2* sw = win + b * WIN_F2;                                   // [KW][CG]
+                        const float4* kw = reinterpret_cast<const float4*>(sw + KW * CG);    // [KW]
+                        const int4* cw = reinterpret_cast<const int4*>(kw + KW);             // [KW / 8]
+                        if (act && ok) {
+                            for (int hh = 0; hh < (kc >> 3); ++hh) {
+                                const int4 ci = cw[hh];
+                                if (ci.x != pn1 || ci.y != pn2) {
+                                    // new column (n1, n2): fold the column's Im sums into E_x, E_y
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) {
-                                    ex[c] = fmaf(pkx, tt[c], ex[c]);
-                                    ey[c] = fmaf(pky, tt[c], ey[c]);
-                                    tt[c] = 0.f;
+                                    for (int c = 0; c < 16; ++c) {
+                                        ex[c] = fmaf(pkx, tt[c], ex[c]);
+                                        ey[c] = fmaf(pky, tt[c], ey[c]);
+                                        tt[c] = 0.f;
+                                    }
+                                    pn1 = ci.x;
+                                    pn2 = ci.y;
+                                    const float4 k0v = kw[hh * 8];
+                                    pkx = k0v.x;
+                                    pky = k0v.y;
                                 }
-                                pn1 = ci.x;
-                                pn2 = ci.y;
-                                const float4 k0v = kw[hh * 8];
-                                pkx = k0v.x;
-                                pky = k0v.y;
-                            }
-                            const float2 xy = cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
-                            for (int t = 0; t < 8; ++t) {
-                                const float4 k4 = kw[hh * 8 + t];
-                                if (k4.w == 0.f) continue;
-                                const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
-                                const float4* s4 = reinterpret_cast<const float4*>(sw + (hh * 8 + t) * CG + c0);
+                                const float2 xy =
+                                    cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
+                                // padding wave vectors carry C = 0 and add nothing: no branch here
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    const float4 v = s4[u];
-                                    // z = C conj(e) for the two candidates of v
-                                    float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
-                                    fphi[2 * u] += zr;
-                                    tt[2 * u] += zi;
-                                    ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
-                                    zr = fmaf(v.z, e.x, v.w * e.y);
-                                    zi = fmaf(v.w, e.x, -v.z * e.y);
-                                    fphi[2 * u + 1] += zr;
-                                    tt[2 * u + 1] += zi;
-                                    ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                                for (int t = 0; t < 8; ++t) {
+                                    const float4 k4 = kw[hh * 8 + t];
+                                    const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
+                                    const float4* s4 = reinterpret_cast<const float4*>(sw + (hh * 8 + t) * CG + c0);
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) {
+                                        const float4 v = s4[u];
+                                        // z = C conj(e) for the two candidates of v
+                                        float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
+                                        fphi[2 * u] += zr;
+                                        tt[2 * u] += zi;
+                                        ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
+                                        zr = fmaf(v.z, e.x, v.w * e.y);
+                                        zi = fmaf(v.w, e.x, -v.z * e.y);
+                                        fphi[2 * u + 1] += zr;
+                                        tt[2 * u + 1] += zi;
+                                        ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                                    }
                                 }
                             }
                         }
+                        __syncthreads();   // window buffer b is refilled by the copy issued next iteration
                     }
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
@@ -1134,12 +1171,10 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     const float4* grows = reinterpret_cast<const float4*>(a.geo_rad + (size_t)(off + m) * a.cap_l * GR);
                     for (int base = 0; base < tot_l; base += 32) {
                         const int cntc = min(32, tot_l - base);
-                        {
-                            float4* t4 = reinterpret_cast<float4*>(tab);
-                            const float4* s4 = grows + (size_t)base * (GR / 4);
-                            for (int i = lane; i < cntc * (GR / 4); i += 32) t4[i] = __ldg(&s4[i]);
-                        }
-                        __syncwarp();
+                        __syncwarp();   // the warp is done with the previous piece
+                        if (lane == 0)
+                            warp_bulk(tab, grows + (size_t)base * (GR / 4), (uint32_t)(cntc * GR * 4), &wbars[warp][0]);
+                        if (!warp_wait(wbars[warp], 0, par, a.status)) continue;
                         // four rows per iteration, their charge loads issued together; rows past
                         // the piece and pairs beyond r_c contribute q_j = 0
                         for (int r0 = 0; r0 < cntc; r0 += 4) {
@@ -1163,7 +1198,6 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                                 gz = fmaf(qj[u], bz[u], gz);
                             }
                         }
-                        __syncwarp();
                     }
                 }
                 // F^r_i = sum_j q_i q_j B'(r) u_ij (u_ij from i to j)
@@ -1226,9 +1260,8 @@ size_t item_smem(int nph_max) {
     const size_t head = sizeof(double) * (NW + NSUMS) * CG + sizeof(float) * 4 * CG;
     const size_t p1 = sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
     const size_t p1b = sizeof(float) * (size_t)NET_FLOATS;
-    const size_t p3 = sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max;
-    const size_t p4 = sizeof(float2) * ((size_t)NW * nph_max * 32 + (size_t)KW * CG) + sizeof(float4) * KW +
-                      sizeof(int4) * (KW / 8);
+    const size_t p3 = 2 * (sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max);
+    const size_t p4 = sizeof(float2) * ((size_t)NW * nph_max * 32 + 2 * (size_t)WIN_F2);
     return head + std::max(std::max(p1, p1b), std::max(p3, p4));
 }
 
