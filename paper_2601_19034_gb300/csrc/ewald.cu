@@ -7,6 +7,8 @@
 //   W^k   = k_e sum G |S|^2 B,  B = I - (2/(4 alpha^2) + 2/k^2) k k^T   (Eq. virial-kspace-total)
 // Per-atom phase factors are separable, exp(-i k.r) = X(n1) Y(n2) Z(n3), and
 // each is evaluated directly from an exactly reduced phase (desc_math.cuh).
+#include <algorithm>
+
 #include "desc_math.cuh"
 #include "tma.cuh"
 
@@ -74,31 +76,34 @@ __device__ __forceinline__ void flush_k_terms(double v[7], Accum* __restrict__ a
     }
 }
 
-constexpr int SK_WARPS = 4;
-constexpr int SK_TILE = 32;   // atoms whose phase rows are staged in shared memory at a time
+constexpr int SK_WARPS = 8;
+constexpr int SK_T = 4;       // atoms per warp tile (one bulk copy of their phase rows)
+constexpr int SK_NB = 4;      // tile buffers in each warp's copy ring
+constexpr int SK_SPAN = 512;  // at most this many atoms per block (FP32 partial sums)
 
-// One thread = one 8-wide chunk of a column.  The block's atoms are staged tile by
-// tile in shared memory: each tile's phase rows are contiguous in global memory and
-// arrive by one TMA bulk copy, double buffered so the next tile streams in while the
-// current one is used; each warp takes every fourth atom of a tile.  The block
-// reduces its four partial sums in FP64 and adds them to S with FP64 atomics.  With
-// a counter array, the last block of each column group (blockIdx.x) also finalises
-// that group's 256 wave vectors (C, U^k, W^k), saving a launch.
+// One thread = one 8-wide chunk of a column.  A block takes at most 512 atoms; they are
+// cut into tiles of 4 whose phase rows are contiguous in global memory, and warp w
+// takes tiles w, w + 8, ...  Each warp streams its tiles through its own ring of four
+// shared-memory buffers by TMA bulk copies (three in flight while one is used) with its
+// own mbarriers, and loads the tiles' charges two tiles ahead, so the warps never wait
+// for one another inside the loop.  The eight warps' FP32 partial sums are added
+// pairwise in FP32 and go to S with FP64 atomics.  With a counter array, the last block
+// of each column group (blockIdx.x) also finalises that group's 256 wave vectors (C,
+// U^k, W^k), saving a launch.
 __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ q_raw, const Accum* __restrict__ acc_in,
                                                       int n, float q_target, int span, EwaldTab tab,
                                                       unsigned int* __restrict__ group_done, Accum* __restrict__ acc,
                                                       unsigned int* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char sk_dyn[];
-    __shared__ float qs[2][SK_TILE];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[SK_WARPS][SK_NB];
     __shared__ bool last;
     __shared__ int failed;
-    float2* bufs[2] = {reinterpret_cast<float2*>(sk_dyn), reinterpret_cast<float2*>(sk_dyn) + SK_TILE * tab.nph};
+    __shared__ float sdelta;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int slot = blockIdx.x * 32 + lane;
     const bool valid = slot < tab.nchunk;
     const int g = valid ? (tab.chunk_order ? __ldg(&tab.chunk_order[slot]) : slot) : 0;
-    int n1 = 0, n2 = 0, zbase = 0, kidx = 0;
+    int n1 = 0, n2 = 0, zbase = 0;
     if (valid) {
         int c = __ldg(&tab.chunk_col[g]);
         int4 ci = __ldg(&tab.col[c]);
@@ -106,47 +111,57 @@ __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ 
         n1 = ci.x;
         n2 = ci.y;
         zbase = tab.zoff + ci.z + 8 * h + tab.n3max;
-        kidx = 8 * g;
+    }
+    if (lane == 0) {
+        for (int b = 0; b < SK_NB; ++b) mbar_init(&bars[w][b], 1);
+        mbar_init_fence();
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init_fence();
         failed = 0;
+        sdelta = (float)(((double)q_target - acc_in->sum_q) / (double)n);   // charge correction, once
     }
     __syncthreads();
-    const float delta = (float)(((double)q_target - acc_in->sum_q) / (double)n);
+    const float delta = sdelta;
     float2 s[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) s[t] = make_float2(0.f, 0.f);
     const int a0 = blockIdx.y * span;
     const int a1 = min(n, a0 + span);
-    const int ntiles = a1 > a0 ? (a1 - a0 + SK_TILE - 1) / SK_TILE : 0;
+    const int ntile = a1 > a0 ? (a1 - a0 + SK_T - 1) / SK_T : 0;
+    const int ntw = w < ntile ? (ntile - w + SK_WARPS - 1) / SK_WARPS : 0;   // this warp's tiles
     const int yoff = tab.yoff + n2 + tab.n2max;
-    auto issue = [&](int t) {
-        const int b = t & 1, t0 = a0 + t * SK_TILE, cnt = min(SK_TILE, a1 - t0);
-        if (threadIdx.x == 0) {
-            const uint32_t bytes = round_up16((uint32_t)(cnt * tab.nph) * (uint32_t)sizeof(float2));
-            fence_proxy_async_smem();
-            mbar_expect_tx(&bars[b], bytes);
-            bulk_g2s(bufs[b], tab.phase + (size_t)t0 * tab.nph, bytes, &bars[b]);
-        }
-        if (threadIdx.x < cnt) qs[b][threadIdx.x] = __ldg(&q_raw[t0 + threadIdx.x]) + delta;
+    const size_t buf_f2 = (size_t)SK_T * tab.nph;
+    float2* const ring = reinterpret_cast<float2*>(sk_dyn) + (size_t)w * SK_NB * buf_f2;
+    // the warp's i-th tile: atoms a0 + (w + 8 i) * 4 ...
+    auto issue = [&](int i) {   // lane 0
+        const int t0 = a0 + (w + SK_WARPS * i) * SK_T, cnt = min(SK_T, a1 - t0);
+        const uint32_t bytes = round_up16((uint32_t)(cnt * tab.nph) * (uint32_t)sizeof(float2));
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bars[w][i % SK_NB], bytes);
+        bulk_g2s(ring + (size_t)(i % SK_NB) * buf_f2, tab.phase + (size_t)t0 * tab.nph, bytes, &bars[w][i % SK_NB]);
     };
-    int t = 0;
-    if (ntiles > 0) issue(0);
-    for (; t < ntiles; ++t) {
-        const int b = t & 1;
-        if (t + 1 < ntiles) issue(t + 1);
-        if (!mbar_wait_bounded(&bars[b], (uint32_t)((t >> 1) & 1))) failed = 1;
-        __syncthreads();
-        if (failed) break;
-        const int cnt = min(SK_TILE, a1 - (a0 + t * SK_TILE));
-        if (valid) {
-            const float2* rows = bufs[b];
-            for (int a = w; a < cnt; a += SK_WARPS) {
+    auto qload = [&](int i) {   // lanes < 4: charge of atom `lane` of the warp's i-th tile
+        const int a = a0 + (w + SK_WARPS * i) * SK_T + lane;
+        return (i < ntw && lane < SK_T && a < a1) ? __ldg(&q_raw[a]) : 0.f;
+    };
+    if (lane == 0)
+        for (int i = 0; i < min(SK_NB - 1, ntw); ++i) issue(i);
+    float q0 = qload(0), q1 = qload(1);   // charges of the current and the next tile
+    int i = 0;
+    bool ok = true;
+    for (; i < ntw; ++i) {
+        __syncwarp();   // the warp is done with buffer (i - 1) % 4, refilled next
+        if (lane == 0 && i + SK_NB - 1 < ntw) issue(i + SK_NB - 1);
+        const float q2 = qload(i + 2);
+        ok = mbar_wait_bounded(&bars[w][i % SK_NB], (uint32_t)((i / SK_NB) & 1));
+        if (!ok) break;
+        const int cnt = min(SK_T, a1 - (a0 + (w + SK_WARPS * i) * SK_T));
+        const float2* rows = ring + (size_t)(i % SK_NB) * buf_f2;
+#pragma unroll
+        for (int a = 0; a < SK_T; ++a) {
+            const float q = __shfl_sync(0xffffffffu, q0, a) + delta;
+            if (a < cnt && valid) {
                 const float2* row = rows + a * tab.nph;
-                const float q = qs[b][a];
                 float2 x = row[n1], y = row[yoff];
                 float2 xy = make_float2(q * fmaf(x.x, y.x, -x.y * y.y), q * fmaf(x.x, y.y, x.y * y.x));
 #pragma unroll
@@ -157,36 +172,43 @@ __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ 
                 }
             }
         }
-        __syncthreads();
+        q0 = q1;
+        q1 = q2;
     }
+    if (!ok) {
+        // a transfer did not complete: record it and give this warp's copies still in flight
+        // a bounded chance to land before the block's shared memory is released
+        for (int u = i; u < min(i + SK_NB, ntw); ++u)
+            mbar_wait_bounded(&bars[w][u % SK_NB], (uint32_t)((u / SK_NB) & 1));
+        if (lane == 0) failed = 1;
+    }
+    __syncthreads();
     if (failed) {
-        // a transfer did not complete: record it, give copies still in flight a bounded
-        // chance to land before the block's shared memory is released, and leave
-        for (int u = t; u < min(t + 2, ntiles); ++u) mbar_wait_bounded(&bars[u & 1], (uint32_t)((u >> 1) & 1));
         if (threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
         return;
     }
-    // the staging buffers are free now: reuse them for the cross-warp reduction
-    double* red = reinterpret_cast<double*>(sk_dyn);   // [SK_WARPS][8][2][32], fits in one tile buffer
+    // the staging buffers are free now: the warps' partial sums, added pairwise in FP32
+    float* red32 = reinterpret_cast<float*>(sk_dyn);   // [SK_WARPS][16][32]
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        red[((w * 8 + u) * 2 + 0) * 32 + lane] = (double)s[u].x;
-        red[((w * 8 + u) * 2 + 1) * 32 + lane] = (double)s[u].y;
+        red32[(w * 16 + 2 * u) * 32 + lane] = s[u].x;
+        red32[(w * 16 + 2 * u + 1) * 32 + lane] = s[u].y;
     }
     __syncthreads();
-    if (w == 0 && valid) {
+    static_assert(SK_WARPS == 8, "pairwise warp sum below");
+    for (int c = threadIdx.x; c < 16 * 32; c += blockDim.x) {
+        const int l = c & 31, uc = c >> 5;
+        const int sl = blockIdx.x * 32 + l;
+        if (sl >= tab.nchunk) continue;
+        float v[SK_WARPS];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            double re = 0.0, im = 0.0;
-#pragma unroll
-            for (int q = 0; q < SK_WARPS; ++q) {
-                re += red[((q * 8 + u) * 2 + 0) * 32 + lane];
-                im += red[((q * 8 + u) * 2 + 1) * 32 + lane];
-            }
-            atomicAdd(&tab.S[kidx + u].x, re);
-            atomicAdd(&tab.S[kidx + u].y, im);
-        }
+        for (int q = 0; q < SK_WARPS; ++q) v[q] = red32[(q * 16 + uc) * 32 + l];
+        const float sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        const int gl = tab.chunk_order ? __ldg(&tab.chunk_order[sl]) : sl;
+        double2* dst = &tab.S[8 * gl + (uc >> 1)];
+        atomicAdd((uc & 1) ? &dst->y : &dst->x, (double)sum);
     }
+    double* red = reinterpret_cast<double*>(sk_dyn);   // [7][32] for the finalisation below
     if (!group_done) return;
     __threadfence();
     __syncthreads();
@@ -227,20 +249,14 @@ void launch_ewald_phases(const float4* pos4, int n, EwaldTab tab, cudaStream_t s
     k_phases<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(pos4, n, tab);
 }
 
-static void sk_grid(int n, const EwaldTab& tab, int& gx, int& gy, int& span) {
-    gx = (tab.nchunk + 31) / 32;
-    // atom split: aim for ~4 blocks per SM over 152 SMs; spans are whole tiles
-    int want = (4 * 152 + gx - 1) / gx;
-    span = (n + want - 1) / want;
-    span = (span + SK_TILE - 1) / SK_TILE * SK_TILE;
-    gy = (n + span - 1) / span;
-}
-
+// Grid: column groups x atom spans (at most 512 atoms), within one wave of resident
+// blocks where the atoms allow (a partial second wave would double the time of the SMs
+// that run it).
 static size_t sk_smem(const EwaldTab& tab) {
-    // two tile buffers; the first also holds the reduction (SK_WARPS x 8 x 2 x 32 doubles)
-    size_t tile = sizeof(float2) * SK_TILE * tab.nph;
-    size_t red = sizeof(double) * SK_WARPS * 8 * 2 * 32;
-    return tile > red ? 2 * tile : tile + red;
+    // each warp's ring of tile buffers; later also the reduction (SK_WARPS x 16 x 32 floats)
+    size_t ring = sizeof(float2) * SK_T * tab.nph * SK_NB * SK_WARPS;
+    size_t red = sizeof(float) * SK_WARPS * 16 * 32;
+    return std::max(ring, red);
 }
 
 static void sk_attr() {
@@ -251,12 +267,31 @@ static void sk_attr() {
     }
 }
 
+static void sk_grid(int n, const EwaldTab& tab, int& gx, int& gy, int& span) {
+    sk_attr();
+    // resident blocks per SM for this shared-memory size (queried once per size)
+    static size_t last_smem = 0;
+    static int sms = 152, per_sm = 1;
+    const size_t smem = sk_smem(tab);
+    if (smem != last_smem) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sk, 32 * SK_WARPS, smem);
+        last_smem = smem;
+    }
+    gx = (tab.nchunk + 31) / 32;
+    const int want = std::max(1, sms * std::max(per_sm, 1) / gx);
+    span = (n + want - 1) / want;
+    span = std::min((span + SK_T * SK_WARPS - 1) / (SK_T * SK_WARPS) * (SK_T * SK_WARPS), SK_SPAN);
+    gy = (n + span - 1) / span;
+}
+
 void launch_ewald_sk(const float* q_raw, const Accum* acc, int n, float q_target, EwaldTab tab, cudaStream_t st) {
     cudaMemsetAsync(tab.S, 0, sizeof(double2) * tab.nk, st);
     if (n == 0 || tab.nchunk == 0) return;
     int gx, gy, span;
     sk_grid(n, tab, gx, gy, span);
-    sk_attr();
     k_sk<<<dim3(gx, gy), 32 * SK_WARPS, sk_smem(tab), st>>>(q_raw, acc, n, q_target, span, tab, nullptr, nullptr,
                                                             &const_cast<Accum*>(acc)->status);
 }
@@ -266,7 +301,6 @@ void launch_ewald_sk_fused(const float* q_raw, Accum* acc, int n, float q_target
     if (n == 0 || tab.nchunk == 0) return;
     int gx, gy, span;
     sk_grid(n, tab, gx, gy, span);
-    sk_attr();
     k_sk<<<dim3(gx, gy), 32 * SK_WARPS, sk_smem(tab), st>>>(q_raw, acc, n, q_target, span, tab, group_done, acc,
                                                             &acc->status);
 }

@@ -13,6 +13,8 @@
 // through the adjoint of the backward kernel.  The kernel also initialises the
 // force / BEC accumulator of each atom (static force; q~^c_i on the BEC diagonal)
 // and adds the FP64 sums: sum phi, U^r = 1/2 sum q phi^r, U^s, P = sum q~^c r.
+#include <algorithm>
+
 #include "desc_math.cuh"
 #include "tma.cuh"
 
@@ -519,11 +521,22 @@ void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cuda
         attr = true;
     }
     const int groups = (n + 31) / 32;
-    // column splits: fill the 152 SMs x 8 resident blocks of 8 warps in one wave
-    int csplit = (152 * 8) / groups;
+    const size_t smem = sizeof(float2) * 32 * tab.nph;
+    // column splits: fill the resident block slots (SMs x blocks per SM at this shared-memory
+    // size) in one wave; a partial second wave would double the time of the SMs running it
+    static size_t last_smem = 0;
+    static int slots = 152 * 8;
+    if (smem != last_smem) {
+        int dev = 0, sms = 152, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_field_k<W>, 32 * W, smem);
+        slots = sms * std::max(per_sm, 1);
+        last_smem = smem;
+    }
+    int csplit = slots / groups;
     if (csplit < 1) csplit = 1;
     if (csplit > tab.ncol) csplit = tab.ncol;
-    size_t smem = sizeof(float2) * 32 * tab.nph;
     k_field_k<W><<<groups * csplit, 32 * W, smem, st>>>(n, tab, csplit, kfield, acc);
 }
 
