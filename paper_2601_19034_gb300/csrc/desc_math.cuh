@@ -173,27 +173,47 @@ __device__ __forceinline__ void zero_atom_fields(float4* __restrict__ base, int 
     else base[2 * (size_t)n + 3 * (size_t)k + (part - 2)] = z;
 }
 
-// Corrected charge q^c_k, total potential phi_k = phi^k + phi^r + phi^s and its
-// mean over atoms (sum phi^k and sum phi^r are accumulated by the field kernels;
-// sum_k phi^s_k = -2 k_e alpha / sqrt(pi) sum q^c = -2 k_e alpha / sqrt(pi) Q / sqrt(eps_inf)).
+// Block-uniform scalars of the charge correction and the adjoint: the shift
+// delta = (Q / sqrt(eps_inf) - sum q) / N of the corrected charges, the mean potential
+// (sum phi^k + sum phi^r + sum phi^s) / N with sum_k phi^s_k = -2 k_e alpha / sqrt(pi) Q / sqrt(eps_inf),
+// and the mean charge weight of a vector-Jacobian product.  Thread 0 forms each numerator
+// from the FP64 sums, rounds it to FP32 and scales it by 1/N: an FP64 division is a long
+// instruction sequence on a unit with 1/64 of the FP32 rate, so it is not evaluated per
+// atom.  Every thread of the block calls this once, before any early exit (it synchronises).
+struct ChargeScalars {
+    float delta, phibar, gq_mean;
+};
+
+__device__ __forceinline__ ChargeScalars block_charge_scalars(const Accum* __restrict__ acc_in, float q_target, int n,
+                                                              int mode, float alpha) {
+    __shared__ ChargeScalars cs_shared;
+    if (threadIdx.x == 0) {
+        const float inv_n = n > 0 ? 1.f / (float)n : 0.f;
+        const double self = mode == 1 ? -2.0 * (double)KE * (double)alpha * 0.564189583547756287 : 0.0;
+        ChargeScalars c;
+        c.delta = (float)((double)q_target - acc_in->sum_q) * inv_n;
+        c.phibar = (float)(acc_in->sum_phi + self * (double)q_target) * inv_n;
+        c.gq_mean = (float)acc_in->sum_gq * inv_n;
+        cs_shared = c;
+    }
+    __syncthreads();
+    return cs_shared;
+}
+
+// Corrected charge q^c_k and total potential phi_k = phi^k + phi^r + phi^s.
 // Weight of dq_k/dD in the adjoint: g_E (phi_k - mean phi) + (g_q,k - mean g_q)
 // (the charge correction makes dq^c_j/dq_l = delta_jl - 1/N).
-__device__ __forceinline__ float charge_adjoint_weight(const FieldIn& fin, const Accum* __restrict__ acc_in, int k,
-                                                       int n, float dphi) {
+__device__ __forceinline__ float charge_adjoint_weight(const FieldIn& fin, const ChargeScalars& cs, int k, float dphi) {
     float w = fin.e_weight * dphi;
-    if (fin.gq) w += __ldg(&fin.gq[__ldg(&fin.sidx[k])]) - (float)(acc_in->sum_gq / (double)n);
+    if (fin.gq) w += __ldg(&fin.gq[__ldg(&fin.sidx[k])]) - cs.gq_mean;
     return w;
 }
 
-__device__ __forceinline__ void assemble_potential(const FieldIn& fin, const Accum* __restrict__ acc_in,
-                                                   const float* __restrict__ q_raw, int k, int n, float& qc,
-                                                   float& phi_k, float& phibar) {
-    const double nd = (double)n;
-    const float delta = (float)(((double)fin.q_target - acc_in->sum_q) / nd);
-    qc = __ldg(&q_raw[k]) + delta;
+__device__ __forceinline__ void assemble_potential(const FieldIn& fin, const ChargeScalars& cs,
+                                                   const float* __restrict__ q_raw, int k, float& qc, float& phi_k) {
+    qc = __ldg(&q_raw[k]) + cs.delta;
     const float self = fin.mode == 1 ? -2.f * KE * fin.alpha * 0.564189583547756287f : 0.f;
     phi_k = fin.kfield[k].w + fin.rfield[k].w + self * qc;
-    phibar = (float)((acc_in->sum_phi + (double)self * (double)fin.q_target) / nd);
 }
 
 }  // namespace

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
     float* sp = sm;
     float* sphi = sm + ((lay.total + 3) & ~3);
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
-    __syncthreads();
+    const ChargeScalars cs = block_charge_scalars(acc_in, fin.q_target, n, fin.mode, fin.alpha);   // synchronises
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / TPA;
     const int lane = gt % TPA;
@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(128) k_desc_bwd(const float4* __restrict__ pos
         const float4 pi = __ldg(&pos4[i]);
         const int ti = __float_as_int(pi.w);
         const float seps = sp[lay.sqrt_eps];
-        float qc, phi_i, phibar;
-        assemble_potential(fin, acc_in, q_raw, i, n, qc, phi_i, phibar);
-        const float wq = charge_adjoint_weight(fin, acc_in, i, n, phi_i - phibar);
+        float qc, phi_i;
+        assemble_potential(fin, cs, q_raw, i, qc, phi_i);
+        const float wq = charge_adjoint_weight(fin, cs, i, phi_i - cs.phibar);
         float lam[NDES], kap[NDES];
 #pragma unroll
         for (int v = 0; v < NDES; ++v) {

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
     float* lk = csm + round4(lay.total) + wib * BW_WARP;
     float* ph = lk + BW_LK;
     float* mu = ph + BW_PHI;
-    __syncthreads();
+    const ChargeScalars cs = block_charge_scalars(acc_in, fin.q_target, n, fin.mode, fin.alpha);   // synchronises
     float w[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) w[q] = 0.f;
@@ -323,9 +323,9 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
             dd4[3] = 1.5f * (t2[0] - t2[1]);
             dd4[4] = 6.f * t2[3];
         }
-        float qc, phi_k, phibar;
-        assemble_potential(fin, acc_in, q_raw, k, n, qc, phi_k, phibar);
-        const float wq = charge_adjoint_weight(fin, acc_in, k, n, phi_k - phibar);
+        float qc, phi_k;
+        assemble_potential(fin, cs, q_raw, k, qc, phi_k);
+        const float wq = charge_adjoint_weight(fin, cs, k, phi_k - cs.phibar);
         const float lkl = fmaf(wq, dqv, fin.e_weight * duv);   // lambda_v in lane v
         const float lkk = seps * dqv;                         // kappa_v in lane v
         // dE/dA_{n,lm} for both adjoints

@@ -49,20 +49,27 @@ __device__ __forceinline__ void finalize_k(const EwaldTab& tab, int k, double v[
     v[6] += e * (double)(-fac * ky * kz);
 }
 
-// Block reduction of the 7 FP64 terms and the atomics into the accumulators.
-__device__ __forceinline__ void flush_k_terms(double v[7], Accum* __restrict__ acc, double* red /* [7][32] */) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Block reduction of the 7 FP64 terms and the atomics into the accumulators.  The terms
+// go through shared memory (red: 7 x blockDim.x + 7 x 32 doubles): 7 x (blockDim.x / 32)
+// threads add 32 terms each, then 7 threads add those partial sums, so the FP64 unit
+// (1/64 of the FP32 rate) sees about 8 adds per term instead of a shuffle tree in every lane.
+__device__ __forceinline__ void flush_k_terms(double v[7], Accum* __restrict__ acc, double* red) {
+    const int nt = blockDim.x, nw = nt >> 5;
+    double* part = red + 7 * nt;   // [7][32]
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        double x = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[q * 32 + w] = x;
+    for (int q = 0; q < 7; ++q) red[q * nt + threadIdx.x] = v[q];
+    __syncthreads();
+    if ((int)threadIdx.x < 7 * nw) {
+        const int q = threadIdx.x / nw, p = threadIdx.x - q * nw;
+        const double* src = red + q * nt + p * 32;
+        double t = 0.0;
+        for (int i = 0; i < 32; ++i) t += src[i];
+        part[q * 32 + p] = t;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
         double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x * 32 + q];
+        for (int p = 0; p < nw; ++p) t += part[threadIdx.x * 32 + p];
         if (threadIdx.x == 0) {
             atomicAdd(&acc->e_kspace, t);
         } else {
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ 
     }
     if (threadIdx.x == 0) {
         failed = 0;
-        sdelta = (float)(((double)q_target - acc_in->sum_q) / (double)n);   // charge correction, once
+        sdelta = (float)((double)q_target - acc_in->sum_q) * (1.f / (float)n);   // charge correction, once
     }
     __syncthreads();
     const float delta = sdelta;
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ 
         double2* dst = &tab.S[8 * gl + (uc >> 1)];
         atomicAdd((uc & 1) ? &dst->y : &dst->x, (double)sum);
     }
-    double* red = reinterpret_cast<double*>(sk_dyn);   // [7][32] for the finalisation below
+    double* red = reinterpret_cast<double*>(sk_dyn);   // 7 x 256 + 7 x 32 doubles for the finalisation
     if (!group_done) return;
     __threadfence();
     __syncthreads();
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(32 * SK_WARPS) k_sk(const float* __restrict__ 
 }
 
 __global__ void k_sk_finalize(EwaldTab tab, Accum* __restrict__ acc) {
-    __shared__ double red[7 * 32];
+    __shared__ double red[7 * 256 + 7 * 32];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (k < tab.nk) finalize_k(tab, k, v);
@@ -253,9 +260,10 @@ void launch_ewald_phases(const float4* pos4, int n, EwaldTab tab, cudaStream_t s
 // blocks where the atoms allow (a partial second wave would double the time of the SMs
 // that run it).
 static size_t sk_smem(const EwaldTab& tab) {
-    // each warp's ring of tile buffers; later also the reduction (SK_WARPS x 16 x 32 floats)
+    // each warp's ring of tile buffers; later also the reductions (SK_WARPS x 16 x 32 floats,
+    // then 7 x 256 + 7 x 32 doubles)
     size_t ring = sizeof(float2) * SK_T * tab.nph * SK_NB * SK_WARPS;
-    size_t red = sizeof(float) * SK_WARPS * 16 * 32;
+    size_t red = std::max(sizeof(float) * SK_WARPS * 16 * 32, sizeof(double) * 7 * (32 * SK_WARPS + 32));
     return std::max(ring, red);
 }
 

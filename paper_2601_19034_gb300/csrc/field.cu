@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
     const int i0 = blockIdx.x * 32;
     const int i = i0 + lane;
     const bool valid = i < n;
-    const float delta = (float)(((double)q_target - acc->sum_q) / (double)n);
+    const float delta = block_charge_scalars(acc, q_target, n, 0, 0.f).delta;   // synchronises
     if (ewald) {
         for (int idx = threadIdx.x; idx < 32 * tab.nph; idx += blockDim.x) {
             int a = idx / tab.nph;
@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
 #pragma unroll
     for (int q = 0; q < 9; ++q) wv[q] = 0.f;
     float phr = 0.f, ereal = 0.f;
+    const float delta = block_charge_scalars(acc_in, q_target, n, 0, 0.f).delta;   // synchronises
     if (k < n) {
-        const float delta = (float)(((double)q_target - acc_in->sum_q) / (double)n);
         const float4 pk = __ldg(&spos4[k]);
         const float qk = __ldg(&q_raw[k]) + delta;
         int total = 0;
@@ -400,9 +400,9 @@ __global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     // FP32 terms summed over a warp (32 atoms), then FP64 across warps and blocks
     float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // P (3), U^s, sum q~^c
+    const float delta = block_charge_scalars(acc, q_target, n, 0, 0.f).delta;   // synchronises
     if (k < n) {
         const int io = sidx ? __ldg(&sidx[k]) : k;
-        const float delta = (float)(((double)q_target - acc->sum_q) / (double)n);
         const float qc = __ldg(&q_raw[k]) + delta;
         const float qt = seps * qc;
         const float* a = acc12 + 12 * (size_t)k;

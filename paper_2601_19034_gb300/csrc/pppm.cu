@@ -59,8 +59,8 @@ __global__ void k_pppm_spread(const float4* __restrict__ spos4, const float* __r
                               const Accum* __restrict__ acc_in, float q_target, PppmTab pm) {
     const int lane = threadIdx.x & 31;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const float delta = block_charge_scalars(acc_in, q_target, n, 0, 0.f).delta;   // synchronises
     if (k >= n) return;
-    const float delta = (float)(((double)q_target - acc_in->sum_q) / (double)n);
     const float4 p = __ldg(&spos4[k]);
     const float q = __ldg(&q_raw[k]) + delta;
     int sx, sy, sz;
