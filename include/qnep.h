@@ -70,7 +70,7 @@ typedef struct {
     double alpha;      /* Ewald splitting parameter (1/A) */
     double rc_real;    /* real-space cutoff (A), mode 1; <= rc_radial */
     double kmax;       /* Ewald: strict wave-vector cutoff |k| < kmax (1/A) */
-    int    mesh[3];    /* PPPM mesh (even sizes) */
+    int    mesh[3];    /* PPPM mesh (even sizes, fewer than 2^31 points in all) */
     int    order;      /* PPPM assignment order; this build supports 5 */
     double q_total;    /* target total charge Q of the naked charges (Eq. charge-scaling) */
 } qnep_elec;

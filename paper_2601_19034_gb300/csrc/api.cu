@@ -205,6 +205,7 @@ qnep_status setup_pppm(qnep_model* m, const double L[3], cudaStream_t st) {
         pm.nz = m->es.mesh[2];
         pm.nreal = (size_t)pm.nx * pm.ny * pm.nz;
         pm.nhalf = (size_t)pm.nx * pm.ny * (pm.nz / 2 + 1);
+        if (pm.nreal >= ((size_t)1 << 31)) return fail(m, QNEP_ERR_ARG, "PPPM mesh above 2^31 points");
         CK(cudaMalloc((void**)&pm.rho, sizeof(float) * pm.nreal));
         CK(cudaMemset(pm.rho, 0, sizeof(float) * pm.nreal));
         CK(cudaMalloc((void**)&pm.shat, sizeof(float2) * pm.nhalf));

@@ -53,6 +53,10 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     float* hb = dbuf + 32;
     __syncthreads();
     double su = 0.0, sq = 0.0, sg = 0.0;
+    // lane 0 sums U, q (and the charge weights) of up to 8 atoms in FP32, then adds the
+    // partial sums in FP64 (FP64 runs at 1/64 of the FP32 rate)
+    float pu = 0.f, pq = 0.f, pg = 0.f;
+    int np = 0;
     // dynamic scheduling: each warp takes the next atom until all are done
     for (;;) {
         int k = 0;
@@ -211,11 +215,20 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
             const float qq = uq - net[ParamLayout::B1Q];
             u_out[k] = uu;
             q_out[k] = qq;
-            su += (double)uu;   // a warp handles several atoms
-            sq += (double)qq;
+            pu += uu;   // a warp handles several atoms
+            pq += qq;
         }
         }
-        if (lane == 0 && gq_in) sg += (double)__ldg(&gq_in[__ldg(&sidx[k])]);
+        if (lane == 0) {
+            if (gq_in) pg += __ldg(&gq_in[__ldg(&sidx[k])]);
+            if (++np == 8) {
+                su += (double)pu;
+                sq += (double)pq;
+                sg += (double)pg;
+                pu = pq = pg = 0.f;
+                np = 0;
+            }
+        }
         if (do_phase) {
             for (int e = lane; e < tab.nph; e += 32) tab.phase[(size_t)k * tab.nph + e] = phase_entry(pk, e, tab);
         }
@@ -226,9 +239,9 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     // block sums of U and q (FP64), one atomic per block
     __shared__ double red[3][CW];
     if (lane == 0) {
-        red[0][wib] = su;
-        red[1][wib] = sq;
-        red[2][wib] = sg;
+        red[0][wib] = su + (double)pu;
+        red[1][wib] = sq + (double)pq;
+        red[2][wib] = sg + (double)pg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -515,6 +528,8 @@ __global__ void __launch_bounds__(32 * CW) k_desc_bwd_coop(
 void set_num_sms(int n) {
     if (n > 0) g_num_sms = n;
 }
+
+int num_sms() { return g_num_sms; }
 
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a) {
     return sizeof(float) * ((size_t)round4(lay.total) + (size_t)CW * coop_fwd_warp_floats(cap_l, cap_a));

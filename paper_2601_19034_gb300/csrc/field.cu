@@ -196,29 +196,34 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
     }
 }
 
-// Real space (mode 1) for sorted atom k, one warp per atom, lanes over list entries:
+// Real space (mode 1), one warp per sorted atom k at a time (persistent warps over the
+// atoms), lanes over list entries:
 //   phi^r_k = k_e sum_j q_j erfc(alpha r)/r,  F^r_k = sum_j 2 F^{r,static}_kj,
 //   W^r -= r_kj (x) F^{r,static}_kj,  U^r = 1/2 sum_k q_k phi^r_k.
-// rfield[k] = (F^r, phi^r); the sums go to the FP64 accumulators once per block.
+// rfield[k] = (F^r, phi^r).  The virial stays in each lane over all of the warp's atoms
+// (one warp reduction at the end); U^r and sum phi^r are summed by lane 0 in FP32 over 8
+// atoms at a time, then in FP64; one set of FP64 atomics per block.
 __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, const float* __restrict__ q_raw,
                                               const int* __restrict__ nbr_list, const int* __restrict__ cnt_list, int n,
                                               int n_species, Geom g, float alpha, float q_target,
                                               const Accum* __restrict__ acc_in, float4* __restrict__ rfield,
                                               Accum* __restrict__ acc) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int k = blockIdx.x * (blockDim.x >> 5) + wib;
     float wv[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) wv[q] = 0.f;
-    float phr = 0.f, ereal = 0.f;
+    double sphi = 0.0, ser = 0.0;
+    float pphi = 0.f, per = 0.f;
+    int np = 0;
     const float delta = block_charge_scalars(acc_in, q_target, n, 0, 0.f).delta;   // synchronises
-    if (k < n) {
+    const float rc2 = g.rc_real * g.rc_real;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + wib; k < n; k += nwarps) {
         const float4 pk = __ldg(&spos4[k]);
         const float qk = __ldg(&q_raw[k]) + delta;
         int total = 0;
         for (int s = 0; s < n_species; ++s) total += __ldg(&cnt_list[(size_t)s * n + k]);
-        const float rc2 = g.rc_real * g.rc_real;
-        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float fx = 0.f, fy = 0.f, fz = 0.f, phr = 0.f;
         for (int e = lane; e < total; e += 32) {
             const int ent = list_entry(nbr_list, k, e, g.list_sa, g.list_se);
             const int j = entry_index(ent);
@@ -248,8 +253,17 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             fz += __shfl_xor_sync(0xffffffffu, fz, o);
         }
-        if (lane == 0) rfield[k] = make_float4(fx, fy, fz, phr);
-        ereal = 0.5f * qk * phr;
+        if (lane == 0) {
+            rfield[k] = make_float4(fx, fy, fz, phr);
+            pphi += phr;
+            per += 0.5f * qk * phr;
+            if (++np == 8) {
+                sphi += (double)pphi;
+                ser += (double)per;
+                pphi = per = 0.f;
+                np = 0;
+            }
+        }
     }
     __shared__ double red[11][8];
 #pragma unroll
@@ -260,8 +274,8 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
         if (lane == 0) red[q][wib] = (double)v;
     }
     if (lane == 0) {
-        red[9][wib] = (double)phr;     // every lane holds the reduced phi^r
-        red[10][wib] = (double)ereal;
+        red[9][wib] = sphi + (double)pphi;
+        red[10][wib] = ser + (double)per;
     }
     __syncthreads();
     if (threadIdx.x < 11) {
@@ -508,8 +522,15 @@ void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, c
                  int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
                  Accum* acc, cudaStream_t st) {
     if (n == 0) return;
-    k_real<<<(n + 7) / 8, 256, 0, st>>>(spos4, q_raw, nbr_list, cnt_list, n, n_species, g, alpha, q_target, acc_in,
-                                        rfield, acc);
+    // persistent warps: one wave of resident blocks, fewer for small systems
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_real, 256, 0);
+        per_sm = std::max(per_sm, 1);
+    }
+    const int blocks = std::max(1, std::min((n + 7) / 8, per_sm * num_sms()));
+    k_real<<<blocks, 256, 0, st>>>(spos4, q_raw, nbr_list, cnt_list, n, n_species, g, alpha, q_target, acc_in, rfield,
+                                   acc);
 }
 
 void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st) {

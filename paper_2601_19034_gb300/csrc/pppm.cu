@@ -16,6 +16,8 @@
 //                Eq. force-static-fft; the potential is the factor of Eq. force-dynamic-fft)
 #include <cufft.h>
 
+#include <algorithm>
+
 #include "desc_math.cuh"
 
 namespace qnep {
@@ -49,18 +51,16 @@ __device__ __forceinline__ void stencil_axis(float x, float inv_h, float inv_h_l
     s0 = (int)r - 2;                    // first of the five points (may be < 0 or >= N: wrapped by the caller)
 }
 
-__device__ __forceinline__ int wrap(int s, int n) {
-    s %= n;
-    return s < 0 ? s + n : s;
-}
+// stencil indices lie in [-2, N + 2) (s0 in [-2, N - 2], offsets 0..4): one periodic shift
+__device__ __forceinline__ int wrap(int s, int n) { return s < 0 ? s + n : (s >= n ? s - n : s); }
 
-// one warp per atom, lanes over the 125 stencil points
+// one warp per atom at a time (persistent warps), lanes over the 125 stencil points
 __global__ void k_pppm_spread(const float4* __restrict__ spos4, const float* __restrict__ q_raw, int n,
                               const Accum* __restrict__ acc_in, float q_target, PppmTab pm) {
     const int lane = threadIdx.x & 31;
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const float delta = block_charge_scalars(acc_in, q_target, n, 0, 0.f).delta;   // synchronises
-    if (k >= n) return;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += nwarps) {
     const float4 p = __ldg(&spos4[k]);
     const float q = __ldg(&q_raw[k]) + delta;
     int sx, sy, sz;
@@ -79,6 +79,7 @@ __global__ void k_pppm_spread(const float4* __restrict__ spos4, const float* __r
         }
         const size_t idx = ((size_t)wrap(sx + a, pm.nx) * pm.ny + wrap(sy + b, pm.ny)) * pm.nz + wrap(sz + c, pm.nz);
         atomicAdd(&pm.rho[idx], q * wa * wb * wc);
+    }
     }
 }
 
@@ -126,13 +127,20 @@ __global__ void k_pppm_gopt(PppmTab pm, double alpha, double vol) {
     pm.gopt[idx] = (float)(g * u / (den * den));
 }
 
-// S G_opt and the three i k S G_opt fields; U^k and W^k (FP32 terms, FP64 across warps)
+// S G_opt and the three i k S G_opt fields; U^k and W^k.  Persistent threads over the half
+// spectrum (indices fit 32 bits: the mesh is limited to 2^31 points); each thread sums its
+// terms in FP32 over 8 points at a time and in FP64 across them, then FP64 across warps.
 __global__ void __launch_bounds__(256) k_pppm_green(PppmTab pm, float alpha, Accum* __restrict__ acc) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double vd[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (idx < pm.nhalf) {
-        int n1, n2, n3;
-        mesh_n(idx, pm, n1, n2, n3);
+    int np = 0;
+    const unsigned nhalf = (unsigned)pm.nhalf, nzc = (unsigned)(pm.nz / 2 + 1), ny = (unsigned)pm.ny;
+    const float fac0 = 2.f / (4.f * alpha * alpha);
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nhalf; idx += gridDim.x * blockDim.x) {
+        const unsigned row = idx / nzc, m2 = row / ny;
+        int n3 = (int)(idx - row * nzc), n2 = (int)(row - m2 * ny), n1 = (int)m2;
+        if (n1 >= (pm.nx + 1) / 2) n1 -= pm.nx;
+        if (n2 >= (pm.ny + 1) / 2) n2 -= pm.ny;
         const float g = pm.gopt[idx];
         const float2 s = pm.shat[idx];
         const float kx = TWO_PI_F * n1 / pm.len[0], ky = TWO_PI_F * n2 / pm.len[1], kz = TWO_PI_F * n3 / pm.len[2];
@@ -149,24 +157,34 @@ __global__ void __launch_bounds__(256) k_pppm_green(PppmTab pm, float alpha, Acc
             const float mult = (n3 == 0 || (pm.nz % 2 == 0 && n3 == pm.nz / 2)) ? 1.f : 2.f;
             const float e = mult * KE * g * (s.x * s.x + s.y * s.y);
             const float k2 = kx * kx + ky * ky + kz * kz;
-            const float fac = 2.f / (4.f * alpha * alpha) + 2.f / k2;
-            v[0] = e;
-            v[1] = e * (1.f - fac * kx * kx);
-            v[2] = e * (1.f - fac * ky * ky);
-            v[3] = e * (1.f - fac * kz * kz);
-            v[4] = -e * fac * kx * ky;
-            v[5] = -e * fac * kx * kz;
-            v[6] = -e * fac * ky * kz;
+            const float fac = fac0 + 2.f / k2;
+            v[0] += e;
+            v[1] += e * (1.f - fac * kx * kx);
+            v[2] += e * (1.f - fac * ky * ky);
+            v[3] += e * (1.f - fac * kz * kz);
+            v[4] -= e * fac * kx * ky;
+            v[5] -= e * fac * kx * kz;
+            v[6] -= e * fac * ky * kz;
+        }
+        if (++np == 8) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                vd[q] += (double)v[q];
+                v[q] = 0.f;
+            }
+            np = 0;
         }
     }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) vd[q] += (double)v[q];
     __shared__ double red[7][8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        float x = v[q];
+        double x = vd[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[q][w] = (double)x;
+        if (lane == 0) red[q][w] = x;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
@@ -185,13 +203,17 @@ __global__ void __launch_bounds__(256) k_pppm_green(PppmTab pm, float alpha, Acc
     }
 }
 
-// one warp per atom, lanes over the 125 stencil points of the 4 fields
+// one warp per atom at a time (persistent warps), lanes over the 125 stencil points of the
+// 4 fields; lane 0 sums phi in FP32 over 8 atoms at a time, then in FP64
 __global__ void k_pppm_gather(const float4* __restrict__ spos4, int n, PppmTab pm, float4* __restrict__ kfield,
                               Accum* __restrict__ acc) {
     const int lane = threadIdx.x & 31;
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    float ph = 0.f;
-    if (k < n) {
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    double sphi = 0.0;
+    float pphi = 0.f;
+    int np = 0;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += nwarps) {
+        float ph = 0.f;
         const float4 p = __ldg(&spos4[k]);
         int sx, sy, sz;
         float wx[5], wy[5], wz[5];
@@ -224,15 +246,23 @@ __global__ void k_pppm_gather(const float4* __restrict__ spos4, int n, PppmTab p
             ez += __shfl_xor_sync(0xffffffffu, ez, o);
         }
         ph *= 2.f * KE;
-        if (lane == 0) kfield[k] = make_float4(-2.f * KE * ex, -2.f * KE * ey, -2.f * KE * ez, ph);
+        if (lane == 0) {
+            kfield[k] = make_float4(-2.f * KE * ex, -2.f * KE * ey, -2.f * KE * ez, ph);
+            pphi += ph;
+            if (++np == 8) {
+                sphi += (double)pphi;
+                pphi = 0.f;
+                np = 0;
+            }
+        }
     }
-    __shared__ float red[8];
+    __shared__ double red[8];
     const int w = threadIdx.x >> 5;
-    if (lane == 0) red[w] = k < n ? ph : 0.f;
+    if (lane == 0) red[w] = sphi + (double)pphi;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += (double)red[q];
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
         atomicAdd(&acc->sum_phi, t);
     }
 }
@@ -247,14 +277,29 @@ int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc
                 float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st) {
     if (n == 0) return 0;
     const int threads = 256;
-    const unsigned blocks = (unsigned)(((long long)n * 32 + threads - 1) / threads);
-    k_pppm_spread<<<blocks, threads, 0, st>>>(spos4, q_raw, n, acc_in, q_target, pm);
+    // persistent warps over the atoms and persistent threads over the half spectrum: one
+    // wave of resident blocks (occupancy queried once per kernel)
+    static int occ_spread = 0, occ_green = 0, occ_gather = 0;
+    if (occ_spread == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_spread, k_pppm_spread, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_green, k_pppm_green, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_gather, k_pppm_gather, threads, 0);
+        occ_spread = std::max(occ_spread, 1);
+        occ_green = std::max(occ_green, 1);
+        occ_gather = std::max(occ_gather, 1);
+    }
+    const long long atom_blocks = ((long long)n * 32 + threads - 1) / threads;
+    const unsigned sblocks = (unsigned)std::min<long long>(atom_blocks, (long long)occ_spread * num_sms());
+    const unsigned hblocks = (unsigned)std::min<long long>(atom_blocks, (long long)occ_gather * num_sms());
+    const unsigned gblocks =
+        (unsigned)std::min<long long>((long long)((pm.nhalf + threads - 1) / threads), (long long)occ_green * num_sms());
+    k_pppm_spread<<<sblocks, threads, 0, st>>>(spos4, q_raw, n, acc_in, q_target, pm);
     if (cufftSetStream(r2c, st) != CUFFT_SUCCESS) return 1;
     if (cufftExecR2C(r2c, pm.rho, reinterpret_cast<cufftComplex*>(pm.shat)) != CUFFT_SUCCESS) return 1;
-    k_pppm_green<<<(unsigned)((pm.nhalf + 255) / 256), 256, 0, st>>>(pm, alpha, acc);
+    k_pppm_green<<<gblocks, threads, 0, st>>>(pm, alpha, acc);
     if (cufftSetStream(c2r, st) != CUFFT_SUCCESS) return 1;
     if (cufftExecC2R(c2r, reinterpret_cast<cufftComplex*>(pm.fhat), pm.field) != CUFFT_SUCCESS) return 1;
-    k_pppm_gather<<<blocks, threads, 0, st>>>(spos4, n, pm, kfield, acc);
+    k_pppm_gather<<<hblocks, threads, 0, st>>>(spos4, n, pm, kfield, acc);
     return 0;
 }
 

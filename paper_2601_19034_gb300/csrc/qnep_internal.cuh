@@ -185,6 +185,7 @@ void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const in
                                float* dtc = nullptr);
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a);
 void set_num_sms(int n);
+int num_sms();   // SMs of the device (persistent grids)
 void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,
