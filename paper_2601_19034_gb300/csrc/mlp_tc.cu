@@ -11,7 +11,9 @@
 // memory in the canonical K-major layout without swizzle (core matrices of 8 rows x
 // 16 bytes; K-adjacent cores 128 B apart, 8-row groups K/kpc x 128 B apart); one
 // thread issues the tcgen05.mma instructions, accumulators are in tensor memory and
-// are read back with tcgen05.ld (warp w owns lanes 32w..32w+31).  Every wait on an
+// are read back with tcgen05.ld (warp w owns lanes 32w..32w+31).  Blocks are persistent over
+// the tiles; each tile's descriptors arrive by one bulk copy into one of two shared-memory
+// buffers, the next tile's copy running while this tile is computed.  Every wait on an
 // mbarrier is bounded; a timeout sets a status bit and the block stops after
 // releasing its tensor memory.
 #include <stdint.h>
@@ -125,7 +127,7 @@ __device__ __forceinline__ void put_row(unsigned char* base, int row, int K, int
 }
 
 struct MlpSmem {   // byte offsets of the operands and small parameters in dynamic shared memory
-    uint32_t a1, a2, a3, b1, b2, par, total;
+    uint32_t a1, a2, a3, b1, b2, par, dtc, total;
 };
 
 template <int PREC>
@@ -139,12 +141,19 @@ __host__ __device__ constexpr MlpSmem mlp_layout(int S) {
     L.b2 = L.b1 + HP * S * KP * ES;
     L.par = L.b2 + KP * HP * S * ES;
     // b0, w1E, w1q [S][HP], b1E, b1Q [S], scaler [KP] (FP32)
-    L.total = L.par + (uint32_t)sizeof(float) * (3 * S * HP + 2 * S + KP);
+    L.dtc = (L.par + (uint32_t)sizeof(float) * (3 * S * HP + 2 * S + KP) + 127u) & ~127u;
+    // two FP32 descriptor tiles [TM][KP], filled by bulk copies
+    L.total = L.dtc + 2u * (uint32_t)sizeof(float) * TM * KP;
     return L;
 }
 
+// tanh(x) = 1 - 2 / (1 + e^{2x}) with the fast exponential and division: absolute error
+// about 1e-6, far below the BF16 / TF32 rounding of h in the next product (2^-9 / 2^-12);
+// +-1 for large |x| (e^{2x} overflows to inf or underflows to 0)
+__device__ __forceinline__ float tanh_fast(float x) { return 1.f - __fdividef(2.f, 1.f + __expf(2.f * x)); }
+
 template <int PREC>
-__global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, const float4* __restrict__ spos4,
+__global__ void __launch_bounds__(TM, 1) k_mlp_tc(const float* __restrict__ dtc, const float4* __restrict__ spos4,
                                                int n, const float* __restrict__ params, ParamLayout lay,
                                                float* __restrict__ du, float* __restrict__ dq, int d_sa, int d_sv,
                                                float* __restrict__ u_out, float* __restrict__ q_out,
@@ -153,6 +162,7 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
     constexpr int ES = O::ES;
     extern __shared__ __align__(128) unsigned char msm[];
     __shared__ uint64_t bar;
+    __shared__ __align__(8) uint64_t dbar[2];   // the two descriptor tiles
     __shared__ uint32_t tmem_base;
     __shared__ double red[2][TM / 32];
     __shared__ int failed;
@@ -170,6 +180,7 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
     float* pwq = par + 2 * S * HP;
     float* pb1 = par + 3 * S * HP;      // [S][2]
     float* psc = pb1 + 2 * S;           // [KP]
+    float* dbuf = reinterpret_cast<float*>(msm + L.dtc);   // [2][TM][KP]
 
     // weights of every species: B1 [32 S rows (s, mu)][32 K (v)] and B2 [32 rows (v)][32 S K (s, mu)]
     for (int row = tid; row < S * HP; row += TM) {   // B1 row (s, mu): W0_s[mu][0..31]
@@ -208,6 +219,8 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
     }
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&dbar[0], 1);
+        mbar_init(&dbar[1], 1);
         mbar_init_fence();
         failed = 0;
     }
@@ -224,24 +237,44 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
     double su = 0.0, sq = 0.0;
 
     const int ntiles = (n + TM - 1) / TM;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // descriptor tile of the block's i-th tile into buffer i & 1 (thread 0): one bulk copy of
+    // the tile's rows (contiguous, 128 B each)
+    auto issue = [&](int i) {
+        const int t = blockIdx.x + i * gridDim.x, cnt = min(TM, n - t * TM);
+        const uint32_t bytes = (uint32_t)(cnt * KP * sizeof(float));
+        fence_proxy_async_smem();
+        mbar_expect_tx(&dbar[i & 1], bytes);
+        bulk_g2s(dbuf + (i & 1) * TM * KP, dtc + (size_t)t * TM * KP, bytes, &dbar[i & 1]);
+    };
+    if (tid == 0 && (int)blockIdx.x < ntiles) issue(0);
+    int ti_next = 0;
+    if ((int)blockIdx.x * TM + tid < n) ti_next = __float_as_int(__ldg(&spos4[blockIdx.x * TM + tid]).w);
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int k = tile * TM + tid;
         const bool valid = k < n;
-        int ti = 0;
+        const int ti = valid ? ti_next : 0;
+        // the next tile streams in while this one is computed (its buffer was last read
+        // before the first barrier of the previous tile); its species are loaded now
+        const int knext = (tile + gridDim.x) * TM + tid;
+        if (tile + (int)gridDim.x < ntiles) {
+            if (tid == 0) issue(i + 1);
+            if (knext < n) ti_next = __float_as_int(__ldg(&spos4[knext]).w);
+        }
+        if (!mbar_wait_bounded(&dbar[i & 1], (uint32_t)((i >> 1) & 1))) failed = 1;
         // operand A1: this atom's scaled descriptor; A2 / A3 cleared (block-diagonal fill below)
         {
             float dv[KP];
             if (valid) {
-                const float4* src = reinterpret_cast<const float4*>(dtc + (size_t)k * KP);
+                const float4* src = reinterpret_cast<const float4*>(dbuf + (i & 1) * TM * KP + tid * KP);
 #pragma unroll
                 for (int q = 0; q < KP / 4; ++q) {
-                    const float4 x = __ldg(&src[q]);
+                    const float4 x = src[q];
                     dv[4 * q] = x.x;
                     dv[4 * q + 1] = x.y;
                     dv[4 * q + 2] = x.z;
                     dv[4 * q + 3] = x.w;
                 }
-                ti = __float_as_int(__ldg(&spos4[k]).w);
             } else {
 #pragma unroll
                 for (int q = 0; q < KP; ++q) dv[q] = 0.f;
@@ -284,7 +317,7 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
         float ue = 0.f, uqv = 0.f, ge[HP], gqv[HP];
 #pragma unroll
         for (int mu = 0; mu < HP; ++mu) {
-            const float h = tanhf(pre[mu] - pb0[ti * HP + mu]);
+            const float h = tanh_fast(pre[mu] - pb0[ti * HP + mu]);
             const float we = pwe[ti * HP + mu], wq = pwq[ti * HP + mu];
             ue = fmaf(we, h, ue);
             uqv = fmaf(wq, h, uqv);
@@ -314,8 +347,22 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
         float gu[KP], gq[KP];
         tmem_ld32(tmem + lane_base + COL_DU, gu);
         tmem_ld32(tmem + lane_base + COL_DQ, gq);
+        // rows of NDES floats in [n][NDES] order: staged in the free A2 / A3 regions (when a
+        // region holds TM x NDES floats) and written back as contiguous float4s (the tile's
+        // rows are one contiguous range)
+        const bool rowmajor = du && d_sv == 1 && d_sa == NDES && HP * S * ES >= NDES * (int)sizeof(float);
+        if (rowmajor) {
+            float* su_ = reinterpret_cast<float*>(A2);
+            float* sq_ = reinterpret_cast<float*>(A3);
+#pragma unroll
+            for (int v = 0; v < NDES; ++v) {
+                su_[tid * NDES + v] = gu[v] * psc[v];
+                sq_[tid * NDES + v] = gq[v] * psc[v];
+            }
+        }
         if (valid) {
-            if (du) {
+            if (rowmajor) {
+            } else if (du) {
 #pragma unroll
                 for (int v = 0; v < NDES; ++v) {
                     du[(size_t)k * d_sa + (size_t)v * d_sv] = gu[v] * psc[v];
@@ -327,10 +374,31 @@ __global__ void __launch_bounds__(TM) k_mlp_tc(const float* __restrict__ dtc, co
             su += (double)U;
             sq += (double)Q;
         }
+        if (rowmajor) {
+            __syncthreads();
+            const int cnt = min(TM, n - tile * TM);
+            const float4* su4 = reinterpret_cast<const float4*>(A2);
+            const float4* sq4 = reinterpret_cast<const float4*>(A3);
+            float4* du4 = reinterpret_cast<float4*>(du + (size_t)tile * TM * NDES);
+            float4* dq4 = reinterpret_cast<float4*>(dq + (size_t)tile * TM * NDES);
+            for (int e = tid; e < cnt * NDES / 4; e += TM) {
+                du4[e] = su4[e];
+                dq4[e] = sq4[e];
+            }
+            if (tid < (cnt * NDES) % 4) {   // a ragged tail (cnt odd): the last floats one by one
+                const int e = cnt * NDES / 4 * 4 + tid;
+                du[(size_t)tile * TM * NDES + e] = reinterpret_cast<const float*>(A2)[e];
+                dq[(size_t)tile * TM * NDES + e] = reinterpret_cast<const float*>(A3)[e];
+            }
+        }
         tc_fence_before();
         __syncthreads();   // operands and accumulators are reused by the next tile
         tc_fence_after();
-        if (failed) break;
+        if (failed) {
+            // a copy or an MMA did not complete in time: let the next tile's copy land (bounded)
+            if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&dbar[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1));
+            break;
+        }
     }
     // block sums of U and q (FP64), one atomic each
 #pragma unroll
@@ -374,15 +442,20 @@ void launch_mlp_tc(int precision, const float* dtc, const float4* spos4, int n, 
     if (n <= 0) return;
     const size_t smem = mlp_tc_smem(precision, lay.n_species);
     const int ntiles = (n + TM - 1) / TM;
-    // two blocks per SM at most (256 tensor-memory columns each)
-    const int grid = ntiles < 2 * num_sms ? ntiles : 2 * num_sms;
-    if (precision == PREC_BF16) {
+    // persistent blocks: at most two per SM (256 tensor-memory columns each), fewer when the
+    // operands of one block take more than half of the shared memory
+    if (precision == PREC_BF16)
         cudaFuncSetAttribute(k_mlp_tc<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_mlp_tc<PREC_BF16><<<grid, TM, smem, st>>>(dtc, spos4, n, params, lay, du, dq, d_sa, d_sv, u, q, acc);
-    } else {
+    else
         cudaFuncSetAttribute(k_mlp_tc<PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // 227 KB of shared memory per SM for blocks (2 KB of it for static data and reserve each)
+    int per_sm = (int)((size_t)227 * 1024 / (smem + 2048));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    const int grid = ntiles < per_sm * num_sms ? ntiles : per_sm * num_sms;
+    if (precision == PREC_BF16)
+        k_mlp_tc<PREC_BF16><<<grid, TM, smem, st>>>(dtc, spos4, n, params, lay, du, dq, d_sa, d_sv, u, q, acc);
+    else
         k_mlp_tc<PREC_TF32><<<grid, TM, smem, st>>>(dtc, spos4, n, params, lay, du, dq, d_sa, d_sv, u, q, acc);
-    }
 }
 
 }  // namespace qnep
