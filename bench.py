@@ -154,6 +154,15 @@ def _ewald_kcount(box, kmax):
     return int(((k2 > 0) & (k2 < kmax * kmax)).sum()) // 2
 
 
+# DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
+# capture of the current kernel on the first 160 structures x 64 candidates (17.49 GB for
+# 6.71e6 atom-evaluations; the traffic grows with the atom-evaluations).  Set to None when the
+# item kernel changes until it is captured again.
+ITEM_DRAM_BYTES_PER_EVAL = 17.49e9 / 6.71e6
+ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 160 x 64 case scaled by "
+                    "atom-evaluations (profiles/k_batch_items_llzo_160x64.md)")
+
+
 def _time_single(model, sysm, dev, steps, warmup, flush, want=None):
     """CUDA-graph replay of one force call; L2 flushed between calls; event-timed ms per call."""
     import torch
@@ -591,7 +600,8 @@ def run_batch(args):
                        else "single GPU", "wall_s": wall},
             "roofline": {"kernel": "k_batch_items", "bound": "alu", "achieved": flop / (item_ms * 1e-3) / 1e12,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / (item_ms * 1e-3) / 1e12 / fp32_peak,
-                         "traffic": None, "ms": item_ms, "prepass_ms": prep_ms,
+                         "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals, "traffic_unit": "bytes per launch",
+                         "traffic_source": ITEM_DRAM_SOURCE, "ms": item_ms, "prepass_ms": prep_ms,
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
                          "whole_call_frac": achieved / fp32_peak},
