@@ -600,7 +600,8 @@ def run_batch(args):
                        else "single GPU", "wall_s": wall},
             "roofline": {"kernel": "k_batch_items", "bound": "alu", "achieved": flop / (item_ms * 1e-3) / 1e12,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / (item_ms * 1e-3) / 1e12 / fp32_peak,
-                         "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals, "traffic_unit": "bytes per launch",
+                         "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals if ITEM_DRAM_BYTES_PER_EVAL else None,
+                         "traffic_unit": "bytes per launch",
                          "traffic_source": ITEM_DRAM_SOURCE, "ms": item_ms, "prepass_ms": prep_ms,
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
