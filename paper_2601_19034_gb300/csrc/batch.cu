@@ -1121,20 +1121,19 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                                 for (int t = 0; t < 8; ++t) {
                                     const float4 k4 = kw[hh * 8 + t];
                                     const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
+                                    // Re and Im of C conj(e) accumulated term by term, the k_z
+                                    // factor folded into the phase: six FMAs per candidate
+                                    const float ney = -e.y, zx = k4.z * e.x, zy = -k4.z * e.y;
                                     const float4* s4 = reinterpret_cast<const float4*>(sw + (hh * 8 + t) * CG + c0);
 #pragma unroll
                                     for (int u = 0; u < 8; ++u) {
-                                        const float4 v = s4[u];
-                                        // z = C conj(e) for the two candidates of v
-                                        float zr = fmaf(v.x, e.x, v.y * e.y), zi = fmaf(v.y, e.x, -v.x * e.y);
-                                        fphi[2 * u] += zr;
-                                        tt[2 * u] += zi;
-                                        ez[2 * u] = fmaf(k4.z, zi, ez[2 * u]);
-                                        zr = fmaf(v.z, e.x, v.w * e.y);
-                                        zi = fmaf(v.w, e.x, -v.z * e.y);
-                                        fphi[2 * u + 1] += zr;
-                                        tt[2 * u + 1] += zi;
-                                        ez[2 * u + 1] = fmaf(k4.z, zi, ez[2 * u + 1]);
+                                        const float4 v = s4[u];   // C of two candidates
+                                        fphi[2 * u] = fmaf(v.y, e.y, fmaf(v.x, e.x, fphi[2 * u]));
+                                        tt[2 * u] = fmaf(v.x, ney, fmaf(v.y, e.x, tt[2 * u]));
+                                        ez[2 * u] = fmaf(v.x, zy, fmaf(v.y, zx, ez[2 * u]));
+                                        fphi[2 * u + 1] = fmaf(v.w, e.y, fmaf(v.z, e.x, fphi[2 * u + 1]));
+                                        tt[2 * u + 1] = fmaf(v.z, ney, fmaf(v.w, e.x, tt[2 * u + 1]));
+                                        ez[2 * u + 1] = fmaf(v.z, zy, fmaf(v.w, zx, ez[2 * u + 1]));
                                     }
                                 }
                             }

@@ -55,8 +55,18 @@ def _errors(sysm, hp, params, elec, dev, precision, path="auto"):
     }
 
 
+def _one_species_water():
+    """The 64-water box with every atom of one species (a single network; the tensor-core
+    kernel then writes dU/dD and dq/dD row by row instead of through shared memory)."""
+    sysm, _, _, elec = wl.config_water_small()
+    sysm = wl.System(positions=sysm.positions, types=np.zeros_like(sysm.types), box=sysm.box, species=("O",))
+    hp = wl.HParams(n_species=1)
+    return sysm, hp, wl.random_params(hp, np.random.default_rng(43))[0], elec
+
+
 CASES = {
     "water64": lambda: wl.config_water_small(),
+    "water64_one_species": _one_species_water,
     "llzo192": lambda: (wl.llzo_base_cell(), wl.HParams(n_species=4),
                         wl.random_params(wl.HParams(n_species=4), np.random.default_rng(41))[0],
                         wl.Elec(mode=1, kind="ewald")),
