@@ -129,6 +129,107 @@ __global__ void k_order(const int* __restrict__ start, int ncells, const int* __
     }
 }
 
+// Small systems (up to 2048 atoms): the four binning steps of k_bin, k_scan, k_fill and
+// k_order in one block (counts, starts and fill cursors in shared memory), saving three
+// launches and their latency.  Same outputs, same atom order (by cell, then by input
+// index).  Measured: 192 atoms 17 -> 11 us for the binning; at 5000 atoms and more the
+// single block is slower than the four grid-wide kernels.
+constexpr int SMALL_BIN_ATOMS = 2048, SMALL_BIN_CELLS = 4096, SMALL_BIN_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_BIN_THREADS) k_bin_small(const float* __restrict__ pos,
+                                                                  const int* __restrict__ types, int n, Geom g,
+                                                                  float4* __restrict__ pos4, int* __restrict__ cell_of,
+                                                                  int* __restrict__ cell_start,
+                                                                  int* __restrict__ slot_atoms,
+                                                                  float4* __restrict__ spos4, int* __restrict__ sidx,
+                                                                  Accum* __restrict__ acc,
+                                                                  double2* __restrict__ zero_buf, int zero_count) {
+    __shared__ int cnt[SMALL_BIN_CELLS];
+    __shared__ int start[SMALL_BIN_CELLS + 1];
+    __shared__ int warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+    const int ncells = g.ncells;
+    if (tid == 0) {
+        double* a = reinterpret_cast<double*>(acc);
+        for (int k = 0; k < (int)(sizeof(Accum) / sizeof(double)); ++k) a[k] = 0.0;
+    }
+    for (int k = tid; k < zero_count; k += nt) zero_buf[k] = make_double2(0.0, 0.0);
+    for (int c = tid; c < ncells; c += nt) cnt[c] = 0;
+    __syncthreads();
+    // wrap, cell of each atom, counts
+    for (int i = tid; i < n; i += nt) {
+        float w[3];
+        for (int d = 0; d < 3; ++d) {
+            float x = pos[3 * i + d];
+            float f = floorf(x * g.invL[d]);
+            float y = fmaf(-f, g.L[d], x);
+            if (y >= g.L[d]) y -= g.L[d];
+            if (y < 0.f) y += g.L[d];
+            if (y >= g.L[d]) y = 0.f;
+            w[d] = y;
+        }
+        pos4[i] = make_float4(w[0], w[1], w[2], __int_as_float(types[i]));
+        const int c = (cell_coord(w[2], g.invL[2], g.nc[2]) * g.nc[1] + cell_coord(w[1], g.invL[1], g.nc[1])) * g.nc[0] +
+                      cell_coord(w[0], g.invL[0], g.nc[0]);
+        cell_of[i] = c;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the counts (chunks of nt cells, carried)
+    int carry = 0;
+    for (int base = 0; base < ncells; base += nt) {
+        const int c = base + tid;
+        const int v = c < ncells ? cnt[c] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = nt >> 5;
+            int t = lane < nw ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;   // inclusive warp prefix; lane 31 holds the chunk total
+        }
+        __syncthreads();
+        const int excl = carry + x - v + (wid > 0 ? warp_tot[wid - 1] : 0);
+        if (c < ncells) start[c] = excl;
+        carry += warp_tot[31];
+        __syncthreads();   // warp_tot is rewritten by the next chunk
+    }
+    if (tid == 0) start[ncells] = carry;
+    for (int c = tid; c < ncells; c += nt) cnt[c] = 0;   // fill cursors
+    __syncthreads();
+    for (int c = tid; c <= ncells; c += nt) cell_start[c] = start[c];
+    for (int i = tid; i < n; i += nt) {
+        const int c = cell_of[i];
+        slot_atoms[start[c] + atomicAdd(&cnt[c], 1)] = i;
+    }
+    __syncthreads();
+    // one warp per cell: rank the cell's atoms by input index
+    for (int c = wid; c < ncells; c += nt >> 5) {
+        const int s0 = start[c], m = start[c + 1] - s0;
+        for (int a = lane; a - lane < m; a += 32) {
+            const int mine = a < m ? slot_atoms[s0 + a] : 0x7fffffff;
+            int rank = 0;
+            for (int b = 0; b < m; b += 32) {
+                const int other = (b + lane) < m ? slot_atoms[s0 + b + lane] : 0x7fffffff;
+#pragma unroll 8
+                for (int q = 0; q < 32; ++q) rank += (__shfl_sync(0xffffffffu, other, q) < mine) ? 1 : 0;
+            }
+            if (a < m) {
+                spos4[s0 + rank] = pos4[mine];
+                sidx[s0 + rank] = mine;
+            }
+        }
+    }
+}
+
 __global__ void k_neighbors(const float4* __restrict__ spos4, const int* __restrict__ cell_start, int n,
                             int n_species, Geom g, int cap_list, int cap_ang, int* __restrict__ nbr_list,
                             int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang,
@@ -155,6 +256,12 @@ __global__ void k_neighbors(const float4* __restrict__ spos4, const int* __restr
 void launch_bin(const float* pos, const int* types, int n, const Geom& g, float4* pos4, int* cell_of, int* cell_count,
                 int* cell_start, int* cell_fill, int* slot_atoms, float4* spos4, int* sidx, Accum* acc,
                 double2* zero_buf, int zero_count, cudaStream_t st) {
+    if (n <= SMALL_BIN_ATOMS && g.ncells <= SMALL_BIN_CELLS && zero_count <= 64 * SMALL_BIN_THREADS) {
+        // counts in shared memory: cell_count / cell_fill are not used (and stay zero)
+        k_bin_small<<<1, SMALL_BIN_THREADS, 0, st>>>(pos, types, n, g, pos4, cell_of, cell_start, slot_atoms, spos4,
+                                                     sidx, acc, zero_buf, zero_count);
+        return;
+    }
     int blocks = (n + 255) / 256;
     int zb = (zero_count + 255) / 256;
     if (zb > blocks) blocks = zb;
