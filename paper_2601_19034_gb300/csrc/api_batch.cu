@@ -37,6 +37,7 @@ struct qnep_batch {
     BatchKTab* d_kt = nullptr;
     int4* d_chunk = nullptr;
     float4* d_kvec = nullptr;
+    int* d_kreal = nullptr;
     int2* d_items_lpt = nullptr;
     int2* d_items_nat = nullptr;
     int n_items = 0;
@@ -123,6 +124,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     std::vector<BatchStruct> sts(n_struct);
     std::vector<BatchKTab> kts;
     std::vector<int4> chunks;
+    std::vector<int> kreal;
     std::vector<float4> kvec;
     std::map<std::tuple<double, double, double>, int> tab_of;
     std::vector<int> nk_of;   // padded k count per table
@@ -181,16 +183,24 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
                 kt.invl_hi[d] = (float)il;
                 kt.invl_lo[d] = (float)(il - (double)kt.invl_hi[d]);
             }
+            kt.kreal_off = (int)kreal.size();
             for (int h = 0; h < kt.nchunk; ++h) {
                 const int4& c = ks.cols[ks.chunk_col[h]];
                 const int n3 = c.z + (8 * h - c.w);
-                chunks.push_back(make_int4(c.x, c.y, n3, 0));
+                int cnt = 0;   // the column's entries are contiguous from the chunk start
+                for (int q = 0; q < 8; ++q)
+                    if (ks.kg[8 * h + q] > 0.f) {
+                        kreal.push_back(8 * h + q);
+                        ++cnt;
+                    }
+                chunks.push_back(make_int4(c.x, c.y, n3, cnt));
                 for (int q = 0; q < 8; ++q) {
                     const float gk = ks.kg[8 * h + q];
                     kvec.push_back(make_float4((float)(two_pi * c.x / L[0]), (float)(two_pi * c.y / L[1]),
                                                (float)(two_pi * (n3 + q) / L[2]), (float)(4.0 * ke * gk)));
                 }
             }
+            kt.nkr = (int)kreal.size() - kt.kreal_off;
             nph_max = std::max(nph_max, kt.nph);
             nk_max = std::max(nk_max, 8 * kt.nchunk);
             it = tab_of.emplace(key, (int)kts.size()).first;
@@ -233,6 +243,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(upload(&b->d_kt, kts));
     CKB(upload(&b->d_chunk, chunks));
     CKB(upload(&b->d_kvec, kvec));
+    CKB(upload(&b->d_kreal, kreal));
     CKB(upload(&b->d_items_lpt, b->items_lpt));
     CKB(upload(&b->d_items_nat, b->items_nat));
     b->n_items = (int)b->items_lpt.size();
@@ -466,6 +477,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.kt = b->d_kt;
     a.chunk = b->d_chunk;
     a.kvec = b->d_kvec;
+    a.kreal = b->d_kreal;
     a.pt = b->d_pt;
     a.lay = b->lay;
     a.n_cand = b->n_cand;
@@ -593,7 +605,7 @@ const char* qnep_batch_last_error(const qnep_batch* b) { return b ? b->err.c_str
 void qnep_batch_destroy(qnep_batch* b) {
     if (!b) return;
     if (b->last_stream) cudaStreamSynchronize(b->last_stream);
-    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,     b->d_items_lpt,
+    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,

@@ -941,7 +941,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             // (task round, atom tile) sequence is copied while tile T - 1 is summed
             const int ps = a.nph_stride;
             const int tile_f = QT * CG + 2 * QT * ps;
-            const int ntask = (kt.nchunk + 3) >> 2;
+            const int ntask = (kt.nkr + 31) >> 5;   // 32 wave vectors per task, padding left out
             const int nfl = (n + QT * FLUSH_TILES - 1) / (QT * FLUSH_TILES);
             const int ntile = (n + QT - 1) / QT;
             const int total = ((ntask + NW - 1) / NW) * ntile;
@@ -959,14 +959,15 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             for (int tb = 0; tb < ntask; tb += NW) {
                 const int task = tb + warp;
                 const bool act = task < ntask;
-                const int h = task * 4 + (lane >> 3), t = lane & 7;
-                const bool kval = act && h < kt.nchunk;
-                int e1 = 0, e2 = kt.yoff, e3 = kt.zoff;
+                const int v = task * 32 + lane;
+                const bool kval = act && v < kt.nkr;
+                int kl = 0, e1 = 0, e2 = kt.yoff, e3 = kt.zoff;   // kl: padded index of the lane's k
                 if (kval) {
-                    const int4 ci = __ldg(&a.chunk[kt.chunk_off + h]);
+                    kl = __ldg(&a.kreal[kt.kreal_off + v]);
+                    const int4 ci = __ldg(&a.chunk[kt.chunk_off + (kl >> 3)]);
                     e1 = ci.x;
                     e2 = kt.yoff + ci.y + kt.n2max;
-                    e3 = kt.zoff + ci.z + t + kt.n3max;
+                    e3 = kt.zoff + ci.z + (kl & 7) + kt.n3max;
                 }
                 float sr[CG], si[CG];
 #pragma unroll
@@ -1006,7 +1007,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     if (act && (++tiles == FLUSH_TILES || j0 + QT >= n)) {
                         tiles = 0;
                         if (kval) {
-                            float4* dst = reinterpret_cast<float4*>(skp + ((size_t)fl * nkp + 8 * h + t) * CG);
+                            float4* dst = reinterpret_cast<float4*>(skp + ((size_t)fl * nkp + kl) * CG);
 #pragma unroll
                             for (int c = 0; c < CG; c += 2) dst[c >> 1] = make_float4(sr[c], si[c], sr[c + 1], si[c + 1]);
                         }
@@ -1024,9 +1025,9 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     // lane = candidate: S in FP64 over the partial sums, U^k += (w/2)|S|^2 and the
                     // FP32 copy C = w S, w = 4 k_e G(k)
                     for (int kk = 0; kk < 32; ++kk) {
-                        const int hk = task * 4 + (kk >> 3);
-                        if (hk >= kt.nchunk) break;
-                        const int kl = 8 * hk + (kk & 7);
+                        const int vk = task * 32 + kk;
+                        if (vk >= kt.nkr) break;
+                        const int kl = __ldg(&a.kreal[kt.kreal_off + vk]);
                         const float w = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]).w;
                         double Sr = 0.0, Si = 0.0;
                         for (int f = 0; f < nfl; ++f) {
@@ -1116,9 +1117,10 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                                 }
                                 const float2 xy =
                                     cmul(ph[ci.x * 32 + lane], ph[(kt.yoff + ci.y + kt.n2max) * 32 + lane]);
-                                // padding wave vectors carry C = 0 and add nothing: no branch here
+                                // the chunk's entries that are not padding (C of padding is not written)
 #pragma unroll
                                 for (int t = 0; t < 8; ++t) {
+                                    if (t >= ci.w) break;
                                     const float4 k4 = kw[hh * 8 + t];
                                     const float2 e = cmul(xy, ph[(kt.zoff + ci.z + t + kt.n3max) * 32 + lane]);
                                     // Re and Im of C conj(e) accumulated term by term, the k_z

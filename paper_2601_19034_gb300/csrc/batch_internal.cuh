@@ -42,6 +42,8 @@ struct BatchKTab {
     int yoff, zoff;
     int nchunk;
     int chunk_off;
+    int nkr;         // wave vectors of the half space (the chunks' non-padding entries)
+    int kreal_off;   // their padded indices: kreal[kreal_off .. kreal_off + nkr)
     float invl_hi[3], invl_lo[3];
 };
 
@@ -79,7 +81,8 @@ struct BatchArgs {
     // tables
     const BatchStruct* st;
     const BatchKTab* kt;
-    const int4* chunk;       // [n_chunks] (n1, n2, first n3, 0)
+    const int4* chunk;       // [n_chunks] (n1, n2, first n3, entries of the chunk that are not padding)
+    const int* kreal;        // padded index (8 h + t) of every wave vector, per k-table
     const float4* kvec;      // [8 n_chunks] (kx, ky, kz, 4 k_e G) (G = 0 on padding)
     // parameters by candidate group: [group][p][CG] (lane-minor)
     const float* pt;
