@@ -58,7 +58,7 @@ constexpr int PR_S = PR_A + MAX_SPECIES * NA * KA * CG;  // descriptor scaler [N
 constexpr int PARAM_FLOATS = PR_S + NDES * CG;
 constexpr int QT = 64;                         // atoms per charge tile of the S(k) phase
 constexpr int FLUSH_TILES = 8;                 // FP32 partial sums cover 512 atoms
-constexpr int KW = 32;                         // wave vectors per staged window of the field pass
+constexpr int KW = 64;                         // wave vectors per staged window of the field pass
 constexpr int NSUMS = 6;                       // per-candidate FP64 sums
 constexpr int WIN_F2 = KW * CG + 2 * KW + KW / 4;   // float2 per field window: C(k) | k | chunks
 
@@ -1255,6 +1255,12 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         }
     }
 }
+
+// the field pass at the largest phase rows fits the 227 KB of shared memory of a block
+static_assert(sizeof(double) * (8 + NSUMS) * CG + sizeof(float) * 4 * CG +
+                      sizeof(float2) * ((size_t)8 * BATCH_MAX_NPH * 32 + 2 * (size_t)WIN_F2) <=
+                  227 * 1024,
+              "field windows and phase rows exceed shared memory");
 
 template <int NW>
 size_t item_smem(int nph_max) {

@@ -20,8 +20,8 @@
 namespace qnep {
 
 constexpr int CG = 32;               // candidates per item (one per lane)
-constexpr int BATCH_MAX_NPH = 96;    // phase factors per atom (n_max <= 17 per axis: edges up to
-                                     // ~48 A at k_max = 2.23 1/A)
+constexpr int BATCH_MAX_NPH = 94;    // phase factors per atom (n_max <= 16 per axis: edges up to
+                                     // ~45 A at k_max = 2.23 1/A; bounds the field pass's shared memory)
 constexpr int BATCH_MAX_CELLS = 512; // cell grid per structure (8 per axis at most)
 constexpr int BATCH_GR = 20, BATCH_GA = 48;   // floats per radial / angular pair row
 

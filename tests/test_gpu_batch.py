@@ -161,6 +161,9 @@ def test_argument_errors_before_gpu_work(dev):
     with pytest.raises(_lib.QnepError) as e:   # box edge below the 6 A list cutoff
         b.compute(pos, typ, [0, 10], np.diag([5.0, 20.0, 20.0])[None])
     assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    with pytest.raises(_lib.QnepError) as e:   # box edge above the k-space tables' limit (~45 A)
+        b.compute(pos, typ, [0, 10], np.diag([50.0, 50.0, 50.0])[None])
+    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
     with pytest.raises(_lib.QnepError) as e:   # offsets must not decrease
         b.compute(pos, typ, [0, 10, 5], np.stack([np.eye(3) * 20.0] * 2))
     assert e.value.status == _lib.QNEP_ERR_ARG
