@@ -155,10 +155,10 @@ def _ewald_kcount(box, kmax):
 
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
-# capture of the current kernel on the first 160 structures x 64 candidates (17.49 GB for
+# capture of the current kernel on the first 160 structures x 64 candidates (17.36 GB for
 # 6.71e6 atom-evaluations; the traffic grows with the atom-evaluations).  Set to None when the
 # item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = None   # the item kernel changed: capture again
+ITEM_DRAM_BYTES_PER_EVAL = 17.36e9 / 6.71e6
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 160 x 64 case scaled by "
                     "atom-evaluations (profiles/k_batch_items_llzo_160x64.md)")
 
