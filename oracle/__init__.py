@@ -19,6 +19,7 @@ Modules
   ewald       real-space, reciprocal-space (direct k sum) and self energies
   pppm        PPPM mesh energy, potential and ik-differentiated force (Sec. II.F)
   forcecall   the full force call: energy, forces, virial, charges, BEC, P
+  field       external-field force and polarization current from the BEC (Sec. II.D)
   params      unpacking of the documented parameter blob
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
