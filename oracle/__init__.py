@@ -20,6 +20,7 @@ Modules
   pppm        PPPM mesh energy, potential and ik-differentiated force (Sec. II.F)
   forcecall   the full force call: energy, forces, virial, charges, BEC, P
   field       external-field force and polarization current from the BEC (Sec. II.D)
+  training    population loss terms of Sec. II.E and the SNES update it drives
   params      unpacking of the documented parameter blob
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against

@@ -1,0 +1,97 @@
+"""Pins of the oracle's population loss and SNES update (Sec. II.E; SNES of Schaul et al. 2011).
+
+D_e and D_f against brute-force loops over structures and atoms and against
+closed forms; the utilities' zero sum and ordering; rank invariance of the
+update; and SNES converging on a separable quadratic (a sign error in either
+gradient, or in the utilities, stops it converging).
+"""
+import math
+
+import numpy as np
+
+from oracle import training as tr
+
+
+def _case(seed=0, c=5, sizes=(3, 0, 7, 1)):
+    rng = np.random.default_rng(seed)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    n, s = off[-1], len(sizes)
+    e = rng.normal(size=(c, s)) * 10
+    e_ref = rng.normal(size=s) * 10
+    f = rng.normal(size=(c, n, 3))
+    f_ref = rng.normal(size=(n, 3))
+    z = rng.normal(size=(c, 11))
+    return e, f, e_ref, f_ref, off, z
+
+
+def test_loss_terms_match_brute_force():
+    e, f, e_ref, f_ref, off, z = _case()
+    d_e, d_f, l1, l2 = tr.loss_terms(e, f, e_ref, f_ref, off, z)
+    for c in range(e.shape[0]):
+        acc, cnt = 0.0, 0
+        for s in range(len(off) - 1):
+            n_s = off[s + 1] - off[s]
+            if n_s == 0:
+                continue
+            acc += ((e[c, s] - e_ref[s]) / n_s) ** 2
+            cnt += 1
+        assert abs(d_e[c] - math.sqrt(acc / cnt)) < 1e-12
+        acc = 0.0
+        for i in range(off[-1]):
+            for b in range(3):
+                acc += (f[c, i, b] - f_ref[i, b]) ** 2
+        assert abs(d_f[c] - math.sqrt(acc / (3 * off[-1]))) < 1e-12
+        assert abs(l1[c] - sum(abs(x) for x in z[c])) < 1e-12
+        assert abs(l2[c] - sum(x * x for x in z[c])) < 1e-12
+
+
+def test_loss_closed_forms():
+    e, f, e_ref, f_ref, off, z = _case(seed=1)
+    n_s = np.diff(off)
+    delta = np.array([0.3, -0.02, 0.0, 1.5, -0.7])
+    e_shift = e_ref[None, :] + delta[:, None] * n_s[None, :]
+    c_f = np.array([0.1, -0.25, 0.0, 2.0, 0.04])
+    f_shift = f_ref[None] + c_f[:, None, None]
+    d_e, d_f, _, _ = tr.loss_terms(e_shift, f_shift, e_ref, f_ref, off, z)
+    np.testing.assert_allclose(d_e, np.abs(delta), atol=1e-12)
+    np.testing.assert_allclose(d_f, np.abs(c_f), atol=1e-12)
+    terms = tr.loss_terms(e_ref[None].repeat(5, 0), f_ref[None].repeat(5, 0), e_ref, f_ref, off, z)
+    np.testing.assert_allclose(tr.loss(terms, 1.0, 1.0, 0.05, 0.01),
+                               0.05 * np.abs(z).sum(1) + 0.01 * (z ** 2).sum(1), atol=1e-12)
+
+
+def test_utilities_and_ranks():
+    for n in (2, 3, 4, 7, 64, 100):
+        u = tr.utilities(n)
+        assert abs(u.sum()) < 1e-12
+        assert np.all(np.diff(u) <= 1e-15)
+        top = (n + 1) // 2                    # ranks k < n/2 + 1 have a positive raw weight
+        assert np.all(u[:top] > -1.0 / n) and np.allclose(u[top:], -1.0 / n)
+    f = np.array([3.0, np.nan, 1.0, 1.0, -2.0])
+    np.testing.assert_array_equal(tr.ranks(f), [3, 4, 1, 2, 0])
+
+
+def test_update_is_rank_invariant():
+    rng = np.random.default_rng(5)
+    mu, sigma = rng.normal(size=9), np.abs(rng.normal(size=9)) + 0.1
+    s = rng.normal(size=(12, 9))
+    f = rng.normal(size=12)
+    a = tr.update(mu, sigma, s, f)
+    b = tr.update(mu, sigma, s, np.exp(3 * f) + 7.0)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=0)
+    np.testing.assert_allclose(a[1], b[1], rtol=0, atol=0)
+
+
+def test_snes_minimises_separable_quadratic():
+    rng = np.random.default_rng(6)
+    d, lam = 10, 10
+    a = rng.uniform(0.5, 3.0, size=d)
+    target = rng.normal(size=d) * 2
+    mu, sigma = np.zeros(d) + 5.0, np.ones(d)
+    for _ in range(400):
+        s = rng.normal(size=(lam, d))
+        z = tr.sample(mu, sigma, s)
+        f = ((z - target) ** 2 * a).sum(1)
+        mu, sigma = tr.update(mu, sigma, s, f)
+    assert np.abs(mu - target).max() < 1e-3
+    assert sigma.max() < 1e-3
