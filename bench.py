@@ -51,6 +51,10 @@ WORKLOADS["mgwater_nve"] = (
     "cores; PPPM mesh 256 x 256 x 384, order 5, alpha 0.3, r_c 6 A, mode 1; NVE velocity Verlet 0.5 fs "
     "from 300 K Maxwell-Boltzmann; a step = one MD step (force call + two half kicks + drift)")
 WORKLOAD = WORKLOADS["batio3"]
+WORKLOADS["field_response"] = (
+    "external-field force F^ext_i = E . Z_i and polarization current Pdot = sum_i Z_i v_i (Sec. II.D) over "
+    "4,194,304 atoms: Born effective charges [N][3][3], velocities and forces [N][3] float32 (252 MB, > L2), "
+    "one qnep_field_response launch per step")
 
 
 def _config(name):
@@ -452,6 +456,100 @@ def _batch_flop(systems, hp, elec, n_cand):
     return total
 
 
+# DRAM bytes of one k_field_response launch (forces + Pdot, 4,194,304 atoms) from the ncu capture of
+# the current kernel (profiles/k_field_response_4m.md): 211.97 MB read + 30.22 MB written (the rest of
+# the 50 MB of forces is still in L2 when the kernel ends); None whenever the kernel changes
+FIELD_DRAM_BYTES = 211.97e6 + 30.22e6
+FIELD_BYTES_PER_ATOM = 36 + 12 + 12      # read Z and v, write F^ext
+
+
+def _time_field_response(dev, flush, peaks, reps):
+    """qnep_field_response (forces and Pdot) on FIELD_RESPONSE_ATOMS atoms; HBM roofline.
+
+    CUDA events on torch's current stream, which the call launches on; L2 flushed
+    before every timed call.  Returns the roofline object and the call times (ms).
+    """
+    import torch
+
+    from paper_2601_19034_gb300 import workloads
+    from paper_2601_19034_gb300.qnep import field_response
+
+    n = workloads.FIELD_RESPONSE_ATOMS
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    z = torch.randn(n, 3, 3, device=dev, generator=g)
+    v = torch.randn(n, 3, device=dev, generator=g) * 0.02
+    f = torch.empty(n, 3, device=dev)
+    pdot = torch.empty(3, dtype=torch.float64, device=dev)
+    efield = (0.12, 0.05, -0.33)
+    for _ in range(3):
+        field_response(z, efield, v, forces=f, pdot=pdot)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        starts[k].record(cur)
+        field_response(z, efield, v, forces=f, pdot=pdot)
+        ends[k].record(cur)
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = float(np.median(times))
+    algo = n * FIELD_BYTES_PER_ATOM
+    achieved = algo / (ms * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"]
+    del z, v, f
+    return {"kernel": "k_field_response", "atoms": n, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "ms": ms, "traffic": FIELD_DRAM_BYTES,
+            "work": f"{algo} algorithmic bytes per launch ({FIELD_BYTES_PER_ATOM} B per atom: Z 36, v 12, F 12)",
+            "timing": "median of CUDA-event times of single calls (memset of Pdot + one kernel), L2 flushed "
+                      "before each"}, times
+
+
+def _time_snes_step(b, graph, stream, out, off, params, dev, reps):
+    """Median time (ms) of one training iteration on the device: randn, sample, set_params,
+    batched call (graph replay), loss (weights 1, 1, 0, 1e-6), SNES update."""
+    import torch
+
+    from paper_2601_19034_gb300.qnep import batch_loss, snes_sample, snes_update
+
+    c, p = params.shape
+    mu = torch.tensor(params.mean(0), dtype=torch.float32, device=dev)
+    sigma = torch.full((p,), 0.01, dtype=torch.float32, device=dev)
+    noise = torch.empty(c, p, dtype=torch.float32, device=dev)
+    z = torch.empty(c, p, dtype=torch.float32, device=dev)
+    off_d = torch.tensor(np.asarray(off, dtype=np.int32), device=dev)
+    with torch.cuda.stream(stream):
+        graph.replay()
+        e_ref = out["energy"][0].clone()
+        f_ref = out["forces"][0].clone()
+    loss = torch.empty(c, dtype=torch.float64, device=dev)
+    terms = torch.empty(c, 4, dtype=torch.float64, device=dev)
+    times = []
+    with torch.cuda.stream(stream):
+        for k in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            noise.normal_()
+            snes_sample(mu, sigma, noise, out=z, stream=stream.cuda_stream)
+            b.set_params(z, stream=stream.cuda_stream)
+            graph.replay()
+            batch_loss(out["energy"], out["forces"], e_ref, f_ref, off_d, z, (1.0, 1.0, 0.0, 1e-6), loss=loss,
+                       terms=terms, stream=stream.cuda_stream)
+            snes_update(loss, noise, mu, sigma, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                times.append(e0.elapsed_time(e1))
+    b.set_params(torch.tensor(params, dtype=torch.float32, device=dev), stream=stream.cuda_stream)
+    stream.synchronize()
+    ms = float(np.median(times))
+    return {"ms": ms, "loss_best": float(loss.min().item()),
+            "what": "normal deviates + qnep_snes_sample + qnep_batch_set_params + batched call (graph replay) "
+                    "+ qnep_batch_loss + qnep_snes_update, CUDA events on the call's stream, median"}
+
+
 def run_batch(args):
     """Batched form: every (candidate, structure) pair of the LLZO batch in one persistent launch."""
     import torch
@@ -537,6 +635,9 @@ def run_batch(args):
     item_ms = stage["items"] / max(calls, 1)
     prep_ms = stage["prepass"] / max(calls, 1)
 
+    # external-field response from the Born effective charges (Sec. II.D), its own HBM roofline
+    field_roof, _ = _time_field_response(dev, flush, peaks, min(args.steps, 20))
+
     # precision form on liquid water (8000 H2O, PPPM 64^3): FP32 vs BF16 / TF32 network
     mixed = {"workload": WORKLOADS["water_pppm"]}
     sy_w, hp_w, par_w, el_w = _config("water_pppm")
@@ -584,6 +685,10 @@ def run_batch(args):
         dt = time.perf_counter() - t
         if k >= args.warmup:
             e2e_ms.append(dt * 1e3)
+    # one device-resident SNES iteration around the same call (Sec. II.E): normal deviates,
+    # sampling, parameter upload, the batched call (graph replay), the loss against reference
+    # energies and forces (here candidate 0's outputs), the update of (mu, sigma)
+    snes = _time_snes_step(b, graph, stream, out, off, params, dev, min(args.steps, 10))
     line = None
     if rank == 0:
         achieved = flop / (ms_per_step * 1e-3) / 1e12
@@ -607,6 +712,8 @@ def run_batch(args):
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
                          "whole_call_frac": achieved / fp32_peak},
             "mixed": mixed,
+            "field_response": field_roof,
+            "snes_step": dict(snes, batched_call_ms=ms_per_step),
             "plain_fp32": {"value": plain_value, "unit": UNIT,
                            "what": "single-structure qnep_compute, forces + charges, one call per structure "
                                    "(first 64 structures, candidate 0)",
@@ -772,6 +879,27 @@ def run_nve(args):
     return line
 
 
+def run_field(args):
+    """Field response alone (profiling and its own line): forces + Pdot per step."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, peak_kind = _peaks()
+    with ClockSampler(0) as clk:
+        roof, times = _time_field_response(dev, flush, peaks, args.steps)
+    from paper_2601_19034_gb300 import workloads
+    n = workloads.FIELD_RESPONSE_ATOMS
+    ms = float(sum(times)) / len(times)
+    return {"metric": "qNEP field response (E.Z_i, sum_i Z_i v_i) atoms/s", "value": n / (ms * 1e-3),
+            "unit": "atoms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Pdot sum)",
+            "data": "synthetic", "config": {"workload": WORKLOADS["field_response"],
+                                            "l2": "flushed before each step (512 MB write)"},
+            "roofline": dict(roof, peak_source=peak_kind), "gpu_launches": args.steps,
+            "clocks": clk.summary(peaks.get("sm_max_mhz", 2070.0))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -791,6 +919,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "llzo_batch":
         line = run_batch(args)
+    elif args.workload == "field_response":
+        line = run_field(args)
     elif args.workload == "mgwater_nve":
         line = run_nve(args)
     else:

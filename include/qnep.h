@@ -202,6 +202,27 @@ qnep_status qnep_set_profiling(qnep_model* m, int enable);
 qnep_status qnep_stage_times(qnep_model* m, float* ms_out, int max_stages, int* n_calls);
 const char* qnep_stage_name(int stage);
 
+/* Response to a uniform external electric field from the Born effective charges
+ * (Sec. II.D):
+ *   Eq. electric_force:          forces[i][b] (+)= sum_a E_a Z_i,ab      (eV/A)
+ *   Eq. polarization_derivative: pdot[a] = sum_i sum_b Z_i,ab v_i,b      (e A per time unit of v)
+ *   bec:        device [N][3][3] float32 Z_i,ab (a = polarization component, b = position
+ *               component), as written by qnep_compute; NULL only when n_atoms = 0
+ *   efield:     host double[3] E (V/A); needed when forces != NULL
+ *   velocities: device [N][3] float32; needed when pdot != NULL and n_atoms > 0, ignored otherwise
+ *   forces:     device [N][3] float32 F^ext, overwritten (accumulate = 0) or added to an
+ *               existing force array (accumulate = 1), or NULL
+ *   pdot:       device double[3], cleared on the stream and then summed (FP32 over at most
+ *               8 atoms per thread, FP64 beyond, FP64 atomics: the last bits depend on the
+ *               order of the blocks), or NULL
+ * Float arrays must be 4-byte aligned (16-byte alignment of all of them takes the
+ * vectorised path), pdot 8-byte aligned.  Asynchronous on `stream`.  Returns
+ * QNEP_ERR_ARG for a negative n_atoms, a missing input, a non-finite field or a
+ * misaligned pointer, QNEP_ERR_CUDA if a launch fails; with neither forces nor pdot
+ * requested it does nothing.  Caller owns every buffer; nothing is allocated. */
+qnep_status qnep_field_response(int n_atoms, const float* bec, const double efield[3], const float* velocities,
+                                float* forces, int accumulate, double* pdot, void* stream);
+
 /* Reciprocal-space Ewald sum of given charges that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory -- host programs that give all of the GPU's memory
@@ -291,6 +312,56 @@ qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_off
 qnep_status qnep_batch_set_profiling(qnep_batch* b, int enable);
 qnep_status qnep_batch_stage_times(qnep_batch* b, float* ms_out /* [2] */, int* n_calls);
 const char* qnep_batch_last_error(const qnep_batch* b);
+
+/* Replace the candidates' parameter vectors of a batch from device memory (asynchronous on
+ * `stream`, ordered before later qnep_batch_compute calls on that stream, including replays
+ * of a captured graph of one): params = device [n_candidates][qnep_param_count] float32, the
+ * blob layout of qnep_create.  Used by the training loop below; values are not checked (a
+ * non-finite candidate gives non-finite outputs and a NaN loss, which ranks last). */
+qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stream);
+
+/* ---- Training: population loss and separable NES (Sec. II.E) ----------------
+ * The paper trains every parameter z (descriptor, network, sqrt(eps_inf)) with SNES on
+ *   L(z) = l_e D_e + l_f D_f + l_v D_v + l_Z D_Z + l_Q D_Q + l_1 |z|_1 + l_2 |z|_2^2.
+ * The batched call feeds D_e and D_f (its corrected charges meet the total-charge target
+ * exactly; it computes neither virials nor BEC), read as
+ *   D_e = sqrt(1/S' sum_s ((E_s - E_s^ref) / N_s)^2)   over the S' structures with atoms (eV/atom)
+ *   D_f = sqrt(1/(3N) sum_i,b (F_ib - F_ib^ref)^2)      over all N atoms (eV/A).
+ * One device-resident iteration: qnep_snes_sample -> qnep_batch_set_params ->
+ * qnep_batch_compute -> qnep_batch_loss -> qnep_snes_update.  All pointers are device memory
+ * unless stated; calls are asynchronous on `stream`; nothing is allocated. */
+typedef struct {
+    double energy;   /* l_e */
+    double force;    /* l_f */
+    double l1;       /* l_1 */
+    double l2;       /* l_2 */
+} qnep_loss_weights;
+
+/* Candidates z_k = mu + sigma * s_k (SNES sampling; the normal deviates s are the caller's):
+ * mu, sigma [P], noise [C][P], params [C][P] float32 (params = fmaf(sigma, noise, mu)). */
+qnep_status qnep_snes_sample(int n_candidates, int n_params, const float* mu, const float* sigma, const float* noise,
+                             float* params, void* stream);
+
+/* Loss of every candidate.  atom_offsets: device [S+1] as for qnep_batch_compute; energy
+ * [C][S] f64 and forces [C][N][3] f32 as qnep_batch_compute writes them; energy_ref [S] f64,
+ * forces_ref [N][3] f32 (forces and forces_ref both given or both NULL: D_f = 0); params [C][P]
+ * for the regularisation (NULL: no norm terms); w: host weights.  Writes loss [C] f64 and
+ * terms [C][4] f64 = (D_e, D_f, |z|_1, |z|_2^2).  D_f sums 8 squares per thread in FP32, the
+ * rest is FP64 (FP64 atomics across blocks: the last bits depend on the block order).
+ * QNEP_ERR_ARG for missing buffers, C outside [1, 65535], non-finite weights. */
+qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                            const double* energy, const float* forces, const double* energy_ref,
+                            const float* forces_ref, const float* params, int n_params,
+                            const qnep_loss_weights* w, double* loss, double* terms, void* stream);
+
+/* One SNES step (Schaul et al. 2011) from the losses of the population sampled with `noise`:
+ * candidates ranked by loss (lowest first, ties by index, NaN last); utilities
+ * u_k = max(0, ln(C/2 + 1) - ln k) / sum_j max(0, ln(C/2 + 1) - ln j) - 1/C for rank k;
+ * mu += eta_mu sigma sum_k u_k s_k; sigma *= exp(eta_sigma / 2 sum_k u_k (s_k^2 - 1)),
+ * in FP64, stored to the float32 mu and sigma [P] in place.  A negative rate selects the
+ * published default (eta_mu = 1, eta_sigma = (3 + ln P) / (5 sqrt P)).  1 <= C <= 1024. */
+qnep_status qnep_snes_update(int n_candidates, int n_params, const double* loss, const float* noise, float* mu,
+                             float* sigma, double eta_mu, double eta_sigma, void* stream);
 void        qnep_batch_destroy(qnep_batch* b);
 
 void        qnep_destroy(qnep_model* m);

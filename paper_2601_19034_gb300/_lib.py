@@ -60,6 +60,11 @@ class VjpC(ctypes.Structure):
                 ("polar_weight", ctypes.c_double * 3), ("grad", ctypes.c_void_p)]
 
 
+class LossWeightsC(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("force", ctypes.c_double), ("l1", ctypes.c_double),
+                ("l2", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +105,8 @@ def _declare(lib):
     lib.qnep_stage_name.restype = ctypes.c_char_p
     lib.qnep_nve_run.argtypes = [p, i, p, p, p, p, p, ctypes.c_double, i, p, p, p]
     lib.qnep_nve_run.restype = i
+    lib.qnep_field_response.argtypes = [i, p, p, p, p, i, p, p]
+    lib.qnep_field_response.restype = i
     # batched evaluation
     lib.qnep_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(HParamsC), p, ctypes.c_size_t, i,
                                       ctypes.POINTER(ElecC)]
@@ -124,6 +131,14 @@ def _declare(lib):
     lib.qnep_batch_stage_times.restype = i
     lib.qnep_batch_last_error.argtypes = [p]
     lib.qnep_batch_last_error.restype = ctypes.c_char_p
+    lib.qnep_batch_set_params.argtypes = [p, p, p]
+    lib.qnep_batch_set_params.restype = i
+    lib.qnep_snes_sample.argtypes = [i, i, p, p, p, p, p]
+    lib.qnep_snes_sample.restype = i
+    lib.qnep_batch_loss.argtypes = [i, i, p, i, p, p, p, p, p, i, ctypes.POINTER(LossWeightsC), p, p, p]
+    lib.qnep_batch_loss.restype = i
+    lib.qnep_snes_update.argtypes = [i, i, p, p, p, p, ctypes.c_double, ctypes.c_double, p]
+    lib.qnep_snes_update.restype = i
     lib.qnep_batch_destroy.argtypes = [p]
     lib.qnep_batch_destroy.restype = None
     return lib

@@ -325,6 +325,26 @@ bool same_desc(const qnep_batch* b, int n_struct, const int* off, const double* 
 
 }  // namespace
 
+namespace {
+
+// Candidate-major parameters [C][P] into the lane-minor layout [group][p][CG] through a
+// 32 x 32 shared-memory tile (coalesced reads along p, coalesced writes along the lanes).
+__global__ void k_set_params(const float* __restrict__ src, float* __restrict__ dst, int n_cand, int n_par) {
+    __shared__ float tile[CG][CG + 1];
+    const int g = blockIdx.y, p0 = blockIdx.x * CG;
+    for (int r = threadIdx.y; r < CG; r += blockDim.y) {
+        const int c = g * CG + r, p = p0 + threadIdx.x;
+        if (c < n_cand && p < n_par) tile[r][threadIdx.x] = src[(size_t)c * n_par + p];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < CG; r += blockDim.y) {
+        const int p = p0 + r, lane = threadIdx.x, c = g * CG + lane;
+        if (c < n_cand && p < n_par) dst[((size_t)g * n_par + p) * CG + lane] = tile[lane][r];
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const float* params_host, size_t n_params,
@@ -601,6 +621,16 @@ qnep_status qnep_batch_stage_times(qnep_batch* b, float* ms_out, int* n_calls) {
 }
 
 const char* qnep_batch_last_error(const qnep_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stream) {
+    if (!b) return QNEP_ERR_ARG;
+    if (!params) return failb(b, QNEP_ERR_ARG, "params is NULL");
+    const int P = b->lay.total;
+    dim3 grid((unsigned)((P + CG - 1) / CG), (unsigned)b->n_groups), block(CG, 8);
+    k_set_params<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(params, b->d_pt, b->n_cand, P);
+    CKB(cudaGetLastError());
+    return QNEP_OK;
+}
 
 void qnep_batch_destroy(qnep_batch* b) {
     if (!b) return;

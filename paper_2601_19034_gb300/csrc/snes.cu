@@ -1,0 +1,217 @@
+// Training side of the batched force call (Sec. II.E): the loss of every candidate of a
+// population and the separable natural evolution strategy (SNES, Schaul et al. 2011, the
+// method the paper trains every parameter with) that moves the search distribution.
+//
+//   qnep_snes_sample   z_k = mu + sigma * s_k                         [C][P]
+//   qnep_batch_loss    D_e, D_f (energy RMSE per atom, force RMSE per component), |z|_1,
+//                      |z|_2^2 and L = l_e D_e + l_f D_f + l_1 |z|_1 + l_2 |z|_2^2 per candidate
+//   qnep_snes_update   rank the losses, rank-based utilities, natural-gradient step on
+//                      (mu, sigma)
+// The batched call feeds energies and forces; its corrected charges meet the total-charge
+// target exactly and it computes neither virials nor BEC, so the loss has no D_Q, D_v, D_Z.
+//
+// Loss: the force term is the large one (C x N x 3 floats, HBM bound): blocks over
+// (2048-float chunk, candidate) read forces and references with coalesced loads, sum 8 squares
+// per thread in FP32, reduce the block in FP64 and add one FP64 atomic per block; one more block
+// per candidate sums the energy terms and the parameter norms in FP64 and writes them directly;
+// a one-block pass forms the roots and the weighted sum.
+// Update: every block ranks the (at most 1024) losses in shared memory (ties by index, NaN last),
+// forms the utilities in FP64 (their normaliser is the sum of all candidates' raw weights, each
+// rank occurring once), then takes its parameters: g_mu = sum_k u_k s_k, g_sigma = sum_k u_k
+// (s_k^2 - 1) in FP64, mu += eta_mu sigma g_mu, sigma *= exp(eta_sigma / 2 g_sigma).
+#include <climits>
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/qnep.h"
+
+namespace qnep {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPerThread = 8;                       // force elements per thread (FP32 partial)
+constexpr int kChunk = kThreads * kPerThread;       // force elements per block
+constexpr int kMaxCandidates = 1024;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();                                // red may still be read by an earlier call
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += red[k];
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_snes_sample(long long total, int n_params, const float* __restrict__ mu, const float* __restrict__ sigma,
+              const float* __restrict__ noise, float* __restrict__ z) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(i % n_params);
+        z[i] = fmaf(sigma[p], noise[i], mu[p]);
+    }
+}
+
+// blockIdx.y = candidate; blockIdx.x < n_chunks: a chunk of the force stream; == n_chunks: the
+// energy term and the parameter norms.
+__global__ void __launch_bounds__(kThreads)
+k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n_chunks,
+             const double* __restrict__ energy, const float* __restrict__ forces,
+             const double* __restrict__ energy_ref, const float* __restrict__ forces_ref,
+             const float* __restrict__ params, int n_params, double* __restrict__ terms) {
+    __shared__ double red[kThreads / 32];
+    const int c = blockIdx.y;
+    if ((int)blockIdx.x < n_chunks) {
+        const long long base = (long long)blockIdx.x * kChunk + threadIdx.x;
+        const float* fc = forces + (long long)c * n_force;
+        float d[kPerThread];
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const long long i = base + (long long)k * kThreads;
+            d[k] = i < n_force ? fc[i] - forces_ref[i] : 0.f;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) acc = fmaf(d[k], d[k], acc);
+        const double s = block_sum((double)acc, red);
+        if (threadIdx.x == 0) atomicAdd(terms + 4 * c + 1, s);
+        return;
+    }
+    double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0;
+    for (int s = threadIdx.x; s < n_struct; s += kThreads) {
+        const int n_s = off[s + 1] - off[s];
+        if (n_s > 0) {
+            const double de = (energy[(long long)c * n_struct + s] - energy_ref[s]) / (double)n_s;
+            se += de * de;
+            cnt += 1.0;
+        }
+    }
+    if (params)
+        for (int p = threadIdx.x; p < n_params; p += kThreads) {
+            const double z = params[(long long)c * n_params + p];
+            l1 += fabs(z);
+            l2 += z * z;
+        }
+    se = block_sum(se, red);
+    cnt = block_sum(cnt, red);
+    l1 = block_sum(l1, red);
+    l2 = block_sum(l2, red);
+    if (threadIdx.x == 0) {
+        terms[4 * c + 0] = cnt > 0.0 ? sqrt(se / cnt) : 0.0;
+        terms[4 * c + 2] = l1;
+        terms[4 * c + 3] = l2;
+    }
+}
+
+__global__ void k_loss_finalize(int n_cand, long long n_force, double we, double wf, double w1, double w2,
+                                double* __restrict__ terms, double* __restrict__ loss) {
+    for (int c = threadIdx.x; c < n_cand; c += blockDim.x) {
+        const double df = n_force > 0 ? sqrt(terms[4 * c + 1] / (double)n_force) : 0.0;
+        terms[4 * c + 1] = df;
+        loss[c] = we * terms[4 * c + 0] + wf * df + w1 * terms[4 * c + 2] + w2 * terms[4 * c + 3];
+    }
+}
+
+// true when candidate j ranks before candidate c: lower loss, NaN last, ties by index
+__device__ __forceinline__ bool ranks_before(double fj, int j, double fc, int c) {
+    const bool nj = isnan(fj), nc = isnan(fc);
+    if (nj != nc) return nc;
+    if (!nj && fj != fc) return fj < fc;
+    return j < c;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_snes_update(int n_cand, int n_params, const double* __restrict__ loss, const float* __restrict__ noise,
+              float* __restrict__ mu, float* __restrict__ sigma, double eta_mu, double eta_sigma) {
+    __shared__ double f[kMaxCandidates];
+    __shared__ double u[kMaxCandidates];
+    __shared__ double red[kThreads / 32];
+    for (int c = threadIdx.x; c < n_cand; c += kThreads) f[c] = loss[c];
+    __syncthreads();
+    const double top = log(0.5 * n_cand + 1.0);
+    double wsum = 0.0;
+    for (int c = threadIdx.x; c < n_cand; c += kThreads) {
+        int rank = 0;
+        const double fc = f[c];
+        for (int j = 0; j < n_cand; ++j) rank += ranks_before(f[j], j, fc, c) ? 1 : 0;
+        const double w = fmax(0.0, top - log((double)(rank + 1)));
+        u[c] = w;
+        wsum += w;
+    }
+    wsum = block_sum(wsum, red);                    // also orders the writes of u before the reads
+    const double inv_c = 1.0 / n_cand;
+    for (int c = threadIdx.x; c < n_cand; c += kThreads) u[c] = u[c] / wsum - inv_c;
+    __syncthreads();
+    for (int p = blockIdx.x * kThreads + threadIdx.x; p < n_params; p += gridDim.x * kThreads) {
+        double gm = 0.0, gs = 0.0;
+        for (int c = 0; c < n_cand; ++c) {
+            const double s = noise[(long long)c * n_params + p];
+            gm = fma(u[c], s, gm);
+            gs = fma(u[c], fma(s, s, -1.0), gs);
+        }
+        const double sg = sigma[p];
+        mu[p] = (float)(mu[p] + eta_mu * sg * gm);
+        sigma[p] = (float)(sg * exp(0.5 * eta_sigma * gs));
+    }
+}
+
+int grid_for(long long work, int per_block) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks = (work + per_block - 1) / per_block;
+    const long long cap = (long long)(sms > 0 ? sms : 152) * 8;
+    return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
+}
+
+}  // namespace
+}  // namespace qnep
+
+using namespace qnep;
+
+extern "C" qnep_status qnep_snes_sample(int n_candidates, int n_params, const float* mu, const float* sigma,
+                                        const float* noise, float* params, void* stream) {
+    if (n_candidates < 1 || n_params < 1 || !mu || !sigma || !noise || !params) return QNEP_ERR_ARG;
+    const long long total = (long long)n_candidates * n_params;
+    k_snes_sample<<<grid_for(total, kThreads), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        total, n_params, mu, sigma, noise, params);
+    return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
+}
+
+extern "C" qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                                      const double* energy, const float* forces, const double* energy_ref,
+                                      const float* forces_ref, const float* params, int n_params,
+                                      const qnep_loss_weights* w, double* loss, double* terms, void* stream) {
+    if (n_candidates < 1 || n_candidates > 65535 || n_struct < 1 || n_total < 0 || !atom_offsets || !energy ||
+        !energy_ref || !w || !loss || !terms)
+        return QNEP_ERR_ARG;
+    if ((forces == nullptr) != (forces_ref == nullptr)) return QNEP_ERR_ARG;
+    if (params && n_params < 1) return QNEP_ERR_ARG;
+    if (!std::isfinite(w->energy) || !std::isfinite(w->force) || !std::isfinite(w->l1) || !std::isfinite(w->l2))
+        return QNEP_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n_force = forces ? 3LL * n_total : 0;
+    const long long chunks = (n_force + kChunk - 1) / kChunk;
+    if (chunks + 1 > INT_MAX) return QNEP_ERR_ARG;
+    if (cudaMemsetAsync(terms, 0, sizeof(double) * 4 * (size_t)n_candidates, st) != cudaSuccess)
+        return QNEP_ERR_CUDA;
+    dim3 grid((unsigned)(chunks + 1), (unsigned)n_candidates);
+    k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, n_force, (int)chunks, energy, forces, energy_ref,
+                                            forces_ref, params, params ? n_params : 0, terms);
+    if (cudaGetLastError() != cudaSuccess) return QNEP_ERR_CUDA;
+    k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, w->energy, w->force, w->l1, w->l2, terms, loss);
+    return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
+}
+
+extern "C" qnep_status qnep_snes_update(int n_candidates, int n_params, const double* loss, const float* noise,
+                                        float* mu, float* sigma, double eta_mu, double eta_sigma, void* stream) {
+    if (n_candidates < 1 || n_candidates > kMaxCandidates || n_params < 1 || !loss || !noise || !mu || !sigma)
+        return QNEP_ERR_ARG;
+    if (!std::isfinite(eta_mu) || !std::isfinite(eta_sigma)) return QNEP_ERR_ARG;
+    if (eta_mu < 0) eta_mu = 1.0;
+    if (eta_sigma < 0) eta_sigma = (3.0 + std::log((double)n_params)) / (5.0 * std::sqrt((double)n_params));
+    k_snes_update<<<grid_for(n_params, kThreads), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_candidates, n_params, loss, noise, mu, sigma, eta_mu, eta_sigma);
+    return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
+}

@@ -228,6 +228,44 @@ def nve(model: "QNEP", positions: torch.Tensor, velocities: torch.Tensor, types:
     return forces, energies
 
 
+def field_response(bec: torch.Tensor, efield=None, velocities: torch.Tensor = None, forces: torch.Tensor = None,
+                   accumulate: bool = False, pdot: torch.Tensor = None, stream=None):
+    """External-field force E . Z_i and polarization current sum_i Z_i v_i (Sec. II.D).
+
+    ``bec`` [N, 3, 3] from ``QNEP.compute``; ``efield`` (3 values, V/A) gives the
+    force [N, 3] (written into ``forces`` when given, added to it with
+    ``accumulate``); ``velocities`` [N, 3] give Pdot [3] (FP64).  One
+    ``qnep_field_response`` launch on torch's current stream; returns
+    (force or None, pdot or None) without synchronising.
+    """
+    lib = _lib.load()
+    assert bec.is_cuda and bec.dtype == torch.float32 and bec.is_contiguous()
+    n = bec.shape[0]
+    dev = bec.device
+    e = None
+    if efield is not None:
+        e = (ctypes.c_double * 3)(*[float(x) for x in np.asarray(efield, dtype=np.float64).reshape(3)])
+        if forces is None:
+            forces = torch.zeros(n, 3, dtype=torch.float32, device=dev) if accumulate else \
+                torch.empty(n, 3, dtype=torch.float32, device=dev)
+        assert forces.is_cuda and forces.dtype == torch.float32 and forces.is_contiguous()
+    else:
+        forces = None
+    if velocities is not None:
+        assert velocities.is_cuda and velocities.dtype == torch.float32 and velocities.is_contiguous()
+        if pdot is None:
+            pdot = torch.empty(3, dtype=torch.float64, device=dev)
+    else:
+        pdot = None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    st = lib.qnep_field_response(n, bec.data_ptr(), e, velocities.data_ptr() if velocities is not None else None,
+                                 forces.data_ptr() if forces is not None else None, 1 if accumulate else 0,
+                                 pdot.data_ptr() if pdot is not None else None, ctypes.c_void_p(stream))
+    _lib.check(st)
+    return forces, pdot
+
+
 class QNEPFunction(torch.autograd.Function):
     """Differentiable qNEP force call: positions [N, 3] -> (U^tot, q^c [N], P [3]).
 
@@ -384,6 +422,69 @@ class QNEPBatch:
         args = self._args(positions, types, offsets, boxes, out, None)
         _lib.check(self.lib.qnep_batch_autotune(*args, int(reps), ctypes.byref(best)), batch=self.handle)
         return best.value
+
+    def set_params(self, params: torch.Tensor, stream=None):
+        """Replace the candidates' parameter vectors from a CUDA tensor [n_candidates, n_params]."""
+        assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
+        assert params.numel() == self.n_cand * self.hp.n_params
+        if stream is None:
+            stream = torch.cuda.current_stream(params.device).cuda_stream
+        _lib.check(self.lib.qnep_batch_set_params(self.handle, params.data_ptr(), ctypes.c_void_p(stream)),
+                   batch=self.handle)
+
+
+def _stream(t, stream):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream if stream is None else stream)
+
+
+def snes_sample(mu: torch.Tensor, sigma: torch.Tensor, noise: torch.Tensor, out: torch.Tensor = None, stream=None):
+    """Candidates mu + sigma * noise [C, P] (float32, one launch)."""
+    c, p = noise.shape
+    if out is None:
+        out = torch.empty(c, p, dtype=torch.float32, device=noise.device)
+    for t in (mu, sigma, noise, out):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    _lib.check(_lib.load().qnep_snes_sample(c, p, mu.data_ptr(), sigma.data_ptr(), noise.data_ptr(),
+                                            out.data_ptr(), _stream(noise, stream)))
+    return out
+
+
+def batch_loss(energy, forces, energy_ref, forces_ref, atom_offsets, params=None, weights=(1.0, 1.0, 0.0, 0.0),
+               loss: torch.Tensor = None, terms: torch.Tensor = None, stream=None):
+    """Per-candidate loss L [C] and terms [C, 4] = (D_e, D_f, |z|_1, |z|_2^2) on the device.
+
+    ``atom_offsets`` is a CUDA int32 tensor [S + 1]; ``weights`` = (l_e, l_f, l_1, l_2).
+    """
+    c, s = energy.shape
+    n_total = int(forces_ref.shape[0]) if forces_ref is not None else 0
+    dev = energy.device
+    if loss is None:
+        loss = torch.empty(c, dtype=torch.float64, device=dev)
+    if terms is None:
+        terms = torch.empty(c, 4, dtype=torch.float64, device=dev)
+    assert atom_offsets.is_cuda and atom_offsets.dtype == torch.int32 and atom_offsets.numel() == s + 1
+    w = _lib.LossWeightsC(*[float(x) for x in weights])
+
+    def ptr(t):
+        return t.data_ptr() if t is not None else None
+
+    n_par = int(params.shape[1]) if params is not None else 0
+    _lib.check(_lib.load().qnep_batch_loss(c, s, atom_offsets.data_ptr(), n_total, energy.data_ptr(), ptr(forces),
+                                           energy_ref.data_ptr(), ptr(forces_ref), ptr(params), n_par,
+                                           ctypes.byref(w), loss.data_ptr(), terms.data_ptr(),
+                                           _stream(energy, stream)))
+    return loss, terms
+
+
+def snes_update(loss: torch.Tensor, noise: torch.Tensor, mu: torch.Tensor, sigma: torch.Tensor, eta_mu: float = -1.0,
+                eta_sigma: float = -1.0, stream=None):
+    """One SNES step on (mu, sigma) in place from the population's losses [C] and noise [C, P]."""
+    c, p = noise.shape
+    assert loss.is_cuda and loss.dtype == torch.float64 and loss.numel() == c
+    _lib.check(_lib.load().qnep_snes_update(c, p, loss.data_ptr(), noise.data_ptr(), mu.data_ptr(),
+                                            sigma.data_ptr(), float(eta_mu), float(eta_sigma),
+                                            _stream(noise, stream)))
+    return mu, sigma
 
 
 def stack_structures(systems) -> tuple:

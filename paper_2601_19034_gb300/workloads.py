@@ -27,6 +27,10 @@ MASSES = {"H": 1.008, "O": 15.999, "Mg": 24.305, "Li": 6.94, "La": 138.905, "Zr"
           "Ti": 47.867}   # amu
 
 AVOGADRO = 6.02214076e23
+
+# Atom count of the field-response measurement (Born effective charges [N][3][3],
+# velocities and forces [N][3], float32: 252 MB, above the 129 MB L2 of the GPU).
+FIELD_RESPONSE_ATOMS = 4_194_304
 M_H2O = 18.01528  # g/mol
 
 

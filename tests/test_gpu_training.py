@@ -1,0 +1,190 @@
+"""GPU parity of the training loop around the batched call (Sec. II.E; SNES of Schaul et al. 2011).
+
+qnep_snes_sample, qnep_batch_set_params, qnep_batch_loss and qnep_snes_update against
+the oracle (oracle/training.py) on the same inputs:
+  * sampling: one FP32 fused multiply-add per element, within 1 ulp of the FP64 value;
+  * loss: seeded energies, forces and parameters (an empty structure, ragged force
+    chunks), D_e / |z|_1 / |z|_2^2 in FP64 (relative 1e-12), D_f from FP32 squares of
+    FP32 differences (relative 2e-6);
+  * update: 64 candidates x the 4-species blob, losses with a tie and a NaN: identical
+    ranks, so mu and sigma agree to the float32 rounding of the FP64 step (1e-6 relative);
+  * set_params: a batch whose candidates are replaced on the device gives the outputs of a
+    batch created with those candidates (up to the order of FP32 / FP64 atomics);
+  * the chain on a small LLZO batch (targets from a teacher candidate): the device loss of
+    the batched outputs equals the oracle loss of the same outputs, and one SNES step
+    equals the oracle's step.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import training as tr  # noqa: E402
+from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19034_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def _t(a, dev, dtype=None):
+    return torch.tensor(np.ascontiguousarray(a), device=dev, dtype=dtype)
+
+
+def test_sample_matches_oracle(dev):
+    from paper_2601_19034_gb300.qnep import snes_sample
+    rng = np.random.default_rng(1)
+    c, p = 37, 1001
+    mu = rng.normal(size=p).astype(np.float32)
+    sigma = (np.abs(rng.normal(size=p)) * 0.1).astype(np.float32)
+    s = rng.normal(size=(c, p)).astype(np.float32)
+    z = snes_sample(_t(mu, dev), _t(sigma, dev), _t(s, dev)).cpu().numpy()
+    ref = tr.sample(mu, sigma, s)
+    assert np.all(np.abs(z - ref) <= np.spacing(np.abs(ref).astype(np.float32)))
+
+
+@pytest.mark.parametrize("sizes", [(192, 0, 384, 7, 1536), (1,), (300, 300)])
+def test_loss_matches_oracle(dev, sizes):
+    from paper_2601_19034_gb300.qnep import batch_loss
+    rng = np.random.default_rng(len(sizes))
+    c, p = 9, 613
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    n, s = int(off[-1]), len(sizes)
+    e = rng.normal(size=(c, s)) * 50
+    e_ref = rng.normal(size=s) * 50
+    f = rng.normal(size=(c, n, 3)).astype(np.float32)
+    f_ref = rng.normal(size=(n, 3)).astype(np.float32)
+    z = rng.normal(size=(c, p)).astype(np.float32)
+    weights = (1.0, 2.5, 0.01, 0.003)
+    loss, terms = batch_loss(_t(e, dev), _t(f, dev), _t(e_ref, dev), _t(f_ref, dev), _t(off, dev), _t(z, dev),
+                             weights)
+    loss, terms = loss.cpu().numpy(), terms.cpu().numpy()
+    d_e, d_f, l1, l2 = tr.loss_terms(e, f, e_ref, f_ref, off, z)
+    np.testing.assert_allclose(terms[:, 0], d_e, rtol=1e-12)
+    np.testing.assert_allclose(terms[:, 1], d_f, rtol=2e-6)
+    np.testing.assert_allclose(terms[:, 2], l1, rtol=1e-12)
+    np.testing.assert_allclose(terms[:, 3], l2, rtol=1e-12)
+    np.testing.assert_allclose(loss, tr.loss((d_e, d_f, l1, l2), *weights), rtol=2e-6)
+    # no forces, no parameters: D_f and the norms are zero
+    loss0, terms0 = batch_loss(_t(e, dev), None, _t(e_ref, dev), None, _t(off, dev), None, weights)
+    np.testing.assert_allclose(terms0.cpu().numpy()[:, 0], d_e, rtol=1e-12)
+    assert np.all(terms0.cpu().numpy()[:, 1:] == 0.0)
+
+
+def test_update_matches_oracle(dev):
+    from paper_2601_19034_gb300.qnep import snes_update
+    hp = wl.HParams(n_species=4)
+    p, c = hp.n_params, 64
+    rng = np.random.default_rng(3)
+    mu = rng.normal(size=p).astype(np.float32) * 0.1
+    sigma = (np.abs(rng.normal(size=p)) * 0.1 + 0.01).astype(np.float32)
+    s = rng.normal(size=(c, p)).astype(np.float32)
+    f = rng.normal(size=c)
+    f[5] = f[17]           # a tie (broken by index)
+    f[40] = np.nan         # ranks last
+    mu_d, sg_d = _t(mu, dev), _t(sigma, dev)
+    snes_update(_t(f, dev), _t(s, dev), mu_d, sg_d)
+    mu_r, sg_r = tr.update(mu, sigma, s, f)
+    np.testing.assert_allclose(mu_d.cpu().numpy(), mu_r, rtol=1e-6, atol=1e-6 * np.abs(sigma).max())
+    np.testing.assert_allclose(sg_d.cpu().numpy(), sg_r, rtol=1e-6)
+    # explicit rates
+    mu_d, sg_d = _t(mu, dev), _t(sigma, dev)
+    snes_update(_t(f, dev), _t(s, dev), mu_d, sg_d, eta_mu=0.5, eta_sigma=0.02)
+    mu_r, sg_r = tr.update(mu, sigma, s, f, 0.5, 0.02)
+    np.testing.assert_allclose(mu_d.cpu().numpy(), mu_r, rtol=1e-6, atol=1e-6 * np.abs(sigma).max())
+    np.testing.assert_allclose(sg_d.cpu().numpy(), sg_r, rtol=1e-6)
+
+
+def _small_batch():
+    from tests.test_gpu_batch import _llzo
+    systems = [_llzo((1, 1, 1), 61), _llzo((2, 1, 1), 62), _llzo((1, 1, 1), 63)]
+    return systems
+
+
+def test_set_params_equals_fresh_batch(dev):
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    systems = _small_batch()
+    hp = wl.HParams(n_species=4)
+    a = wl.random_params(hp, np.random.default_rng(71), n_candidates=35)
+    b = wl.random_params(hp, np.random.default_rng(72), n_candidates=35)
+    pos, typ, off, boxes = stack_structures(systems)
+    pos_d, typ_d = _t(pos, dev), _t(typ, dev)
+    elec = wl.Elec(mode=1, kind="ewald")
+    ba = QNEPBatch(hp, a, elec)
+    ba.compute(pos_d, typ_d, off, boxes)
+    ba.set_params(_t(b.astype(np.float32), dev))
+    out_a = ba.compute(pos_d, typ_d, off, boxes)
+    bb = QNEPBatch(hp, b, elec)
+    out_b = bb.compute(pos_d, typ_d, off, boxes)
+    torch.cuda.synchronize()
+    # the same arithmetic; only the order of the force and charge-sum atomics may differ
+    assert torch.allclose(out_a["energy"], out_b["energy"], rtol=1e-12, atol=1e-9)
+    assert (out_a["forces"] - out_b["forces"]).abs().max().item() <= 1e-5
+    assert (out_a["charges"] - out_b["charges"]).abs().max().item() <= 1e-7
+    ba.close()
+    bb.close()
+
+
+def test_one_training_iteration_chain(dev):
+    """sample -> set_params -> batched call -> loss -> update, against the oracle on the same outputs."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, batch_loss, snes_sample, snes_update, stack_structures
+    systems = _small_batch()
+    hp = wl.HParams(n_species=4)
+    p, c = hp.n_params, 32
+    rng = np.random.default_rng(81)
+    teacher = wl.random_params(hp, rng, n_candidates=1)[0].astype(np.float32)
+    mu = (teacher + rng.normal(size=p) * 0.02).astype(np.float32)
+    sigma = np.full(p, 0.01, np.float32)
+    s = rng.normal(size=(c, p)).astype(np.float32)
+    pos, typ, off, boxes = stack_structures(systems)
+    pos_d, typ_d = _t(pos, dev), _t(typ, dev)
+    elec = wl.Elec(mode=1, kind="ewald")
+    tb = QNEPBatch(hp, teacher[None], elec)
+    ref = tb.compute(pos_d, typ_d, off, boxes)
+    e_ref, f_ref = ref["energy"][0].contiguous(), ref["forces"][0].contiguous()
+    b = QNEPBatch(hp, np.repeat(mu[None], c, 0), elec)
+    mu_d, sg_d, s_d = _t(mu, dev), _t(sigma, dev), _t(s, dev)
+    z_d = snes_sample(mu_d, sg_d, s_d)
+    b.set_params(z_d)
+    out = b.compute(pos_d, typ_d, off, boxes, charges=False)
+    weights = (1.0, 1.0, 1e-4, 1e-4)
+    loss, terms = batch_loss(out["energy"], out["forces"], e_ref, f_ref, _t(off.astype(np.int32), dev), z_d, weights)
+    loss_h = loss.cpu().numpy()
+    snes_update(loss, s_d, mu_d, sg_d)
+    torch.cuda.synchronize()
+    terms_o = tr.loss_terms(out["energy"].cpu().numpy(), out["forces"].cpu().numpy(), e_ref.cpu().numpy(),
+                            f_ref.cpu().numpy(), off, z_d.cpu().numpy())
+    np.testing.assert_allclose(loss_h, tr.loss(terms_o, *weights), rtol=2e-6)
+    assert np.isfinite(loss_h).all() and loss_h.min() > 0
+    mu_r, sg_r = tr.update(mu, sigma, s, loss_h)
+    np.testing.assert_allclose(mu_d.cpu().numpy(), mu_r, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(sg_d.cpu().numpy(), sg_r, rtol=1e-6)
+    tb.close()
+    b.close()
+
+
+def test_argument_errors(dev):
+    from paper_2601_19034_gb300 import _lib
+    lib = _lib.load()
+    x = torch.zeros(64, device=dev)
+    d = torch.zeros(64, dtype=torch.float64, device=dev)
+    w = _lib.LossWeightsC(1.0, 1.0, 0.0, 0.0)
+    bad = _lib.LossWeightsC(float("inf"), 1.0, 0.0, 0.0)
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.qnep_snes_sample(0, 4, x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr(), st) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_snes_update(1025, 4, d.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr(), -1.0, -1.0,
+                                st) == _lib.QNEP_ERR_ARG
+    off = torch.zeros(2, dtype=torch.int32, device=dev)
+    # forces without references
+    assert lib.qnep_batch_loss(1, 1, off.data_ptr(), 0, d.data_ptr(), x.data_ptr(), d.data_ptr(), None, None, 0,
+                               w, d.data_ptr(), d.data_ptr(), st) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_batch_loss(1, 1, off.data_ptr(), 0, d.data_ptr(), None, d.data_ptr(), None, None, 0,
+                               bad, d.data_ptr(), d.data_ptr(), st) == _lib.QNEP_ERR_ARG
+    torch.cuda.synchronize()
