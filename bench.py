@@ -790,7 +790,12 @@ def run_nve(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sysm, hp, params, elec = workloads.config_mg_water()
+    if args.mg_cells:   # a narrower slab of the same construction (profiling), mesh scaled to keep h
+        nx, ny = (int(x) for x in args.mg_cells.split(","))
+        mesh = (2 * max(4, round(128 * nx / 112)), 2 * max(4, round(128 * ny / 65)), 384)
+        sysm, hp, params, elec = workloads.config_mg_water(nx=nx, ny=ny, mesh=mesh)
+    else:
+        sysm, hp, params, elec = workloads.config_mg_water()
     n = sysm.n_atoms
     masses = workloads.species_masses(workloads.MGWATER_SPECIES)
     v0 = workloads.maxwell_boltzmann(masses[sysm.types], 300.0).astype(np.float32)
@@ -912,6 +917,8 @@ def main():
                     help="single-structure workloads: network precision")
     ap.add_argument("--structures", type=int, default=0, help="llzo_batch: first N structures only (profiling)")
     ap.add_argument("--candidates", type=int, default=0, help="llzo_batch: first C candidates only (profiling)")
+    ap.add_argument("--mg-cells", default="", help="mgwater_nve: NX,NY orthohexagonal cells instead of 112,65 "
+                                                   "(profiling on a smaller slab)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

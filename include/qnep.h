@@ -179,6 +179,24 @@ qnep_status qnep_nve_run(qnep_model* m, int n_atoms, float* positions, float* ve
                          const double* masses, const double box[9], double dt_fs, int n_steps, void* stream,
                          float* forces, double* energies);
 
+/* NVE in a uniform external electric field, with the ionic current along the trajectory
+ * (Sec. II.D): as qnep_nve_run, but every force call also computes the Born effective charges
+ * (Eq. bec_2) and the ions move under F_i + F^ext_i, F^ext_i,b = sum_a E_a Z_i,ab
+ * (Eq. electric_force); after the initial state and after every step the polarization current
+ * Pdot_a = sum_i sum_b Z_i,ab v_i,b (Eq. polarization_derivative) of that state is recorded,
+ * the series whose autocorrelation gives the infrared spectrum and the ionic conductivity.
+ *   efield: host double[3] (V/A), finite; zero gives plain NVE dynamics plus the current
+ *   forces: device [N][3], left holding F + F^ext of the final positions
+ *   bec:    device [N][3][3] float32 workspace, left holding Z of the final positions
+ *   energies: device [n_steps + 1][2] (U_pot, K) as for qnep_nve_run (U_pot is the force
+ *           call's energy; the field's work is not in it)
+ *   pdot:   device [n_steps + 1][3] doubles (e A/fs), 8-byte aligned
+ * Asynchronous on `stream`; qnep_sync_status reports the status of the last force call. */
+qnep_status qnep_nve_run_field(qnep_model* m, int n_atoms, float* positions, float* velocities, const int* types,
+                               const double* masses, const double box[9], double dt_fs, int n_steps,
+                               const double efield[3], void* stream, float* forces, float* bec, double* energies,
+                               double* pdot);
+
 /* Synchronize the stream and return the device-side status of the last call. */
 qnep_status qnep_sync_status(qnep_model* m, void* stream);
 

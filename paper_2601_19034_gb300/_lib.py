@@ -105,6 +105,8 @@ def _declare(lib):
     lib.qnep_stage_name.restype = ctypes.c_char_p
     lib.qnep_nve_run.argtypes = [p, i, p, p, p, p, p, ctypes.c_double, i, p, p, p]
     lib.qnep_nve_run.restype = i
+    lib.qnep_nve_run_field.argtypes = [p, i, p, p, p, p, p, ctypes.c_double, i, p, p, p, p, p, p]
+    lib.qnep_nve_run_field.restype = i
     lib.qnep_field_response.argtypes = [i, p, p, p, p, i, p, p]
     lib.qnep_field_response.restype = i
     # batched evaluation

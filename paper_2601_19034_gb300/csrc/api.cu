@@ -1,5 +1,6 @@
 // C ABI of the qNEP force call: model lifetime, workspaces, k-tables and the
 // launch sequence of one force call (see include/qnep.h for the contract).
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -729,6 +730,67 @@ qnep_status qnep_nve_run(qnep_model* m, int n, float* positions, float* velociti
         if (s != QNEP_OK) return s;
         launch_vv_kick_energy(n, velocities, forces, types, ms, m->hp.n_species, dt, true, m->md_scalars, energies,
                               m->md_step, m->md_ke, m->md_done, st);
+    }
+    CK(cudaGetLastError());
+    return QNEP_OK;
+}
+
+qnep_status qnep_nve_run_field(qnep_model* m, int n, float* positions, float* velocities, const int* types,
+                               const double* masses, const double box[9], double dt_fs, int n_steps,
+                               const double efield[3], void* stream, float* forces, float* bec, double* energies,
+                               double* pdot) {
+    if (!m) return QNEP_ERR_ARG;
+    if (!positions || !velocities || !types || !masses || !forces || !bec || !energies || !pdot || !efield ||
+        n_steps < 0 || !(dt_fs > 0))
+        return fail(m, QNEP_ERR_ARG, "bad NVE-in-field arguments");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(efield[a])) return fail(m, QNEP_ERR_ARG, "the field must be finite");
+    if (((uintptr_t)pdot & 7u) != 0) return fail(m, QNEP_ERR_ARG, "pdot must be 8-byte aligned");
+    float ms[MAX_SPECIES] = {1.f, 1.f, 1.f, 1.f};
+    for (int t = 0; t < m->hp.n_species; ++t) {
+        if (!(masses[t] > 0) || !std::isfinite(masses[t])) return fail(m, QNEP_ERR_ARG, "masses must be positive");
+        ms[t] = (float)masses[t];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!m->md_step) {
+        CK(cudaMalloc((void**)&m->md_step, sizeof(int)));
+        CK(cudaMalloc((void**)&m->md_ke, sizeof(double)));
+        CK(cudaMalloc((void**)&m->md_done, sizeof(unsigned int)));
+        CK(cudaMalloc((void**)&m->md_scalars, sizeof(double) * QNEP_NSCALARS));
+    }
+    CK(cudaMemsetAsync(m->md_step, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(m->md_ke, 0, sizeof(double), st));
+    CK(cudaMemsetAsync(m->md_done, 0, sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(energies, 0, sizeof(double) * 2 * (size_t)(n_steps + 1), st));
+    qnep_outputs o{};
+    o.scalars = m->md_scalars;
+    o.forces = forces;
+    o.bec = bec;
+    o.want_virial = 0;
+    const float dt = (float)dt_fs;
+    // force call at the current positions, then F += E . Z (Eq. electric_force)
+    auto field_forces = [&]() -> qnep_status {
+        qnep_status s = compute_impl(m, n, positions, types, box, stream, &o, nullptr);
+        if (s != QNEP_OK) return s;
+        s = qnep_field_response(n, bec, efield, nullptr, forces, 1, nullptr, stream);
+        return s == QNEP_OK ? s : fail(m, s, "field response failed");
+    };
+    // Pdot = sum_i Z_i v_i (Eq. polarization_derivative) of the state after step k
+    auto current = [&](int k) -> qnep_status {
+        qnep_status s = qnep_field_response(n, bec, efield, velocities, nullptr, 0, pdot + 3 * (size_t)k, stream);
+        return s == QNEP_OK ? s : fail(m, s, "polarization current failed");
+    };
+    qnep_status s = field_forces();
+    if (s != QNEP_OK) return s;
+    launch_vv_kick_energy(n, velocities, forces, types, ms, m->hp.n_species, dt, false, m->md_scalars, energies,
+                          m->md_step, m->md_ke, m->md_done, st);
+    if ((s = current(0)) != QNEP_OK) return s;
+    for (int k = 0; k < n_steps; ++k) {
+        launch_vv_kick_drift(n, positions, velocities, forces, types, ms, m->hp.n_species, dt, st);
+        if ((s = field_forces()) != QNEP_OK) return s;
+        launch_vv_kick_energy(n, velocities, forces, types, ms, m->hp.n_species, dt, true, m->md_scalars, energies,
+                              m->md_step, m->md_ke, m->md_done, st);
+        if ((s = current(k + 1)) != QNEP_OK) return s;
     }
     CK(cudaGetLastError());
     return QNEP_OK;

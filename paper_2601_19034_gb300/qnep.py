@@ -228,6 +228,34 @@ def nve(model: "QNEP", positions: torch.Tensor, velocities: torch.Tensor, types:
     return forces, energies
 
 
+def nve_field(model: "QNEP", positions: torch.Tensor, velocities: torch.Tensor, types: torch.Tensor, masses, box,
+              dt_fs: float, n_steps: int, efield, stream=None):
+    """NVE in a uniform field E (V/A) with the polarization current recorded at every step.
+
+    Returns (forces [N, 3] = F + E.Z of the final positions, bec [N, 3, 3] of the final positions,
+    energies [n_steps + 1, 2] = (U_pot, K), pdot [n_steps + 1, 3] in e A/fs).
+    """
+    assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
+    assert velocities.is_cuda and velocities.dtype == torch.float32 and velocities.is_contiguous()
+    n = positions.shape[0]
+    dev = positions.device
+    forces = torch.empty(n, 3, dtype=torch.float32, device=dev)
+    bec = torch.empty(n, 3, 3, dtype=torch.float32, device=dev)
+    energies = torch.zeros(n_steps + 1, 2, dtype=torch.float64, device=dev)
+    pdot = torch.zeros(n_steps + 1, 3, dtype=torch.float64, device=dev)
+    ms = np.ascontiguousarray(np.asarray(masses, dtype=np.float64))
+    e = (ctypes.c_double * 3)(*[float(x) for x in np.asarray(efield, dtype=np.float64).reshape(3)])
+    model._set_box(box)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    st = model.lib.qnep_nve_run_field(model.handle, n, positions.data_ptr(), velocities.data_ptr(), types.data_ptr(),
+                                      ms.ctypes.data, model._box, float(dt_fs), int(n_steps), e,
+                                      ctypes.c_void_p(stream), forces.data_ptr(), bec.data_ptr(), energies.data_ptr(),
+                                      pdot.data_ptr())
+    _lib.check(st, model.handle)
+    return forces, bec, energies, pdot
+
+
 def field_response(bec: torch.Tensor, efield=None, velocities: torch.Tensor = None, forces: torch.Tensor = None,
                    accumulate: bool = False, pdot: torch.Tensor = None, stream=None):
     """External-field force E . Z_i and polarization current sum_i Z_i v_i (Sec. II.D).

@@ -6,11 +6,13 @@ qnep_field_response against the oracle's contractions, on the same inputs:
   * seeded random Z, v and force arrays at sizes around the tile (0, 1, 255, 256,
     257, 1000, 65,537 atoms), with 16-byte-aligned and 4-byte-offset arrays, in
     every output combination, overwrite and accumulate;
-  * the 4,194,304-atom launch the benchmark times: sampled atoms and the full Pdot.
+  * the 4,194,304-atom launch the benchmark times: sampled atoms and the full Pdot;
+  * NVE in a field (qnep_nve_run_field): one velocity-Verlet step under F + E.Z and the current
+    of both states against the oracle; E = 0 against qnep_nve_run; momentum kept when Q = 0.
 Tolerances: the kernel forms each component with three FP32 fused multiply-adds
-(relative error <= 2^-22 of sum_a |E_a Z_i,ab|, bound here by 1e-6 of it); Pdot adds
-FP32 partials over <= 8 atoms before FP64, so its error is <= 1e-6 of
-sum_i sum_b |Z_i,ab v_i,b|.  Through the force call the BEC bound (1e-4 e) carries
+(relative error <= 2^-22 of sum_a |E_a Z_i,ab|, bound here by 1e-6 of it); Pdot is a
+compensated FP32 sum per thread, FP32 warp sums (5 roundings) and FP64 beyond, so its
+error is <= 7 x 2^-24 < 1e-6 of sum_i sum_b |Z_i,ab v_i,b|.  Through the force call the BEC bound (1e-4 e) carries
 over: |dF^ext| <= 1e-4 sum_a |E_a|, |dPdot_a| <= 1e-4 sum_i sum_b |v_i,b| (+ the FP32 term).
 """
 import ctypes
@@ -151,3 +153,78 @@ def test_argument_errors(dev):
     assert call(10, z.data_ptr(), e, None, f.data_ptr(), 2, None, s) == _lib.QNEP_ERR_ARG          # accumulate flag
     assert call(10, z.data_ptr(), None, None, None, 0, None, s) == _lib.QNEP_OK                    # nothing asked
     torch.cuda.synchronize()
+
+
+ACC_UNIT = 9.6485332e-3   # (eV/A)/amu in A/fs^2
+
+
+def _batio3_md():
+    s = wl.batio3_supercell(4, seed=91)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(92))[0]
+    # k-space-only electrostatics: the truncated real-space sum jumps at r_c, and this lattice has
+    # many Ti-O pairs within 1e-4 A of 6 A, where FP32 and FP64 may classify a pair differently
+    elec = wl.Elec(mode=2, kind="ewald")
+    masses = wl.species_masses(wl.BATIO3_SPECIES)
+    v0 = wl.maxwell_boltzmann(masses[s.types], 300.0, seed=93).astype(np.float32)
+    return s, hp, params, elec, masses, v0
+
+
+def test_nve_in_field_step_against_oracle(dev):
+    """One velocity-Verlet step under F + E.Z, and Pdot of both states, against the oracle."""
+    from paper_2601_19034_gb300.qnep import QNEP, nve_field
+    s, hp, params, elec, masses, v0 = _batio3_md()
+    m_atom = masses[s.types]
+    e = np.array([0.05, -0.02, 0.08])
+    dt = 0.5
+    model = QNEP(hp, params, elec)
+    pos = torch.tensor(s.positions, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    f1, z1, en, pdot = nve_field(model, pos, vel, torch.tensor(s.types, device=dev), masses, s.box, dt, 1, e)
+    torch.cuda.synchronize()
+    assert model.sync_status() == 0
+    x0 = s.positions.astype(np.float64)
+    r0 = forcecall.force_call(x0, s.box, s.types, hp, params, elec)
+    ft0 = r0["forces"] + field.electric_force(r0["bec"], e)
+    a0 = ft0 * ACC_UNIT / m_atom[:, None]
+    x1 = x0 + dt * (v0 + 0.5 * dt * a0)
+    x1_gpu = pos.cpu().numpy()
+    np.testing.assert_allclose(x1_gpu, x1, atol=2e-5)
+    r1 = forcecall.force_call(x1_gpu.astype(np.float64), s.box, s.types, hp, params, elec)
+    ft1 = r1["forces"] + field.electric_force(r1["bec"], e)
+    np.testing.assert_allclose(f1.cpu().numpy(), ft1, atol=1e-4 + 1e-4 * np.abs(e).sum())
+    np.testing.assert_allclose(z1.cpu().numpy(), r1["bec"], atol=1e-4)
+    v1 = v0 + 0.5 * dt * (a0 + ft1 * ACC_UNIT / m_atom[:, None])
+    v1_gpu = vel.cpu().numpy()
+    np.testing.assert_allclose(v1_gpu, v1, atol=1e-6)
+    p = pdot.cpu().numpy()
+    for k, (z_ref, v) in enumerate(((r0["bec"], v0), (r1["bec"], v1_gpu))):
+        p_ref = field.polarization_current(z_ref, v)
+        assert np.all(np.abs(p[k] - p_ref) <= 1e-4 * np.abs(v).sum()), (k, p[k], p_ref)
+    model.close()
+
+
+def test_nve_in_zero_field_is_plain_nve_and_momentum_is_kept(dev):
+    """E = 0 reproduces qnep_nve_run; in a field with Q = 0 the total momentum stays zero
+    (sum_i F^ext_i = Q E by the sum rule of Eq. bec_2)."""
+    from paper_2601_19034_gb300.qnep import QNEP, nve, nve_field
+    s, hp, params, elec, masses, v0 = _batio3_md()
+    m_atom = masses[s.types]
+    typ = torch.tensor(s.types, device=dev)
+    model = QNEP(hp, params, elec)
+    pos_a, vel_a = torch.tensor(s.positions, device=dev), torch.tensor(v0, device=dev)
+    nve(model, pos_a, vel_a, typ, masses, s.box, 0.5, 5)
+    pos_b, vel_b = torch.tensor(s.positions, device=dev), torch.tensor(v0, device=dev)
+    _, _, _, pdot = nve_field(model, pos_b, vel_b, typ, masses, s.box, 0.5, 5, (0.0, 0.0, 0.0))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(pos_b.cpu().numpy(), pos_a.cpu().numpy(), atol=1e-5)
+    np.testing.assert_allclose(vel_b.cpu().numpy(), vel_a.cpu().numpy(), atol=1e-6)
+    assert np.isfinite(pdot.cpu().numpy()).all()
+    pos_c, vel_c = torch.tensor(s.positions, device=dev), torch.tensor(v0, device=dev)
+    nve_field(model, pos_c, vel_c, typ, masses, s.box, 0.5, 10, (0.3, -0.2, 0.25))
+    torch.cuda.synchronize()
+    assert model.sync_status() == 0
+    mom = (m_atom[:, None] * vel_c.cpu().numpy().astype(np.float64)).sum(0)
+    scale = (m_atom[:, None] * np.abs(vel_c.cpu().numpy())).sum(0)
+    assert np.all(np.abs(mom) <= 1e-4 * scale), (mom, scale)
+    model.close()
