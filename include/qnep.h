@@ -230,9 +230,9 @@ const char* qnep_stage_name(int stage);
  *   velocities: device [N][3] float32; needed when pdot != NULL and n_atoms > 0, ignored otherwise
  *   forces:     device [N][3] float32 F^ext, overwritten (accumulate = 0) or added to an
  *               existing force array (accumulate = 1), or NULL
- *   pdot:       device double[3], cleared on the stream and then summed (FP32 over at most
- *               8 atoms per thread, FP64 beyond, FP64 atomics: the last bits depend on the
- *               order of the blocks), or NULL
+ *   pdot:       device double[3], cleared on the stream and then summed (a compensated FP32
+ *               sum per thread, FP32 warp sums, FP64 across warps and blocks with FP64
+ *               atomics: the last bits depend on the order of the blocks), or NULL
  * Float arrays must be 4-byte aligned (16-byte alignment of all of them takes the
  * vectorised path), pdot 8-byte aligned.  Asynchronous on `stream`.  Returns
  * QNEP_ERR_ARG for a negative n_atoms, a missing input, a non-finite field or a
