@@ -56,3 +56,33 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.ElecC) == 56
     assert ctypes.sizeof(_lib.HParamsC) == 40
     assert ctypes.sizeof(_lib.OutputsC) == 64
+
+
+def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
+    """Host-side checks of the field-response and training entry points (no CUDA call is reached)."""
+    dummy = ctypes.c_void_p(0x1000)       # never dereferenced: every call below returns before using it
+    e = (ctypes.c_double * 3)(0.1, 0.0, 0.0)
+    nan_e = (ctypes.c_double * 3)(float("nan"), 0.0, 0.0)
+    fr = lib.qnep_field_response
+    assert fr(-1, dummy, e, dummy, dummy, 0, dummy, None) == _lib.QNEP_ERR_ARG
+    assert fr(4, dummy, None, None, dummy, 0, None, None) == _lib.QNEP_ERR_ARG       # forces without a field
+    assert fr(4, dummy, e, None, None, 0, dummy, None) == _lib.QNEP_ERR_ARG          # Pdot without velocities
+    assert fr(4, None, e, None, dummy, 0, None, None) == _lib.QNEP_ERR_ARG           # no Z
+    assert fr(4, dummy, nan_e, None, dummy, 0, None, None) == _lib.QNEP_ERR_ARG      # non-finite field
+    assert fr(4, ctypes.c_void_p(0x1002), e, None, dummy, 0, None, None) == _lib.QNEP_ERR_ARG   # misaligned
+    assert fr(4, dummy, e, None, dummy, 3, None, None) == _lib.QNEP_ERR_ARG          # accumulate flag
+    assert fr(4, dummy, None, None, None, 0, None, None) == _lib.QNEP_OK             # nothing asked: no work
+    assert lib.qnep_snes_sample(0, 5, dummy, dummy, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_snes_sample(3, 5, None, dummy, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_snes_update(1025, 5, dummy, dummy, dummy, dummy, -1.0, -1.0, None) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_snes_update(4, 5, dummy, dummy, dummy, dummy, float("inf"), -1.0, None) == _lib.QNEP_ERR_ARG
+    w = _lib.LossWeightsC(1.0, 1.0, 0.0, 0.0)
+    bad = _lib.LossWeightsC(1.0, float("nan"), 0.0, 0.0)
+    bl = lib.qnep_batch_loss
+    assert bl(0, 1, dummy, 4, dummy, dummy, dummy, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert bl(2, 1, dummy, 4, dummy, dummy, dummy, None, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert bl(2, 1, dummy, 4, dummy, None, dummy, None, dummy, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert bl(2, 1, dummy, 4, dummy, None, dummy, None, None, 0, bad, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_batch_set_params(None, dummy, None) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_nve_run_field(None, 4, dummy, dummy, dummy, dummy, dummy, 0.5, 1, e, None, dummy, dummy,
+                                  dummy, dummy) == _lib.QNEP_ERR_ARG
