@@ -536,26 +536,44 @@ def _time_snes_step(b, graph, stream, out, off, params, dev, reps):
         f_ref = out["forces"][0].clone()
     loss = torch.empty(c, dtype=torch.float64, device=dev)
     terms = torch.empty(c, 4, dtype=torch.float64, device=dev)
-    times = []
+    names = ("normal_deviates", "snes_sample", "set_params", "batched_call", "batch_loss", "snes_update")
+    times, parts = [], {k: [] for k in names}
     with torch.cuda.stream(stream):
         for k in range(reps + 2):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+            ev[0].record(stream)
             noise.normal_()
+            ev[1].record(stream)
             snes_sample(mu, sigma, noise, out=z, stream=stream.cuda_stream)
+            ev[2].record(stream)
             b.set_params(z, stream=stream.cuda_stream)
+            ev[3].record(stream)
             graph.replay()
+            ev[4].record(stream)
             batch_loss(out["energy"], out["forces"], e_ref, f_ref, off_d, z, (1.0, 1.0, 0.0, 1e-6), loss=loss,
                        terms=terms, stream=stream.cuda_stream)
+            ev[5].record(stream)
             snes_update(loss, noise, mu, sigma, stream=stream.cuda_stream)
-            e1.record(stream)
-            e1.synchronize()
+            ev[6].record(stream)
+            ev[6].synchronize()
             if k >= 2:
-                times.append(e0.elapsed_time(e1))
+                times.append(ev[0].elapsed_time(ev[6]))
+                for q, name in enumerate(names):
+                    parts[name].append(ev[q].elapsed_time(ev[q + 1]))
     b.set_params(torch.tensor(params, dtype=torch.float32, device=dev), stream=stream.cuda_stream)
     stream.synchronize()
     ms = float(np.median(times))
-    return {"ms": ms, "loss_best": float(loss.min().item()),
+    stage_ms = {k: float(np.median(v)) for k, v in parts.items()}
+    # the loss pass streams the candidates' forces once (12 B per atom and candidate); the reference
+    # forces (12 B per atom) are re-read per candidate from L2, the energies and parameters are small
+    n_total = int(out["forces"].shape[1])
+    loss_bytes = c * n_total * 12 + n_total * 12 + c * (len(off) - 1) * 8 + c * p * 4
+    loss_gbs = loss_bytes / (stage_ms["batch_loss"] * 1e-3) / 1e9
+    hbm = _peaks()[0]["hbm_gbs"]
+    return {"ms": ms, "stage_ms": stage_ms, "loss_best": float(loss.min().item()),
+            "batch_loss_roofline": {"kernel": "k_batch_loss (+ memset, k_loss_finalize)", "bound": "hbm",
+                                    "achieved": loss_gbs, "peak": hbm, "unit": "GB/s", "frac": loss_gbs / hbm,
+                                    "work": f"{loss_bytes} algorithmic bytes per call"},
             "what": "normal deviates + qnep_snes_sample + qnep_batch_set_params + batched call (graph replay) "
                     "+ qnep_batch_loss + qnep_snes_update, CUDA events on the call's stream, median"}
 

@@ -10,11 +10,14 @@
 // The batched call feeds energies and forces; its corrected charges meet the total-charge
 // target exactly and it computes neither virials nor BEC, so the loss has no D_Q, D_v, D_Z.
 //
-// Loss: the force term is the large one (C x N x 3 floats, HBM bound): blocks over
-// (2048-float chunk, candidate) read forces and references with coalesced loads, sum 8 squares
-// per thread in FP32, reduce the block in FP64 and add one FP64 atomic per block; one more block
-// per candidate sums the energy terms and the parameter norms in FP64 and writes them directly;
-// a one-block pass forms the roots and the weighted sum.
+// Loss: the force term is the large one (C x N x 3 floats, HBM bound): for every candidate a
+// one-wave set of blocks walks the force stream in 2048-float chunks (coalesced loads, 8 per
+// thread in flight), each thread keeps a compensated (Kahan) FP32 sum of its squares, warps add
+// their 32 sums in FP32 and one thread adds the block's 8 warp sums in FP64 and the block total
+// with an FP64 atomic (GB300 runs FP64 at 1/64 of the FP32 rate: FP64 warp reductions in every
+// one of ~31,000 small blocks held the pass to 16 % of HBM); one more block per candidate sums
+// the energy terms and the parameter norms in FP64 and writes them directly; a one-block pass
+// forms the roots and the weighted sum.
 // Update: every block ranks the (at most 1024) losses in shared memory (ties by index, NaN last),
 // forms the utilities in FP64 (their normaliser is the sum of all candidates' raw weights, each
 // rank occurring once), then takes its parameters: g_mu = sum_k u_k s_k, g_sigma = sum_k u_k
@@ -54,29 +57,44 @@ k_snes_sample(long long total, int n_params, const float* __restrict__ mu, const
     }
 }
 
-// blockIdx.y = candidate; blockIdx.x < n_chunks: a chunk of the force stream; == n_chunks: the
-// energy term and the parameter norms.
+// blockIdx.y = candidate; blockIdx.x < n_fblocks: every n_fblocks-th chunk of the force stream;
+// == n_fblocks: the energy term and the parameter norms.
 __global__ void __launch_bounds__(kThreads)
-k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n_chunks,
+k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n_fblocks,
              const double* __restrict__ energy, const float* __restrict__ forces,
              const double* __restrict__ energy_ref, const float* __restrict__ forces_ref,
              const float* __restrict__ params, int n_params, double* __restrict__ terms) {
     __shared__ double red[kThreads / 32];
+    __shared__ float redf[kThreads / 32];
     const int c = blockIdx.y;
-    if ((int)blockIdx.x < n_chunks) {
-        const long long base = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if ((int)blockIdx.x < n_fblocks) {
         const float* fc = forces + (long long)c * n_force;
-        float d[kPerThread];
+        float s = 0.f, comp = 0.f;                     // Kahan sum of this thread's squares
+        for (long long base = (long long)blockIdx.x * kChunk + threadIdx.x; base < n_force;
+             base += (long long)n_fblocks * kChunk) {
+            float d[kPerThread];
 #pragma unroll
-        for (int k = 0; k < kPerThread; ++k) {
-            const long long i = base + (long long)k * kThreads;
-            d[k] = i < n_force ? fc[i] - forces_ref[i] : 0.f;
+            for (int k = 0; k < kPerThread; ++k) {
+                const long long i = base + (long long)k * kThreads;
+                d[k] = i < n_force ? fc[i] - forces_ref[i] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kPerThread; ++k) {
+                const float y = d[k] * d[k] - comp;
+                const float t = s + y;
+                comp = (t - s) - y;
+                s = t;
+            }
         }
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < kPerThread; ++k) acc = fmaf(d[k], d[k], acc);
-        const double s = block_sum((double)acc, red);
-        if (threadIdx.x == 0) atomicAdd(terms + 4 * c + 1, s);
+        float v = s - comp;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += (double)redf[w];
+            atomicAdd(terms + 4 * c + 1, t);
+        }
         return;
     }
     double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0;
@@ -193,11 +211,15 @@ extern "C" qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long n_force = forces ? 3LL * n_total : 0;
     const long long chunks = (n_force + kChunk - 1) / kChunk;
-    if (chunks + 1 > INT_MAX) return QNEP_ERR_ARG;
+    // one wave of 8 blocks per SM over all candidates, at least one block per candidate
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long per_cand = ((long long)(sms > 0 ? sms : 152) * 8 + n_candidates - 1) / n_candidates;
+    const int n_fblocks = (int)(chunks < per_cand ? chunks : per_cand);
     if (cudaMemsetAsync(terms, 0, sizeof(double) * 4 * (size_t)n_candidates, st) != cudaSuccess)
         return QNEP_ERR_CUDA;
-    dim3 grid((unsigned)(chunks + 1), (unsigned)n_candidates);
-    k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, n_force, (int)chunks, energy, forces, energy_ref,
+    dim3 grid((unsigned)(n_fblocks + 1), (unsigned)n_candidates);
+    k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, n_force, n_fblocks, energy, forces, energy_ref,
                                             forces_ref, params, params ? n_params : 0, terms);
     if (cudaGetLastError() != cudaSuccess) return QNEP_ERR_CUDA;
     k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, w->energy, w->force, w->l1, w->l2, terms, loss);
