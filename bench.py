@@ -11,7 +11,9 @@ item kernel's roofline (CUDA events around it) and the FP64 oracle on the host.
 Single-structure workloads (--workload batio3 | water_pppm, --precision): one full
 force call per step (forces, virial, BEC, polarization).  Inputs are resident in
 HBM; L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
-The JSON line follows the repository's measurement contract ("Measurement").
+The JSON line carries value, roofline (dominant kernel against the measured peak), cpu_baseline
+(the FP64 oracle on the host cores), e2e (host buffers, copies inside the timed region), clocks
+(nvidia-smi samples during the timed region) and gpu_launches.
 """
 from __future__ import annotations
 
@@ -362,7 +364,9 @@ def _roofline_generic(stage_avg, sysm, clocks, peaks):
             "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
 
 
-# algorithmic FP32 flop per atom of the descriptor kernels (BaTiO3 neighbour counts)
+# algorithmic FP32 flop per atom of the descriptor kernels at the BaTiO3 neighbour counts (68 list and
+# 18 angular entries per atom): forward radial 68 x 30 + angular 18 x 230 + network 3 x 900; backward
+# radial 68 x 40 + angular 18 x 2 x 700
 FLOP_PER_ATOM = {"descriptor_forward": 18000, "descriptor_backward": 45000}
 
 
@@ -435,7 +439,7 @@ BATCH_KERNELS_PER_CALL = 3
 
 
 def _batch_flop(systems, hp, elec, n_cand):
-    """Algorithmic FP32 flop of one batched call (per (atom, candidate) counts).
+    """Algorithmic FP32 flop of one batched call (per (atom, candidate) counts below).
 
     Neighbour counts are the density estimates 4/3 pi r_c^3 rho of each structure.
     Per (atom, candidate): descriptor contractions 2 S (K_R N_R + K_A N_A N_lm),
@@ -676,7 +680,7 @@ def run_batch(args):
         mw.close()
     for prec in ("bf16", "tf32"):
         mixed[f"speedup_{prec}_vs_fp32"] = mixed[prec]["value"] / mixed["fp32"]["value"]
-    mixed["errors_vs_oracle"] = "per-output table in DESIGN.md (tests/test_gpu_precision.py bounds)"
+    mixed["errors_vs_oracle"] = "per-output bounds against the FP64 oracle in tests/test_gpu_precision.py"
 
     # plain FP32 single-structure path on the same structures (candidate 0; one call per structure)
     single = QNEP(hp, params[0], elec)

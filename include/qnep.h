@@ -38,12 +38,12 @@ typedef enum {
     QNEP_ERR_ARG = 1,           /* invalid argument (NULL, size, range, NaN box) */
     QNEP_ERR_CUDA = 2,          /* a CUDA call failed; the model should be destroyed */
     QNEP_ERR_NBR_OVERFLOW = 3,  /* an atom had more neighbours than the list capacity */
-    QNEP_ERR_UNSUPPORTED = 4,   /* shape / box / option not supported by this build */
+    QNEP_ERR_UNSUPPORTED = 4,   /* shape / box / option not supported by this library */
     QNEP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
     QNEP_ERR_OOM = 6            /* device allocation failed */
 } qnep_status;
 
-/* Descriptor and network sizes (Sec. II.A).  This build supports
+/* Descriptor and network sizes (Sec. II.A).  This library supports
  * n_radial = n_angular = 5, basis_radial = basis_angular = 9, l_max = 4,
  * use_4body = 1, n_neurons = 30 (descriptor length 30) and 1..4 species;
  * other sizes return QNEP_ERR_UNSUPPORTED. */
@@ -71,7 +71,7 @@ typedef struct {
     double rc_real;    /* real-space cutoff (A), mode 1; <= rc_radial */
     double kmax;       /* Ewald: strict wave-vector cutoff |k| < kmax (1/A) */
     int    mesh[3];    /* PPPM mesh (even sizes, fewer than 2^31 points in all) */
-    int    order;      /* PPPM assignment order; this build supports 5 */
+    int    order;      /* PPPM assignment order; this library supports 5 */
     double q_total;    /* target total charge Q of the naked charges (Eq. charge-scaling) */
 } qnep_elec;
 

@@ -14,7 +14,7 @@
 
 namespace qnep {
 
-// Descriptor / network shape supported by the kernels of this build.
+// Descriptor / network shape supported by the kernels of this library.
 constexpr int NR = 5;      // radial functions
 constexpr int KR = 9;      // Chebyshev terms (radial)
 constexpr int NA = 5;      // angular radial functions

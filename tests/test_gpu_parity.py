@@ -1,6 +1,6 @@
 """GPU parity: the CUDA force call against the FP64 oracle, element by element.
 
-Tolerances (FP32 path; derivation in DESIGN.md, "Parity tolerances"):
+Tolerances (FP32 path; each from the FP32 rounding of the sums that form the output):
   energy        |dE| / N          <= 1e-6 eV/atom (also each energy part)
   forces        max |dF|          <= 1e-4 eV/A
   charges       max |dq|          <= 2e-6 e
