@@ -21,6 +21,7 @@ Modules
   forcecall   the full force call: energy, forces, virial, charges, BEC, P
   field       external-field force and polarization current from the BEC (Sec. II.D)
   training    population loss terms of Sec. II.E and the SNES update it drives
+  virial      per-atom virial of Eq. per-atom_virial (Ewald and PPPM)
   params      unpacking of the documented parameter blob
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against

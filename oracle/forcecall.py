@@ -170,6 +170,9 @@ def force_call(positions, box, types, hp, blob, elec, want_bec: bool = True,
         "polarization": (qt_c[:, None] * pos).sum(0),
         "n_radial_entries": len(ent_r.i), "n_angular_entries": len(ent_a.i),
         "adjoint": lam, "charge_adjoint": kap, "sample_valid": done,
+        # per-entry partial forces F_ij = dE/dr_ij of the radial and angular entry sets (the
+        # gradients behind the forces and the virial above), with their entries
+        "partials": ((ent_r, g_r), (ent_a, g_a)),
     }
     if want_bec:
         bec = qt_c[:, None, None] * np.eye(3)[None]
