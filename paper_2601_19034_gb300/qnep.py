@@ -256,6 +256,47 @@ def nve_field(model: "QNEP", positions: torch.Tensor, velocities: torch.Tensor, 
     return forces, bec, energies, pdot
 
 
+def candidate_shard(n_cand: int, world: int, rank: int) -> tuple:
+    """Contiguous, balanced range [c0, c1) of a population of n_cand candidates evaluated by ``rank``.
+
+    With SNES on several GPUs each rank evaluates its own candidates on every structure; the
+    only exchange of the iteration is then the all-gather of the C losses (``gather_losses``).
+    """
+    base, extra = divmod(int(n_cand), int(world))
+    c0 = rank * base + min(rank, extra)
+    return c0, c0 + base + (1 if rank < extra else 0)
+
+
+def gather_losses(local: torch.Tensor, n_cand: int, group=None) -> torch.Tensor:
+    """All ranks' loss shards (``candidate_shard`` order) into the population's losses [n_cand].
+
+    One all-gather of fixed-size float64 buffers (shards padded to the largest); every rank
+    receives the same vector, so every rank's SNES update is the same.
+    """
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    width = -(-int(n_cand) // world)
+    c0, c1 = candidate_shard(n_cand, world, rank)
+    assert local.numel() == c1 - c0
+    buf = torch.zeros(width, dtype=torch.float64, device=local.device)
+    buf[:c1 - c0] = local.to(torch.float64)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    pieces = []
+    for r in range(world):
+        a, b = candidate_shard(n_cand, world, r)
+        pieces.append(parts[r][:b - a])
+    return torch.cat(pieces)
+
+
+def snes_noise(n_cand: int, n_params: int, step: int, seed: int, device) -> torch.Tensor:
+    """Normal deviates [n_cand, n_params] of SNES iteration ``step``: the same on every rank
+    (a generator seeded with seed + step), so no rank has to send them."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + int(step))
+    return torch.randn(int(n_cand), int(n_params), generator=g, device=device, dtype=torch.float32)
+
+
 def field_response(bec: torch.Tensor, efield=None, velocities: torch.Tensor = None, forces: torch.Tensor = None,
                    accumulate: bool = False, pdot: torch.Tensor = None, stream=None):
     """External-field force E . Z_i and polarization current sum_i Z_i v_i (Sec. II.D).
