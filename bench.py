@@ -395,6 +395,30 @@ def run_reference(args):
     cores = torch.get_num_threads()
     if args.workload == "llzo_batch":
         return _reference_batch(args, world, cores)
+    if args.workload == "field_response":
+        # bounded sample: 262,144 atoms of the same synthetic Z and v per step
+        from oracle import field
+        n = 262144
+        rng = np.random.default_rng(7)
+        z = rng.normal(size=(n, 3, 3)).astype(np.float32)
+        v = (rng.normal(size=(n, 3)) * 0.02).astype(np.float32)
+        e = np.array([0.12, 0.05, -0.33])
+        times = []
+        for k in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            field.electric_force(z, e)
+            field.polarization_current(z, v)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t)
+        value = n * len(times) / sum(times)
+        return {"impl": "reference", "metric": "qNEP field response (E.Z_i, sum_i Z_i v_i) atoms/s",
+                "value": value, "unit": "atoms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS["field_response"]},
+                "cpu_baseline": {"value": value, "unit": "atoms/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"each step the oracle's two contractions over {n} atoms"},
+                "e2e": {"value": value, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.workload == "mgwater_nve":
         # bounded sample: each step one force call of a 3297-atom slab of the same construction
         sy0, hp, params, _ = workloads.config_mg_water(nx=6, ny=4)
