@@ -191,7 +191,10 @@ qnep_status qnep_nve_run(qnep_model* m, int n_atoms, float* positions, float* ve
  *   energies: device [n_steps + 1][2] (U_pot, K) as for qnep_nve_run (U_pot is the force
  *           call's energy; the field's work is not in it)
  *   pdot:   device [n_steps + 1][3] doubles (e A/fs), 8-byte aligned
- * Asynchronous on `stream`; qnep_sync_status reports the status of the last force call. */
+ * Asynchronous on `stream`; qnep_sync_status reports the status of the last force call.
+ * QNEP_ERR_ARG for a NULL pointer, n_steps < 0, dt_fs <= 0, a non-finite field, non-positive
+ * masses or a misaligned pdot; force-call errors as for qnep_compute.  The model owns its small
+ * MD state buffers; the caller owns every argument buffer. */
 qnep_status qnep_nve_run_field(qnep_model* m, int n_atoms, float* positions, float* velocities, const int* types,
                                const double* masses, const double box[9], double dt_fs, int n_steps,
                                const double efield[3], void* stream, float* forces, float* bec, double* energies,
@@ -335,7 +338,9 @@ const char* qnep_batch_last_error(const qnep_batch* b);
  * `stream`, ordered before later qnep_batch_compute calls on that stream, including replays
  * of a captured graph of one): params = device [n_candidates][qnep_param_count] float32, the
  * blob layout of qnep_create.  Used by the training loop below; values are not checked (a
- * non-finite candidate gives non-finite outputs and a NaN loss, which ranks last). */
+ * non-finite candidate gives non-finite outputs and a NaN loss, which ranks last).  The batch owns
+ * its copy; the caller keeps `params`.  QNEP_ERR_ARG for a NULL batch or params, QNEP_ERR_CUDA if
+ * the launch fails. */
 qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stream);
 
 /* ---- Training: population loss and separable NES (Sec. II.E) ----------------
@@ -356,7 +361,8 @@ typedef struct {
 } qnep_loss_weights;
 
 /* Candidates z_k = mu + sigma * s_k (SNES sampling; the normal deviates s are the caller's):
- * mu, sigma [P], noise [C][P], params [C][P] float32 (params = fmaf(sigma, noise, mu)). */
+ * mu, sigma [P], noise [C][P], params [C][P] float32 (params = fmaf(sigma, noise, mu)).
+ * QNEP_ERR_ARG for C or P below 1 or a NULL pointer, QNEP_ERR_CUDA if the launch fails. */
 qnep_status qnep_snes_sample(int n_candidates, int n_params, const float* mu, const float* sigma, const float* noise,
                              float* params, void* stream);
 
@@ -377,7 +383,10 @@ qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offs
  * u_k = max(0, ln(C/2 + 1) - ln k) / sum_j max(0, ln(C/2 + 1) - ln j) - 1/C for rank k;
  * mu += eta_mu sigma sum_k u_k s_k; sigma *= exp(eta_sigma / 2 sum_k u_k (s_k^2 - 1)),
  * in FP64, stored to the float32 mu and sigma [P] in place.  A negative rate selects the
- * published default (eta_mu = 1, eta_sigma = (3 + ln P) / (5 sqrt P)).  1 <= C <= 1024. */
+ * published default (eta_mu = 1, eta_sigma = (3 + ln P) / (5 sqrt P)).  loss [C] f64 and noise
+ * [C][P] f32 are read, mu and sigma [P] f32 updated.  QNEP_ERR_ARG for C outside [1, 1024], P below
+ * 1, a NULL pointer or a non-finite rate; QNEP_ERR_CUDA if the launch fails.  The update is
+ * deterministic (fixed summation order), so ranks given the same losses and deviates agree. */
 qnep_status qnep_snes_update(int n_candidates, int n_params, const double* loss, const float* noise, float* mu,
                              float* sigma, double eta_mu, double eta_sigma, void* stream);
 void        qnep_batch_destroy(qnep_batch* b);
