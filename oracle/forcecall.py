@@ -175,13 +175,22 @@ def force_call(positions, box, types, hp, blob, elec, want_bec: bool = True,
         "partials": ((ent_r, g_r), (ent_a, g_a)),
     }
     if want_bec:
-        bec = qt_c[:, None, None] * np.eye(3)[None]
-        for ent, a in ((ent_r, a_r), (ent_a, a_a)):
-            half = 0.5 * np.einsum("ea,eb->eab", ent.vec, a)
-            np.add.at(bec, ent.i, half)
-            np.subtract.at(bec, ent.j, half)
-        out["bec"] = bec
+        out["bec"] = periodic_bec(qt_c, ((ent_r, a_r), (ent_a, a_a)))
     return out
+
+
+def periodic_bec(qt_c, entry_derivs):
+    """Eq. (bec_2) from per-entry charge derivatives a_ij = dq~_i/dr_ij.
+
+    Z_i = q~^c_i I + 1/2 sum over i's entries r_ij (x) a_ij - 1/2 sum over the entries
+    (j -> i) of r_ji (x) a_ji (the second term of Eq. bec_2, -r_ji (x) dq~_j/dr_ji).
+    """
+    bec = qt_c[:, None, None] * np.eye(3)[None]
+    for ent, a in entry_derivs:
+        half = 0.5 * np.einsum("ea,eb->eab", ent.vec, a)
+        np.add.at(bec, ent.i, half)
+        np.subtract.at(bec, ent.j, half)
+    return bec
 
 
 def total_energy_autograd(positions, box, types, hp, blob, elec, strain=None):

@@ -204,3 +204,28 @@ def test_charge_gradient_matches_finite_differences(batio3_subcell):
     # and it agrees with the staged force call's charges
     out = fc.force_call(pos, box, types, hp, blob, elec, want_bec=False)
     np.testing.assert_allclose(qc.detach().numpy(), out["charges"], atol=1e-12)
+
+
+def test_periodic_bec_is_dp_dr_for_an_isolated_dimer():
+    """For two atoms alone in a large box, Eq. bec_2 (raw per-entry charge derivatives, corrected
+    charge on the diagonal) must equal the exact dP/dr_i: with q~^c_A = (q~_A - q~_B) / 2 and
+    P = -q~^c_A r_AB, both give Z_A = q~^c_A I + 1/2 (q~_A' - q~_B') r_AB (x) r_AB / r.
+    This fixes the factor 1/2 of Eq. bec_2, which the sum rule and translation do not."""
+    pos = np.array([[30.0, 30.0, 30.0], [31.1, 30.9, 30.7]])       # 1.59 A: radial and angular terms
+    types = np.array([0, 1])
+    box = np.diag([60.0] * 3)
+    hp = wl.HParams(n_species=2)
+    blob = wl.random_params(hp, np.random.default_rng(23))[0]
+    elec = wl.Elec(mode=2, kind="ewald")
+    z = fc.force_call(pos, box, types, hp, blob, elec)["bec"]
+    h = 1e-5
+    for i in range(2):
+        for b in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, b] += h
+            pm[i, b] -= h
+            with torch.no_grad():
+                dp = (fc.polarization_autograd(pp, box, types, hp, blob, elec)[0].numpy()
+                      - fc.polarization_autograd(pm, box, types, hp, blob, elec)[0].numpy()) / (2 * h)
+            np.testing.assert_allclose(z[i][:, b], dp, atol=1e-8)
+    assert np.abs(z[0] - z[0][0, 0] * np.eye(3)).max() > 1e-3      # the off-diagonal part is exercised

@@ -1,0 +1,162 @@
+"""Planted mistakes: each pin of the oracle must fail when a plausible error is put into the oracle.
+
+Every test here replaces one oracle function, on the CPU and for the duration of the
+test only (pytest's monkeypatch), by a variant with a typical slip -- a dropped term,
+a wrong sign, an index off by one, a transposed operand, a term given to the wrong
+atom -- and checks that the pin written for that function then fails.  The pins are
+the ordinary tests of tests/test_oracle_*.py, called directly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import descriptor as dm
+from oracle import ewald, field, forcecall, pppm, training, virial
+from tests import test_oracle_descriptor as t_desc
+from tests import test_oracle_electrostatics as t_es
+from tests import test_oracle_forces as t_forces
+from tests import test_oracle_training as t_tr
+from tests import test_oracle_virial as t_vir
+from tests.test_oracle_field import cluster  # noqa: F401  (fixture for the field pins)
+from tests import test_oracle_field as t_field
+
+
+def _fails(pin, *args):
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+def test_control_pins_pass_unmodified(cluster):  # noqa: F811
+    t_desc.test_cutoff_and_basis_edges()
+    t_desc.test_chebyshev_matches_numpy()
+    t_es.test_nacl_madelung_constant()
+    t_field.test_cluster_electric_force_is_gradient_of_field_energy(cluster)
+    t_tr.test_utilities_and_ranks()
+
+
+def test_cutoff_with_the_wrong_sign(monkeypatch):
+    monkeypatch.setattr(dm, "cutoff_function", lambda r, rc: 0.5 * (1.0 - torch.cos(math.pi * r / rc)))
+    _fails(t_desc.test_cutoff_and_basis_edges)
+
+
+def test_chebyshev_index_off_by_one(monkeypatch):
+    orig = dm.chebyshev_t
+    monkeypatch.setattr(dm, "chebyshev_t", lambda x, count: orig(x, count + 1)[..., 1:])
+    _fails(t_desc.test_chebyshev_matches_numpy)
+
+
+def test_legendre_recurrence_slip(monkeypatch):
+    def wrong(c, l_max):
+        p = [torch.ones_like(c), c]
+        for l in range(1, l_max):
+            p.append(((2 * l - 1) * c * p[l] - l * p[l - 1]) / (l + 1))
+        return torch.stack(p[1:l_max + 1], dim=-1)
+    monkeypatch.setattr(dm, "legendre", wrong)
+    _fails(t_desc.test_legendre_matches_scipy)
+    _fails(t_desc.test_angular_descriptor_addition_theorem)
+
+
+def test_angular_sum_without_the_diagonal(monkeypatch):
+    orig = dm._pair_indices
+
+    def off_diagonal(counts, starts):
+        owner, e1, e2 = orig(counts, starts)
+        keep = e1 != e2
+        return owner[keep], e1[keep], e2[keep]
+    monkeypatch.setattr(dm, "_pair_indices", off_diagonal)
+    _fails(t_desc.test_angular_descriptor_addition_theorem)
+
+
+def test_self_energy_dropped(monkeypatch):
+    monkeypatch.setattr(ewald, "self_energy", lambda q, alpha: 0.0 * q.sum())
+    _fails(t_es.test_nacl_madelung_constant)
+
+
+def test_real_space_with_erf_for_erfc(monkeypatch):
+    def wrong(vec, i, j, q, alpha):
+        r = torch.linalg.norm(vec, dim=1)
+        ii, jj = torch.as_tensor(i), torch.as_tensor(j)
+        return 0.5 * ewald.KE * (q[ii] * q[jj] * torch.special.erf(alpha * r) / r).sum()
+    monkeypatch.setattr(ewald, "real_space_energy", wrong)
+    _fails(t_es.test_nacl_madelung_constant)
+
+
+def test_reciprocal_green_function_without_1_over_k2(monkeypatch):
+    def wrong(pos, box, q, alpha, nvec):
+        inv = torch.linalg.inv(box)
+        kv = 2.0 * math.pi * torch.as_tensor(nvec, dtype=torch.float64) @ inv.T
+        k2 = (kv * kv).sum(1)
+        omega = torch.abs(torch.linalg.det(box))
+        g = (2.0 * math.pi / omega) * torch.exp(-k2 / (4.0 * alpha * alpha))
+        phase = pos @ kv.T
+        s_re = (q[:, None] * torch.cos(phase)).sum(0)
+        s_im = -(q[:, None] * torch.sin(phase)).sum(0)
+        return ewald.KE * (g * (s_re * s_re + s_im * s_im)).sum()
+    monkeypatch.setattr(ewald, "reciprocal_energy", wrong)
+    _fails(t_es.test_nacl_madelung_constant)
+
+
+def test_alias_sum_with_the_printed_sign(monkeypatch):
+    orig = pppm.alias_sum
+
+    def printed(n, mesh, order, terms=None):
+        if terms is None and order == 5:
+            z2 = np.sin(math.pi * n / mesh) ** 2
+            return 1.0 - 5.0 / 3.0 * z2 + 7.0 / 9.0 * z2 ** 2 + 17.0 / 189.0 * z2 ** 3 + 2.0 / 2835.0 * z2 ** 4
+        return orig(n, mesh, order, terms)
+    monkeypatch.setattr(pppm, "alias_sum", printed)
+    _fails(t_es.test_alias_sum_closed_form_and_sign)
+
+
+def test_field_force_with_z_transposed(monkeypatch, cluster):  # noqa: F811
+    monkeypatch.setattr(field, "electric_force",
+                        lambda bec, e: np.einsum("b,iab->ia", np.asarray(e, float), np.asarray(bec).reshape(-1, 3, 3)))
+    _fails(t_field.test_cluster_electric_force_is_gradient_of_field_energy, cluster)
+
+
+def test_polarization_current_with_z_transposed(monkeypatch, cluster):  # noqa: F811
+    monkeypatch.setattr(field, "polarization_current",
+                        lambda bec, v: np.einsum("iba,ib->a", np.asarray(bec).reshape(-1, 3, 3), np.asarray(v)))
+    _fails(t_field.test_cluster_polarization_current_is_time_derivative, cluster)
+
+
+def test_utilities_without_the_baseline(monkeypatch):
+    def wrong(n):
+        k = np.arange(1, n + 1, dtype=np.float64)
+        w = np.maximum(0.0, math.log(n / 2.0 + 1.0) - np.log(k))
+        return w / w.sum()
+    monkeypatch.setattr(training, "utilities", wrong)
+    _fails(t_tr.test_utilities_and_ranks)
+
+
+def test_snes_sigma_step_with_the_wrong_sign(monkeypatch):
+    def wrong(mu, sigma, s, fitness, eta_mu=None, eta_sigma=None):
+        s = np.asarray(s, dtype=np.float64)
+        em, es = training.default_rates(s.shape[1])
+        u = training.utilities(s.shape[0])[training.ranks(fitness)]
+        return (np.asarray(mu) + em * np.asarray(sigma) * (u @ s),
+                np.asarray(sigma) * np.exp(-0.5 * es * (u @ (s * s - 1.0))))
+    monkeypatch.setattr(training, "update", wrong)
+    _fails(t_tr.test_snes_minimises_separable_quadratic)
+
+
+def test_per_atom_virial_given_to_the_central_atom(monkeypatch):
+    def wrong(w, ent, g):
+        if len(ent.i):
+            np.add.at(w, ent.i, -np.einsum("ea,eb->eab", ent.vec, g))
+    monkeypatch.setattr(virial, "_entry_term", wrong)
+    _fails(t_vir.test_energy_moment_identity_fixes_the_convention)
+
+
+def test_bec_without_the_half(monkeypatch):
+    def doubled(qt_c, entry_derivs):
+        bec = np.asarray(qt_c)[:, None, None] * np.eye(3)[None]
+        for ent, a in entry_derivs:
+            full = np.einsum("ea,eb->eab", ent.vec, a)
+            np.add.at(bec, ent.i, full)
+            np.subtract.at(bec, ent.j, full)
+        return bec
+    monkeypatch.setattr(forcecall, "periodic_bec", doubled)
+    _fails(t_forces.test_periodic_bec_is_dp_dr_for_an_isolated_dimer)
