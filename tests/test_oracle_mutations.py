@@ -160,3 +160,45 @@ def test_bec_without_the_half(monkeypatch):
         return bec
     monkeypatch.setattr(forcecall, "periodic_bec", doubled)
     _fails(t_forces.test_periodic_bec_is_dp_dr_for_an_isolated_dimer)
+
+
+def test_network_bias_added(monkeypatch):
+    from oracle import network
+
+    def wrong(d, types, model):
+        t = torch.as_tensor(types, dtype=torch.long)
+        h = torch.tanh(torch.einsum("imn,in->im", model.w0[t], d) + model.b0[t])
+        return (model.w1e[t] * h).sum(1) - model.b1e[t], (model.w1q[t] * h).sum(1) - model.b1q[t]
+    monkeypatch.setattr(network, "site_energy_and_charge", wrong)
+    _fails(t_desc.test_network_matches_explicit_loop)
+
+
+def test_bspline_of_the_wrong_order(monkeypatch):
+    def one_order_up(order, x):
+        # the centred cardinal B-spline of order p + 1 from truncated powers (not recursive, so the
+        # oracle's own recursion is not re-entered)
+        p = order + 1
+        x = np.asarray(x, dtype=np.float64)
+        terms = [(-1) ** k * math.comb(p, k) * np.clip(x + p / 2.0 - k, 0.0, None) ** (p - 1) for k in range(p + 1)]
+        return sum(terms) / math.factorial(p - 1)
+    monkeypatch.setattr(pppm, "bspline", one_order_up)
+    _fails(t_es.test_bspline_identities)
+
+
+def test_influence_function_with_the_printed_single_power(monkeypatch):
+    orig = pppm.influence
+    monkeypatch.setattr(pppm, "influence", lambda lengths, mesh, order, alpha, printed_form=False:
+                        orig(lengths, mesh, order, alpha, True))
+    _fails(t_es.test_pppm_converges_to_ewald)
+
+
+def test_neighbour_search_without_periodic_images(monkeypatch):
+    from oracle import geometry
+    orig = geometry.neighbor_entries
+
+    def no_images(pos, box, rc, chunk=256):
+        ent = orig(pos, box, rc, chunk)
+        return ent.select(np.all(ent.shift == 0, axis=1))
+    monkeypatch.setattr(geometry, "neighbor_entries", no_images)
+    _fails(t_desc.test_image_enumeration_counts_and_kdtree)
+    _fails(t_desc.test_descriptor_supercell_replication_small_box)
