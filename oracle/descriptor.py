@@ -71,6 +71,11 @@ def _pair_indices(counts: np.ndarray, starts: np.ndarray):
     return owner, s_rep + local // np.maximum(c_rep, 1), s_rep + local % np.maximum(c_rep, 1)
 
 
+def four_body(t_n: torch.Tensor) -> torch.Tensor:
+    """D^4b_n = tr(T_n^3) of the traceless tensors T_n = sum_j g_n (u u^T - I/3), [atoms, n]."""
+    return torch.einsum("inab,inbc,inca->in", t_n, t_n, t_n)
+
+
 def descriptor(vec_r: torch.Tensor, i_r: np.ndarray, j_r: np.ndarray,
                vec_a: torch.Tensor, i_a: np.ndarray, j_a: np.ndarray,
                types: np.ndarray, atoms: np.ndarray, model) -> torch.Tensor:
@@ -114,5 +119,5 @@ def descriptor(vec_r: torch.Tensor, i_r: np.ndarray, j_r: np.ndarray,
         outer = u[:, :, None] * u[:, None, :] - eye / 3.0               # [E, 3, 3]
         t_e = g_a[:, :, None, None] * outer[:, None, :, :]               # [E, n, 3, 3]
         t_n = torch.zeros(n_loc, n_a, 3, 3, dtype=torch.float64).index_add(0, li_a, t_e)
-        parts.append(torch.einsum("inab,inbc,inca->in", t_n, t_n, t_n))
+        parts.append(four_body(t_n))
     return torch.cat(parts, dim=1) * model.scaler[None, :]

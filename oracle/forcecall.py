@@ -31,6 +31,12 @@ from . import ewald, geometry, network, pppm
 from .params import unpack
 
 
+def correct_charges(qt, q_total):
+    """Total-charge correction of the naked charges, read as q~_i + (Q - sum_j q~_j) / N
+    (Eq. charge-scaling as printed does not give sum q~ = Q); numpy or torch."""
+    return qt + (q_total - qt.sum()) / len(qt)
+
+
 def _entry_sets(pos, box, hp, elec):
     rc_all = max(hp.rc_radial, hp.rc_angular, elec.rc_real if elec.mode == 1 else 0.0)
     ent = geometry.find_entries(pos, box, rc_all)
@@ -104,7 +110,7 @@ def force_call(positions, box, types, hp, blob, elec, want_bec: bool = True,
     # 3. charges
     s = model.sqrt_eps_inf
     qt = s * q
-    qt_c = qt + (elec.q_total - qt.sum()) / n
+    qt_c = correct_charges(qt, elec.q_total)
     q_c = qt_c / s
 
     # 4. electrostatics
@@ -219,7 +225,7 @@ def total_energy_autograd(positions, box, types, hp, blob, elec, strain=None):
     u, q = network.site_energy_and_charge(d, types, model)
     s = model.sqrt_eps_inf
     qt = s * q
-    q_c = (qt + (elec.q_total - qt.sum()) / n) / s
+    q_c = correct_charges(qt, elec.q_total) / s
     e = u.sum()
     if elec.mode == 1:
         e = e + ewald.real_space_energy(vecs(ent_real), ent_real.i, ent_real.j, q_c, elec.alpha)
@@ -247,7 +253,7 @@ def polarization_autograd(positions, box, types, hp, blob, elec):
     _, q = network.site_energy_and_charge(d, types, model)
     s = model.sqrt_eps_inf
     qt = s * q
-    qt_c = qt + (elec.q_total - qt.sum()) / n
+    qt_c = correct_charges(qt, elec.q_total)
     return (qt_c[:, None] * pos).sum(0), pos
 
 
@@ -273,4 +279,4 @@ def charges_autograd(positions, box, types, hp, blob, elec):
     _, q = network.site_energy_and_charge(d, types, model)
     s = model.sqrt_eps_inf
     qt = s * q
-    return (qt + (elec.q_total - qt.sum()) / n) / s, pos
+    return correct_charges(qt, elec.q_total) / s, pos

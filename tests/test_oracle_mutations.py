@@ -20,7 +20,9 @@ from tests import test_oracle_forces as t_forces
 from tests import test_oracle_training as t_tr
 from tests import test_oracle_virial as t_vir
 from tests.test_oracle_field import cluster  # noqa: F401  (fixture for the field pins)
+from tests.test_oracle_forces import batio3_subcell  # noqa: F401  (fixture for the force pins)
 from tests import test_oracle_field as t_field
+from paper_2601_19034_gb300 import workloads as wl
 
 
 def _fails(pin, *args):
@@ -202,3 +204,57 @@ def test_neighbour_search_without_periodic_images(monkeypatch):
     monkeypatch.setattr(geometry, "neighbor_entries", no_images)
     _fails(t_desc.test_image_enumeration_counts_and_kdtree)
     _fails(t_desc.test_descriptor_supercell_replication_small_box)
+
+
+def test_charge_correction_with_the_wrong_sign(monkeypatch, batio3_subcell):  # noqa: F811
+    monkeypatch.setattr(forcecall, "correct_charges", lambda qt, q_total: qt - (q_total - qt.sum()) / len(qt))
+    _fails(t_forces.test_charge_correction_and_bec_sum_rule, batio3_subcell)
+
+
+def test_four_body_as_the_cube_of_the_trace(monkeypatch):
+    monkeypatch.setattr(dm, "four_body", lambda t_n: torch.einsum("inaa->in", t_n) ** 3)
+    _fails(t_desc.test_four_body_brute_force_triple_sum)
+
+
+def test_heyes_kernel_with_half_the_gaussian_term(monkeypatch):
+    def wrong(pos, box, q, alpha, kmax, chunk=2048):
+        pos, q, box = np.asarray(pos, float), np.asarray(q, float), np.asarray(box, float)
+        nvec = ewald.kspace_integers(box, kmax)
+        kv = 2.0 * math.pi * nvec @ np.linalg.inv(box).T
+        k2 = np.einsum("kd,kd->k", kv, kv)
+        g = (2.0 * math.pi / abs(np.linalg.det(box))) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+        th = pos @ kv.T
+        s_re, s_im = (q[:, None] * np.cos(th)).sum(0), -(q[:, None] * np.sin(th)).sum(0)
+        re = q[:, None] * (np.cos(th) * s_re[None] - np.sin(th) * s_im[None])
+        fac = 1.0 / (4.0 * alpha * alpha) + 2.0 / k2
+        bmat = np.eye(3)[None] - fac[:, None, None] * np.einsum("ka,kb->kab", kv, kv)
+        return ewald.KE * np.einsum("ik,k,kab->iab", re, g, bmat)
+    monkeypatch.setattr(virial, "kspace_static_ewald", wrong)
+    s = wl.batio3_supercell(2, seed=31)
+    cell = (s.positions.astype(np.float64), s.box, s.types, None, None)
+    _fails(t_vir.test_kspace_per_atom_sums_to_the_mesh_and_ewald_totals, cell)
+
+
+def test_ranks_with_nan_first(monkeypatch):
+    def wrong(fitness):
+        f = np.asarray(fitness, dtype=np.float64)
+        order = sorted(range(len(f)), key=lambda c: (not np.isnan(f[c]), np.nan_to_num(f[c]), c))
+        r = np.empty(len(f), dtype=np.int64)
+        for k, c in enumerate(order):
+            r[c] = k
+        return r
+    monkeypatch.setattr(training, "ranks", wrong)
+    _fails(t_tr.test_utilities_and_ranks)
+
+
+def test_energy_error_per_structure_not_per_atom(monkeypatch):
+    orig = training.loss_terms
+
+    def wrong(energy, forces, energy_ref, forces_ref, atom_offsets, params):
+        d_e, d_f, l1, l2 = orig(energy, forces, energy_ref, forces_ref, atom_offsets, params)
+        off = np.asarray(atom_offsets)
+        has = np.diff(off) > 0
+        de = np.asarray(energy)[:, has] - np.asarray(energy_ref)[None, has]
+        return np.sqrt((de ** 2).mean(1)), d_f, l1, l2
+    monkeypatch.setattr(training, "loss_terms", wrong)
+    _fails(t_tr.test_loss_closed_forms)
