@@ -229,3 +229,21 @@ def test_periodic_bec_is_dp_dr_for_an_isolated_dimer():
                       - fc.polarization_autograd(pm, box, types, hp, blob, elec)[0].numpy()) / (2 * h)
             np.testing.assert_allclose(z[i][:, b], dp, atol=1e-8)
     assert np.abs(z[0] - z[0][0, 0] * np.eye(3)).max() > 1e-3      # the off-diagonal part is exercised
+
+
+@pytest.mark.parametrize("q_total", [0.0, 0.7])
+def test_polarization_moves_by_q_total_under_translation(q_total):
+    """P = sum_i q~^c_i r_i (Eq. polarization, positions as given): a uniform shift d of all atoms
+    leaves the charges unchanged and moves P by (sum_i q~^c_i) d = Q d exactly (the corrected
+    charges meet the target Q; the uncorrected ones would not)."""
+    rng = np.random.default_rng(29)
+    pos = rng.uniform(-2.5, 2.5, size=(9, 3)) + 30.0
+    types = rng.integers(0, 3, size=9)
+    box = np.diag([60.0] * 3)
+    hp = wl.HParams(n_species=3)
+    blob = wl.random_params(hp, np.random.default_rng(30))[0]
+    elec = wl.Elec(mode=2, kind="ewald", q_total=q_total)
+    d = np.array([0.37, -1.21, 0.58])
+    p0 = fc.force_call(pos, box, types, hp, blob, elec, want_bec=False)["polarization"]
+    p1 = fc.force_call(pos + d, box, types, hp, blob, elec, want_bec=False)["polarization"]
+    np.testing.assert_allclose(p1 - p0, q_total * d, atol=1e-11)
