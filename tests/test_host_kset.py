@@ -1,0 +1,96 @@
+"""Host logic of the Ewald path on the CPU: the half-space k-set the kernels use (csrc/kset_host.h).
+
+The header is compiled into a small host program (g++; CUDA headers only for the vector
+types) that prints every real wave vector of the set with its G(k).  Against the oracle's
+full-sphere enumeration (oracle/ewald.py, written separately): the set is exactly one of
+each +-k pair with 0 < |k| < k_max, every G(k) = (2 pi / V) exp(-k^2 / 4 alpha^2) / k^2 to
+FP32 rounding, the padding entries carry G = 0, and the columns hold contiguous n3 runs.
+"""
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import ewald
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CUDA_INC = "/usr/local/cuda/include"
+
+HARNESS = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "kset_host.h"
+int main(int argc, char** argv) {
+    double L[3] = {atof(argv[1]), atof(argv[2]), atof(argv[3])};
+    qnep::KSet ks = qnep::build_kset(L, atof(argv[4]), atof(argv[5]));
+    int ncol = (int)ks.cols.size() - 1;
+    printf("%d %d %d %zu %zu\n", ncol, (int)ks.chunk_col.size(), (int)ks.cols[ncol].w, ks.kg.size(), ks.chunk_col.size());
+    for (int c = 0; c < ncol; ++c) {
+        int4 col = ks.cols[c];
+        int len = ks.cols[c + 1].w - col.w;
+        for (int t = 0; t < len; ++t) printf("%d %d %d %d %.9e\n", c, col.x, col.y, col.z + t, ks.kg[col.w + t]);
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are not available")
+    d = tmp_path_factory.mktemp("kset")
+    src = d / "kset_main.cpp"
+    src.write_text(HARNESS)
+    exe = d / "kset_main"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2601_19034_gb300", "csrc"),
+                    "-I", CUDA_INC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    return str(exe)
+
+
+def _run(exe, lengths, kmax, alpha):
+    out = subprocess.run([exe, *[repr(float(x)) for x in lengths], repr(kmax), repr(alpha)], check=True,
+                         capture_output=True, text=True).stdout.split("\n")
+    head = [int(x) for x in out[0].split()]
+    rows = np.array([[float(x) for x in ln.split()] for ln in out[1:] if ln.strip()])
+    return head, rows
+
+
+@pytest.mark.parametrize("lengths", [(12.42, 12.42, 12.42), (40.0, 40.0, 40.0), (12.97, 25.94, 12.97),
+                                     (20.3, 31.7, 100.5), (8.0, 8.0, 8.0)])
+def test_half_space_kset_matches_the_oracle(harness, lengths):
+    alpha = 0.3
+    kmax = 2.0 * alpha * math.sqrt(math.log(1e6))
+    head, rows = _run(harness, lengths, kmax, alpha)
+    ncol, nchunk, nk_padded = head[0], head[1], head[2]
+    assert nk_padded == 8 * nchunk and len(rows) == nk_padded
+    real = rows[rows[:, 4] > 0]
+    n = real[:, 1:4].astype(np.int64)
+    full = ewald.kspace_integers(np.diag(lengths), kmax)
+    # exactly one of each +-k pair
+    assert 2 * len(n) == len(full)
+    half = {tuple(v) for v in n}
+    assert len(half) == len(n)
+    for v in map(tuple, full):
+        assert (v in half) != (tuple(-x for x in v) in half)
+    # G(k) to FP32 rounding
+    k = 2 * math.pi * n / np.asarray(lengths)
+    k2 = (k * k).sum(1)
+    g = (2 * math.pi / np.prod(lengths)) * np.exp(-k2 / (4 * alpha * alpha)) / k2
+    np.testing.assert_allclose(real[:, 4], g, rtol=2e-7)
+    # padding carries G = 0 and lies outside the sphere or past the column's run
+    pad = rows[rows[:, 4] == 0]
+    kp = 2 * math.pi * pad[:, 1:4] / np.asarray(lengths)
+    inside = ((kp * kp).sum(1) < kmax * kmax) & ((kp * kp).sum(1) > 0)
+    for (c, n1, n2, n3, _), ins in zip(pad, inside):
+        if ins:   # a padded slot inside the sphere must be past the column's last real n3
+            col = real[real[:, 0] == c]
+            assert n3 > col[:, 3].max()
+    # each column's real entries are one contiguous run of n3
+    for c in range(ncol):
+        col = real[real[:, 0] == c][:, 3]
+        assert len(col) and np.array_equal(col, np.arange(col.min(), col.max() + 1))
