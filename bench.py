@@ -165,8 +165,8 @@ def _ewald_kcount(box, kmax):
 # 6.71e6 atom-evaluations; the traffic grows with the atom-evaluations).  Set to None when the
 # item kernel changes until it is captured again.
 ITEM_DRAM_BYTES_PER_EVAL = 17.36e9 / 6.71e6
-ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 160 x 64 case scaled by "
-                    "atom-evaluations (profiles/k_batch_items_llzo_160x64.md)")
+ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
+                    "first 160 structures x 64 candidates, scaled by atom-evaluations")
 
 
 def _time_single(model, sysm, dev, steps, warmup, flush, want=None):
@@ -322,6 +322,14 @@ def run_ours(args):
     return line
 
 
+def _fp32_peak(mhz):
+    """FP32 FMA peak (TFLOP/s) of the current device at the sampled SM clock, and how it was formed."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count \
+        if torch.cuda.is_available() else 152
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"
+
+
 # kernels of one Ewald force call with forces + BEC (warp-per-atom path): k_bin, k_scan,
 # k_fill, k_order, k_nbr_desc_coop, k_real (second stream), k_sk (with its fused
 # finalisation), k_field_k, k_desc_bwd_coop, k_finalize
@@ -335,7 +343,7 @@ def _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind):
     n = sysm.n_atoms
     nk = _ewald_kcount(sysm.box, elec.kmax)
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12     # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    fp32_peak, peak_src = _fp32_peak(mhz)
     if name in ("field_kspace", "ewald_structure_factor"):
         # algorithmic FP32 work: per (atom, half-space k) one complex multiply-accumulate
         # for S(k) (8 flop) or potential + force (16 flop)
@@ -343,25 +351,25 @@ def _roofline(stage_avg, sysm, hp, elec, clocks, peaks, peak_kind):
         achieved = flop / (ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None, "ms": ms,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+                "peak_source": peak_src,
                 "work": f"{n} atoms x {nk} half-space k"}
     flop = n * FLOP_PER_ATOM.get(name, 0)
     achieved = flop / (ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": None, "ms": ms,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
+            "peak_source": peak_src}
 
 
 def _roofline_generic(stage_avg, sysm, clocks, peaks):
     name = max(stage_avg, key=stage_avg.get)
     ms = stage_avg[name]
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    fp32_peak, peak_src = _fp32_peak(mhz)
     flop = sysm.n_atoms * FLOP_PER_ATOM.get(name, 0)
     achieved = flop / (ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": None, "ms": ms,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)"}
+            "peak_source": peak_src}
 
 
 # algorithmic FP32 flop per atom of the descriptor kernels at the BaTiO3 neighbour counts (68 list and
@@ -485,7 +493,7 @@ def _batch_flop(systems, hp, elec, n_cand):
 
 
 # DRAM bytes of one k_field_response launch (forces + Pdot, 4,194,304 atoms) from the ncu capture of
-# the current kernel (profiles/k_field_response_4m.md): 211.97 MB read + 30.22 MB written (the rest of
+# the current kernel (dram__bytes_read.sum / write.sum): 211.97 MB read + 30.22 MB written (the rest of
 # the 50 MB of forces is still in L2 when the kernel ends); None whenever the kernel changes
 FIELD_DRAM_BYTES = 211.97e6 + 30.22e6
 FIELD_BYTES_PER_ATOM = 36 + 12 + 12      # read Z and v, write F^ext
@@ -677,7 +685,7 @@ def run_batch(args):
 
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    fp32_peak, peak_src = _fp32_peak(mhz)
     flop = _batch_flop(systems, hp, elec, n_cand)
 
     # the item kernel alone: CUDA events around it on the launching stream (eager calls)
@@ -764,7 +772,7 @@ def run_batch(args):
                          "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals if ITEM_DRAM_BYTES_PER_EVAL else None,
                          "traffic_unit": "bytes per launch",
                          "traffic_source": ITEM_DRAM_SOURCE, "ms": item_ms, "prepass_ms": prep_ms,
-                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+                         "peak_source": peak_src,
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
                          "whole_call_frac": achieved / fp32_peak},
             "mixed": mixed,

@@ -40,7 +40,7 @@ typedef enum {
     QNEP_ERR_NBR_OVERFLOW = 3,  /* an atom had more neighbours than the list capacity */
     QNEP_ERR_UNSUPPORTED = 4,   /* shape / box / option not supported by this library */
     QNEP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-    QNEP_ERR_OOM = 6            /* device allocation failed */
+    QNEP_ERR_OOM = 6            /* an allocation (device, or host for a table) failed */
 } qnep_status;
 
 /* Descriptor and network sizes (Sec. II.A).  This library supports
@@ -153,7 +153,10 @@ qnep_status qnep_compute_host(qnep_model* m, int n_atoms, const float* positions
  * g_P (polarization) writes, per atom i (input order),
  *   grad[i][b] = g_E dU^tot/dr_ib + sum_j g_q,j dq^c_j/dr_ib + sum_a g_P,a Z_i,ab
  * where the charge derivative includes the total-charge correction and the last term
- * uses the periodic Born effective charges of Eq. bec_2 as dP/dr.  The descriptor
+ * uses the periodic Born effective charges of Eq. bec_2 as dP/dr (the periodic
+ * definition: it is not the derivative of the polarization output P = sum q~^c r of
+ * the positions as given, so a finite-difference check of P against it fails in a
+ * periodic box by construction; E and q^c are exact derivatives).  The descriptor
  * derivatives are recomputed, nothing per pair is stored.  Other outputs in `out`
  * behave as in qnep_compute except `forces`, which must be NULL; the virial in the
  * scalars is then that of the weighted objective g_E U + sum g_q q^c. */
@@ -200,8 +203,23 @@ qnep_status qnep_nve_run_field(qnep_model* m, int n_atoms, float* positions, flo
                                const double efield[3], void* stream, float* forces, float* bec, double* energies,
                                double* pdot);
 
-/* Synchronize the stream and return the device-side status of the last call. */
+/* Synchronize the stream and return the device-side status of the last call:
+ * the status word its kernels wrote, decoded by qnep_status_from_device_bits. */
 qnep_status qnep_sync_status(qnep_model* m, void* stream);
+
+/* Device status word of a force call (single-structure and batched): bit 0 an atom
+ * had more neighbours than the list capacity, bit 1 a bounded device-side wait on a
+ * bulk copy or a tensor-core operation gave up (the outputs of that call are not
+ * valid), bit 2 a species index outside [0, n_species).  Decoded in that order of
+ * precedence: bit 2 -> QNEP_ERR_ARG, bit 0 -> QNEP_ERR_NBR_OVERFLOW, bit 1 ->
+ * QNEP_ERR_TIMEOUT, none -> QNEP_OK.  A pure host function. */
+qnep_status qnep_status_from_device_bits(unsigned int bits);
+
+/* Test hooks: OR `bits` into the device status word of the model's (or batch's) last
+ * call, as a kernel would, after synchronizing with it; the next qnep_sync_status
+ * (qnep_batch_sync_status) reports them.  They let a test check the decoding of a
+ * device-side timeout without making a device wait run out. */
+qnep_status qnep_debug_set_status(qnep_model* m, unsigned int bits);
 
 /* Change the neighbour-list capacities (entries per atom); 0 keeps the value. */
 qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
@@ -313,6 +331,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
                                const int* types, const double* boxes, void* stream, double* energy,
                                float* forces, float* charges);
 qnep_status qnep_batch_sync_status(qnep_batch* b);
+qnep_status qnep_batch_debug_set_status(qnep_batch* b, unsigned int bits);   /* test hook, as above */
 /* Neighbour capacities (entries per atom; 0 = from the densest structure) and their current values. */
 qnep_status qnep_batch_set_capacity(qnep_batch* b, int cap_list, int cap_angular);
 qnep_status qnep_batch_capacity(const qnep_batch* b, int* cap_list, int* cap_angular);

@@ -87,6 +87,12 @@ def _declare(lib):
     lib.qnep_compute_host.restype = i
     lib.qnep_sync_status.argtypes = [p, p]
     lib.qnep_sync_status.restype = i
+    lib.qnep_status_from_device_bits.argtypes = [ctypes.c_uint]
+    lib.qnep_status_from_device_bits.restype = i
+    lib.qnep_debug_set_status.argtypes = [p, ctypes.c_uint]
+    lib.qnep_debug_set_status.restype = i
+    lib.qnep_batch_debug_set_status.argtypes = [p, ctypes.c_uint]
+    lib.qnep_batch_debug_set_status.restype = i
     lib.qnep_set_path.argtypes = [p, i]
     lib.qnep_set_path.restype = i
     lib.qnep_set_capacity.argtypes = [p, i, i]

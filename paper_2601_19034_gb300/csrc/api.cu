@@ -13,6 +13,7 @@
 #include "../../include/qnep.h"
 #include "qnep_internal.cuh"
 #include "kset_host.h"
+#include "tma.cuh"
 
 using namespace qnep;
 
@@ -461,10 +462,8 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
-            set_num_sms(sms);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
             m->num_sms = sms;
-        }
     }
     CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
@@ -647,11 +646,28 @@ qnep_status qnep_compute_vjp(qnep_model* m, int n, const float* positions, const
     return compute_impl(m, n, positions, types, box, stream, out, vjp);
 }
 
+qnep_status qnep_status_from_device_bits(unsigned int bits) {
+    if (bits & 4u) return QNEP_ERR_ARG;
+    if (bits & 1u) return QNEP_ERR_NBR_OVERFLOW;
+    if (bits & kStatusTimeout) return QNEP_ERR_TIMEOUT;
+    return QNEP_OK;
+}
+
 qnep_status qnep_sync_status(qnep_model* m, void* stream) {
     if (!m) return QNEP_ERR_ARG;
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    unsigned st = *m->h_status;
-    if (st & 1u) return fail(m, QNEP_ERR_NBR_OVERFLOW, "an atom had more neighbours than the list capacity");
+    const qnep_status s = qnep_status_from_device_bits(*m->h_status);
+    if (s == QNEP_ERR_ARG) return fail(m, s, "a species index is outside [0, n_species)");
+    if (s == QNEP_ERR_NBR_OVERFLOW) return fail(m, s, "an atom had more neighbours than the list capacity");
+    if (s == QNEP_ERR_TIMEOUT)
+        return fail(m, s, "a bounded device-side wait gave up (a bulk copy or a tensor-core operation did not complete)");
+    return QNEP_OK;
+}
+
+qnep_status qnep_debug_set_status(qnep_model* m, unsigned int bits) {
+    if (!m) return QNEP_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    *m->h_status |= bits;
     return QNEP_OK;
 }
 

@@ -530,8 +530,21 @@ qnep_status qnep_batch_sync_status(qnep_batch* b) {
     CKB(cudaStreamSynchronize(b->last_stream));
     unsigned int h = 0;
     CKB(cudaMemcpy(&h, b->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost));
-    if (h & 4u) return failb(b, QNEP_ERR_ARG, "a species index is outside [0, n_species)");
-    if (h & 1u) return failb(b, QNEP_ERR_NBR_OVERFLOW, "neighbour list capacity exceeded");
+    const qnep_status s = qnep_status_from_device_bits(h);
+    if (s == QNEP_ERR_ARG) return failb(b, s, "a species index is outside [0, n_species)");
+    if (s == QNEP_ERR_NBR_OVERFLOW) return failb(b, s, "neighbour list capacity exceeded");
+    if (s == QNEP_ERR_TIMEOUT)
+        return failb(b, s, "a bounded device-side wait gave up (a bulk copy or a tensor-core operation did not complete)");
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_debug_set_status(qnep_batch* b, unsigned int bits) {
+    if (!b || !b->d_status) return QNEP_ERR_ARG;
+    CKB(cudaDeviceSynchronize());
+    unsigned int h = 0;
+    CKB(cudaMemcpy(&h, b->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    h |= bits;
+    CKB(cudaMemcpy(b->d_status, &h, sizeof(unsigned int), cudaMemcpyHostToDevice));
     return QNEP_OK;
 }
 

@@ -1282,15 +1282,9 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
     if (n_struct <= 0) return;
     const size_t sm1 = sizeof(int) * ((size_t)nmax + BATCH_MAX_CELLS + 1 + MAX_SPECIES + 1);
     const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a + 32 * TAB_P + 16);
-    static size_t attr1 = 0, attr2 = 0;
-    if (sm1 > 48 * 1024 && sm1 > attr1) {
-        cudaFuncSetAttribute(k_batch_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-        attr1 = sm1;
-    }
-    if (sm2 > 48 * 1024 && sm2 > attr2) {
-        cudaFuncSetAttribute(k_batch_lists, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-        attr2 = sm2;
-    }
+    static std::atomic<int> attr1[kMaxDevices], attr2[kMaxDevices];
+    if (sm1 > 48 * 1024) ensure_smem_attr(k_batch_sort, attr1, (int)sm1);
+    if (sm2 > 48 * 1024) ensure_smem_attr(k_batch_lists, attr2, (int)sm2);
     k_batch_sort<<<n_struct, PREP_THREADS, sm1, st_>>>(pos, types, nmax, n_species, st, cell_start, spos4, sidx,
                                                         order, spec_off, status);
     // about one warp per 32 atoms of the largest structure

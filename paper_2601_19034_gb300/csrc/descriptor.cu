@@ -484,11 +484,8 @@ void bwd_launch(const float4* pos4, const int* nl, const int* cl, const int* na,
     const int threads = 128;
     long long blocks = ((long long)n * TPA + threads - 1) / threads;
     size_t smem = sizeof(float) * (((lay.total + 3) & ~3) + (threads / TPA) * PHI_STRIDE);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_desc_bwd<TPA, BEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_desc_bwd<TPA, BEC>, attr, 200 * 1024);
     k_desc_bwd<TPA, BEC><<<(unsigned)blocks, threads, smem, st>>>(pos4, nl, cl, na, ca, n, g, params, lay, ang, du, dq,
                                                                   q_raw, fin, acc_in, acc12, acc);
 }

@@ -23,7 +23,6 @@ namespace qnep {
 namespace {
 
 constexpr int CW = 8;            // warps per block
-int g_num_sms = 152;             // refreshed from the device at model creation
 constexpr int GY_STRIDE = 29;    // g_n (5) + Y_lm (24) of one angular neighbour
 
 __host__ __device__ inline int coop_fwd_warp_floats(int cap_l, int cap_a) {
@@ -527,11 +526,16 @@ __global__ void __launch_bounds__(32 * CW, BEC ? 2 : 3) k_desc_bwd_coop(
 
 }  // namespace
 
-void set_num_sms(int n) {
-    if (n > 0) g_num_sms = n;
+int num_sms() {
+    static std::atomic<int> cache[kMaxDevices];
+    const int d = device_slot();
+    int v = cache[d].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v < 1) v = 1;
+        cache[d].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
-
-int num_sms() { return g_num_sms; }
 
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a) {
     return sizeof(float) * ((size_t)round4(lay.total) + (size_t)CW * coop_fwd_warp_floats(cap_l, cap_a));
@@ -543,16 +547,13 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
                           float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
                           const float* gq, Accum* acc, cudaStream_t st, float* dtc) {
     if (n == 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_nbr_desc_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_nbr_desc_coop, attr, 220 * 1024);
     const size_t smem = coop_forward_smem(lay, cap_l, cap_a);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nbr_desc_coop, 32 * CW, smem);
+    static std::atomic<long long> occ[kMaxDevices];
+    const int per_sm = cached_occupancy(k_nbr_desc_coop, occ, 32 * CW, smem);
     int blocks = (n + CW - 1) / CW;
-    if (per_sm > 0 && blocks > per_sm * g_num_sms) blocks = per_sm * g_num_sms;
+    if (blocks > per_sm * num_sms()) blocks = per_sm * num_sms();
     k_nbr_desc_coop<<<blocks, 32 * CW, smem, st>>>(
         spos4, cell_start, sidx, n, g, params, lay, cap_l, cap_a, nbr_list, cnt_list, nbr_ang, cnt_ang, ang_coef, du,
         dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc, dtc);
@@ -566,17 +567,18 @@ void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* c
     if (n == 0) return;
     size_t smem = sizeof(float) * ((size_t)round4(lay.total) + (size_t)CW * BW_WARP);
     float4* a4 = reinterpret_cast<float4*>(acc12);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_desc_bwd_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        cudaFuncSetAttribute(k_desc_bwd_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr = true;
+    static std::atomic<int> attr_t[kMaxDevices], attr_f[kMaxDevices];
+    static std::atomic<long long> occ_t[kMaxDevices], occ_f[kMaxDevices];
+    int per_sm;
+    if (want_bec) {
+        ensure_smem_attr(k_desc_bwd_coop<true>, attr_t, 100 * 1024);
+        per_sm = cached_occupancy(k_desc_bwd_coop<true>, occ_t, 32 * CW, smem);
+    } else {
+        ensure_smem_attr(k_desc_bwd_coop<false>, attr_f, 100 * 1024);
+        per_sm = cached_occupancy(k_desc_bwd_coop<false>, occ_f, 32 * CW, smem);
     }
-    int per_sm = 0;
-    if (want_bec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_desc_bwd_coop<true>, 32 * CW, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_desc_bwd_coop<false>, 32 * CW, smem);
     int blocks = (n + CW - 1) / CW;
-    if (per_sm > 0 && blocks > per_sm * g_num_sms) blocks = per_sm * g_num_sms;
+    if (blocks > per_sm * num_sms()) blocks = per_sm * num_sms();
     if (want_bec)
         k_desc_bwd_coop<true><<<blocks, 32 * CW, smem, st>>>(spos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n,
                                                                        g, params, lay, ang_coef, du, dq, q_raw, fin,

@@ -267,27 +267,14 @@ static size_t sk_smem(const EwaldTab& tab) {
     return std::max(ring, red);
 }
 
-static void sk_attr() {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(k_sk, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        done = true;
-    }
-}
-
 static void sk_grid(int n, const EwaldTab& tab, int& gx, int& gy, int& span) {
-    sk_attr();
-    // resident blocks per SM for this shared-memory size (queried once per size)
-    static size_t last_smem = 0;
-    static int sms = 152, per_sm = 1;
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_sk, attr, 160 * 1024);
+    // resident blocks per SM for this shared-memory size (queried once per size and device)
+    static std::atomic<long long> occ[kMaxDevices];
     const size_t smem = sk_smem(tab);
-    if (smem != last_smem) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sk, 32 * SK_WARPS, smem);
-        last_smem = smem;
-    }
+    const int per_sm = cached_occupancy(k_sk, occ, 32 * SK_WARPS, smem);
+    const int sms = num_sms();
     gx = (tab.nchunk + 31) / 32;
     const int want = std::max(1, sms * std::max(per_sm, 1) / gx);
     span = (n + want - 1) / want;

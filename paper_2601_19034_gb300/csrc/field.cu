@@ -508,11 +508,8 @@ void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, c
     if (n == 0) return;
     constexpr int W = 32;
     size_t smem = ewald ? sizeof(float2) * 32 * tab.nph : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_field<W>, attr, 160 * 1024);
     k_field<W><<<(n + 31) / 32, 32 * W, smem, st>>>(pos4, pos_in, q_raw, nbr_list, cnt_list, n, n_species, g, ec,
                                                     q_target, sqrt_eps, ewald ? 1 : 0, tab, pppm_field, phi,
                                                     reinterpret_cast<float4*>(acc12), charges_out, sidx, acc);
@@ -523,11 +520,8 @@ void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, c
                  Accum* acc, cudaStream_t st) {
     if (n == 0) return;
     // persistent warps: one wave of resident blocks, fewer for small systems
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_real, 256, 0);
-        per_sm = std::max(per_sm, 1);
-    }
+    static std::atomic<long long> occ[kMaxDevices];
+    const int per_sm = cached_occupancy(k_real, occ, 256, 0);
     const int blocks = std::max(1, std::min((n + 7) / 8, per_sm * num_sms()));
     k_real<<<blocks, 256, 0, st>>>(spos4, q_raw, nbr_list, cnt_list, n, n_species, g, alpha, q_target, acc_in, rfield,
                                    acc);
@@ -536,25 +530,14 @@ void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, c
 void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st) {
     if (n == 0 || tab.ncol == 0) return;
     constexpr int W = 8;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_field_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_field_k<W>, attr, 160 * 1024);
     const int groups = (n + 31) / 32;
     const size_t smem = sizeof(float2) * 32 * tab.nph;
     // column splits: fill the resident block slots (SMs x blocks per SM at this shared-memory
     // size) in one wave; a partial second wave would double the time of the SMs running it
-    static size_t last_smem = 0;
-    static int slots = 152 * 8;
-    if (smem != last_smem) {
-        int dev = 0, sms = 152, per_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_field_k<W>, 32 * W, smem);
-        slots = sms * std::max(per_sm, 1);
-        last_smem = smem;
-    }
+    static std::atomic<long long> occ[kMaxDevices];
+    const int slots = num_sms() * cached_occupancy(k_field_k<W>, occ, 32 * W, smem);
     int csplit = slots / groups;
     if (csplit < 1) csplit = 1;
     if (csplit > tab.ncol) csplit = tab.ncol;

@@ -280,11 +280,8 @@ void launch_neighbors(const float4* spos4, const int* cell_start, int n, int n_s
     if (n == 0) return;
     const int threads = 128;
     size_t smem = sizeof(int) * (threads / 32) * (cap_list + cap_ang) * 2;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    static std::atomic<int> attr[kMaxDevices];
+    ensure_smem_attr(k_neighbors, attr, 200 * 1024);
     long long blocks = ((long long)n * 32 + threads - 1) / threads;
     k_neighbors<<<(unsigned)blocks, threads, smem, st>>>(spos4, cell_start, n, n_species, g, cap_list, cap_ang,
                                                         nbr_list, cnt_list, nbr_ang, cnt_ang, acc);

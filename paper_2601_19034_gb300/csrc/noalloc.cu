@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/qnep.h"
+#include "kset_host.h"
 #include "qnep_internal.cuh"
 
 namespace qnep {
@@ -129,40 +130,38 @@ extern "C" qnep_status qnep_ewald_kspace_noalloc(int n, const float* positions, 
     }
     const double L[3] = {box[0], box[4], box[8]};
     const double two_pi = 6.283185307179586;
-    int nmax[3];
-    for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(kmax * L[d] / two_pi);
-
-    // half-space k columns (n1, n2) with runs of n3 in chunks of 8 (the layout of EwaldTab)
-    std::vector<int4> cols;
-    std::vector<int> chunk_col;
-    std::vector<float> kg;
-    const double vol = L[0] * L[1] * L[2];
-    for (int n1 = 0; n1 <= nmax[0]; ++n1)
-        for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2) {
-            if (n1 == 0 && n2 < 0) continue;
-            const double kx = two_pi * n1 / L[0], ky = two_pi * n2 / L[1];
-            int lo = 1 << 30, hi = -(1 << 30);
-            for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
-                if (n1 == 0 && n2 == 0 && n3 <= 0) continue;
-                const double kz = two_pi * n3 / L[2], k2 = kx * kx + ky * ky + kz * kz;
-                if (k2 > 0 && k2 < kmax * kmax) {
-                    lo = n3 < lo ? n3 : lo;
-                    hi = n3 > hi ? n3 : hi;
-                }
-            }
-            if (hi < lo) continue;
-            const int nch = (hi - lo + 8) / 8;
-            cols.push_back(make_int4(n1, n2, lo, (int)kg.size()));
-            for (int h = 0; h < nch; ++h) chunk_col.push_back((int)cols.size() - 1);
-            for (int t = 0; t < 8 * nch; ++t) {
-                const int n3 = lo + t;
-                const double kz = two_pi * n3 / L[2], k2 = kx * kx + ky * ky + kz * kz;
-                const bool ok = n3 <= hi && k2 > 0 && k2 < kmax * kmax;
-                kg.push_back(ok ? (float)(two_pi / vol * std::exp(-k2 / (4 * alpha * alpha)) / k2) : 0.f);
-            }
+    // Bound the k-set before enumerating it: n_max of each axis fixes the phase factors per atom,
+    // so a k_max * L that would overflow an int, or loop for long, is refused here.
+    long long nm[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = std::floor(kmax * L[d] / two_pi);
+        if (!(x < (double)kMaxPhase)) {
+            put_err(err, err_len,
+                    "k_max * box edge too large for the fixed scratch array (QNEP_NOALLOC_MAX_PHASE / _KPAD)");
+            return QNEP_ERR_UNSUPPORTED;
         }
-    const int ncol = (int)cols.size();
-    cols.push_back(make_int4(0, 0, 0, (int)kg.size()));
+        nm[d] = (long long)x;
+    }
+    long long nph = (nm[0] + 1) + (2 * nm[1] + 1) + (2 * nm[2] + 8);
+    if ((nph & 1) == 0) nph += 1;
+    if ((size_t)nph > kMaxPhase) {
+        put_err(err, err_len, "k_max * box edge too large for the fixed scratch array (QNEP_NOALLOC_MAX_PHASE / _KPAD)");
+        return QNEP_ERR_UNSUPPORTED;
+    }
+    // the half-space k columns and their 8-wide chunks, as for qnep_compute (at most
+    // 128^3 / 2 candidate triples once n_max is bounded)
+    KSet ks;
+    try {
+        ks = build_kset(L, kmax, alpha);
+    } catch (...) {
+        put_err(err, err_len, "host memory for the k-set could not be obtained");
+        return QNEP_ERR_OOM;
+    }
+    const std::vector<int4>& cols = ks.cols;
+    const std::vector<int>& chunk_col = ks.chunk_col;
+    const std::vector<float>& kg = ks.kg;
+    const int* nmax = ks.nmax;
+    const int ncol = (int)cols.size() - 1;
     EwaldTab t{};
     t.n1max = nmax[0];
     t.n2max = nmax[1];

@@ -279,15 +279,10 @@ int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc
     const int threads = 256;
     // persistent warps over the atoms and persistent threads over the half spectrum: one
     // wave of resident blocks (occupancy queried once per kernel)
-    static int occ_spread = 0, occ_green = 0, occ_gather = 0;
-    if (occ_spread == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_spread, k_pppm_spread, threads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_green, k_pppm_green, threads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_gather, k_pppm_gather, threads, 0);
-        occ_spread = std::max(occ_spread, 1);
-        occ_green = std::max(occ_green, 1);
-        occ_gather = std::max(occ_gather, 1);
-    }
+    static std::atomic<long long> c_spread[kMaxDevices], c_green[kMaxDevices], c_gather[kMaxDevices];
+    const int occ_spread = cached_occupancy(k_pppm_spread, c_spread, threads, 0);
+    const int occ_green = cached_occupancy(k_pppm_green, c_green, threads, 0);
+    const int occ_gather = cached_occupancy(k_pppm_gather, c_gather, threads, 0);
     const long long atom_blocks = ((long long)n * 32 + threads - 1) / threads;
     const unsigned sblocks = (unsigned)std::min<long long>(atom_blocks, (long long)occ_spread * num_sms());
     const unsigned hblocks = (unsigned)std::min<long long>(atom_blocks, (long long)occ_gather * num_sms());

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace qnep {
 
 // Descriptor / network shape supported by the kernels of this library.
@@ -184,8 +186,41 @@ void launch_descriptor_forward(const float4* pos4, const int* nbr_list, const in
                                const int* sidx, float4* fields, const float* gq, Accum* acc, cudaStream_t st,
                                float* dtc = nullptr);
 size_t coop_forward_smem(const ParamLayout& lay, int cap_l, int cap_a);
-void set_num_sms(int n);
-int num_sms();   // SMs of the device (persistent grids)
+// Launch caches are kept per device ordinal: a kernel's dynamic shared-memory limit
+// (cudaFuncSetAttribute) and the occupancy and SM-count answers hold for one device only.
+// Host threads may race on a slot only to repeat the same idempotent query.
+constexpr int kMaxDevices = 64;
+inline int device_slot() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+    return d;
+}
+// Raise `kernel`'s dynamic shared-memory limit on the current device to `bytes` (once per
+// device and value; `cache` is a zero-initialised static [kMaxDevices] of the call site).
+template <class K>
+inline void ensure_smem_attr(K kernel, std::atomic<int>* cache, int bytes) {
+    const int d = device_slot();
+    if (cache[d].load(std::memory_order_relaxed) >= bytes) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cache[d].store(bytes, std::memory_order_relaxed);
+}
+// Resident blocks per SM of `kernel` at (threads, smem) on the current device, cached per
+// device for the last shared-memory size asked (at least 1).
+template <class K>
+inline int cached_occupancy(K kernel, std::atomic<long long>* cache, int threads, size_t smem) {
+    const int d = device_slot();
+    // the slot holds ((smem, threads) key << 8) | blocks per SM
+    const long long key = (long long)smem * 4096 + threads;
+    long long v = cache[d].load(std::memory_order_relaxed);
+    if (v > 0 && (v >> 8) == key) return (int)(v & 255);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (per_sm > 255) per_sm = 255;
+    cache[d].store((key << 8) | per_sm, std::memory_order_relaxed);
+    return per_sm;
+}
+int num_sms();   // SMs of the current device (persistent grids), queried once per device
 void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int* sidx, int n, const Geom& g,
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,

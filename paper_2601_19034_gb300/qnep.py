@@ -343,6 +343,14 @@ class QNEPFunction(torch.autograd.Function):
     weights (qnep_compute_vjp): g_E dU/dr + sum g_q dq^c/dr + g_P . Z, where the
     polarization derivative is the periodic Born effective charge of Eq. bec_2.
     No per-pair derivative is stored between the two calls.
+
+    The P output and its gradient differ by design in a periodic box: forward
+    returns P = sum_i q~^c_i r_i with the positions as given (Eq. polarization),
+    while backward uses Z of Eq. bec_2, the periodic definition of dP/dr, which
+    is not the derivative of that sum (it leaves out the dependence on where the
+    atoms sit relative to the box).  So torch.autograd.gradcheck on the P output
+    fails by construction; the energy and charge outputs are exact derivatives
+    of what forward returns.  For an isolated cluster use the cluster form.
     """
 
     @staticmethod

@@ -86,3 +86,35 @@ def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
     assert lib.qnep_batch_set_params(None, dummy, None) == _lib.QNEP_ERR_ARG
     assert lib.qnep_nve_run_field(None, 4, dummy, dummy, dummy, dummy, dummy, 0.5, 1, e, None, dummy, dummy,
                                   dummy, dummy) == _lib.QNEP_ERR_ARG
+
+
+def test_device_status_bits_decode(lib):
+    """The status word the kernels write maps to the documented codes (bit 1: a bounded wait gave up)."""
+    f = lib.qnep_status_from_device_bits
+    f.argtypes = [ctypes.c_uint]
+    assert f(0) == _lib.QNEP_OK
+    assert f(1) == _lib.QNEP_ERR_NBR_OVERFLOW
+    assert f(2) == _lib.QNEP_ERR_TIMEOUT
+    assert f(4) == _lib.QNEP_ERR_ARG
+    assert f(3) == _lib.QNEP_ERR_NBR_OVERFLOW     # precedence: species, overflow, timeout
+    assert f(6) == _lib.QNEP_ERR_ARG
+    assert f(8) == _lib.QNEP_OK                    # undefined bits are ignored
+
+
+def test_noalloc_refuses_oversized_k_set_before_any_gpu_work(lib):
+    """A huge k_max * L is refused from the arguments alone (no enumeration, no CUDA call)."""
+    fn = lib.qnep_ewald_kspace_noalloc
+    p = ctypes.c_void_p
+    fn.argtypes = [ctypes.c_int, p, p, p, ctypes.c_double, ctypes.c_double, p, p, p, p, ctypes.c_char_p,
+                   ctypes.c_size_t]
+    dummy = ctypes.c_void_p(0x1000)       # never dereferenced: every call below returns before using it
+    box = (ctypes.c_double * 9)(10.0, 0, 0, 0, 10.0, 0, 0, 0, 10.0)
+    err = ctypes.create_string_buffer(256)
+    for kmax in (1e3, 1e12, 1e300):
+        assert fn(16, dummy, dummy, box, 0.3, kmax, None, None, None, None, err, len(err)) == _lib.QNEP_ERR_UNSUPPORTED
+        assert b"QNEP_NOALLOC_MAX_PHASE" in err.value
+    # n_max = 40 per axis: 41 + 81 + 88 = 210 phase factors > 128
+    assert fn(16, dummy, dummy, box, 0.3, 2 * np.pi * 40.5 / 10.0, None, None, None, None, err,
+              len(err)) == _lib.QNEP_ERR_UNSUPPORTED
+    assert fn(16, dummy, dummy, box, 0.3, float("inf"), None, None, None, None, err, len(err)) == _lib.QNEP_ERR_ARG
+    assert fn(8193, dummy, dummy, box, 0.3, 2.0, None, None, None, None, err, len(err)) == _lib.QNEP_ERR_UNSUPPORTED

@@ -6,6 +6,8 @@ where cudaMalloc would synchronise the device).  This test calls it through the
 C ABI twice in a row on the charges and positions of a mode-2 Ewald force call
 (mode 2 has no real-space or self term, so the existing entry point's potential
 is exactly the reciprocal-space potential) and compares potential and energy
+with it, and potential, energy, forces and the 3x3 static virial element by
+element with the FP64 oracle's reciprocal-space Ewald sum of the same charges,
 with the tolerances of the parity tests.  The file is named so that pytest
 collects it last; it also runs alone in a fresh process.
 """
@@ -48,6 +50,11 @@ def test_noalloc_matches_qnep_compute_twice():
     torch.cuda.synchronize()
     ref_sc = parse_scalars(ref["scalars"])
     n = sysm.n_atoms
+    # the oracle's reciprocal-space sum (mode 2: U^k only) of the same charges and positions
+    from oracle import ewald as oewald
+    q64 = ref["charges"].double().cpu().numpy()
+    ora = oewald.ewald_static(sysm.positions.astype(np.float64), np.asarray(sysm.box, np.float64), q64, None, elec,
+                              with_kspace=True)
     box = (ctypes.c_double * 9)(*np.asarray(sysm.box, np.float64).ravel())
     err = ctypes.create_string_buffer(256)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -61,8 +68,12 @@ def test_noalloc_matches_qnep_compute_twice():
         torch.cuda.synchronize()
         assert abs(ev[0].item() - ref_sc["e_kspace"]) / n <= 1e-6
         assert (phi - ref["potential"]).abs().max().item() <= 2e-5
-        assert torch.isfinite(force).all()
-        assert abs(force.double().sum(0)).max().item() < 1e-3
+        evh = ev.cpu().numpy()
+        assert abs(evh[0] - ora["e_kspace"]) / n <= 1e-6
+        phih = phi.double().cpu().numpy()
+        assert np.abs(phih - ora["phi"]).max() <= 1e-5 * np.abs(ora["phi"]).max()
+        assert np.abs(force.double().cpu().numpy() - ora["force"]).max() <= 1e-4
+        assert np.abs(evh[1:10].reshape(3, 3) - ora["virial"]).max() / n <= 1e-5
     # sizes beyond the fixed array are refused before any GPU work, with a message
     big = torch.zeros((8193, 3), dtype=torch.float32, device=dev)
     q = torch.zeros(8193, dtype=torch.float32, device=dev)
