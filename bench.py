@@ -161,10 +161,10 @@ def _ewald_kcount(box, kmax):
 
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
-# capture of the current kernel on the first 160 structures x 64 candidates (17.36 GB for
-# 6.71e6 atom-evaluations; the traffic grows with the atom-evaluations).  Set to None when the
-# item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = 17.36e9 / 6.71e6
+# capture of the current kernel (tensor-core contraction) on the first 160 structures x 64
+# candidates (10.258 GB read + 7.221 GB written for 6,709,248 atom-evaluations; the traffic grows
+# with the atom-evaluations).  Set to None when the item kernel changes until it is captured again.
+ITEM_DRAM_BYTES_PER_EVAL = (10.258313e9 + 7.221287e9) / 6709248
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
                     "first 160 structures x 64 candidates, scaled by atom-evaluations")
 
@@ -614,6 +614,68 @@ def _time_snes_step(b, graph, stream, out, off, params, dev, reps):
                     "+ qnep_batch_loss + qnep_snes_update, CUDA events on the call's stream, median"}
 
 
+def _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, flush, contract, steps, evals):
+    """The same batched call with the other descriptor contraction (graph replay, L2 flushed)."""
+    import torch
+    from paper_2601_19034_gb300.qnep import QNEPBatch
+    b2 = QNEPBatch(hp, params, elec)
+    b2.set_contraction(contract)
+    b2.set_config(8, "largest_first")
+    out2 = b2.compute(pos_d, typ_d, off, boxes)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b2.compute_into(pos_d, typ_d, off, boxes, out2, stream=stream.cuda_stream)
+    stream.synchronize()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=stream):
+        b2.compute_into(pos_d, typ_d, off, boxes, out2, stream=stream.cuda_stream)
+    ts = []
+    for k in range(steps + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            g2.replay()
+            e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            ts.append(e0.elapsed_time(e1))
+    b2.set_profiling(True)
+    for _ in range(4):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            b2.compute_into(pos_d, typ_d, off, boxes, out2, stream=stream.cuda_stream)
+    st2, calls2 = b2.stage_times()
+    b2.close()
+    ms = float(np.median(ts))
+    return {"contraction": contract, "ms_per_step": ms, "value": evals / (ms * 1e-3), "unit": UNIT,
+            "item_kernel_ms": st2["items"] / max(calls2, 1),
+            "what": "same batch, warps 8, largest first, CUDA graph replay, L2 flushed, median"}
+
+
+def _tensor_roofline(systems, hp, n_cand, item_ms, peaks):
+    """Tensor-pipe share of the batched item kernel: the BF16x3 angular descriptor contraction.
+
+    Useful work per (atom, candidate): A_{n,lm} = sum over 9 S (s, k) terms for 5 n x 24 lm,
+    2 flop each, three BF16 products (hi.hi, hi.lo, lo.hi); issued work adds the padding of the
+    MMA shapes (M 256 rows for 160 (n, candidate) rows per 32 candidates, K 48 for 9 S, N 128 for
+    120 (atom, lm) columns per 5-atom tile).
+    """
+    S = hp.n_species
+    atoms = sum(sy.n_atoms for sy in systems)
+    useful = 3 * 2 * 5 * 24 * 9 * S * atoms * n_cand
+    groups = (n_cand + 31) // 32
+    issued = 3 * 2 * 256 * 48 * (128 / 5.0) * atoms * groups
+    peak = peaks["bf16_tflops"]
+    ach = useful / (item_ms * 1e-3) / 1e12
+    return {"kernel": "k_batch_items (tcgen05.mma kind::f16, BF16x3 descriptor contraction)", "bound": "tensor",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "work": f"{useful:.4g} useful / {issued:.4g} issued tensor flop per launch (BF16x3, 3 products)",
+            "note": "averaged over the whole item kernel; the contraction is one phase of it (the kernel as a "
+                    "whole is bound by the FP32 pipes, see roofline)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16)"}
+
+
 def run_batch(args):
     """Batched form: every (candidate, structure) pair of the LLZO batch in one persistent launch."""
     import torch
@@ -641,6 +703,7 @@ def run_batch(args):
     n_total = int(off[-1])
     pos_d, typ_d = torch.tensor(pos, device=dev), torch.tensor(typ, device=dev)
     b = QNEPBatch(hp, params, elec)
+    b.set_contraction(args.contract)
     out = b.compute(pos_d, typ_d, off, boxes)          # lists sized, status checked
     tune_ms = b.autotune(pos_d, typ_d, off, boxes, reps=2, out=out)
     warps, order = b.config()
@@ -698,6 +761,8 @@ def run_batch(args):
     b.set_profiling(False)
     item_ms = stage["items"] / max(calls, 1)
     prep_ms = stage["prepass"] / max(calls, 1)
+    other = _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, flush,
+                                    "fp32" if args.contract == "bf16x3" else "bf16x3", min(args.steps, 10), evals)
 
     # external-field response from the Born effective charges (Sec. II.D), its own HBM roofline
     field_roof, _ = _time_field_response(dev, flush, peaks, min(args.steps, 20))
@@ -765,16 +830,21 @@ def run_batch(args):
                        "l2": "flushed between steps (512 MB write); working set > L2",
                        "launch": "CUDA graph replay of one qnep_batch_compute (pre-pass + persistent item kernel)",
                        "autotuned": {"warps": warps, "order": order, "ms": tune_ms},
+                       "contraction": args.contract,
                        "parallelism": f"{world} ranks, one batch each (no data-path collective)" if world > 1
                        else "single GPU", "wall_s": wall},
             "roofline": {"kernel": "k_batch_items", "bound": "alu", "achieved": flop / (item_ms * 1e-3) / 1e12,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": flop / (item_ms * 1e-3) / 1e12 / fp32_peak,
-                         "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals if ITEM_DRAM_BYTES_PER_EVAL else None,
+                         "traffic": ITEM_DRAM_BYTES_PER_EVAL * evals
+                         if (ITEM_DRAM_BYTES_PER_EVAL and args.contract == "bf16x3") else None,
                          "traffic_unit": "bytes per launch",
                          "traffic_source": ITEM_DRAM_SOURCE, "ms": item_ms, "prepass_ms": prep_ms,
                          "peak_source": peak_src,
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
                          "whole_call_frac": achieved / fp32_peak},
+            "roofline_tensor": _tensor_roofline(systems, hp, n_cand, item_ms, peaks) if args.contract == "bf16x3"
+            else None,
+            "contraction_compare": other,
             "mixed": mixed,
             "field_response": field_roof,
             "snes_step": dict(snes, batched_call_ms=ms_per_step),
@@ -979,6 +1049,8 @@ def main():
     ap.add_argument("--workload", default="llzo_batch", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32"],
                     help="single-structure workloads: network precision")
+    ap.add_argument("--contract", default="bf16x3", choices=["fp32", "bf16x3"],
+                    help="llzo_batch: descriptor contraction on the FP32 pipes or on the tensor cores (BF16x3)")
     ap.add_argument("--structures", type=int, default=0, help="llzo_batch: first N structures only (profiling)")
     ap.add_argument("--candidates", type=int, default=0, help="llzo_batch: first C candidates only (profiling)")
     ap.add_argument("--mg-cells", default="", help="mgwater_nve: NX,NY orthohexagonal cells instead of 112,65 "

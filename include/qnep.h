@@ -339,6 +339,17 @@ qnep_status qnep_batch_capacity(const qnep_batch* b, int* cap_list, int* cap_ang
  * in which blocks take the (structure, candidate-group) items. */
 qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order);
 qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
+/* Descriptor contraction of the batched call: the angular expansion coefficients
+ * A_{n,lm} = sum_{s,k} c^A[t_i][s][n][k] B^A[s][k][lm] of every atom and candidate (Sec. II.A)
+ * in FP32 on the FP32 pipes (QNEP_BATCH_CONTRACT_FP32, the default), or on the tensor cores
+ * (QNEP_BATCH_CONTRACT_BF16X3: each operand split into BF16 hi + lo parts, three products
+ * hi.hi + hi.lo + lo.hi accumulated in FP32, about 2^-16 relative error per term; the energy
+ * stays within the FP32 path's 1e-6 eV/atom of the FP64 oracle).  The tensor-core form runs
+ * 8-warp blocks (it sets warps = 8; qnep_batch_set_config(4, ...) then makes the next call
+ * return QNEP_ERR_UNSUPPORTED).  Everything after the contraction is the same in both. */
+enum { QNEP_BATCH_CONTRACT_FP32 = 0, QNEP_BATCH_CONTRACT_BF16X3 = 1 };
+qnep_status qnep_batch_set_contraction(qnep_batch* b, int contract);
+qnep_status qnep_batch_get_contraction(const qnep_batch* b, int* contract);
 /* Autotuner: times every launch configuration on this batch (`reps` calls each,
  * median, CUDA events on `stream`), keeps the fastest and returns its time (ms).
  * Writes the same outputs as qnep_batch_compute. Synchronizes the stream. */

@@ -19,6 +19,8 @@ QNEP_ERR_NBR_OVERFLOW = 3
 QNEP_ERR_UNSUPPORTED = 4
 QNEP_ERR_TIMEOUT = 5
 QNEP_ERR_OOM = 6
+QNEP_BATCH_CONTRACT_FP32 = 0
+QNEP_BATCH_CONTRACT_BF16X3 = 1
 QNEP_EWALD = 0
 QNEP_PPPM = 1
 QNEP_PREC_FP32 = 0
@@ -121,6 +123,10 @@ def _declare(lib):
     lib.qnep_batch_create.restype = i
     lib.qnep_batch_compute.argtypes = [p, i, p, p, p, p, p, p, p, p]
     lib.qnep_batch_compute.restype = i
+    lib.qnep_batch_set_contraction.argtypes = [p, i]
+    lib.qnep_batch_set_contraction.restype = i
+    lib.qnep_batch_get_contraction.argtypes = [p, ctypes.POINTER(i)]
+    lib.qnep_batch_get_contraction.restype = i
     lib.qnep_batch_sync_status.argtypes = [p]
     lib.qnep_batch_sync_status.restype = i
     lib.qnep_batch_set_capacity.argtypes = [p, i, i]

@@ -15,6 +15,10 @@
 
 using namespace qnep;
 
+static_assert((int)QNEP_BATCH_CONTRACT_FP32 == (int)BATCH_CONTRACT_FP32 &&
+                  (int)QNEP_BATCH_CONTRACT_BF16X3 == (int)BATCH_CONTRACT_BF16X3,
+              "contraction codes of the C ABI and of the kernels agree");
+
 struct qnep_batch {
     qnep_hparams hp{};
     qnep_elec es{};
@@ -24,6 +28,7 @@ struct qnep_batch {
     int cap_l_user = 0, cap_a_user = 0;
     int warps = 8;                          // warps per block of the item kernel (4 or 8)
     int order_policy = QNEP_BATCH_ORDER_LARGEST_FIRST;
+    int contract = QNEP_BATCH_CONTRACT_FP32;   // descriptor contraction: FP32 FMAs or tensor cores
     int num_sms = 152;
     // batch description (rebuilt when the structures or boxes change)
     bool have_desc = false;
@@ -44,7 +49,7 @@ struct qnep_batch {
     // pre-pass outputs (element counts allocated)
     struct {
         size_t spos4 = 0, sidx = 0, order = 0, spec = 0, cells = 0, list = 0, ang = 0, cnt_list = 0, cnt_ang = 0,
-               phase = 0, geo_rad = 0, geo_ang = 0, bsum = 0;
+               phase = 0, geo_rad = 0, geo_ang = 0, bsum = 0, bimg = 0;
     } alloc;
     float4* spos4 = nullptr;
     int* sidx = nullptr;
@@ -59,6 +64,7 @@ struct qnep_batch {
     float* geo_rad = nullptr;
     float* geo_ang = nullptr;
     float* bsum = nullptr;
+    unsigned char* bimg = nullptr;          // B^A operand images (tensor-core contraction only)
     // per-slot scratch
     size_t slot_bytes_alloc = 0;
     int slots_alloc = 0;
@@ -67,7 +73,7 @@ struct qnep_batch {
     unsigned int* d_work = nullptr;
     unsigned int* d_status = nullptr;
     cudaStream_t last_stream = nullptr;
-    std::map<std::pair<int, int>, int> per_sm_cache;   // (warps, nph_max) -> resident blocks per SM
+    std::map<std::tuple<int, int, int>, int> per_sm_cache;   // (warps, nph_max, contract) -> blocks per SM
     // stage timers: events around the pre-pass and the item kernel of each profiled call
     bool profiling = false, pending = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -268,6 +274,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(regrow(&b->geo_rad, N * (size_t)cl * BATCH_GR, &b->alloc.geo_rad));
     CKB(regrow(&b->geo_ang, N * (size_t)ca * BATCH_GA, &b->alloc.geo_ang));
     CKB(regrow(&b->bsum, N * (size_t)batch_bstride(b->hp.n_species), &b->alloc.bsum));
+    if (b->contract == QNEP_BATCH_CONTRACT_BF16X3) CKB(regrow(&b->bimg, N * (size_t)BIMG_BYTES, &b->alloc.bimg));
     b->h_off.assign(off, off + n_struct + 1);
     b->h_box.assign(boxes, boxes + 9 * (size_t)n_struct);
     b->have_desc = true;
@@ -422,6 +429,19 @@ qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order) {
     return QNEP_OK;
 }
 
+qnep_status qnep_batch_set_contraction(qnep_batch* b, int contract) {
+    if (!b || (contract != QNEP_BATCH_CONTRACT_FP32 && contract != QNEP_BATCH_CONTRACT_BF16X3)) return QNEP_ERR_ARG;
+    b->contract = contract;
+    if (contract == QNEP_BATCH_CONTRACT_BF16X3) b->warps = 8;   // the tensor-core form runs 8 warps
+    return QNEP_OK;
+}
+
+qnep_status qnep_batch_get_contraction(const qnep_batch* b, int* contract) {
+    if (!b || !contract) return QNEP_ERR_ARG;
+    *contract = b->contract;
+    return QNEP_OK;
+}
+
 qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order) {
     if (!b || !warps || !order) return QNEP_ERR_ARG;
     *warps = b->warps;
@@ -447,12 +467,17 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     }
     // blocks per SM of this shape (cached: no CUDA calls beyond launches once the batch is known,
     // so the call can be captured in a graph)
-    const auto key = std::make_pair(b->warps, b->nph_max);
+    const auto key = std::make_tuple(b->warps, b->nph_max, b->contract);
     auto hit = b->per_sm_cache.find(key);
     if (hit == b->per_sm_cache.end())
-        hit = b->per_sm_cache.emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max)).first;
+        hit = b->per_sm_cache.emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max, b->contract)).first;
     const int per_sm = hit->second;
     if (per_sm <= 0) return failb(b, QNEP_ERR_UNSUPPORTED, "item kernel does not fit on an SM");
+    const bool tc = b->contract == QNEP_BATCH_CONTRACT_BF16X3;
+    if (tc && (!b->bimg || b->alloc.bimg < (size_t)b->n_total * BIMG_BYTES)) {
+        CKB(cudaStreamSynchronize(st));
+        CKB(regrow(&b->bimg, (size_t)std::max(b->n_total, 1) * BIMG_BYTES, &b->alloc.bimg));
+    }
     const int slots = per_sm * b->num_sms;
     qnep_status s = ensure_scratch(b, slots, st);
     if (s != QNEP_OK) return s;
@@ -475,7 +500,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
                       b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
                       b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->geo_rad, b->geo_ang, b->bsum,
-                      batch_bstride(b->hp.n_species), (float)b->es.alpha, b->d_status, st);
+                      batch_bstride(b->hp.n_species), tc ? b->bimg : nullptr, (float)b->es.alpha, b->d_status, st);
     BatchArgs a{};
     a.spos4 = b->spos4;
     a.sidx = b->sidx;
@@ -492,6 +517,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.geo_rad = b->geo_rad;
     a.geo_ang = b->geo_ang;
     a.bsum = b->bsum;
+    a.bimg = tc ? b->bimg : nullptr;
     a.bstride = batch_bstride(b->hp.n_species);
     a.st = b->d_st;
     a.kt = b->d_kt;
@@ -515,7 +541,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.n_total = b->n_total;
     a.status = b->d_status;
     if (b->profiling) CKB(cudaEventRecord(b->ev[1], st));
-    launch_batch_items(a, b->warps, b->nph_max, std::min(slots, std::max(b->n_items, 1)), st);
+    launch_batch_items(a, b->warps, b->nph_max, b->contract, std::min(slots, std::max(b->n_items, 1)), st);
     if (b->profiling) {
         CKB(cudaEventRecord(b->ev[2], st));
         b->pending = true;
@@ -651,7 +677,7 @@ void qnep_batch_destroy(qnep_batch* b) {
     void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
-                    b->geo_rad,   b->geo_ang,  b->bsum,
+                    b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,
                     b->d_work,    b->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);

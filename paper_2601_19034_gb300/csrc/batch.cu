@@ -23,9 +23,12 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "batch_internal.cuh"
 #include "desc_math.cuh"
 #include "nbr_common.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace qnep {
@@ -183,8 +186,8 @@ __device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, con
                                               int S, const int* __restrict__ lst, const int* __restrict__ cl,
                                               const int* __restrict__ lsa, const int* __restrict__ ca,
                                               float* __restrict__ grad_rows, float* __restrict__ gang_rows,
-                                              float* __restrict__ bs_out, float* __restrict__ tab,
-                                              int* __restrict__ cum) {
+                                              float* __restrict__ bs_out, unsigned char* __restrict__ bimg,
+                                              float* __restrict__ tab, int* __restrict__ cum) {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
         int tl = 0, ta = 0;
@@ -328,6 +331,32 @@ __device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, con
             if (t < S)
 #pragma unroll
                 for (int k = 0; k < KA; ++k) bs_out[MAX_SPECIES * KR + (t * KA + k) * NLM + lane] = ba[t][k];
+        if (bimg) {
+            // operand image, row lm = lane: K index 9 t + k, BF16 hi and lo (x - hi) planes
+            static_assert(MAX_SPECIES * KA <= BIMG_K, "the (species, k) index fits the padded K");
+#pragma unroll
+            for (int kc = 0; kc < BIMG_K / 8; ++kc) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    float x[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int kidx = 8 * kc + 2 * h + e;
+                        const int t = kidx < MAX_SPECIES * KA ? kidx / KA : 0, k = kidx % KA;
+                        x[e] = kidx < S * KA ? ba[t][k] : 0.f;
+                    }
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(x[0], x[1]);
+                    const __nv_bfloat162 lo =
+                        __floats2bfloat162_rn(x[0] - __bfloat162float(hi.x), x[1] - __bfloat162float(hi.y));
+                    hw[h] = *reinterpret_cast<const uint32_t*>(&hi);
+                    lw[h] = *reinterpret_cast<const uint32_t*>(&lo);
+                }
+                const int o = ((lane >> 3) * (BIMG_K / 8) + kc) * 128 + (lane & 7) * 16;
+                *reinterpret_cast<uint4*>(bimg + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(bimg + BIMG_PLANE + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+        }
     }
     __syncwarp();
 }
@@ -338,7 +367,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
     const int* __restrict__ cell_start_all, const float4* __restrict__ spos4, int cap_l, int cap_a,
     int* __restrict__ nbr_list, int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang,
     float2* __restrict__ phase, int nph_stride, float* __restrict__ geo_rad, float* __restrict__ geo_ang,
-    float* __restrict__ bsum, int bstride, float alpha, unsigned int* __restrict__ status) {
+    float* __restrict__ bsum, int bstride, unsigned char* __restrict__ bimg, float alpha,
+    unsigned int* __restrict__ status) {
     extern __shared__ int psm[];
     const BatchStruct bs = sts[blockIdx.x];
     const int n = bs.n, off = bs.atom_off;
@@ -369,7 +399,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
         __syncwarp();   // this warp's list writes are visible to its lanes
         geometry_atom(sp, g, alpha, m, n, n_species, lst_s + (size_t)m * cap_l, cl_s, lsa_s + (size_t)m * cap_a, ca_s,
                       geo_rad + (size_t)(off + m) * cap_l * GR, geo_ang + (size_t)(off + m) * cap_a * GA,
-                      bsum + (size_t)(off + m) * bstride, tab, cum);
+                      bsum + (size_t)(off + m) * bstride, bimg ? bimg + (size_t)(off + m) * BIMG_BYTES : nullptr,
+                      tab, cum);
     }
     const BatchKTab kt = kts[bs.ktab];
     for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < n * kt.nph; idx += blockDim.x * gridDim.y) {
@@ -636,6 +667,224 @@ __device__ __noinline__ void network_pair(const float* __restrict__ net, int m0,
     }
 }
 
+// ---- tensor-core form of the descriptor contraction (BF16x3) -----------------------------
+// Per species block t_i and tile of TC_TA atoms, with the candidate group on the M side:
+//   D[(n, c)][(atom, lm)] = sum_{(s, k)} c^A[t_i][s][n][k][c] B^A[atom][s][k][lm]   (Sec. II.A)
+// M = 5 n x 32 candidates in two 128-row tiles (n = 0..3, then n = 4 in rows 0..31 of the
+// second; its other rows are never read back), K = (s, k) padded to 48, N = 24 x atoms (120,
+// issued as 128).  Each operand is split x = hi + lo in BF16 and D = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi is accumulated in FP32 in tensor memory.  Tensor-memory lane = candidate and
+// warp = n, so the epilogue thread (n, c) holds A_{n,lm} of its candidate for every atom of the
+// tile and forms the invariants D^A_{nl} and D^4b_n itself; warps 5-7 form the radial
+// descriptor D^R_n in FP32 from B^R rows that arrive with the tile.  Pipeline: two operand
+// buffers and two accumulator buffers, so the products of tile j + 1 run while the warps
+// read tile j, and the copies of tile j + 2 are in flight.
+constexpr int TC_TA = 5;                           // atoms per tile
+constexpr int TC_N = 128;                          // MMA N (24 TC_TA = 120 columns used)
+constexpr int TC_SBO = 8 * BIMG_ROWB;              // 768 B between 8-row groups
+constexpr int TC_APLANE = 256 * BIMG_ROWB;         // rows (n, c), n < 5 (160..255 unused)
+constexpr int TC_BPLANE = TC_N * BIMG_ROWB;        // 12288 B (rows past 24 TC_TA never read back)
+constexpr int TC_BR = MAX_SPECIES * KR;            // B^R floats per atom (first floats of its basis sums)
+constexpr int TC_OFF_B = 2 * TC_APLANE;            // A hi | A lo | B[2] (hi | lo) | B^R[3] | c^R | scaler
+constexpr int TC_OFF_BR = TC_OFF_B + 4 * TC_BPLANE;
+constexpr int TC_OFF_R = TC_OFF_BR + 3 * TC_TA * TC_BR * 4;
+constexpr int TC_OFF_S = TC_OFF_R + MAX_SPECIES * NR * KR * CG * 4;
+constexpr int TC_BYTES = TC_OFF_S + NDES * CG * 4;
+constexpr uint32_t TC_COLS = 512;                  // tensor-memory columns of the block
+static_assert(24 * TC_TA <= TC_N && 4 * TC_N <= (int)TC_COLS, "two accumulator buffers of two M tiles");
+static_assert((TC_OFF_B % 128) == 0 && (TC_OFF_BR % 16) == 0 && (TC_OFF_R % 16) == 0 && (TC_BR * 4) % 16 == 0,
+              "bulk-copy and descriptor alignment");
+
+struct TcBars {
+    uint64_t* b;        // [2] operand buffers
+    uint64_t* m;        // [2] MMA completion per accumulator buffer
+};
+
+// false when a bounded wait gave up (status bit set; results of the block are not valid)
+__device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayout lay, int ti, int p0, int p1,
+                                        const int* __restrict__ order_s, const unsigned char* __restrict__ bimg_s,
+                                        const float* __restrict__ bsum_s, int bstride, unsigned char* __restrict__ sm,
+                                        uint32_t tmem, TcBars bars, uint32_t& tcpar, float* __restrict__ A,
+                                        float* __restrict__ duq, unsigned int* __restrict__ status) {
+    constexpr int NW = 8;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int S = lay.n_species;
+    unsigned char* Ahi = sm;
+    unsigned char* Alo = sm + TC_APLANE;
+    const float* bring = reinterpret_cast<const float*>(sm + TC_OFF_BR);   // [3][TC_TA][TC_BR]
+    float* cR = reinterpret_cast<float*>(sm + TC_OFF_R);   // [S][NR][KR][CG]
+    float* scl = reinterpret_cast<float*>(sm + TC_OFF_S);  // [NDES][CG]
+    bool ok_all = true;
+    // operand A: row (n, c), K (s, k); lanes over candidates (coalesced parameter reads)
+    const int abase = lay.c_angular + ti * S * NA * KA;
+    for (int job = warp; job < NA * (BIMG_K / 8); job += NW) {
+        const int n = job / (BIMG_K / 8), kc = job - n * (BIMG_K / 8);
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float x[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int kidx = 8 * kc + 2 * h + e, sj = kidx / KA, k = kidx - sj * KA;
+                x[e] = sj < S ? __ldg(&pg[(size_t)(abase + (sj * NA + n) * KA + k) * CG + lane]) : 0.f;
+            }
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[0], x[1]);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[0] - __bfloat162float(hi.x), x[1] - __bfloat162float(hi.y));
+            hw[h] = *reinterpret_cast<const uint32_t*>(&hi);
+            lw[h] = *reinterpret_cast<const uint32_t*>(&lo);
+        }
+        const int r = n * 32 + lane;
+        const int o = ((r >> 3) * (BIMG_K / 8) + kc) * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(Alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    // c^R[t_i] and the scaler for the radial descriptor (FP32, lane-minor)
+    const int nr = S * NR * KR;
+    for (int idx = tid; idx < (nr + NDES) * CG; idx += NW * 32) {
+        const int p = idx >> 5, c = idx & 31;
+        if (p < nr) cR[p * CG + c] = __ldg(&pg[(size_t)(lay.c_radial + ti * nr + p) * CG + c]);
+        else scl[(p - nr) * CG + c] = __ldg(&pg[(size_t)(lay.scaler + p - nr) * CG + c]);
+    }
+    fence_proxy_async_smem();   // operand A (and the earlier phases' shared-memory use) before async writes / reads
+    __syncthreads();
+
+    const int ntile = (p1 - p0 + TC_TA - 1) / TC_TA;
+    // tile j: the B operand images (hi, lo) into buffer j & 1 and the B^R rows into ring slot j % 3
+    auto issue_b = [&](int j) {
+        const int a0 = p0 + j * TC_TA, cnt = min(TC_TA, p1 - a0);
+        unsigned char* dst = sm + TC_OFF_B + (j & 1) * 2 * TC_BPLANE;
+        unsigned char* dbr = sm + TC_OFF_BR + (j % 3) * TC_TA * TC_BR * 4;
+        mbar_expect_tx(&bars.b[j & 1], (uint32_t)(cnt * (2 * BIMG_PLANE + TC_BR * 4)));
+        for (int q = 0; q < cnt; ++q) {
+            const int m = order_s[a0 + q];
+            const unsigned char* src = bimg_s + (size_t)m * BIMG_BYTES;
+            bulk_g2s(dst + q * BIMG_PLANE, src, BIMG_PLANE, &bars.b[j & 1]);
+            bulk_g2s(dst + TC_BPLANE + q * BIMG_PLANE, src + BIMG_PLANE, BIMG_PLANE, &bars.b[j & 1]);
+            bulk_g2s(dbr + q * TC_BR * 4, bsum_s + (size_t)m * bstride, TC_BR * 4, &bars.b[j & 1]);
+        }
+    };
+    // products of tile j into accumulator buffer j & 1 (thread 0, after its operands landed)
+    auto issue_mma = [&](int j) {
+        const int b = j & 1;
+        const bool ok = mbar_wait_bounded(&bars.b[b], (tcpar >> b) & 1u);
+        if (ok) {
+            tc_fence_after();
+            const uint32_t idesc = instr_desc(TC_FMT_BF16, 128, TC_N);
+            const uint32_t bh = smem_u32(sm + TC_OFF_B + b * 2 * TC_BPLANE), bl = bh + TC_BPLANE;
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const uint32_t d = tmem + (uint32_t)(b * 2 * TC_N + mt * TC_N), ao = (uint32_t)mt * 16 * TC_SBO;
+#pragma unroll
+                for (int kk = 0; kk < BIMG_K / 16; ++kk) {
+                    const uint32_t ko = (uint32_t)kk * 256;   // 16 K = two core matrices
+                    const uint64_t dah = smem_desc(ah + ao + ko, 128, TC_SBO);
+                    const uint64_t dal = smem_desc(al + ao + ko, 128, TC_SBO);
+                    const uint64_t dbh = smem_desc(bh + ko, 128, TC_SBO);
+                    const uint64_t dbl = smem_desc(bl + ko, 128, TC_SBO);
+                    mma_bf16(d, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+                    mma_bf16(d, dah, dbl, idesc, 1u);
+                    mma_bf16(d, dal, dbh, idesc, 1u);
+                }
+            }
+            mma_commit(&bars.m[b]);
+        } else {
+            atomicOr(status, kStatusTimeout);
+            mbar_arrive(&bars.m[b]);   // no products: release the waiting warps at once
+        }
+    };
+    if (tid == 0 && ntile > 0) {
+        issue_b(0);
+        if (ntile > 1) issue_b(1);
+        issue_mma(0);
+    }
+    // Tile j's B^R rows are read with ordinary loads: thread 0 saw their copy complete before a
+    // block barrier (this one for tile 0, the end of iteration j - 1 for the others).
+    __syncthreads();
+    for (int j = 0; j < ntile; ++j) {
+        const int a0 = p0 + j * TC_TA, cnt = min(TC_TA, p1 - a0);
+        const int b = j & 1;
+        // every thread keeps the phase bits of the operand barriers in step with thread 0
+        if (tid == 0 && j + 1 < ntile) issue_mma(j + 1);
+        if (j == 0) tcpar ^= 1u;
+        if (j + 1 < ntile) tcpar ^= 1u << ((j + 1) & 1);
+        const bool okm = mbar_wait_bounded(&bars.m[b], (tcpar >> (2 + b)) & 1u);
+        tcpar ^= 1u << (2 + b);
+        if (!okm) {
+            ok_all = false;
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+        }
+        tc_fence_after();
+        // operand buffer b is free once tile j's products are complete: tile j + 2 streams in
+        if (tid == 0 && j + 2 < ntile) issue_b(j + 2);
+        const float* brow = bring + (j % 3) * TC_TA * TC_BR;
+        if (warp < NA) {
+            // epilogue: n = warp, c = lane
+            const int n = warp;
+            const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                   (uint32_t)(b * 2 * TC_N + (warp == 4 ? TC_N : 0));
+            for (int q = 0; q < cnt; ++q) {
+                const int m = order_s[a0 + q];
+                uint32_t r[24];
+                tmem_ld8_nowait(tbase + q * NLM, r);
+                tmem_ld8_nowait(tbase + q * NLM + 8, r + 8);
+                tmem_ld8_nowait(tbase + q * NLM + 16, r + 16);
+                tmem_wait_ld();
+                float v[NLM];
+#pragma unroll
+                for (int M = 0; M < NLM; ++M) v[M] = __uint_as_float(r[M]);
+                float* Ao = A + (size_t)m * NANG * CG + (size_t)n * NLM * CG + lane;
+                float dA[LMAX] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int M = 0; M < NLM; ++M) {
+                    const int l = M < 3 ? 0 : (M < 8 ? 1 : (M < 15 ? 2 : 3));
+                    Ao[M * CG] = v[M];
+                    dA[l] = fmaf(c_wlm[M], v[M] * v[M], dA[l]);
+                }
+                float a2[5], t[6], t2[6];
+#pragma unroll
+                for (int kk = 0; kk < 5; ++kk) a2[kk] = v[3 + kk];
+                tensor_from_a(a2, t);
+                tensor_square(t, t2);
+                const float d4 = t2[0] * t[0] + t2[1] * t[1] + t2[2] * t[2] + 2.f * (t2[3] * t[3] + t2[4] * t[4] + t2[5] * t[5]);
+                float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+#pragma unroll
+                for (int l = 0; l < LMAX; ++l) {
+                    const int vi = NR + l * NA + n;
+                    dd[vi * CG] = dA[l] * scl[vi * CG + lane];
+                }
+                const int v4 = NR + 4 * NA + n;
+                dd[v4 * CG] = d4 * scl[v4 * CG + lane];
+            }
+        } else {
+            // radial descriptor D^R_n = sum c^R[t_i][t_j][n][k] B^R[t_j][k] (FP32), lane = candidate
+            for (int q = warp - NA; q < cnt; q += NW - NA) {
+                const int m = order_s[a0 + q];
+                const float* br = brow + q * TC_BR;
+                float d[NR];
+#pragma unroll
+                for (int u = 0; u < NR; ++u) d[u] = 0.f;
+                for (int tj = 0; tj < S; ++tj) {
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) {
+                        const float bv = br[tj * KR + k];
+#pragma unroll
+                        for (int u = 0; u < NR; ++u) d[u] = fmaf(cR[((tj * NR + u) * KR + k) * CG + lane], bv, d[u]);
+                    }
+                }
+                float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
+#pragma unroll
+                for (int u = 0; u < NR; ++u) dd[u * CG] = d[u] * scl[u * CG + lane];
+            }
+        }
+        fence_proxy_async_smem();   // the B^R ring slot read here is refilled by a later bulk copy
+        tc_fence_before();
+        __syncthreads();            // accumulator buffer b is reused by tile j + 2
+        tc_fence_after();
+    }
+    return ok_all;
+}
+
 // Stage the network block of species ti and the scaler (layout of network_pair).
 __device__ __forceinline__ void stage_network(const float* __restrict__ pg, const ParamLayout& lay, int ti,
                                               float* __restrict__ net) {
@@ -651,14 +900,14 @@ __device__ __forceinline__ void stage_network(const float* __restrict__ pg, cons
 // Backward of sorted atom m: partial forces of every list entry (Sec. II.C).  The atom's
 // pair rows arrive in 32-row pieces by double-buffered bulk copies: the copy of the next
 // piece is in flight while the current one is used.
-__device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStruct& bs, int m,
+__device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n, int m,
                                               const float* __restrict__ prm, float* __restrict__ wb,
                                               uint64_t* bars, uint32_t& par, const float* __restrict__ A,
                                               const float* __restrict__ duq, const float* __restrict__ qcs,
                                               const float4* __restrict__ fk, const float4* __restrict__ fr,
                                               float4* __restrict__ fsum, int nmax, float selfc, float phibar) {
     const int lane = threadIdx.x & 31;
-    const int S = a.lay.n_species, off = bs.atom_off, n = bs.n;
+    const int S = a.lay.n_species;
     int* cum = reinterpret_cast<int*>(wb + WCUM);
     species_cum(a, off, n, m, S, cum);
     const int tot_a = cum[8 + S];
@@ -836,12 +1085,15 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, const BatchStr
               make_float4(fx + fmaf(qc, kf.y, rf.y), fy + fmaf(qc, kf.z, rf.z), fz + fmaf(qc, kf.w, rf.w), 0.f));
 }
 
-template <int NW>
+template <int NW, bool TC>
 __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
-    extern __shared__ __align__(16) unsigned char bsm[];
+    static_assert(!TC || NW == 8, "the tensor-core descriptor contraction uses 8 warps");
+    extern __shared__ __align__(128) unsigned char bsm[];
     __shared__ int s_item;
     __shared__ __align__(8) uint64_t wbars[NW][2];   // per-warp barriers of the two row buffers
     __shared__ __align__(8) uint64_t tbars[2];       // block barriers of the two S(k) / field tiles
+    __shared__ __align__(8) uint64_t tcbars[4];      // tensor-core form: two operand buffers, two accumulators
+    __shared__ uint32_t s_tmem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         mbar_init(&wbars[warp][0], 1);
@@ -849,11 +1101,21 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         if (warp == 0) {
             mbar_init(&tbars[0], 1);
             mbar_init(&tbars[1], 1);
+            if (TC)
+                for (int q = 0; q < 4; ++q) mbar_init(&tcbars[q], 1);
         }
         mbar_init_fence();
     }
+    if (TC && warp == 0) tmem_alloc(&s_tmem, TC_COLS);   // one block per SM (shared memory > half an SM)
+    if (TC) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     uint32_t par = 0;    // phase bits of this warp's two buffers
     uint32_t tpar = 0;   // phase bits of the two block tiles
+    uint32_t tcpar = 0;  // phase bits of the tensor-core barriers
+    bool tc_fail = false;
     double* red = reinterpret_cast<double*>(bsm);     // [NW][CG]
     double* sums = red + NW * CG;                      // [NSUMS][CG]
     float* cst = reinterpret_cast<float*>(sums + NSUMS * CG);   // delta, phibar, q_target, pad [4][CG]
@@ -893,6 +1155,18 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             const int p0 = so[ti], p1 = so[ti + 1];
             if (p1 == p0) continue;
             __syncthreads();
+            if constexpr (TC) {
+                if (!forward_tc(pg, a.lay, ti, p0, p1, a.order + off, a.bimg + (size_t)off * BIMG_BYTES,
+                                a.bsum + (size_t)off * a.bstride, a.bstride, reinterpret_cast<unsigned char*>(un),
+                                s_tmem, TcBars{&tcbars[0], &tcbars[2]}, tcpar, A, duq, a.status))
+                    tc_fail = true;
+                __syncthreads();
+                stage_network(pg, a.lay, ti, un);
+                __syncthreads();
+                for (int p = p0 + 2 * warp; p < p1; p += 2 * NW)
+                    network_pair(un, a.order[off + p], p + 1 < p1 ? a.order[off + p + 1] : -1, duq, uq, su, sq);
+                continue;
+            }
             stage_params(pg, a.lay, ti, un);
             __syncthreads();
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
@@ -1227,7 +1501,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
             const float phibar = cst[CG + lane];
             for (int p = p0 + warp; p < p1; p += NW)
-                backward_atom(a, bs, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum, nmax,
+                backward_atom(a, off, n, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum, nmax,
                               selfc, phibar);
         }
         __syncthreads();
@@ -1254,6 +1528,17 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             a.energy[(size_t)cand * a.n_struct + item.x] = e;
         }
     }
+    if (TC) {
+        // after a wait that gave up, give the products in flight a second bounded wait
+        if (__syncthreads_or(tc_fail) && threadIdx.x == 0) {
+            mbar_wait_bounded(&tcbars[2], ((tcpar >> 2) & 1u) ^ 1u);
+            mbar_wait_bounded(&tcbars[3], ((tcpar >> 3) & 1u) ^ 1u);
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (warp == 0) tmem_free(s_tmem, TC_COLS);
+    }
 }
 
 // the field pass at the largest phase rows fits the 227 KB of shared memory of a block
@@ -1263,9 +1548,10 @@ static_assert(sizeof(double) * (8 + NSUMS) * CG + sizeof(float) * 4 * CG +
               "field windows and phase rows exceed shared memory");
 
 template <int NW>
-size_t item_smem(int nph_max) {
+size_t item_smem(int nph_max, bool tc) {
     const size_t head = sizeof(double) * (NW + NSUMS) * CG + sizeof(float) * 4 * CG;
-    const size_t p1 = sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
+    const size_t p1 = tc ? std::max((size_t)TC_BYTES, sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS))
+                         : sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
     const size_t p1b = sizeof(float) * (size_t)NET_FLOATS;
     const size_t p3 = 2 * (sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max);
     const size_t p4 = sizeof(float2) * ((size_t)NW * nph_max * 32 + 2 * (size_t)WIN_F2);
@@ -1278,7 +1564,7 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
                        const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
-                       int bstride, float alpha, unsigned int* status, cudaStream_t st_) {
+                       int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_) {
     if (n_struct <= 0) return;
     const size_t sm1 = sizeof(int) * ((size_t)nmax + BATCH_MAX_CELLS + 1 + MAX_SPECIES + 1);
     const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a + 32 * TAB_P + 16);
@@ -1291,33 +1577,46 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
     const int ysplit = std::max(1, std::min(64, (nmax + 32 * (PREP_THREADS / 32) - 1) / (32 * (PREP_THREADS / 32)) * 4));
     k_batch_lists<<<dim3(n_struct, ysplit), PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
                                                          cnt_list, nbr_ang, cnt_ang, phase, nph_stride, geo_rad,
-                                                         geo_ang, bsum, bstride, alpha, status);
+                                                         geo_ang, bsum, bstride, bimg, alpha, status);
 }
 
-size_t batch_item_smem(int warps, int nph_max) {
-    return warps == 4 ? item_smem<4>(nph_max) : item_smem<8>(nph_max);
+size_t batch_item_smem(int warps, int nph_max, int contract) {
+    const bool tc = contract == BATCH_CONTRACT_BF16X3;
+    return warps == 4 ? item_smem<4>(nph_max, false) : item_smem<8>(nph_max, tc);
 }
 
-int batch_item_blocks_per_sm(int warps, int nph_max) {
-    const size_t smem = batch_item_smem(warps, nph_max);
+// The tensor-core form holds 512 tensor-memory columns per block: it runs only where its
+// shared memory keeps it to one block per SM (0 otherwise, like a shape that does not fit).
+int batch_item_blocks_per_sm(int warps, int nph_max, int contract) {
+    if (contract == BATCH_CONTRACT_BF16X3 && warps != 8) return 0;
+    const size_t smem = batch_item_smem(warps, nph_max, contract);
     int nb = 0;
     if (warps == 4) {
-        cudaFuncSetAttribute(k_batch_items<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<4>, 128, smem) != cudaSuccess) nb = 0;
+        cudaFuncSetAttribute(k_batch_items<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<4, false>, 128, smem) != cudaSuccess)
+            nb = 0;
+    } else if (contract == BATCH_CONTRACT_BF16X3) {
+        cudaFuncSetAttribute(k_batch_items<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8, true>, 256, smem) != cudaSuccess)
+            nb = 0;
+        if (nb > 1) nb = 0;
     } else {
-        cudaFuncSetAttribute(k_batch_items<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8>, 256, smem) != cudaSuccess) nb = 0;
+        cudaFuncSetAttribute(k_batch_items<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8, false>, 256, smem) != cudaSuccess)
+            nb = 0;
     }
     return nb;
 }
 
-void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int grid, cudaStream_t st_) {
+void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract, int grid, cudaStream_t st_) {
     if (grid <= 0 || a.n_items <= 0) return;
-    const size_t smem = batch_item_smem(warps, nph_max);
+    const size_t smem = batch_item_smem(warps, nph_max, contract);
     if (warps == 4)
-        k_batch_items<4><<<grid, 128, smem, st_>>>(a);
+        k_batch_items<4, false><<<grid, 128, smem, st_>>>(a);
+    else if (contract == BATCH_CONTRACT_BF16X3)
+        k_batch_items<8, true><<<grid, 256, smem, st_>>>(a);
     else
-        k_batch_items<8><<<grid, 256, smem, st_>>>(a);
+        k_batch_items<8, false><<<grid, 256, smem, st_>>>(a);
 }
 
 }  // namespace qnep

@@ -25,6 +25,17 @@ constexpr int BATCH_MAX_NPH = 94;    // phase factors per atom (n_max <= 16 per 
 constexpr int BATCH_MAX_CELLS = 512; // cell grid per structure (8 per axis at most)
 constexpr int BATCH_GR = 20, BATCH_GA = 48;   // floats per radial / angular pair row
 
+// Tensor-core form of the angular contraction A_{n,lm} = sum_{s,k} c^A[t_i][s][n][k] B^A[s][k][lm]
+// (BF16x3: operands split into BF16 hi + lo, three products, FP32 accumulation).  The pre-pass
+// writes B^A of every atom as its operand image: 24 rows (lm) x 48 K ((s, k) = 9 s + k, zero
+// past 9 S) of BF16 in the canonical K-major layout without swizzle, the hi plane then the lo
+// plane, so a tile of atoms is a concatenation of bulk copies.
+constexpr int BIMG_K = 48;                       // (species, k) padded to a multiple of 16
+constexpr int BIMG_ROWB = BIMG_K * 2;            // bytes per operand row
+constexpr int BIMG_PLANE = NLM * BIMG_ROWB;      // 2304 bytes: one atom's 24 rows
+constexpr int BIMG_BYTES = 2 * BIMG_PLANE;       // hi | lo
+enum { BATCH_CONTRACT_FP32 = 0, BATCH_CONTRACT_BF16X3 = 1 };
+
 // One structure of the batch (host-built).
 struct BatchStruct {
     int atom_off;    // first atom in the concatenated inputs
@@ -78,6 +89,7 @@ struct BatchArgs {
     const float* geo_ang;    // [N][cap_a][48] angular pair rows
     const float* bsum;       // [N][bstride] basis sums B^R | B^A
     int bstride;
+    const unsigned char* bimg;   // [N][BIMG_BYTES] B^A operand images (tensor-core form), or NULL
     // tables
     const BatchStruct* st;
     const BatchKTab* kt;
@@ -110,12 +122,14 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
                        const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
-                       int bstride, float alpha, unsigned int* status, cudaStream_t st_);
+                       int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_);
 // Floats per atom of the basis sums: B^R padded to MAX_SPECIES species, then B^A of n_species.
 inline int batch_bstride(int n_species) { return MAX_SPECIES * KR + n_species * KA * NLM; }
 // Dynamic shared memory of the item kernel and its resident blocks per SM (0: does not fit).
-size_t batch_item_smem(int warps, int nph_max);
-int batch_item_blocks_per_sm(int warps, int nph_max);
-void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int grid, cudaStream_t st_);
+// contract: BATCH_CONTRACT_FP32 (FP32 FMAs, 4 or 8 warps) or BATCH_CONTRACT_BF16X3 (tensor cores,
+// 8 warps only)
+size_t batch_item_smem(int warps, int nph_max, int contract);
+int batch_item_blocks_per_sm(int warps, int nph_max, int contract);
+void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract, int grid, cudaStream_t st_);
 
 }  // namespace qnep

@@ -41,11 +41,12 @@ def _llzo(reps, seed, sigma=0.1):
                      wl.LLZO_SPECIES)
 
 
-def _run_batch(systems, hp, params, elec, dev, warps=8, order="largest_first"):
+def _run_batch(systems, hp, params, elec, dev, warps=8, order="largest_first", contract="fp32"):
     from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
     pos, typ, off, boxes = stack_structures(systems)
     b = QNEPBatch(hp, params, elec)
     b.set_config(warps, order)
+    b.set_contraction(contract)
     out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
@@ -66,13 +67,13 @@ def _check_pair(res, off, systems, s, c, hp, params, elec):
     assert dq <= TOL["q"], (s, c, dq)
 
 
-@pytest.mark.parametrize("warps", [8, 4])
-def test_small_batch_every_pair_against_oracle(dev, warps):
+@pytest.mark.parametrize("warps,contract", [(8, "fp32"), (4, "fp32"), (8, "bf16x3")])
+def test_small_batch_every_pair_against_oracle(dev, warps, contract):
     systems = [_llzo((1, 1, 1), 1), _llzo((2, 1, 1), 2), _llzo((1, 1, 2), 3)]
     hp = wl.HParams(n_species=4)
     params = wl.random_params(hp, np.random.default_rng(11), n_candidates=3)
     elec = wl.Elec(mode=1, kind="ewald")
-    res, off = _run_batch(systems, hp, params, elec, dev, warps=warps)
+    res, off = _run_batch(systems, hp, params, elec, dev, warps=warps, contract=contract)
     for s in range(len(systems)):
         for c in range(3):
             _check_pair(res, off, systems, s, c, hp, params, elec)
@@ -102,13 +103,14 @@ def test_two_groups_against_single_structure_path(dev):
         _check_pair(res, off, systems, s, c, hp, params, elec)
 
 
-def test_mode2_total_charge_and_one_species_water(dev):
+@pytest.mark.parametrize("contract", ["fp32", "bf16x3"])
+def test_mode2_total_charge_and_one_species_water(dev, contract):
     """k-space-only electrostatics, a charged target and 2-species water boxes of uneven size."""
     systems = [wl.water_box(4, seed=21), wl.water_box(5, seed=22)]
     hp = wl.HParams(n_species=2)
     params = wl.random_params(hp, np.random.default_rng(13), n_candidates=33)
     elec = wl.Elec(mode=2, kind="ewald", q_total=0.5)
-    res, off = _run_batch(systems, hp, params, elec, dev)
+    res, off = _run_batch(systems, hp, params, elec, dev, contract=contract)
     for s, c in ((0, 0), (1, 32), (1, 7)):
         _check_pair(res, off, systems, s, c, hp, params, elec)
     # total corrected charge is Q / sqrt(eps_inf) per pair
@@ -188,7 +190,8 @@ def test_full_llzo_batch_sampled_pairs(dev):
         _check_pair(res, off, systems, s, c, hp, params, elec)
 
 
-def test_edge_cases_empty_single_atom_and_one_candidate(dev):
+@pytest.mark.parametrize("contract", ["fp32", "bf16x3"])
+def test_edge_cases_empty_single_atom_and_one_candidate(dev, contract):
     """Empty and one-/two-atom structures next to a normal cell; one candidate (31 padded lanes)."""
     from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
     hp = wl.HParams(n_species=4)
@@ -203,6 +206,7 @@ def test_edge_cases_empty_single_atom_and_one_candidate(dev):
     systems = [one, _llzo((1, 1, 1), 17), empty, two]
     pos, typ, off, boxes = stack_structures(systems)
     b = QNEPBatch(hp, params, elec)
+    b.set_contraction(contract)
     out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
@@ -212,12 +216,32 @@ def test_edge_cases_empty_single_atom_and_one_candidate(dev):
     assert res["energy"][0, 2] == 0.0     # an empty structure contributes nothing
 
 
-def test_batched_three_species_perovskite_mix(dev):
+@pytest.mark.parametrize("contract", ["fp32", "bf16x3"])
+def test_batched_three_species_perovskite_mix(dev, contract):
     """BaTiO3 cells of several sizes (cubic 8 A to 12 A) in one batch, mode 1 with a charge target."""
     systems = [wl.batio3_supercell(2, seed=51), wl.batio3_supercell(3, seed=52), wl.batio3_supercell(2, seed=53)]
     hp = wl.HParams(n_species=3)
     params = wl.random_params(hp, np.random.default_rng(18), n_candidates=35)
     elec = wl.Elec(mode=1, kind="ewald", q_total=-0.4)
-    res, off = _run_batch(systems, hp, params, elec, dev)
+    res, off = _run_batch(systems, hp, params, elec, dev, contract=contract)
     for s, c in ((0, 0), (1, 34), (2, 17)):
         _check_pair(res, off, systems, s, c, hp, params, elec)
+
+
+def test_full_llzo_batch_tensor_core_contraction(dev):
+    """The full 512 x 64 batch with the BF16x3 tensor-core contraction: sampled pairs against the
+    oracle at the FP32 tolerances, and every pair against the FP32 contraction (energy per atom
+    1e-6 eV, forces 1e-4 eV/A, charges 2e-6 e)."""
+    systems, hp, params, elec = wl.config_llzo_batch()
+    res_tc, off = _run_batch(systems, hp, params, elec, dev, contract="bf16x3")
+    assert np.isfinite(res_tc["energy"]).all() and np.isfinite(res_tc["forces"]).all()
+    sizes = np.diff(off)
+    big = int(np.argmax(sizes))
+    small = int(np.argmin(sizes))
+    for s, c in ((big, 62), (small, 1), (int(np.argsort(sizes)[len(sizes) // 2]), 31)):
+        _check_pair(res_tc, off, systems, s, c, hp, params, elec)
+    res_fp, _ = _run_batch(systems, hp, params, elec, dev, contract="fp32")
+    de = np.abs(res_tc["energy"] - res_fp["energy"]) / sizes[None, :]
+    assert de.max() <= TOL["e"], de.max()
+    assert np.abs(res_tc["forces"] - res_fp["forces"]).max() <= TOL["f"]
+    assert np.abs(res_tc["charges"] - res_fp["charges"]).max() <= TOL["q"]
