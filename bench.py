@@ -614,6 +614,89 @@ def _time_snes_step(b, graph, stream, out, off, params, dev, reps):
                     "+ qnep_batch_loss + qnep_snes_update, CUDA events on the call's stream, median"}
 
 
+def _time_plain_single(hp, params0, elec, systems, dev, stream, flush):
+    """Single-structure FP32 calls (forces + charges) on the given structures, candidate 0."""
+    import torch
+    from paper_2601_19034_gb300.qnep import QNEP
+    models, graphs, outs = {}, [], []
+    eager_ms = 0.0
+    for sy in systems:
+        key = tuple(np.round(np.diag(sy.box), 6))
+        if key not in models:
+            models[key] = QNEP(hp, params0, elec)
+            models[key].reserve(max(x.n_atoms for x in systems), sy.box)
+        m = models[key]
+        p1, t1 = torch.tensor(sy.positions, device=dev), torch.tensor(sy.types, device=dev)
+        o1 = m.compute(p1, t1, sy.box, bec=False, virial=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(3):
+            m.compute_into(p1, t1, sy.box, o1)
+        ev1.record()
+        ev1.synchronize()
+        eager_ms += ev0.elapsed_time(ev1) / 3
+        with torch.cuda.stream(stream):
+            m.compute_into(p1, t1, sy.box, o1, stream=stream.cuda_stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            m.compute_into(p1, t1, sy.box, o1, stream=stream.cuda_stream)
+        graphs.append(g)
+        outs.append((p1, t1, o1))
+    torch.cuda.synchronize()
+    times = []
+    for k in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            for g in graphs:
+                g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        if k:
+            times.append(e0.elapsed_time(e1))
+    for m in models.values():
+        m.close()
+    atoms = int(sum(sy.n_atoms for sy in systems))
+    ms = float(np.median(times))
+    return {"value": atoms / (ms * 1e-3), "unit": UNIT, "ms": ms,
+            "eager_value": atoms / (eager_ms * 1e-3), "eager_ms": eager_ms,
+            "what": f"single-structure qnep_compute (forces + charges), one call per structure on the first "
+                    f"{len(systems)} structures, candidate 0: each call a CUDA graph (one model per box shape), "
+                    f"replayed back to back after one L2 flush (median of 3); eager calls beside it"}
+
+
+def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals):
+    """The headline batched call with the per-(candidate, structure) virial as well."""
+    import torch
+    out = b.outputs(len(off) - 1, pos_d.shape[0], pos_d.device, virial=True)
+    b.compute_into(pos_d, typ_d, off, boxes, out)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+    ts = []
+    for k in range(steps + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    return {"ms_per_step": ms, "value": evals / (ms * 1e-3), "unit": UNIT,
+            "what": "the same graph-replayed batched call writing energies, forces, charges and the 3x3 virial "
+                    "of every (candidate, structure) (qnep_batch_compute_outputs)"}
+
+
 def _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, flush, contract, steps, evals):
     """The same batched call with the other descriptor contraction (graph replay, L2 flushed)."""
     import torch
@@ -779,41 +862,31 @@ def run_batch(args):
         mixed[f"speedup_{prec}_vs_fp32"] = mixed[prec]["value"] / mixed["fp32"]["value"]
     mixed["errors_vs_oracle"] = "per-output bounds against the FP64 oracle in tests/test_gpu_precision.py"
 
-    # plain FP32 single-structure path on the same structures (candidate 0; one call per structure)
-    single = QNEP(hp, params[0], elec)
-    single_ms = 0.0
-    for sy in systems[:64]:
-        p1, t1 = torch.tensor(sy.positions, device=dev), torch.tensor(sy.types, device=dev)
-        o1 = single.compute(p1, t1, sy.box, bec=False, virial=False)
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        for _ in range(3):
-            single.compute_into(p1, t1, sy.box, o1)
-        ev1.record()
-        ev1.synchronize()
-        single_ms += ev0.elapsed_time(ev1) / 3
-    n64 = int(sum(sy.n_atoms for sy in systems[:64]))
-    plain_value = n64 / (single_ms * 1e-3)
-    single.close()
+    # plain FP32 single-structure path on the same structures (candidate 0; one call per structure):
+    # every call captured in its own CUDA graph (one model per box shape, so no call rebuilds its
+    # k-tables), the 64 graphs replayed back to back; the eager calls are reported beside it
+    plain = _time_plain_single(hp, params[0], elec, systems[:64], dev, stream, flush)
 
-    # end to end: positions / types from pinned host memory, energies back, through the public API
+    # end to end through the C ABI's host-buffer entry point (qnep_batch_compute_host): positions
+    # and types from pinned host memory in, energies, forces and charges back to pinned host
+    # memory, stream synchronised, every step
     pos_h = torch.tensor(pos).pin_memory()
     typ_h = torch.tensor(typ).pin_memory()
-    e_h = torch.empty(n_cand, len(systems), dtype=torch.float64).pin_memory()
+    out_h = {"energy": torch.empty(n_cand, len(systems), dtype=torch.float64).pin_memory(),
+             "forces": torch.empty(n_cand, n_total, 3, dtype=torch.float32).pin_memory(),
+             "charges": torch.empty(n_cand, n_total, dtype=torch.float32).pin_memory()}
     e2e_ms = []
     for k in range(args.warmup + min(args.steps, 10)):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        with torch.cuda.stream(stream):
-            pos_d.copy_(pos_h, non_blocking=True)
-            typ_d.copy_(typ_h, non_blocking=True)
-            b.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
-            e_h.copy_(out["energy"], non_blocking=True)
-        stream.synchronize()
+        b.compute_host(pos_h, typ_h, off, boxes, out_h, stream=stream.cuda_stream)
         dt = time.perf_counter() - t
         if k >= args.warmup:
             e2e_ms.append(dt * 1e3)
+    d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+    # the same call with the per-(candidate, structure) virial (graph replay, L2 flushed)
+    with_virial = _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, min(args.steps, 10), evals)
+
     # one device-resident SNES iteration around the same call (Sec. II.E): normal deviates,
     # sampling, parameter upload, the batched call (graph replay), the loss against reference
     # energies and forces (here candidate 0's outputs), the update of (mu, sigma)
@@ -848,13 +921,13 @@ def run_batch(args):
             "mixed": mixed,
             "field_response": field_roof,
             "snes_step": dict(snes, batched_call_ms=ms_per_step),
-            "plain_fp32": {"value": plain_value, "unit": UNIT,
-                           "what": "single-structure qnep_compute, forces + charges, one call per structure "
-                                   "(first 64 structures, candidate 0)",
-                           "speedup_batched_vs_plain": value / plain_value},
+            "plain_fp32": dict(plain, speedup_batched_vs_plain=value / plain["value"]),
+            "with_virial": with_virial,
             "e2e": {"value": evals / (statistics.median(e2e_ms) * 1e-3) * world, "unit": UNIT,
-                    "h2d_bytes_per_step": n_total * 16, "d2h_bytes_per_step": n_cand * len(systems) * 8,
-                    "ms_per_step": statistics.median(e2e_ms)},
+                    "h2d_bytes_per_step": n_total * 16, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.median(e2e_ms),
+                    "entry_point": "qnep_batch_compute_host (C ABI, host buffers): positions + types in; "
+                                   "energies, forces and charges of every (candidate, structure) back"},
             "gpu_launches": BATCH_KERNELS_PER_CALL * args.steps,
             "clocks": clocks,
             "device_status": status,

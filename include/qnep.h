@@ -302,7 +302,8 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * (Eq. U_i, Eq. U_ES with the charges of Sec. II.D), the forces including the
  * charge-derivative terms (Sec. II.C) and the corrected charges q^c.
  * Electrostatics: Ewald (mode 1 or 2) per structure; PPPM is not offered here.
- * Virial, BEC and polarization are not computed by the batched call.
+ * The virial per (candidate, structure) comes with qnep_batch_compute_outputs; BEC and
+ * polarization are not computed by the batched call.
  *
  * qnep_batch_create: hp and es as for qnep_create (es->kind must be QNEP_EWALD);
  *   params_host = n_candidates blobs of qnep_param_count(hp) floats, candidate-major.
@@ -331,6 +332,35 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
                                const int* types, const double* boxes, void* stream, double* energy,
                                float* forces, float* charges);
 qnep_status qnep_batch_sync_status(qnep_batch* b);
+
+/* Outputs of a batched call, indexed [candidate][structure] (energy, virial) or
+ * [candidate][atom] (forces, charges); energy is required, the others may be NULL.
+ *   energy:  [C][S] doubles, U^tot (eV)
+ *   forces:  [C][N_total][3] float32 (eV/A)
+ *   charges: [C][N_total] float32, corrected charges q^c (e)
+ *   virial:  [C][S][9] doubles, W_ab = -dU/d eps_ab under the homogeneous strain
+ *            r -> (I + eps) r of positions and cell (eV; row-major 3x3): the sum over neighbour
+ *            entries of -r_ij (x) F_ij (descriptor and dynamic-charge partial forces, Sec. II.C),
+ *            the static real-space pair terms and the k-space W^k = sum k_e G |S|^2 B
+ *            (Eq. virial-kspace-total), each FP32 per atom or per k and FP64 across them. */
+typedef struct {
+    double* energy;
+    float*  forces;
+    float*  charges;
+    double* virial;
+} qnep_batch_outputs;
+/* As qnep_batch_compute, with every output of qnep_batch_outputs (device pointers). */
+qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                                       const int* types, const double* boxes, void* stream,
+                                       const qnep_batch_outputs* out);
+/* The end-to-end form on HOST buffers: positions [N_total][3] and types [N_total] from host
+ * memory, every requested output of out_host (host pointers) copied back, then a stream
+ * synchronisation and the device status (as qnep_batch_sync_status).  The batch keeps device
+ * copies of the inputs and outputs (grown on demand, freed by qnep_batch_destroy); pinned host
+ * memory makes the copies asynchronous, pageable memory works but copies synchronously. */
+qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions_host,
+                                    const int* types_host, const double* boxes, void* stream,
+                                    const qnep_batch_outputs* out_host);
 qnep_status qnep_batch_debug_set_status(qnep_batch* b, unsigned int bits);   /* test hook, as above */
 /* Neighbour capacities (entries per atom; 0 = from the densest structure) and their current values. */
 qnep_status qnep_batch_set_capacity(qnep_batch* b, int cap_list, int cap_angular);
@@ -407,6 +437,25 @@ qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offs
                             const double* energy, const float* forces, const double* energy_ref,
                             const float* forces_ref, const float* params, int n_params,
                             const qnep_loss_weights* w, double* loss, double* terms, void* stream);
+
+/* Loss with the virial term: as qnep_batch_loss, plus
+ *   D_v = sqrt(1/(6 S') sum_s sum_{ab in xx,yy,zz,xy,yz,zx} ((W_s,ab - W^ref_s,ab) / N_s)^2)
+ * over the S' structures with atoms (virial per atom, eV; the NEP convention of an RMSE over
+ * the six independent components) and L = l_e D_e + l_f D_f + l_v D_v + l_1 |z|_1 + l_2 |z|_2^2.
+ * virial [C][S][9] f64 as qnep_batch_compute_outputs writes it and virial_ref [S][9] f64, both
+ * given or both NULL (D_v = 0); terms [C][5] f64 = (D_e, D_f, D_v, |z|_1, |z|_2^2). */
+typedef struct {
+    double energy;   /* l_e */
+    double force;    /* l_f */
+    double virial;   /* l_v */
+    double l1;       /* l_1 */
+    double l2;       /* l_2 */
+} qnep_loss_weights_v;
+qnep_status qnep_batch_loss_v(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                              const double* energy, const float* forces, const double* virial,
+                              const double* energy_ref, const float* forces_ref, const double* virial_ref,
+                              const float* params, int n_params, const qnep_loss_weights_v* w, double* loss,
+                              double* terms, void* stream);
 
 /* One SNES step (Schaul et al. 2011) from the losses of the population sampled with `noise`:
  * candidates ranked by loss (lowest first, ties by index, NaN last); utilities

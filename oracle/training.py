@@ -7,12 +7,16 @@ with the separable natural evolution strategy (SNES, Schaul et al. 2011, cited
 there) on the loss
     L(z) = l_e D_e + l_f D_f + l_v D_v + l_Z D_Z + l_Q D_Q + l_1 |z|_1 + l_2 |z|_2^2,
 the D being root-mean-square errors against reference data.  The batched force
-call returns energies, forces and corrected charges per (candidate, structure);
-the terms it can feed are D_e and D_f (its corrected charges sum to the target
-exactly, and it computes neither virials nor BEC), read as
+call returns energies, forces, corrected charges and virials per (candidate, structure);
+the terms it can feed are D_e, D_f and D_v (its corrected charges sum to the target
+exactly, and it computes no BEC), read as
     D_e = sqrt( 1/S sum_s ((E_s - E_s^ref) / N_s)^2 )        energy RMSE per atom
     D_f = sqrt( 1/(3 N) sum_i sum_b (F_ib - F_ib^ref)^2 )     force RMSE per component
-over the S structures with atoms (N_s > 0) and their N atoms in all.
+    D_v = sqrt( 1/(6 S) sum_s sum_ab ((W_s,ab - W_s,ab^ref) / N_s)^2 ),  ab in xx, yy, zz, xy, yz, zx
+                                                               virial RMSE per atom
+over the S structures with atoms (N_s > 0) and their N atoms in all; the paper names the
+RMSEs only, the normalisations are the NEP convention (per atom; the six independent
+components of the virial, read from its upper triangle).
 
 SNES, as published: a population of lambda candidates z_k = mu + sigma * s_k with
 s_k ~ N(0, I) (drawn by the caller and passed in); candidates ranked by loss
@@ -22,11 +26,12 @@ for rank k = 1..lambda; gradients g_mu = sum_k u_k s_k, g_sigma = sum_k u_k (s_k
 updates mu <- mu + eta_mu sigma g_mu, sigma <- sigma exp(eta_sigma / 2 g_sigma), with the
 published rates eta_mu = 1, eta_sigma = (3 + ln d) / (5 sqrt d) for d parameters.
 
-Pins (tests/test_oracle_training.py): D_e and D_f against brute-force loops and
+Pins (tests/test_oracle_training.py): D_e, D_f and D_v against brute-force loops and
 closed forms (a uniform per-atom energy offset d gives D_e = |d|, a uniform force
-offset c gives D_f = |c|); the utilities sum to zero and decrease with rank; the
-update is invariant under a monotone transform of the losses; SNES minimises a
-separable quadratic from a distant start.
+offset c gives D_f = |c|, a uniform per-atom virial offset v on every component gives
+D_v = |v|, on the three off-diagonal ones D_v = |v| / sqrt(2), on the lower triangle only
+0); the utilities sum to zero and decrease with rank; the update is invariant under a
+monotone transform of the losses; SNES minimises a separable quadratic from a distant start.
 """
 from __future__ import annotations
 
@@ -54,6 +59,35 @@ def loss_terms(energy, forces, energy_ref, forces_ref, atom_offsets, params):
         d_f = np.sqrt((df ** 2).reshape(df.shape[0], -1).mean(axis=1))
     z = np.asarray(params, dtype=np.float64)
     return d_e, d_f, np.abs(z).sum(axis=1), (z ** 2).sum(axis=1)
+
+
+VIRIAL_COMPONENTS = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2))
+
+
+def virial_rmse(virial, virial_ref, atom_offsets):
+    """D_v per candidate: virial [C, S, 3, 3], virial_ref [S, 3, 3] (eV), atom_offsets [S + 1]."""
+    off = np.asarray(atom_offsets, dtype=np.int64)
+    n_s = np.diff(off)
+    has = n_s > 0
+    w = np.asarray(virial, dtype=np.float64).reshape(-1, len(n_s), 3, 3)
+    wr = np.asarray(virial_ref, dtype=np.float64).reshape(len(n_s), 3, 3)
+    if not has.any():
+        return np.zeros(w.shape[0])
+    dv = np.stack([(w[:, has, a, b] - wr[None, has, a, b]) / n_s[None, has] for a, b in VIRIAL_COMPONENTS], -1)
+    return np.sqrt((dv ** 2).reshape(w.shape[0], -1).mean(axis=1))
+
+
+def loss_terms_v(energy, forces, virial, energy_ref, forces_ref, virial_ref, atom_offsets, params):
+    """Per candidate: (D_e, D_f, D_v, |z|_1, |z|_2^2); virial None gives D_v = 0."""
+    d_e, d_f, l1, l2 = loss_terms(energy, forces, energy_ref, forces_ref, atom_offsets, params)
+    d_v = np.zeros_like(d_e) if virial is None else virial_rmse(virial, virial_ref, atom_offsets)
+    return d_e, d_f, d_v, l1, l2
+
+
+def loss_v(terms, lambda_e, lambda_f, lambda_v, lambda_1, lambda_2):
+    """L(z) of Sec. II.E with the virial term."""
+    d_e, d_f, d_v, l1, l2 = terms
+    return lambda_e * d_e + lambda_f * d_f + lambda_v * d_v + lambda_1 * l1 + lambda_2 * l2
 
 
 def loss(terms, lambda_e, lambda_f, lambda_1, lambda_2):

@@ -62,6 +62,16 @@ class VjpC(ctypes.Structure):
                 ("polar_weight", ctypes.c_double * 3), ("grad", ctypes.c_void_p)]
 
 
+class BatchOutputsC(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p), ("charges", ctypes.c_void_p),
+                ("virial", ctypes.c_void_p)]
+
+
+class LossWeightsVC(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("force", ctypes.c_double), ("virial", ctypes.c_double),
+                ("l1", ctypes.c_double), ("l2", ctypes.c_double)]
+
+
 class LossWeightsC(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("force", ctypes.c_double), ("l1", ctypes.c_double),
                 ("l2", ctypes.c_double)]
@@ -123,6 +133,12 @@ def _declare(lib):
     lib.qnep_batch_create.restype = i
     lib.qnep_batch_compute.argtypes = [p, i, p, p, p, p, p, p, p, p]
     lib.qnep_batch_compute.restype = i
+    lib.qnep_batch_compute_outputs.argtypes = [p, i, p, p, p, p, p, ctypes.POINTER(BatchOutputsC)]
+    lib.qnep_batch_compute_outputs.restype = i
+    lib.qnep_batch_compute_host.argtypes = [p, i, p, p, p, p, p, ctypes.POINTER(BatchOutputsC)]
+    lib.qnep_batch_compute_host.restype = i
+    lib.qnep_batch_loss_v.argtypes = [i, i, p, i, p, p, p, p, p, p, p, i, ctypes.POINTER(LossWeightsVC), p, p, p]
+    lib.qnep_batch_loss_v.restype = i
     lib.qnep_batch_set_contraction.argtypes = [p, i]
     lib.qnep_batch_set_contraction.restype = i
     lib.qnep_batch_get_contraction.argtypes = [p, ctypes.POINTER(i)]

@@ -73,7 +73,15 @@ struct qnep_batch {
     unsigned int* d_work = nullptr;
     unsigned int* d_status = nullptr;
     cudaStream_t last_stream = nullptr;
-    std::map<std::tuple<int, int, int>, int> per_sm_cache;   // (warps, nph_max, contract) -> blocks per SM
+    std::map<std::tuple<int, int, int, bool>, int> per_sm_cache;   // (warps, nph_max, contract, virial) -> blocks per SM
+    // host-buffer entry point: device copies of the inputs and outputs (grown on demand)
+    float* io_pos = nullptr;
+    int* io_types = nullptr;
+    double* io_energy = nullptr;
+    float* io_forces = nullptr;
+    float* io_charges = nullptr;
+    double* io_virial = nullptr;
+    size_t io_atoms = 0, io_evals = 0, io_pairs = 0;
     // stage timers: events around the pre-pass and the item kernel of each profiled call
     bool profiling = false, pending = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -287,8 +295,10 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     BatchScratch& sc = b->sc;
     const size_t sA = nm * NANG * CG, sD = nm * 2 * NDES * CG, sN = nm * CG, sK = nk * CG;
     const size_t sP = (size_t)((nm + 511) / 512) * sK;   // partial structure factors per 512 atoms
-    // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2), skp (2)
-    const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 2 * sP + 64;
+    // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2), skp (2), virial sums
+    // (8 warps x 9 x CG doubles)
+    const size_t sV = (size_t)8 * 9 * CG;
+    const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 2 * sP + 2 * sV + 64;
     const size_t bytes = per * sizeof(float) * (size_t)slots;
     if (bytes > b->slot_bytes_alloc || !b->scratch) {
         CKB(cudaStreamSynchronize(st));
@@ -320,6 +330,7 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     sc.sk = reinterpret_cast<float2*>(take(2 * sK * slots));
     sc.stride_p = sP;
     sc.skp = reinterpret_cast<float2*>(take(2 * sP * slots));
+    sc.vir = reinterpret_cast<double*>(take(2 * sV * slots));
     b->slots_alloc = slots;
     return QNEP_OK;
 }
@@ -452,7 +463,19 @@ qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order) {
 qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
                                const int* types, const double* boxes, void* stream, double* energy, float* forces,
                                float* charges) {
+    qnep_batch_outputs o{energy, forces, charges, nullptr};
+    return qnep_batch_compute_outputs(b, n_struct, atom_offsets, positions, types, boxes, stream, &o);
+}
+
+qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
+                                       const int* types, const double* boxes, void* stream,
+                                       const qnep_batch_outputs* out) {
     if (!b) return QNEP_ERR_ARG;
+    if (!out) return failb(b, QNEP_ERR_ARG, "outputs are NULL");
+    double* energy = out->energy;
+    float* forces = out->forces;
+    float* charges = out->charges;
+    double* virial = out->virial;
     if (n_struct < 1 || !atom_offsets || !boxes || !energy) return failb(b, QNEP_ERR_ARG, "bad batch arguments");
     if (atom_offsets[0] != 0) return failb(b, QNEP_ERR_ARG, "atom_offsets[0] must be 0");
     if (atom_offsets[n_struct] > 0 && (!positions || !types))
@@ -467,10 +490,12 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     }
     // blocks per SM of this shape (cached: no CUDA calls beyond launches once the batch is known,
     // so the call can be captured in a graph)
-    const auto key = std::make_tuple(b->warps, b->nph_max, b->contract);
+    const auto key = std::make_tuple(b->warps, b->nph_max, b->contract, virial != nullptr);
     auto hit = b->per_sm_cache.find(key);
     if (hit == b->per_sm_cache.end())
-        hit = b->per_sm_cache.emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max, b->contract)).first;
+        hit = b->per_sm_cache
+                  .emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max, b->contract, virial != nullptr))
+                  .first;
     const int per_sm = hit->second;
     if (per_sm <= 0) return failb(b, QNEP_ERR_UNSUPPORTED, "item kernel does not fit on an SM");
     const bool tc = b->contract == QNEP_BATCH_CONTRACT_BF16X3;
@@ -483,8 +508,10 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     if (s != QNEP_OK) return s;
     CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
     CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
-    if (b->has_empty)   // structures without atoms have no item: their energies are zero
+    if (b->has_empty) {   // structures without atoms have no item: their energies (and virials) are zero
         CKB(cudaMemsetAsync(energy, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
+        if (virial) CKB(cudaMemsetAsync(virial, 0, sizeof(double) * 9 * (size_t)b->n_cand * n_struct, st));
+    }
     if (b->profiling) {
         if (b->pending) {   // previous profiled call: harvest its events
             CKB(cudaEventSynchronize(b->ev[2]));
@@ -537,6 +564,7 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
     a.energy = energy;
     a.forces = forces;
     a.charges = charges;
+    a.virial = virial;
     a.n_struct = n_struct;
     a.n_total = b->n_total;
     a.status = b->d_status;
@@ -562,6 +590,60 @@ qnep_status qnep_batch_sync_status(qnep_batch* b) {
     if (s == QNEP_ERR_TIMEOUT)
         return failb(b, s, "a bounded device-side wait gave up (a bulk copy or a tensor-core operation did not complete)");
     return QNEP_OK;
+}
+
+qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions_host,
+                                    const int* types_host, const double* boxes, void* stream,
+                                    const qnep_batch_outputs* out_host) {
+    if (!b) return QNEP_ERR_ARG;
+    if (n_struct < 1 || !atom_offsets || !boxes || !out_host || !out_host->energy)
+        return failb(b, QNEP_ERR_ARG, "bad batch arguments");
+    const int n_total = atom_offsets[n_struct];
+    if (n_total < 0) return failb(b, QNEP_ERR_ARG, "atom_offsets must not decrease");
+    if (n_total > 0 && (!positions_host || !types_host)) return failb(b, QNEP_ERR_ARG, "positions and types are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t evals = (size_t)b->n_cand * (size_t)n_total, pairs = (size_t)b->n_cand * (size_t)n_struct;
+    if ((size_t)n_total > b->io_atoms || evals > b->io_evals || pairs > b->io_pairs || !b->io_energy) {
+        // device copies of the inputs and of every output, kept for the next call of this shape
+        CKB(cudaStreamSynchronize(st));
+        void* old[] = {b->io_pos, b->io_types, b->io_energy, b->io_forces, b->io_charges, b->io_virial};
+        for (void* q : old)
+            if (q) cudaFree(q);
+        b->io_pos = nullptr;
+        b->io_types = nullptr;
+        b->io_energy = nullptr;
+        b->io_forces = nullptr;
+        b->io_charges = nullptr;
+        b->io_virial = nullptr;
+        b->io_atoms = b->io_evals = b->io_pairs = 0;
+        const size_t na = std::max<size_t>(n_total, 1), ne = std::max<size_t>(evals, 1), np = std::max<size_t>(pairs, 1);
+        CKB(cudaMalloc((void**)&b->io_pos, sizeof(float) * 3 * na));
+        CKB(cudaMalloc((void**)&b->io_types, sizeof(int) * na));
+        CKB(cudaMalloc((void**)&b->io_energy, sizeof(double) * np));
+        CKB(cudaMalloc((void**)&b->io_forces, sizeof(float) * 3 * ne));
+        CKB(cudaMalloc((void**)&b->io_charges, sizeof(float) * ne));
+        CKB(cudaMalloc((void**)&b->io_virial, sizeof(double) * 9 * np));
+        b->io_atoms = na;
+        b->io_evals = ne;
+        b->io_pairs = np;
+    }
+    if (n_total > 0) {
+        CKB(cudaMemcpyAsync(b->io_pos, positions_host, sizeof(float) * 3 * (size_t)n_total, cudaMemcpyHostToDevice, st));
+        CKB(cudaMemcpyAsync(b->io_types, types_host, sizeof(int) * (size_t)n_total, cudaMemcpyHostToDevice, st));
+    }
+    qnep_batch_outputs dev{b->io_energy, out_host->forces ? b->io_forces : nullptr,
+                           out_host->charges ? b->io_charges : nullptr, out_host->virial ? b->io_virial : nullptr};
+    qnep_status s = qnep_batch_compute_outputs(b, n_struct, atom_offsets, b->io_pos, b->io_types, boxes, stream, &dev);
+    if (s != QNEP_OK) return s;
+    CKB(cudaMemcpyAsync(out_host->energy, b->io_energy, sizeof(double) * pairs, cudaMemcpyDeviceToHost, st));
+    if (out_host->forces)
+        CKB(cudaMemcpyAsync(out_host->forces, b->io_forces, sizeof(float) * 3 * evals, cudaMemcpyDeviceToHost, st));
+    if (out_host->charges)
+        CKB(cudaMemcpyAsync(out_host->charges, b->io_charges, sizeof(float) * evals, cudaMemcpyDeviceToHost, st));
+    if (out_host->virial)
+        CKB(cudaMemcpyAsync(out_host->virial, b->io_virial, sizeof(double) * 9 * pairs, cudaMemcpyDeviceToHost, st));
+    b->last_stream = st;
+    return qnep_batch_sync_status(b);
 }
 
 qnep_status qnep_batch_debug_set_status(qnep_batch* b, unsigned int bits) {
@@ -678,7 +760,8 @@ void qnep_batch_destroy(qnep_batch* b) {
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,
-                    b->d_work,    b->d_status};
+                    b->d_work,    b->d_status, b->io_pos,   b->io_types, b->io_energy, b->io_forces,
+                    b->io_charges, b->io_virial};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto e : b->ev)

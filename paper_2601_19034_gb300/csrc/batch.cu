@@ -39,12 +39,13 @@ constexpr int PREP_THREADS = 256;
 
 // Candidate-independent pair geometry, written once per structure by the pre-pass:
 //   radial row  (GR floats per list entry):  f'_k (9) | u (3) | j if r < r_c^R else -1 |
-//                B(r) | B'(r) u (3) | j if r < r_c (real space) else -1 | pad
+//                B(r) | B'(r) u (3) | j if r < r_c (real space) else -1 | r | pad
 //   angular row (GA floats per angular entry): f_k (9) | f'_k (9) | u (3) | 1/r | j | pad | Y_lm (24)
 //   basis sums  (per atom): B^R[t][k] (padded to MAX_SPECIES species) | B^A[t][k][lm]
 // with B(r) = k_e erfc(alpha r) / r.  Rows are copied into shared memory (float4) by the item kernel.
-constexpr int GR = 20, GR_DF = 0, GR_U = 9, GR_JD = 12, GR_B = 13, GR_BU = 14, GR_JR = 17;
-static_assert(GR_JD == 12 && GR_B == 13 && GR_BU == 14 && GR_JR == 17, "float4 row reads assume this layout");
+constexpr int GR = 20, GR_DF = 0, GR_U = 9, GR_JD = 12, GR_B = 13, GR_BU = 14, GR_JR = 17, GR_R = 18;
+static_assert(GR_JD == 12 && GR_B == 13 && GR_BU == 14 && GR_JR == 17 && GR_R == 18,
+              "float4 row reads assume this layout");
 constexpr int GA = 48, GA_F = 0, GA_DF = 9, GA_U = 18, GA_IR = 21, GA_J = 22, GA_Y = 24;
 static_assert(GA_DF == 9 && GA_U == 18 && GA_Y == 24, "float4 row reads assume this layout");
 constexpr int TAB_P = KA + NLM;                // pre-pass staging row: f_k, Y_lm
@@ -224,6 +225,7 @@ __device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, con
             row[GR_U + 2] = vz * ir;
             row[GR_JD] = __int_as_float(-1);
             row[GR_JR] = __int_as_float(-1);
+            row[GR_R] = r;
             const int j = entry_index(ent);
             if (r2 < rcr2) {
                 float df[KR];
@@ -900,14 +902,24 @@ __device__ __forceinline__ void stage_network(const float* __restrict__ pg, cons
 // Backward of sorted atom m: partial forces of every list entry (Sec. II.C).  The atom's
 // pair rows arrive in 32-row pieces by double-buffered bulk copies: the copy of the next
 // piece is in flight while the current one is used.
+template <bool VIR>
 __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n, int m,
                                               const float* __restrict__ prm, float* __restrict__ wb,
                                               uint64_t* bars, uint32_t& par, const float* __restrict__ A,
                                               const float* __restrict__ duq, const float* __restrict__ qcs,
                                               const float4* __restrict__ fk, const float4* __restrict__ fr,
-                                              float4* __restrict__ fsum, int nmax, float selfc, float phibar) {
+                                              float4* __restrict__ fsum, int nmax, float selfc, float phibar,
+                                              double* __restrict__ vw) {
     const int lane = threadIdx.x & 31;
     const int S = a.lay.n_species;
+    // virial of this atom's entries: W -= r_ij (x) F_ij (the partial force F_ij acts on i, -F_ij
+    // on j); the radial part is symmetric (F_ij along u_ij)
+    float wv[9], wr[3];
+    if (VIR) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) wv[q] = 0.f;
+        wr[0] = wr[1] = wr[2] = 0.f;
+    }
     int* cum = reinterpret_cast<int*>(wb + WCUM);
     species_cum(a, off, n, m, S, cum);
     const int tot_a = cum[8 + S];
@@ -1002,6 +1014,15 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
                     Fv[u][0] = sv * d2.y;
                     Fv[u][1] = sv * d2.z;
                     Fv[u][2] = sv * d2.w;
+                    if (VIR) {
+                        const float rsv = r0 + u < cntc ? rw[4].z * sv : 0.f;   // r sv (row past the piece: 0)
+                        wv[0] = fmaf(-rsv * d2.y, d2.y, wv[0]);
+                        wv[4] = fmaf(-rsv * d2.z, d2.z, wv[4]);
+                        wv[8] = fmaf(-rsv * d2.w, d2.w, wv[8]);
+                        wr[0] = fmaf(-rsv * d2.y, d2.z, wr[0]);
+                        wr[1] = fmaf(-rsv * d2.y, d2.w, wr[1]);
+                        wr[2] = fmaf(-rsv * d2.z, d2.w, wr[2]);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1071,6 +1092,18 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
                     fy += Fy;
                     fz += Fz;
                     atomicAdd(&fsum[(size_t)__float_as_int(a5.z) * CG + lane], make_float4(-Fx, -Fy, -Fz, 0.f));
+                    if (VIR) {
+                        const float rr = 1.f / ir, vx = ux * rr, vy = uy * rr, vz = uz * rr;
+                        wv[0] = fmaf(-vx, Fx, wv[0]);
+                        wv[1] = fmaf(-vx, Fy, wv[1]);
+                        wv[2] = fmaf(-vx, Fz, wv[2]);
+                        wv[3] = fmaf(-vy, Fx, wv[3]);
+                        wv[4] = fmaf(-vy, Fy, wv[4]);
+                        wv[5] = fmaf(-vy, Fz, wv[5]);
+                        wv[6] = fmaf(-vz, Fx, wv[6]);
+                        wv[7] = fmaf(-vz, Fy, wv[7]);
+                        wv[8] = fmaf(-vz, Fz, wv[8]);
+                    }
                 }
             }
         }
@@ -1083,9 +1116,20 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
     // own force: network part plus the static electrostatic forces q F^k/q + F^r
     atomicAdd(&fsum[(size_t)m * CG + lane],
               make_float4(fx + fmaf(qc, kf.y, rf.y), fy + fmaf(qc, kf.z, rf.z), fz + fmaf(qc, kf.w, rf.w), 0.f));
+    if (VIR) {
+        // FP32 over the atom's entries, FP64 across atoms (this warp's slot, lane = candidate)
+        wv[1] += wr[0];
+        wv[3] += wr[0];
+        wv[2] += wr[1];
+        wv[6] += wr[1];
+        wv[5] += wr[2];
+        wv[7] += wr[2];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vw[q * CG + lane] += (double)wv[q];
+    }
 }
 
-template <int NW, bool TC>
+template <int NW, bool TC, bool VIR>
 __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     static_assert(!TC || NW == 8, "the tensor-core descriptor contraction uses 8 warps");
     extern __shared__ __align__(128) unsigned char bsm[];
@@ -1131,6 +1175,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     float4* fsum = a.sc.fsum + slot * a.sc.stride_n;
     float2* sk = a.sc.sk + slot * a.sc.stride_k;
     float2* skp = a.sc.skp + slot * a.sc.stride_p;
+    double* vacc = VIR ? a.sc.vir + slot * (size_t)NW * 9 * CG : nullptr;   // virial [NW][9][CG] FP64
     const int nmax = (int)(a.sc.stride_n / CG);
     const float selfc = a.mode == 1 ? -2.f * KE * a.alpha * 0.564189583547756287f : 0.f;
 
@@ -1147,6 +1192,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         const float* pg = a.pt + (size_t)grp * a.lay.total * CG;
         const int* so = a.spec_off + item.x * (MAX_SPECIES + 1);
         for (int i = threadIdx.x; i < n * CG; i += NW * 32) fsum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (VIR)
+            for (int i = threadIdx.x; i < NW * 9 * CG; i += NW * 32) vacc[i] = 0.0;
 
         // 1 forward, one species block at a time: descriptor with c^R, c^A staged, then the
         // network with its weights staged (two atoms per weight load)
@@ -1311,6 +1358,25 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         }
                         ek += 0.5 * (double)w * (Sr * Sr + Si * Si);
                         sk[(size_t)kl * CG + lane] = make_float2((float)((double)w * Sr), (float)((double)w * Si));
+                        if (VIR) {
+                            // W^k += e (I - (2 / (4 alpha^2) + 2 / k^2) k k^T), e = 2 k_e G |S|^2 (Sec. II.C)
+                            const float4 kv = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]);
+                            const double e = 0.5 * (double)w * (Sr * Sr + Si * Si);
+                            const float fac = 2.f / (4.f * a.alpha * a.alpha) + 2.f / (kv.x * kv.x + kv.y * kv.y + kv.z * kv.z);
+                            double* vw = vacc + (size_t)warp * 9 * CG + lane;
+                            const double xx = e * (double)(1.f - fac * kv.x * kv.x), yy = e * (double)(1.f - fac * kv.y * kv.y);
+                            const double zz = e * (double)(1.f - fac * kv.z * kv.z), xy = e * (double)(-fac * kv.x * kv.y);
+                            const double xz = e * (double)(-fac * kv.x * kv.z), yz = e * (double)(-fac * kv.y * kv.z);
+                            vw[0 * CG] += xx;
+                            vw[4 * CG] += yy;
+                            vw[8 * CG] += zz;
+                            vw[1 * CG] += xy;
+                            vw[3 * CG] += xy;
+                            vw[2 * CG] += xz;
+                            vw[6 * CG] += xz;
+                            vw[5 * CG] += yz;
+                            vw[7 * CG] += yz;
+                        }
                     }
                 }
             }
@@ -1440,6 +1506,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             for (int m = warp; m < n; m += NW) {
                 const float qi = qcs[(size_t)m * CG + lane];
                 float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
                 if (a.mode == 1) {
                     species_cum(a, off, n, m, S, cum);
                     const int tot_l = cum[S];
@@ -1459,11 +1526,22 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                             for (int u = 0; u < 4; ++u) {
                                 const int r = min(r0 + u, cntc - 1);
                                 const float4* rw = reinterpret_cast<const float4*>(tab + r * GR);
-                                const float4 d4 = rw[4];   // (B'u_z, j_real, -, -)
+                                const float4 d4 = rw[4];   // (B'u_z, j_real, r, -)
                                 d3[u] = rw[3];             // (j_desc, B, B'u_x, B'u_y)
                                 bz[u] = d4.x;
                                 const int j = __float_as_int(d4.y);
                                 qj[u] = (j >= 0 && r0 + u < cntc) ? qcs[(size_t)j * CG + lane] : 0.f;
+                                if (VIR) {
+                                    // pair virial: sum_j q_j B'(r) r u (x) u, with B' u from the row
+                                    const float4 d2 = rw[2];   // (f'_8, u)
+                                    const float t = qj[u] * d4.z;
+                                    sxx = fmaf(t * d3[u].z, d2.y, sxx);
+                                    syy = fmaf(t * d3[u].w, d2.z, syy);
+                                    szz = fmaf(t * d4.x, d2.w, szz);
+                                    sxy = fmaf(t * d3[u].z, d2.z, sxy);
+                                    sxz = fmaf(t * d3[u].z, d2.w, sxz);
+                                    syz = fmaf(t * d3[u].w, d2.w, syz);
+                                }
                             }
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
@@ -1477,6 +1555,20 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 }
                 // F^r_i = sum_j q_i q_j B'(r) u_ij (u_ij from i to j)
                 fr[(size_t)m * CG + lane] = make_float4(ph, qi * gx, qi * gy, qi * gz);
+                if (VIR && a.mode == 1) {
+                    // W^r -= 1/2 sum_j r_ij (x) F^r_ij over the full list (each pair seen twice)
+                    double* vw = vacc + (size_t)warp * 9 * CG + lane;
+                    const double h = -0.5 * (double)qi;
+                    vw[0 * CG] += h * (double)sxx;
+                    vw[4 * CG] += h * (double)syy;
+                    vw[8 * CG] += h * (double)szz;
+                    vw[1 * CG] += h * (double)sxy;
+                    vw[3 * CG] += h * (double)sxy;
+                    vw[2 * CG] += h * (double)sxz;
+                    vw[6 * CG] += h * (double)sxz;
+                    vw[5 * CG] += h * (double)syz;
+                    vw[7 * CG] += h * (double)syz;
+                }
                 const float4 kf = fk[(size_t)lane * nmax + m];
                 sphi += (double)ph + (double)kf.x;
                 er += 0.5 * (double)qi * (double)ph;
@@ -1501,8 +1593,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
             const float phibar = cst[CG + lane];
             for (int p = p0 + warp; p < p1; p += NW)
-                backward_atom(a, off, n, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum, nmax,
-                              selfc, phibar);
+                backward_atom<VIR>(a, off, n, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum,
+                                   nmax, selfc, phibar, vacc + (size_t)warp * 9 * CG);
         }
         __syncthreads();
 
@@ -1520,6 +1612,16 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     fo[2] = F.z;
                 }
                 if (a.charges) a.charges[(size_t)c * a.n_total + gi] = qcs[i];
+            }
+        }
+        if (VIR && warp == 1 && cand < a.n_cand) {
+            // W = sum over the warps' FP64 slots (entries, real space, k space), per candidate
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) t += vacc[((size_t)w * 9 + q) * CG + lane];
+                a.virial[((size_t)cand * a.n_struct + item.x) * 9 + q] = t;
             }
         }
         if (warp == 0 && cand < a.n_cand) {
@@ -1548,7 +1650,7 @@ static_assert(sizeof(double) * (8 + NSUMS) * CG + sizeof(float) * 4 * CG +
               "field windows and phase rows exceed shared memory");
 
 template <int NW>
-size_t item_smem(int nph_max, bool tc) {
+size_t item_smem(int nph_max, bool tc) {   // the same with and without the virial (its sums are in global scratch)
     const size_t head = sizeof(double) * (NW + NSUMS) * CG + sizeof(float) * 4 * CG;
     const size_t p1 = tc ? std::max((size_t)TC_BYTES, sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS))
                          : sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
@@ -1585,38 +1687,45 @@ size_t batch_item_smem(int warps, int nph_max, int contract) {
     return warps == 4 ? item_smem<4>(nph_max, false) : item_smem<8>(nph_max, tc);
 }
 
+namespace {
+template <int NW, bool TC, bool VIR>
+int blocks_per_sm_of(size_t smem) {
+    int nb = 0;
+    cudaFuncSetAttribute(k_batch_items<NW, TC, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<NW, TC, VIR>, NW * 32, smem) != cudaSuccess)
+        nb = 0;
+    return nb;
+}
+}  // namespace
+
 // The tensor-core form holds 512 tensor-memory columns per block: it runs only where its
 // shared memory keeps it to one block per SM (0 otherwise, like a shape that does not fit).
-int batch_item_blocks_per_sm(int warps, int nph_max, int contract) {
+int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial) {
     if (contract == BATCH_CONTRACT_BF16X3 && warps != 8) return 0;
     const size_t smem = batch_item_smem(warps, nph_max, contract);
-    int nb = 0;
-    if (warps == 4) {
-        cudaFuncSetAttribute(k_batch_items<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<4, false>, 128, smem) != cudaSuccess)
-            nb = 0;
-    } else if (contract == BATCH_CONTRACT_BF16X3) {
-        cudaFuncSetAttribute(k_batch_items<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8, true>, 256, smem) != cudaSuccess)
-            nb = 0;
+    int nb;
+    if (warps == 4) nb = virial ? blocks_per_sm_of<4, false, true>(smem) : blocks_per_sm_of<4, false, false>(smem);
+    else if (contract == BATCH_CONTRACT_BF16X3) {
+        nb = virial ? blocks_per_sm_of<8, true, true>(smem) : blocks_per_sm_of<8, true, false>(smem);
         if (nb > 1) nb = 0;
-    } else {
-        cudaFuncSetAttribute(k_batch_items<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<8, false>, 256, smem) != cudaSuccess)
-            nb = 0;
-    }
+    } else nb = virial ? blocks_per_sm_of<8, false, true>(smem) : blocks_per_sm_of<8, false, false>(smem);
     return nb;
 }
 
 void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract, int grid, cudaStream_t st_) {
     if (grid <= 0 || a.n_items <= 0) return;
     const size_t smem = batch_item_smem(warps, nph_max, contract);
-    if (warps == 4)
-        k_batch_items<4, false><<<grid, 128, smem, st_>>>(a);
-    else if (contract == BATCH_CONTRACT_BF16X3)
-        k_batch_items<8, true><<<grid, 256, smem, st_>>>(a);
-    else
-        k_batch_items<8, false><<<grid, 256, smem, st_>>>(a);
+    const bool vir = a.virial != nullptr;
+    if (warps == 4) {
+        if (vir) k_batch_items<4, false, true><<<grid, 128, smem, st_>>>(a);
+        else k_batch_items<4, false, false><<<grid, 128, smem, st_>>>(a);
+    } else if (contract == BATCH_CONTRACT_BF16X3) {
+        if (vir) k_batch_items<8, true, true><<<grid, 256, smem, st_>>>(a);
+        else k_batch_items<8, true, false><<<grid, 256, smem, st_>>>(a);
+    } else {
+        if (vir) k_batch_items<8, false, true><<<grid, 256, smem, st_>>>(a);
+        else k_batch_items<8, false, false><<<grid, 256, smem, st_>>>(a);
+    }
 }
 
 }  // namespace qnep

@@ -4,11 +4,13 @@
 //
 //   qnep_snes_sample   z_k = mu + sigma * s_k                         [C][P]
 //   qnep_batch_loss    D_e, D_f (energy RMSE per atom, force RMSE per component), |z|_1,
-//                      |z|_2^2 and L = l_e D_e + l_f D_f + l_1 |z|_1 + l_2 |z|_2^2 per candidate
+//                      |z|_2^2 and L = l_e D_e + l_f D_f + l_1 |z|_1 + l_2 |z|_2^2 per candidate;
+//                      qnep_batch_loss_v adds D_v (virial RMSE per atom over the six
+//                      independent components) and l_v D_v
 //   qnep_snes_update   rank the losses, rank-based utilities, natural-gradient step on
 //                      (mu, sigma)
-// The batched call feeds energies and forces; its corrected charges meet the total-charge
-// target exactly and it computes neither virials nor BEC, so the loss has no D_Q, D_v, D_Z.
+// The batched call feeds energies, forces and virials; its corrected charges meet the
+// total-charge target exactly and it computes no BEC, so the loss has no D_Q and no D_Z.
 //
 // Loss: the force term is the large one (C x N x 3 floats, HBM bound): for every candidate a
 // one-wave set of blocks walks the force stream in 2048-float chunks (coalesced loads, 8 per
@@ -58,12 +60,15 @@ k_snes_sample(long long total, int n_params, const float* __restrict__ mu, const
 }
 
 // blockIdx.y = candidate; blockIdx.x < n_fblocks: every n_fblocks-th chunk of the force stream;
-// == n_fblocks: the energy term and the parameter norms.
+// == n_fblocks: the energy and virial terms and the parameter norms.  terms[ts c + k]: D_e (0),
+// sum of squared force errors (1, rooted by k_loss_finalize), D_v (2, ts = 5 only), |z|_1, |z|_2^2
+// (the last two).
 __global__ void __launch_bounds__(kThreads)
 k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n_fblocks,
              const double* __restrict__ energy, const float* __restrict__ forces,
              const double* __restrict__ energy_ref, const float* __restrict__ forces_ref,
-             const float* __restrict__ params, int n_params, double* __restrict__ terms) {
+             const double* __restrict__ virial, const double* __restrict__ virial_ref,
+             const float* __restrict__ params, int n_params, int ts, double* __restrict__ terms) {
     __shared__ double red[kThreads / 32];
     __shared__ float redf[kThreads / 32];
     const int c = blockIdx.y;
@@ -93,17 +98,28 @@ k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < kThreads / 32; ++w) t += (double)redf[w];
-            atomicAdd(terms + 4 * c + 1, t);
+            atomicAdd(terms + ts * c + 1, t);
         }
         return;
     }
-    double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0;
+    double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0, sv = 0.0;
     for (int s = threadIdx.x; s < n_struct; s += kThreads) {
         const int n_s = off[s + 1] - off[s];
         if (n_s > 0) {
             const double de = (energy[(long long)c * n_struct + s] - energy_ref[s]) / (double)n_s;
             se += de * de;
             cnt += 1.0;
+            if (virial) {
+                // the six independent components xx, yy, zz, xy, yz, zx of the 3x3 virial, per atom
+                const double* w = virial + ((long long)c * n_struct + s) * 9;
+                const double* wr = virial_ref + (long long)s * 9;
+                const int comp[6] = {0, 4, 8, 1, 5, 2};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const double dv = (w[comp[q]] - wr[comp[q]]) / (double)n_s;
+                    sv += dv * dv;
+                }
+            }
         }
     }
     if (params)
@@ -116,19 +132,22 @@ k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n
     cnt = block_sum(cnt, red);
     l1 = block_sum(l1, red);
     l2 = block_sum(l2, red);
+    sv = block_sum(sv, red);
     if (threadIdx.x == 0) {
-        terms[4 * c + 0] = cnt > 0.0 ? sqrt(se / cnt) : 0.0;
-        terms[4 * c + 2] = l1;
-        terms[4 * c + 3] = l2;
+        terms[ts * c + 0] = cnt > 0.0 ? sqrt(se / cnt) : 0.0;
+        if (ts == 5) terms[ts * c + 2] = (virial && cnt > 0.0) ? sqrt(sv / (6.0 * cnt)) : 0.0;
+        terms[ts * c + ts - 2] = l1;
+        terms[ts * c + ts - 1] = l2;
     }
 }
 
-__global__ void k_loss_finalize(int n_cand, long long n_force, double we, double wf, double w1, double w2,
-                                double* __restrict__ terms, double* __restrict__ loss) {
+__global__ void k_loss_finalize(int n_cand, long long n_force, double we, double wf, double wv, double w1, double w2,
+                                int ts, double* __restrict__ terms, double* __restrict__ loss) {
     for (int c = threadIdx.x; c < n_cand; c += blockDim.x) {
-        const double df = n_force > 0 ? sqrt(terms[4 * c + 1] / (double)n_force) : 0.0;
-        terms[4 * c + 1] = df;
-        loss[c] = we * terms[4 * c + 0] + wf * df + w1 * terms[4 * c + 2] + w2 * terms[4 * c + 3];
+        double* t = terms + ts * c;
+        const double df = n_force > 0 ? sqrt(t[1] / (double)n_force) : 0.0;
+        t[1] = df;
+        loss[c] = we * t[0] + wf * df + (ts == 5 ? wv * t[2] : 0.0) + w1 * t[ts - 2] + w2 * t[ts - 1];
     }
 }
 
@@ -197,16 +216,19 @@ extern "C" qnep_status qnep_snes_sample(int n_candidates, int n_params, const fl
     return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
 }
 
-extern "C" qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
-                                      const double* energy, const float* forces, const double* energy_ref,
-                                      const float* forces_ref, const float* params, int n_params,
-                                      const qnep_loss_weights* w, double* loss, double* terms, void* stream) {
+namespace {
+qnep_status batch_loss_impl(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                            const double* energy, const float* forces, const double* virial,
+                            const double* energy_ref, const float* forces_ref, const double* virial_ref,
+                            const float* params, int n_params, double we, double wf, double wv, double w1, double w2,
+                            int ts, double* loss, double* terms, void* stream) {
     if (n_candidates < 1 || n_candidates > 65535 || n_struct < 1 || n_total < 0 || !atom_offsets || !energy ||
-        !energy_ref || !w || !loss || !terms)
+        !energy_ref || !loss || !terms)
         return QNEP_ERR_ARG;
     if ((forces == nullptr) != (forces_ref == nullptr)) return QNEP_ERR_ARG;
+    if ((virial == nullptr) != (virial_ref == nullptr)) return QNEP_ERR_ARG;
     if (params && n_params < 1) return QNEP_ERR_ARG;
-    if (!std::isfinite(w->energy) || !std::isfinite(w->force) || !std::isfinite(w->l1) || !std::isfinite(w->l2))
+    if (!std::isfinite(we) || !std::isfinite(wf) || !std::isfinite(wv) || !std::isfinite(w1) || !std::isfinite(w2))
         return QNEP_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long n_force = forces ? 3LL * n_total : 0;
@@ -216,14 +238,36 @@ extern "C" qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long per_cand = ((long long)(sms > 0 ? sms : 152) * 8 + n_candidates - 1) / n_candidates;
     const int n_fblocks = (int)(chunks < per_cand ? chunks : per_cand);
-    if (cudaMemsetAsync(terms, 0, sizeof(double) * 4 * (size_t)n_candidates, st) != cudaSuccess)
+    if (cudaMemsetAsync(terms, 0, sizeof(double) * ts * (size_t)n_candidates, st) != cudaSuccess)
         return QNEP_ERR_CUDA;
     dim3 grid((unsigned)(n_fblocks + 1), (unsigned)n_candidates);
     k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, n_force, n_fblocks, energy, forces, energy_ref,
-                                            forces_ref, params, params ? n_params : 0, terms);
+                                            forces_ref, virial, virial_ref, params, params ? n_params : 0, ts, terms);
     if (cudaGetLastError() != cudaSuccess) return QNEP_ERR_CUDA;
-    k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, w->energy, w->force, w->l1, w->l2, terms, loss);
+    k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, we, wf, wv, w1, w2, ts, terms, loss);
     return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" qnep_status qnep_batch_loss(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                                      const double* energy, const float* forces, const double* energy_ref,
+                                      const float* forces_ref, const float* params, int n_params,
+                                      const qnep_loss_weights* w, double* loss, double* terms, void* stream) {
+    if (!w) return QNEP_ERR_ARG;
+    return batch_loss_impl(n_candidates, n_struct, atom_offsets, n_total, energy, forces, nullptr, energy_ref,
+                           forces_ref, nullptr, params, n_params, w->energy, w->force, 0.0, w->l1, w->l2, 4, loss,
+                           terms, stream);
+}
+
+extern "C" qnep_status qnep_batch_loss_v(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                                        const double* energy, const float* forces, const double* virial,
+                                        const double* energy_ref, const float* forces_ref, const double* virial_ref,
+                                        const float* params, int n_params, const qnep_loss_weights_v* w,
+                                        double* loss, double* terms, void* stream) {
+    if (!w) return QNEP_ERR_ARG;
+    return batch_loss_impl(n_candidates, n_struct, atom_offsets, n_total, energy, forces, virial, energy_ref,
+                           forces_ref, virial_ref, params, n_params, w->energy, w->force, w->virial, w->l1, w->l2, 5,
+                           loss, terms, stream);
 }
 
 extern "C" qnep_status qnep_snes_update(int n_candidates, int n_params, const double* loss, const float* noise,

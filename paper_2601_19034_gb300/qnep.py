@@ -416,13 +416,24 @@ class QNEPBatch:
         self._desc = (off, bx)   # kept alive: the library reads them on every call
         return off, bx
 
-    def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True) -> dict:
+    def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True, virial=False) -> dict:
         out = {"energy": torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)}
         if forces:
             out["forces"] = torch.empty(self.n_cand, n_total, 3, dtype=torch.float32, device=device)
         if charges:
             out["charges"] = torch.empty(self.n_cand, n_total, dtype=torch.float32, device=device)
+        if virial:
+            out["virial"] = torch.empty(self.n_cand, n_struct, 3, 3, dtype=torch.float64, device=device)
         return out
+
+    @staticmethod
+    def _outputs_c(out: dict) -> _lib.BatchOutputsC:
+        def ptr(name):
+            t = out.get(name)
+            if t is None:
+                return None
+            return t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data
+        return _lib.BatchOutputsC(ptr("energy"), ptr("forces"), ptr("charges"), ptr("virial"))
 
     def _args(self, positions, types, offsets, boxes, out, stream):
         assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
@@ -440,16 +451,43 @@ class QNEPBatch:
 
     def compute_into(self, positions, types, offsets, boxes, out: dict, stream=None):
         """Enqueue one batched call writing into ``out`` (from ``outputs``); no synchronisation."""
+        if "virial" in out:
+            args = self._args(positions, types, offsets, boxes, out, stream)
+            oc = self._outputs_c(out)
+            _lib.check(self.lib.qnep_batch_compute_outputs(*args[:7], ctypes.byref(oc)), batch=self.handle)
+            return
         _lib.check(self.lib.qnep_batch_compute(*self._args(positions, types, offsets, boxes, out, stream)),
                    batch=self.handle)
+
+    def compute_host(self, positions, types, offsets, boxes, out: dict, stream=None):
+        """End-to-end call on host buffers: positions [N, 3] float32 and types [N] int32 (numpy
+        arrays or pinned CPU tensors) in, every array of ``out`` (host energy [C, S] float64,
+        optional forces [C, N, 3], charges [C, N], virial [C, S, 3, 3]) filled, synchronised."""
+        off, bx = self._describe(offsets, boxes)
+
+        def hptr(a):
+            return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+        for name, a in list(out.items()) + [("positions", positions), ("types", types)]:
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.is_contiguous(), name
+            else:
+                assert a.flags["C_CONTIGUOUS"], name
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        oc = self._outputs_c(out)
+        _lib.check(self.lib.qnep_batch_compute_host(self.handle, len(off) - 1, off.ctypes.data, hptr(positions),
+                                                    hptr(types), bx.ctypes.data, ctypes.c_void_p(stream),
+                                                    ctypes.byref(oc)), batch=self.handle)
 
     def sync_status(self) -> int:
         return self.lib.qnep_batch_sync_status(self.handle)
 
-    def compute(self, positions, types, offsets, boxes, retries: int = 3, forces=True, charges=True) -> dict:
+    def compute(self, positions, types, offsets, boxes, retries: int = 3, forces=True, charges=True,
+                virial=False) -> dict:
         """Batched call with a status check; grows the neighbour lists and retries on overflow."""
         n_struct = len(offsets) - 1
-        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges)
+        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges, virial)
         for _ in range(retries + 1):
             self.compute_into(positions, types, offsets, boxes, out)
             st = self.sync_status()
@@ -582,3 +620,32 @@ def stack_structures(systems) -> tuple:
     off[1:] = np.cumsum([s.n_atoms for s in systems])
     boxes = np.stack([np.asarray(s.box, dtype=np.float64).reshape(3, 3) for s in systems])
     return pos, typ, off, boxes
+
+
+def batch_loss_v(energy, forces, virial, energy_ref, forces_ref, virial_ref, atom_offsets, params=None,
+                 weights=(1.0, 1.0, 1.0, 0.0, 0.0), loss: torch.Tensor = None, terms: torch.Tensor = None,
+                 stream=None):
+    """Per-candidate loss L [C] and terms [C, 5] = (D_e, D_f, D_v, |z|_1, |z|_2^2) on the device.
+
+    ``virial`` [C, S, 3, 3] and ``virial_ref`` [S, 3, 3] float64 (both or neither);
+    ``weights`` = (l_e, l_f, l_v, l_1, l_2).
+    """
+    c, s = energy.shape
+    n_total = int(forces_ref.shape[0]) if forces_ref is not None else 0
+    dev = energy.device
+    if loss is None:
+        loss = torch.empty(c, dtype=torch.float64, device=dev)
+    if terms is None:
+        terms = torch.empty(c, 5, dtype=torch.float64, device=dev)
+    assert atom_offsets.is_cuda and atom_offsets.dtype == torch.int32 and atom_offsets.numel() == s + 1
+    w = _lib.LossWeightsVC(*[float(x) for x in weights])
+
+    def ptr(t):
+        return t.data_ptr() if t is not None else None
+
+    n_par = int(params.shape[1]) if params is not None else 0
+    _lib.check(_lib.load().qnep_batch_loss_v(c, s, atom_offsets.data_ptr(), n_total, energy.data_ptr(), ptr(forces),
+                                             ptr(virial), energy_ref.data_ptr(), ptr(forces_ref), ptr(virial_ref),
+                                             ptr(params), n_par, ctypes.byref(w), loss.data_ptr(), terms.data_ptr(),
+                                             _stream(energy, stream)))
+    return loss, terms

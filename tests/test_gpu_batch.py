@@ -41,13 +41,13 @@ def _llzo(reps, seed, sigma=0.1):
                      wl.LLZO_SPECIES)
 
 
-def _run_batch(systems, hp, params, elec, dev, warps=8, order="largest_first", contract="fp32"):
+def _run_batch(systems, hp, params, elec, dev, warps=8, order="largest_first", contract="fp32", virial=False):
     from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
     pos, typ, off, boxes = stack_structures(systems)
     b = QNEPBatch(hp, params, elec)
     b.set_config(warps, order)
     b.set_contraction(contract)
-    out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes)
+    out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes, virial=virial)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
     b.close()
@@ -233,15 +233,111 @@ def test_full_llzo_batch_tensor_core_contraction(dev):
     oracle at the FP32 tolerances, and every pair against the FP32 contraction (energy per atom
     1e-6 eV, forces 1e-4 eV/A, charges 2e-6 e)."""
     systems, hp, params, elec = wl.config_llzo_batch()
-    res_tc, off = _run_batch(systems, hp, params, elec, dev, contract="bf16x3")
+    res_tc, off = _run_batch(systems, hp, params, elec, dev, contract="bf16x3", virial=True)
     assert np.isfinite(res_tc["energy"]).all() and np.isfinite(res_tc["forces"]).all()
+    assert np.isfinite(res_tc["virial"]).all()
     sizes = np.diff(off)
     big = int(np.argmax(sizes))
     small = int(np.argmin(sizes))
     for s, c in ((big, 62), (small, 1), (int(np.argsort(sizes)[len(sizes) // 2]), 31)):
         _check_pair(res_tc, off, systems, s, c, hp, params, elec)
+        _check_virial(res_tc, off, systems, s, c, hp, params, elec)
     res_fp, _ = _run_batch(systems, hp, params, elec, dev, contract="fp32")
     de = np.abs(res_tc["energy"] - res_fp["energy"]) / sizes[None, :]
     assert de.max() <= TOL["e"], de.max()
     assert np.abs(res_tc["forces"] - res_fp["forces"]).max() <= TOL["f"]
     assert np.abs(res_tc["charges"] - res_fp["charges"]).max() <= TOL["q"]
+
+
+def _check_virial(res, off, systems, s, c, hp, params, elec):
+    sysm = systems[s]
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params[c], elec,
+                               want_bec=False)
+    dw = np.abs(res["virial"][c, s] - ref["virial"]).max() / sysm.n_atoms
+    assert dw <= 1e-5, (s, c, dw)
+
+
+@pytest.mark.parametrize("contract", ["fp32", "bf16x3"])
+def test_batched_virial_against_oracle(dev, contract):
+    """The per-(candidate, structure) virial (entries, static real space, W^k) against the oracle's
+    strain derivative, 1e-5 eV per atom; energies, forces and charges unchanged by asking for it."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    systems = [_llzo((1, 1, 1), 31), _llzo((2, 1, 1), 32), _llzo((1, 2, 2), 33)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(34), n_candidates=33)
+    elec = wl.Elec(mode=1, kind="ewald", q_total=0.3)
+    pos, typ, off, boxes = stack_structures(systems)
+    b = QNEPBatch(hp, params, elec)
+    b.set_contraction(contract)
+    pd, td = torch.tensor(pos, device=dev), torch.tensor(typ, device=dev)
+    out_v = b.compute(pd, td, off, boxes, virial=True)
+    out = b.compute(pd, td, off, boxes)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out_v.items()}
+    b.close()
+    n = np.diff(off)
+    assert np.abs(res["energy"] - out["energy"].cpu().numpy()).max() / n.min() <= 1e-9
+    assert np.abs(res["forces"] - out["forces"].cpu().numpy()).max() <= 1e-5
+    for s_, c in ((0, 0), (1, 32), (2, 7)):
+        _check_virial(res, off, systems, s_, c, hp, params, elec)
+        _check_pair(res, off, systems, s_, c, hp, params, elec)
+    # the virial of every pair is symmetric to the FP32 rounding of its parts
+    w = res["virial"]
+    assert np.abs(w - np.swapaxes(w, 2, 3)).max() / n.min() <= 1e-5
+
+
+def test_batched_virial_mode2_water_and_perovskite(dev):
+    """k-space-only electrostatics (2-species water) and mode 1 on 3-species BaTiO3 cells."""
+    for systems, hp, elec, seed in (
+            ([wl.water_box(4, seed=41), wl.water_box(5, seed=42)], wl.HParams(n_species=2),
+             wl.Elec(mode=2, kind="ewald", q_total=0.5), 43),
+            ([wl.batio3_supercell(2, seed=44), wl.batio3_supercell(3, seed=45)], wl.HParams(n_species=3),
+             wl.Elec(mode=1, kind="ewald", q_total=-0.4), 46)):
+        params = wl.random_params(hp, np.random.default_rng(seed), n_candidates=3)
+        from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+        pos, typ, off, boxes = stack_structures(systems)
+        b = QNEPBatch(hp, params, elec)
+        out = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes, virial=True)
+        torch.cuda.synchronize()
+        res = {k: v.cpu().numpy() for k, v in out.items()}
+        b.close()
+        for s_ in range(len(systems)):
+            _check_virial(res, off, systems, s_, s_ % 3, hp, params, elec)
+
+
+def test_host_buffer_call_equals_device_call(dev):
+    """qnep_batch_compute_host: host inputs in, every output back (pinned and pageable host memory),
+    equal to the device-buffer call of the same batch; then a new batch shape on the same object."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    systems = [_llzo((1, 1, 1), 51), _llzo((2, 1, 1), 52)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(53), n_candidates=5)
+    elec = wl.Elec(mode=1, kind="ewald")
+    pos, typ, off, boxes = stack_structures(systems)
+    b = QNEPBatch(hp, params, elec)
+    b.set_contraction("bf16x3")
+    ref = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes, virial=True)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    c, s_, n = 5, len(systems), int(off[-1])
+    for pinned in (True, False):
+        def h(shape, dtype):
+            t = torch.full(shape, float("nan") if dtype.is_floating_point else 0, dtype=dtype)
+            return t.pin_memory() if pinned else t.numpy()
+        out = {"energy": h((c, s_), torch.float64), "forces": h((c, n, 3), torch.float32),
+               "charges": h((c, n), torch.float32), "virial": h((c, s_, 3, 3), torch.float64)}
+        ph = torch.tensor(pos).pin_memory() if pinned else np.ascontiguousarray(pos)
+        th = torch.tensor(typ).pin_memory() if pinned else np.ascontiguousarray(typ)
+        b.compute_host(ph, th, off, boxes, out)
+        for k in out:
+            got = out[k].numpy() if isinstance(out[k], torch.Tensor) else out[k]
+            assert np.array_equal(got, ref[k]) or np.abs(got - ref[k]).max() <= (1e-9 if k == "energy" else 1e-5), k
+    # a larger batch on the same object: the host-buffer workspaces grow
+    systems2 = systems + [_llzo((1, 2, 2), 54)]
+    pos2, typ2, off2, boxes2 = stack_structures(systems2)
+    out2 = {"energy": np.zeros((c, 3)), "forces": np.zeros((c, int(off2[-1]), 3), np.float32)}
+    b.compute_host(pos2, typ2, off2, boxes2, out2)
+    _check_pair({"energy": out2["energy"], "forces": out2["forces"],
+                 "charges": b.compute(torch.tensor(pos2, device=dev), torch.tensor(typ2, device=dev), off2,
+                                      boxes2)["charges"].cpu().numpy()}, off2, systems2, 2, 4, hp, params, elec)
+    b.close()

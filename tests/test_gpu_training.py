@@ -188,3 +188,37 @@ def test_argument_errors(dev):
     assert lib.qnep_batch_loss(1, 1, off.data_ptr(), 0, d.data_ptr(), None, d.data_ptr(), None, None, 0,
                                bad, d.data_ptr(), d.data_ptr(), st) == _lib.QNEP_ERR_ARG
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("sizes", [(192, 0, 384, 7, 1536), (300, 300)])
+def test_loss_with_virial_matches_oracle(dev, sizes):
+    """D_v (virial RMSE per atom over the six independent components) and the weighted sum."""
+    from paper_2601_19034_gb300.qnep import batch_loss_v
+    rng = np.random.default_rng(10 + len(sizes))
+    c, p = 7, 301
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    n, s = int(off[-1]), len(sizes)
+    e = rng.normal(size=(c, s)) * 50
+    e_ref = rng.normal(size=s) * 50
+    f = rng.normal(size=(c, n, 3)).astype(np.float32)
+    f_ref = rng.normal(size=(n, 3)).astype(np.float32)
+    w = rng.normal(size=(c, s, 3, 3)) * 30
+    w_ref = rng.normal(size=(s, 3, 3)) * 30
+    z = rng.normal(size=(c, p)).astype(np.float32)
+    weights = (1.0, 0.5, 0.3, 0.01, 0.002)
+    loss, terms = batch_loss_v(_t(e, dev), _t(f, dev), _t(w, dev), _t(e_ref, dev), _t(f_ref, dev), _t(w_ref, dev),
+                               _t(off, dev), _t(z, dev), weights)
+    terms = terms.cpu().numpy()
+    ref = tr.loss_terms_v(e, f.astype(np.float64), w, e_ref, f_ref.astype(np.float64), w_ref, off,
+                          z.astype(np.float64))
+    np.testing.assert_allclose(terms[:, 0], ref[0], rtol=1e-12)
+    np.testing.assert_allclose(terms[:, 1], ref[1], rtol=2e-6)
+    np.testing.assert_allclose(terms[:, 2], ref[2], rtol=1e-12)
+    np.testing.assert_allclose(terms[:, 3], ref[3], rtol=1e-12)
+    np.testing.assert_allclose(terms[:, 4], ref[4], rtol=1e-12)
+    np.testing.assert_allclose(loss.cpu().numpy(), tr.loss_v(ref, *weights), rtol=2e-6)
+    # no virial given: D_v = 0 and the rest unchanged
+    loss0, terms0 = batch_loss_v(_t(e, dev), _t(f, dev), None, _t(e_ref, dev), _t(f_ref, dev), None, _t(off, dev),
+                                 _t(z, dev), weights)
+    assert np.all(terms0.cpu().numpy()[:, 2] == 0.0)
+    np.testing.assert_allclose(terms0.cpu().numpy()[:, [0, 1, 3, 4]], terms[:, [0, 1, 3, 4]], rtol=1e-12)

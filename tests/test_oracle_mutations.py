@@ -258,3 +258,18 @@ def test_energy_error_per_structure_not_per_atom(monkeypatch):
         return np.sqrt((de ** 2).mean(1)), d_f, l1, l2
     monkeypatch.setattr(training, "loss_terms", wrong)
     _fails(t_tr.test_loss_closed_forms)
+
+
+def test_virial_rmse_over_all_nine_components(monkeypatch):
+    """Averaging over all nine components (lower triangle counted too) fails the six-component pins."""
+    def wrong(virial, virial_ref, atom_offsets):
+        off = np.asarray(atom_offsets, dtype=np.int64)
+        n_s = np.diff(off)
+        has = n_s > 0
+        w = np.asarray(virial, dtype=np.float64).reshape(-1, len(n_s), 3, 3)
+        wr = np.asarray(virial_ref, dtype=np.float64).reshape(len(n_s), 3, 3)
+        dv = (w[:, has] - wr[None, has]) / n_s[None, has, None, None]
+        return np.sqrt((dv ** 2).reshape(w.shape[0], -1).mean(axis=1))
+    monkeypatch.setattr(training, "virial_rmse", wrong)
+    with pytest.raises(AssertionError):
+        t_tr.test_virial_rmse_closed_forms()

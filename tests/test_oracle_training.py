@@ -95,3 +95,47 @@ def test_snes_minimises_separable_quadratic():
         mu, sigma = tr.update(mu, sigma, s, f)
     assert np.abs(mu - target).max() < 1e-3
     assert sigma.max() < 1e-3
+
+
+def _virial_case(seed=3, c=4, sizes=(5, 0, 2, 9)):
+    rng = np.random.default_rng(seed)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    w = rng.normal(size=(c, len(sizes), 3, 3)) * 20
+    w_ref = rng.normal(size=(len(sizes), 3, 3)) * 20
+    return w, w_ref, off
+
+
+def test_virial_rmse_matches_brute_force():
+    w, w_ref, off = _virial_case()
+    d_v = tr.virial_rmse(w, w_ref, off)
+    for c in range(w.shape[0]):
+        acc, cnt = 0.0, 0
+        for s in range(len(off) - 1):
+            n_s = off[s + 1] - off[s]
+            if n_s == 0:
+                continue
+            for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2)):
+                acc += ((w[c, s, a, b] - w_ref[s, a, b]) / n_s) ** 2
+                cnt += 1
+        assert abs(d_v[c] - math.sqrt(acc / cnt)) < 1e-12
+
+
+def test_virial_rmse_closed_forms():
+    """Per-atom offsets: all components -> |v|; the three off-diagonal (upper) ones -> |v|/sqrt(2);
+    the lower triangle only (not one of the six read) -> 0."""
+    _, w_ref, off = _virial_case(seed=4)
+    n_s = np.diff(off).astype(np.float64)
+    v = np.array([0.2, -1.3, 0.0, 0.05])
+    all_c = w_ref[None] + v[:, None, None, None] * n_s[None, :, None, None]
+    np.testing.assert_allclose(tr.virial_rmse(all_c, w_ref, off), np.abs(v), atol=1e-12)
+    upper = np.zeros((3, 3))
+    upper[0, 1] = upper[1, 2] = upper[0, 2] = 1.0
+    off_c = w_ref[None] + v[:, None, None, None] * n_s[None, :, None, None] * upper
+    np.testing.assert_allclose(tr.virial_rmse(off_c, w_ref, off), np.abs(v) / math.sqrt(2.0), atol=1e-12)
+    low_c = w_ref[None] + v[:, None, None, None] * n_s[None, :, None, None] * upper.T
+    np.testing.assert_allclose(tr.virial_rmse(low_c, w_ref, off), 0.0, atol=1e-12)
+    e, f, e_ref, f_ref, off2, z = _case(seed=2, c=4)
+    terms = tr.loss_terms_v(e_ref[None].repeat(4, 0), f_ref[None].repeat(4, 0), None, e_ref, f_ref, None, off2, z)
+    np.testing.assert_allclose(terms[2], 0.0)
+    np.testing.assert_allclose(tr.loss_v(terms, 1.0, 1.0, 0.3, 0.05, 0.01),
+                               0.05 * np.abs(z).sum(1) + 0.01 * (z ** 2).sum(1), atol=1e-12)
