@@ -224,6 +224,21 @@ qnep_status qnep_debug_set_status(qnep_model* m, unsigned int bits);
 /* Change the neighbour-list capacities (entries per atom); 0 keeps the value. */
 qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
 
+/* Verlet skin for repeated force calls on moving atoms (MD; warp-per-atom kernels).  With
+ * skin > 0 (A) the model keeps candidate lists with cutoff r_list + skin (r_list = the
+ * larger of the radial descriptor and real-space cutoffs) and rebuilds them (cell binning and
+ * search) only when an atom has moved more than skin / 2 since the last build; otherwise the
+ * force call filters the kept candidates by the current distances, which gives the same
+ * neighbours as a fresh search (sums in another order: FP32 rounding).  The test and the
+ * choice run on the device, so a call needs no host synchronisation (it can be captured in a
+ * CUDA graph once the lists exist).  A new box, atom count or capacity forces a rebuild; atom
+ * types must not change while a list is kept (call qnep_set_skin again to force a rebuild).
+ * skin = 0 (the default) rebuilds the lists at every call.  QNEP_ERR_ARG for a negative,
+ * non-finite or > 5 A skin.  List overflow is reported as for qnep_compute.
+ * qnep_skin_rebuilds: the number of rebuilds so far (synchronises the device). */
+qnep_status qnep_set_skin(qnep_model* m, double skin);
+qnep_status qnep_skin_rebuilds(qnep_model* m, unsigned int* count);
+
 /* Kernel family for the per-atom stages: QNEP_PATH_AUTO picks the warp-per-atom
  * kernels (the faster family at every size measured, 40 atoms to 1 M atoms);
  * QNEP_PATH_WARP / QNEP_PATH_THREAD force one family (both compute the same

@@ -109,6 +109,10 @@ def _declare(lib):
     lib.qnep_set_path.restype = i
     lib.qnep_set_capacity.argtypes = [p, i, i]
     lib.qnep_set_capacity.restype = i
+    lib.qnep_set_skin.argtypes = [p, ctypes.c_double]
+    lib.qnep_set_skin.restype = i
+    lib.qnep_skin_rebuilds.argtypes = [p, ctypes.POINTER(ctypes.c_uint)]
+    lib.qnep_skin_rebuilds.restype = i
     lib.qnep_destroy.argtypes = [p]
     lib.qnep_destroy.restype = None
     lib.qnep_status_string.argtypes = [i]

@@ -86,6 +86,18 @@ struct qnep_model {
     int* io_types = nullptr;
     float* io_out[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double* io_scalars = nullptr;
+    // Verlet skin (warp-per-atom path): candidate lists [n][skin_cap] with cutoff r_list + skin,
+    // reused while no atom has moved more than skin / 2 (decided on the device)
+    float skin = 0.f;
+    bool skin_valid = false;               // a list built for this (n, box) exists
+    int skin_n = 0, skin_cap = 0, skin_n_alloc = 0, skin_cap_alloc = 0;
+    double skin_box[9]{};
+    int* skin_gate = nullptr;
+    unsigned int* skin_rebuilds = nullptr;
+    int* skin_list = nullptr;
+    int* skin_cnt = nullptr;
+    float4* skin_sref4 = nullptr;
+    float* skin_xref = nullptr;
     // second stream for the real-space kernel (runs beside the structure factor)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -482,6 +494,23 @@ qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular) {
     if (!m || cap_list < 0 || cap_angular < 0) return QNEP_ERR_ARG;
     if (cap_list) m->cap_list = cap_list;
     if (cap_angular) m->cap_ang = cap_angular;
+    m->skin_valid = false;   // the skin lists are sized from the list capacity
+    return QNEP_OK;
+}
+
+qnep_status qnep_set_skin(qnep_model* m, double skin) {
+    if (!m || !(skin >= 0) || !std::isfinite(skin) || skin > 5.0) return QNEP_ERR_ARG;
+    m->skin = (float)skin;
+    m->skin_valid = false;
+    return QNEP_OK;
+}
+
+qnep_status qnep_skin_rebuilds(qnep_model* m, unsigned int* count) {
+    if (!m || !count) return QNEP_ERR_ARG;
+    *count = 0;
+    if (!m->skin_rebuilds) return QNEP_OK;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(count, m->skin_rebuilds, sizeof(unsigned int), cudaMemcpyDeviceToHost));
     return QNEP_OK;
 }
 
@@ -547,15 +576,57 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
     // the structure-factor sums (Ewald) or the charge mesh (PPPM) start from zero
     double2* zbuf = ewald ? m->tab.S : (pppm ? reinterpret_cast<double2*>(m->pm.rho) : nullptr);
     const int zcount = ewald ? m->tab.nk : (pppm ? (int)(m->pm.nreal / 4) : 0);
-    launch_bin(positions, types, n, g, m->pos4, m->cell_of, m->cell_count, m->cell_start, m->cell_fill, m->cell_atoms,
-               m->spos4, m->sidx, m->d_acc, zbuf, zcount, st);
+    const bool use_skin = m->skin > 0.f && coop;
+    if (use_skin) {
+        // candidate capacity: the list capacity scaled by the volume of the longer cutoff
+        const float rcl = g.rc_list, rs = rcl + m->skin;
+        const int cap_s = ((int)((double)cl * (rs * rs * rs) / (rcl * rcl * rcl)) + 31) / 32 * 32;
+        if (!m->skin_gate) {
+            CK(cudaMalloc((void**)&m->skin_gate, sizeof(int)));
+            CK(cudaMalloc((void**)&m->skin_rebuilds, sizeof(unsigned int)));
+            CK(cudaMemset(m->skin_rebuilds, 0, sizeof(unsigned int)));
+        }
+        if (n > m->skin_n_alloc || cap_s > m->skin_cap_alloc) {
+            const int na = std::max(n, m->skin_n_alloc), nc = std::max(cap_s, m->skin_cap_alloc);
+            CK(cudaStreamSynchronize(st));
+            CK(grow(&m->skin_list, (size_t)na * nc));
+            CK(grow(&m->skin_cnt, (size_t)na));
+            CK(grow(&m->skin_sref4, (size_t)na));
+            CK(grow(&m->skin_xref, (size_t)3 * na));
+            m->skin_n_alloc = na;
+            m->skin_cap_alloc = nc;
+            m->skin_valid = false;
+        }
+        const bool force = !m->skin_valid || m->skin_n != n || m->skin_cap != cap_s ||
+                           std::memcmp(m->skin_box, box, sizeof(double) * 9) != 0;
+        // cells no smaller than r_list + skin, so the 27-cell search reaches every candidate
+        Geom gk = g;
+        gk.ncells = 1;
+        for (int d = 0; d < 3; ++d) {
+            if (g.L[d] < rs) return fail(m, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff plus the skin");
+            const int nc = (int)std::floor((double)g.L[d] / (double)rs);
+            gk.nc[d] = nc < 1 ? 1 : nc;
+            gk.ncells *= gk.nc[d];
+        }
+        launch_skin(positions, types, n, gk, m->skin, force, cap_s, m->pos4, m->cell_of, m->cell_count, m->cell_start,
+                    m->cell_fill, m->cell_atoms, m->spos4, m->sidx, m->d_acc, zbuf, zcount, m->skin_gate,
+                    m->skin_list, m->skin_cnt, m->skin_sref4, m->skin_xref, m->skin_rebuilds, st);
+        m->skin_valid = true;
+        m->skin_n = n;
+        m->skin_cap = cap_s;
+        std::memcpy(m->skin_box, box, sizeof(double) * 9);
+    } else {
+        launch_bin(positions, types, n, g, m->pos4, m->cell_of, m->cell_count, m->cell_start, m->cell_fill,
+                   m->cell_atoms, m->spos4, m->sidx, m->d_acc, zbuf, zcount, st);
+    }
     tm.end(0, st);
     if (coop) {
         tm.begin(2, st);
         launch_nbr_desc_coop(m->spos4, m->cell_start, m->sidx, n, g, m->d_params, m->lay, cl, ca, m->nbr_list,
                              m->cnt_list, m->nbr_ang, m->cnt_ang, backward ? m->ang : nullptr,
                              backward ? m->du : nullptr, m->dq, m->u, m->q, out->descriptor, m->tab, ewald, m->fields,
-                             vjp ? vjp->charge_weight : nullptr, m->d_acc, st, mixed ? m->dtc : nullptr);
+                             vjp ? vjp->charge_weight : nullptr, m->d_acc, st, mixed ? m->dtc : nullptr,
+                             use_skin ? m->skin_list : nullptr, m->skin_cnt, m->skin_cap);
         if (mixed)
             launch_mlp_tc(m->precision, m->dtc, m->spos4, n, m->d_params, m->lay, backward ? m->du : nullptr, m->dq,
                           NDES, 1, m->u, m->q, m->d_acc, m->num_sms, st);
@@ -818,7 +889,8 @@ void qnep_destroy(qnep_model* m) {
                     m->cnt_ang, m->ang, m->du, m->dq, m->u, m->q, m->phase, m->cell_count,
                     m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_chunk_order, m->d_kg, m->d_S, m->d_C,
                     m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
-                    m->io_out[4], m->io_out[5], m->dtc, m->md_step, m->md_ke, m->md_done, m->md_scalars};
+                    m->io_out[4], m->io_out[5], m->dtc, m->md_step, m->md_ke, m->md_done, m->md_scalars,
+                    m->skin_gate, m->skin_rebuilds, m->skin_list, m->skin_cnt, m->skin_sref4, m->skin_xref};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->h_status) cudaFreeHost(m->h_status);

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
     int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang, float* __restrict__ ang_coef,
     float* __restrict__ du, float* __restrict__ dq, float* __restrict__ u_out, float* __restrict__ q_out,
     float* __restrict__ des_out, EwaldTab tab, int do_phase, float4* __restrict__ fields,
-    const float* __restrict__ gq_in, Accum* __restrict__ acc, float* __restrict__ dtc) {
+    const float* __restrict__ gq_in, Accum* __restrict__ acc, float* __restrict__ dtc,
+    const int* __restrict__ skin_list, const int* __restrict__ skin_cnt, int cap_s) {
     extern __shared__ float csm[];
     float* sp = csm;
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
@@ -66,7 +67,10 @@ __global__ void __launch_bounds__(32 * CW) k_nbr_desc_coop(
         const float4 pk = __ldg(&spos4[k]);
         const int ti = __float_as_int(pk.w);
         int nl = 0, na = 0;
-        bool ovf = warp_build_lists(spos4, cell_start, k, pk, g, cap_l, cap_a, sl, slt, sa, sat, nl, na);
+        // lists from a cell search, or from the Verlet-skin candidates when a skin is kept
+        bool ovf = skin_list ? warp_lists_from_skin(spos4, skin_list + (size_t)k * cap_s, __ldg(&skin_cnt[k]), pk, g,
+                                                    cap_l, cap_a, sl, slt, sa, sat, nl, na)
+                             : warp_build_lists(spos4, cell_start, k, pk, g, cap_l, cap_a, sl, slt, sa, sat, nl, na);
         warp_write_grouped(sl, slt, nl, S, n, k, nbr_list, (size_t)cap_l, 1, cnt_list);
         warp_write_grouped(sa, sat, na, S, n, k, nbr_ang, (size_t)cap_a, 1, cnt_ang);
         if (ovf && lane == 0) atomicOr(&acc->status, 1u);
@@ -545,7 +549,8 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq, float* u,
                           float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
-                          const float* gq, Accum* acc, cudaStream_t st, float* dtc) {
+                          const float* gq, Accum* acc, cudaStream_t st, float* dtc, const int* skin_list,
+                          const int* skin_cnt, int cap_s) {
     if (n == 0) return;
     static std::atomic<int> attr[kMaxDevices];
     ensure_smem_attr(k_nbr_desc_coop, attr, 220 * 1024);
@@ -556,7 +561,7 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
     if (blocks > per_sm * num_sms()) blocks = per_sm * num_sms();
     k_nbr_desc_coop<<<blocks, 32 * CW, smem, st>>>(
         spos4, cell_start, sidx, n, g, params, lay, cap_l, cap_a, nbr_list, cnt_list, nbr_ang, cnt_ang, ang_coef, du,
-        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc, dtc);
+        dq, u, q, des_out, tab, do_phase ? 1 : 0, fields, gq, acc, dtc, skin_list, skin_cnt, cap_s);
 }
 
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,

@@ -125,6 +125,70 @@ __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos
     return cl > cap_l || ca > cap_a;
 }
 
+// The lists of sorted atom k from its Verlet-skin candidates cand[0..total) (entries with image
+// codes, built with a longer cutoff): the same tests, staging and return value as
+// warp_build_lists, on the current positions.  Whole warp only.
+__device__ __forceinline__ bool warp_lists_from_skin(const float4* __restrict__ spos4, const int* __restrict__ cand,
+                                                     int total, float4 pk, const Geom& g, int cap_l, int cap_a,
+                                                     int* sl, int* slt, int* sa, int* sat, int& nl, int& na) {
+    const int lane = threadIdx.x & 31;
+    const float rl2 = g.rc_list * g.rc_list;
+    const float ra2 = g.rc_angular * g.rc_angular;
+    const unsigned below = (1u << lane) - 1u;
+    int cl = 0, ca = 0;
+    for (int base = 0; base < total; base += 128) {
+        int ent[4];
+        float4 pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = base + 32 * u + lane;
+            ent[u] = t < total ? __ldg(&cand[t]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            pj[u] = base + 32 * u + lane < total ? __ldg(&spos4[ent[u] & INDEX_MASK]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (base + 32 * u >= total) break;   // warp-uniform
+            const int t = base + 32 * u + lane;
+            bool inl = false, ina = false;
+            int typ = 0;
+            if (t < total) {
+                const unsigned code = (unsigned)ent[u] >> CODE_SHIFT;
+                const float sx = (float)((int)(code & 3u) - 1) * g.L[0], sy = (float)((int)((code >> 2) & 3u) - 1) * g.L[1],
+                            sz = (float)((int)(code >> 4) - 1) * g.L[2];
+                const float vx = (pj[u].x - pk.x) + sx, vy = (pj[u].y - pk.y) + sy, vz = (pj[u].z - pk.z) + sz;
+                const float r2 = vx * vx + vy * vy + vz * vz;
+                inl = r2 < rl2;
+                ina = inl && r2 < ra2;
+                typ = __float_as_int(pj[u].w);
+            }
+            const unsigned ml = __ballot_sync(0xffffffffu, inl);
+            const unsigned ma = __ballot_sync(0xffffffffu, ina);
+            if (inl) {
+                const int slot = cl + __popc(ml & below);
+                if (slot < cap_l) {
+                    sl[slot] = ent[u];
+                    slt[slot] = typ;
+                }
+            }
+            if (ina) {
+                const int slot = ca + __popc(ma & below);
+                if (slot < cap_a) {
+                    sa[slot] = ent[u];
+                    sat[slot] = typ;
+                }
+            }
+            cl += __popc(ml);
+            ca += __popc(ma);
+        }
+    }
+    __syncwarp();
+    nl = cl < cap_l ? cl : cap_l;
+    na = ca < cap_a ? ca : cap_a;
+    return cl > cap_l || ca > cap_a;
+}
+
 // Write staged entries grouped by neighbour species: out[k * sa + slot * se], counts cnt[s][n].
 __device__ __forceinline__ void warp_write_grouped(const int* se_buf, const int* st_buf, int cnt, int n_species, int n,
                                                    int k, int* __restrict__ out, size_t stride_atom,

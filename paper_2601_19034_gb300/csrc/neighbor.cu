@@ -28,7 +28,9 @@ __device__ __forceinline__ int cell_coord(float x, float invL, int nc) {
 // FP64 accumulators and (optionally) the structure-factor array of this call.
 __global__ void k_bin(const float* __restrict__ pos, const int* __restrict__ types, int n, Geom g,
                       float4* __restrict__ pos4, int* __restrict__ cell_of, int* __restrict__ cell_count,
-                      Accum* __restrict__ acc, double2* __restrict__ zero_buf, int zero_count) {
+                      Accum* __restrict__ acc, double2* __restrict__ zero_buf, int zero_count,
+                      const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;   // Verlet skin: the list is reused, positions come from k_skin_refresh
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         double* a = reinterpret_cast<double*>(acc);
@@ -55,7 +57,9 @@ __global__ void k_bin(const float* __restrict__ pos, const int* __restrict__ typ
 }
 
 // Exclusive scan of the cell counts (one block); clears the counts for the next call.
-__global__ void k_scan(int* __restrict__ count, int ncells, int* __restrict__ start, int* __restrict__ fill) {
+__global__ void k_scan(int* __restrict__ count, int ncells, int* __restrict__ start, int* __restrict__ fill,
+                       const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ int warp_tot[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -95,7 +99,8 @@ __global__ void k_scan(int* __restrict__ count, int ncells, int* __restrict__ st
 }
 
 __global__ void k_fill(const int* __restrict__ cell_of, int n, const int* __restrict__ start, int* __restrict__ fill,
-                       int* __restrict__ slot_atoms) {
+                       int* __restrict__ slot_atoms, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cell_of[i];
@@ -106,7 +111,8 @@ __global__ void k_fill(const int* __restrict__ cell_of, int n, const int* __rest
 // One warp per cell: rank the cell's atoms by input index (the fill order is
 // arbitrary) and write the sorted arrays: spos4[k], sidx[k] = input index.
 __global__ void k_order(const int* __restrict__ start, int ncells, const int* __restrict__ slot_atoms,
-                        const float4* __restrict__ pos4, float4* __restrict__ spos4, int* __restrict__ sidx) {
+                        const float4* __restrict__ pos4, float4* __restrict__ spos4, int* __restrict__ sidx, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (c >= ncells) return;
@@ -143,7 +149,8 @@ __global__ void __launch_bounds__(SMALL_BIN_THREADS) k_bin_small(const float* __
                                                                   int* __restrict__ slot_atoms,
                                                                   float4* __restrict__ spos4, int* __restrict__ sidx,
                                                                   Accum* __restrict__ acc,
-                                                                  double2* __restrict__ zero_buf, int zero_count) {
+                                                                  double2* __restrict__ zero_buf, int zero_count, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ int cnt[SMALL_BIN_CELLS];
     __shared__ int start[SMALL_BIN_CELLS + 1];
     __shared__ int warp_tot[32];
@@ -255,23 +262,118 @@ __global__ void k_neighbors(const float4* __restrict__ spos4, const int* __restr
 
 void launch_bin(const float* pos, const int* types, int n, const Geom& g, float4* pos4, int* cell_of, int* cell_count,
                 int* cell_start, int* cell_fill, int* slot_atoms, float4* spos4, int* sidx, Accum* acc,
-                double2* zero_buf, int zero_count, cudaStream_t st) {
+                double2* zero_buf, int zero_count, cudaStream_t st, const int* gate) {
     if (n <= SMALL_BIN_ATOMS && g.ncells <= SMALL_BIN_CELLS && zero_count <= 64 * SMALL_BIN_THREADS) {
         // counts in shared memory: cell_count / cell_fill are not used (and stay zero)
         k_bin_small<<<1, SMALL_BIN_THREADS, 0, st>>>(pos, types, n, g, pos4, cell_of, cell_start, slot_atoms, spos4,
-                                                     sidx, acc, zero_buf, zero_count);
+                                                     sidx, acc, zero_buf, zero_count, gate);
         return;
     }
     int blocks = (n + 255) / 256;
     int zb = (zero_count + 255) / 256;
     if (zb > blocks) blocks = zb;
     if (blocks < 1) blocks = 1;
-    k_bin<<<blocks, 256, 0, st>>>(pos, types, n, g, pos4, cell_of, cell_count, acc, zero_buf, zero_count);
-    k_scan<<<1, 1024, 0, st>>>(cell_count, g.ncells, cell_start, cell_fill);
+    k_bin<<<blocks, 256, 0, st>>>(pos, types, n, g, pos4, cell_of, cell_count, acc, zero_buf, zero_count, gate);
+    k_scan<<<1, 1024, 0, st>>>(cell_count, g.ncells, cell_start, cell_fill, gate);
     if (n > 0) {
-        k_fill<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, cell_start, cell_fill, slot_atoms);
-        k_order<<<(g.ncells * 32 + 127) / 128, 128, 0, st>>>(cell_start, g.ncells, slot_atoms, pos4, spos4, sidx);
+        k_fill<<<(n + 255) / 256, 256, 0, st>>>(cell_of, n, cell_start, cell_fill, slot_atoms, gate);
+        k_order<<<(g.ncells * 32 + 127) / 128, 128, 0, st>>>(cell_start, g.ncells, slot_atoms, pos4, spos4, sidx,
+                                                              gate);
     }
+}
+
+// ---- Verlet skin ----------------------------------------------------------------------------
+// A candidate list with cutoff r_list + skin is kept while no atom has moved more than skin / 2
+// since it was built: then every pair now within r_list was within r_list + skin at the build,
+// so filtering the candidates by the current distances gives exactly the lists of a fresh cell
+// search (in another order).  The test and the choice between rebuilding and reusing are made
+// on the device (a gate word), so a step needs no host synchronisation:
+//   k_skin_check    gate = 1 if |x_i - x_i^ref| > skin / 2 for any atom (the host sets the gate
+//                   to 1 instead when there is no valid list: first call, new box or size)
+//   gate = 1:       the binning kernels sort the atoms again, k_skin_build writes the candidate
+//                   lists, the reference positions (input order) and the sorted positions at the build
+//   gate = 0:       k_skin_refresh moves the sorted positions by the displacement since the build
+//                   (not wrapped into the box: the stored image shifts stay valid) and clears the
+//                   accumulators as the binning would
+__global__ void k_skin_check(const float* __restrict__ pos, const float* __restrict__ xref, int n, float lim2,
+                             int* __restrict__ gate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float dx = pos[3 * i] - xref[3 * i], dy = pos[3 * i + 1] - xref[3 * i + 1], dz = pos[3 * i + 2] - xref[3 * i + 2];
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (!(d2 <= lim2)) *gate = 1;   // also a non-finite displacement
+}
+
+__global__ void __launch_bounds__(128) k_skin_build(const float4* __restrict__ spos4, const int* __restrict__ cell_start,
+                                                    const int* __restrict__ sidx, const float* __restrict__ pos, int n,
+                                                    Geom gs, int cap_s, int* __restrict__ skin_list,
+                                                    int* __restrict__ skin_cnt, float4* __restrict__ sref4,
+                                                    float* __restrict__ xref, const int* __restrict__ gate,
+                                                    Accum* __restrict__ acc, unsigned int* __restrict__ rebuilds) {
+    if (*gate == 0) return;
+    extern __shared__ int ksm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rebuilds, 1u);
+    if (k >= n) return;
+    int* sl = ksm + wib * 2 * cap_s;
+    int* slt = sl + cap_s;
+    const float4 pk = spos4[k];
+    int nl = 0, na = 0;
+    // gs: list cutoff r_list + skin, no angular part (rc_angular 0, capacity 0)
+    const bool ovf = warp_build_lists(spos4, cell_start, k, pk, gs, cap_s, 0, sl, slt, nullptr, nullptr, nl, na);
+    for (int e = lane; e < nl; e += 32) skin_list[(size_t)k * cap_s + e] = sl[e];
+    if (lane == 0) {
+        skin_cnt[k] = nl;
+        sref4[k] = pk;
+        const int i = sidx[k];
+        xref[3 * i] = pos[3 * i];
+        xref[3 * i + 1] = pos[3 * i + 1];
+        xref[3 * i + 2] = pos[3 * i + 2];
+        if (ovf) atomicOr(&acc->status, 1u);
+    }
+}
+
+__global__ void k_skin_refresh(const float* __restrict__ pos, const float* __restrict__ xref,
+                               const float4* __restrict__ sref4, const int* __restrict__ sidx, int n,
+                               const int* __restrict__ gate, Accum* __restrict__ acc, double2* __restrict__ zero_buf,
+                               int zero_count, float4* __restrict__ spos4) {
+    if (*gate != 0) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        double* a = reinterpret_cast<double*>(acc);
+        for (int q = 0; q < (int)(sizeof(Accum) / sizeof(double)); ++q) a[q] = 0.0;
+    }
+    for (int q = t; q < zero_count; q += gridDim.x * blockDim.x) zero_buf[q] = make_double2(0.0, 0.0);
+    if (t >= n) return;
+    const int i = sidx[t];
+    const float4 r = sref4[t];
+    spos4[t] = make_float4(r.x + (pos[3 * i] - xref[3 * i]), r.y + (pos[3 * i + 1] - xref[3 * i + 1]),
+                           r.z + (pos[3 * i + 2] - xref[3 * i + 2]), r.w);
+}
+
+void launch_skin(const float* pos, const int* types, int n, const Geom& g, float skin, bool force, int cap_s,
+                 float4* pos4, int* cell_of, int* cell_count, int* cell_start, int* cell_fill, int* slot_atoms,
+                 float4* spos4, int* sidx, Accum* acc, double2* zero_buf, int zero_count, int* gate, int* skin_list,
+                 int* skin_cnt, float4* sref4, float* xref, unsigned int* rebuilds, cudaStream_t st) {
+    // the gate is read as zero / non-zero: without a valid list it starts non-zero (every byte 1)
+    cudaMemsetAsync(gate, force ? 1 : 0, sizeof(int), st);
+    if (!force) {
+        const float h = 0.5f * skin;
+        k_skin_check<<<(n + 255) / 256, 256, 0, st>>>(pos, xref, n, h * h, gate);
+    }
+    launch_bin(pos, types, n, g, pos4, cell_of, cell_count, cell_start, cell_fill, slot_atoms, spos4, sidx, acc,
+               zero_buf, zero_count, st, gate);
+    Geom gs = g;
+    gs.rc_list = g.rc_list + skin;
+    gs.rc_angular = 0.f;
+    const size_t smem = sizeof(int) * 4 * 2 * (size_t)cap_s;
+    static std::atomic<int> attr[kMaxDevices];
+    if (smem > 48 * 1024) ensure_smem_attr(k_skin_build, attr, (int)smem);
+    k_skin_build<<<(n + 3) / 4, 128, smem, st>>>(spos4, cell_start, sidx, pos, n, gs, cap_s, skin_list, skin_cnt,
+                                                 sref4, xref, gate, acc, rebuilds);
+    const int zb = std::max((n + 255) / 256, (zero_count + 255) / 256);
+    k_skin_refresh<<<std::max(zb, 1), 256, 0, st>>>(pos, xref, sref4, sidx, n, gate, acc, zero_buf, zero_count, spos4);
 }
 
 void launch_neighbors(const float4* spos4, const int* cell_start, int n, int n_species, const Geom& g, int cap_list,

@@ -173,9 +173,17 @@ __device__ __forceinline__ void entry_shift(int e, float& tx, float& ty, float& 
 
 // ---- host-side launchers (defined in the .cu files) ---------------------------------
 
+// gate (optional): the kernels do nothing while *gate == 0 (Verlet skin: a reused list)
 void launch_bin(const float* pos, const int* types, int n, const Geom& g, float4* pos4, int* cell_of,
                 int* cell_count, int* cell_start, int* cell_fill, int* slot_atoms, float4* spos4, int* sidx,
-                Accum* acc, double2* zero_buf, int zero_count, cudaStream_t st);
+                Accum* acc, double2* zero_buf, int zero_count, cudaStream_t st, const int* gate = nullptr);
+// Verlet skin: displacement test, then either the binning and the candidate lists (cutoff
+// r_list + skin, [n][cap_s] entries, counts [n]) or the refreshed sorted positions of the kept
+// list; force = no valid list.  rebuilds counts the rebuilds (device counter).
+void launch_skin(const float* pos, const int* types, int n, const Geom& g, float skin, bool force, int cap_s,
+                 float4* pos4, int* cell_of, int* cell_count, int* cell_start, int* cell_fill, int* slot_atoms,
+                 float4* spos4, int* sidx, Accum* acc, double2* zero_buf, int zero_count, int* gate, int* skin_list,
+                 int* skin_cnt, float4* sref4, float* xref, unsigned int* rebuilds, cudaStream_t st);
 void launch_neighbors(const float4* spos4, const int* cell_start, int n, int n_species, const Geom& g,
                       int cap_list, int cap_ang, int* nbr_list, int* cnt_list, int* nbr_ang, int* cnt_ang,
                       Accum* acc, cudaStream_t st);
@@ -225,7 +233,8 @@ void launch_nbr_desc_coop(const float4* spos4, const int* cell_start, const int*
                           const float* params, const ParamLayout& lay, int cap_l, int cap_a, int* nbr_list,
                           int* cnt_list, int* nbr_ang, int* cnt_ang, float* ang_coef, float* du, float* dq,
                           float* u, float* q, float* des_out, const EwaldTab& tab, bool do_phase, float4* fields,
-                          const float* gq, Accum* acc, cudaStream_t st, float* dtc = nullptr);
+                          const float* gq, Accum* acc, cudaStream_t st, float* dtc = nullptr,
+                          const int* skin_list = nullptr, const int* skin_cnt = nullptr, int cap_s = 0);
 void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* cnt_list, const int* nbr_ang,
                           const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                           const float* ang_coef, const float* du, const float* dq, const float* q_raw,

@@ -74,6 +74,16 @@ class QNEP:
     def set_capacity(self, cap_list: int = 0, cap_angular: int = 0):
         _lib.check(self.lib.qnep_set_capacity(self.handle, int(cap_list), int(cap_angular)), self.handle)
 
+    def set_skin(self, skin: float = 0.0):
+        """Verlet skin (A) of the neighbour lists for repeated calls on moving atoms (0: rebuild every call)."""
+        _lib.check(self.lib.qnep_set_skin(self.handle, float(skin)), self.handle)
+
+    def skin_rebuilds(self) -> int:
+        """Number of list rebuilds since the skin was set (synchronises the device)."""
+        c = ctypes.c_uint()
+        _lib.check(self.lib.qnep_skin_rebuilds(self.handle, ctypes.byref(c)), self.handle)
+        return c.value
+
     def _set_box(self, box):
         b = np.asarray(box, dtype=np.float64).reshape(9)
         for k in range(9):

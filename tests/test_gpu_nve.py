@@ -145,3 +145,87 @@ def test_full_size_mg_water(dev):
     assert np.isfinite(e).all()
     assert np.abs(e.sum(1) - e[0].sum()).max() / sysm.n_atoms <= 1e-3
     model.close()
+
+
+def _skin_pair(dev, sysm, hp, params, elec, skin=1.0):
+    from paper_2601_19034_gb300.qnep import QNEP
+    a = QNEP(hp, params, elec)
+    a.set_skin(skin)
+    b = QNEP(hp, params, elec)
+    return a, b
+
+
+def _compare_calls(dev, a, b, pos, typ, box, n):
+    from paper_2601_19034_gb300.qnep import parse_scalars
+    pa = torch.tensor(pos, device=dev)
+    ta = torch.tensor(typ, device=dev)
+    oa = a.compute(pa, ta, box, bec=False)
+    ob = b.compute(pa, ta, box, bec=False)
+    torch.cuda.synchronize()
+    sa, sb = parse_scalars(oa["scalars"]), parse_scalars(ob["scalars"])
+    assert abs(sa["energy"] - sb["energy"]) / n <= 1e-6
+    assert (oa["forces"] - ob["forces"]).abs().max().item() <= 1e-4
+    assert (oa["charges"] - ob["charges"]).abs().max().item() <= 2e-6
+    assert np.abs(sa["virial"] - sb["virial"]).max() / n <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["mg_water_pppm", "water_ewald"])
+def test_skin_lists_give_the_fresh_search_result(dev, case):
+    """A kept candidate list (skin 1 A) gives the force call of a fresh cell search: at the build,
+    after moves below skin / 2 (no rebuild) and after one atom moved beyond it (a rebuild)."""
+    if case == "mg_water_pppm":
+        sysm, hp, params, elec = _small()
+    else:
+        sysm, hp, params, elec = wl.config_water_small()
+    a, b = _skin_pair(dev, sysm, hp, params, elec)
+    rng = np.random.default_rng(3)
+    x0 = sysm.positions.astype(np.float32)
+    n = sysm.n_atoms
+    _compare_calls(dev, a, b, x0, sysm.types, sysm.box, n)
+    assert a.skin_rebuilds() == 1
+    for _ in range(3):   # moves of at most 0.4 A (below skin / 2): the list is kept
+        d = rng.normal(size=x0.shape)
+        d *= 0.4 * rng.uniform(size=(n, 1)) / np.linalg.norm(d, axis=1, keepdims=True)
+        _compare_calls(dev, a, b, (x0 + d).astype(np.float32), sysm.types, sysm.box, n)
+    assert a.skin_rebuilds() == 1
+    x1 = x0.copy()
+    x1[7] += np.array([0.6, 0.0, 0.0], np.float32)   # one atom beyond skin / 2: rebuilt
+    _compare_calls(dev, a, b, x1, sysm.types, sysm.box, n)
+    assert a.skin_rebuilds() == 2
+    # an atom that crosses the box face between rebuilds keeps its image shifts
+    x2 = x1.copy()
+    x2[11] = np.float32(sysm.box[0, 0] - 0.05) if x2[11, 0] > sysm.box[0, 0] / 2 else x2[11]
+    x3 = x2.copy()
+    x3[11, 0] += 0.2
+    _compare_calls(dev, a, b, x2, sysm.types, sysm.box, n)
+    _compare_calls(dev, a, b, x3, sysm.types, sysm.box, n)
+    a.close()
+    b.close()
+
+
+def test_nve_with_skin_equals_rebuild_every_step(dev):
+    """50 velocity-Verlet steps of 0.5 fs on the Mg-water slab with a 1 A skin and with lists rebuilt
+    at every step: the same trajectory to FP32 rounding (the sums run in another order), and
+    fewer rebuilds than steps."""
+    from paper_2601_19034_gb300.qnep import QNEP, nve
+    sysm, hp, params, elec = _small()
+    masses = wl.species_masses(wl.MGWATER_SPECIES)
+    v0 = wl.maxwell_boltzmann(masses[sysm.types], 300.0, seed=9).astype(np.float32)
+    res = []
+    for skin in (1.0, 0.0):
+        model = QNEP(hp, params, elec)
+        model.set_skin(skin)
+        pos = torch.tensor(sysm.positions, device=dev)
+        vel = torch.tensor(v0, device=dev)
+        f, en = nve(model, pos, vel, torch.tensor(sysm.types, device=dev), masses, sysm.box, 0.5, 50)
+        torch.cuda.synchronize()
+        res.append((pos.cpu().numpy(), vel.cpu().numpy(), en.cpu().numpy(), model.skin_rebuilds() if skin else None))
+        model.close()
+    (p1, v1, e1, nreb), (p0, v0_, e0, _) = res
+    n = sysm.n_atoms
+    print(f"\nskin 1 A: {nreb} rebuilds in 51 force calls; max |dx| {np.abs(p1 - p0).max():.3g} A, "
+          f"max |dE|/N {np.abs(e1 - e0).max() / n:.3g} eV")
+    assert 1 <= nreb < 51
+    assert np.abs(p1 - p0).max() <= 1e-3
+    assert np.abs(v1 - v0_).max() <= 1e-3
+    assert np.abs(e1 - e0).max() / n <= 1e-5
