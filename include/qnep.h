@@ -114,6 +114,14 @@ typedef struct {
     float*  potential;    /* device [N] phi_i = dU^ES/dq^c_i (optional) */
     float*  descriptor;   /* device [N][n_des] (optional, for parity checks) */
     int     want_virial;  /* 1: compute the virial into scalars (needs the backward pass) */
+    float*  atom_virial;  /* device [N][3][3] per-atom virial W_i (Sec. II.C, Eq. per-atom_virial; eV),
+                           * summing to the total virial: -r_ij (x) F_ij of every neighbour entry
+                           * (i -> j) added to W_j (descriptor and dynamic-charge partial forces), the
+                           * static real-space pair terms split evenly, and the static reciprocal-space
+                           * term in the Heyes form k_e sum_k G Re[q_i e^{i k.r_i} S(k)] B(k) (Ewald) or
+                           * its mesh form with six more inverse FFTs (PPPM, Sec. II.F).  Optional;
+                           * warp-per-atom kernels only (QNEP_ERR_UNSUPPORTED with QNEP_PATH_THREAD or
+                           * a vector-Jacobian product). */
 } qnep_outputs;
 
 /* Create a model: copies n_candidates parameter blobs (host, candidate-major,

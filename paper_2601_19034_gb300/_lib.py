@@ -54,7 +54,7 @@ class ElecC(ctypes.Structure):
 class OutputsC(ctypes.Structure):
     _fields_ = [("scalars", ctypes.c_void_p), ("forces", ctypes.c_void_p), ("charges", ctypes.c_void_p),
                 ("bec", ctypes.c_void_p), ("site_energy", ctypes.c_void_p), ("potential", ctypes.c_void_p),
-                ("descriptor", ctypes.c_void_p), ("want_virial", ctypes.c_int)]
+                ("descriptor", ctypes.c_void_p), ("want_virial", ctypes.c_int), ("atom_virial", ctypes.c_void_p)]
 
 
 class VjpC(ctypes.Structure):

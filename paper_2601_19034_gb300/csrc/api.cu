@@ -76,6 +76,14 @@ struct qnep_model {
     float* d_kg = nullptr;
     double2* d_S = nullptr;
     float2* d_C = nullptr;
+    float4* d_kb = nullptr;        // B(k) per padded wave vector (per-atom virial), 2 float4 each
+    // per-atom virial scratch [n][AVIR] (allocated on the first request) and the PPPM extras
+    float* avir = nullptr;
+    int avir_alloc = 0;
+    float2* pm_fhat6 = nullptr;
+    float* pm_field6 = nullptr;
+    cufftHandle c2r6 = 0;
+    bool have_c2r6 = false;
     // PPPM meshes and FFT plans (created with the first box)
     PppmTab pm{};
     cufftHandle r2c = 0, c2r = 0;
@@ -178,7 +186,27 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
         CK(grow(&m->d_kg, nk));
         CK(grow(&m->d_S, nk));
         CK(grow(&m->d_C, nk));
+        CK(grow(&m->d_kb, 2 * (size_t)nk));
         m->nk_alloc = nk;
+    }
+    {
+        // B(k) = I - (2 / (4 alpha^2) + 2 / k^2) k k^T of every padded wave vector (zero on padding)
+        std::vector<float4> kb(2 * (size_t)std::max(nk, 1), make_float4(0.f, 0.f, 0.f, 0.f));
+        const double tp = 6.283185307179586;
+        for (int gi = 0; gi < nch; ++gi) {
+            const int4& c = cols[chunk_col[gi]];
+            for (int t = 0; t < 8; ++t) {
+                const int k = 8 * gi + t;
+                if (!(kg[k] > 0.f)) continue;
+                const int n3 = c.z + (k - c.w);
+                const double kx = tp * c.x / L[0], ky = tp * c.y / L[1], kz = tp * n3 / L[2];
+                const double fac = 2.0 / (4.0 * m->es.alpha * m->es.alpha) + 2.0 / (kx * kx + ky * ky + kz * kz);
+                kb[2 * k] = make_float4((float)(1.0 - fac * kx * kx), (float)(1.0 - fac * ky * ky),
+                                        (float)(1.0 - fac * kz * kz), (float)(-fac * kx * ky));
+                kb[2 * k + 1] = make_float4((float)(-fac * kx * kz), (float)(-fac * ky * kz), 0.f, 0.f);
+            }
+        }
+        if (nk) CK(cudaMemcpy(m->d_kb, kb.data(), sizeof(float4) * 2 * (size_t)nk, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(m->d_col, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice));
     if (nch) CK(cudaMemcpy(m->d_chunk_col, chunk_col.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
@@ -207,6 +235,7 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
     t.kg = m->d_kg;
     t.S = m->d_S;
     t.C = m->d_C;
+    t.kb = m->d_kb;
     return QNEP_OK;
 }
 
@@ -539,7 +568,7 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
     const bool ewald = m->es.mode != 0 && m->es.kind == QNEP_EWALD;
     const bool pppm = m->es.mode != 0 && m->es.kind == QNEP_PPPM;
     const bool gp_nonzero = vjp && (vjp->polar_weight[0] != 0 || vjp->polar_weight[1] != 0 || vjp->polar_weight[2] != 0);
-    const bool backward = out->forces || out->bec || out->want_virial || vjp;
+    const bool backward = out->forces || out->bec || out->want_virial || vjp || out->atom_virial;
     const bool want_bec = out->bec != nullptr || gp_nonzero;
     if (vjp && m->precision != QNEP_PREC_FP32)
         return fail(m, QNEP_ERR_UNSUPPORTED, "the vector-Jacobian product runs on the FP32 path only");
@@ -555,6 +584,29 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
     Geom g = m->geom;
     const bool mixed = m->precision != QNEP_PREC_FP32;
     const bool coop = m->path == QNEP_PATH_WARP || (m->path == QNEP_PATH_AUTO && n <= kCoopMaxAtoms);
+    float* avir = nullptr;
+    if (out->atom_virial) {
+        if (!coop || vjp)
+            return fail(m, QNEP_ERR_UNSUPPORTED,
+                        "the per-atom virial runs with the warp-per-atom kernels and without a vector-Jacobian product");
+        if (n > m->avir_alloc) {
+            CK(cudaStreamSynchronize(st));
+            CK(grow(&m->avir, (size_t)AVIR * n));
+            m->avir_alloc = n;
+        }
+        if (pppm && !m->pm_fhat6) {
+            CK(cudaStreamSynchronize(st));
+            CK(cudaMalloc((void**)&m->pm_fhat6, sizeof(float2) * 6 * m->pm.nhalf));
+            CK(cudaMalloc((void**)&m->pm_field6, sizeof(float) * 6 * m->pm.nreal));
+            int dims[3] = {m->pm.nx, m->pm.ny, m->pm.nz};
+            if (cufftPlanMany(&m->c2r6, 3, dims, nullptr, 1, (int)m->pm.nhalf, nullptr, 1, (int)m->pm.nreal, CUFFT_C2R,
+                              6) != CUFFT_SUCCESS)
+                return fail(m, QNEP_ERR_CUDA, "cufftPlanMany (C2R x 6) failed");
+            m->have_c2r6 = true;
+        }
+        avir = m->avir;
+        CK(cudaMemsetAsync(avir, 0, sizeof(float) * AVIR * (size_t)n, st));
+    }
     if (coop) {   // atom-major lists for the warp-per-atom kernels
         g.list_sa = cl;
         g.list_se = 1;
@@ -655,7 +707,7 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         CK(cudaStreamWaitEvent(m->aux, m->ev_fork, 0));
         tm.begin(6, m->aux);
         launch_real(m->spos4, m->q, m->nbr_list, m->cnt_list, n, m->hp.n_species, g, (float)m->es.alpha, q_target,
-                    m->d_acc, rfield, m->d_acc, m->aux);
+                    m->d_acc, rfield, m->d_acc, m->aux, avir);
         tm.end(6, m->aux);
         CK(cudaEventRecord(m->ev_join, m->aux));
     }
@@ -664,13 +716,16 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         launch_ewald_sk_fused(m->q, m->d_acc, n, q_target, m->tab, m->sk_done, st);
         tm.end(4, st);
         tm.begin(5, st);
-        launch_field_k(n, m->tab, kfield, m->d_acc, st);
+        launch_field_k(n, m->tab, kfield, m->d_acc, st, avir);
         tm.end(5, st);
     }
     if (pppm) {
         tm.begin(9, st);
-        if (launch_pppm(m->spos4, m->q, n, m->d_acc, q_target, m->pm, (float)m->es.alpha, m->r2c, m->c2r, kfield,
-                        m->d_acc, st) != 0)
+        PppmTab pmc = m->pm;   // the six per-atom virial fields only when they are asked for
+        pmc.fhat6 = avir ? m->pm_fhat6 : nullptr;
+        pmc.field6 = avir ? m->pm_field6 : nullptr;
+        if (launch_pppm(m->spos4, m->q, n, m->d_acc, q_target, pmc, (float)m->es.alpha, m->r2c, m->c2r, kfield,
+                        m->d_acc, st, (int)m->c2r6, avir) != 0)
             return fail(m, QNEP_ERR_CUDA, "cuFFT execution failed");
         tm.end(9, st);
     }
@@ -679,7 +734,7 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         tm.begin(7, st);
         if (coop)
             launch_desc_bwd_coop(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params, m->lay,
-                                 m->ang, m->du, m->dq, m->q, fin, m->d_acc, want_bec, acc12, m->d_acc, st);
+                                 m->ang, m->du, m->dq, m->q, fin, m->d_acc, want_bec, acc12, m->d_acc, st, avir);
         else
             launch_descriptor_backward(m->spos4, m->nbr_list, m->cnt_list, m->nbr_ang, m->cnt_ang, n, g, m->d_params,
                                        m->lay, m->ang, m->du, m->dq, m->q, fin, m->d_acc, want_bec, acc12, m->d_acc,
@@ -692,7 +747,7 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         for (int d = 0; d < 3; ++d) gp[d] = (float)vjp->polar_weight[d];
     launch_finalize(acc12, n, m->sidx, positions, m->q, q_target, m->sqrt_eps, ec, kfield, rfield, out->forces,
                     out->bec, out->charges, out->potential, m->u, out->site_energy, m->d_acc, out->scalars,
-                    m->d_status, m->fin_done, st, vjp ? vjp->grad : nullptr, gp);
+                    m->d_status, m->fin_done, st, vjp ? vjp->grad : nullptr, gp, avir, out->atom_virial);
     tm.end(8, st);
     if (m->profiling) m->pending = true;
     CK(cudaGetLastError());
@@ -890,7 +945,8 @@ void qnep_destroy(qnep_model* m) {
                     m->cell_start, m->cell_fill, m->d_acc, m->d_col, m->d_chunk_col, m->d_chunk_order, m->d_kg, m->d_S, m->d_C,
                     m->io_pos, m->io_types, m->io_scalars, m->io_out[0], m->io_out[1], m->io_out[2], m->io_out[3],
                     m->io_out[4], m->io_out[5], m->dtc, m->md_step, m->md_ke, m->md_done, m->md_scalars,
-                    m->skin_gate, m->skin_rebuilds, m->skin_list, m->skin_cnt, m->skin_sref4, m->skin_xref};
+                    m->skin_gate, m->skin_rebuilds, m->skin_list, m->skin_cnt, m->skin_sref4, m->skin_xref,
+                    m->d_kb, m->avir, m->pm_fhat6, m->pm_field6};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->h_status) cudaFreeHost(m->h_status);
@@ -901,6 +957,7 @@ void qnep_destroy(qnep_model* m) {
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     if (m->ev_join) cudaEventDestroy(m->ev_join);
     if (m->aux) cudaStreamDestroy(m->aux);
+    if (m->have_c2r6) cufftDestroy(m->c2r6);
     if (m->have_mesh) {
         cufftDestroy(m->r2c);
         cufftDestroy(m->c2r);

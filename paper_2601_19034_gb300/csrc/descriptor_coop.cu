@@ -265,10 +265,17 @@ constexpr int BW_PHI = 2 * NANG;                // dE/dA weighted by lambda and 
 constexpr int BW_MU = 2 * MAX_SPECIES * KR;     // radial contractions per species
 constexpr int BW_WARP = BW_LK + BW_PHI + BW_MU;
 
-template <bool BEC>
-__device__ __forceinline__ void scatter_entry(float4* __restrict__ acc12, int j, float vx, float vy, float vz, float fx,
-                                              float fy, float fz, float ax, float ay, float az, float fi[3],
-                                              float zi[9], float w[9]) {
+template <bool BEC, bool AV>
+__device__ __forceinline__ void scatter_entry(float4* __restrict__ acc12, float* __restrict__ avir, int j, float vx,
+                                              float vy, float vz, float fx, float fy, float fz, float ax, float ay,
+                                              float az, float fi[3], float zi[9], float w[9]) {
+    if (AV) {
+        // per-atom virial: the entry (i -> j) adds -r_ij (x) F_ij to W_j (Sec. II.C, Eq. per-atom_virial)
+        float4* a4 = reinterpret_cast<float4*>(avir + (size_t)AVIR * j);
+        atomicAdd(&a4[0], make_float4(-vx * fx, -vx * fy, -vx * fz, -vy * fx));
+        atomicAdd(&a4[1], make_float4(-vy * fy, -vy * fz, -vz * fx, -vz * fy));
+        atomicAdd(avir + (size_t)AVIR * j + 8, -vz * fz);
+    }
     fi[0] += fx; fi[1] += fy; fi[2] += fz;
     w[0] -= vx * fx; w[1] -= vx * fy; w[2] -= vx * fz;
     w[3] -= vy * fx; w[4] -= vy * fy; w[5] -= vy * fz;
@@ -289,13 +296,13 @@ __device__ __forceinline__ void scatter_entry(float4* __restrict__ acc12, int j,
 
 // Three blocks per SM without BEC (80 registers; 1 M-atom Mg-water backward 3.29 -> 2.73 ms
 // against two blocks at 128), two with BEC (its larger scatter spills at 80 registers).
-template <bool BEC>
-__global__ void __launch_bounds__(32 * CW, BEC ? 2 : 3) k_desc_bwd_coop(
+template <bool BEC, bool AV>
+__global__ void __launch_bounds__(32 * CW, (BEC || AV) ? 2 : 3) k_desc_bwd_coop(
     const float4* __restrict__ spos4, const int* __restrict__ nbr_list, const int* __restrict__ cnt_list,
     const int* __restrict__ nbr_ang, const int* __restrict__ cnt_ang, int n, Geom g, const float* __restrict__ params,
     ParamLayout lay, const float* __restrict__ ang_coef, const float* __restrict__ du, const float* __restrict__ dqp,
     const float* __restrict__ q_raw, FieldIn fin, const Accum* __restrict__ acc_in, float4* __restrict__ acc12,
-    Accum* __restrict__ acc) {
+    Accum* __restrict__ acc, float* __restrict__ avir) {
     extern __shared__ float csm[];
     float* sp = csm;
     for (int k = threadIdx.x; k < lay.total; k += blockDim.x) sp[k] = params[k];
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(32 * CW, BEC ? 2 : 3) k_desc_bwd_coop(
                     skk = fmaf(mk[kk], df[kk], skk);
                 }
                 float ir = 1.f / r, ux = vx * ir, uy = vy * ir, uz = vz * ir;
-                scatter_entry<BEC>(acc12, entry_index(ent), vx, vy, vz, sl * ux, sl * uy, sl * uz, skk * ux,
+                scatter_entry<BEC, AV>(acc12, avir, entry_index(ent), vx, vy, vz, sl * ux, sl * uy, sl * uz, skk * ux,
                                    skk * uy, skk * uz, fi, zi, w);
             }
         };
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(32 * CW, BEC ? 2 : 3) k_desc_bwd_coop(
                 out[pass][1] = rho * uy + (gyy - gu * uy) * ir;
                 out[pass][2] = rho * uz + (gz - gu * uz) * ir;
             }
-            scatter_entry<BEC>(acc12, j, vx, vy, vz, out[0][0], out[0][1], out[0][2], out[1][0], out[1][1], out[1][2],
+            scatter_entry<BEC, AV>(acc12, avir, j, vx, vy, vz, out[0][0], out[0][1], out[0][2], out[1][0], out[1][1], out[1][2],
                                fi, zi, w);
         }
 #pragma unroll
@@ -568,30 +575,24 @@ void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* c
                           const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                           const float* ang_coef, const float* du, const float* dq, const float* q_raw,
                           const FieldIn& fin, const Accum* acc_in, bool want_bec, float* acc12, Accum* acc,
-                          cudaStream_t st) {
+                          cudaStream_t st, float* avir) {
     if (n == 0) return;
     size_t smem = sizeof(float) * ((size_t)round4(lay.total) + (size_t)CW * BW_WARP);
     float4* a4 = reinterpret_cast<float4*>(acc12);
-    static std::atomic<int> attr_t[kMaxDevices], attr_f[kMaxDevices];
-    static std::atomic<long long> occ_t[kMaxDevices], occ_f[kMaxDevices];
-    int per_sm;
-    if (want_bec) {
-        ensure_smem_attr(k_desc_bwd_coop<true>, attr_t, 100 * 1024);
-        per_sm = cached_occupancy(k_desc_bwd_coop<true>, occ_t, 32 * CW, smem);
-    } else {
-        ensure_smem_attr(k_desc_bwd_coop<false>, attr_f, 100 * 1024);
-        per_sm = cached_occupancy(k_desc_bwd_coop<false>, occ_f, 32 * CW, smem);
-    }
     int blocks = (n + CW - 1) / CW;
-    if (blocks > per_sm * num_sms()) blocks = per_sm * num_sms();
-    if (want_bec)
-        k_desc_bwd_coop<true><<<blocks, 32 * CW, smem, st>>>(spos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n,
-                                                                       g, params, lay, ang_coef, du, dq, q_raw, fin,
-                                                                       acc_in, a4, acc);
-    else
-        k_desc_bwd_coop<false><<<blocks, 32 * CW, smem, st>>>(spos4, nbr_list, cnt_list, nbr_ang, cnt_ang,
-                                                                        n, g, params, lay, ang_coef, du, dq, q_raw,
-                                                                        fin, acc_in, a4, acc);
+    auto run = [&](auto kernel, std::atomic<int>* attr, std::atomic<long long>* occ) {
+        ensure_smem_attr(kernel, attr, 100 * 1024);
+        const int per_sm = cached_occupancy(kernel, occ, 32 * CW, smem);
+        if (blocks > per_sm * num_sms()) blocks = per_sm * num_sms();
+        kernel<<<blocks, 32 * CW, smem, st>>>(spos4, nbr_list, cnt_list, nbr_ang, cnt_ang, n, g, params, lay, ang_coef,
+                                              du, dq, q_raw, fin, acc_in, a4, acc, avir);
+    };
+    static std::atomic<int> at[4][kMaxDevices];
+    static std::atomic<long long> oc[4][kMaxDevices];
+    if (want_bec && avir) run(k_desc_bwd_coop<true, true>, at[3], oc[3]);
+    else if (want_bec) run(k_desc_bwd_coop<true, false>, at[2], oc[2]);
+    else if (avir) run(k_desc_bwd_coop<false, true>, at[1], oc[1]);
+    else run(k_desc_bwd_coop<false, false>, at[0], oc[0]);
 }
 
 }  // namespace qnep

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
                                               const int* __restrict__ nbr_list, const int* __restrict__ cnt_list, int n,
                                               int n_species, Geom g, float alpha, float q_target,
                                               const Accum* __restrict__ acc_in, float4* __restrict__ rfield,
-                                              Accum* __restrict__ acc) {
+                                              Accum* __restrict__ acc, float* __restrict__ avir) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float wv[9];
 #pragma unroll
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
         int total = 0;
         for (int s = 0; s < n_species; ++s) total += __ldg(&cnt_list[(size_t)s * n + k]);
         float fx = 0.f, fy = 0.f, fz = 0.f, phr = 0.f;
+        float wa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // this atom's pair virial (xx, yy, zz, xy, xz, yz)
         for (int e = lane; e < total; e += 32) {
             const int ent = list_entry(nbr_list, k, e, g.list_sa, g.list_se);
             const int j = entry_index(ent);
@@ -244,6 +245,30 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
                 wv[0] -= vx * ax; wv[1] -= vx * ay; wv[2] -= vx * az;
                 wv[3] -= vy * ax; wv[4] -= vy * ay; wv[5] -= vy * az;
                 wv[6] -= vz * ax; wv[7] -= vz * ay; wv[8] -= vz * az;
+                if (avir) {
+                    // per atom: -r_kj (x) F^{r,static}_kj over the atom's entries (the pair's other entry
+                    // gives atom j the same symmetric tensor)
+                    wa[0] -= vx * ax; wa[1] -= vy * ay; wa[2] -= vz * az;
+                    wa[3] -= vx * ay; wa[4] -= vx * az; wa[5] -= vy * az;
+                }
+            }
+        }
+        if (avir) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wa[q] += __shfl_xor_sync(0xffffffffu, wa[q], o);
+            if (lane == 0) {
+                float* a = avir + (size_t)AVIR * k;
+                atomicAdd(a + 0, wa[0]);
+                atomicAdd(a + 4, wa[1]);
+                atomicAdd(a + 8, wa[2]);
+                atomicAdd(a + 1, wa[3]);
+                atomicAdd(a + 3, wa[3]);
+                atomicAdd(a + 2, wa[4]);
+                atomicAdd(a + 6, wa[4]);
+                atomicAdd(a + 5, wa[5]);
+                atomicAdd(a + 7, wa[5]);
             }
         }
 #pragma unroll
@@ -292,11 +317,13 @@ __global__ void __launch_bounds__(256) k_real(const float4* __restrict__ spos4, 
 //   phi^k_i = sum_half Re[C e^{i k.r_i}],  F^k_i = q_i sum_half k Im[C e^{i k.r_i}]
 // per column (n1, n2): T = sum_n3 C conj(Z(n3)), then conj(X Y) T.  Partial
 // results of the splits are added with float4 atomics to kfield = (F^k / q, phi^k).
-template <int W>
+// With the per-atom virial (AV) the same column sums are also weighted by B(k) per wave vector:
+//   V_i,ab = sum_half Re[C e^{i k.r_i}] B_ab(k)   (W_i^k = q_i / 2 V_i, the Heyes form of Sec. II.C)
+template <int W, bool AV>
 __global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csplit, float4* __restrict__ kfield,
-                                                    Accum* __restrict__ acc) {
+                                                    Accum* __restrict__ acc, float* __restrict__ avir) {
     extern __shared__ __align__(16) float2 stab[];
-    __shared__ float red[W][4][33];
+    __shared__ float red[W][AV ? 10 : 4][33];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int failed;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -322,6 +349,7 @@ __global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csp
         return;
     }
     float phk = 0.f, fk0 = 0.f, fk1 = 0.f, fk2 = 0.f;
+    float hv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (lane < cnt) {
         const float2* row = stab + lane * tab.nph;
         const float kxs = TWO_PI / tab.L[0], kys = TWO_PI / tab.L[1], kzs = TWO_PI / tab.L[2];
@@ -331,8 +359,22 @@ __global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csp
             const float2 x = row[ci.x], y = row[tab.yoff + ci.y + tab.n2max];
             const float2 xy = make_float2(fmaf(x.x, y.x, -x.y * y.y), fmaf(x.x, y.y, x.y * y.x));
             float tr = 0.f, ti = 0.f, tzr = 0.f, tzi = 0.f;
+            float hr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, hi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float2* zr = row + tab.zoff + ci.z + tab.n3max - ci.w;   // zr[k] = Z(n3(k))
             const float4* c4 = reinterpret_cast<const float4*>(tab.C);
+            if (AV) {
+                for (int k = ci.w; k < kend; ++k) {
+                    const float2 cc = tab.C[k], z0 = zr[k];
+                    const float pr = fmaf(cc.x, z0.x, cc.y * z0.y), pim = fmaf(cc.y, z0.x, -cc.x * z0.y);
+                    const float4 b0 = __ldg(&tab.kb[2 * k]), b1 = __ldg(&tab.kb[2 * k + 1]);
+                    const float bv[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        hr[q] = fmaf(bv[q], pr, hr[q]);
+                        hi[q] = fmaf(bv[q], pim, hi[q]);
+                    }
+                }
+            }
             for (int k = ci.w; k < kend; k += 8) {
                 const float n3b = (float)(ci.z + (k - ci.w));
 #pragma unroll
@@ -360,23 +402,35 @@ __global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csp
             fk0 = fmaf(kxs * ci.x, zim, fk0);
             fk1 = fmaf(kys * ci.y, zim, fk1);
             fk2 = fmaf(kzs, zzi, fk2);
+            if (AV) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) hv[q] += fmaf(xy.x, hr[q], xy.y * hi[q]);
+            }
         }
     }
     red[w][0][lane] = phk;
     red[w][1][lane] = fk0;
     red[w][2][lane] = fk1;
     red[w][3][lane] = fk2;
+    if (AV) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) red[w][4 + q][lane] = hv[q];
+    }
     __syncthreads();
     if (w == 0) {
-        float t[4];
+        float t[10];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < (AV ? 10 : 4); ++q) {
             float v = 0.f;
 #pragma unroll
             for (int u = 0; u < W; ++u) v += red[u][q][lane];
             t[q] = v;
         }
         if (lane < cnt) atomicAdd(&kfield[i], make_float4(t[1], t[2], t[3], t[0]));
+        if (AV && lane < cnt) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) atomicAdd(&avir[(size_t)AVIR * i + 9 + q], t[4 + q]);
+        }
         float sp = lane < cnt ? t[0] : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
@@ -400,6 +454,10 @@ __device__ __forceinline__ void write_scalars(const Accum* __restrict__ acc, int
     if (status_host) *status_host = acc->status;
 }
 
+__device__ __forceinline__ void atomic_virial_store(float* __restrict__ out, int io, int q, float v) {
+    out[9 * (size_t)io + q] = v;
+}
+
 // Per-atom outputs back in input order (forces, BEC, charges q^c, potential
 // phi = phi^k + phi^r + phi^s, site energies), the block sums of P = sum q~^c r,
 // U^s = -k_e alpha/sqrt(pi) sum q^c^2 and sum q~^c; the last block writes the scalars.
@@ -410,7 +468,8 @@ __global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __
                            float* __restrict__ charges, float* __restrict__ potential, const float* __restrict__ u,
                            float* __restrict__ site_energy, Accum* __restrict__ acc, double* __restrict__ scalars,
                            unsigned int* __restrict__ status_host, unsigned int* __restrict__ done,
-                           float* __restrict__ grad, float gpx, float gpy, float gpz) {
+                           float* __restrict__ grad, float gpx, float gpy, float gpz, const float* __restrict__ avir,
+                           float* __restrict__ atom_virial) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     // FP32 terms summed over a warp (32 atoms), then FP64 across warps and blocks
     float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // P (3), U^s, sum q~^c
@@ -435,6 +494,14 @@ __global__ void k_finalize(const float* __restrict__ acc12, int n, const int* __
                 grad[3 * (size_t)io + b] = -a[b] + gpx * a[3 + b] + gpy * a[6 + b] + gpz * a[9 + b];
         }
         if (charges) charges[io] = qc;
+        if (atom_virial) {
+            // entries and real space, plus q_i / 2 times the reciprocal-space sums (symmetric)
+            const float* w = avir + (size_t)AVIR * k;
+            const float h = 0.5f * qc;
+            const float kv[9] = {w[9], w[12], w[13], w[12], w[10], w[14], w[13], w[14], w[11]};
+#pragma unroll
+            for (int q = 0; q < 9; ++q) atomic_virial_store(atom_virial, io, q, fmaf(h, kv[q], w[q]));
+        }
         const float phs = ec.mode == 1 ? -2.f * KE * ec.alpha * INV_SQRT_PI * qc : 0.f;
         if (potential) potential[io] = kfield[k].w + rfield[k].w + phs;
         if (site_energy) site_energy[io] = u[k];
@@ -517,43 +584,45 @@ void launch_field(const float4* pos4, const float* pos_in, const float* q_raw, c
 
 void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, const int* cnt_list, int n,
                  int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
-                 Accum* acc, cudaStream_t st) {
+                 Accum* acc, cudaStream_t st, float* avir) {
     if (n == 0) return;
     // persistent warps: one wave of resident blocks, fewer for small systems
     static std::atomic<long long> occ[kMaxDevices];
     const int per_sm = cached_occupancy(k_real, occ, 256, 0);
     const int blocks = std::max(1, std::min((n + 7) / 8, per_sm * num_sms()));
     k_real<<<blocks, 256, 0, st>>>(spos4, q_raw, nbr_list, cnt_list, n, n_species, g, alpha, q_target, acc_in, rfield,
-                                   acc);
+                                   acc, avir);
 }
 
-void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st) {
+void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st, float* avir) {
     if (n == 0 || tab.ncol == 0) return;
     constexpr int W = 8;
-    static std::atomic<int> attr[kMaxDevices];
-    ensure_smem_attr(k_field_k<W>, attr, 160 * 1024);
+    static std::atomic<int> attr[kMaxDevices], attr_v[kMaxDevices];
+    ensure_smem_attr(k_field_k<W, false>, attr, 160 * 1024);
+    if (avir) ensure_smem_attr(k_field_k<W, true>, attr_v, 160 * 1024);
     const int groups = (n + 31) / 32;
     const size_t smem = sizeof(float2) * 32 * tab.nph;
     // column splits: fill the resident block slots (SMs x blocks per SM at this shared-memory
     // size) in one wave; a partial second wave would double the time of the SMs running it
     static std::atomic<long long> occ[kMaxDevices];
-    const int slots = num_sms() * cached_occupancy(k_field_k<W>, occ, 32 * W, smem);
+    const int slots = num_sms() * cached_occupancy(k_field_k<W, false>, occ, 32 * W, smem);
     int csplit = slots / groups;
     if (csplit < 1) csplit = 1;
     if (csplit > tab.ncol) csplit = tab.ncol;
-    k_field_k<W><<<groups * csplit, 32 * W, smem, st>>>(n, tab, csplit, kfield, acc);
+    if (avir) k_field_k<W, true><<<groups * csplit, 32 * W, smem, st>>>(n, tab, csplit, kfield, acc, avir);
+    else k_field_k<W, false><<<groups * csplit, 32 * W, smem, st>>>(n, tab, csplit, kfield, acc, nullptr);
 }
 
 void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
                      float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
                      float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
                      Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st,
-                     float* grad, const float* gp) {
+                     float* grad, const float* gp, const float* avir, float* atom_virial) {
     int blocks = (n + 255) / 256;
     if (blocks < 1) blocks = 1;
     k_finalize<<<blocks, 256, 0, st>>>(acc12, n, sidx, pos_in, q_raw, q_target, seps, ec, kfield, rfield, forces, bec,
                                        charges, potential, u, site_energy, acc, scalars, status_host, done, grad,
-                                       gp ? gp[0] : 0.f, gp ? gp[1] : 0.f, gp ? gp[2] : 0.f);
+                                       gp ? gp[0] : 0.f, gp ? gp[1] : 0.f, gp ? gp[2] : 0.f, avir, atom_virial);
 }
 
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi, float* potential,

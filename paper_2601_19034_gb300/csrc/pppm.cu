@@ -153,6 +153,15 @@ __global__ void __launch_bounds__(256) k_pppm_green(PppmTab pm, float alpha, Acc
         pm.fhat[pm.nhalf + idx] = nyx ? make_float2(0.f, 0.f) : make_float2(-kx * sg.y, kx * sg.x);
         pm.fhat[2 * pm.nhalf + idx] = nyy ? make_float2(0.f, 0.f) : make_float2(-ky * sg.y, ky * sg.x);
         pm.fhat[3 * pm.nhalf + idx] = nyz ? make_float2(0.f, 0.f) : make_float2(-kz * sg.y, kz * sg.x);
+        if (pm.fhat6) {
+            // per-atom virial fields G_opt B_ab S, B = I - (2 / (4 alpha^2) + 2 / k^2) k k^T (zero at k = 0)
+            const float k2 = kx * kx + ky * ky + kz * kz;
+            const float fac = k2 > 0.f ? fac0 + 2.f / k2 : 0.f;
+            const float bv[6] = {1.f - fac * kx * kx, 1.f - fac * ky * ky, 1.f - fac * kz * kz, -fac * kx * ky,
+                                 -fac * kx * kz, -fac * ky * kz};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) pm.fhat6[q * pm.nhalf + idx] = make_float2(bv[q] * sg.x, bv[q] * sg.y);
+        }
         if (g > 0.f) {
             const float mult = (n3 == 0 || (pm.nz % 2 == 0 && n3 == pm.nz / 2)) ? 1.f : 2.f;
             const float e = mult * KE * g * (s.x * s.x + s.y * s.y);
@@ -267,6 +276,46 @@ __global__ void k_pppm_gather(const float4* __restrict__ spos4, int n, PppmTab p
     }
 }
 
+// Per-atom reciprocal-space virial on the mesh: 2 k_e sum_s W(r_i - r_s) F^-1[G_opt B_ab S](r_s)
+// for the six components (lanes over the 125 stencil points; one warp per atom at a time).
+__global__ void k_pppm_gather_virial(const float4* __restrict__ spos4, int n, PppmTab pm, float* __restrict__ avir) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += nwarps) {
+        const float4 p = __ldg(&spos4[k]);
+        int sx, sy, sz;
+        float wx[5], wy[5], wz[5];
+        stencil_axis(p.x, pm.inv_h[0], pm.inv_h_lo[0], sx, wx);
+        stencil_axis(p.y, pm.inv_h[1], pm.inv_h_lo[1], sy, wy);
+        stencil_axis(p.z, pm.inv_h[2], pm.inv_h_lo[2], sz, wz);
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int t = lane; t < 125; t += 32) {
+            const int a = t / 25, b = (t / 5) % 5, c = t % 5;
+            float wa = wx[0], wb = wy[0], wc = wz[0];
+#pragma unroll
+            for (int m = 1; m < 5; ++m) {
+                if (a == m) wa = wx[m];
+                if (b == m) wb = wy[m];
+                if (c == m) wc = wz[m];
+            }
+            const float w = wa * wb * wc;
+            const size_t idx =
+                ((size_t)wrap(sx + a, pm.nx) * pm.ny + wrap(sy + b, pm.ny)) * pm.nz + wrap(sz + c, pm.nz);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[q] = fmaf(w, __ldg(&pm.field6[q * pm.nreal + idx]), v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) avir[(size_t)AVIR * k + 9 + q] = 2.f * KE * v[q];
+        }
+    }
+}
+
 }  // namespace
 
 void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t st) {
@@ -274,7 +323,7 @@ void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t 
 }
 
 int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc_in, float q_target, PppmTab pm,
-                float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st) {
+                float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st, int c2r6, float* avir) {
     if (n == 0) return 0;
     const int threads = 256;
     // persistent warps over the atoms and persistent threads over the half spectrum: one
@@ -295,6 +344,11 @@ int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc
     if (cufftSetStream(c2r, st) != CUFFT_SUCCESS) return 1;
     if (cufftExecC2R(c2r, reinterpret_cast<cufftComplex*>(pm.fhat), pm.field) != CUFFT_SUCCESS) return 1;
     k_pppm_gather<<<hblocks, threads, 0, st>>>(spos4, n, pm, kfield, acc);
+    if (avir && pm.fhat6) {   // the six per-atom virial fields (one batched inverse transform)
+        if (cufftSetStream(c2r6, st) != CUFFT_SUCCESS) return 1;
+        if (cufftExecC2R(c2r6, reinterpret_cast<cufftComplex*>(pm.fhat6), pm.field6) != CUFFT_SUCCESS) return 1;
+        k_pppm_gather_virial<<<hblocks, threads, 0, st>>>(spos4, n, pm, avir);
+    }
     return 0;
 }
 

@@ -145,7 +145,17 @@ struct EwaldTab {
     double2* S;           // [nk] structure factor sum_i q_i exp(-i k.r_i) (FP64)
     float2* C;            // [nk] 4 k_e G(k) S(k) (FP32) for the force / potential pass
     float2* phase;        // [N][nph]: X[0..n1max], Y[-n2max..n2max], Z[-n3max..n3max+7]
+    const float4* kb;     // [2 nk] B(k) = I - (2 / (4 alpha^2) + 2 / k^2) k k^T as (xx, yy, zz, xy), (xz, yz, -, -),
+                          // zero on padding (per-atom virial only; may be NULL otherwise)
 };
+
+// Per-atom virial scratch of one force call (sorted order), AVIR floats per atom:
+// [0..8]  W_i of the neighbour entries (partial forces, -r_ij (x) F_ij added to W_j) and of the
+//         static real-space pair terms, row-major 3 x 3;
+// [9..14] the static reciprocal-space term per unit charge, (xx, yy, zz, xy, xz, yz):
+//         sum_half Re[C e^{i k.r_i}] B(k) (Ewald) or 2 k_e sum_s W(r_i - r_s) F^-1[G_opt B S](r_s)
+//         (PPPM); W_i^k = q_i / 2 times it.
+constexpr int AVIR = 16;
 
 // PPPM mesh description (Sec. II.F); meshes are [nx][ny][nz] (z fastest), the half
 // spectrum [nx][ny][nz/2 + 1].
@@ -161,6 +171,9 @@ struct PppmTab {
     float2* fhat;        // 4 x nhalf: S G_opt, i k_x S G_opt, i k_y S G_opt, i k_z S G_opt
     float* field;        // 4 x nreal: their unnormalised inverse transforms
     float* gopt;         // nhalf: optimal influence function
+    float alpha;         // Ewald splitting parameter (per-atom virial fields)
+    float2* fhat6;       // 6 x nhalf: G_opt B_ab S (per-atom virial; NULL when not asked for)
+    float* field6;       // 6 x nreal: their unnormalised inverse transforms
 };
 
 __device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }
@@ -239,7 +252,7 @@ void launch_desc_bwd_coop(const float4* spos4, const int* nbr_list, const int* c
                           const int* cnt_ang, int n, const Geom& g, const float* params, const ParamLayout& lay,
                           const float* ang_coef, const float* du, const float* dq, const float* q_raw,
                           const FieldIn& fin, const Accum* acc_in, bool want_bec, float* acc12, Accum* acc,
-                          cudaStream_t st);
+                          cudaStream_t st, float* avir = nullptr);
 void launch_ewald_phases(const float4* pos4, int n, EwaldTab tab, cudaStream_t st);
 void launch_ewald_sk(const float* q_raw, const Accum* acc, int n, float q_target, EwaldTab tab, cudaStream_t st);
 void launch_ewald_sk_fused(const float* q_raw, Accum* acc, int n, float q_target, EwaldTab tab,
@@ -256,8 +269,8 @@ void launch_descriptor_backward(const float4* pos4, const int* nbr_list, const i
                                 const Accum* acc_in, bool want_bec, float* acc12, Accum* acc, cudaStream_t st);
 void launch_real(const float4* spos4, const float* q_raw, const int* nbr_list, const int* cnt_list, int n,
                  int n_species, const Geom& g, float alpha, float q_target, const Accum* acc_in, float4* rfield,
-                 Accum* acc, cudaStream_t st);
-void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st);
+                 Accum* acc, cudaStream_t st, float* avir = nullptr);
+void launch_field_k(int n, const EwaldTab& tab, float4* kfield, Accum* acc, cudaStream_t st, float* avir = nullptr);
 // Network on the tensor cores for n atoms (precision PREC_BF16 or PREC_TF32): scaled
 // descriptors dtc [n][32] (sorted order) -> u, q, du / dq (element k, v at k d_sa + v d_sv),
 // FP64 sums of u and q into acc.
@@ -273,12 +286,14 @@ void launch_vv_kick_energy(int n, float* vel, const float* f, const int* types, 
                            unsigned int* done, cudaStream_t st);
 void launch_pppm_gopt(const PppmTab& pm, double alpha, double vol, cudaStream_t st);
 int launch_pppm(const float4* spos4, const float* q_raw, int n, const Accum* acc_in, float q_target, PppmTab pm,
-                float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st);
+                float alpha, int r2c, int c2r, float4* kfield, Accum* acc, cudaStream_t st, int c2r6 = 0,
+                float* avir = nullptr);
 void launch_finalize(const float* acc12, int n, const int* sidx, const float* pos_in, const float* q_raw,
                      float q_target, float seps, ElecConst ec, const float4* kfield, const float4* rfield,
                      float* forces, float* bec, float* charges, float* potential, const float* u, float* site_energy,
                      Accum* acc, double* scalars, unsigned int* status_host, unsigned int* done, cudaStream_t st,
-                     float* grad = nullptr, const float* gp = nullptr);
+                     float* grad = nullptr, const float* gp = nullptr, const float* avir = nullptr,
+                     float* atom_virial = nullptr);
 void launch_finalize_atoms(const float* acc12, int n, float* forces, float* bec, const float* phi,
                            float* potential, cudaStream_t st);
 void launch_finalize_scalars(const Accum* acc, int n, float sqrt_eps, double* scalars, cudaStream_t st);

@@ -94,7 +94,7 @@ class QNEP:
         _lib.check(self.lib.qnep_reserve(self.handle, int(n_atoms), self._box), self.handle)
 
     def outputs(self, n: int, device, forces=True, bec=True, charges=True, virial=True,
-                descriptor=False, potential=False, site_energy=False) -> dict:
+                descriptor=False, potential=False, site_energy=False, atom_virial=False) -> dict:
         """Allocate an output dict of CUDA tensors for ``compute_into``."""
         out = {"scalars": torch.zeros(_lib.QNEP_NSCALARS, dtype=torch.float64, device=device)}
         if forces:
@@ -109,6 +109,8 @@ class QNEP:
             out["potential"] = torch.empty(n, dtype=torch.float32, device=device)
         if site_energy:
             out["site_energy"] = torch.empty(n, dtype=torch.float32, device=device)
+        if atom_virial:
+            out["atom_virial"] = torch.empty(n, 3, 3, dtype=torch.float32, device=device)
         out["_virial"] = bool(virial)
         return out
 
@@ -124,7 +126,7 @@ class QNEP:
             return t.data_ptr() if t is not None else None
 
         oc = _lib.OutputsC(ptr("scalars"), ptr("forces"), ptr("charges"), ptr("bec"), ptr("site_energy"),
-                           ptr("potential"), ptr("descriptor"), 1 if out.get("_virial") else 0)
+                           ptr("potential"), ptr("descriptor"), 1 if out.get("_virial") else 0, ptr("atom_virial"))
         if stream is None:
             stream = torch.cuda.current_stream(positions.device).cuda_stream
         st = self.lib.qnep_compute(self.handle, n, positions.data_ptr(), types.data_ptr(), self._box,

@@ -55,7 +55,7 @@ def test_struct_layouts_match_header():
     # qnep_elec: int, int, double x3, int[3], int, double -> 56 bytes with natural alignment
     assert ctypes.sizeof(_lib.ElecC) == 56
     assert ctypes.sizeof(_lib.HParamsC) == 40
-    assert ctypes.sizeof(_lib.OutputsC) == 64
+    assert ctypes.sizeof(_lib.OutputsC) == 72
 
 
 def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
