@@ -140,8 +140,11 @@ qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]);
 /* One force call on one structure with candidate 0.
  *   positions: device [N][3] float32 (A); may lie outside the box (wrapped internally)
  *   types:     device [N] int32 species index in [0, n_species)
- *   box:       host double[9], rows = lattice vectors; orthorhombic only in this
- *              build (QNEP_ERR_UNSUPPORTED otherwise), every edge >= the list cutoff
+ *   box:       host double[9], rows = lattice vectors a, b, c (right-handed); a general
+ *              (triclinic) cell with Ewald electrostatics or none, orthorhombic with PPPM
+ *              (QNEP_ERR_UNSUPPORTED otherwise); every perpendicular width V / |a_e x a_f| >= the
+ *              list cutoff.  In a general cell the images are integer combinations of the rows
+ *              and the Ewald wave vectors are k = 2 pi H^-1 n (Sec. II.B).
  *   stream:    cudaStream_t (NULL = legacy default stream)
  * Asynchronous: returns after enqueueing.  Device-side errors (neighbour
  * overflow) are recorded in scalars[QNEP_S_STATUS] and returned by the next

@@ -67,6 +67,7 @@ struct qnep_model {
     // geometry / Ewald tables, rebuilt when the box changes
     bool have_box = false;
     double box[9]{};
+    double width[3]{};              // perpendicular widths of the cell (the edges of an orthorhombic box)
     Geom geom{};
     EwaldTab tab{};
     int nk_alloc = 0, ncol_alloc = 0, nchunk_alloc = 0;
@@ -155,8 +156,10 @@ float list_cutoff(const qnep_model* m) {
 }
 
 // Half-space Ewald k-set in columns (n1, n2) with runs of n3, chunks of 8.
-qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
-    KSet ks = build_kset(L, m->es.kmax, m->es.alpha);
+qnep_status build_ewald_table(qnep_model* m, const double L[3], const double* box, bool tri) {
+    KSet ks = tri ? build_kset_box(box, m->es.kmax, m->es.alpha) : build_kset(L, m->es.kmax, m->es.alpha);
+    double hinv[9];
+    invert3(box, hinv);
     const int* nmax = ks.nmax;
     const std::vector<int4>& cols = ks.cols;
     const std::vector<int>& chunk_col = ks.chunk_col;
@@ -199,7 +202,12 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
                 const int k = 8 * gi + t;
                 if (!(kg[k] > 0.f)) continue;
                 const int n3 = c.z + (k - c.w);
-                const double kx = tp * c.x / L[0], ky = tp * c.y / L[1], kz = tp * n3 / L[2];
+                double kx = tp * c.x / L[0], ky = tp * c.y / L[1], kz = tp * n3 / L[2];
+                if (tri) {
+                    kx = tp * (hinv[0] * c.x + hinv[1] * c.y + hinv[2] * n3);
+                    ky = tp * (hinv[3] * c.x + hinv[4] * c.y + hinv[5] * n3);
+                    kz = tp * (hinv[6] * c.x + hinv[7] * c.y + hinv[8] * n3);
+                }
                 const double fac = 2.0 / (4.0 * m->es.alpha * m->es.alpha) + 2.0 / (kx * kx + ky * ky + kz * kz);
                 kb[2 * k] = make_float4((float)(1.0 - fac * kx * kx), (float)(1.0 - fac * ky * ky),
                                         (float)(1.0 - fac * kz * kz), (float)(-fac * kx * ky));
@@ -227,6 +235,12 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3]) {
         double il = 1.0 / L[d];
         t.invl_hi[d] = (float)il;
         t.invl_lo[d] = (float)(il - (double)t.invl_hi[d]);
+    }
+    t.tri = tri ? 1 : 0;
+    for (int k = 0; k < 9; ++k) {
+        t.hi_hi[k] = (float)hinv[k];
+        t.hi_lo[k] = (float)(hinv[k] - (double)t.hi_hi[k]);
+        t.krec[k] = (float)(6.283185307179586 * hinv[k]);
     }
     t.alpha = (float)alpha;
     t.col = m->d_col;
@@ -278,23 +292,41 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
     if (!box) return fail(m, QNEP_ERR_ARG, "box is NULL");
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(box[k])) return fail(m, QNEP_ERR_ARG, "box has a non-finite entry");
-    if (box[1] != 0 || box[2] != 0 || box[3] != 0 || box[5] != 0 || box[6] != 0 || box[7] != 0)
-        return fail(m, QNEP_ERR_UNSUPPORTED, "only orthorhombic boxes are supported");
-    double L[3] = {box[0], box[4], box[8]};
+    const bool tri = box[1] != 0 || box[2] != 0 || box[3] != 0 || box[5] != 0 || box[6] != 0 || box[7] != 0;
+    if (tri && m->es.mode != 0 && m->es.kind == QNEP_PPPM)
+        return fail(m, QNEP_ERR_UNSUPPORTED, "PPPM runs on orthorhombic boxes only (Ewald takes general cells)");
+    // edge lengths and the perpendicular widths V / |a_e x a_f| (the cell grid needs width >= cutoff)
+    double L[3], width[3], hinv[9];
+    const double det = invert3(box, hinv);
+    for (int d = 0; d < 3; ++d) {
+        const double* a = box + 3 * d;
+        L[d] = tri ? std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) : box[4 * d];
+        const double* e = box + 3 * ((d + 1) % 3);
+        const double* f = box + 3 * ((d + 2) % 3);
+        const double cx = e[1] * f[2] - e[2] * f[1], cy = e[2] * f[0] - e[0] * f[2], cz = e[0] * f[1] - e[1] * f[0];
+        width[d] = tri ? det / std::sqrt(cx * cx + cy * cy + cz * cz) : L[d];
+    }
+    if (tri && !(det > 0)) return fail(m, QNEP_ERR_ARG, "the cell vectors must be independent and right-handed");
     const float rcl = list_cutoff(m);
     for (int d = 0; d < 3; ++d) {
         if (!(L[d] > 0)) return fail(m, QNEP_ERR_ARG, "box edge must be positive");
-        if (L[d] < rcl) return fail(m, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff");
+        if (width[d] < rcl) return fail(m, QNEP_ERR_UNSUPPORTED, "cell width shorter than the list cutoff");
     }
     bool box_changed = !m->have_box || std::memcmp(m->box, box, sizeof(double) * 9) != 0;
     if (box_changed) {
         if (m->have_box) CK(cudaStreamSynchronize(st));   // in-flight kernels may read the old tables
         Geom& g = m->geom;
         g.ncells = 1;
+        g.tri = tri ? 1 : 0;
+        for (int k = 0; k < 9; ++k) {
+            g.H[k] = (float)box[k];
+            g.Hi[k] = (float)hinv[k];
+        }
         for (int d = 0; d < 3; ++d) {
             g.L[d] = (float)L[d];
             g.invL[d] = (float)(1.0 / L[d]);
-            int nc = (int)std::floor(L[d] / rcl);
+            m->width[d] = width[d];
+            int nc = (int)std::floor(width[d] / rcl);
             g.nc[d] = nc < 1 ? 1 : nc;
             g.ncells *= g.nc[d];
         }
@@ -310,7 +342,7 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             m->ncell_alloc = g.ncells + 1;
         }
         if (m->es.mode != 0 && m->es.kind == QNEP_EWALD) {
-            qnep_status s = build_ewald_table(m, L);
+            qnep_status s = build_ewald_table(m, L, box, tri);
             if (s != QNEP_OK) return s;
             int groups = (m->tab.nchunk + 31) / 32 + 1;
             if (groups > m->sk_done_alloc) {
@@ -655,8 +687,8 @@ qnep_status compute_impl(qnep_model* m, int n, const float* positions, const int
         Geom gk = g;
         gk.ncells = 1;
         for (int d = 0; d < 3; ++d) {
-            if (g.L[d] < rs) return fail(m, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff plus the skin");
-            const int nc = (int)std::floor((double)g.L[d] / (double)rs);
+            if (m->width[d] < rs) return fail(m, QNEP_ERR_UNSUPPORTED, "cell width shorter than the list cutoff plus the skin");
+            const int nc = (int)std::floor(m->width[d] / (double)rs);
             gk.nc[d] = nc < 1 ? 1 : nc;
             gk.ncells *= gk.nc[d];
         }

@@ -159,6 +159,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         if (t.n > 32768) return failb(b, QNEP_ERR_UNSUPPORTED, "batched structures hold at most 32768 atoms");
         nmax = std::max(nmax, t.n);
         Geom& g = t.g;
+        g.tri = 0;
         g.ncells = 1;
         for (int d = 0; d < 3; ++d) {
             if (!(L[d] > 0)) return failb(b, QNEP_ERR_ARG, "box edge must be positive");

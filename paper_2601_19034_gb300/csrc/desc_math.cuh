@@ -109,9 +109,11 @@ __device__ __forceinline__ void entry_vector(const float4* __restrict__ pos4, in
     float tx, ty, tz;
     entry_shift(e, tx, ty, tz);
     float4 pj = __ldg(&pos4[j]);
-    vx = (pj.x - pi.x) + tx * g.L[0];
-    vy = (pj.y - pi.y) + ty * g.L[1];
-    vz = (pj.z - pi.z) + tz * g.L[2];
+    float sx, sy, sz;
+    shift_vector(g, tx, ty, tz, sx, sy, sz);
+    vx = (pj.x - pi.x) + sx;
+    vy = (pj.y - pi.y) + sy;
+    vz = (pj.z - pi.z) + sz;
 }
 
 // 4-body: T_n from the l = 2 expansion coefficients (unnormalised harmonics 3..7)
@@ -156,8 +158,35 @@ __device__ __forceinline__ float2 phase_factor(float x, int nn, float il_hi, flo
     return make_float2(cs, -sn);
 }
 
+// exp(-i 2 pi nn s_c) of a general cell, s_c = sum_d r_d Hi[d][c]: each of the three products
+// nn r_d Hi[d][c] is reduced to its fractional part exactly (as in phase_factor), then the three
+// fractions are added
+__device__ __forceinline__ float2 phase_factor_tri(const float4& p, int nn, int c, const EwaldTab& tab) {
+    const float fn = (float)nn;
+    const float r[3] = {p.x, p.y, p.z};
+    float fr = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float h = tab.hi_hi[3 * d + c], hl = tab.hi_lo[3 * d + c];
+        const float pp = fn * r[d];
+        const float pe = fmaf(fn, r[d], -pp);
+        const float u = pp * h;
+        const float ue = fmaf(pp, h, -u);
+        const float lo = ue + fmaf(pp, hl, pe * h);
+        fr += (u - rintf(u)) + lo;
+    }
+    float sn, cs;
+    sincospif(2.f * fr, &sn, &cs);
+    return make_float2(cs, -sn);
+}
+
 // Row entry e of an atom's phase row: X(n1), Y(n2) or Z(n3) factor (see EwaldTab).
 __device__ __forceinline__ float2 phase_entry(const float4& p, int e, const EwaldTab& tab) {
+    if (tab.tri) {
+        if (e < tab.yoff) return phase_factor_tri(p, e, 0, tab);
+        if (e < tab.zoff) return phase_factor_tri(p, e - tab.yoff - tab.n2max, 1, tab);
+        return phase_factor_tri(p, e - tab.zoff - tab.n3max, 2, tab);
+    }
     if (e < tab.yoff) return phase_factor(p.x, e, tab.invl_hi[0], tab.invl_lo[0]);
     if (e < tab.zoff) return phase_factor(p.y, e - tab.yoff - tab.n2max, tab.invl_hi[1], tab.invl_lo[1]);
     return phase_factor(p.z, e - tab.zoff - tab.n3max, tab.invl_hi[2], tab.invl_lo[2]);

@@ -412,8 +412,9 @@ __global__ void __launch_bounds__(32 * CW, (BEC || AV) ? 2 : 3) k_desc_bwd_coop(
         auto radial_entry = [&](int ent, const float4& pj) {
             float tx, ty, tz;
             entry_shift(ent, tx, ty, tz);
-            const float vx = (pj.x - pk.x) + tx * g.L[0], vy = (pj.y - pk.y) + ty * g.L[1],
-                        vz = (pj.z - pk.z) + tz * g.L[2];
+            float shx, shy, shz;
+            shift_vector(g, tx, ty, tz, shx, shy, shz);
+            const float vx = (pj.x - pk.x) + shx, vy = (pj.y - pk.y) + shy, vz = (pj.z - pk.z) + shz;
             const float r2 = vx * vx + vy * vy + vz * vz;
             if (r2 < rcr2) {
                 const int tj = __float_as_int(pj.w);

@@ -38,6 +38,11 @@ __device__ __forceinline__ void finalize_k(const EwaldTab& tab, int k, double v[
     int n3 = ci.z + (k - ci.w);
     const float tp = 6.28318530717958648f;
     float kx = tp * ci.x / tab.L[0], ky = tp * ci.y / tab.L[1], kz = tp * n3 / tab.L[2];
+    if (tab.tri) {   // k = 2 pi H^-1 n
+        kx = tab.krec[0] * ci.x + tab.krec[1] * ci.y + tab.krec[2] * n3;
+        ky = tab.krec[3] * ci.x + tab.krec[4] * ci.y + tab.krec[5] * n3;
+        kz = tab.krec[6] * ci.x + tab.krec[7] * ci.y + tab.krec[8] * n3;
+    }
     float fac = 2.f / (4.f * tab.alpha * tab.alpha) + 2.f / (kx * kx + ky * ky + kz * kz);
     double e = 2.0 * KE_D * (double)gk * (s.x * s.x + s.y * s.y);
     v[0] += e;

@@ -83,9 +83,16 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
             float zim = fmaf(xy.x, ti, -xy.y * tr);
             float zzi = fmaf(xy.x, tzi, -xy.y * tzr);
             phk += zre;
-            fk[0] = fmaf(kxs * ci.x, zim, fk[0]);
-            fk[1] = fmaf(kys * ci.y, zim, fk[1]);
-            fk[2] = fmaf(kzs, zzi, fk[2]);
+            if (tab.tri) {   // k = 2 pi H^-1 (n1, n2, n3): the n3 part from the n3-weighted sum
+#pragma unroll
+                for (int dd = 0; dd < 3; ++dd)
+                    fk[dd] = fmaf(tab.krec[3 * dd + 2], zzi,
+                                  fmaf(tab.krec[3 * dd] * ci.x + tab.krec[3 * dd + 1] * ci.y, zim, fk[dd]));
+            } else {
+                fk[0] = fmaf(kxs * ci.x, zim, fk[0]);
+                fk[1] = fmaf(kys * ci.y, zim, fk[1]);
+                fk[2] = fmaf(kzs, zzi, fk[2]);
+            }
         }
     }
     if (valid && !ewald && pppm_field && w == 0) {
@@ -106,9 +113,11 @@ __global__ void __launch_bounds__(32 * W) k_field(const float4* __restrict__ pos
             float tx, ty, tz;
             entry_shift(ent, tx, ty, tz);
             float4 pj = __ldg(&pos4[j]);
-            float vx = (pj.x - pi.x) + tx * g.L[0];
-            float vy = (pj.y - pi.y) + ty * g.L[1];
-            float vz = (pj.z - pi.z) + tz * g.L[2];
+            float shx, shy, shz;
+            shift_vector(g, tx, ty, tz, shx, shy, shz);
+            float vx = (pj.x - pi.x) + shx;
+            float vy = (pj.y - pi.y) + shy;
+            float vz = (pj.z - pi.z) + shz;
             float r2 = vx * vx + vy * vy + vz * vz;
             if (r2 < rc2) {
                 float r = sqrtf(r2), ir = 1.f / r;
@@ -399,9 +408,15 @@ __global__ void __launch_bounds__(32 * W) k_field_k(int n, EwaldTab tab, int csp
             const float zim = fmaf(xy.x, ti, -xy.y * tr);
             const float zzi = fmaf(xy.x, tzi, -xy.y * tzr);
             phk += zre;
-            fk0 = fmaf(kxs * ci.x, zim, fk0);
-            fk1 = fmaf(kys * ci.y, zim, fk1);
-            fk2 = fmaf(kzs, zzi, fk2);
+            if (tab.tri) {   // k = 2 pi H^-1 (n1, n2, n3): the n3 part from the n3-weighted sum
+                fk0 = fmaf(tab.krec[2], zzi, fmaf(tab.krec[0] * ci.x + tab.krec[1] * ci.y, zim, fk0));
+                fk1 = fmaf(tab.krec[5], zzi, fmaf(tab.krec[3] * ci.x + tab.krec[4] * ci.y, zim, fk1));
+                fk2 = fmaf(tab.krec[8], zzi, fmaf(tab.krec[6] * ci.x + tab.krec[7] * ci.y, zim, fk2));
+            } else {
+                fk0 = fmaf(kxs * ci.x, zim, fk0);
+                fk1 = fmaf(kys * ci.y, zim, fk1);
+                fk2 = fmaf(kzs, zzi, fk2);
+            }
             if (AV) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) hv[q] += fmaf(xy.x, hr[q], xy.y * hi[q]);

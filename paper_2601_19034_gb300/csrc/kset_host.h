@@ -59,4 +59,73 @@ inline KSet build_kset(const double L[3], double kmax, double alpha) {
     return ks;
 }
 
+// Inverse of a 3 x 3 row-major matrix; returns the determinant (0: singular, inverse not written).
+inline double invert3(const double h[9], double hi[9]) {
+    const double det = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                       h[2] * (h[3] * h[7] - h[4] * h[6]);
+    if (det == 0.0) return 0.0;
+    const double id = 1.0 / det;
+    hi[0] = (h[4] * h[8] - h[5] * h[7]) * id;
+    hi[1] = (h[2] * h[7] - h[1] * h[8]) * id;
+    hi[2] = (h[1] * h[5] - h[2] * h[4]) * id;
+    hi[3] = (h[5] * h[6] - h[3] * h[8]) * id;
+    hi[4] = (h[0] * h[8] - h[2] * h[6]) * id;
+    hi[5] = (h[2] * h[3] - h[0] * h[5]) * id;
+    hi[6] = (h[3] * h[7] - h[4] * h[6]) * id;
+    hi[7] = (h[1] * h[6] - h[0] * h[7]) * id;
+    hi[8] = (h[0] * h[4] - h[1] * h[3]) * id;
+    return det;
+}
+
+// The same half-space set for a general cell: box rows are the lattice vectors a_d, the wave
+// vectors k = 2 pi H^-1 n (k . a_d = 2 pi n_d, so |n_d| <= k_max |a_d| / 2 pi), V = |det H|.
+// For fixed (n1, n2) the k with |k| < k_max form one run of n3 (|k|^2 is convex in n3).
+inline KSet build_kset_box(const double box[9], double kmax, double alpha) {
+    const double two_pi = 6.283185307179586;
+    double hi[9];
+    const double vol = std::fabs(invert3(box, hi));
+    KSet ks;
+    for (int d = 0; d < 3; ++d) {
+        const double len = std::sqrt(box[3 * d] * box[3 * d] + box[3 * d + 1] * box[3 * d + 1] +
+                                     box[3 * d + 2] * box[3 * d + 2]);
+        ks.nmax[d] = (int)std::floor(kmax * len / two_pi);
+    }
+    auto k2_of = [&](int n1, int n2, int n3) {
+        double k2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double kd = two_pi * (hi[3 * d] * n1 + hi[3 * d + 1] * n2 + hi[3 * d + 2] * n3);
+            k2 += kd * kd;
+        }
+        return k2;
+    };
+    const int* nmax = ks.nmax;
+    for (int n1 = 0; n1 <= nmax[0]; ++n1) {
+        for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2) {
+            if (n1 == 0 && n2 < 0) continue;
+            int lo = 1 << 30, hi3 = -(1 << 30);
+            for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3) {
+                if (n1 == 0 && n2 == 0 && n3 <= 0) continue;
+                const double k2 = k2_of(n1, n2, n3);
+                if (k2 > 0 && k2 < kmax * kmax) {
+                    lo = std::min(lo, n3);
+                    hi3 = std::max(hi3, n3);
+                }
+            }
+            if (hi3 < lo) continue;
+            const int nchunk = (hi3 - lo + 1 + 7) / 8;
+            const int c = (int)ks.cols.size();
+            ks.cols.push_back(make_int4(n1, n2, lo, (int)ks.kg.size()));
+            for (int h = 0; h < nchunk; ++h) ks.chunk_col.push_back(c);
+            for (int t = 0; t < 8 * nchunk; ++t) {
+                const int n3 = lo + t;
+                const double k2 = k2_of(n1, n2, n3);
+                const bool ok = n3 <= hi3 && k2 > 0 && k2 < kmax * kmax && !(n1 == 0 && n2 == 0 && n3 <= 0);
+                ks.kg.push_back(ok ? (float)(two_pi / vol * std::exp(-k2 / (4 * alpha * alpha)) / k2) : 0.f);
+            }
+        }
+    }
+    ks.cols.push_back(make_int4(0, 0, 0, (int)ks.kg.size()));
+    return ks;
+}
+
 }  // namespace qnep

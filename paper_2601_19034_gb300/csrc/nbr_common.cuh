@@ -28,10 +28,16 @@ __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos
     float tx = 0.f, ty = 0.f, tz = 0.f;
     if (lane < 27) {
         int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        // the atom's cell: from the position (orthorhombic) or its fractional coordinates
         float p[3] = {pk.x, pk.y, pk.z};
+        if (g.tri) {
+            float sf[3];
+            frac_of(g, pk.x, pk.y, pk.z, sf);
+            for (int q = 0; q < 3; ++q) p[q] = sf[q];
+        }
         int cc[3], tt[3];
         for (int q = 0; q < 3; ++q) {
-            int c = nbr_cell_coord(p[q], g.invL[q], g.nc[q]) + d[q];
+            int c = (g.tri ? nbr_cell_coord(p[q], 1.f, g.nc[q]) : nbr_cell_coord(p[q], g.invL[q], g.nc[q])) + d[q];
             int t = c < 0 ? -1 : (c >= g.nc[q] ? 1 : 0);
             cc[q] = c - t * g.nc[q];
             tt[q] = t;
@@ -40,9 +46,7 @@ __device__ __forceinline__ bool warp_build_lists(const float4* __restrict__ spos
         cstart = cell_start[c];
         ccnt = cell_start[c + 1] - cstart;
         code = (tt[0] + 1) | ((tt[1] + 1) << 2) | ((tt[2] + 1) << 4);
-        tx = tt[0] * g.L[0];
-        ty = tt[1] * g.L[1];
-        tz = tt[2] * g.L[2];
+        shift_vector(g, (float)tt[0], (float)tt[1], (float)tt[2], tx, ty, tz);
     }
     // inclusive prefix counts over the 27 cells (lanes 27..31 add nothing)
     int incl = ccnt;
@@ -155,8 +159,9 @@ __device__ __forceinline__ bool warp_lists_from_skin(const float4* __restrict__ 
             int typ = 0;
             if (t < total) {
                 const unsigned code = (unsigned)ent[u] >> CODE_SHIFT;
-                const float sx = (float)((int)(code & 3u) - 1) * g.L[0], sy = (float)((int)((code >> 2) & 3u) - 1) * g.L[1],
-                            sz = (float)((int)(code >> 4) - 1) * g.L[2];
+                float sx, sy, sz;
+                shift_vector(g, (float)((int)(code & 3u) - 1), (float)((int)((code >> 2) & 3u) - 1),
+                             (float)((int)(code >> 4) - 1), sx, sy, sz);
                 const float vx = (pj[u].x - pk.x) + sx, vy = (pj[u].y - pk.y) + sy, vz = (pj[u].z - pk.z) + sz;
                 const float r2 = vx * vx + vy * vy + vz * vz;
                 inl = r2 < rl2;

@@ -19,11 +19,6 @@ namespace qnep {
 
 namespace {
 
-__device__ __forceinline__ int cell_coord(float x, float invL, int nc) {
-    int c = (int)(x * invL * (float)nc);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
-}
-
 // Wrap positions into the box, assign cells, count atoms per cell, clear the
 // FP64 accumulators and (optionally) the structure-factor array of this call.
 __global__ void k_bin(const float* __restrict__ pos, const int* __restrict__ types, int n, Geom g,
@@ -39,19 +34,12 @@ __global__ void k_bin(const float* __restrict__ pos, const int* __restrict__ typ
     for (int k = i; k < zero_count; k += gridDim.x * blockDim.x) zero_buf[k] = make_double2(0.0, 0.0);
     if (i >= n) return;
     float w[3];
-    for (int d = 0; d < 3; ++d) {
-        float x = pos[3 * i + d];
-        float f = floorf(x * g.invL[d]);
-        float y = fmaf(-f, g.L[d], x);
-        if (y >= g.L[d]) y -= g.L[d];
-        if (y < 0.f) y += g.L[d];
-        if (y >= g.L[d]) y = 0.f;
-        w[d] = y;
-    }
+    int cc[3];
+    const float x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    wrap_and_cell(g, x, w, cc);
     int t = types[i];
     pos4[i] = make_float4(w[0], w[1], w[2], __int_as_float(t));
-    int c = (cell_coord(w[2], g.invL[2], g.nc[2]) * g.nc[1] + cell_coord(w[1], g.invL[1], g.nc[1])) * g.nc[0] +
-            cell_coord(w[0], g.invL[0], g.nc[0]);
+    int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
     cell_of[i] = c;
     atomicAdd(&cell_count[c], 1);
 }
@@ -166,18 +154,11 @@ __global__ void __launch_bounds__(SMALL_BIN_THREADS) k_bin_small(const float* __
     // wrap, cell of each atom, counts
     for (int i = tid; i < n; i += nt) {
         float w[3];
-        for (int d = 0; d < 3; ++d) {
-            float x = pos[3 * i + d];
-            float f = floorf(x * g.invL[d]);
-            float y = fmaf(-f, g.L[d], x);
-            if (y >= g.L[d]) y -= g.L[d];
-            if (y < 0.f) y += g.L[d];
-            if (y >= g.L[d]) y = 0.f;
-            w[d] = y;
-        }
+        int cc[3];
+        const float x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        wrap_and_cell(g, x, w, cc);
         pos4[i] = make_float4(w[0], w[1], w[2], __int_as_float(types[i]));
-        const int c = (cell_coord(w[2], g.invL[2], g.nc[2]) * g.nc[1] + cell_coord(w[1], g.invL[1], g.nc[1])) * g.nc[0] +
-                      cell_coord(w[0], g.invL[0], g.nc[0]);
+        const int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
         cell_of[i] = c;
         atomicAdd(&cnt[c], 1);
     }

@@ -72,9 +72,12 @@ inline ParamLayout make_layout(int s) {
 
 // Orthorhombic box and cell grid, passed by value to kernels.
 struct Geom {
-    float L[3];        // edge lengths
+    float L[3];        // edge lengths (orthorhombic; the diagonal of H otherwise)
     float invL[3];
-    int nc[3];         // cells per dimension
+    int tri;           // 1: a general (triclinic) cell, H and Hi below are used
+    float H[9];        // lattice vectors as rows a, b, c (row-major): r = s H for fractional s
+    float Hi[9];       // H^-1 (row-major): s = r Hi
+    int nc[3];         // cells per dimension (along the fractional axes)
     int ncells;
     float rc_list;     // list cutoff (max of radial descriptor and real-space cutoffs)
     float rc_radial;
@@ -136,6 +139,9 @@ struct EwaldTab {
     int yoff, zoff;       // offsets of the Y and Z tables in an atom's row
     float L[3];
     float invl_hi[3], invl_lo[3];   // 1/L as a float pair (phase reduction)
+    int tri;              // 1: a general cell: phases of the fractional coordinates s = r H^-1, k = 2 pi H^-1 n
+    float hi_hi[9], hi_lo[9];       // H^-1 (row-major) as float pairs (phase reduction of a general cell)
+    float krec[9];        // 2 pi H^-1 (row-major): k_d = sum_e krec[3 d + e] n_e
     float alpha;
     const int4* col;      // [ncol + 1] (n1, n2, lo, padded offset); last entry: (0, 0, 0, nk)
     const int* chunk_col; // [nchunk] column of each chunk
@@ -177,6 +183,61 @@ struct PppmTab {
 };
 
 __device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }
+
+// Cartesian vector of the image shift t (integers, -1..1 per lattice vector): t_x a + t_y b + t_z c
+// (t_d L_d in an orthorhombic box, the same floating-point result as the general form there)
+__device__ __forceinline__ void shift_vector(const Geom& g, float tx, float ty, float tz, float& sx, float& sy,
+                                             float& sz) {
+    if (g.tri) {
+        sx = fmaf(tz, g.H[6], fmaf(ty, g.H[3], tx * g.H[0]));
+        sy = fmaf(tz, g.H[7], fmaf(ty, g.H[4], tx * g.H[1]));
+        sz = fmaf(tz, g.H[8], fmaf(ty, g.H[5], tx * g.H[2]));
+    } else {
+        sx = tx * g.L[0];
+        sy = ty * g.L[1];
+        sz = tz * g.L[2];
+    }
+}
+
+// Fractional coordinates s = r H^-1 of a Cartesian position (general cells only)
+__device__ __forceinline__ void frac_of(const Geom& g, float x, float y, float z, float s[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s[d] = fmaf(z, g.Hi[6 + d], fmaf(y, g.Hi[3 + d], x * g.Hi[d]));
+}
+
+// Position wrapped into the cell and its cell indices.  Orthorhombic: per axis y = x - floor(x / L) L.
+// General: the integer lattice translation f = floor(r H^-1) is subtracted, r' = r - f H, so a
+// position already inside the cell is kept bit for bit.
+__device__ __forceinline__ void wrap_and_cell(const Geom& g, const float* x, float w[3], int c[3]) {
+    if (!g.tri) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float f = floorf(x[d] * g.invL[d]);
+            float y = fmaf(-f, g.L[d], x[d]);
+            if (y >= g.L[d]) y -= g.L[d];
+            if (y < 0.f) y += g.L[d];
+            if (y >= g.L[d]) y = 0.f;
+            w[d] = y;
+            int cc = (int)(y * g.invL[d] * (float)g.nc[d]);
+            c[d] = cc < 0 ? 0 : (cc >= g.nc[d] ? g.nc[d] - 1 : cc);
+        }
+        return;
+    }
+    float s[3];
+    frac_of(g, x[0], x[1], x[2], s);
+    float f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f[d] = floorf(s[d]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        w[d] = x[d] - fmaf(f[2], g.H[6 + d], fmaf(f[1], g.H[3 + d], f[0] * g.H[d]));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float sd = s[d] - f[d];
+        int cc = (int)(sd * (float)g.nc[d]);
+        c[d] = cc < 0 ? 0 : (cc >= g.nc[d] ? g.nc[d] - 1 : cc);
+    }
+}
 __device__ __forceinline__ void entry_shift(int e, float& tx, float& ty, float& tz) {
     const unsigned code = (unsigned)e >> CODE_SHIFT;
     tx = (float)((int)(code & 3u) - 1);

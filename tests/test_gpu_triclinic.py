@@ -1,0 +1,132 @@
+"""GPU force call in general (triclinic) cells, Ewald electrostatics (Sec. II.B with k = 2 pi H^-1 n).
+
+* A sheared 3 x 3 x 3 BaTiO3 cell (every off-diagonal element non-zero) against the FP64 oracle,
+  which handles general cells (tests/test_oracle_triclinic.py pins it): energy, forces, charges,
+  virial, Born effective charges and polarization at the FP32-path tolerances, modes 1 and 2,
+  both kernel families, and the per-atom virial.
+* The same crystal described by a unimodularly transformed cell (rows a1, a2 + a1, a3 + a2)
+  against the orthorhombic call of the 5 x 5 x 5 cell: the same outputs to FP32 rounding.
+* Boxes the library does not take are refused: PPPM in a general cell, a left-handed cell, a
+  cell narrower than the cutoff.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import forcecall, virial  # noqa: E402
+from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = dict(e=1e-6, f=1e-4, q=2e-6, w=1e-5, z=1e-4, p=1e-5)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19034_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def _sheared_batio3(n=3, seed=61):
+    """n^3 perovskite cells mapped into a sheared lattice, N(0, 0.05 A) displacements."""
+    rng = np.random.default_rng(seed)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0.5], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    cells = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    frac = ((cells[:, None, :] + basis[None]) / n).reshape(-1, 3)
+    a = 4.0 * n
+    box = np.array([[a, 0.0, 0.0], [0.9, a, 0.0], [-0.7, 1.1, a]]) + np.array([[0, 0.4, -0.3], [0, 0, 0.5],
+                                                                               [0, 0, 0]])
+    pos = frac @ box + rng.normal(0.0, 0.05, size=frac.shape)
+    types = np.tile(np.array([0, 1, 2, 2, 2], np.int32), n ** 3)
+    return wl.System(pos.astype(np.float32), types, box, ("Ba", "Ti", "O"))
+
+
+def _compute(dev, sysm, hp, params, elec, path="auto", atom_virial=False):
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
+    model = QNEP(hp, params, elec)
+    model.set_path(path)
+    out = model.compute(torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev), sysm.box,
+                        atom_virial=atom_virial)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items() if isinstance(v, torch.Tensor)}
+    res["sc"] = parse_scalars(out["scalars"])
+    model.close()
+    return res
+
+
+@pytest.mark.parametrize("mode,path", [(1, "warp"), (2, "warp"), (1, "thread")])
+def test_sheared_cell_against_oracle(dev, mode, path):
+    sysm = _sheared_batio3()
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(62))[0]
+    elec = wl.Elec(mode=mode, kind="ewald", q_total=0.2)
+    g = _compute(dev, sysm, hp, params, elec, path)
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    n = sysm.n_atoms
+    de = abs(g["sc"]["energy"] - ref["energy"]) / n
+    df = np.abs(g["forces"] - ref["forces"]).max()
+    print(f"\nsheared {n} atoms mode {mode} {path}: |dE|/N {de:.3g}, max|dF| {df:.3g}")
+    assert de <= TOL["e"], de
+    assert df <= TOL["f"], df
+    assert np.abs(g["charges"] - ref["charges"]).max() <= TOL["q"]
+    assert np.abs(g["sc"]["virial"] - ref["virial"]).max() / n <= TOL["w"]
+    assert np.abs(g["bec"] - ref["bec"]).max() <= TOL["z"]
+    assert np.abs(g["sc"]["polarization"] - ref["polarization"]).max() / n <= TOL["p"]
+
+
+def test_sheared_cell_per_atom_virial(dev):
+    sysm = _sheared_batio3(seed=63)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(64))[0]
+    elec = wl.Elec(mode=1, kind="ewald")
+    g = _compute(dev, sysm, hp, params, elec, atom_virial=True)
+    ref, _ = virial.per_atom_virial(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    assert np.abs(g["atom_virial"] - ref).max() <= 1e-4
+
+
+def test_unimodular_change_of_cell_on_the_gpu(dev):
+    sysm = wl.batio3_supercell(5, seed=65)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(66))[0]
+    for mode in (1, 2):
+        elec = wl.Elec(mode=mode, kind="ewald")
+        a = _compute(dev, sysm, hp, params, elec)
+        sheared = sysm.box.copy()
+        sheared[1] = sysm.box[1] + sysm.box[0]
+        sheared[2] = sysm.box[2] + sysm.box[1]
+        b = _compute(dev, wl.System(sysm.positions, sysm.types, sheared, sysm.species), hp, params, elec)
+        n = sysm.n_atoms
+        assert abs(a["sc"]["energy"] - b["sc"]["energy"]) / n <= 1e-6
+        assert np.abs(a["forces"] - b["forces"]).max() <= 1e-4
+        assert np.abs(a["charges"] - b["charges"]).max() <= 2e-6
+        assert np.abs(a["sc"]["virial"] - b["sc"]["virial"]).max() / n <= 1e-5
+        assert np.abs(a["bec"] - b["bec"]).max() <= 1e-4
+
+
+def test_boxes_that_are_refused(dev):
+    from paper_2601_19034_gb300 import _lib
+    from paper_2601_19034_gb300.qnep import QNEP
+    sysm = _sheared_batio3()
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(67))[0]
+    pos, typ = torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev)
+    m = QNEP(hp, params, wl.Elec(mode=1, kind="pppm", mesh=(16, 16, 16), order=5))
+    with pytest.raises(_lib.QnepError) as e:
+        m.compute(pos, typ, sysm.box)
+    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    m.close()
+    m = QNEP(hp, params, wl.Elec(mode=1, kind="ewald"))
+    left = sysm.box[[1, 0, 2]]                     # rows swapped: left-handed
+    with pytest.raises(_lib.QnepError) as e:
+        m.compute(pos, typ, left)
+    assert e.value.status == _lib.QNEP_ERR_ARG
+    thin = sysm.box.copy()
+    thin[1] = sysm.box[1] + 3.0 * sysm.box[0]      # the same volume, a width below 6 A
+    with pytest.raises(_lib.QnepError) as e:
+        m.compute(pos, typ, thin)
+    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    m.close()
