@@ -437,6 +437,27 @@ __device__ __forceinline__ void stage_params(const float* __restrict__ pg, const
     }
 }
 
+// The backward's copy: c^R[t_i] as above, c^A[t_i] per (neighbour species, candidate) as a row
+// of CA_STRIDE floats (q KA + k, padded) in place of the lane-minor c^A and the scaler, so each
+// angular entry reads its 45 coefficients with 12 float4 loads (stride % 32 == 20: conflict-free).
+constexpr int CA_STRIDE = 52;
+static_assert(CA_STRIDE >= NA * KA && CA_STRIDE % 4 == 0 && (CA_STRIDE % 32) % 4 == 0 &&
+                  MAX_SPECIES * CG * CA_STRIDE <= PARAM_FLOATS - PR_A && (PR_A % 4) == 0,
+              "backward coefficient rows fit the parameter region, 16-byte aligned");
+__device__ __forceinline__ void stage_params_bwd(const float* __restrict__ pg, const ParamLayout& lay, int ti,
+                                                 float* __restrict__ prm) {
+    const int S = lay.n_species;
+    const int nr = S * NR * KR, na = S * NA * KA;
+    for (int idx = threadIdx.x; idx < nr * CG; idx += blockDim.x) {
+        const int p = idx >> 5, c = idx & 31;
+        prm[PR_R + p * CG + c] = __ldg(&pg[(size_t)(lay.c_radial + ti * nr + p) * CG + c]);
+    }
+    for (int idx = threadIdx.x; idx < na * CG; idx += blockDim.x) {
+        const int p = idx >> 5, c = idx & 31, t = p / (NA * KA), j = p - t * NA * KA;
+        prm[PR_A + (t * CG + c) * CA_STRIDE + j] = __ldg(&pg[(size_t)(lay.c_angular + ti * na + p) * CG + c]);
+    }
+}
+
 // Cumulative neighbour counts of sorted atom m by species: lanes 0..S-1 load the radial
 // counts and lanes 8..8+S-1 the angular ones (one round trip), scanned by shuffles within
 // each group of 8 lanes; cum[0..S] radial, cum[8..8+S] angular (the warp reads them after).
@@ -593,12 +614,18 @@ __device__ __forceinline__ void descriptor_atom(const BatchArgs& a, const BatchS
 }
 
 // Network of species t_i for two atoms (m1 < 0: one) and the 32 candidates, weights staged
-// in shared memory: net = [W0 (NNEU x NDES) | b0 | w1E | w1q | b1E | b1q | scaler (NDES)][CG].
+// in shared memory: W0 per (neuron, candidate) as a row of NW_STRIDE floats (the N_des inputs,
+// padded: 16-byte rows whose float4 loads are free of bank conflicts, four weights per load),
+// then the other parameters lane-minor [p][CG]: b0 | w1E | w1q | b1E | b1q | scaler (NDES).
 // h = tanh(W0 D - b0), U = w1E.h - b1E, q = w1q.h - b1q (Eq. U_i, Sec. II.B); writes
 // dU/dD and dq/dD (scaled) over D, and (U, q).  Not inlined: its own register allocation keeps
 // the item kernel free of spills.
-constexpr int NET_SCALER = ParamLayout::BLOCK;
-constexpr int NET_FLOATS = (ParamLayout::BLOCK + NDES) * CG;
+constexpr int NW_STRIDE = 36;                              // >= NDES, multiple of 4, stride % 32 == 4
+constexpr int NET_W0 = NNEU * CG * NW_STRIDE;              // floats of the W0 rows
+constexpr int NP_B0 = 0, NP_W1E = NNEU, NP_W1Q = 2 * NNEU, NP_B1E = 3 * NNEU, NP_B1Q = 3 * NNEU + 1,
+              NP_SC = 3 * NNEU + 2;                        // rows of the lane-minor part
+constexpr int NET_FLOATS = NET_W0 + (NP_SC + NDES) * CG;
+static_assert(NW_STRIDE >= NDES && NW_STRIDE % 4 == 0 && NW_STRIDE % 32 == 4, "W0 row layout");
 
 __device__ __noinline__ void network_pair(const float* __restrict__ net, int m0, int m1,
                                              float* __restrict__ duq, float2* __restrict__ uq, double& su,
@@ -607,26 +634,38 @@ __device__ __noinline__ void network_pair(const float* __restrict__ net, int m0,
     const bool two = m1 >= 0;
     float* D0 = duq + (size_t)m0 * 2 * NDES * CG + lane;
     float* D1 = duq + (size_t)(two ? m1 : m0) * 2 * NDES * CG + lane;
-    const float* nl = net + lane;
-    float d0[NDES], d1[NDES];
+    const float* np_ = net + NET_W0 + lane;                // lane-minor parameters
+    float d0[NW_STRIDE], d1[NW_STRIDE];
 #pragma unroll
-    for (int v = 0; v < NDES; ++v) {
-        d0[v] = D0[v * CG];
-        d1[v] = D1[v * CG];
+    for (int v = 0; v < NW_STRIDE; ++v) {
+        d0[v] = v < NDES ? D0[v * CG] : 0.f;
+        d1[v] = v < NDES ? D1[v * CG] : 0.f;
     }
     float ge0[NNEU], gq0[NNEU], ge1[NNEU], gq1[NNEU];
     float ue0 = 0.f, uq0 = 0.f, ue1 = 0.f, uq1 = 0.f;
 #pragma unroll
     for (int mu = 0; mu < NNEU; ++mu) {
-        float p0 = -nl[(ParamLayout::B0 + mu) * CG], p1 = p0;
+        const float4* w4 = reinterpret_cast<const float4*>(net + ((size_t)mu * CG + lane) * NW_STRIDE);
+        // two partial sums per atom (even / odd inputs): four independent chains per warp
+        float p0 = -np_[(NP_B0 + mu) * CG], p1 = p0, p0b = 0.f, p1b = 0.f;
 #pragma unroll
-        for (int v = 0; v < NDES; ++v) {
-            const float w = nl[(ParamLayout::W0 + mu * NDES + v) * CG];
-            p0 = fmaf(w, d0[v], p0);
-            p1 = fmaf(w, d1[v], p1);
+        for (int u = 0; u < (NDES + 3) / 4; ++u) {
+            const float4 w = w4[u];
+            p0 = fmaf(w.x, d0[4 * u], p0);
+            p1 = fmaf(w.x, d1[4 * u], p1);
+            p0b = fmaf(w.y, d0[4 * u + 1], p0b);
+            p1b = fmaf(w.y, d1[4 * u + 1], p1b);
+            if (4 * u + 2 < NDES) {
+                p0 = fmaf(w.z, d0[4 * u + 2], p0);
+                p1 = fmaf(w.z, d1[4 * u + 2], p1);
+                p0b = fmaf(w.w, d0[4 * u + 3], p0b);
+                p1b = fmaf(w.w, d1[4 * u + 3], p1b);
+            }
         }
+        p0 += p0b;
+        p1 += p1b;
         const float h0 = tanhf(p0), h1 = tanhf(p1);
-        const float we = nl[(ParamLayout::W1E + mu) * CG], wq = nl[(ParamLayout::W1Q + mu) * CG];
+        const float we = np_[(NP_W1E + mu) * CG], wq = np_[(NP_W1Q + mu) * CG];
         ue0 = fmaf(we, h0, ue0);
         uq0 = fmaf(wq, h0, uq0);
         ue1 = fmaf(we, h1, ue1);
@@ -637,24 +676,35 @@ __device__ __noinline__ void network_pair(const float* __restrict__ net, int m0,
         ge1[mu] = we * dh1;
         gq1[mu] = wq * dh1;
     }
-    const float b1e = nl[ParamLayout::B1E * CG], b1q = nl[ParamLayout::B1Q * CG];
-#pragma unroll 2
-    for (int v = 0; v < NDES; ++v) {
-        float du0 = 0.f, dq0 = 0.f, du1 = 0.f, dq1 = 0.f;
+    const float b1e = np_[NP_B1E * CG], b1q = np_[NP_B1Q * CG];
+    // dU/dD and dq/dD four inputs at a time: one float4 of W0 per neuron serves 16 products
+#pragma unroll 1
+    for (int u = 0; u < (NDES + 3) / 4; ++u) {
+        float du0[4] = {0.f, 0.f, 0.f, 0.f}, dq0[4] = {0.f, 0.f, 0.f, 0.f};
+        float du1[4] = {0.f, 0.f, 0.f, 0.f}, dq1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int mu = 0; mu < NNEU; ++mu) {
-            const float w = nl[(ParamLayout::W0 + mu * NDES + v) * CG];
-            du0 = fmaf(ge0[mu], w, du0);
-            dq0 = fmaf(gq0[mu], w, dq0);
-            du1 = fmaf(ge1[mu], w, du1);
-            dq1 = fmaf(gq1[mu], w, dq1);
+            const float4 w = reinterpret_cast<const float4*>(net + ((size_t)mu * CG + lane) * NW_STRIDE)[u];
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                du0[e] = fmaf(ge0[mu], wv[e], du0[e]);
+                dq0[e] = fmaf(gq0[mu], wv[e], dq0[e]);
+                du1[e] = fmaf(ge1[mu], wv[e], du1[e]);
+                dq1[e] = fmaf(gq1[mu], wv[e], dq1[e]);
+            }
         }
-        const float sv = nl[(NET_SCALER + v) * CG];
-        D0[v * CG] = du0 * sv;
-        D0[(NDES + v) * CG] = dq0 * sv;
-        if (two) {
-            D1[v * CG] = du1 * sv;
-            D1[(NDES + v) * CG] = dq1 * sv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int v = 4 * u + e;
+            if (v >= NDES) break;
+            const float sv = np_[(NP_SC + v) * CG];
+            D0[v * CG] = du0[e] * sv;
+            D0[(NDES + v) * CG] = dq0[e] * sv;
+            if (two) {
+                D1[v * CG] = du1[e] * sv;
+                D1[(NDES + v) * CG] = dq1[e] * sv;
+            }
         }
     }
     const float U0 = ue0 - b1e, Q0 = uq0 - b1q;
@@ -887,15 +937,27 @@ __device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayou
     return ok_all;
 }
 
-// Stage the network block of species ti and the scaler (layout of network_pair).
+// Stage the network block of species ti and the scaler (layout of network_pair).  Global
+// reads are coalesced over the candidates; the W0 rows are written transposed (4-way bank
+// conflicts on these stores, once per species block).
 __device__ __forceinline__ void stage_network(const float* __restrict__ pg, const ParamLayout& lay, int ti,
                                               float* __restrict__ net) {
-    const int tot = NET_FLOATS;
     const float* src = pg + (size_t)(lay.mlp + ti * lay.mlp_stride) * CG;
     const float* scl = pg + (size_t)lay.scaler * CG;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-        const int p = idx >> 5;
-        net[idx] = p < ParamLayout::BLOCK ? __ldg(&src[idx]) : __ldg(&scl[idx - ParamLayout::BLOCK * CG]);
+    for (int idx = threadIdx.x; idx < NNEU * NW_STRIDE * CG; idx += blockDim.x) {
+        const int c = idx & 31, r = idx >> 5, mu = r / NW_STRIDE, v = r - mu * NW_STRIDE;
+        net[((size_t)mu * CG + c) * NW_STRIDE + v] =
+            v < NDES ? __ldg(&src[(size_t)(ParamLayout::W0 + mu * NDES + v) * CG + c]) : 0.f;
+    }
+    float* np_ = net + NET_W0;
+    for (int idx = threadIdx.x; idx < (NP_SC + NDES) * CG; idx += blockDim.x) {
+        const int p = idx >> 5, c = idx & 31;
+        float x;
+        if (p < NP_B1E) x = __ldg(&src[(size_t)(ParamLayout::B0 + p) * CG + c]);           // b0 | w1E | w1q
+        else if (p == NP_B1E) x = __ldg(&src[(size_t)ParamLayout::B1E * CG + c]);
+        else if (p == NP_B1Q) x = __ldg(&src[(size_t)ParamLayout::B1Q * CG + c]);
+        else x = __ldg(&scl[(size_t)(p - NP_SC) * CG + c]);
+        np_[idx] = x;
     }
 }
 
@@ -1038,20 +1100,29 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
             const int cntc = min(32, tot_a - base);
             for (int t = 0; t < S; ++t) {
                 const int lo = max(cum[8 + t] - base, 0), hi = min(cum[8 + t + 1] - base, cntc);
-                const float* cA = prm + PR_A + t * NA * KA * CG + lane;
+                const float4* cA4 = reinterpret_cast<const float4*>(prm + PR_A + (t * CG + lane) * CA_STRIDE);
                 for (int r = lo; r < hi; ++r) {
                     // row: f_0..8 | f'_0..8 | u | 1/r | j | pad | Y_lm (GA = 48 floats, 16-byte aligned)
                     const float4* r4 = reinterpret_cast<const float4*>(rows + r * GA);
                     const float4 a0 = r4[0], a1 = r4[1], a2 = r4[2], a3 = r4[3], a4 = r4[4], a5 = r4[5];
                     const float fv[KA] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x};
                     const float dfv[KA] = {a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w, a4.x, a4.y};
+                    float cc[4 * ((NA * KA + 3) / 4)];
+#pragma unroll
+                    for (int u = 0; u < (NA * KA + 3) / 4; ++u) {
+                        const float4 v = cA4[u];
+                        cc[4 * u] = v.x;
+                        cc[4 * u + 1] = v.y;
+                        cc[4 * u + 2] = v.z;
+                        cc[4 * u + 3] = v.w;
+                    }
                     float gn[NA], dgn[NA];
 #pragma unroll
                     for (int q = 0; q < NA; ++q) {
                         float x = 0.f, y = 0.f;
 #pragma unroll
                         for (int k = 0; k < KA; ++k) {
-                            const float c = cA[(q * KA + k) * CG];
+                            const float c = cc[q * KA + k];
                             x = fmaf(c, fv[k], x);
                             y = fmaf(c, dfv[k], y);
                         }
@@ -1588,7 +1659,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             const int p0 = so[ti], p1 = so[ti + 1];
             if (p1 == p0) continue;
             __syncthreads();
-            stage_params(pg, a.lay, ti, un);
+            stage_params_bwd(pg, a.lay, ti, un);
             __syncthreads();
             float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
             const float phibar = cst[CG + lane];
