@@ -402,8 +402,11 @@ qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
  * hi.hi + hi.lo + lo.hi accumulated in FP32, about 2^-16 relative error per term; the energy
  * stays within the FP32 path's 1e-6 eV/atom of the FP64 oracle).  The tensor-core form runs
  * 8-warp blocks (it sets warps = 8; qnep_batch_set_config(4, ...) then makes the next call
- * return QNEP_ERR_UNSUPPORTED).  Everything after the contraction is the same in both. */
-enum { QNEP_BATCH_CONTRACT_FP32 = 0, QNEP_BATCH_CONTRACT_BF16X3 = 1 };
+ * return QNEP_ERR_UNSUPPORTED).  QNEP_BATCH_CONTRACT_BF16 is the reduced-precision (mixed)
+ * form: one BF16 product hi.hi (about 2^-9 relative per term), for uses that accept the mixed
+ * path's accuracy (force RMSE <= 5e-3 eV/A against the FP64 oracle).  Everything after the
+ * contraction is the same in all three. */
+enum { QNEP_BATCH_CONTRACT_FP32 = 0, QNEP_BATCH_CONTRACT_BF16X3 = 1, QNEP_BATCH_CONTRACT_BF16 = 2 };
 qnep_status qnep_batch_set_contraction(qnep_batch* b, int contract);
 qnep_status qnep_batch_get_contraction(const qnep_batch* b, int* contract);
 /* Autotuner: times every launch configuration on this batch (`reps` calls each,

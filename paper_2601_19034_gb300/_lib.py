@@ -21,6 +21,7 @@ QNEP_ERR_TIMEOUT = 5
 QNEP_ERR_OOM = 6
 QNEP_BATCH_CONTRACT_FP32 = 0
 QNEP_BATCH_CONTRACT_BF16X3 = 1
+QNEP_BATCH_CONTRACT_BF16 = 2
 QNEP_EWALD = 0
 QNEP_PPPM = 1
 QNEP_PREC_FP32 = 0

@@ -18,6 +18,7 @@ using namespace qnep;
 static_assert((int)QNEP_BATCH_CONTRACT_FP32 == (int)BATCH_CONTRACT_FP32 &&
                   (int)QNEP_BATCH_CONTRACT_BF16X3 == (int)BATCH_CONTRACT_BF16X3,
               "contraction codes of the C ABI and of the kernels agree");
+static_assert((int)QNEP_BATCH_CONTRACT_BF16 == (int)BATCH_CONTRACT_BF16, "contraction codes agree");
 
 struct qnep_batch {
     qnep_hparams hp{};
@@ -283,7 +284,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(regrow(&b->geo_rad, N * (size_t)cl * BATCH_GR, &b->alloc.geo_rad));
     CKB(regrow(&b->geo_ang, N * (size_t)ca * BATCH_GA, &b->alloc.geo_ang));
     CKB(regrow(&b->bsum, N * (size_t)batch_bstride(b->hp.n_species), &b->alloc.bsum));
-    if (b->contract == QNEP_BATCH_CONTRACT_BF16X3) CKB(regrow(&b->bimg, N * (size_t)BIMG_BYTES, &b->alloc.bimg));
+    if (batch_contract_tc(b->contract)) CKB(regrow(&b->bimg, N * (size_t)BIMG_BYTES, &b->alloc.bimg));
     b->h_off.assign(off, off + n_struct + 1);
     b->h_box.assign(boxes, boxes + 9 * (size_t)n_struct);
     b->have_desc = true;
@@ -442,9 +443,11 @@ qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order) {
 }
 
 qnep_status qnep_batch_set_contraction(qnep_batch* b, int contract) {
-    if (!b || (contract != QNEP_BATCH_CONTRACT_FP32 && contract != QNEP_BATCH_CONTRACT_BF16X3)) return QNEP_ERR_ARG;
+    if (!b || (contract != QNEP_BATCH_CONTRACT_FP32 && contract != QNEP_BATCH_CONTRACT_BF16X3 &&
+               contract != QNEP_BATCH_CONTRACT_BF16))
+        return QNEP_ERR_ARG;
     b->contract = contract;
-    if (contract == QNEP_BATCH_CONTRACT_BF16X3) b->warps = 8;   // the tensor-core form runs 8 warps
+    if (batch_contract_tc(contract)) b->warps = 8;   // the tensor-core form runs 8 warps
     return QNEP_OK;
 }
 
@@ -499,7 +502,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
                   .first;
     const int per_sm = hit->second;
     if (per_sm <= 0) return failb(b, QNEP_ERR_UNSUPPORTED, "item kernel does not fit on an SM");
-    const bool tc = b->contract == QNEP_BATCH_CONTRACT_BF16X3;
+    const bool tc = batch_contract_tc(b->contract);
     if (tc && (!b->bimg || b->alloc.bimg < (size_t)b->n_total * BIMG_BYTES)) {
         CKB(cudaStreamSynchronize(st));
         CKB(regrow(&b->bimg, (size_t)std::max(b->n_total, 1) * BIMG_BYTES, &b->alloc.bimg));
@@ -562,6 +565,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     a.mode = b->es.mode;
     a.alpha = (float)b->es.alpha;
     a.q_total = (float)b->es.q_total;
+    a.contract = b->contract;
     a.energy = energy;
     a.forces = forces;
     a.charges = charges;

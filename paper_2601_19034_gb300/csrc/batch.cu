@@ -757,7 +757,7 @@ __device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayou
                                         const int* __restrict__ order_s, const unsigned char* __restrict__ bimg_s,
                                         const float* __restrict__ bsum_s, int bstride, unsigned char* __restrict__ sm,
                                         uint32_t tmem, TcBars bars, uint32_t& tcpar, float* __restrict__ A,
-                                        float* __restrict__ duq, unsigned int* __restrict__ status) {
+                                        float* __restrict__ duq, unsigned int* __restrict__ status, bool x3) {
     constexpr int NW = 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int S = lay.n_species;
@@ -806,12 +806,12 @@ __device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayou
         const int a0 = p0 + j * TC_TA, cnt = min(TC_TA, p1 - a0);
         unsigned char* dst = sm + TC_OFF_B + (j & 1) * 2 * TC_BPLANE;
         unsigned char* dbr = sm + TC_OFF_BR + (j % 3) * TC_TA * TC_BR * 4;
-        mbar_expect_tx(&bars.b[j & 1], (uint32_t)(cnt * (2 * BIMG_PLANE + TC_BR * 4)));
+        mbar_expect_tx(&bars.b[j & 1], (uint32_t)(cnt * ((x3 ? 2 : 1) * BIMG_PLANE + TC_BR * 4)));
         for (int q = 0; q < cnt; ++q) {
             const int m = order_s[a0 + q];
             const unsigned char* src = bimg_s + (size_t)m * BIMG_BYTES;
             bulk_g2s(dst + q * BIMG_PLANE, src, BIMG_PLANE, &bars.b[j & 1]);
-            bulk_g2s(dst + TC_BPLANE + q * BIMG_PLANE, src + BIMG_PLANE, BIMG_PLANE, &bars.b[j & 1]);
+            if (x3) bulk_g2s(dst + TC_BPLANE + q * BIMG_PLANE, src + BIMG_PLANE, BIMG_PLANE, &bars.b[j & 1]);
             bulk_g2s(dbr + q * TC_BR * 4, bsum_s + (size_t)m * bstride, TC_BR * 4, &bars.b[j & 1]);
         }
     };
@@ -835,8 +835,10 @@ __device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayou
                     const uint64_t dbh = smem_desc(bh + ko, 128, TC_SBO);
                     const uint64_t dbl = smem_desc(bl + ko, 128, TC_SBO);
                     mma_bf16(d, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-                    mma_bf16(d, dah, dbl, idesc, 1u);
-                    mma_bf16(d, dal, dbh, idesc, 1u);
+                    if (x3) {   // BF16x3: the two cross products of the lo parts
+                        mma_bf16(d, dah, dbl, idesc, 1u);
+                        mma_bf16(d, dal, dbh, idesc, 1u);
+                    }
                 }
             }
             mma_commit(&bars.m[b]);
@@ -1276,7 +1278,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             if constexpr (TC) {
                 if (!forward_tc(pg, a.lay, ti, p0, p1, a.order + off, a.bimg + (size_t)off * BIMG_BYTES,
                                 a.bsum + (size_t)off * a.bstride, a.bstride, reinterpret_cast<unsigned char*>(un),
-                                s_tmem, TcBars{&tcbars[0], &tcbars[2]}, tcpar, A, duq, a.status))
+                                s_tmem, TcBars{&tcbars[0], &tcbars[2]}, tcpar, A, duq, a.status,
+                                a.contract != BATCH_CONTRACT_BF16))
                     tc_fail = true;
                 __syncthreads();
                 stage_network(pg, a.lay, ti, un);
@@ -1754,7 +1757,7 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
 }
 
 size_t batch_item_smem(int warps, int nph_max, int contract) {
-    const bool tc = contract == BATCH_CONTRACT_BF16X3;
+    const bool tc = batch_contract_tc(contract);
     return warps == 4 ? item_smem<4>(nph_max, false) : item_smem<8>(nph_max, tc);
 }
 
@@ -1772,11 +1775,11 @@ int blocks_per_sm_of(size_t smem) {
 // The tensor-core form holds 512 tensor-memory columns per block: it runs only where its
 // shared memory keeps it to one block per SM (0 otherwise, like a shape that does not fit).
 int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial) {
-    if (contract == BATCH_CONTRACT_BF16X3 && warps != 8) return 0;
+    if (batch_contract_tc(contract) && warps != 8) return 0;
     const size_t smem = batch_item_smem(warps, nph_max, contract);
     int nb;
     if (warps == 4) nb = virial ? blocks_per_sm_of<4, false, true>(smem) : blocks_per_sm_of<4, false, false>(smem);
-    else if (contract == BATCH_CONTRACT_BF16X3) {
+    else if (batch_contract_tc(contract)) {
         nb = virial ? blocks_per_sm_of<8, true, true>(smem) : blocks_per_sm_of<8, true, false>(smem);
         if (nb > 1) nb = 0;
     } else nb = virial ? blocks_per_sm_of<8, false, true>(smem) : blocks_per_sm_of<8, false, false>(smem);
@@ -1790,7 +1793,7 @@ void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract
     if (warps == 4) {
         if (vir) k_batch_items<4, false, true><<<grid, 128, smem, st_>>>(a);
         else k_batch_items<4, false, false><<<grid, 128, smem, st_>>>(a);
-    } else if (contract == BATCH_CONTRACT_BF16X3) {
+    } else if (batch_contract_tc(contract)) {
         if (vir) k_batch_items<8, true, true><<<grid, 256, smem, st_>>>(a);
         else k_batch_items<8, true, false><<<grid, 256, smem, st_>>>(a);
     } else {

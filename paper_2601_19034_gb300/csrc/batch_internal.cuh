@@ -34,7 +34,8 @@ constexpr int BIMG_K = 48;                       // (species, k) padded to a mul
 constexpr int BIMG_ROWB = BIMG_K * 2;            // bytes per operand row
 constexpr int BIMG_PLANE = NLM * BIMG_ROWB;      // 2304 bytes: one atom's 24 rows
 constexpr int BIMG_BYTES = 2 * BIMG_PLANE;       // hi | lo
-enum { BATCH_CONTRACT_FP32 = 0, BATCH_CONTRACT_BF16X3 = 1 };
+enum { BATCH_CONTRACT_FP32 = 0, BATCH_CONTRACT_BF16X3 = 1, BATCH_CONTRACT_BF16 = 2 };
+inline bool batch_contract_tc(int c) { return c == BATCH_CONTRACT_BF16X3 || c == BATCH_CONTRACT_BF16; }
 
 // One structure of the batch (host-built).
 struct BatchStruct {
@@ -110,6 +111,7 @@ struct BatchArgs {
     int mode;
     float alpha;
     float q_total;
+    int contract;            // BATCH_CONTRACT_*: the tensor-core form's products (3, or 1 for BF16)
     // outputs
     double* energy;          // [n_cand][n_struct]
     float* forces;           // [n_cand][N_total][3] or NULL

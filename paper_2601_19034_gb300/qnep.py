@@ -526,14 +526,17 @@ class QNEPBatch:
         _lib.check(self.lib.qnep_batch_set_config(self.handle, int(warps), code), batch=self.handle)
 
     def set_contraction(self, contract: str = "fp32"):
-        """Descriptor contraction: "fp32" (FP32 FMAs) or "bf16x3" (tensor cores, BF16 hi/lo split)."""
-        code = {"fp32": _lib.QNEP_BATCH_CONTRACT_FP32, "bf16x3": _lib.QNEP_BATCH_CONTRACT_BF16X3}[contract]
+        """Descriptor contraction: "fp32" (FP32 FMAs), "bf16x3" (tensor cores, BF16 hi/lo split, FP32-path
+        accuracy) or "bf16" (tensor cores, one BF16 product: the reduced-precision form)."""
+        code = {"fp32": _lib.QNEP_BATCH_CONTRACT_FP32, "bf16x3": _lib.QNEP_BATCH_CONTRACT_BF16X3,
+                "bf16": _lib.QNEP_BATCH_CONTRACT_BF16}[contract]
         _lib.check(self.lib.qnep_batch_set_contraction(self.handle, code), batch=self.handle)
 
     def contraction(self) -> str:
         c = ctypes.c_int()
         _lib.check(self.lib.qnep_batch_get_contraction(self.handle, ctypes.byref(c)), batch=self.handle)
-        return {_lib.QNEP_BATCH_CONTRACT_FP32: "fp32", _lib.QNEP_BATCH_CONTRACT_BF16X3: "bf16x3"}[c.value]
+        return {_lib.QNEP_BATCH_CONTRACT_FP32: "fp32", _lib.QNEP_BATCH_CONTRACT_BF16X3: "bf16x3",
+                _lib.QNEP_BATCH_CONTRACT_BF16: "bf16"}[c.value]
 
     def config(self) -> tuple:
         w, o = ctypes.c_int(), ctypes.c_int()

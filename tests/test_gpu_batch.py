@@ -341,3 +341,32 @@ def test_host_buffer_call_equals_device_call(dev):
                  "charges": b.compute(torch.tensor(pos2, device=dev), torch.tensor(typ2, device=dev), off2,
                                       boxes2)["charges"].cpu().numpy()}, off2, systems2, 2, 4, hp, params, elec)
     b.close()
+
+
+def test_reduced_precision_contraction_meets_the_mixed_bounds(dev):
+    """The single-product BF16 contraction (the batched call's reduced-precision form) on small LLZO
+    and perovskite batches: every pair against the FP64 oracle at the mixed-path bounds (force RMSE
+    5e-3 eV/A, max 3e-2 eV/A, |dE|/N 2e-3 eV, charges 5e-3 e), and measurably different from the
+    FP32 contraction (the products really are reduced)."""
+    cases = [([_llzo((1, 1, 1), 71), _llzo((2, 1, 1), 72)], wl.HParams(n_species=4), wl.Elec(mode=1, kind="ewald")),
+             ([wl.batio3_supercell(2, seed=73), wl.batio3_supercell(3, seed=74)], wl.HParams(n_species=3),
+              wl.Elec(mode=2, kind="ewald", q_total=0.3))]
+    worst = dict(rmse=0.0, fmax=0.0, de=0.0, dq=0.0)
+    for k, (systems, hp, elec) in enumerate(cases):
+        params = wl.random_params(hp, np.random.default_rng(75 + k), n_candidates=3)
+        res, off = _run_batch(systems, hp, params, elec, dev, contract="bf16")
+        res32, _ = _run_batch(systems, hp, params, elec, dev, contract="fp32")
+        assert np.abs(res["forces"] - res32["forces"]).max() > 0.0
+        for s in range(len(systems)):
+            for c in range(3):
+                sysm = systems[s]
+                ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params[c],
+                                           elec, want_bec=False)
+                sl = slice(off[s], off[s + 1])
+                df = res["forces"][c, sl] - ref["forces"]
+                worst["rmse"] = max(worst["rmse"], float(np.sqrt((df ** 2).mean())))
+                worst["fmax"] = max(worst["fmax"], float(np.abs(df).max()))
+                worst["de"] = max(worst["de"], abs(res["energy"][c, s] - ref["energy"]) / sysm.n_atoms)
+                worst["dq"] = max(worst["dq"], float(np.abs(res["charges"][c, sl] - ref["charges"]).max()))
+    print(f"\nBF16 contraction against the oracle: {worst}")
+    assert worst["rmse"] <= 5e-3 and worst["fmax"] <= 3e-2 and worst["de"] <= 2e-3 and worst["dq"] <= 5e-3, worst
