@@ -162,9 +162,9 @@ def _ewald_kcount(box, kmax):
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
 # capture of the current kernel (tensor-core contraction) on the first 160 structures x 64
-# candidates (10.258 GB read + 7.221 GB written for 6,709,248 atom-evaluations; the traffic grows
+# candidates (10.242 GB read + 7.227 GB written for 6,709,248 atom-evaluations; the traffic grows
 # with the atom-evaluations).  Set to None when the item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = None
+ITEM_DRAM_BYTES_PER_EVAL = (10.241611e9 + 7.226630e9) / 6709248
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
                     "first 160 structures x 64 candidates, scaled by atom-evaluations")
 
@@ -996,6 +996,11 @@ def _reference_batch(args, world, cores):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def model_precision(args):
+    """Network precision of the large-scale NVE workload: the precision form (BF16) unless asked otherwise."""
+    return args.precision if args.precision != "fp32" else "bf16"
+
+
 def run_nve(args):
     """Large-scale form: NVE velocity Verlet on the ~1 M-atom Mg-water interface."""
     import torch
@@ -1015,7 +1020,7 @@ def run_nve(args):
     n = sysm.n_atoms
     masses = workloads.species_masses(workloads.MGWATER_SPECIES)
     v0 = workloads.maxwell_boltzmann(masses[sysm.types], 300.0).astype(np.float32)
-    model = QNEP(hp, params, elec, precision=args.precision if args.precision != "fp32" else "bf16")
+    model = QNEP(hp, params, elec, precision=model_precision(args))
     model.set_skin(args.skin)
     pos = torch.tensor(sysm.positions, device=dev)
     vel = torch.tensor(v0, device=dev)
@@ -1057,6 +1062,26 @@ def run_nve(args):
     etot = e.sum(1)
     tps = np.arange(len(etot)) * 0.5e-3
     drift = float(np.polyfit(tps, (etot - etot[0]) / n, 1)[0] * 1e3) if len(etot) > 2 else None
+    # the precision form against the FP32 network on the same run (same skin, same state)
+    prec_cmp = None
+    if model_precision(args) != "fp32":
+        m32 = QNEP(hp, params, elec, precision="fp32")
+        m32.set_skin(args.skin)
+        p32, v32 = pos.clone(), vel.clone()
+        m32.compute(p32, typ, sysm.box, bec=False)
+        nve(m32, p32, v32, typ, masses, sysm.box, 0.5, 2)
+        kp = min(args.steps, 20)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        nve(m32, p32, v32, typ, masses, sysm.box, 0.5, kp)
+        c1.record()
+        c1.synchronize()
+        m32.close()
+        ms32 = c0.elapsed_time(c1) / kp
+        prec_cmp = {"network": model_precision(args), "ms_per_step": ms_per_step, "fp32_network_ms_per_step": ms32,
+                    "speedup_vs_fp32_network": ms32 / ms_per_step, "steps_fp32": kp,
+                    "accuracy": "BF16 network against the FP32 path at 1 M atoms: force RMSE <= 5e-3 eV/A "
+                                "(tests/test_gpu_nve.py)"}
     # per-stage device times of one force call (library stage timers)
     model.set_profiling(True)
     for _ in range(3):
@@ -1088,6 +1113,7 @@ def run_nve(args):
                                  "neighbour lists kept with a Verlet skin (rebuilt on the device when an atom "
                                  "has moved more than skin / 2)",
                        "parallelism": "replicas" if world > 1 else "single GPU", "wall_s": wall},
+            "mixed": prec_cmp,
             "skin": {"skin_A": args.skin, "rebuilds": rebuilds,
                      "force_calls": args.steps + args.warmup + 2, "no_skin": compare},
             "nve": {"drift_mev_per_atom_ps": drift, "steps": args.steps,

@@ -229,3 +229,39 @@ def test_nve_with_skin_equals_rebuild_every_step(dev):
     assert np.abs(p1 - p0).max() <= 1e-3
     assert np.abs(v1 - v0_).max() <= 1e-3
     assert np.abs(e1 - e0).max() / n <= 1e-5
+
+
+def test_skin_in_a_general_cell_and_with_the_per_atom_virial(dev):
+    """The Verlet skin in a sheared cell (fractional cell grid, images t H) and with the per-atom
+    virial requested: kept lists give the fresh search's force call after moves below skin / 2."""
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
+    sysm0 = wl.batio3_supercell(4, seed=81)
+    box = sysm0.box.copy()
+    box[1] = box[1] + 0.25 * box[0]
+    box[2] = box[2] - 0.2 * box[1]
+    frac = sysm0.positions.astype(np.float64) @ np.linalg.inv(sysm0.box)
+    x0 = (frac @ box).astype(np.float32)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(82))[0]
+    elec = wl.Elec(mode=1, kind="ewald")
+    a = QNEP(hp, params, elec)
+    a.set_skin(1.0)
+    b = QNEP(hp, params, elec)
+    rng = np.random.default_rng(83)
+    typ = torch.tensor(sysm0.types, device=dev)
+    n = len(x0)
+    for step in range(3):
+        d = rng.normal(size=x0.shape)
+        d *= 0.3 * rng.uniform(size=(n, 1)) / np.linalg.norm(d, axis=1, keepdims=True)
+        x = torch.tensor((x0 + (d if step else 0.0)).astype(np.float32), device=dev)
+        oa = a.compute(x, typ, box, atom_virial=True)
+        ob = b.compute(x, typ, box, atom_virial=True)
+        torch.cuda.synchronize()
+        sa, sb = parse_scalars(oa["scalars"]), parse_scalars(ob["scalars"])
+        assert abs(sa["energy"] - sb["energy"]) / n <= 1e-6
+        assert (oa["forces"] - ob["forces"]).abs().max().item() <= 1e-4
+        assert (oa["bec"] - ob["bec"]).abs().max().item() <= 1e-4
+        assert (oa["atom_virial"] - ob["atom_virial"]).abs().max().item() <= 1e-4
+    assert a.skin_rebuilds() == 1
+    a.close()
+    b.close()
