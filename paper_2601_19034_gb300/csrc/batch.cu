@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "batch_internal.cuh"
 #include "desc_math.cuh"
@@ -834,10 +835,10 @@ __device__ __noinline__ bool forward_tc(const float* __restrict__ pg, ParamLayou
                     const uint64_t dal = smem_desc(al + ao + ko, 128, TC_SBO);
                     const uint64_t dbh = smem_desc(bh + ko, 128, TC_SBO);
                     const uint64_t dbl = smem_desc(bl + ko, 128, TC_SBO);
-                    mma_bf16(d, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+                    mma_f16(d, dah, dbh, idesc, kk > 0 ? 1u : 0u);
                     if (x3) {   // BF16x3: the two cross products of the lo parts
-                        mma_bf16(d, dah, dbl, idesc, 1u);
-                        mma_bf16(d, dal, dbh, idesc, 1u);
+                        mma_f16(d, dah, dbl, idesc, 1u);
+                        mma_f16(d, dal, dbh, idesc, 1u);
                     }
                 }
             }
@@ -961,6 +962,204 @@ __device__ __forceinline__ void stage_network(const float* __restrict__ pg, cons
         else x = __ldg(&scl[(size_t)(p - NP_SC) * CG + c]);
         np_[idx] = x;
     }
+}
+
+// ---- tensor-core form of the k-space potential and field (FP16x3) ---------------------------
+// Per tile of FT_M = 128 atoms and chunk of 8 wave vectors (K = 16: the real and imaginary parts
+// of e = exp(i k.r_j) for each):
+//   D[j][(c, o)] = sum_k e_r(k, j) B[2k][(c, o)] + e_i(k, j) B[2k + 1][(c, o)]
+// with, for C = 4 k_e G(k) S(k) of candidate c,
+//   o = 0:     B = (C_r, C_i)            D = sum_k Re(C conj(e))       = phi^k_j
+//   o = 1..3:  B = k_o (C_i, -C_r)       D = sum_k k_o Im(C conj(e))   = E^k_j,o   (Sec. II.C)
+// M = atoms, N = 32 candidates x 4 = 128, one K = 16 product per chunk.  The block's threads
+// form both operands in shared memory (the phase products from the atoms' staged separable
+// factors; C(k) and k from a staged window) in the canonical K-major layout, each value split
+// x = hi + lo in FP16 (11 significant bits each, as TF32, at half the bytes: the operand reads
+// of the tensor cores and the threads' stores share the shared-memory bandwidth, which bounds
+// this pass); the products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32 in tensor
+// memory.  |e| <= 1; the B values stay far inside the FP16 range (|C k| < 6.5e4 for any
+// structure the batched call takes; values below 6e-5 keep an absolute error under 3e-8).
+// Two stages of FT_CPI chunks: stage i + 1 is formed while the products of stage i run (the
+// fixed cost of a stage, its commit, proxy fence and block barrier, is shared by its chunks).  Tensor-memory
+// lane = atom, so the epilogue's stores of (phi, E) per candidate are coalesced over the atoms.
+constexpr int FT_M = 128;                  // atoms per tile
+constexpr int FT_PLANE = FT_M * 16 * 2;    // 4096 B: 128 rows x 16 FP16
+constexpr int FT_BUF = 4 * FT_PLANE;       // A hi | A lo | B hi | B lo
+constexpr int FT_WC = 8;                   // chunks per staged window of C(k), k and the chunk table
+constexpr int FT_WIN_SK = FT_WC * 8 * CG * 8;                  // 16384 B of C(k)
+constexpr int FT_WIN = FT_WIN_SK + FT_WC * 8 * 16 + FT_WC * 16;   // + wave vectors + chunk entries
+constexpr int FT_CPI = 2;                  // chunks per pipeline stage (one commit, one block barrier)
+constexpr int FT_STAGE = FT_CPI * FT_BUF;
+constexpr int FT_OFF_WIN = 2 * FT_STAGE;   // two stages, then two windows
+constexpr int FT_OFF_PH = FT_OFF_WIN + 2 * FT_WIN;   // staged phase factors [nph][FT_PHS] float2
+constexpr int FT_PHS = FT_M + 1;           // odd row stride: the transposing stores spread over banks
+constexpr int FT_SBO = 2 * 128;            // 8-row groups 256 B apart (16 FP16 = 2 core matrices)
+static_assert(FT_WIN % 16 == 0 && FT_OFF_PH % 16 == 0, "bulk-copy alignment");
+static_assert(FT_WC % FT_CPI == 0, "a stage never straddles two windows");
+static_assert(FT_OFF_PH + BATCH_MAX_NPH * FT_PHS * 8 <= 220 * 1024, "field operands, windows and phase factors");
+
+// (x, y) = hi + lo + d with hi, lo FP16 pairs (rounded to nearest, x in the low half) and
+// |d| <= 2^-22 max(|x|, |y|) in the normal range; x - hi is exact in FP32
+__device__ __forceinline__ void f16_split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(x, y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Row r (K = 16 FP16) of an operand plane: byte offset of its core matrix kc (8 values)
+__device__ __forceinline__ int ft_off(int r, int kc) { return ((r >> 3) * 2 + kc) * 128 + (r & 7) * 16; }
+
+// false when a bounded wait gave up (status bit set; results of the block are not valid).
+// chunk, kvec: the structure's chunk table and wave vectors; sk: C(k) [8 nchunk][CG] (real
+// entries only), written by this block; phb: phase rows [n][ps]; fk: output [CG][nmax] (phi^k, E^k).
+// mbar: the two MMA barriers (phase bits 2, 3 of tcpar); wbar: the two window barriers (phase
+// bits 0, 1 of wpar).  C(k), k and the chunk entries of FT_WC chunks arrive by bulk copies, the
+// window after next issued once the block is done with a window, so the operand formation reads
+// shared memory only.
+__device__ __noinline__ bool field_tc(int n, int nmax, const float2* __restrict__ phb, int ps, BatchKTab kt,
+                                      const int4* __restrict__ chunk, const float4* __restrict__ kvec,
+                                      const float2* __restrict__ sk, float4* __restrict__ fk,
+                                      unsigned char* __restrict__ sm, uint32_t tmem, uint64_t* mbar, uint32_t& tcpar,
+                                      uint64_t* wbar, uint32_t& wpar, unsigned int* __restrict__ status) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nch = kt.nchunk, nph = kt.nph;
+    const int ey = kt.yoff + kt.n2max, ez = kt.zoff + kt.n3max;
+    if (nch == 0) {   // no wave vectors: no k-space potential or field
+        for (int i = tid; i < CG * n; i += blockDim.x) fk[(size_t)(i / n) * nmax + i % n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return true;
+    }
+    float2* ph = reinterpret_cast<float2*>(sm + FT_OFF_PH);
+    const uint32_t idesc = instr_desc(TC_FMT_F16, FT_M, 128);
+    // shared-memory addresses stay below 2^18, so the 14-bit start-address field (address / 16) of
+    // the base descriptor takes the operand offsets / 16 by plain addition
+    const uint64_t dbase = smem_desc(smem_u32(sm), 128, FT_SBO);
+    const int r = tid & (FT_M - 1), half = tid >> 7;   // operand row r, wave vectors 4 half .. 4 half + 3
+    const int c = r >> 2, oo = r & 3;                  // B row r: candidate c, output oo
+    const int nwin = (nch + FT_WC - 1) / FT_WC;
+    bool ok_all = true;
+    auto fail = [&]() {
+        ok_all = false;
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+    };
+    auto wait_mma = [&](int b) {
+        const bool ok = mbar_wait_bounded(&mbar[b], (tcpar >> (2 + b)) & 1u);
+        tcpar ^= 1u << (2 + b);
+        if (!ok) fail();
+    };
+    // window w: C(k) of its chunks, their wave vectors and table entries (thread 0)
+    auto issue_win = [&](int w) {
+        const int h0 = w * FT_WC, cc = min(FT_WC, nch - h0);
+        unsigned char* dst = sm + FT_OFF_WIN + (w & 1) * FT_WIN;
+        const uint32_t sb = (uint32_t)(cc * 8 * CG * 8), kb = (uint32_t)(cc * 8 * 16), cb = (uint32_t)(cc * 16);
+        fence_proxy_async_all();   // C(k) was written by this block with ordinary stores
+        mbar_expect_tx(&wbar[w & 1], sb + kb + cb);
+        bulk_g2s(dst, sk + (size_t)h0 * 8 * CG, sb, &wbar[w & 1]);
+        bulk_g2s(dst + FT_WIN_SK, kvec + (size_t)h0 * 8, kb, &wbar[w & 1]);
+        bulk_g2s(dst + FT_WIN_SK + FT_WC * 8 * 16, chunk + h0, cb, &wbar[w & 1]);
+    };
+    for (int j0 = 0; j0 < n; j0 += FT_M) {
+        const int cnt = min(FT_M, n - j0);
+        __syncthreads();   // the previous tile's phase factors, windows and accumulator are no longer read
+        if (tid == 0) {
+            issue_win(0);
+            if (nwin > 1) issue_win(1);
+        }
+        for (int idx = tid; idx < FT_M * nph; idx += blockDim.x) {
+            const int q = idx / nph, e = idx - q * nph;
+            ph[e * FT_PHS + q] = q < cnt ? __ldg(&phb[(size_t)(j0 + q) * ps + e]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int nit = (nch + FT_CPI - 1) / FT_CPI;
+        for (int it = 0; it < nit; ++it) {
+            const int b = it & 1, h0 = it * FT_CPI, w = h0 / FT_WC, hl0 = h0 - w * FT_WC;
+            const int nq = min(FT_CPI, nch - h0);   // chunks of this stage
+            unsigned char* stage = sm + b * FT_STAGE;
+            if (hl0 == 0) {   // the window's copies have landed
+                const bool ok = mbar_wait_bounded(&wbar[w & 1], (wpar >> (w & 1)) & 1u);
+                wpar ^= 1u << (w & 1);
+                if (!ok) fail();
+            }
+            if (it >= 2) wait_mma(b);   // the products of stage it - 2 have read buffer b
+            const unsigned char* win = sm + FT_OFF_WIN + (w & 1) * FT_WIN;
+#pragma unroll
+            for (int q = 0; q < FT_CPI; ++q) {
+                if (q >= nq) break;
+                const int hl = hl0 + q;
+                unsigned char* buf = stage + q * FT_BUF;
+                const int4 ci = reinterpret_cast<const int4*>(win + FT_WIN_SK + FT_WC * 8 * 16)[hl];
+                uint32_t hw[4], lw[4];
+                {   // A row r = atom j0 + r: e = X[n1] Y[n2] Z[n3 + t]
+                    const float2 xy = cmul(ph[ci.x * FT_PHS + r], ph[(ey + ci.y) * FT_PHS + r]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 e = cmul(xy, ph[(ez + ci.z + 4 * half + u) * FT_PHS + r]);
+                        f16_split2(e.x, e.y, hw[u], lw[u]);
+                    }
+                    const int o = ft_off(r, half);
+                    *reinterpret_cast<uint4*>(buf + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(buf + FT_PLANE + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                {   // B row r = (candidate c, output oo); the chunk's padding entries are zero
+                    const float2* sw = reinterpret_cast<const float2*>(win) + hl * 8 * CG;
+                    const float* kw = reinterpret_cast<const float*>(win + FT_WIN_SK) + hl * 8 * 4 + (oo > 0 ? oo - 1 : 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = 4 * half + u;
+                        const bool real = t < ci.w;
+                        const float2 C = sw[t * CG + c];
+                        const float kf = kw[t * 4];
+                        const float v0 = real ? (oo == 0 ? C.x : kf * C.y) : 0.f;
+                        const float v1 = real ? (oo == 0 ? C.y : -kf * C.x) : 0.f;
+                        f16_split2(v0, v1, hw[u], lw[u]);
+                    }
+                    const int o = 2 * FT_PLANE + ft_off(r, half);
+                    *reinterpret_cast<uint4*>(buf + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(buf + FT_PLANE + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+            }
+            fence_proxy_async_smem();   // the operands, written by ordinary stores, are read by the tensor cores
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < FT_CPI; ++q) {
+                    if (q >= nq) break;
+                    // descriptors of the chunk's planes: the base descriptor's start address plus offset / 16
+                    const uint64_t dah = dbase + (uint64_t)((b * FT_STAGE + q * FT_BUF) >> 4);
+                    const uint64_t dal = dah + (uint64_t)(FT_PLANE >> 4);
+                    const uint64_t dbh = dah + (uint64_t)(2 * FT_PLANE >> 4), dbl = dah + (uint64_t)(3 * FT_PLANE >> 4);
+                    mma_f16(tmem, dah, dbh, idesc, (it | q) ? 1u : 0u);
+                    mma_f16(tmem, dah, dbl, idesc, 1u);
+                    mma_f16(tmem, dal, dbh, idesc, 1u);
+                }
+                mma_commit(&mbar[b]);
+                // the block is done with window w after its last chunk: window w + 2 streams into it
+                if (hl0 + nq == FT_WC && w + 2 < nwin) issue_win(w + 2);
+            }
+        }
+        for (int it = max(0, nit - 2); it < nit; ++it) wait_mma(it & 1);   // the tile's last products
+        tc_fence_after();
+        {   // epilogue: lane = atom of the tile, warps 4-7 take candidates 16-31
+            const int row = (warp & 3) * 32 + lane, cb = (warp >> 2) * 16;
+            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cb * 4);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                float v[32];
+                tmem_ld32(ta + (uint32_t)(hh * 32), v);
+                if (row < cnt) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        fk[(size_t)(cb + hh * 8 + q) * nmax + j0 + row] =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+        }
+        tc_fence_before();   // the next tile's first products overwrite the accumulator
+    }
+    fence_proxy_async_smem();   // the next phase refills this shared memory by bulk copies
+    return ok_all;
 }
 
 // Backward of sorted atom m: partial forces of every list entry (Sec. II.C).  The atom's
@@ -1459,8 +1658,12 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
 
         // 4a k-space potential and field: lanes over atoms (32 per warp task), 16 candidates per
         // pass; C(k), the wave vectors and the chunk list come in windows of KW wave vectors,
-        // window W + 1 copied while window W is used
-        {
+        // window W + 1 copied while window W is used (the tensor-core form: field_tc)
+        if constexpr (TC) {
+            if (!field_tc(n, nmax, phb, a.nph_stride, kt, a.chunk + kt.chunk_off, a.kvec + 8 * (size_t)kt.chunk_off, sk,
+                          fk, reinterpret_cast<unsigned char*>(un), s_tmem, &tcbars[2], tcpar, tbars, tpar, a.status))
+                tc_fail = true;
+        } else {
             const int nph = kt.nph;
             float2* ph = reinterpret_cast<float2*>(un) + (size_t)warp * nph * 32;   // [nph][32 atoms]
             float2* win = reinterpret_cast<float2*>(un) + (size_t)NW * nph * 32;    // 2 x window
@@ -1730,7 +1933,8 @@ size_t item_smem(int nph_max, bool tc) {   // the same with and without the viri
                          : sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
     const size_t p1b = sizeof(float) * (size_t)NET_FLOATS;
     const size_t p3 = 2 * (sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max);
-    const size_t p4 = sizeof(float2) * ((size_t)NW * nph_max * 32 + 2 * (size_t)WIN_F2);
+    const size_t p4 = tc ? (size_t)FT_OFF_PH + sizeof(float2) * (size_t)FT_PHS * nph_max
+                         : sizeof(float2) * ((size_t)NW * nph_max * 32 + 2 * (size_t)WIN_F2);
     return head + std::max(std::max(p1, p1b), std::max(p3, p4));
 }
 

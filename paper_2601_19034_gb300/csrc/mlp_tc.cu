@@ -43,7 +43,7 @@ template <> struct Op<PREC_TF32> { static constexpr int ES = 4, KSTEP = 8, FMT =
 
 template <int PREC>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-    if (PREC == PREC_BF16) mma_bf16(tmem_d, a, b, idesc, accumulate);
+    if (PREC == PREC_BF16) mma_f16(tmem_d, a, b, idesc, accumulate);
     else mma_tf32(tmem_d, a, b, idesc, accumulate);
 }
 

@@ -1,6 +1,6 @@
 // 5th-generation tensor-core building blocks (tcgen05 in inline PTX): shared-memory matrix
 // descriptors of the canonical K-major layout without swizzle, the instruction descriptor of
-// kind::f16 / kind::tf32 with FP32 accumulation, the MMA itself, its commit to an mbarrier,
+// kind::f16 (FP16 or BF16 operands) / kind::tf32 with FP32 accumulation, the MMA itself, its commit to an mbarrier,
 // the thread-sync fences and the tensor-memory loads.
 //
 // Canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes; K-adjacent
@@ -30,10 +30,12 @@ __host__ __device__ constexpr uint32_t instr_desc(int fmt, int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+constexpr int TC_FMT_F16 = 0;    // kind::f16 operand format of FP16
 constexpr int TC_FMT_BF16 = 1;   // kind::f16 operand format of BF16
 constexpr int TC_FMT_TF32 = 2;   // kind::tf32
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+// kind::f16: FP16 or BF16 operands (the format is in the instruction descriptor)
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
