@@ -280,7 +280,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(regrow(&b->nbr_ang, N * (size_t)ca, &b->alloc.ang));
     CKB(regrow(&b->cnt_list, N * S, &b->alloc.cnt_list));
     CKB(regrow(&b->cnt_ang, N * S, &b->alloc.cnt_ang));
-    CKB(regrow(&b->phase, N * (size_t)nph_max, &b->alloc.phase));
+    CKB(regrow(&b->phase, N * (size_t)batch_phase_stride(nph_max), &b->alloc.phase));
     CKB(regrow(&b->geo_rad, N * (size_t)cl * BATCH_GR, &b->alloc.geo_rad));
     CKB(regrow(&b->geo_ang, N * (size_t)ca * BATCH_GA, &b->alloc.geo_ang));
     CKB(regrow(&b->bsum, N * (size_t)batch_bstride(b->hp.n_species), &b->alloc.bsum));
@@ -530,7 +530,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     }
     launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
                       b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
-                      b->nbr_ang, b->cnt_ang, b->phase, b->nph_max, b->geo_rad, b->geo_ang, b->bsum,
+                      b->nbr_ang, b->cnt_ang, b->phase, batch_phase_stride(b->nph_max), b->geo_rad, b->geo_ang, b->bsum,
                       batch_bstride(b->hp.n_species), tc ? b->bimg : nullptr, (float)b->es.alpha, b->d_status, st);
     BatchArgs a{};
     a.spos4 = b->spos4;
@@ -544,7 +544,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     a.cap_l = b->cap_l;
     a.cap_a = b->cap_a;
     a.phase = b->phase;
-    a.nph_stride = b->nph_max;
+    a.nph_stride = batch_phase_stride(b->nph_max);
     a.geo_rad = b->geo_rad;
     a.geo_ang = b->geo_ang;
     a.bsum = b->bsum;

@@ -14,7 +14,7 @@
 //                network U_i, q_i and dU/dD, dq/dD (Eq. U_i, Sec. II.B), weights staged
 //   2 charges    total-charge correction (block sum, FP64)
 //   3 S(k)       lanes over 32 wave vectors, FP32 terms over 512-atom blocks summed in
-//                FP64; U^k per candidate (FP64)
+//                FP64 (tensor-core form: sk_tc); U^k per candidate (FP64)
 //   4 fields     lanes over atoms: phi^k_i and the k-space field (Sec. II.C);
 //                lanes over candidates: real-space phi^r_i and F^r_i
 //   5 backward   per species block: lambda = dU/dD + (phi_i - mean phi) dq/dD; radial
@@ -976,13 +976,16 @@ __device__ __forceinline__ void stage_network(const float* __restrict__ pg, cons
 // factors; C(k) and k from a staged window) in the canonical K-major layout, each value split
 // x = hi + lo in FP16 (11 significant bits each, as TF32, at half the bytes: the operand reads
 // of the tensor cores and the threads' stores share the shared-memory bandwidth, which bounds
-// this pass); the products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32 in tensor
-// memory.  |e| <= 1; the B values stay far inside the FP16 range (|C k| < 6.5e4 for any
+// this pass); A_hi B_hi and A_hi B_lo + A_lo B_hi accumulate in FP32 in two tensor-memory
+// accumulators (so the small products are not added into the large sum, whose FP32
+// accumulation would lose part of each), added in the epilogue.  |e| <= 1; the B values stay far inside the FP16 range (|C k| < 6.5e4 for any
 // structure the batched call takes; values below 6e-5 keep an absolute error under 3e-8).
 // Two stages of FT_CPI chunks: stage i + 1 is formed while the products of stage i run (the
-// fixed cost of a stage, its commit, proxy fence and block barrier, is shared by its chunks).  Tensor-memory
-// lane = atom, so the epilogue's stores of (phi, E) per candidate are coalesced over the atoms.
+// fixed cost of a stage, its commit, proxy fence and block barrier, is shared by its chunks).
+// Tensor-memory lane = atom, so the epilogue's stores of (phi, E) per candidate are coalesced
+// over the atoms.
 constexpr int FT_M = 128;                  // atoms per tile
+constexpr int FT_N = 4 * CG;               // accumulator columns: hi x hi at 0, the cross products at FT_N
 constexpr int FT_PLANE = FT_M * 16 * 2;    // 4096 B: 128 rows x 16 FP16
 constexpr int FT_BUF = 4 * FT_PLANE;       // A hi | A lo | B hi | B lo
 constexpr int FT_WC = 8;                   // chunks per staged window of C(k), k and the chunk table
@@ -1130,9 +1133,10 @@ __device__ __noinline__ bool field_tc(int n, int nmax, const float2* __restrict_
                     const uint64_t dah = dbase + (uint64_t)((b * FT_STAGE + q * FT_BUF) >> 4);
                     const uint64_t dal = dah + (uint64_t)(FT_PLANE >> 4);
                     const uint64_t dbh = dah + (uint64_t)(2 * FT_PLANE >> 4), dbl = dah + (uint64_t)(3 * FT_PLANE >> 4);
-                    mma_f16(tmem, dah, dbh, idesc, (it | q) ? 1u : 0u);
-                    mma_f16(tmem, dah, dbl, idesc, 1u);
-                    mma_f16(tmem, dal, dbh, idesc, 1u);
+                    const uint32_t acc = (it | q) ? 1u : 0u;
+                    mma_f16(tmem, dah, dbh, idesc, acc);                 // hi x hi
+                    mma_f16(tmem + FT_N, dah, dbl, idesc, acc);          // the cross products
+                    mma_f16(tmem + FT_N, dal, dbh, idesc, 1u);
                 }
                 mma_commit(&mbar[b]);
                 // the block is done with window w after its last chunk: window w + 2 streams into it
@@ -1146,8 +1150,11 @@ __device__ __noinline__ bool field_tc(int n, int nmax, const float2* __restrict_
             const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cb * 4);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
-                float v[32];
+                float v[32], v2[32];
                 tmem_ld32(ta + (uint32_t)(hh * 32), v);
+                tmem_ld32(ta + (uint32_t)(FT_N + hh * 32), v2);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] += v2[q];
                 if (row < cnt) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
@@ -1157,6 +1164,219 @@ __device__ __noinline__ bool field_tc(int n, int nmax, const float2* __restrict_
             }
         }
         tc_fence_before();   // the next tile's first products overwrite the accumulator
+    }
+    fence_proxy_async_smem();   // the next phase refills this shared memory by bulk copies
+    return ok_all;
+}
+
+// ---- tensor-core form of the structure factor (FP16x3) ---------------------------------------
+// S_c(k) = sum_j q_jc exp(i k.r_j) (Sec. II.B) for windows of 64 padded wave vectors:
+//   D[2 t + part][c] = sum_j A[2 t + part][j] Q[c][j],  A = (Re, Im) e(k_t, r_j)
+// M = 128, N = 32 candidates, K = atoms in tiles of SK_AT = 32 (two K = 16 products, three for the
+// FP16 hi + lo split of both operands, as in the field pass).  The tensor cores' FP32
+// accumulation loses a little of every small product added to a large sum, and over a long sum
+// these losses share a sign: so the hi x hi products and the two cross products accumulate in
+// separate tensor-memory columns, and the sums restart every SK_FT tiles (512 atoms, the blocks
+// of the FP32 path) with their FP32 partial sums written to skp [block][nkp][CG] as (Re, Im)
+// and added in FP64 afterwards.  Up to SK_WMAX = 8 windows (512 wave vectors, 64 columns each)
+// accumulate at once while the atoms stream through; larger k-sets take further passes.  Each
+// atom tile's charges and phase rows arrive by bulk copy (double-buffered); a pipeline stage
+// forms the phases of SK_WPS windows (and, at a tile's first stage, the charge operand) and ends
+// in one commit; one thread forms the 8 wave vectors of a chunk for one atom (X Y once, then the
+// chunk's Z factors), written along M (the operand is MN-major).  The epilogue stages each
+// window in shared memory so the global stores are coalesced.
+constexpr int SK_AT = 32;                         // atoms per tile (K)
+constexpr int SK_APLANE = 128 * SK_AT * 2;        // 8192 B: 128 rows x 32 FP16
+constexpr int SK_ABUF = 2 * SK_APLANE;            // hi | lo of one window
+constexpr int SK_WPS = 4;                         // windows per pipeline stage
+constexpr int SK_STAGE = SK_WPS * SK_ABUF;
+constexpr int SK_BPLANE = CG * SK_AT * 2;         // 2048 B: 32 candidate rows x 32 FP16
+constexpr int SK_BBUF = 2 * SK_BPLANE;
+constexpr int SK_OFF_B = 2 * SK_STAGE;            // two stages, then two charge operands,
+constexpr int SK_OFF_T = SK_OFF_B + 2 * SK_BBUF;  // then two atom tiles: charges [SK_AT][CG] | phase rows [SK_AT][ps]
+constexpr int SK_WMAX = (int)TC_COLS / (2 * CG);  // windows per pass (hi x hi and cross-product columns)
+constexpr int SK_FT = 16;                         // tiles per block of partial sums (512 atoms)
+constexpr int SK_SBO = 4 * 128;                   // charge operand: 8-row groups 512 B apart (K-major, 32 FP16)
+// Phase operand, MN-major (M = 128 rows kk = 2 t + part contiguous): core matrices of 8 atoms x 8
+// rows (16 B); M-adjacent cores 128 B apart (SBO), 8-atom groups 2048 B apart (LBO).
+constexpr int SK_ALBO = 16 * 128, SK_ASBO = 128;
+// a tile's phase rows keep their global stride ps (= 2 mod 16 float2): the lanes (atoms) of a load
+// spread over the banks
+__host__ __device__ constexpr int sk_tile_bytes(int ps) { return SK_AT * CG * 4 + SK_AT * ps * 8; }
+// the pass's chunk-table entries follow the tiles
+__host__ __device__ constexpr int sk_smem(int ps) { return SK_OFF_T + 2 * sk_tile_bytes(ps) + SK_WMAX * 8 * 16; }
+static_assert(sk_smem(batch_phase_stride(BATCH_MAX_NPH)) <= 220 * 1024 && SK_OFF_T % 16 == 0, "structure-factor buffers");
+static_assert(SK_APLANE == (SK_AT / 8) * SK_ALBO, "phase operand plane: 4 atom groups of 16 cores");
+static_assert(SK_AT == 32, "one atom per lane in the formation");
+static_assert(64 * (CG + 1) * 8 <= 2 * SK_STAGE, "epilogue staging fits the stage buffers");
+static_assert(SK_AT * SK_FT == QT * FLUSH_TILES, "blocks of partial sums as in the FP32 path (buffer size)");
+
+// Row r (K = 32 FP16) of a structure-factor operand plane: byte offset of its core matrix kc
+__device__ __forceinline__ int sk_off(int r, int kc) { return ((r >> 3) * 4 + kc) * 128 + (r & 7) * 16; }
+
+// false when a bounded wait gave up (status bit set; results of the block are not valid).
+// qcs: corrected charges [n][CG] (written by this block); phb: phase rows [n][ps]; chunk: the
+// structure's chunk table; skp: output [ceil(n / 512)][8 nchunk][CG].  mbar: the two MMA barriers (phase bits
+// 2, 3 of tcpar); tbar: the two tile barriers (phase bits 0, 1 of tpar).
+__device__ __noinline__ bool sk_tc(int n, const float2* __restrict__ phb, int ps, BatchKTab kt,
+                                   const int4* __restrict__ chunk, const float* __restrict__ qcs,
+                                   float2* __restrict__ skp, unsigned char* __restrict__ sm, uint32_t tmem,
+                                   uint64_t* mbar, uint32_t& tcpar, uint64_t* tbar, uint32_t& tpar,
+                                   unsigned int* __restrict__ status) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nch = kt.nchunk;
+    if (nch == 0 || n == 0) return true;
+    const int nkp = 8 * nch, nwin = (nkp + 63) / 64, ntile = (n + SK_AT - 1) / SK_AT;
+    const int ey = kt.yoff + kt.n2max, ez = kt.zoff + kt.n3max;
+    const uint32_t idesc = instr_desc(TC_FMT_F16, 128, CG) | (1u << 15);   // A (the phases) MN-major
+    const uint64_t dbase = smem_desc(smem_u32(sm), 128, SK_SBO);          // charge operand (K-major)
+    const uint64_t pbase = smem_desc(smem_u32(sm), SK_ALBO, SK_ASBO);     // phase operand (MN-major)
+    // offsets / 16 add to the start-address field of either
+    const int tb = sk_tile_bytes(ps);
+    const int ja = tid & (SK_AT - 1), cq = tid >> 5;   // phase operand: atom ja of the tile, chunk cq of the window
+    bool ok_all = true;
+    auto fail = [&]() {
+        ok_all = false;
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+    };
+    auto wait_mma = [&](int b) {
+        const bool ok = mbar_wait_bounded(&mbar[b], (tcpar >> (2 + b)) & 1u);
+        tcpar ^= 1u << (2 + b);
+        if (!ok) fail();
+    };
+    auto issue_tile = [&](int i) {   // thread 0: the charges and phase rows of atom tile i
+        const int j0 = i * SK_AT, cnt = min(SK_AT, n - j0);
+        unsigned char* dst = sm + SK_OFF_T + (i & 1) * tb;
+        const uint32_t qb = (uint32_t)(cnt * CG * 4), rb = (uint32_t)(cnt * ps * 8);
+        fence_proxy_async_all();   // the charges were written by this block with ordinary stores
+        mbar_expect_tx(&tbar[i & 1], qb + rb);
+        bulk_g2s(dst, qcs + (size_t)j0 * CG, qb, &tbar[i & 1]);
+        bulk_g2s(dst + SK_AT * CG * 4, phb + (size_t)j0 * ps, rb, &tbar[i & 1]);
+    };
+    for (int w0 = 0; w0 < nwin; w0 += SK_WMAX) {
+        const int nw = min(SK_WMAX, nwin - w0);
+        const int nst = (nw + SK_WPS - 1) / SK_WPS;   // stages per atom tile
+        __syncthreads();   // the previous pass's epilogue is done with shared and tensor memory
+        if (tid == 0) {
+            issue_tile(0);
+            if (ntile > 1) issue_tile(1);
+        }
+        int4* cpass = reinterpret_cast<int4*>(sm + SK_OFF_T + 2 * tb);   // chunk entries of the pass's windows
+        for (int h = tid; h < nw * 8; h += blockDim.x)
+            if (w0 * 8 + h < nch) cpass[h] = __ldg(&chunk[w0 * 8 + h]);
+        __syncthreads();
+        for (int fb = 0; fb * SK_FT < ntile; ++fb) {   // blocks of partial sums
+        const int i0 = fb * SK_FT, i1 = min(ntile, i0 + SK_FT);
+        int s = 0;   // stage counter of the block
+        for (int i = i0; i < i1; ++i) {
+            const int cnt = min(SK_AT, n - i * SK_AT);
+            const unsigned char* tile = sm + SK_OFF_T + (i & 1) * tb;
+            const float* qt = reinterpret_cast<const float*>(tile);
+            const float2* pr = reinterpret_cast<const float2*>(tile + SK_AT * CG * 4);
+            unsigned char* bq = sm + SK_OFF_B + (i & 1) * SK_BBUF;
+            for (int st = 0; st < nst; ++st, ++s) {
+                const int b = s & 1;
+                if (st == 0) {   // tile i has landed
+                    const bool ok = mbar_wait_bounded(&tbar[i & 1], (tpar >> (i & 1)) & 1u);
+                    tpar ^= 1u << (i & 1);
+                    if (!ok) fail();
+                }
+                if (s >= 2) wait_mma(b);   // the products of stage s - 2 (and of tile i - 2) are complete
+                if (st == 0 && tid < 4 * CG) {   // charge operand of tile i: row c, atoms 8 g2 .. 8 g2 + 7
+                    const int c = tid & (CG - 1), g2 = tid >> 5;
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int a0 = 8 * g2 + 2 * u;
+                        const float q0 = a0 < cnt ? qt[a0 * CG + c] : 0.f;
+                        const float q1 = a0 + 1 < cnt ? qt[(a0 + 1) * CG + c] : 0.f;
+                        f16_split2(q0, q1, hw[u], lw[u]);
+                    }
+                    const int o = sk_off(c, g2);
+                    *reinterpret_cast<uint4*>(bq + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(bq + SK_BPLANE + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+#pragma unroll
+                for (int q = 0; q < SK_WPS; ++q) {   // phase operand of window w0 + st SK_WPS + q
+                    const int wl = st * SK_WPS + q;
+                    if (wl >= nw) break;
+                    const int h = (w0 + wl) * 8 + cq;   // the thread's chunk
+                    uint32_t hw[8], lw[8];
+                    if (h < nch && ja < cnt) {
+                        const int4 ci = cpass[h - w0 * 8];
+                        const float2* row = pr + ja * ps;
+                        const float2 xy = cmul(row[ci.x], row[ey + ci.y]);
+                        const float2* zr = row + ez + ci.z;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float2 e = cmul(xy, zr[u]);
+                            f16_split2(e.x, e.y, hw[u], lw[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) hw[u] = lw[u] = 0u;
+                    }
+                    unsigned char* ab = sm + b * SK_STAGE + q * SK_ABUF;
+                    const int o = (ja >> 3) * SK_ALBO + 2 * cq * SK_ASBO + (ja & 7) * 16;   // rows 16 cq .. 16 cq + 15
+                    *reinterpret_cast<uint4*>(ab + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(ab + o + SK_ASBO) = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+                    *reinterpret_cast<uint4*>(ab + SK_APLANE + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    *reinterpret_cast<uint4*>(ab + SK_APLANE + o + SK_ASBO) = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+                }
+                fence_proxy_async_smem();   // the operands, written by ordinary stores, are read by the tensor cores
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint64_t dq = dbase + (uint64_t)((SK_OFF_B + (i & 1) * SK_BBUF) >> 4);
+#pragma unroll
+                    for (int q = 0; q < SK_WPS; ++q) {
+                        const int wl = st * SK_WPS + q;
+                        if (wl >= nw) break;
+                        const uint64_t da = pbase + (uint64_t)((b * SK_STAGE + q * SK_ABUF) >> 4);
+                        const uint32_t d1 = tmem + (uint32_t)(wl * 2 * CG), d2 = d1 + (uint32_t)CG;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {   // K = 16 atoms per product: two 8-atom groups
+                            const uint64_t ah = da + (uint64_t)(ks * 2 * SK_ALBO >> 4), al = ah + (uint64_t)(SK_APLANE >> 4);
+                            const uint64_t bh = dq + (uint64_t)(ks * 16), bl = bh + (uint64_t)(SK_BPLANE >> 4);
+                            const uint32_t acc = (i > i0 || ks) ? 1u : 0u;
+                            mma_f16(d1, ah, bh, idesc, acc);   // hi x hi
+                            mma_f16(d2, ah, bl, idesc, acc);   // the cross products
+                            mma_f16(d2, al, bh, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&mbar[b]);
+                }
+                // the block is done with tile i after its last stage: tile i + 2 streams into it
+                if (tid == 0 && st == nst - 1 && i + 2 < ntile) issue_tile(i + 2);
+            }
+        }
+        for (int s2 = max(0, s - 2); s2 < s; ++s2) wait_mma(s2 & 1);   // the block's last products
+        tc_fence_after();
+        // epilogue per window: warps 0-3 (tensor-memory lanes = rows) stage the block's S as
+        // [64][CG + 1] float2 (Re, Im) in the stage buffers, then the block stores it coalesced
+        float2* stg = reinterpret_cast<float2*>(sm);
+        float2* dst = skp + (size_t)fb * nkp * CG;
+        for (int wl = 0; wl < nw; ++wl) {
+            if (warp < 4) {
+                float v[32], v2[32];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(wl * 2 * CG);
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + (uint32_t)CG, v2);
+                tc_fence_before();   // the next block's first products overwrite these columns
+                const int row = warp * 32 + lane, tt = row >> 1, part = row & 1;
+                float* sf = reinterpret_cast<float*>(stg + tt * (CG + 1));
+#pragma unroll
+                for (int c = 0; c < CG; ++c) sf[2 * c + part] = v[c] + v2[c];
+            }
+            __syncthreads();
+            for (int idx = tid; idx < 64 * CG; idx += blockDim.x) {
+                const int tt = idx >> 5, c = idx & (CG - 1), kl = (w0 + wl) * 64 + tt;
+                if (kl < nkp) dst[(size_t)kl * CG + c] = stg[tt * (CG + 1) + c];
+            }
+            __syncthreads();
+        }
+        }
+        tc_fence_before();   // the next pass's first products overwrite the accumulators
     }
     fence_proxy_async_smem();   // the next phase refills this shared memory by bulk copies
     return ok_all;
@@ -1530,7 +1750,53 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         const float2* phb = a.phase + (size_t)off * a.nph_stride;
         const int nkp = 8 * kt.nchunk;
         double ek = 0.0;
-        {
+        // lane = candidate, for the real wave vectors 32 task .. 32 task + 31 (the warp, after its
+        // partial sums): S in FP64 over the nfl partial sums, U^k += (w/2)|S|^2, the FP32 copy C = w S
+        // (w = 4 k_e G(k)) and the k-space virial
+        auto sk_finalize = [&](int task, int nfl) {
+            for (int kk = 0; kk < 32; ++kk) {
+                const int vk = task * 32 + kk;
+                if (vk >= kt.nkr) break;
+                const int kl = __ldg(&a.kreal[kt.kreal_off + vk]);
+                const float w = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]).w;
+                double Sr = 0.0, Si = 0.0;
+                for (int f = 0; f < nfl; ++f) {
+                    const float2 v = skp[((size_t)f * nkp + kl) * CG + lane];
+                    Sr += (double)v.x;
+                    Si += (double)v.y;
+                }
+                ek += 0.5 * (double)w * (Sr * Sr + Si * Si);
+                sk[(size_t)kl * CG + lane] = make_float2((float)((double)w * Sr), (float)((double)w * Si));
+                if (VIR) {
+                    // W^k += e (I - (2 / (4 alpha^2) + 2 / k^2) k k^T), e = 2 k_e G |S|^2 (Sec. II.C)
+                    const float4 kv = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]);
+                    const double e = 0.5 * (double)w * (Sr * Sr + Si * Si);
+                    const float fac = 2.f / (4.f * a.alpha * a.alpha) + 2.f / (kv.x * kv.x + kv.y * kv.y + kv.z * kv.z);
+                    double* vw = vacc + (size_t)warp * 9 * CG + lane;
+                    const double xx = e * (double)(1.f - fac * kv.x * kv.x), yy = e * (double)(1.f - fac * kv.y * kv.y);
+                    const double zz = e * (double)(1.f - fac * kv.z * kv.z), xy = e * (double)(-fac * kv.x * kv.y);
+                    const double xz = e * (double)(-fac * kv.x * kv.z), yz = e * (double)(-fac * kv.y * kv.z);
+                    vw[0 * CG] += xx;
+                    vw[4 * CG] += yy;
+                    vw[8 * CG] += zz;
+                    vw[1 * CG] += xy;
+                    vw[3 * CG] += xy;
+                    vw[2 * CG] += xz;
+                    vw[6 * CG] += xz;
+                    vw[5 * CG] += yz;
+                    vw[7 * CG] += yz;
+                }
+            }
+        };
+        if constexpr (TC) {   // tensor-core form: S of all wave vectors, then the FP64 finalisation
+            if (!sk_tc(n, phb, a.nph_stride, kt, a.chunk + kt.chunk_off, qcs, skp, reinterpret_cast<unsigned char*>(un),
+                       s_tmem, &tcbars[2], tcpar, tbars, tpar, a.status))
+                tc_fail = true;
+            __syncthreads();
+            const int ntask = (kt.nkr + 31) >> 5;
+            const int nfl = (n + SK_AT * SK_FT - 1) / (SK_AT * SK_FT);
+            for (int task = warp; task < ntask; task += NW) sk_finalize(task, nfl);
+        } else {
             // tile buffer b: charges [QT][CG] | phase rows [QT][nph_stride]; tile T of the
             // (task round, atom tile) sequence is copied while tile T - 1 is summed
             const int ps = a.nph_stride;
@@ -1616,41 +1882,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 }
                 if (act) {
                     __syncwarp();
-                    // lane = candidate: S in FP64 over the partial sums, U^k += (w/2)|S|^2 and the
-                    // FP32 copy C = w S, w = 4 k_e G(k)
-                    for (int kk = 0; kk < 32; ++kk) {
-                        const int vk = task * 32 + kk;
-                        if (vk >= kt.nkr) break;
-                        const int kl = __ldg(&a.kreal[kt.kreal_off + vk]);
-                        const float w = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]).w;
-                        double Sr = 0.0, Si = 0.0;
-                        for (int f = 0; f < nfl; ++f) {
-                            const float2 v = skp[((size_t)f * nkp + kl) * CG + lane];
-                            Sr += (double)v.x;
-                            Si += (double)v.y;
-                        }
-                        ek += 0.5 * (double)w * (Sr * Sr + Si * Si);
-                        sk[(size_t)kl * CG + lane] = make_float2((float)((double)w * Sr), (float)((double)w * Si));
-                        if (VIR) {
-                            // W^k += e (I - (2 / (4 alpha^2) + 2 / k^2) k k^T), e = 2 k_e G |S|^2 (Sec. II.C)
-                            const float4 kv = __ldg(&a.kvec[8 * (size_t)kt.chunk_off + kl]);
-                            const double e = 0.5 * (double)w * (Sr * Sr + Si * Si);
-                            const float fac = 2.f / (4.f * a.alpha * a.alpha) + 2.f / (kv.x * kv.x + kv.y * kv.y + kv.z * kv.z);
-                            double* vw = vacc + (size_t)warp * 9 * CG + lane;
-                            const double xx = e * (double)(1.f - fac * kv.x * kv.x), yy = e * (double)(1.f - fac * kv.y * kv.y);
-                            const double zz = e * (double)(1.f - fac * kv.z * kv.z), xy = e * (double)(-fac * kv.x * kv.y);
-                            const double xz = e * (double)(-fac * kv.x * kv.z), yz = e * (double)(-fac * kv.y * kv.z);
-                            vw[0 * CG] += xx;
-                            vw[4 * CG] += yy;
-                            vw[8 * CG] += zz;
-                            vw[1 * CG] += xy;
-                            vw[3 * CG] += xy;
-                            vw[2 * CG] += xz;
-                            vw[6 * CG] += xz;
-                            vw[5 * CG] += yz;
-                            vw[7 * CG] += yz;
-                        }
-                    }
+                    sk_finalize(task, nfl);
                 }
             }
         }
@@ -1932,7 +2164,8 @@ size_t item_smem(int nph_max, bool tc) {   // the same with and without the viri
     const size_t p1 = tc ? std::max((size_t)TC_BYTES, sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS))
                          : sizeof(float) * ((size_t)PARAM_FLOATS + (size_t)NW * WARP_FLOATS);
     const size_t p1b = sizeof(float) * (size_t)NET_FLOATS;
-    const size_t p3 = 2 * (sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * nph_max);
+    const size_t p3 = tc ? (size_t)sk_smem(batch_phase_stride(nph_max))
+                         : 2 * (sizeof(float) * (size_t)QT * CG + sizeof(float2) * (size_t)QT * batch_phase_stride(nph_max));
     const size_t p4 = tc ? (size_t)FT_OFF_PH + sizeof(float2) * (size_t)FT_PHS * nph_max
                          : sizeof(float2) * ((size_t)NW * nph_max * 32 + 2 * (size_t)WIN_F2);
     return head + std::max(std::max(p1, p1b), std::max(p3, p4));

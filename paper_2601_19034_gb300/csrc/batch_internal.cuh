@@ -24,6 +24,10 @@ constexpr int BATCH_MAX_NPH = 94;    // phase factors per atom (n_max <= 16 per 
                                      // ~45 A at k_max = 2.23 1/A; bounds the field pass's shared memory)
 constexpr int BATCH_MAX_CELLS = 512; // cell grid per structure (8 per axis at most)
 constexpr int BATCH_GR = 20, BATCH_GA = 48;   // floats per radial / angular pair row
+// Row stride (float2) of the atoms' phase factors for phase rows of up to nph_max entries: even,
+// so every row starts on a 16-byte boundary (bulk copies), and = 2 mod 16, so the rows of
+// consecutive atoms start in different shared-memory banks once a tile of them is copied.
+constexpr int batch_phase_stride(int nph_max) { return nph_max + (18 - nph_max % 16) % 16; }
 
 // Tensor-core form of the angular contraction A_{n,lm} = sum_{s,k} c^A[t_i][s][n][k] B^A[s][k][lm]
 // (BF16x3: operands split into BF16 hi + lo, three products, FP32 accumulation).  The pre-pass
