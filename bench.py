@@ -161,10 +161,10 @@ def _ewald_kcount(box, kmax):
 
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
-# capture of the current kernel (tensor-core contraction) on the first 160 structures x 64
-# candidates (10.242 GB read + 7.227 GB written for 6,709,248 atom-evaluations; the traffic grows
+# capture of the current kernel (tensor-core form) on the first 160 structures x 64
+# candidates (10.363 GB read + 7.387 GB written for 6,709,248 atom-evaluations; the traffic grows
 # with the atom-evaluations).  Set to None when the item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = None
+ITEM_DRAM_BYTES_PER_EVAL = (10.362708e9 + 7.387106e9) / 6709248
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
                     "first 160 structures x 64 candidates, scaled by atom-evaluations")
 
@@ -738,28 +738,65 @@ def _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, 
             "what": "same batch, warps 8, largest first, CUDA graph replay, L2 flushed, median"}
 
 
-def _tensor_roofline(systems, hp, n_cand, item_ms, peaks, contract="bf16x3"):
-    """Tensor-pipe share of the batched item kernel: the BF16x3 angular descriptor contraction.
+_CHUNKS = {}
 
-    Useful work per (atom, candidate): A_{n,lm} = sum over 9 S (s, k) terms for 5 n x 24 lm,
-    2 flop each, three BF16 products (hi.hi, hi.lo, lo.hi); issued work adds the padding of the
-    MMA shapes (M 256 rows for 160 (n, candidate) rows per 32 candidates, K 48 for 9 S, N 128 for
-    120 (atom, lm) columns per 5-atom tile).
+
+def _ewald_chunks(box, kmax):
+    """Chunks of 8 wave vectors of the half-space k-set (orthorhombic box): per (n1, n2) column
+    the contiguous n3 range with 0 < |k| < kmax, split into chunks of 8 (cached per box shape)."""
+    key = (tuple(np.round(np.diag(box), 9)), kmax)
+    if key not in _CHUNKS:
+        _CHUNKS[key] = _ewald_chunks_of(np.diag(box), kmax)
+    return _CHUNKS[key]
+
+
+def _ewald_chunks_of(lengths, kmax):
+    nmax = [int(math.floor(kmax * ln / (2 * math.pi))) for ln in lengths]
+    chunks = 0
+    for n1 in range(0, nmax[0] + 1):
+        for n2 in range(-nmax[1], nmax[1] + 1):
+            n3s = [n3 for n3 in range(-nmax[2], nmax[2] + 1)
+                   if (n1 > 0 or (n1 == 0 and (n2 > 0 or (n2 == 0 and n3 > 0))))
+                   and 0 < sum((2 * math.pi * m / ln) ** 2 for m, ln in zip((n1, n2, n3), lengths)) < kmax * kmax]
+            if n3s:
+                chunks += (n3s[-1] - n3s[0] + 8) // 8
+    return chunks
+
+
+def _tensor_roofline(systems, hp, elec, n_cand, item_ms, peaks, contract="bf16x3"):
+    """Tensor-pipe share of the batched item kernel: its three tcgen05.mma kind::f16 contractions.
+
+    Useful work (real data only, the products of the hi / lo splits counted), per (atom, candidate):
+    the angular descriptor contraction 2 x 5 n x 24 lm x 9 S per product (three BF16 products, one
+    for the BF16 form); the k-space potential and field 4 outputs x 2 x 2 per real half-space k and
+    the structure factor 2 x 2 per real k, three FP16 products each.  Issued work adds the padding
+    of the MMA shapes: descriptor M 256 / K 48 / N 128 per 5-atom tile; field M 128 atoms x N 128 x
+    K 16 per (128-atom tile, chunk of 8 wave vectors); structure factor M 128 x N 32 x K 32 per
+    (32-atom tile, window of 8 chunks).
     """
     S = hp.n_species
     atoms = sum(sy.n_atoms for sy in systems)
-    prod = 3 if contract == "bf16x3" else 1
-    useful = prod * 2 * 5 * 24 * 9 * S * atoms * n_cand
     groups = (n_cand + 31) // 32
-    issued = prod * 2 * 256 * 48 * (128 / 5.0) * atoms * groups
+    prod = 3 if contract == "bf16x3" else 1
+    useful_d = prod * 2 * 5 * 24 * 9 * S * atoms * n_cand
+    issued_d = prod * 2 * 256 * 48 * (128 / 5.0) * atoms * groups
+    useful_k = issued_k = 0.0
+    for sy in systems:
+        nk = _ewald_kcount(sy.box, elec.kmax)
+        nch = _ewald_chunks(sy.box, elec.kmax)
+        useful_k += 3 * (16 + 4) * sy.n_atoms * n_cand * nk
+        issued_k += groups * 3 * (math.ceil(sy.n_atoms / 128) * nch * 2 * 128 * 128 * 16
+                                  + math.ceil(sy.n_atoms / 32) * math.ceil(nch / 8) * 2 * 2 * 128 * 32 * 16)
+    useful, issued = useful_d + useful_k, issued_d + issued_k
     peak = peaks["bf16_tflops"]
     ach = useful / (item_ms * 1e-3) / 1e12
-    return {"kernel": "k_batch_items (tcgen05.mma kind::f16, BF16x3 descriptor contraction)", "bound": "tensor",
-            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-            "work": f"{useful:.4g} useful / {issued:.4g} issued tensor flop per launch ({contract}, {prod} products)",
-            "note": "averaged over the whole item kernel; the contraction is one phase of it (the kernel as a "
+    return {"kernel": "k_batch_items (tcgen05.mma kind::f16: descriptor contraction, k-space field, S(k))",
+            "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "work": f"{useful:.4g} useful / {issued:.4g} issued tensor flop per launch (descriptor {useful_d:.3g}, "
+                    f"k space {useful_k:.3g} useful; {contract} descriptor products, FP16x3 k space)",
+            "note": "averaged over the whole item kernel; the contractions are three phases of it (the kernel as a "
                     "whole is bound by the FP32 pipes, see roofline)",
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16)"}
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16; FP16 has the same kind::f16 rate)"}
 
 
 def run_batch(args):
@@ -924,7 +961,7 @@ def run_batch(args):
                          "peak_source": peak_src,
                          "work": f"{flop:.4g} algorithmic flop per launch (whole batch)",
                          "whole_call_frac": achieved / fp32_peak},
-            "roofline_tensor": _tensor_roofline(systems, hp, n_cand, item_ms, peaks, args.contract)
+            "roofline_tensor": _tensor_roofline(systems, hp, elec, n_cand, item_ms, peaks, args.contract)
             if args.contract != "fp32" else None,
             "contraction_compare": other,
             "mixed": mixed,
