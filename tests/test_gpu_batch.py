@@ -370,3 +370,18 @@ def test_reduced_precision_contraction_meets_the_mixed_bounds(dev):
                 worst["dq"] = max(worst["dq"], float(np.abs(res["charges"][c, sl] - ref["charges"]).max()))
     print(f"\nBF16 contraction against the oracle: {worst}")
     assert worst["rmse"] <= 5e-3 and worst["fmax"] <= 3e-2 and worst["de"] <= 2e-3 and worst["dq"] <= 5e-3, worst
+
+
+@pytest.mark.parametrize("contract", ["fp32", "bf16x3"])
+def test_few_or_no_wave_vectors(dev, contract):
+    """k_max 0.3 1/A: the 12.97 A cells have no wave vector inside the sphere (U^k = 0, no k-space
+    field), the 25.9 A cells a single partly filled chunk; every pair against the oracle, so the
+    tensor-core passes' empty and ragged k-sets meet the FP32-path tolerances."""
+    systems = [_llzo((1, 1, 1), 91), _llzo((2, 2, 1), 92), _llzo((2, 2, 2), 93)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(94), n_candidates=3)
+    elec = wl.Elec(mode=1, kind="ewald", kmax=0.3, q_total=0.2)
+    res, off = _run_batch(systems, hp, params, elec, dev, contract=contract)
+    for s in range(len(systems)):
+        for c in range(3):
+            _check_pair(res, off, systems, s, c, hp, params, elec)
