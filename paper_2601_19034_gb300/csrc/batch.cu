@@ -329,11 +329,14 @@ __device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, con
         __syncwarp();
     }
     if (lane < NLM) {
+        // FP32 B^A for the FP32 contraction; the tensor-core form reads only the operand image
+        if (!bimg) {
 #pragma unroll
-        for (int t = 0; t < MAX_SPECIES; ++t)
-            if (t < S)
+            for (int t = 0; t < MAX_SPECIES; ++t)
+                if (t < S)
 #pragma unroll
-                for (int k = 0; k < KA; ++k) bs_out[MAX_SPECIES * KR + (t * KA + k) * NLM + lane] = ba[t][k];
+                    for (int k = 0; k < KA; ++k) bs_out[MAX_SPECIES * KR + (t * KA + k) * NLM + lane] = ba[t][k];
+        }
         if (bimg) {
             // operand image, row lm = lane: K index 9 t + k, BF16 hi and lo (x - hi) planes
             static_assert(MAX_SPECIES * KA <= BIMG_K, "the (species, k) index fits the padded K");
@@ -2107,8 +2110,9 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         }
         __syncthreads();
 
-        // 6 outputs in input order, candidate-major
-        if (a.forces || a.charges) {
+        // 6 outputs in input order, candidate-major: lanes over consecutive input atoms (through the
+        // inverse of the sort permutation), so each warp writes contiguous rows of the outputs
+        if ((a.forces || a.charges) && n > a.inv_cap) {   // a structure too large for the permutation
             for (int i = threadIdx.x; i < n * CG; i += NW * 32) {
                 const int m = i >> 5, c = grp * CG + (i & 31);
                 if (c >= a.n_cand) continue;
@@ -2121,6 +2125,26 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     fo[2] = F.z;
                 }
                 if (a.charges) a.charges[(size_t)c * a.n_total + gi] = qcs[i];
+            }
+        } else if (a.forces || a.charges) {
+            int* inv = reinterpret_cast<int*>(un);   // [n]: sorted index of input atom g
+            for (int m = threadIdx.x; m < n; m += NW * 32) inv[__ldg(&a.sidx[off + m])] = m;
+            __syncthreads();
+            for (int cl = warp; cl < CG; cl += NW) {
+                const int c = grp * CG + cl;
+                if (c >= a.n_cand) break;
+                float* fo = a.forces ? a.forces + ((size_t)c * a.n_total + off) * 3 : nullptr;
+                float* qo = a.charges ? a.charges + (size_t)c * a.n_total + off : nullptr;
+                for (int g = lane; g < n; g += 32) {
+                    const int i = inv[g] * CG + cl;
+                    if (fo) {
+                        const float4 F = fsum[i];
+                        fo[3 * g] = F.x;
+                        fo[3 * g + 1] = F.y;
+                        fo[3 * g + 2] = F.z;
+                    }
+                    if (qo) qo[g] = qcs[i];
+                }
             }
         }
         if (VIR && warp == 1 && cand < a.n_cand) {
@@ -2223,9 +2247,12 @@ int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial) 
     return nb;
 }
 
-void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract, int grid, cudaStream_t st_) {
-    if (grid <= 0 || a.n_items <= 0) return;
+void launch_batch_items(const BatchArgs& a_in, int warps, int nph_max, int contract, int grid, cudaStream_t st_) {
+    if (grid <= 0 || a_in.n_items <= 0) return;
     const size_t smem = batch_item_smem(warps, nph_max, contract);
+    BatchArgs a = a_in;
+    const size_t head = sizeof(double) * ((warps == 4 ? 4 : 8) + NSUMS) * CG + sizeof(float) * 4 * CG;
+    a.inv_cap = (int)((smem - head) / sizeof(int));
     const bool vir = a.virial != nullptr;
     if (warps == 4) {
         if (vir) k_batch_items<4, false, true><<<grid, 128, smem, st_>>>(a);

@@ -123,6 +123,7 @@ struct BatchArgs {
     double* virial;          // [n_cand][n_struct][9] or NULL (W = -dU/d eps, eV)
     int n_struct;
     int n_total;
+    int inv_cap;             // ints of shared memory for the outputs' inverse permutation (set at launch)
     unsigned int* status;    // bit 0: neighbour overflow
 };
 
