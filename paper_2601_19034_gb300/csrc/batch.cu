@@ -55,6 +55,9 @@ constexpr int TAB_P = KA + NLM;                // pre-pass staging row: f_k, Y_l
 constexpr int WBUF = 32 * GA;                  // floats per buffer
 constexpr int WCUM = 2 * WBUF;                 // ints
 constexpr int WARP_FLOATS = WCUM + 16;
+// the real-space phase's per-warp buffer: 32 radial pair rows, then the species counts
+constexpr int RS_CUM = 32 * GR;
+constexpr int RS_WARP = RS_CUM + 16;
 constexpr int BS_MAX = MAX_SPECIES * KR + MAX_SPECIES * KA * NLM;   // basis-sum floats per atom
 static_assert(BS_MAX <= WBUF, "basis sums fit a row buffer");
 constexpr int PR_R = 0;                                  // c^R[t_i] staged [S][NR][KR][CG]
@@ -2013,10 +2016,20 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         // 4b real space (lanes over candidates, pair rows from the pre-pass) and the potential sums
         double er = 0.0, sphi = 0.0, sq2 = 0.0;
         {
-            float* tab = un + PARAM_FLOATS + warp * WARP_FLOATS;
-            int* cum = reinterpret_cast<int*>(tab + WCUM);
+            // the structure's corrected charges staged in shared memory where they fit (each list
+            // entry reads its neighbour's 32 candidate charges), the warps' row buffers after them
+            const bool qsm = a.mode == 1 && (size_t)n * CG + (size_t)NW * RS_WARP <= (size_t)a.inv_cap;
+            const float* qs = qsm ? un : qcs;
+            float* tab = qsm ? un + (size_t)n * CG + warp * RS_WARP : un + PARAM_FLOATS + warp * WARP_FLOATS;
+            int* cum = reinterpret_cast<int*>(tab + (qsm ? RS_CUM : WCUM));
+            if (qsm) {
+                const float4* src = reinterpret_cast<const float4*>(qcs);
+                float4* dst = reinterpret_cast<float4*>(un);
+                for (int i = threadIdx.x; i < n * CG / 4; i += NW * 32) dst[i] = src[i];
+                __syncthreads();
+            }
             for (int m = warp; m < n; m += NW) {
-                const float qi = qcs[(size_t)m * CG + lane];
+                const float qi = qs[(size_t)m * CG + lane];
                 float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                 float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
                 if (a.mode == 1) {
@@ -2042,7 +2055,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                                 d3[u] = rw[3];             // (j_desc, B, B'u_x, B'u_y)
                                 bz[u] = d4.x;
                                 const int j = __float_as_int(d4.y);
-                                qj[u] = (j >= 0 && r0 + u < cntc) ? qcs[(size_t)j * CG + lane] : 0.f;
+                                qj[u] = (j >= 0 && r0 + u < cntc) ? qs[(size_t)j * CG + lane] : 0.f;
                                 if (VIR) {
                                     // pair virial: sum_j q_j B'(r) r u (x) u, with B' u from the row
                                     const float4 d2 = rw[2];   // (f'_8, u)
