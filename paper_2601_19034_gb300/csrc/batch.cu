@@ -1194,7 +1194,7 @@ __device__ __noinline__ bool field_tc(int n, int nmax, const float2* __restrict_
 constexpr int SK_AT = 32;                         // atoms per tile (K)
 constexpr int SK_APLANE = 128 * SK_AT * 2;        // 8192 B: 128 rows x 32 FP16
 constexpr int SK_ABUF = 2 * SK_APLANE;            // hi | lo of one window
-constexpr int SK_WPS = 4;                         // windows per pipeline stage
+constexpr int SK_WPS = 2;                         // windows per pipeline stage
 constexpr int SK_STAGE = SK_WPS * SK_ABUF;
 constexpr int SK_BPLANE = CG * SK_AT * 2;         // 2048 B: 32 candidate rows x 32 FP16
 constexpr int SK_BBUF = 2 * SK_BPLANE;
