@@ -172,6 +172,8 @@ def force_call(positions, box, types, hp, blob, elec, want_bec: bool = True,
         "e_nep": float(u.sum()), "e_real": es["e_real"], "e_kspace": es["e_kspace"],
         "e_self": es["e_self"], "site_energy": u, "descriptor": d_all,
         "q_raw": q, "charges": q_c, "qtilde": qt_c, "phi": phi,
+        # predicted total charge before the correction, sum_i q~_i (the D_Q term of Sec. II.E)
+        "total_charge_raw": float(qt.sum()),
         "forces": force, "virial": virial,
         "polarization": (qt_c[:, None] * pos).sum(0),
         "n_radial_entries": len(ent_r.i), "n_angular_entries": len(ent_a.i),

@@ -273,3 +273,26 @@ def test_virial_rmse_over_all_nine_components(monkeypatch):
     monkeypatch.setattr(training, "virial_rmse", wrong)
     with pytest.raises(AssertionError):
         t_tr.test_virial_rmse_closed_forms()
+
+
+def test_bec_rmse_over_every_structure(monkeypatch):
+    """Counting the structures without reference BEC fails the closed forms."""
+    def wrong(bec, bec_ref, atom_offsets, has_ref):
+        off = np.asarray(atom_offsets, dtype=np.int64)
+        z = np.asarray(bec, dtype=np.float64).reshape(-1, off[-1], 9)
+        zr = np.asarray(bec_ref, dtype=np.float64).reshape(off[-1], 9)
+        return np.sqrt(((z - zr[None]) ** 2).reshape(z.shape[0], -1).mean(axis=1))
+    monkeypatch.setattr(training, "bec_rmse", wrong)
+    _fails(t_tr.test_bec_rmse_closed_forms)
+
+
+def test_total_charge_after_the_correction(monkeypatch):
+    """Reporting the corrected charges' sum (the target, by construction) fails the closed form."""
+    orig = forcecall.force_call
+
+    def wrong(*args, **kw):
+        out = orig(*args, **kw)
+        out["total_charge_raw"] = float(out["qtilde"].sum())
+        return out
+    monkeypatch.setattr(forcecall, "force_call", wrong)
+    _fails(t_tr.test_force_call_total_charge_before_the_correction)

@@ -139,3 +139,95 @@ def test_virial_rmse_closed_forms():
     np.testing.assert_allclose(terms[2], 0.0)
     np.testing.assert_allclose(tr.loss_v(terms, 1.0, 1.0, 0.3, 0.05, 0.01),
                                0.05 * np.abs(z).sum(1) + 0.01 * (z ** 2).sum(1), atol=1e-12)
+
+
+def _bec_case(seed=7, c=3, sizes=(4, 0, 6, 2), has=(True, True, False, True)):
+    rng = np.random.default_rng(seed)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    z = rng.normal(size=(c, off[-1], 3, 3))
+    z_ref = rng.normal(size=(off[-1], 3, 3))
+    return z, z_ref, off, np.asarray(has)
+
+
+def test_bec_rmse_matches_brute_force():
+    z, z_ref, off, has = _bec_case()
+    d_z = tr.bec_rmse(z, z_ref, off, has)
+    for c in range(z.shape[0]):
+        acc, cnt = 0.0, 0
+        for s in range(len(off) - 1):
+            if not has[s]:
+                continue
+            for i in range(off[s], off[s + 1]):
+                for a in range(3):
+                    for b in range(3):
+                        acc += (z[c, i, a, b] - z_ref[i, a, b]) ** 2
+                        cnt += 1
+        assert abs(d_z[c] - math.sqrt(acc / cnt)) < 1e-12
+    np.testing.assert_allclose(tr.bec_rmse(z, z_ref, off, np.zeros(4, bool)), 0.0)
+
+
+def test_bec_rmse_closed_forms():
+    """A uniform offset on every component of the referenced structures gives its size; on the
+    diagonal only, its size / sqrt(3); on the structures without reference, 0."""
+    _, z_ref, off, has = _bec_case(seed=8)
+    d = np.array([0.4, -0.03, 1.7])
+    mask = np.zeros(off[-1], bool)
+    for s in range(len(has)):
+        mask[off[s]:off[s + 1]] = has[s]
+    every = z_ref[None] + d[:, None, None, None] * mask[None, :, None, None]
+    np.testing.assert_allclose(tr.bec_rmse(every, z_ref, off, has), np.abs(d), atol=1e-12)
+    diag = z_ref[None] + d[:, None, None, None] * mask[None, :, None, None] * np.eye(3)
+    np.testing.assert_allclose(tr.bec_rmse(diag, z_ref, off, has), np.abs(d) / math.sqrt(3.0), atol=1e-12)
+    other = z_ref[None] + d[:, None, None, None] * (~mask)[None, :, None, None]
+    np.testing.assert_allclose(tr.bec_rmse(other, z_ref, off, has), 0.0, atol=1e-12)
+
+
+def test_total_charge_rmse_brute_force_and_offset():
+    rng = np.random.default_rng(9)
+    off = np.array([0, 3, 3, 8, 9])
+    q = rng.normal(size=(4, 4))
+    q_ref = rng.normal(size=4)
+    d_q = tr.total_charge_rmse(q, q_ref, off)
+    for c in range(4):
+        acc = [(q[c, s] - q_ref[s]) ** 2 for s in range(4) if off[s + 1] > off[s]]
+        assert abs(d_q[c] - math.sqrt(sum(acc) / len(acc))) < 1e-12
+    d = np.array([0.25, -0.5, 0.0, 3.0])
+    np.testing.assert_allclose(tr.total_charge_rmse(q_ref[None] + d[:, None], q_ref, off), np.abs(d), atol=1e-12)
+    # the full loss: every term zero at the reference leaves the norms, each weight on its own term
+    e, f, e_ref, f_ref, off2, z = _case(seed=10, c=4)
+    n = off2[-1]
+    terms = tr.loss_terms_full(e_ref[None].repeat(4, 0), f_ref[None].repeat(4, 0), None,
+                               np.zeros((4, n, 3, 3)) + d[:, None, None, None], np.zeros((4, 4)) + d[:, None],
+                               e_ref, f_ref, None, np.zeros((n, 3, 3)), np.ones(4, bool), np.zeros(4), off2, z)
+    np.testing.assert_allclose(terms[3], np.abs(d), atol=1e-12)
+    np.testing.assert_allclose(terms[4], np.abs(d), atol=1e-12)
+    np.testing.assert_allclose(tr.loss_full(terms, 1.0, 1.0, 1.0, 0.7, 0.2, 0.05, 0.01),
+                               0.9 * np.abs(d) + 0.05 * np.abs(z).sum(1) + 0.01 * (z ** 2).sum(1), atol=1e-12)
+
+
+def test_force_call_total_charge_before_the_correction():
+    """With the charge output weights zero every raw charge is -b1q of its species (the bias is
+    subtracted, Eq. U_i's convention for the charge node), so the predicted total charge is
+    -sqrt(eps_inf) sum_i b1q[t_i], whatever the positions and the target Q; the corrected
+    charges still sum to Q / sqrt(eps_inf)."""
+    from oracle import forcecall
+    from paper_2601_19034_gb300 import workloads as wl
+    sysm = wl.water_box(2, seed=3)
+    hp = wl.HParams(n_species=2)
+    blob = wl.random_params(hp, np.random.default_rng(4))[0].astype(np.float32)
+    s, nn, nd = hp.n_species, hp.n_neurons, hp.n_des
+    o = s * s * (hp.n_radial * hp.basis_radial + hp.n_angular * hp.basis_angular) + nd
+    b1q = []
+    for _ in range(s):
+        o += nn * nd + nn + nn          # W0, b0, w1E
+        blob[o:o + nn] = 0.0            # w1q
+        o += nn
+        b1q.append(float(blob[o + 1]))  # b1E, b1q
+        o += 2
+    seps = float(blob[-1])
+    expect = -seps * sum(b1q[t] for t in sysm.types)
+    for q_total in (0.0, 0.6):
+        out = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, blob,
+                                   wl.Elec(mode=1, kind="ewald", q_total=q_total), want_bec=False)
+        assert abs(out["total_charge_raw"] - expect) < 1e-9 * max(1.0, abs(expect))
+        assert abs(out["charges"].sum() - q_total / seps) < 1e-9
