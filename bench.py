@@ -670,10 +670,12 @@ def _time_plain_single(hp, params0, elec, systems, dev, stream, flush):
                     f"replayed back to back after one L2 flush (median of 3); eager calls beside it"}
 
 
-def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals):
-    """The headline batched call with the per-(candidate, structure) virial as well."""
+def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals, bec=False):
+    """The headline batched call with the per-(candidate, structure) virial as well (and, with
+    bec, the per-atom Born effective charges and the uncorrected total charges: every input of
+    the full training loss)."""
     import torch
-    out = b.outputs(len(off) - 1, pos_d.shape[0], pos_d.device, virial=True)
+    out = b.outputs(len(off) - 1, pos_d.shape[0], pos_d.device, virial=True, bec=bec, total_charge=bec)
     b.compute_into(pos_d, typ_d, off, boxes, out)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -694,9 +696,12 @@ def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals):
         if k >= 3:
             ts.append(e0.elapsed_time(e1))
     ms = float(np.median(ts))
-    return {"ms_per_step": ms, "value": evals / (ms * 1e-3), "unit": UNIT,
-            "what": "the same graph-replayed batched call writing energies, forces, charges and the 3x3 virial "
-                    "of every (candidate, structure) (qnep_batch_compute_outputs)"}
+    what = ("the same graph-replayed batched call writing energies, forces, charges and the 3x3 virial "
+            "of every (candidate, structure) (qnep_batch_compute_outputs)")
+    if bec:
+        what += ", the 3x3 Born effective charge of every atom and the total charge before the correction"
+    del out, g
+    return {"ms_per_step": ms, "value": evals / (ms * 1e-3), "unit": UNIT, "what": what}
 
 
 def _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, flush, contract, steps, evals):
@@ -932,6 +937,7 @@ def run_batch(args):
     d2h = sum(v.numel() * v.element_size() for v in out_h.values())
     # the same call with the per-(candidate, structure) virial (graph replay, L2 flushed)
     with_virial = _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, min(args.steps, 10), evals)
+    with_bec = _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, min(args.steps, 10), evals, bec=True)
 
     # one device-resident SNES iteration around the same call (Sec. II.E): normal deviates,
     # sampling, parameter upload, the batched call (graph replay), the loss against reference
@@ -969,6 +975,7 @@ def run_batch(args):
             "snes_step": dict(snes, batched_call_ms=ms_per_step),
             "plain_fp32": dict(plain, speedup_batched_vs_plain=value / plain["value"]),
             "with_virial": with_virial,
+            "with_bec": with_bec,
             "e2e": {"value": evals / (statistics.median(e2e_ms) * 1e-3) * world, "unit": UNIT,
                     "h2d_bytes_per_step": n_total * 16, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.median(e2e_ms),

@@ -328,8 +328,9 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * (Eq. U_i, Eq. U_ES with the charges of Sec. II.D), the forces including the
  * charge-derivative terms (Sec. II.C) and the corrected charges q^c.
  * Electrostatics: Ewald (mode 1 or 2) per structure; PPPM is not offered here.
- * The virial per (candidate, structure) comes with qnep_batch_compute_outputs; BEC and
- * polarization are not computed by the batched call.
+ * The virial per (candidate, structure), the per-atom Born effective charges (Eq. bec_2) and the
+ * total charge before the correction come with qnep_batch_compute_outputs; the polarization is
+ * not computed by the batched call.
  *
  * qnep_batch_create: hp and es as for qnep_create (es->kind must be QNEP_EWALD);
  *   params_host = n_candidates blobs of qnep_param_count(hp) floats, candidate-major.
@@ -345,7 +346,10 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  *   charges:      device [n_candidates][N_total] float32 (e), or NULL
  * The first call with a new (atom_offsets, boxes) builds the k-tables and work
  * list on the host and (re)allocates workspaces; later identical calls only
- * launch.  Errors in the arguments return before any GPU work; device-side
+ * launch.  A graph captured from a call keeps that call's workspaces: re-capture it
+ * after a call that reallocated them (a new description, a capacity change, a
+ * launch shape with more resident blocks).  Asking for BEC allocates its accumulators
+ * in a buffer of their own, so it does not move the workspaces of calls without BEC.  Errors in the arguments return before any GPU work; device-side
  * conditions (list overflow, a species index out of range) are reported by
  * qnep_batch_sync_status (QNEP_ERR_NBR_OVERFLOW: raise the capacity with
  * qnep_batch_set_capacity and call again; outputs of that call are invalid).
@@ -359,8 +363,8 @@ qnep_status qnep_batch_compute(qnep_batch* b, int n_struct, const int* atom_offs
                                float* forces, float* charges);
 qnep_status qnep_batch_sync_status(qnep_batch* b);
 
-/* Outputs of a batched call, indexed [candidate][structure] (energy, virial) or
- * [candidate][atom] (forces, charges); energy is required, the others may be NULL.
+/* Outputs of a batched call, indexed [candidate][structure] (energy, virial, total charge) or
+ * [candidate][atom] (forces, charges, BEC); energy is required, the others may be NULL.
  *   energy:  [C][S] doubles, U^tot (eV)
  *   forces:  [C][N_total][3] float32 (eV/A)
  *   charges: [C][N_total] float32, corrected charges q^c (e)
@@ -368,12 +372,24 @@ qnep_status qnep_batch_sync_status(qnep_batch* b);
  *            r -> (I + eps) r of positions and cell (eV; row-major 3x3): the sum over neighbour
  *            entries of -r_ij (x) F_ij (descriptor and dynamic-charge partial forces, Sec. II.C),
  *            the static real-space pair terms and the k-space W^k = sum k_e G |S|^2 B
- *            (Eq. virial-kspace-total), each FP32 per atom or per k and FP64 across them. */
+ *            (Eq. virial-kspace-total), each FP32 per atom or per k and FP64 across them.
+ *   bec:     [C][N_total][9] float32, Born effective charges Z_i,ab = dP_a/dr_ib of Eq. bec_2 (e;
+ *            row-major, first index the polarization component): q~^c_i on the diagonal plus
+ *            1/2 r_ij (x) a_ij for each of i's neighbour entries and -1/2 r_ji (x) a_ji for each
+ *            entry (j -> i), a_ij = dq~_i/dr_ij from the charge adjoint sqrt(eps_inf) dq_i/dD
+ *            (Sec. II.D).  Asking for it adds a second pass over the neighbour entries (about
+ *            the backward's time again) and 48 bytes of scratch per atom, candidate and
+ *            resident block; it is the input of the D_Z term of the training loss.
+ *   total_charge: [C][S] doubles, sum_i q~_i = sqrt(eps_inf) sum_i q_i of the network's charges
+ *            BEFORE the correction of Eq. charge-scaling (e; after it the sum is the target),
+ *            the input of the D_Q term of the training loss; 0 for a structure without atoms. */
 typedef struct {
     double* energy;
     float*  forces;
     float*  charges;
     double* virial;
+    float*  bec;
+    double* total_charge;
 } qnep_batch_outputs;
 /* As qnep_batch_compute, with every output of qnep_batch_outputs (device pointers). */
 qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,
@@ -435,8 +451,8 @@ qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stre
 /* ---- Training: population loss and separable NES (Sec. II.E) ----------------
  * The paper trains every parameter z (descriptor, network, sqrt(eps_inf)) with SNES on
  *   L(z) = l_e D_e + l_f D_f + l_v D_v + l_Z D_Z + l_Q D_Q + l_1 |z|_1 + l_2 |z|_2^2.
- * The batched call feeds D_e and D_f (its corrected charges meet the total-charge target
- * exactly; it computes neither virials nor BEC), read as
+ * The batched call feeds every term (qnep_batch_loss_full); qnep_batch_loss and
+ * qnep_batch_loss_v are its shorter forms.  Read as
  *   D_e = sqrt(1/S' sum_s ((E_s - E_s^ref) / N_s)^2)   over the S' structures with atoms (eV/atom)
  *   D_f = sqrt(1/(3N) sum_i,b (F_ib - F_ib^ref)^2)      over all N atoms (eV/A).
  * One device-resident iteration: qnep_snes_sample -> qnep_batch_set_params ->
@@ -485,6 +501,43 @@ qnep_status qnep_batch_loss_v(int n_candidates, int n_struct, const int* atom_of
                               const double* energy_ref, const float* forces_ref, const double* virial_ref,
                               const float* params, int n_params, const qnep_loss_weights_v* w, double* loss,
                               double* terms, void* stream);
+
+/* The full loss of Sec. II.E:
+ *   L = l_e D_e + l_f D_f + l_v D_v + l_Z D_Z + l_Q D_Q + l_1 |z|_1 + l_2 |z|_2^2
+ * with D_e, D_f, D_v as above and
+ *   D_Z = sqrt(1/(9 N_Z) sum_{s: bec_has_ref[s] != 0} sum_{i in s} sum_ab (Z_i,ab - Z^ref_i,ab)^2)
+ *         over the N_Z atoms of the structures that carry reference BEC (the paper makes BEC
+ *         targets optional, for a subset of the training structures; 0 when none has atoms)
+ *   D_Q = sqrt(1/S' sum_s (Q_s - Q^ref_s)^2) over the S' structures with atoms, Q_s the total
+ *         charge before the correction (qnep_batch_outputs.total_charge), Q^ref_s its target.
+ * `in` holds the batched call's outputs (device): energy [C][S] f64 (required), forces
+ * [C][N][3] f32, virial [C][S][9] f64, bec [C][N][9] f32, total_charge [C][S] f64; `ref` the
+ * references in the same order without the candidate index (energy [S], forces [N][3], virial
+ * [S][9], bec [N][9], total_charge [S]).  Each output and its reference are given or NULL together
+ * (a NULL pair gives its term 0); bec_has_ref: device [S] int, required with bec.  Writes loss [C]
+ * f64 and terms [C][7] f64 = (D_e, D_f, D_v, D_Z, D_Q, |z|_1, |z|_2^2).  The BEC squares are summed
+ * like the forces' (compensated FP32 per thread, FP64 across blocks).  QNEP_ERR_ARG for missing
+ * or unpaired buffers, C outside [1, 65535], non-finite weights. */
+typedef struct {
+    const double* energy;
+    const float*  forces;
+    const double* virial;
+    const float*  bec;
+    const double* total_charge;
+} qnep_loss_inputs;
+typedef struct {
+    double energy;   /* l_e */
+    double force;    /* l_f */
+    double virial;   /* l_v */
+    double bec;      /* l_Z */
+    double charge;   /* l_Q */
+    double l1;       /* l_1 */
+    double l2;       /* l_2 */
+} qnep_loss_weights_full;
+qnep_status qnep_batch_loss_full(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                                 const qnep_loss_inputs* in, const qnep_loss_inputs* ref, const int* bec_has_ref,
+                                 const float* params, int n_params, const qnep_loss_weights_full* w, double* loss,
+                                 double* terms, void* stream);
 
 /* One SNES step (Schaul et al. 2011) from the losses of the population sampled with `noise`:
  * candidates ranked by loss (lowest first, ties by index, NaN last); utilities

@@ -65,7 +65,18 @@ class VjpC(ctypes.Structure):
 
 class BatchOutputsC(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p), ("charges", ctypes.c_void_p),
-                ("virial", ctypes.c_void_p)]
+                ("virial", ctypes.c_void_p), ("bec", ctypes.c_void_p), ("total_charge", ctypes.c_void_p)]
+
+
+class LossInputsC(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p), ("virial", ctypes.c_void_p),
+                ("bec", ctypes.c_void_p), ("total_charge", ctypes.c_void_p)]
+
+
+class LossWeightsFullC(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("force", ctypes.c_double), ("virial", ctypes.c_double),
+                ("bec", ctypes.c_double), ("charge", ctypes.c_double), ("l1", ctypes.c_double),
+                ("l2", ctypes.c_double)]
 
 
 class LossWeightsVC(ctypes.Structure):
@@ -144,6 +155,9 @@ def _declare(lib):
     lib.qnep_batch_compute_host.restype = i
     lib.qnep_batch_loss_v.argtypes = [i, i, p, i, p, p, p, p, p, p, p, i, ctypes.POINTER(LossWeightsVC), p, p, p]
     lib.qnep_batch_loss_v.restype = i
+    lib.qnep_batch_loss_full.argtypes = [i, i, p, i, ctypes.POINTER(LossInputsC), ctypes.POINTER(LossInputsC), p, p,
+                                         i, ctypes.POINTER(LossWeightsFullC), p, p, p]
+    lib.qnep_batch_loss_full.restype = i
     lib.qnep_batch_set_contraction.argtypes = [p, i]
     lib.qnep_batch_set_contraction.restype = i
     lib.qnep_batch_get_contraction.argtypes = [p, ctypes.POINTER(i)]

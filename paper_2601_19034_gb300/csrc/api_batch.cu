@@ -50,7 +50,7 @@ struct qnep_batch {
     // pre-pass outputs (element counts allocated)
     struct {
         size_t spos4 = 0, sidx = 0, order = 0, spec = 0, cells = 0, list = 0, ang = 0, cnt_list = 0, cnt_ang = 0,
-               phase = 0, geo_rad = 0, geo_ang = 0, bsum = 0, bimg = 0;
+               phase = 0, geo_rad = 0, geo_ang = 0, bsum = 0, bimg = 0, zsum = 0;
     } alloc;
     float4* spos4 = nullptr;
     int* sidx = nullptr;
@@ -66,6 +66,7 @@ struct qnep_batch {
     float* geo_ang = nullptr;
     float* bsum = nullptr;
     unsigned char* bimg = nullptr;          // B^A operand images (tensor-core contraction only)
+    float4* zsum = nullptr;                 // per-slot BEC accumulators (calls with BEC only)
     // per-slot scratch
     size_t slot_bytes_alloc = 0;
     int slots_alloc = 0;
@@ -74,7 +75,7 @@ struct qnep_batch {
     unsigned int* d_work = nullptr;
     unsigned int* d_status = nullptr;
     cudaStream_t last_stream = nullptr;
-    std::map<std::tuple<int, int, int, bool>, int> per_sm_cache;   // (warps, nph_max, contract, virial) -> blocks per SM
+    std::map<std::tuple<int, int, int, int>, int> per_sm_cache;   // (warps, nph_max, contract, 0 | virial 1 | BEC 2) -> blocks per SM
     // host-buffer entry point: device copies of the inputs and outputs (grown on demand)
     float* io_pos = nullptr;
     int* io_types = nullptr;
@@ -82,6 +83,8 @@ struct qnep_batch {
     float* io_forces = nullptr;
     float* io_charges = nullptr;
     double* io_virial = nullptr;
+    float* io_bec = nullptr;
+    double* io_qtot = nullptr;
     size_t io_atoms = 0, io_evals = 0, io_pairs = 0;
     // stage timers: events around the pre-pass and the item kernel of each profiled call
     bool profiling = false, pending = false;
@@ -292,7 +295,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
 }
 
 // Per-slot scratch for the current description and block shape.
-qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
+qnep_status ensure_scratch(qnep_batch* b, int slots, bool bec, cudaStream_t st) {
     const size_t nm = (size_t)std::max(b->nmax, 1), nk = (size_t)std::max(b->nk_max, 8);
     BatchScratch& sc = b->sc;
     const size_t sA = nm * NANG * CG, sD = nm * 2 * NDES * CG, sN = nm * CG, sK = nk * CG;
@@ -300,6 +303,7 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     // floats per slot: A, duq, uq (2), qc (1), fk/fr/fsum (4 each), sk (2), skp (2), virial sums
     // (8 warps x 9 x CG doubles)
     const size_t sV = (size_t)8 * 9 * CG;
+    // (8 warps x 9 x CG doubles)
     const size_t per = sA + sD + 2 * sN + sN + 12 * sN + 2 * sK + 2 * sP + 2 * sV + 64;
     const size_t bytes = per * sizeof(float) * (size_t)slots;
     if (bytes > b->slot_bytes_alloc || !b->scratch) {
@@ -334,6 +338,18 @@ qnep_status ensure_scratch(qnep_batch* b, int slots, cudaStream_t st) {
     sc.skp = reinterpret_cast<float2*>(take(2 * sP * slots));
     sc.vir = reinterpret_cast<double*>(take(2 * sV * slots));
     b->slots_alloc = slots;
+    // BEC accumulators (three float4 per atom and candidate) in a buffer of their own: asking for BEC
+    // never moves the scratch above, which graphs captured from calls without BEC keep using
+    sc.zsum = nullptr;
+    if (bec) {
+        const size_t nz = 3 * sN * (size_t)slots;
+        if (nz > b->alloc.zsum) {
+            CKB(cudaStreamSynchronize(st));
+            if (b->last_stream) CKB(cudaStreamSynchronize(b->last_stream));
+        }
+        CKB(regrow(&b->zsum, nz, &b->alloc.zsum));
+        sc.zsum = b->zsum;
+    }
     return QNEP_OK;
 }
 
@@ -480,6 +496,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     float* forces = out->forces;
     float* charges = out->charges;
     double* virial = out->virial;
+    const bool bec = out->bec != nullptr;
     if (n_struct < 1 || !atom_offsets || !boxes || !energy) return failb(b, QNEP_ERR_ARG, "bad batch arguments");
     if (atom_offsets[0] != 0) return failb(b, QNEP_ERR_ARG, "atom_offsets[0] must be 0");
     if (atom_offsets[n_struct] > 0 && (!positions || !types))
@@ -494,11 +511,11 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     }
     // blocks per SM of this shape (cached: no CUDA calls beyond launches once the batch is known,
     // so the call can be captured in a graph)
-    const auto key = std::make_tuple(b->warps, b->nph_max, b->contract, virial != nullptr);
+    const auto key = std::make_tuple(b->warps, b->nph_max, b->contract, bec ? 2 : (virial ? 1 : 0));
     auto hit = b->per_sm_cache.find(key);
     if (hit == b->per_sm_cache.end())
         hit = b->per_sm_cache
-                  .emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max, b->contract, virial != nullptr))
+                  .emplace(key, batch_item_blocks_per_sm(b->warps, b->nph_max, b->contract, virial != nullptr, bec))
                   .first;
     const int per_sm = hit->second;
     if (per_sm <= 0) return failb(b, QNEP_ERR_UNSUPPORTED, "item kernel does not fit on an SM");
@@ -508,13 +525,15 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
         CKB(regrow(&b->bimg, (size_t)std::max(b->n_total, 1) * BIMG_BYTES, &b->alloc.bimg));
     }
     const int slots = per_sm * b->num_sms;
-    qnep_status s = ensure_scratch(b, slots, st);
+    qnep_status s = ensure_scratch(b, slots, bec, st);
     if (s != QNEP_OK) return s;
     CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
     CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
     if (b->has_empty) {   // structures without atoms have no item: their energies (and virials) are zero
         CKB(cudaMemsetAsync(energy, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
         if (virial) CKB(cudaMemsetAsync(virial, 0, sizeof(double) * 9 * (size_t)b->n_cand * n_struct, st));
+        if (out->total_charge)
+            CKB(cudaMemsetAsync(out->total_charge, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
     }
     if (b->profiling) {
         if (b->pending) {   // previous profiled call: harvest its events
@@ -570,6 +589,8 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     a.forces = forces;
     a.charges = charges;
     a.virial = virial;
+    a.bec = out->bec;
+    a.total_charge = out->total_charge;
     a.n_struct = n_struct;
     a.n_total = b->n_total;
     a.status = b->d_status;
@@ -611,7 +632,8 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
     if ((size_t)n_total > b->io_atoms || evals > b->io_evals || pairs > b->io_pairs || !b->io_energy) {
         // device copies of the inputs and of every output, kept for the next call of this shape
         CKB(cudaStreamSynchronize(st));
-        void* old[] = {b->io_pos, b->io_types, b->io_energy, b->io_forces, b->io_charges, b->io_virial};
+        void* old[] = {b->io_pos, b->io_types, b->io_energy, b->io_forces, b->io_charges, b->io_virial, b->io_bec,
+                       b->io_qtot};
         for (void* q : old)
             if (q) cudaFree(q);
         b->io_pos = nullptr;
@@ -620,6 +642,8 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         b->io_forces = nullptr;
         b->io_charges = nullptr;
         b->io_virial = nullptr;
+        b->io_bec = nullptr;
+        b->io_qtot = nullptr;
         b->io_atoms = b->io_evals = b->io_pairs = 0;
         const size_t na = std::max<size_t>(n_total, 1), ne = std::max<size_t>(evals, 1), np = std::max<size_t>(pairs, 1);
         CKB(cudaMalloc((void**)&b->io_pos, sizeof(float) * 3 * na));
@@ -628,6 +652,7 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         CKB(cudaMalloc((void**)&b->io_forces, sizeof(float) * 3 * ne));
         CKB(cudaMalloc((void**)&b->io_charges, sizeof(float) * ne));
         CKB(cudaMalloc((void**)&b->io_virial, sizeof(double) * 9 * np));
+        CKB(cudaMalloc((void**)&b->io_qtot, sizeof(double) * np));
         b->io_atoms = na;
         b->io_evals = ne;
         b->io_pairs = np;
@@ -636,8 +661,13 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         CKB(cudaMemcpyAsync(b->io_pos, positions_host, sizeof(float) * 3 * (size_t)n_total, cudaMemcpyHostToDevice, st));
         CKB(cudaMemcpyAsync(b->io_types, types_host, sizeof(int) * (size_t)n_total, cudaMemcpyHostToDevice, st));
     }
+    if (out_host->bec && !b->io_bec) {   // BEC copies only for callers that ask for them (9 floats per evaluation)
+        CKB(cudaStreamSynchronize(st));
+        CKB(cudaMalloc((void**)&b->io_bec, sizeof(float) * 9 * b->io_evals));
+    }
     qnep_batch_outputs dev{b->io_energy, out_host->forces ? b->io_forces : nullptr,
-                           out_host->charges ? b->io_charges : nullptr, out_host->virial ? b->io_virial : nullptr};
+                           out_host->charges ? b->io_charges : nullptr, out_host->virial ? b->io_virial : nullptr,
+                           out_host->bec ? b->io_bec : nullptr, out_host->total_charge ? b->io_qtot : nullptr};
     qnep_status s = qnep_batch_compute_outputs(b, n_struct, atom_offsets, b->io_pos, b->io_types, boxes, stream, &dev);
     if (s != QNEP_OK) return s;
     CKB(cudaMemcpyAsync(out_host->energy, b->io_energy, sizeof(double) * pairs, cudaMemcpyDeviceToHost, st));
@@ -647,6 +677,10 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         CKB(cudaMemcpyAsync(out_host->charges, b->io_charges, sizeof(float) * evals, cudaMemcpyDeviceToHost, st));
     if (out_host->virial)
         CKB(cudaMemcpyAsync(out_host->virial, b->io_virial, sizeof(double) * 9 * pairs, cudaMemcpyDeviceToHost, st));
+    if (out_host->bec)
+        CKB(cudaMemcpyAsync(out_host->bec, b->io_bec, sizeof(float) * 9 * evals, cudaMemcpyDeviceToHost, st));
+    if (out_host->total_charge)
+        CKB(cudaMemcpyAsync(out_host->total_charge, b->io_qtot, sizeof(double) * pairs, cudaMemcpyDeviceToHost, st));
     b->last_stream = st;
     return qnep_batch_sync_status(b);
 }
@@ -766,7 +800,7 @@ void qnep_batch_destroy(qnep_batch* b) {
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,
                     b->d_work,    b->d_status, b->io_pos,   b->io_types, b->io_energy, b->io_forces,
-                    b->io_charges, b->io_virial};
+                    b->io_charges, b->io_virial, b->io_bec, b->io_qtot, b->zsum};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto e : b->ev)

@@ -1391,16 +1391,43 @@ __device__ __noinline__ bool sk_tc(int n, const float2* __restrict__ phb, int ps
 // Backward of sorted atom m: partial forces of every list entry (Sec. II.C).  The atom's
 // pair rows arrive in 32-row pieces by double-buffered bulk copies: the copy of the next
 // piece is in flight while the current one is used.
-template <bool VIR>
+// One entry's share of Eq. bec_2: z = 1/2 r_ij (x) a_ij (h = r_ij / 2; row-major, the first index
+// from r), added to the central atom's registers and subtracted from atom j's accumulator.
+__device__ __forceinline__ void bec_entry(float4* __restrict__ zsum, int j, int lane, float hx, float hy, float hz,
+                                          float ax, float ay, float az, float zi[9]) {
+    const float z0 = hx * ax, z1 = hx * ay, z2 = hx * az, z3 = hy * ax, z4 = hy * ay, z5 = hy * az, z6 = hz * ax,
+                z7 = hz * ay, z8 = hz * az;
+    zi[0] += z0; zi[1] += z1; zi[2] += z2; zi[3] += z3; zi[4] += z4;
+    zi[5] += z5; zi[6] += z6; zi[7] += z7; zi[8] += z8;
+    float4* zj = zsum + (size_t)j * 3 * CG + lane;
+    atomicAdd(&zj[0], make_float4(-z0, -z1, -z2, -z3));
+    atomicAdd(&zj[CG], make_float4(-z4, -z5, -z6, -z7));
+    atomicAdd(reinterpret_cast<float*>(&zj[2 * CG]), -z8);
+}
+
+// BEC = false: the forces (and, with VIR, the virial) of atom m's entries from the adjoint
+// lambda_i = dU_i/dD + (phi_i - mean phi) dq_i/dD.  BEC = true: the same contraction with the
+// charge adjoint kappa_i = sqrt(eps_inf) dq_i/dD gives the per-entry charge derivatives
+// a_ij = dq~_i/dr_ij, scattered as Eq. bec_2: Z_i += 1/2 r_ij (x) a_ij, Z_j -= 1/2 r_ij (x) a_ij
+// (first index the polarization component), plus the diagonal q~^c_i of atom m (zsum, three
+// float4 per atom and candidate: Z_xx..Z_yx | Z_yy..Z_zy | Z_zz, -, -, -).
+template <bool VIR, bool BEC = false>
 __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n, int m,
                                               const float* __restrict__ prm, float* __restrict__ wb,
                                               uint64_t* bars, uint32_t& par, const float* __restrict__ A,
                                               const float* __restrict__ duq, const float* __restrict__ qcs,
                                               const float4* __restrict__ fk, const float4* __restrict__ fr,
                                               float4* __restrict__ fsum, int nmax, float selfc, float phibar,
-                                              double* __restrict__ vw) {
+                                              double* __restrict__ vw, float seps = 0.f,
+                                              float4* __restrict__ zsum = nullptr) {
+    static_assert(!(VIR && BEC), "the BEC pass carries no virial");
     const int lane = threadIdx.x & 31;
     const int S = a.lay.n_species;
+    float zi[9];   // BEC: this atom's own share of its entries' Z terms
+    if (BEC) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) zi[q] = 0.f;
+    }
     // virial of this atom's entries: W -= r_ij (x) F_ij (the partial force F_ij acts on i, -F_ij
     // on j); the radial part is symmetric (F_ij along u_ij)
     float wv[9], wr[3];
@@ -1431,7 +1458,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
     float lam[NDES];
     const float* dd = duq + (size_t)m * 2 * NDES * CG + lane;
 #pragma unroll
-    for (int v = 0; v < NDES; ++v) lam[v] = fmaf(wq, dd[(NDES + v) * CG], dd[v * CG]);
+    for (int v = 0; v < NDES; ++v) lam[v] = BEC ? seps * dd[(NDES + v) * CG] : fmaf(wq, dd[(NDES + v) * CG], dd[v * CG]);
     // Phi_{n,lm} = d(lambda . D)/dA_{n,lm}
     float Phi[NA][NLM];
     const float* Ai = A + (size_t)m * NANG * CG + lane;
@@ -1483,7 +1510,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
             const int cntc = min(32, cum[tj + 1] - base);
             // four rows per iteration: independent chains (rows past the piece are skipped)
             for (int r0 = 0; r0 < cntc; r0 += 4) {
-                float Fv[4][3];
+                float Fv[4][3], hv[4][3];
                 int jv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1503,6 +1530,12 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
                     Fv[u][0] = sv * d2.y;
                     Fv[u][1] = sv * d2.z;
                     Fv[u][2] = sv * d2.w;
+                    if (BEC) {
+                        const float h = 0.5f * rw[4].z;   // r_ij / 2 along u
+                        hv[u][0] = h * d2.y;
+                        hv[u][1] = h * d2.z;
+                        hv[u][2] = h * d2.w;
+                    }
                     if (VIR) {
                         const float rsv = r0 + u < cntc ? rw[4].z * sv : 0.f;   // r sv (row past the piece: 0)
                         wv[0] = fmaf(-rsv * d2.y, d2.y, wv[0]);
@@ -1516,6 +1549,10 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (jv[u] < 0) continue;
+                    if (BEC) {
+                        bec_entry(zsum, jv[u], lane, hv[u][0], hv[u][1], hv[u][2], Fv[u][0], Fv[u][1], Fv[u][2], zi);
+                        continue;
+                    }
                     fx += Fv[u][0];
                     fy += Fv[u][1];
                     fz += Fv[u][2];
@@ -1586,6 +1623,11 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
                     const float Fx = rho * ux + (gx - gu * ux) * ir;
                     const float Fy = rho * uy + (gy - gu * uy) * ir;
                     const float Fz = rho * uz + (gz - gu * uz) * ir;
+                    if (BEC) {
+                        const float h = 0.5f / ir;   // r_ij / 2 along u
+                        bec_entry(zsum, __float_as_int(a5.z), lane, h * ux, h * uy, h * uz, Fx, Fy, Fz, zi);
+                        continue;
+                    }
                     fx += Fx;
                     fy += Fy;
                     fz += Fz;
@@ -1611,6 +1653,15 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
         b ^= 1;
     }
     __syncwarp();   // buffers and counts are reused by the warp's next atom
+    if (BEC) {
+        // own share plus the diagonal q~^c_i = sqrt(eps_inf) q^c_i
+        const float qt = seps * qc;
+        float4* zm = zsum + (size_t)m * 3 * CG + lane;
+        atomicAdd(&zm[0], make_float4(zi[0] + qt, zi[1], zi[2], zi[3]));
+        atomicAdd(&zm[CG], make_float4(zi[4] + qt, zi[5], zi[6], zi[7]));
+        atomicAdd(reinterpret_cast<float*>(&zm[2 * CG]), zi[8] + qt);
+        return;
+    }
     // own force: network part plus the static electrostatic forces q F^k/q + F^r
     atomicAdd(&fsum[(size_t)m * CG + lane],
               make_float4(fx + fmaf(qc, kf.y, rf.y), fy + fmaf(qc, kf.z, rf.z), fz + fmaf(qc, kf.w, rf.w), 0.f));
@@ -1627,9 +1678,10 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
     }
 }
 
-template <int NW, bool TC, bool VIR>
+template <int NW, bool TC, bool VIR, bool BEC>
 __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     static_assert(!TC || NW == 8, "the tensor-core descriptor contraction uses 8 warps");
+    static_assert(!BEC || VIR, "the BEC form is built on the virial form");
     extern __shared__ __align__(128) unsigned char bsm[];
     __shared__ int s_item;
     __shared__ __align__(8) uint64_t wbars[NW][2];   // per-warp barriers of the two row buffers
@@ -1674,6 +1726,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
     float2* sk = a.sc.sk + slot * a.sc.stride_k;
     float2* skp = a.sc.skp + slot * a.sc.stride_p;
     double* vacc = VIR ? a.sc.vir + slot * (size_t)NW * 9 * CG : nullptr;   // virial [NW][9][CG] FP64
+    float4* zsum = BEC ? a.sc.zsum + slot * 3 * a.sc.stride_n : nullptr;     // BEC [nmax][3][CG] float4
     const int nmax = (int)(a.sc.stride_n / CG);
     const float selfc = a.mode == 1 ? -2.f * KE * a.alpha * 0.564189583547756287f : 0.f;
 
@@ -1690,6 +1743,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         const float* pg = a.pt + (size_t)grp * a.lay.total * CG;
         const int* so = a.spec_off + item.x * (MAX_SPECIES + 1);
         for (int i = threadIdx.x; i < n * CG; i += NW * 32) fsum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (BEC)
+            for (int i = threadIdx.x; i < 3 * n * CG; i += NW * 32) zsum[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (VIR)
             for (int i = threadIdx.x; i < NW * 9 * CG; i += NW * 32) vacc[i] = 0.0;
 
@@ -2121,11 +2176,28 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 backward_atom<VIR>(a, off, n, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk, fr, fsum,
                                    nmax, selfc, phibar, vacc + (size_t)warp * 9 * CG);
         }
+        if constexpr (BEC) {
+            // 5b Born effective charges (Eq. bec_2): the same entry contractions with the charge
+            // adjoint kappa = sqrt(eps_inf) dq/dD, scattered as Z terms
+            const float seps = __ldg(&pg[(size_t)a.lay.sqrt_eps * CG + lane]);
+            for (int ti = 0; ti < S; ++ti) {
+                const int p0 = so[ti], p1 = so[ti + 1];
+                if (p1 == p0) continue;
+                __syncthreads();
+                stage_params_bwd(pg, a.lay, ti, un);
+                __syncthreads();
+                float* wb = un + PARAM_FLOATS + warp * WARP_FLOATS;
+                for (int p = p0 + warp; p < p1; p += NW)
+                    backward_atom<false, true>(a, off, n, a.order[off + p], un, wb, wbars[warp], par, A, duq, qcs, fk,
+                                               fr, fsum, nmax, selfc, 0.f, nullptr, seps, zsum);
+            }
+        }
         __syncthreads();
 
         // 6 outputs in input order, candidate-major: lanes over consecutive input atoms (through the
         // inverse of the sort permutation), so each warp writes contiguous rows of the outputs
-        if ((a.forces || a.charges) && n > a.inv_cap) {   // a structure too large for the permutation
+        const bool zout = BEC && a.bec;
+        if ((a.forces || a.charges || zout) && n > a.inv_cap) {   // a structure too large for the permutation
             for (int i = threadIdx.x; i < n * CG; i += NW * 32) {
                 const int m = i >> 5, c = grp * CG + (i & 31);
                 if (c >= a.n_cand) continue;
@@ -2138,8 +2210,15 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     fo[2] = F.z;
                 }
                 if (a.charges) a.charges[(size_t)c * a.n_total + gi] = qcs[i];
+                if (zout) {
+                    const float4 z0 = zsum[(size_t)(3 * m) * CG + (i & 31)], z1 = zsum[(size_t)(3 * m + 1) * CG + (i & 31)];
+                    const float z8 = zsum[(size_t)(3 * m + 2) * CG + (i & 31)].x;
+                    float* zo = a.bec + ((size_t)c * a.n_total + gi) * 9;
+                    zo[0] = z0.x; zo[1] = z0.y; zo[2] = z0.z; zo[3] = z0.w;
+                    zo[4] = z1.x; zo[5] = z1.y; zo[6] = z1.z; zo[7] = z1.w; zo[8] = z8;
+                }
             }
-        } else if (a.forces || a.charges) {
+        } else if (a.forces || a.charges || zout) {
             int* inv = reinterpret_cast<int*>(un);   // [n]: sorted index of input atom g
             for (int m = threadIdx.x; m < n; m += NW * 32) inv[__ldg(&a.sidx[off + m])] = m;
             __syncthreads();
@@ -2148,6 +2227,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 if (c >= a.n_cand) break;
                 float* fo = a.forces ? a.forces + ((size_t)c * a.n_total + off) * 3 : nullptr;
                 float* qo = a.charges ? a.charges + (size_t)c * a.n_total + off : nullptr;
+                float* zo = zout ? a.bec + ((size_t)c * a.n_total + off) * 9 : nullptr;
                 for (int g = lane; g < n; g += 32) {
                     const int i = inv[g] * CG + cl;
                     if (fo) {
@@ -2157,10 +2237,18 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         fo[3 * g + 2] = F.z;
                     }
                     if (qo) qo[g] = qcs[i];
+                    if (zo) {
+                        const int zm = 3 * inv[g] * CG + cl;
+                        const float4 z0 = zsum[zm], z1 = zsum[zm + CG];
+                        const float z8 = zsum[zm + 2 * CG].x;
+                        float* zr = zo + 9 * (size_t)g;
+                        zr[0] = z0.x; zr[1] = z0.y; zr[2] = z0.z; zr[3] = z0.w;
+                        zr[4] = z1.x; zr[5] = z1.y; zr[6] = z1.z; zr[7] = z1.w; zr[8] = z8;
+                    }
                 }
             }
         }
-        if (VIR && warp == 1 && cand < a.n_cand) {
+        if (VIR && a.virial && warp == 1 && cand < a.n_cand) {
             // W = sum over the warps' FP64 slots (entries, real space, k space), per candidate
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
@@ -2174,6 +2262,10 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
             double e = sums[lane] + sums[CG + lane];
             if (a.mode == 1) e += sums[2 * CG + lane] - (double)KE * (double)a.alpha * 0.564189583547756287 * sums[3 * CG + lane];
             a.energy[(size_t)cand * a.n_struct + item.x] = e;
+            // predicted total charge before the correction, sum_i q~_i = sqrt(eps_inf) sum_i q_i
+            if (a.total_charge)
+                a.total_charge[(size_t)cand * a.n_struct + item.x] =
+                    (double)__ldg(&pg[(size_t)a.lay.sqrt_eps * CG + lane]) * sums[4 * CG + lane];
         }
     }
     if (TC) {
@@ -2236,27 +2328,39 @@ size_t batch_item_smem(int warps, int nph_max, int contract) {
 }
 
 namespace {
-template <int NW, bool TC, bool VIR>
+template <int NW, bool TC, bool VIR, bool BEC = false>
 int blocks_per_sm_of(size_t smem) {
     int nb = 0;
-    cudaFuncSetAttribute(k_batch_items<NW, TC, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<NW, TC, VIR>, NW * 32, smem) != cudaSuccess)
+    cudaFuncSetAttribute(k_batch_items<NW, TC, VIR, BEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_items<NW, TC, VIR, BEC>, NW * 32, smem) !=
+        cudaSuccess)
         nb = 0;
     return nb;
+}
+template <int NW, bool TC>
+int blocks_per_sm_mode(size_t smem, bool virial, bool bec) {
+    if (bec) return blocks_per_sm_of<NW, TC, true, true>(smem);
+    return virial ? blocks_per_sm_of<NW, TC, true>(smem) : blocks_per_sm_of<NW, TC, false>(smem);
+}
+template <int NW, bool TC>
+void launch_mode(const BatchArgs& a, int grid, size_t smem, cudaStream_t st_) {
+    if (a.bec) k_batch_items<NW, TC, true, true><<<grid, NW * 32, smem, st_>>>(a);
+    else if (a.virial) k_batch_items<NW, TC, true, false><<<grid, NW * 32, smem, st_>>>(a);
+    else k_batch_items<NW, TC, false, false><<<grid, NW * 32, smem, st_>>>(a);
 }
 }  // namespace
 
 // The tensor-core form holds 512 tensor-memory columns per block: it runs only where its
 // shared memory keeps it to one block per SM (0 otherwise, like a shape that does not fit).
-int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial) {
+int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial, bool bec) {
     if (batch_contract_tc(contract) && warps != 8) return 0;
     const size_t smem = batch_item_smem(warps, nph_max, contract);
     int nb;
-    if (warps == 4) nb = virial ? blocks_per_sm_of<4, false, true>(smem) : blocks_per_sm_of<4, false, false>(smem);
+    if (warps == 4) nb = blocks_per_sm_mode<4, false>(smem, virial, bec);
     else if (batch_contract_tc(contract)) {
-        nb = virial ? blocks_per_sm_of<8, true, true>(smem) : blocks_per_sm_of<8, true, false>(smem);
+        nb = blocks_per_sm_mode<8, true>(smem, virial, bec);
         if (nb > 1) nb = 0;
-    } else nb = virial ? blocks_per_sm_of<8, false, true>(smem) : blocks_per_sm_of<8, false, false>(smem);
+    } else nb = blocks_per_sm_mode<8, false>(smem, virial, bec);
     return nb;
 }
 
@@ -2266,17 +2370,9 @@ void launch_batch_items(const BatchArgs& a_in, int warps, int nph_max, int contr
     BatchArgs a = a_in;
     const size_t head = sizeof(double) * ((warps == 4 ? 4 : 8) + NSUMS) * CG + sizeof(float) * 4 * CG;
     a.inv_cap = (int)((smem - head) / sizeof(int));
-    const bool vir = a.virial != nullptr;
-    if (warps == 4) {
-        if (vir) k_batch_items<4, false, true><<<grid, 128, smem, st_>>>(a);
-        else k_batch_items<4, false, false><<<grid, 128, smem, st_>>>(a);
-    } else if (batch_contract_tc(contract)) {
-        if (vir) k_batch_items<8, true, true><<<grid, 256, smem, st_>>>(a);
-        else k_batch_items<8, true, false><<<grid, 256, smem, st_>>>(a);
-    } else {
-        if (vir) k_batch_items<8, false, true><<<grid, 256, smem, st_>>>(a);
-        else k_batch_items<8, false, false><<<grid, 256, smem, st_>>>(a);
-    }
+    if (warps == 4) launch_mode<4, false>(a, grid, smem, st_);
+    else if (batch_contract_tc(contract)) launch_mode<8, true>(a, grid, smem, st_);
+    else launch_mode<8, false>(a, grid, smem, st_);
 }
 
 }  // namespace qnep

@@ -75,6 +75,7 @@ struct BatchScratch {
     float2* sk;      // [nk_max][CG] 4 k_e G(k) S(k) (FP32)
     float2* skp;     // [n_flush][nk_max][CG] FP32 partial structure factors (512-atom blocks)
     double* vir;     // [8][9][CG] per-warp FP64 virial sums of the item (8 warps; NULL without a virial)
+    float4* zsum;    // [nmax][3][CG] BEC accumulators (Z_xx..Z_yx | Z_yy..Z_zy | Z_zz, pad; NULL without BEC)
     size_t stride_A, stride_duq, stride_n, stride_k, stride_p;   // per-slot strides (elements)
 };
 
@@ -121,6 +122,8 @@ struct BatchArgs {
     float* forces;           // [n_cand][N_total][3] or NULL
     float* charges;          // [n_cand][N_total] or NULL
     double* virial;          // [n_cand][n_struct][9] or NULL (W = -dU/d eps, eV)
+    float* bec;              // [n_cand][N_total][9] or NULL (Z_i,ab = dP_a/dr_ib, Eq. bec_2; needs sc.zsum)
+    double* total_charge;    // [n_cand][n_struct] or NULL (sum of q~ before the correction)
     int n_struct;
     int n_total;
     int inv_cap;             // ints of shared memory for the outputs' inverse permutation (set at launch)
@@ -138,7 +141,7 @@ inline int batch_bstride(int n_species) { return MAX_SPECIES * KR + n_species * 
 // contract: BATCH_CONTRACT_FP32 (FP32 FMAs, 4 or 8 warps) or BATCH_CONTRACT_BF16X3 (tensor cores,
 // 8 warps only)
 size_t batch_item_smem(int warps, int nph_max, int contract);
-int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial);
+int batch_item_blocks_per_sm(int warps, int nph_max, int contract, bool virial, bool bec);
 void launch_batch_items(const BatchArgs& a, int warps, int nph_max, int contract, int grid, cudaStream_t st_);
 
 }  // namespace qnep

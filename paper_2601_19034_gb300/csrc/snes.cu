@@ -6,11 +6,12 @@
 //   qnep_batch_loss    D_e, D_f (energy RMSE per atom, force RMSE per component), |z|_1,
 //                      |z|_2^2 and L = l_e D_e + l_f D_f + l_1 |z|_1 + l_2 |z|_2^2 per candidate;
 //                      qnep_batch_loss_v adds D_v (virial RMSE per atom over the six
-//                      independent components) and l_v D_v
+//                      independent components) and l_v D_v; qnep_batch_loss_full adds D_Z (BEC
+//                      RMSE over the structures with reference BEC) and D_Q (RMSE of the total
+//                      charge before the correction) with their weights
 //   qnep_snes_update   rank the losses, rank-based utilities, natural-gradient step on
 //                      (mu, sigma)
-// The batched call feeds energies, forces and virials; its corrected charges meet the
-// total-charge target exactly and it computes no BEC, so the loss has no D_Q and no D_Z.
+// The batched call feeds energies, forces, virials, BEC and the uncorrected total charges.
 //
 // Loss: the force term is the large one (C x N x 3 floats, HBM bound): for every candidate a
 // one-wave set of blocks walks the force stream in 2048-float chunks (coalesced loads, 8 per
@@ -59,19 +60,71 @@ k_snes_sample(long long total, int n_params, const float* __restrict__ mu, const
     }
 }
 
+// BEC terms of the full loss (NULL bec: none)
+struct BecLoss {
+    const float* bec;        // [C][N][9]
+    const float* bec_ref;    // [N][9]
+    const int* has;          // [S] nonzero: the structure has reference BEC
+    int n_zblocks;           // blocks per candidate over the referenced structures
+    const double* qtot;      // [C][S] total charge before the correction, or NULL
+    const double* qtot_ref;  // [S]
+};
+
+// Kahan sum of one thread's squares, the warps' sums in FP32, the block's in FP64, added to *dst
+__device__ __forceinline__ void add_block_squares(float s, float comp, float* redf, double* dst) {
+    float v = s - comp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += (double)redf[w];
+        atomicAdd(dst, t);
+    }
+}
+
 // blockIdx.y = candidate; blockIdx.x < n_fblocks: every n_fblocks-th chunk of the force stream;
-// == n_fblocks: the energy and virial terms and the parameter norms.  terms[ts c + k]: D_e (0),
-// sum of squared force errors (1, rooted by k_loss_finalize), D_v (2, ts = 5 only), |z|_1, |z|_2^2
-// (the last two).
+// then n_zblocks blocks over the BEC of the referenced structures (every n_zblocks-th structure);
+// the last: the energy, virial and total-charge terms and the parameter norms.  terms[ts c + k]:
+// D_e (0), sum of squared force errors (1, rooted by k_loss_finalize), D_v (2, ts >= 5), sum of
+// squared BEC errors (3, ts = 7, rooted by k_loss_finalize), D_Q (4, ts = 7), |z|_1, |z|_2^2 (the
+// last two).
 __global__ void __launch_bounds__(kThreads)
 k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n_fblocks,
              const double* __restrict__ energy, const float* __restrict__ forces,
              const double* __restrict__ energy_ref, const float* __restrict__ forces_ref,
-             const double* __restrict__ virial, const double* __restrict__ virial_ref,
+             const double* __restrict__ virial, const double* __restrict__ virial_ref, BecLoss bz,
              const float* __restrict__ params, int n_params, int ts, double* __restrict__ terms) {
     __shared__ double red[kThreads / 32];
     __shared__ float redf[kThreads / 32];
     const int c = blockIdx.y;
+    if ((int)blockIdx.x >= n_fblocks && (int)blockIdx.x < n_fblocks + bz.n_zblocks) {
+        // BEC: the 9 n_s components of each referenced structure, 8 loads per thread in flight
+        const long long n_z = 3 * n_force;   // 9 N
+        const float* zc = bz.bec + (long long)c * n_z;
+        float s = 0.f, comp = 0.f;
+        for (int st = (int)blockIdx.x - n_fblocks; st < n_struct; st += bz.n_zblocks) {
+            if (!bz.has[st]) continue;
+            const long long lo = 9LL * off[st], hi = 9LL * off[st + 1];
+            for (long long base = lo + threadIdx.x; base < hi; base += kChunk) {
+                float d[kPerThread];
+#pragma unroll
+                for (int k = 0; k < kPerThread; ++k) {
+                    const long long i = base + (long long)k * kThreads;
+                    d[k] = i < hi ? zc[i] - bz.bec_ref[i] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kPerThread; ++k) {
+                    const float y = d[k] * d[k] - comp;
+                    const float t = s + y;
+                    comp = (t - s) - y;
+                    s = t;
+                }
+            }
+        }
+        add_block_squares(s, comp, redf, terms + ts * c + 3);
+        return;
+    }
     if ((int)blockIdx.x < n_fblocks) {
         const float* fc = forces + (long long)c * n_force;
         float s = 0.f, comp = 0.f;                     // Kahan sum of this thread's squares
@@ -91,18 +144,10 @@ k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n
                 s = t;
             }
         }
-        float v = s - comp;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += (double)redf[w];
-            atomicAdd(terms + ts * c + 1, t);
-        }
+        add_block_squares(s, comp, redf, terms + ts * c + 1);
         return;
     }
-    double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0, sv = 0.0;
+    double se = 0.0, cnt = 0.0, l1 = 0.0, l2 = 0.0, sv = 0.0, sq = 0.0;
     for (int s = threadIdx.x; s < n_struct; s += kThreads) {
         const int n_s = off[s + 1] - off[s];
         if (n_s > 0) {
@@ -120,6 +165,10 @@ k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n
                     sv += dv * dv;
                 }
             }
+            if (bz.qtot) {
+                const double dq = bz.qtot[(long long)c * n_struct + s] - bz.qtot_ref[s];
+                sq += dq * dq;
+            }
         }
     }
     if (params)
@@ -133,21 +182,36 @@ k_batch_loss(int n_struct, const int* __restrict__ off, long long n_force, int n
     l1 = block_sum(l1, red);
     l2 = block_sum(l2, red);
     sv = block_sum(sv, red);
+    sq = block_sum(sq, red);
     if (threadIdx.x == 0) {
         terms[ts * c + 0] = cnt > 0.0 ? sqrt(se / cnt) : 0.0;
-        if (ts == 5) terms[ts * c + 2] = (virial && cnt > 0.0) ? sqrt(sv / (6.0 * cnt)) : 0.0;
+        if (ts >= 5) terms[ts * c + 2] = (virial && cnt > 0.0) ? sqrt(sv / (6.0 * cnt)) : 0.0;
+        if (ts == 7) terms[ts * c + 4] = (bz.qtot && cnt > 0.0) ? sqrt(sq / cnt) : 0.0;
         terms[ts * c + ts - 2] = l1;
         terms[ts * c + ts - 1] = l2;
     }
 }
 
-__global__ void k_loss_finalize(int n_cand, long long n_force, double we, double wf, double wv, double w1, double w2,
-                                int ts, double* __restrict__ terms, double* __restrict__ loss) {
+__global__ void k_loss_finalize(int n_cand, long long n_force, double we, double wf, double wv, double wz, double wq,
+                                double w1, double w2, int ts, int n_struct, const int* __restrict__ off,
+                                const int* __restrict__ has, double* __restrict__ terms, double* __restrict__ loss) {
+    __shared__ double red[kThreads / 32];
+    double nz = 0.0;   // atoms of the structures with reference BEC
+    if (has)
+        for (int s = threadIdx.x; s < n_struct; s += blockDim.x)
+            if (has[s]) nz += (double)(off[s + 1] - off[s]);
+    nz = block_sum(nz, red);
     for (int c = threadIdx.x; c < n_cand; c += blockDim.x) {
         double* t = terms + ts * c;
         const double df = n_force > 0 ? sqrt(t[1] / (double)n_force) : 0.0;
         t[1] = df;
-        loss[c] = we * t[0] + wf * df + (ts == 5 ? wv * t[2] : 0.0) + w1 * t[ts - 2] + w2 * t[ts - 1];
+        double l = we * t[0] + wf * df + (ts >= 5 ? wv * t[2] : 0.0) + w1 * t[ts - 2] + w2 * t[ts - 1];
+        if (ts == 7) {
+            const double dz = nz > 0.0 ? sqrt(t[3] / (9.0 * nz)) : 0.0;
+            t[3] = dz;
+            l += wz * dz + wq * t[4];
+        }
+        loss[c] = l;
     }
 }
 
@@ -221,14 +285,16 @@ qnep_status batch_loss_impl(int n_candidates, int n_struct, const int* atom_offs
                             const double* energy, const float* forces, const double* virial,
                             const double* energy_ref, const float* forces_ref, const double* virial_ref,
                             const float* params, int n_params, double we, double wf, double wv, double w1, double w2,
-                            int ts, double* loss, double* terms, void* stream) {
+                            int ts, double* loss, double* terms, void* stream, BecLoss bz = BecLoss{},
+                            double wz = 0.0, double wq = 0.0) {
     if (n_candidates < 1 || n_candidates > 65535 || n_struct < 1 || n_total < 0 || !atom_offsets || !energy ||
         !energy_ref || !loss || !terms)
         return QNEP_ERR_ARG;
     if ((forces == nullptr) != (forces_ref == nullptr)) return QNEP_ERR_ARG;
     if ((virial == nullptr) != (virial_ref == nullptr)) return QNEP_ERR_ARG;
     if (params && n_params < 1) return QNEP_ERR_ARG;
-    if (!std::isfinite(we) || !std::isfinite(wf) || !std::isfinite(wv) || !std::isfinite(w1) || !std::isfinite(w2))
+    if (!std::isfinite(we) || !std::isfinite(wf) || !std::isfinite(wv) || !std::isfinite(w1) || !std::isfinite(w2) ||
+        !std::isfinite(wz) || !std::isfinite(wq))
         return QNEP_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long n_force = forces ? 3LL * n_total : 0;
@@ -238,13 +304,16 @@ qnep_status batch_loss_impl(int n_candidates, int n_struct, const int* atom_offs
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long per_cand = ((long long)(sms > 0 ? sms : 152) * 8 + n_candidates - 1) / n_candidates;
     const int n_fblocks = (int)(chunks < per_cand ? chunks : per_cand);
+    bz.n_zblocks = bz.bec ? (int)(n_struct < per_cand ? n_struct : per_cand) : 0;
     if (cudaMemsetAsync(terms, 0, sizeof(double) * ts * (size_t)n_candidates, st) != cudaSuccess)
         return QNEP_ERR_CUDA;
-    dim3 grid((unsigned)(n_fblocks + 1), (unsigned)n_candidates);
-    k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, n_force, n_fblocks, energy, forces, energy_ref,
-                                            forces_ref, virial, virial_ref, params, params ? n_params : 0, ts, terms);
+    dim3 grid((unsigned)(n_fblocks + bz.n_zblocks + 1), (unsigned)n_candidates);
+    k_batch_loss<<<grid, kThreads, 0, st>>>(n_struct, atom_offsets, 3LL * n_total, n_fblocks, energy, forces,
+                                            energy_ref, forces_ref, virial, virial_ref, bz, params,
+                                            params ? n_params : 0, ts, terms);
     if (cudaGetLastError() != cudaSuccess) return QNEP_ERR_CUDA;
-    k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, we, wf, wv, w1, w2, ts, terms, loss);
+    k_loss_finalize<<<1, kThreads, 0, st>>>(n_candidates, n_force, we, wf, wv, wz, wq, w1, w2, ts, n_struct,
+                                            atom_offsets, bz.bec ? bz.has : nullptr, terms, loss);
     return cudaGetLastError() == cudaSuccess ? QNEP_OK : QNEP_ERR_CUDA;
 }
 }  // namespace
@@ -268,6 +337,20 @@ extern "C" qnep_status qnep_batch_loss_v(int n_candidates, int n_struct, const i
     return batch_loss_impl(n_candidates, n_struct, atom_offsets, n_total, energy, forces, virial, energy_ref,
                            forces_ref, virial_ref, params, n_params, w->energy, w->force, w->virial, w->l1, w->l2, 5,
                            loss, terms, stream);
+}
+
+extern "C" qnep_status qnep_batch_loss_full(int n_candidates, int n_struct, const int* atom_offsets, int n_total,
+                                           const qnep_loss_inputs* in, const qnep_loss_inputs* ref,
+                                           const int* bec_has_ref, const float* params, int n_params,
+                                           const qnep_loss_weights_full* w, double* loss, double* terms,
+                                           void* stream) {
+    if (!w || !in || !ref) return QNEP_ERR_ARG;
+    if ((in->bec == nullptr) != (ref->bec == nullptr) || (in->bec && !bec_has_ref)) return QNEP_ERR_ARG;
+    if ((in->total_charge == nullptr) != (ref->total_charge == nullptr)) return QNEP_ERR_ARG;
+    BecLoss bz{in->bec, ref->bec, bec_has_ref, 0, in->total_charge, ref->total_charge};
+    return batch_loss_impl(n_candidates, n_struct, atom_offsets, n_total, in->energy, in->forces, in->virial,
+                           ref->energy, ref->forces, ref->virial, params, n_params, w->energy, w->force, w->virial,
+                           w->l1, w->l2, 7, loss, terms, stream, bz, w->bec, w->charge);
 }
 
 extern "C" qnep_status qnep_snes_update(int n_candidates, int n_params, const double* loss, const float* noise,

@@ -428,7 +428,8 @@ class QNEPBatch:
         self._desc = (off, bx)   # kept alive: the library reads them on every call
         return off, bx
 
-    def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True, virial=False) -> dict:
+    def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True, virial=False, bec=False,
+                total_charge=False) -> dict:
         out = {"energy": torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)}
         if forces:
             out["forces"] = torch.empty(self.n_cand, n_total, 3, dtype=torch.float32, device=device)
@@ -436,6 +437,10 @@ class QNEPBatch:
             out["charges"] = torch.empty(self.n_cand, n_total, dtype=torch.float32, device=device)
         if virial:
             out["virial"] = torch.empty(self.n_cand, n_struct, 3, 3, dtype=torch.float64, device=device)
+        if bec:
+            out["bec"] = torch.empty(self.n_cand, n_total, 3, 3, dtype=torch.float32, device=device)
+        if total_charge:
+            out["total_charge"] = torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)
         return out
 
     @staticmethod
@@ -445,7 +450,8 @@ class QNEPBatch:
             if t is None:
                 return None
             return t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data
-        return _lib.BatchOutputsC(ptr("energy"), ptr("forces"), ptr("charges"), ptr("virial"))
+        return _lib.BatchOutputsC(ptr("energy"), ptr("forces"), ptr("charges"), ptr("virial"), ptr("bec"),
+                                  ptr("total_charge"))
 
     def _args(self, positions, types, offsets, boxes, out, stream):
         assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
@@ -463,7 +469,7 @@ class QNEPBatch:
 
     def compute_into(self, positions, types, offsets, boxes, out: dict, stream=None):
         """Enqueue one batched call writing into ``out`` (from ``outputs``); no synchronisation."""
-        if "virial" in out:
+        if "virial" in out or "bec" in out or "total_charge" in out:
             args = self._args(positions, types, offsets, boxes, out, stream)
             oc = self._outputs_c(out)
             _lib.check(self.lib.qnep_batch_compute_outputs(*args[:7], ctypes.byref(oc)), batch=self.handle)
@@ -474,7 +480,8 @@ class QNEPBatch:
     def compute_host(self, positions, types, offsets, boxes, out: dict, stream=None):
         """End-to-end call on host buffers: positions [N, 3] float32 and types [N] int32 (numpy
         arrays or pinned CPU tensors) in, every array of ``out`` (host energy [C, S] float64,
-        optional forces [C, N, 3], charges [C, N], virial [C, S, 3, 3]) filled, synchronised."""
+        optional forces [C, N, 3], charges [C, N], virial [C, S, 3, 3], bec [C, N, 3, 3] float32,
+        total_charge [C, S] float64) filled, synchronised."""
         off, bx = self._describe(offsets, boxes)
 
         def hptr(a):
@@ -496,10 +503,10 @@ class QNEPBatch:
         return self.lib.qnep_batch_sync_status(self.handle)
 
     def compute(self, positions, types, offsets, boxes, retries: int = 3, forces=True, charges=True,
-                virial=False) -> dict:
+                virial=False, bec=False, total_charge=False) -> dict:
         """Batched call with a status check; grows the neighbour lists and retries on overflow."""
         n_struct = len(offsets) - 1
-        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges, virial)
+        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges, virial, bec, total_charge)
         for _ in range(retries + 1):
             self.compute_into(positions, types, offsets, boxes, out)
             st = self.sync_status()
@@ -663,4 +670,39 @@ def batch_loss_v(energy, forces, virial, energy_ref, forces_ref, virial_ref, ato
                                              ptr(virial), energy_ref.data_ptr(), ptr(forces_ref), ptr(virial_ref),
                                              ptr(params), n_par, ctypes.byref(w), loss.data_ptr(), terms.data_ptr(),
                                              _stream(energy, stream)))
+    return loss, terms
+
+
+def batch_loss_full(outputs: dict, refs: dict, atom_offsets, bec_has_ref=None, params=None,
+                    weights=(1.0, 1.0, 1.0, 1.0, 1.0, 0.0, 0.0), loss: torch.Tensor = None,
+                    terms: torch.Tensor = None, stream=None):
+    """Per-candidate loss L [C] and terms [C, 7] = (D_e, D_f, D_v, D_Z, D_Q, |z|_1, |z|_2^2) on the device.
+
+    ``outputs``: the batched call's device tensors by name (energy [C, S] required; forces, virial,
+    bec, total_charge optional); ``refs``: the references by the same names without the candidate
+    axis.  An output and its reference come together; ``bec_has_ref`` (device int32 [S]) marks the
+    structures with reference BEC.  ``weights`` = (l_e, l_f, l_v, l_Z, l_Q, l_1, l_2).
+    """
+    energy = outputs["energy"]
+    c, s = energy.shape
+    dev = energy.device
+    n_total = int(atom_offsets[-1].item()) if isinstance(atom_offsets, torch.Tensor) else int(atom_offsets[-1])
+    if loss is None:
+        loss = torch.empty(c, dtype=torch.float64, device=dev)
+    if terms is None:
+        terms = torch.empty(c, 7, dtype=torch.float64, device=dev)
+    assert atom_offsets.is_cuda and atom_offsets.dtype == torch.int32 and atom_offsets.numel() == s + 1
+
+    def ptr(t):
+        return t.data_ptr() if t is not None else None
+
+    names = ("energy", "forces", "virial", "bec", "total_charge")
+    inp = _lib.LossInputsC(*[ptr(outputs.get(k)) for k in names])
+    ref = _lib.LossInputsC(*[ptr(refs.get(k)) for k in names])
+    w = _lib.LossWeightsFullC(*[float(x) for x in weights])
+    n_par = int(params.shape[1]) if params is not None else 0
+    _lib.check(_lib.load().qnep_batch_loss_full(c, s, atom_offsets.data_ptr(), n_total, ctypes.byref(inp),
+                                                ctypes.byref(ref), ptr(bec_has_ref), ptr(params), n_par,
+                                                ctypes.byref(w), loss.data_ptr(), terms.data_ptr(),
+                                                _stream(energy, stream)))
     return loss, terms

@@ -56,6 +56,29 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.ElecC) == 56
     assert ctypes.sizeof(_lib.HParamsC) == 40
     assert ctypes.sizeof(_lib.OutputsC) == 72
+    assert ctypes.sizeof(_lib.BatchOutputsC) == 48      # six pointers
+    assert ctypes.sizeof(_lib.LossInputsC) == 40        # five pointers
+    assert ctypes.sizeof(_lib.LossWeightsFullC) == 56   # seven doubles
+
+
+def test_full_loss_rejects_unpaired_buffers_before_any_gpu_work(lib):
+    """qnep_batch_loss_full: each output comes with its reference, BEC with its structure mask."""
+    dummy = ctypes.c_void_p(0x1000)       # never dereferenced: every call below returns before using it
+    fn = lib.qnep_batch_loss_full
+    w = _lib.LossWeightsFullC(1, 1, 1, 1, 1, 0, 0)
+    full = _lib.LossInputsC(dummy, dummy, dummy, dummy, dummy)
+    for k in ("forces", "virial", "bec", "total_charge"):
+        half = _lib.LossInputsC(dummy, dummy, dummy, dummy, dummy)
+        setattr(half, k, None)
+        assert fn(2, 1, dummy, 4, full, half, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG, k
+        assert fn(2, 1, dummy, 4, half, full, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG, k
+    assert fn(2, 1, dummy, 4, full, full, None, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG   # no mask
+    no_energy = _lib.LossInputsC(None, dummy, dummy, dummy, dummy)
+    assert fn(2, 1, dummy, 4, no_energy, full, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    bad = _lib.LossWeightsFullC(1, 1, 1, float("nan"), 1, 0, 0)
+    assert fn(2, 1, dummy, 4, full, full, dummy, None, 0, bad, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert fn(0, 1, dummy, 4, full, full, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
+    assert fn(2, 1, dummy, 4, None, full, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
 
 
 def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
