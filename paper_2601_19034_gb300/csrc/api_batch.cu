@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <map>
 #include <string>
 #include <tuple>
@@ -144,7 +145,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     std::vector<int4> chunks;
     std::vector<int> kreal;
     std::vector<float4> kvec;
-    std::map<std::tuple<double, double, double>, int> tab_of;
+    std::map<std::array<double, 9>, int> tab_of;
     std::vector<int> nk_of;   // padded k count per table
     int cell_total = 0, nmax = 0, nph_max = 0, nk_max = 0;
     double dens_max = 0.0;
@@ -153,9 +154,28 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         const double* bx = boxes + 9 * (size_t)s;
         for (int k = 0; k < 9; ++k)
             if (!std::isfinite(bx[k])) return failb(b, QNEP_ERR_ARG, "box has a non-finite entry");
-        if (bx[1] != 0 || bx[2] != 0 || bx[3] != 0 || bx[5] != 0 || bx[6] != 0 || bx[7] != 0)
-            return failb(b, QNEP_ERR_UNSUPPORTED, "only orthorhombic boxes are supported");
-        const double L[3] = {bx[0], bx[4], bx[8]};
+        // orthorhombic, or a general cell in the restricted form a = (a_x, 0, 0), b = (b_x, b_y, 0),
+        // c = (c_x, c_y, c_z) with a_x, b_y, c_z > 0 (every cell can be rotated into it): its H and
+        // H^-1 are lower triangular, so the x and y components of k = 2 pi H^-1 n depend on (n1, n2)
+        // only, as the k-space field pass assumes for a column of wave vectors
+        const bool tri = bx[3] != 0 || bx[6] != 0 || bx[7] != 0 || bx[1] != 0 || bx[2] != 0 || bx[5] != 0;
+        if (tri && (bx[1] != 0 || bx[2] != 0 || bx[5] != 0))
+            return failb(b, QNEP_ERR_UNSUPPORTED,
+                         "general cells must have a along x and b in the xy plane (rotate the cell)");
+        if (tri && !(bx[0] > 0 && bx[4] > 0 && bx[8] > 0))
+            return failb(b, QNEP_ERR_ARG, "the cell vectors must be right-handed (a_x, b_y, c_z > 0)");
+        double hinv[9];
+        const double det = invert3(bx, hinv);
+        double L[3], width[3];
+        for (int d = 0; d < 3; ++d) {
+            const double* av = bx + 3 * d;
+            L[d] = tri ? std::sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]) : bx[4 * d];
+            // perpendicular width V / |a_e x a_f| (the cell grid needs width >= cutoff); the edge if orthorhombic
+            const double* e = bx + 3 * ((d + 1) % 3);
+            const double* f = bx + 3 * ((d + 2) % 3);
+            const double cx = e[1] * f[2] - e[2] * f[1], cy = e[2] * f[0] - e[0] * f[2], cz = e[0] * f[1] - e[1] * f[0];
+            width[d] = tri ? det / std::sqrt(cx * cx + cy * cy + cz * cz) : L[d];
+        }
         BatchStruct& t = sts[s];
         t.atom_off = off[s];
         t.n = off[s + 1] - off[s];
@@ -163,14 +183,18 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         if (t.n > 32768) return failb(b, QNEP_ERR_UNSUPPORTED, "batched structures hold at most 32768 atoms");
         nmax = std::max(nmax, t.n);
         Geom& g = t.g;
-        g.tri = 0;
+        g.tri = tri ? 1 : 0;
+        for (int k = 0; k < 9; ++k) {
+            g.H[k] = (float)bx[k];
+            g.Hi[k] = (float)hinv[k];
+        }
         g.ncells = 1;
         for (int d = 0; d < 3; ++d) {
             if (!(L[d] > 0)) return failb(b, QNEP_ERR_ARG, "box edge must be positive");
-            if (L[d] < rcl) return failb(b, QNEP_ERR_UNSUPPORTED, "box edge shorter than the list cutoff");
+            if (width[d] < rcl) return failb(b, QNEP_ERR_UNSUPPORTED, "cell width shorter than the list cutoff");
             g.L[d] = (float)L[d];
             g.invL[d] = (float)(1.0 / L[d]);
-            int nc = (int)std::floor(L[d] / rcl);
+            int nc = (int)std::floor(width[d] / rcl);
             g.nc[d] = std::min(std::max(nc, 1), 8);
             g.ncells *= g.nc[d];
         }
@@ -181,11 +205,12 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         g.list_sa = g.list_se = g.ang_sa = g.ang_se = 0;
         t.cell_off = cell_total;
         cell_total += g.ncells + 1;
-        dens_max = std::max(dens_max, t.n / (L[0] * L[1] * L[2]));
-        auto key = std::make_tuple(L[0], L[1], L[2]);
+        dens_max = std::max(dens_max, t.n / std::fabs(det));
+        std::array<double, 9> key;
+        for (int k = 0; k < 9; ++k) key[k] = bx[k];
         auto it = tab_of.find(key);
         if (it == tab_of.end()) {
-            KSet ks = build_kset(L, b->es.kmax, b->es.alpha);
+            KSet ks = tri ? build_kset_box(bx, b->es.kmax, b->es.alpha) : build_kset(L, b->es.kmax, b->es.alpha);
             BatchKTab kt{};
             kt.n1max = ks.nmax[0];
             kt.n2max = ks.nmax[1];
@@ -202,6 +227,11 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
                 kt.invl_hi[d] = (float)il;
                 kt.invl_lo[d] = (float)(il - (double)kt.invl_hi[d]);
             }
+            kt.tri = tri ? 1 : 0;
+            for (int k = 0; k < 9; ++k) {
+                kt.hi_hi[k] = (float)hinv[k];
+                kt.hi_lo[k] = (float)(hinv[k] - (double)kt.hi_hi[k]);
+            }
             kt.kreal_off = (int)kreal.size();
             for (int h = 0; h < kt.nchunk; ++h) {
                 const int4& c = ks.cols[ks.chunk_col[h]];
@@ -215,8 +245,16 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
                 chunks.push_back(make_int4(c.x, c.y, n3, cnt));
                 for (int q = 0; q < 8; ++q) {
                     const float gk = ks.kg[8 * h + q];
-                    kvec.push_back(make_float4((float)(two_pi * c.x / L[0]), (float)(two_pi * c.y / L[1]),
-                                               (float)(two_pi * (n3 + q) / L[2]), (float)(4.0 * ke * gk)));
+                    if (tri) {   // k_d = 2 pi sum_c H^-1[d][c] n_c
+                        const double nv[3] = {(double)c.x, (double)c.y, (double)(n3 + q)};
+                        double kd[3];
+                        for (int d = 0; d < 3; ++d)
+                            kd[d] = two_pi * (hinv[3 * d] * nv[0] + hinv[3 * d + 1] * nv[1] + hinv[3 * d + 2] * nv[2]);
+                        kvec.push_back(make_float4((float)kd[0], (float)kd[1], (float)kd[2], (float)(4.0 * ke * gk)));
+                    } else {
+                        kvec.push_back(make_float4((float)(two_pi * c.x / L[0]), (float)(two_pi * c.y / L[1]),
+                                                   (float)(two_pi * (n3 + q) / L[2]), (float)(4.0 * ke * gk)));
+                    }
                 }
             }
             kt.nkr = (int)kreal.size() - kt.kreal_off;

@@ -77,6 +77,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 __device__ __forceinline__ float2 batch_phase(const float4& p, int e, const BatchKTab& kt) {
+    if (kt.tri) {
+        if (e < kt.yoff) return phase_factor_frac(p, e, 0, kt.hi_hi, kt.hi_lo);
+        if (e < kt.zoff) return phase_factor_frac(p, e - kt.yoff - kt.n2max, 1, kt.hi_hi, kt.hi_lo);
+        return phase_factor_frac(p, e - kt.zoff - kt.n3max, 2, kt.hi_hi, kt.hi_lo);
+    }
     if (e < kt.yoff) return phase_factor(p.x, e, kt.invl_hi[0], kt.invl_lo[0]);
     if (e < kt.zoff) return phase_factor(p.y, e - kt.yoff - kt.n2max, kt.invl_hi[1], kt.invl_lo[1]);
     return phase_factor(p.z, e - kt.zoff - kt.n3max, kt.invl_hi[2], kt.invl_lo[2]);
@@ -123,10 +128,17 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __rest
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int cc[3];
-        for (int d = 0; d < 3; ++d) {
-            float y = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
-            int c = (int)(y * g.invL[d] * (float)g.nc[d]);
-            cc[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+        if (g.tri) {   // cells along the fractional axes; the position wrapped by lattice translations
+            const float x[3] = {pos[3 * (size_t)(off + i)], pos[3 * (size_t)(off + i) + 1],
+                                pos[3 * (size_t)(off + i) + 2]};
+            float w[3];
+            wrap_and_cell(g, x, w, cc);
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                float y = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
+                int c = (int)(y * g.invL[d] * (float)g.nc[d]);
+                cc[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+            }
         }
         const int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
         cell_of[i] = c;
@@ -164,7 +176,14 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __rest
             if (in) {
                 const int slot = base + __popc(mk & below);
                 float w[3];
-                for (int d = 0; d < 3; ++d) w[d] = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
+                if (g.tri) {
+                    const float x[3] = {pos[3 * (size_t)(off + i)], pos[3 * (size_t)(off + i) + 1],
+                                        pos[3 * (size_t)(off + i) + 2]};
+                    int cd[3];
+                    wrap_and_cell(g, x, w, cd);
+                } else {
+                    for (int d = 0; d < 3; ++d) w[d] = wrap_coord(pos[3 * (size_t)(off + i) + d], g.L[d], g.invL[d]);
+                }
                 spos4[off + slot] = make_float4(w[0], w[1], w[2],
                                                 __int_as_float(species_of(types, off + i, n_species, nullptr)));
                 sidx[off + slot] = i;

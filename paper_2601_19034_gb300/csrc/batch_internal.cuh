@@ -61,6 +61,10 @@ struct BatchKTab {
     int nkr;         // wave vectors of the half space (the chunks' non-padding entries)
     int kreal_off;   // their padded indices: kreal[kreal_off .. kreal_off + nkr)
     float invl_hi[3], invl_lo[3];
+    int tri;         // 1: a general cell in the restricted form (a along x, b in the xy plane):
+                     // phases of the fractional coordinates s = r H^-1, k = 2 pi H^-1 n, whose x and
+                     // y components depend on (n1, n2) only (H^-1 is lower triangular as H is)
+    float hi_hi[9], hi_lo[9];   // H^-1 (row-major) as float pairs
 };
 
 // Per-slot scratch (one slot per resident block), in floats, for nmax atoms.

@@ -158,16 +158,17 @@ __device__ __forceinline__ float2 phase_factor(float x, int nn, float il_hi, flo
     return make_float2(cs, -sn);
 }
 
-// exp(-i 2 pi nn s_c) of a general cell, s_c = sum_d r_d Hi[d][c]: each of the three products
-// nn r_d Hi[d][c] is reduced to its fractional part exactly (as in phase_factor), then the three
-// fractions are added
-__device__ __forceinline__ float2 phase_factor_tri(const float4& p, int nn, int c, const EwaldTab& tab) {
+// exp(-i 2 pi nn s_c) of a general cell, s_c = sum_d r_d Hi[d][c] (H^-1 as float pairs hi_hi +
+// hi_lo, row-major): each of the three products nn r_d Hi[d][c] is reduced to its fractional part
+// exactly (as in phase_factor), then the three fractions are added
+__device__ __forceinline__ float2 phase_factor_frac(const float4& p, int nn, int c, const float* hi_hi,
+                                                    const float* hi_lo) {
     const float fn = (float)nn;
     const float r[3] = {p.x, p.y, p.z};
     float fr = 0.f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const float h = tab.hi_hi[3 * d + c], hl = tab.hi_lo[3 * d + c];
+        const float h = hi_hi[3 * d + c], hl = hi_lo[3 * d + c];
         const float pp = fn * r[d];
         const float pe = fmaf(fn, r[d], -pp);
         const float u = pp * h;
@@ -178,6 +179,10 @@ __device__ __forceinline__ float2 phase_factor_tri(const float4& p, int nn, int 
     float sn, cs;
     sincospif(2.f * fr, &sn, &cs);
     return make_float2(cs, -sn);
+}
+
+__device__ __forceinline__ float2 phase_factor_tri(const float4& p, int nn, int c, const EwaldTab& tab) {
+    return phase_factor_frac(p, nn, c, tab.hi_hi, tab.hi_lo);
 }
 
 // Row entry e of an atom's phase row: X(n1), Y(n2) or Z(n3) factor (see EwaldTab).
