@@ -89,19 +89,23 @@ def kspace_static_ewald(pos, box, q, alpha, kmax, chunk: int = 2048):
 
 
 def kspace_static_pppm(pos, box, q, mesh, order, alpha, chunk: int = 65536):
-    """Per-atom static mesh virial [N, 3, 3] from the six inverse FFTs of G_opt B_ab S."""
+    """Per-atom static mesh virial [N, 3, 3] from the six inverse FFTs of G_opt B_ab S (a general
+    cell: the fractional mesh and k = 2 pi H^-1 n of the PPPM module)."""
     pos = np.asarray(pos, np.float64)
     q = np.asarray(q, np.float64)
-    lengths = np.diag(np.asarray(box, np.float64)).copy()
+    box = np.asarray(box, np.float64)
+    general = bool(np.count_nonzero(box - np.diag(np.diag(box))))
+    hinv = np.linalg.inv(box) if general else None
+    lengths = np.linalg.norm(box, axis=1) if general else np.diag(box).copy()
     mesh = tuple(int(m) for m in mesh)
     ntot = int(np.prod(mesh))
     rho = np.zeros(ntot)
     for a0 in range(0, len(pos), chunk):
-        pts, wt_ = pppm._gather_weights(pos[a0:a0 + chunk], lengths, mesh, order)
+        pts, wt_ = pppm._gather_weights(pos[a0:a0 + chunk], lengths, mesh, order, hinv)
         flat, wt = pppm._flat_stencil(pts, wt_, mesh)
         np.add.at(rho, flat.ravel(), (wt * q[a0:a0 + chunk, None]).ravel())
     s = np.fft.fftn(rho.reshape(mesh))
-    gopt, k, k2, _ = pppm.influence(lengths, mesh, order, alpha)
+    gopt, k, k2 = pppm.influence(lengths, mesh, order, alpha, box=box if general else None)[:3]
     with np.errstate(divide="ignore", invalid="ignore"):
         fac = np.where(k2 > 0, 2.0 / (4 * alpha * alpha) + 2.0 / k2, 0.0)
     w = np.zeros((len(pos), 3, 3))
@@ -110,7 +114,7 @@ def kspace_static_pppm(pos, box, q, mesh, order, alpha, chunk: int = 65536):
             bab = (1.0 if a == b else 0.0) - fac * k[a] * k[b]
             field = (np.fft.ifftn(gopt * bab * s) * ntot).real.ravel()
             for a0 in range(0, len(pos), chunk):
-                pts, wt_ = pppm._gather_weights(pos[a0:a0 + chunk], lengths, mesh, order)
+                pts, wt_ = pppm._gather_weights(pos[a0:a0 + chunk], lengths, mesh, order, hinv)
                 flat, wt = pppm._flat_stencil(pts, wt_, mesh)
                 val = KE * q[a0:a0 + chunk] * (wt * field[flat]).sum(1)
                 w[a0:a0 + chunk, a, b] = val

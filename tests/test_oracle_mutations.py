@@ -296,3 +296,35 @@ def test_total_charge_after_the_correction(monkeypatch):
         return out
     monkeypatch.setattr(forcecall, "force_call", wrong)
     _fails(t_tr.test_force_call_total_charge_before_the_correction)
+
+
+def test_general_cell_pppm_gradient_with_h_inverse_transposed(monkeypatch):
+    """Mapping the fractional gradients with H^-1 instead of H^-T fails the PPPM -> Ewald pin."""
+    from tests import test_oracle_triclinic as t_tri
+    orig = np.linalg.inv
+
+    def general(pos, box, q, mesh, order, alpha, printed_form=False, chunk=65536):
+        # the module's code with the transposed map: d/dr = gf @ H^-1
+        pos = np.asarray(pos, np.float64)
+        q = np.asarray(q, np.float64)
+        hinv = orig(np.asarray(box, np.float64))
+        out = pppm_general_orig(pos, box, q, mesh, order, alpha, printed_form, chunk)
+        lengths = np.linalg.norm(box, axis=1)
+        mesh_t = tuple(int(m) for m in mesh)
+        ntot = int(np.prod(mesh_t))
+        s = np.fft.fftn(out["rho"])
+        gopt, k, k2, nyq, n = pppm.influence(lengths, mesh_t, order, alpha, printed_form, box=box)
+        sg = s * gopt
+        ff = []
+        for c in range(3):
+            comp = 1j * (2.0 * math.pi * n[c]) * sg
+            comp[nyq[c]] = 0.0
+            ff.append((np.fft.ifftn(comp) * ntot).real.ravel())
+        pts, w = pppm._gather_weights(pos, lengths, mesh_t, order, hinv)
+        flat, wt = pppm._flat_stencil(pts, w, mesh_t)
+        gf = np.stack([(wt * ff[c][flat]).sum(1) for c in range(3)], -1)
+        out["force"] = -2.0 * pppm.KE * q[:, None] * (gf @ hinv)
+        return out
+    pppm_general_orig = pppm.pppm_general
+    monkeypatch.setattr(pppm, "pppm_general", general)
+    _fails(t_tri.test_pppm_in_a_general_cell_converges_to_ewald)
