@@ -140,11 +140,13 @@ qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]);
 /* One force call on one structure with candidate 0.
  *   positions: device [N][3] float32 (A); may lie outside the box (wrapped internally)
  *   types:     device [N] int32 species index in [0, n_species)
- *   box:       host double[9], rows = lattice vectors a, b, c (right-handed); a general
- *              (triclinic) cell with Ewald electrostatics or none, orthorhombic with PPPM
- *              (QNEP_ERR_UNSUPPORTED otherwise); every perpendicular width V / |a_e x a_f| >= the
- *              list cutoff.  In a general cell the images are integer combinations of the rows
- *              and the Ewald wave vectors are k = 2 pi H^-1 n (Sec. II.B).
+ *   box:       host double[9], rows = lattice vectors a, b, c (right-handed); orthorhombic or a
+ *              general (triclinic) cell, with Ewald, PPPM or no electrostatics; every
+ *              perpendicular width V / |a_e x a_f| >= the list cutoff.  In a general cell the
+ *              images are integer combinations of the rows and the wave vectors are
+ *              k = 2 pi H^-1 n (Sec. II.B); PPPM puts its mesh along the lattice vectors (an
+ *              atom's mesh coordinates N_d (r H^-1)_d) and takes the three field components as
+ *              fractional gradients mapped to Cartesian ones by H^-1 at the interpolation.
  *   stream:    cudaStream_t (NULL = legacy default stream)
  * Asynchronous: returns after enqueueing.  Device-side errors (neighbour
  * overflow) are recorded in scalars[QNEP_S_STATUS] and returned by the next
@@ -339,8 +341,12 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  *   atom_offsets: host [n_struct + 1], atom_offsets[0] = 0, non-decreasing;
  *                 structure s holds atoms atom_offsets[s] .. atom_offsets[s+1]-1
  *   positions:    device [N_total][3] float32 (A), types: device [N_total] int32
- *   boxes:        host [n_struct][9] doubles, orthorhombic, every edge >= the
- *                 neighbour-list cutoff; at most 32768 atoms per structure
+ *   boxes:        host [n_struct][9] doubles, rows = lattice vectors: orthorhombic, or a general
+ *                 cell in the restricted form a = (a_x, 0, 0), b = (b_x, b_y, 0),
+ *                 c = (c_x, c_y, c_z), a_x, b_y, c_z > 0 (every cell can be rotated into it;
+ *                 QNEP_ERR_UNSUPPORTED for other general cells, QNEP_ERR_ARG for a left-handed
+ *                 one); every perpendicular width >= the neighbour-list cutoff; at most 32768
+ *                 atoms per structure
  *   energy:       device [n_candidates][n_struct] doubles (eV)
  *   forces:       device [n_candidates][N_total][3] float32 (eV/A), or NULL
  *   charges:      device [n_candidates][N_total] float32 (e), or NULL

@@ -254,7 +254,7 @@ qnep_status build_ewald_table(qnep_model* m, const double L[3], const double* bo
 }
 
 // PPPM meshes, cuFFT plans (once) and the influence function (every new box).
-qnep_status setup_pppm(qnep_model* m, const double L[3], cudaStream_t st) {
+qnep_status setup_pppm(qnep_model* m, const double L[3], const double box[9], bool tri, cudaStream_t st) {
     PppmTab& pm = m->pm;
     if (!m->have_mesh) {
         pm.nx = m->es.mesh[0];
@@ -283,7 +283,22 @@ qnep_status setup_pppm(qnep_model* m, const double L[3], cudaStream_t st) {
         pm.inv_h[d] = (float)(nd / L[d]);
         pm.inv_h_lo[d] = (float)(nd / L[d] - (double)pm.inv_h[d]);
     }
-    launch_pppm_gopt(pm, m->es.alpha, L[0] * L[1] * L[2], st);
+    // general cells: mesh along the lattice vectors (mesh coordinates N_d (r H^-1)_d), k = 2 pi H^-1 n
+    double hinv[9];
+    const double det = invert3(box, hinv);
+    pm.tri = tri ? 1 : 0;
+    for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+            const int nd = d == 0 ? pm.nx : (d == 1 ? pm.ny : pm.nz);
+            const double v = nd * hinv[3 * c + d];
+            pm.nh_hi[3 * c + d] = (float)v;
+            pm.nh_lo[3 * c + d] = (float)(v - (double)pm.nh_hi[3 * c + d]);
+        }
+    for (int k = 0; k < 9; ++k) {
+        pm.hi[k] = (float)hinv[k];
+        pm.hid[k] = hinv[k];
+    }
+    launch_pppm_gopt(pm, m->es.alpha, tri ? std::fabs(det) : L[0] * L[1] * L[2], st);
     CK(cudaStreamSynchronize(st));
     return QNEP_OK;
 }
@@ -293,8 +308,6 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(box[k])) return fail(m, QNEP_ERR_ARG, "box has a non-finite entry");
     const bool tri = box[1] != 0 || box[2] != 0 || box[3] != 0 || box[5] != 0 || box[6] != 0 || box[7] != 0;
-    if (tri && m->es.mode != 0 && m->es.kind == QNEP_PPPM)
-        return fail(m, QNEP_ERR_UNSUPPORTED, "PPPM runs on orthorhombic boxes only (Ewald takes general cells)");
     // edge lengths and the perpendicular widths V / |a_e x a_f| (the cell grid needs width >= cutoff)
     double L[3], width[3], hinv[9];
     const double det = invert3(box, hinv);
@@ -352,14 +365,14 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             }
         }
         if (m->es.mode != 0 && m->es.kind == QNEP_PPPM) {
-            qnep_status s = setup_pppm(m, L, st);
+            qnep_status s = setup_pppm(m, L, box, tri, st);
             if (s != QNEP_OK) return s;
         }
         std::memcpy(m->box, box, sizeof(double) * 9);
         m->have_box = true;
     }
     // neighbour capacities from the mean density (2x the mean count + margin)
-    const double vol = L[0] * L[1] * L[2];
+    const double vol = tri ? std::fabs(det) : L[0] * L[1] * L[2];
     const double dens = n / vol;
     const double pi43 = 4.18879020478639;
     int cl = m->cap_list, ca = m->cap_ang;

@@ -14,6 +14,11 @@
 //                unnormalised inverse transforms (cuFFT C2R, batch of 4)
 //   gather       phi^k_i = 2 k_e sum_s W phi_s,  F^k_i / q_i = -2 k_e sum_s W E_s  (ik differentiation,
 //                Eq. force-static-fft; the potential is the factor of Eq. force-dynamic-fft)
+// General cells (rows of H the lattice vectors): the mesh lies along the lattice vectors, an
+// atom's mesh coordinates are N_d times its fractional coordinates r H^-1, k = 2 pi H^-1 n with
+// V = det H in G(k) (the alias sums depend on n_d / N_d only), and the three fields are the
+// fractional gradients F^-1[i 2 pi n_c S G_opt] (each zero on the Nyquist plane of n_c), mapped
+// at the gather to d/dr_a = sum_c H^-1[a][c] d/ds_c; a diagonal H gives the ik form above.
 #include <cufft.h>
 
 #include <algorithm>
@@ -51,6 +56,42 @@ __device__ __forceinline__ void stencil_axis(float x, float inv_h, float inv_h_l
     s0 = (int)r - 2;                    // first of the five points (may be < 0 or >= N: wrapped by the caller)
 }
 
+// the same for a general cell along fractional axis d: u = N_d sum_c r_c H^-1[c][d], each product
+// error-free (hi / lo pairs of N_d H^-1) and the three added with compensated sums, so the offset
+// from the nearest mesh point keeps the precision of the orthorhombic form
+__device__ __forceinline__ void stencil_frac(const float4& p, const PppmTab& pm, int d, int& s0, float w[5]) {
+    const float r[3] = {p.x, p.y, p.z};
+    float s = 0.f, lo = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float h = pm.nh_hi[3 * c + d], hl = pm.nh_lo[3 * c + d];
+        const float pp = r[c] * h;
+        const float pe = fmaf(r[c], h, -pp);   // exact: r_c h = pp + pe
+        lo += fmaf(r[c], hl, pe);
+        const float t = s + pp;                // two-sum: s + pp = t + err exactly
+        const float bp = t - s;
+        lo += (s - (t - bp)) + (pp - bp);
+        s = t;
+    }
+    const float rr = rintf(s);
+    assign5((s - rr) + lo, w);
+    s0 = (int)rr - 2;
+}
+
+// the five-point stencils of an atom along the three mesh axes
+__device__ __forceinline__ void stencil3(const float4& p, const PppmTab& pm, int& sx, int& sy, int& sz, float wx[5],
+                                         float wy[5], float wz[5]) {
+    if (pm.tri) {
+        stencil_frac(p, pm, 0, sx, wx);
+        stencil_frac(p, pm, 1, sy, wy);
+        stencil_frac(p, pm, 2, sz, wz);
+        return;
+    }
+    stencil_axis(p.x, pm.inv_h[0], pm.inv_h_lo[0], sx, wx);
+    stencil_axis(p.y, pm.inv_h[1], pm.inv_h_lo[1], sy, wy);
+    stencil_axis(p.z, pm.inv_h[2], pm.inv_h_lo[2], sz, wz);
+}
+
 // stencil indices lie in [-2, N + 2) (s0 in [-2, N - 2], offsets 0..4): one periodic shift
 __device__ __forceinline__ int wrap(int s, int n) { return s < 0 ? s + n : (s >= n ? s - n : s); }
 
@@ -65,9 +106,7 @@ __global__ void k_pppm_spread(const float4* __restrict__ spos4, const float* __r
     const float q = __ldg(&q_raw[k]) + delta;
     int sx, sy, sz;
     float wx[5], wy[5], wz[5];
-    stencil_axis(p.x, pm.inv_h[0], pm.inv_h_lo[0], sx, wx);
-    stencil_axis(p.y, pm.inv_h[1], pm.inv_h_lo[1], sy, wy);
-    stencil_axis(p.z, pm.inv_h[2], pm.inv_h_lo[2], sz, wz);
+    stencil3(p, pm, sx, sy, sz, wx, wy, wz);
     for (int t = lane; t < 125; t += 32) {
         const int a = t / 25, b = (t / 5) % 5, c = t % 5;
         float wa = wx[0], wb = wy[0], wc = wz[0];
@@ -111,7 +150,12 @@ __global__ void k_pppm_gopt(PppmTab pm, double alpha, double vol) {
     int n1, n2, n3;
     mesh_n(idx, pm, n1, n2, n3);
     const double tp = 6.283185307179586;
-    const double kx = tp * n1 / pm.len[0], ky = tp * n2 / pm.len[1], kz = tp * n3 / pm.len[2];
+    double kx = tp * n1 / pm.len[0], ky = tp * n2 / pm.len[1], kz = tp * n3 / pm.len[2];
+    if (pm.tri) {   // k = 2 pi H^-1 n
+        kx = tp * (pm.hid[0] * n1 + pm.hid[1] * n2 + pm.hid[2] * n3);
+        ky = tp * (pm.hid[3] * n1 + pm.hid[4] * n2 + pm.hid[5] * n3);
+        kz = tp * (pm.hid[6] * n1 + pm.hid[7] * n2 + pm.hid[8] * n3);
+    }
     const double k2 = kx * kx + ky * ky + kz * kz;
     if (k2 == 0.0) {
         pm.gopt[idx] = 0.f;
@@ -143,16 +187,26 @@ __global__ void __launch_bounds__(256) k_pppm_green(PppmTab pm, float alpha, Acc
         if (n2 >= (pm.ny + 1) / 2) n2 -= pm.ny;
         const float g = pm.gopt[idx];
         const float2 s = pm.shat[idx];
-        const float kx = TWO_PI_F * n1 / pm.len[0], ky = TWO_PI_F * n2 / pm.len[1], kz = TWO_PI_F * n3 / pm.len[2];
+        float kx = TWO_PI_F * n1 / pm.len[0], ky = TWO_PI_F * n2 / pm.len[1], kz = TWO_PI_F * n3 / pm.len[2];
+        // the three gradient fields: i k_d (orthorhombic) or the fractional i 2 pi n_c (general)
+        float gx = kx, gy = ky, gz = kz;
+        if (pm.tri) {
+            gx = TWO_PI_F * n1;
+            gy = TWO_PI_F * n2;
+            gz = TWO_PI_F * n3;
+            kx = fmaf(pm.hi[2], gz, fmaf(pm.hi[1], gy, pm.hi[0] * gx));
+            ky = fmaf(pm.hi[5], gz, fmaf(pm.hi[4], gy, pm.hi[3] * gx));
+            kz = fmaf(pm.hi[8], gz, fmaf(pm.hi[7], gy, pm.hi[6] * gx));
+        }
         const float2 sg = make_float2(s.x * g, s.y * g);
         pm.fhat[idx] = sg;
-        // i k_d S G, zero on the Nyquist plane of component d
+        // i g_d S G, zero on the Nyquist plane of component d
         const bool nyx = (pm.nx % 2 == 0) && n1 == -pm.nx / 2;
         const bool nyy = (pm.ny % 2 == 0) && n2 == -pm.ny / 2;
         const bool nyz = (pm.nz % 2 == 0) && n3 == pm.nz / 2;
-        pm.fhat[pm.nhalf + idx] = nyx ? make_float2(0.f, 0.f) : make_float2(-kx * sg.y, kx * sg.x);
-        pm.fhat[2 * pm.nhalf + idx] = nyy ? make_float2(0.f, 0.f) : make_float2(-ky * sg.y, ky * sg.x);
-        pm.fhat[3 * pm.nhalf + idx] = nyz ? make_float2(0.f, 0.f) : make_float2(-kz * sg.y, kz * sg.x);
+        pm.fhat[pm.nhalf + idx] = nyx ? make_float2(0.f, 0.f) : make_float2(-gx * sg.y, gx * sg.x);
+        pm.fhat[2 * pm.nhalf + idx] = nyy ? make_float2(0.f, 0.f) : make_float2(-gy * sg.y, gy * sg.x);
+        pm.fhat[3 * pm.nhalf + idx] = nyz ? make_float2(0.f, 0.f) : make_float2(-gz * sg.y, gz * sg.x);
         if (pm.fhat6) {
             // per-atom virial fields G_opt B_ab S, B = I - (2 / (4 alpha^2) + 2 / k^2) k k^T (zero at k = 0)
             const float k2 = kx * kx + ky * ky + kz * kz;
@@ -226,9 +280,7 @@ __global__ void k_pppm_gather(const float4* __restrict__ spos4, int n, PppmTab p
         const float4 p = __ldg(&spos4[k]);
         int sx, sy, sz;
         float wx[5], wy[5], wz[5];
-        stencil_axis(p.x, pm.inv_h[0], pm.inv_h_lo[0], sx, wx);
-        stencil_axis(p.y, pm.inv_h[1], pm.inv_h_lo[1], sy, wy);
-        stencil_axis(p.z, pm.inv_h[2], pm.inv_h_lo[2], sz, wz);
+        stencil3(p, pm, sx, sy, sz, wx, wy, wz);
         float ex = 0.f, ey = 0.f, ez = 0.f;
         for (int t = lane; t < 125; t += 32) {
             const int a = t / 25, b = (t / 5) % 5, c = t % 5;
@@ -255,6 +307,12 @@ __global__ void k_pppm_gather(const float4* __restrict__ spos4, int n, PppmTab p
             ez += __shfl_xor_sync(0xffffffffu, ez, o);
         }
         ph *= 2.f * KE;
+        if (pm.tri) {   // fractional gradients -> Cartesian: d/dr_a = sum_c H^-1[a][c] d/ds_c
+            const float gx = ex, gy = ey, gz = ez;
+            ex = fmaf(pm.hi[2], gz, fmaf(pm.hi[1], gy, pm.hi[0] * gx));
+            ey = fmaf(pm.hi[5], gz, fmaf(pm.hi[4], gy, pm.hi[3] * gx));
+            ez = fmaf(pm.hi[8], gz, fmaf(pm.hi[7], gy, pm.hi[6] * gx));
+        }
         if (lane == 0) {
             kfield[k] = make_float4(-2.f * KE * ex, -2.f * KE * ey, -2.f * KE * ez, ph);
             pphi += ph;
@@ -285,9 +343,7 @@ __global__ void k_pppm_gather_virial(const float4* __restrict__ spos4, int n, Pp
         const float4 p = __ldg(&spos4[k]);
         int sx, sy, sz;
         float wx[5], wy[5], wz[5];
-        stencil_axis(p.x, pm.inv_h[0], pm.inv_h_lo[0], sx, wx);
-        stencil_axis(p.y, pm.inv_h[1], pm.inv_h_lo[1], sy, wy);
-        stencil_axis(p.z, pm.inv_h[2], pm.inv_h_lo[2], sz, wz);
+        stencil3(p, pm, sx, sy, sz, wx, wy, wz);
         float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int t = lane; t < 125; t += 32) {
             const int a = t / 25, b = (t / 5) % 5, c = t % 5;

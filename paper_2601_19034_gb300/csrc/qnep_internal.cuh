@@ -180,6 +180,13 @@ struct PppmTab {
     float alpha;         // Ewald splitting parameter (per-atom virial fields)
     float2* fhat6;       // 6 x nhalf: G_opt B_ab S (per-atom virial; NULL when not asked for)
     float* field6;       // 6 x nreal: their unnormalised inverse transforms
+    // general cells: mesh points sum_d (s_d / N_d) a_d, an atom's mesh coordinates N_d (r H^-1)_d,
+    // k = 2 pi H^-1 n; the three i k fields are the fractional gradients i 2 pi n_c S G_opt,
+    // mapped to Cartesian components by H^-1 at the gather
+    int tri;
+    float nh_hi[9], nh_lo[9];   // N_d H^-1[c][d] (row-major [c][d]) as float pairs
+    float hi[9];                // H^-1 (row-major)
+    double hid[9];              // H^-1 in FP64 (influence function)
 };
 
 __device__ __forceinline__ int entry_index(int e) { return e & INDEX_MASK; }

@@ -6,8 +6,11 @@
   both kernel families, and the per-atom virial.
 * The same crystal described by a unimodularly transformed cell (rows a1, a2 + a1, a3 + a2)
   against the orthorhombic call of the 5 x 5 x 5 cell: the same outputs to FP32 rounding.
-* Boxes the library does not take are refused: PPPM in a general cell, a left-handed cell, a
-  cell narrower than the cutoff.
+* PPPM in general cells (mesh along the lattice vectors, fractional gradients mapped by H^-1):
+  the sheared BaTiO3 cell and a sheared 64-water box against the oracle's general-cell PPPM,
+  every output including the per-atom virial's mesh term, both kernel families.
+* Boxes the library does not take are refused: a left-handed cell, a cell narrower than the
+  cutoff.
 """
 import numpy as np
 import pytest
@@ -45,12 +48,12 @@ def _sheared_batio3(n=3, seed=61):
     return wl.System(pos.astype(np.float32), types, box, ("Ba", "Ti", "O"))
 
 
-def _compute(dev, sysm, hp, params, elec, path="auto", atom_virial=False):
+def _compute(dev, sysm, hp, params, elec, path="auto", atom_virial=False, potential=False):
     from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
     model = QNEP(hp, params, elec)
     model.set_path(path)
     out = model.compute(torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev), sysm.box,
-                        atom_virial=atom_virial)
+                        atom_virial=atom_virial, potential=potential)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items() if isinstance(v, torch.Tensor)}
     res["sc"] = parse_scalars(out["scalars"])
@@ -114,11 +117,6 @@ def test_boxes_that_are_refused(dev):
     hp = wl.HParams(n_species=3)
     params = wl.random_params(hp, np.random.default_rng(67))[0]
     pos, typ = torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev)
-    m = QNEP(hp, params, wl.Elec(mode=1, kind="pppm", mesh=(16, 16, 16), order=5))
-    with pytest.raises(_lib.QnepError) as e:
-        m.compute(pos, typ, sysm.box)
-    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
-    m.close()
     m = QNEP(hp, params, wl.Elec(mode=1, kind="ewald"))
     left = sysm.box[[1, 0, 2]]                     # rows swapped: left-handed
     with pytest.raises(_lib.QnepError) as e:
@@ -130,3 +128,55 @@ def test_boxes_that_are_refused(dev):
         m.compute(pos, typ, thin)
     assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
     m.close()
+
+
+def _sheared_water(seed=71):
+    """64 H2O at the fractional coordinates of the 12.42 A cube in a cell with every off-diagonal
+    element non-zero."""
+    s = wl.water_box(4, seed=seed)
+    length = s.box[0, 0]
+    box = length * np.array([[1.0, 0.05, -0.04], [0.2, 1.0, 0.06], [-0.1, 0.15, 1.0]])
+    pos = (s.positions.astype(np.float64) / length) @ box
+    return wl.System(pos.astype(np.float32), s.types, box, s.species)
+
+
+@pytest.mark.parametrize("case,mode,path", [("batio3", 1, "warp"), ("batio3", 2, "thread"), ("water", 1, "warp")])
+def test_pppm_in_a_general_cell_against_oracle(dev, case, mode, path):
+    """The PPPM call in a sheared cell against the oracle's general-cell PPPM (the same scheme):
+    energy, forces, charges, virial, BEC, polarization and the potential at the FP32-path
+    tolerances (the potential to 1e-5 of its largest value, as for orthorhombic PPPM)."""
+    if case == "batio3":
+        sysm = _sheared_batio3(seed=72)
+        hp = wl.HParams(n_species=3)
+        mesh = (16, 16, 16)
+    else:
+        sysm = _sheared_water()
+        hp = wl.HParams(n_species=2)
+        mesh = (16, 18, 14)
+    params = wl.random_params(hp, np.random.default_rng(73))[0]
+    elec = wl.Elec(mode=mode, kind="pppm", mesh=mesh, order=5, q_total=0.2)
+    g = _compute(dev, sysm, hp, params, elec, path, potential=True)
+    ref = forcecall.force_call(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    n = sysm.n_atoms
+    de = abs(g["sc"]["energy"] - ref["energy"]) / n
+    df = np.abs(g["forces"] - ref["forces"]).max()
+    print(f"\nPPPM sheared {case} {n} atoms mode {mode} {path}: |dE|/N {de:.3g}, max|dF| {df:.3g}")
+    assert de <= TOL["e"], de
+    assert df <= TOL["f"], df
+    assert np.abs(g["charges"] - ref["charges"]).max() <= TOL["q"]
+    assert np.abs(g["sc"]["virial"] - ref["virial"]).max() / n <= TOL["w"]
+    assert np.abs(g["bec"] - ref["bec"]).max() <= TOL["z"]
+    assert np.abs(g["sc"]["polarization"] - ref["polarization"]).max() / n <= TOL["p"]
+    phi_scale = max(1.0, float(np.abs(ref["phi"]).max()))
+    assert np.abs(g["potential"] - ref["phi"]).max() <= 1e-5 * phi_scale
+
+
+def test_pppm_in_a_general_cell_per_atom_virial(dev):
+    """The per-atom virial with the mesh term of the six extra inverse FFTs in a sheared cell."""
+    sysm = _sheared_batio3(seed=74)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(75))[0]
+    elec = wl.Elec(mode=1, kind="pppm", mesh=(16, 16, 16), order=5)
+    g = _compute(dev, sysm, hp, params, elec, atom_virial=True)
+    ref, _ = virial.per_atom_virial(sysm.positions.astype(np.float64), sysm.box, sysm.types, hp, params, elec)
+    assert np.abs(g["atom_virial"] - ref).max() <= 1e-4
