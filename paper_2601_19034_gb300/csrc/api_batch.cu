@@ -42,6 +42,7 @@ struct qnep_batch {
     std::vector<int2> items_lpt, items_nat;
     BatchStruct* d_st = nullptr;
     BatchKTab* d_kt = nullptr;
+    BatchKTri* d_ktri = nullptr;          // general-cell phase data per k-table (pre-pass)
     int4* d_chunk = nullptr;
     float4* d_kvec = nullptr;
     int* d_kreal = nullptr;
@@ -142,6 +143,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     const float rcl = list_cutoff_b(b);
     std::vector<BatchStruct> sts(n_struct);
     std::vector<BatchKTab> kts;
+    std::vector<BatchKTri> ktris;
     std::vector<int4> chunks;
     std::vector<int> kreal;
     std::vector<float4> kvec;
@@ -227,10 +229,11 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
                 kt.invl_hi[d] = (float)il;
                 kt.invl_lo[d] = (float)(il - (double)kt.invl_hi[d]);
             }
-            kt.tri = tri ? 1 : 0;
+            BatchKTri kr{};
+            kr.tri = tri ? 1 : 0;
             for (int k = 0; k < 9; ++k) {
-                kt.hi_hi[k] = (float)hinv[k];
-                kt.hi_lo[k] = (float)(hinv[k] - (double)kt.hi_hi[k]);
+                kr.hi_hi[k] = (float)hinv[k];
+                kr.hi_lo[k] = (float)(hinv[k] - (double)kr.hi_hi[k]);
             }
             kt.kreal_off = (int)kreal.size();
             for (int h = 0; h < kt.nchunk; ++h) {
@@ -262,6 +265,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
             nk_max = std::max(nk_max, 8 * kt.nchunk);
             it = tab_of.emplace(key, (int)kts.size()).first;
             kts.push_back(kt);
+            ktris.push_back(kr);
             nk_of.push_back(8 * kt.nchunk);
         }
         t.ktab = it->second;
@@ -298,6 +302,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(cudaStreamSynchronize(st));
     CKB(upload(&b->d_st, sts));
     CKB(upload(&b->d_kt, kts));
+    CKB(upload(&b->d_ktri, ktris));
     CKB(upload(&b->d_chunk, chunks));
     CKB(upload(&b->d_kvec, kvec));
     CKB(upload(&b->d_kreal, kreal));
@@ -585,7 +590,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
         }
         CKB(cudaEventRecord(b->ev[0], st));
     }
-    launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->cell_start,
+    launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->d_ktri, b->cell_start,
                       b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list, b->cnt_list,
                       b->nbr_ang, b->cnt_ang, b->phase, batch_phase_stride(b->nph_max), b->geo_rad, b->geo_ang, b->bsum,
                       batch_bstride(b->hp.n_species), tc ? b->bimg : nullptr, (float)b->es.alpha, b->d_status, st);
@@ -833,7 +838,7 @@ qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stre
 void qnep_batch_destroy(qnep_batch* b) {
     if (!b) return;
     if (b->last_stream) cudaStreamSynchronize(b->last_stream);
-    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
+    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_ktri,   b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,

@@ -55,9 +55,16 @@ constexpr int TAB_P = KA + NLM;                // pre-pass staging row: f_k, Y_l
 constexpr int WBUF = 32 * GA;                  // floats per buffer
 constexpr int WCUM = 2 * WBUF;                 // ints
 constexpr int WARP_FLOATS = WCUM + 16;
-// the real-space phase's per-warp buffer: 32 radial pair rows, then the species counts
-constexpr int RS_CUM = 32 * GR;
+// the real-space phase's per-warp buffers: two pieces of 32 radial pair rows (double-buffered
+// bulk copies), then the species counts
+constexpr int RS_BUF = 32 * GR;
+constexpr int RS_CUM = 2 * RS_BUF;
 constexpr int RS_WARP = RS_CUM + 16;
+static_assert(RS_CUM <= WCUM, "the real-space buffers fit a warp's row buffers");
+// radial entries per piece of the backward (a row buffer holds WBUF / GR of them; the angular
+// pieces stay at 32 rows)
+constexpr int RPIECE = 64;
+static_assert(RPIECE * GR <= WBUF, "a radial piece fits a row buffer");
 constexpr int BS_MAX = MAX_SPECIES * KR + MAX_SPECIES * KA * NLM;   // basis-sum floats per atom
 static_assert(BS_MAX <= WBUF, "basis sums fit a row buffer");
 constexpr int PR_R = 0;                                  // c^R[t_i] staged [S][NR][KR][CG]
@@ -76,11 +83,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ float2 batch_phase(const float4& p, int e, const BatchKTab& kt) {
-    if (kt.tri) {
-        if (e < kt.yoff) return phase_factor_frac(p, e, 0, kt.hi_hi, kt.hi_lo);
-        if (e < kt.zoff) return phase_factor_frac(p, e - kt.yoff - kt.n2max, 1, kt.hi_hi, kt.hi_lo);
-        return phase_factor_frac(p, e - kt.zoff - kt.n3max, 2, kt.hi_hi, kt.hi_lo);
+__device__ __forceinline__ float2 batch_phase(const float4& p, int e, const BatchKTab& kt, const BatchKTri& kr) {
+    if (kr.tri) {
+        if (e < kt.yoff) return phase_factor_frac(p, e, 0, kr.hi_hi, kr.hi_lo);
+        if (e < kt.zoff) return phase_factor_frac(p, e - kt.yoff - kt.n2max, 1, kr.hi_hi, kr.hi_lo);
+        return phase_factor_frac(p, e - kt.zoff - kt.n3max, 2, kr.hi_hi, kr.hi_lo);
     }
     if (e < kt.yoff) return phase_factor(p.x, e, kt.invl_hi[0], kt.invl_lo[0]);
     if (e < kt.zoff) return phase_factor(p.y, e - kt.yoff - kt.n2max, kt.invl_hi[1], kt.invl_lo[1]);
@@ -392,7 +399,7 @@ __device__ __forceinline__ void geometry_atom(const float4* __restrict__ sp, con
 // pre-pass 2: neighbour lists, pair geometry, basis sums and phase rows
 __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
     int n_species, const BatchStruct* __restrict__ sts, const BatchKTab* __restrict__ kts,
-    const int* __restrict__ cell_start_all, const float4* __restrict__ spos4, int cap_l, int cap_a,
+    const BatchKTri* __restrict__ ktris, const int* __restrict__ cell_start_all, const float4* __restrict__ spos4, int cap_l, int cap_a,
     int* __restrict__ nbr_list, int* __restrict__ cnt_list, int* __restrict__ nbr_ang, int* __restrict__ cnt_ang,
     float2* __restrict__ phase, int nph_stride, float* __restrict__ geo_rad, float* __restrict__ geo_ang,
     float* __restrict__ bsum, int bstride, unsigned char* __restrict__ bimg, float alpha,
@@ -431,9 +438,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_lists(
                       tab, cum);
     }
     const BatchKTab kt = kts[bs.ktab];
+    const BatchKTri kr = ktris[bs.ktab];
     for (int idx = blockIdx.y * blockDim.x + threadIdx.x; idx < n * kt.nph; idx += blockDim.x * gridDim.y) {
         const int m = idx / kt.nph, e = idx - m * kt.nph;
-        phase[(size_t)(off + m) * nph_stride + e] = batch_phase(sp[m], e, kt);
+        phase[(size_t)(off + m) * nph_stride + e] = batch_phase(sp[m], e, kt, kr);
     }
 }
 
@@ -1465,7 +1473,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
     job_settle(cum, S, kind, tj, base);
     int b = 0;
     if (kind != 2 && lane == 0) {
-        const int cnt = kind == 0 ? min(32, cum[tj + 1] - base) : min(32, tot_a - base);
+        const int cnt = kind == 0 ? min(RPIECE, cum[tj + 1] - base) : min(32, tot_a - base);
         warp_bulk(wb, kind == 0 ? rad_src + (size_t)base * GR : ang_src + (size_t)base * GA,
                   (uint32_t)(cnt * (kind == 0 ? GR : GA) * 4), &bars[0]);
     }
@@ -1504,11 +1512,11 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
     float mu[KR];
     int mu_tj = -1;
     while (kind != 2) {
-        int k2 = kind, t2 = tj, b2 = base + 32;
+        int k2 = kind, t2 = tj, b2 = base + (kind == 0 ? RPIECE : 32);
         job_settle(cum, S, k2, t2, b2);
         __syncwarp();   // every lane is done with the other buffer (previous piece)
         if (k2 != 2 && lane == 0) {
-            const int cnt = k2 == 0 ? min(32, cum[t2 + 1] - b2) : min(32, tot_a - b2);
+            const int cnt = k2 == 0 ? min(RPIECE, cum[t2 + 1] - b2) : min(32, tot_a - b2);
             warp_bulk(b ? wb : wb + WBUF, k2 == 0 ? rad_src + (size_t)b2 * GR : ang_src + (size_t)b2 * GA,
                       (uint32_t)(cnt * (k2 == 0 ? GR : GA) * 4), &bars[b ^ 1]);
         }
@@ -1526,7 +1534,7 @@ __device__ __forceinline__ void backward_atom(const BatchArgs& a, int off, int n
                 }
                 mu_tj = tj;
             }
-            const int cntc = min(32, cum[tj + 1] - base);
+            const int cntc = min(RPIECE, cum[tj + 1] - base);
             // four rows per iteration: independent chains (rows past the piece are skipped)
             for (int r0 = 0; r0 < cntc; r0 += 4) {
                 float Fv[4][3], hv[4][3];
@@ -2110,12 +2118,18 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     species_cum(a, off, n, m, S, cum);
                     const int tot_l = cum[S];
                     const float4* grows = reinterpret_cast<const float4*>(a.geo_rad + (size_t)(off + m) * a.cap_l * GR);
-                    for (int base = 0; base < tot_l; base += 32) {
+                    // pieces of 32 rows, double-buffered: the copy of piece p + 1 overlaps piece p
+                    if (tot_l > 0 && lane == 0)
+                        warp_bulk(tab, grows, (uint32_t)(min(32, tot_l) * GR * 4), &wbars[warp][0]);
+                    int rb = 0;
+                    for (int base = 0; base < tot_l; base += 32, rb ^= 1) {
                         const int cntc = min(32, tot_l - base);
-                        __syncwarp();   // the warp is done with the previous piece
-                        if (lane == 0)
-                            warp_bulk(tab, grows + (size_t)base * (GR / 4), (uint32_t)(cntc * GR * 4), &wbars[warp][0]);
-                        if (!warp_wait(wbars[warp], 0, par, a.status)) continue;
+                        __syncwarp();   // the warp is done with the other buffer (previous piece)
+                        if (base + 32 < tot_l && lane == 0)
+                            warp_bulk(tab + (rb ^ 1) * RS_BUF, grows + (size_t)(base + 32) * (GR / 4),
+                                      (uint32_t)(min(32, tot_l - base - 32) * GR * 4), &wbars[warp][rb ^ 1]);
+                        if (!warp_wait(wbars[warp], rb, par, a.status)) continue;
+                        const float* rows = tab + rb * RS_BUF;
                         // four rows per iteration, their charge loads issued together; rows past
                         // the piece and pairs beyond r_c contribute q_j = 0
                         for (int r0 = 0; r0 < cntc; r0 += 4) {
@@ -2124,7 +2138,7 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
                                 const int r = min(r0 + u, cntc - 1);
-                                const float4* rw = reinterpret_cast<const float4*>(tab + r * GR);
+                                const float4* rw = reinterpret_cast<const float4*>(rows + r * GR);
                                 const float4 d4 = rw[4];   // (B'u_z, j_real, r, -)
                                 d3[u] = rw[3];             // (j_desc, B, B'u_x, B'u_y)
                                 bz[u] = d4.x;
@@ -2322,7 +2336,7 @@ size_t item_smem(int nph_max, bool tc) {   // the same with and without the viri
 }  // namespace
 
 void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
-                       const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
+                       const BatchStruct* st, const BatchKTab* kt, const BatchKTri* ktri, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
                        int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_) {
@@ -2336,7 +2350,7 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
                                                         order, spec_off, status);
     // about one warp per 32 atoms of the largest structure
     const int ysplit = std::max(1, std::min(64, (nmax + 32 * (PREP_THREADS / 32) - 1) / (32 * (PREP_THREADS / 32)) * 4));
-    k_batch_lists<<<dim3(n_struct, ysplit), PREP_THREADS, sm2, st_>>>(n_species, st, kt, cell_start, spos4, cap_l, cap_a, nbr_list,
+    k_batch_lists<<<dim3(n_struct, ysplit), PREP_THREADS, sm2, st_>>>(n_species, st, kt, ktri, cell_start, spos4, cap_l, cap_a, nbr_list,
                                                          cnt_list, nbr_ang, cnt_ang, phase, nph_stride, geo_rad,
                                                          geo_ang, bsum, bstride, bimg, alpha, status);
 }

@@ -61,9 +61,14 @@ struct BatchKTab {
     int nkr;         // wave vectors of the half space (the chunks' non-padding entries)
     int kreal_off;   // their padded indices: kreal[kreal_off .. kreal_off + nkr)
     float invl_hi[3], invl_lo[3];
-    int tri;         // 1: a general cell in the restricted form (a along x, b in the xy plane):
-                     // phases of the fractional coordinates s = r H^-1, k = 2 pi H^-1 n, whose x and
-                     // y components depend on (n1, n2) only (H^-1 is lower triangular as H is)
+};
+
+// The phase-factor data of a general cell (restricted form: a along x, b in the xy plane), read by
+// the pre-pass only (kept apart from BatchKTab, which the item kernel's phases take by value):
+// phases of the fractional coordinates s = r H^-1; k = 2 pi H^-1 n in the table then has x and
+// y components that depend on (n1, n2) only, as H^-1 is lower triangular like H.
+struct BatchKTri {
+    int tri;                    // 0: orthorhombic (BatchKTab.invl_* are used)
     float hi_hi[9], hi_lo[9];   // H^-1 (row-major) as float pairs
 };
 
@@ -135,7 +140,7 @@ struct BatchArgs {
 };
 
 void launch_batch_prep(const float* pos, const int* types, int n_struct, int nmax, int n_species,
-                       const BatchStruct* st, const BatchKTab* kt, int* cell_start, float4* spos4, int* sidx,
+                       const BatchStruct* st, const BatchKTab* kt, const BatchKTri* ktri, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
                        int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_);
