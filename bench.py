@@ -162,9 +162,9 @@ def _ewald_kcount(box, kmax):
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
 # capture of the current kernel (tensor-core form) on the first 160 structures x 64
-# candidates (10.308 GB read + 7.347 GB written for 6,709,248 atom-evaluations; the traffic grows
+# candidates (10.299 GB read + 7.348 GB written for 6,709,248 atom-evaluations; the traffic grows
 # with the atom-evaluations).  Set to None when the item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = (10.308279e9 + 7.347090e9) / 6709248
+ITEM_DRAM_BYTES_PER_EVAL = (10.298995e9 + 7.348247e9) / 6709248
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
                     "first 160 structures x 64 candidates, scaled by atom-evaluations")
 
@@ -675,7 +675,8 @@ def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals, 
     bec, the per-atom Born effective charges and the uncorrected total charges: every input of
     the full training loss)."""
     import torch
-    out = b.outputs(len(off) - 1, pos_d.shape[0], pos_d.device, virial=True, bec=bec, total_charge=bec)
+    out = b.outputs(len(off) - 1, pos_d.shape[0], pos_d.device, virial=True, bec=bec, total_charge=bec,
+                    polarization=bec)
     b.compute_into(pos_d, typ_d, off, boxes, out)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -699,7 +700,8 @@ def _time_with_virial(b, pos_d, typ_d, off, boxes, stream, flush, steps, evals, 
     what = ("the same graph-replayed batched call writing energies, forces, charges and the 3x3 virial "
             "of every (candidate, structure) (qnep_batch_compute_outputs)")
     if bec:
-        what += ", the 3x3 Born effective charge of every atom and the total charge before the correction"
+        what += (", the 3x3 Born effective charge of every atom, the polarization and the total charge before "
+                 "the correction of every (candidate, structure)")
     del out, g
     return {"ms_per_step": ms, "value": evals / (ms * 1e-3), "unit": UNIT, "what": what}
 

@@ -330,9 +330,8 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * (Eq. U_i, Eq. U_ES with the charges of Sec. II.D), the forces including the
  * charge-derivative terms (Sec. II.C) and the corrected charges q^c.
  * Electrostatics: Ewald (mode 1 or 2) per structure; PPPM is not offered here.
- * The virial per (candidate, structure), the per-atom Born effective charges (Eq. bec_2) and the
- * total charge before the correction come with qnep_batch_compute_outputs; the polarization is
- * not computed by the batched call.
+ * The virial and the polarization per (candidate, structure), the per-atom Born effective charges
+ * (Eq. bec_2) and the total charge before the correction come with qnep_batch_compute_outputs.
  *
  * qnep_batch_create: hp and es as for qnep_create (es->kind must be QNEP_EWALD);
  *   params_host = n_candidates blobs of qnep_param_count(hp) floats, candidate-major.
@@ -388,7 +387,10 @@ qnep_status qnep_batch_sync_status(qnep_batch* b);
  *            resident block; it is the input of the D_Z term of the training loss.
  *   total_charge: [C][S] doubles, sum_i q~_i = sqrt(eps_inf) sum_i q_i of the network's charges
  *            BEFORE the correction of Eq. charge-scaling (e; after it the sum is the target),
- *            the input of the D_Q term of the training loss; 0 for a structure without atoms. */
+ *            the input of the D_Q term of the training loss; 0 for a structure without atoms.
+ *   polarization: [C][S][3] doubles, P = sum_i q~^c_i r_i (Eq. polarization; e A) over the
+ *            positions as given (not wrapped), as qnep_compute reports it; FP32 products over 8
+ *            atoms per candidate, FP64 across them. */
 typedef struct {
     double* energy;
     float*  forces;
@@ -396,6 +398,7 @@ typedef struct {
     double* virial;
     float*  bec;
     double* total_charge;
+    double* polarization;
 } qnep_batch_outputs;
 /* As qnep_batch_compute, with every output of qnep_batch_outputs (device pointers). */
 qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* atom_offsets, const float* positions,

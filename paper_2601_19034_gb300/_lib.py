@@ -65,7 +65,8 @@ class VjpC(ctypes.Structure):
 
 class BatchOutputsC(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_void_p), ("forces", ctypes.c_void_p), ("charges", ctypes.c_void_p),
-                ("virial", ctypes.c_void_p), ("bec", ctypes.c_void_p), ("total_charge", ctypes.c_void_p)]
+                ("virial", ctypes.c_void_p), ("bec", ctypes.c_void_p), ("total_charge", ctypes.c_void_p),
+                ("polarization", ctypes.c_void_p)]
 
 
 class LossInputsC(ctypes.Structure):

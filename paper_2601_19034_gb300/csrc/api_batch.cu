@@ -87,6 +87,7 @@ struct qnep_batch {
     double* io_virial = nullptr;
     float* io_bec = nullptr;
     double* io_qtot = nullptr;
+    double* io_pol = nullptr;
     size_t io_atoms = 0, io_evals = 0, io_pairs = 0;
     // stage timers: events around the pre-pass and the item kernel of each profiled call
     bool profiling = false, pending = false;
@@ -577,6 +578,8 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
         if (virial) CKB(cudaMemsetAsync(virial, 0, sizeof(double) * 9 * (size_t)b->n_cand * n_struct, st));
         if (out->total_charge)
             CKB(cudaMemsetAsync(out->total_charge, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
+        if (out->polarization)
+            CKB(cudaMemsetAsync(out->polarization, 0, sizeof(double) * 3 * (size_t)b->n_cand * n_struct, st));
     }
     if (b->profiling) {
         if (b->pending) {   // previous profiled call: harvest its events
@@ -634,6 +637,8 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     a.virial = virial;
     a.bec = out->bec;
     a.total_charge = out->total_charge;
+    a.polarization = out->polarization;
+    a.pos_in = positions;
     a.n_struct = n_struct;
     a.n_total = b->n_total;
     a.status = b->d_status;
@@ -676,7 +681,7 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         // device copies of the inputs and of every output, kept for the next call of this shape
         CKB(cudaStreamSynchronize(st));
         void* old[] = {b->io_pos, b->io_types, b->io_energy, b->io_forces, b->io_charges, b->io_virial, b->io_bec,
-                       b->io_qtot};
+                       b->io_qtot, b->io_pol};
         for (void* q : old)
             if (q) cudaFree(q);
         b->io_pos = nullptr;
@@ -687,6 +692,7 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         b->io_virial = nullptr;
         b->io_bec = nullptr;
         b->io_qtot = nullptr;
+        b->io_pol = nullptr;
         b->io_atoms = b->io_evals = b->io_pairs = 0;
         const size_t na = std::max<size_t>(n_total, 1), ne = std::max<size_t>(evals, 1), np = std::max<size_t>(pairs, 1);
         CKB(cudaMalloc((void**)&b->io_pos, sizeof(float) * 3 * na));
@@ -696,6 +702,7 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         CKB(cudaMalloc((void**)&b->io_charges, sizeof(float) * ne));
         CKB(cudaMalloc((void**)&b->io_virial, sizeof(double) * 9 * np));
         CKB(cudaMalloc((void**)&b->io_qtot, sizeof(double) * np));
+        CKB(cudaMalloc((void**)&b->io_pol, sizeof(double) * 3 * np));
         b->io_atoms = na;
         b->io_evals = ne;
         b->io_pairs = np;
@@ -710,7 +717,8 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
     }
     qnep_batch_outputs dev{b->io_energy, out_host->forces ? b->io_forces : nullptr,
                            out_host->charges ? b->io_charges : nullptr, out_host->virial ? b->io_virial : nullptr,
-                           out_host->bec ? b->io_bec : nullptr, out_host->total_charge ? b->io_qtot : nullptr};
+                           out_host->bec ? b->io_bec : nullptr, out_host->total_charge ? b->io_qtot : nullptr,
+                           out_host->polarization ? b->io_pol : nullptr};
     qnep_status s = qnep_batch_compute_outputs(b, n_struct, atom_offsets, b->io_pos, b->io_types, boxes, stream, &dev);
     if (s != QNEP_OK) return s;
     CKB(cudaMemcpyAsync(out_host->energy, b->io_energy, sizeof(double) * pairs, cudaMemcpyDeviceToHost, st));
@@ -724,6 +732,8 @@ qnep_status qnep_batch_compute_host(qnep_batch* b, int n_struct, const int* atom
         CKB(cudaMemcpyAsync(out_host->bec, b->io_bec, sizeof(float) * 9 * evals, cudaMemcpyDeviceToHost, st));
     if (out_host->total_charge)
         CKB(cudaMemcpyAsync(out_host->total_charge, b->io_qtot, sizeof(double) * pairs, cudaMemcpyDeviceToHost, st));
+    if (out_host->polarization)
+        CKB(cudaMemcpyAsync(out_host->polarization, b->io_pol, sizeof(double) * 3 * pairs, cudaMemcpyDeviceToHost, st));
     b->last_stream = st;
     return qnep_batch_sync_status(b);
 }
@@ -843,7 +853,7 @@ void qnep_batch_destroy(qnep_batch* b) {
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,
                     b->d_work,    b->d_status, b->io_pos,   b->io_types, b->io_energy, b->io_forces,
-                    b->io_charges, b->io_virial, b->io_bec, b->io_qtot, b->zsum};
+                    b->io_charges, b->io_virial, b->io_bec, b->io_qtot, b->io_pol, b->zsum};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto e : b->ev)

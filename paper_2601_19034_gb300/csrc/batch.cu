@@ -2300,6 +2300,36 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 a.total_charge[(size_t)cand * a.n_struct + item.x] =
                     (double)__ldg(&pg[(size_t)a.lay.sqrt_eps * CG + lane]) * sums[4 * CG + lane];
         }
+        if (a.polarization) {
+            // P = sum_i q~^c_i r_i (Eq. polarization) over the positions as given, lanes over
+            // candidates: FP32 over 8 atoms per lane, FP64 across them and across the warps
+            const float seps = __ldg(&pg[(size_t)a.lay.sqrt_eps * CG + lane]);
+            double pd[3] = {0.0, 0.0, 0.0};
+            float pf[3] = {0.f, 0.f, 0.f};
+            int np = 0;
+            for (int m = warp; m < n; m += NW) {
+                const float qt = seps * qcs[(size_t)m * CG + lane];
+                const float* r = a.pos_in + 3 * ((size_t)off + __ldg(&a.sidx[off + m]));
+#pragma unroll
+                for (int d = 0; d < 3; ++d) pf[d] = fmaf(qt, __ldg(&r[d]), pf[d]);
+                if (++np == 8) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        pd[d] += (double)pf[d];
+                        pf[d] = 0.f;
+                    }
+                    np = 0;
+                }
+            }
+            // the FP64 sums of the energy are consumed above: their slots take the three components
+#pragma unroll
+            for (int d = 0; d < 3; ++d) block_sum<NW>(pd[d] + (double)pf[d], red, sums + d * CG);
+            if (warp == 0 && cand < a.n_cand) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    a.polarization[((size_t)cand * a.n_struct + item.x) * 3 + d] = sums[d * CG + lane];
+            }
+        }
     }
     if (TC) {
         // after a wait that gave up, give the products in flight a second bounded wait

@@ -133,6 +133,8 @@ struct BatchArgs {
     double* virial;          // [n_cand][n_struct][9] or NULL (W = -dU/d eps, eV)
     float* bec;              // [n_cand][N_total][9] or NULL (Z_i,ab = dP_a/dr_ib, Eq. bec_2; needs sc.zsum)
     double* total_charge;    // [n_cand][n_struct] or NULL (sum of q~ before the correction)
+    double* polarization;    // [n_cand][n_struct][3] or NULL (P = sum q~^c_i r_i, positions as given)
+    const float* pos_in;     // [N_total][3] the call's positions (for the polarization)
     int n_struct;
     int n_total;
     int inv_cap;             // ints of shared memory for the outputs' inverse permutation (set at launch)

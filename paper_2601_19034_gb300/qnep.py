@@ -429,7 +429,7 @@ class QNEPBatch:
         return off, bx
 
     def outputs(self, n_struct: int, n_total: int, device, forces=True, charges=True, virial=False, bec=False,
-                total_charge=False) -> dict:
+                total_charge=False, polarization=False) -> dict:
         out = {"energy": torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)}
         if forces:
             out["forces"] = torch.empty(self.n_cand, n_total, 3, dtype=torch.float32, device=device)
@@ -441,6 +441,8 @@ class QNEPBatch:
             out["bec"] = torch.empty(self.n_cand, n_total, 3, 3, dtype=torch.float32, device=device)
         if total_charge:
             out["total_charge"] = torch.empty(self.n_cand, n_struct, dtype=torch.float64, device=device)
+        if polarization:
+            out["polarization"] = torch.empty(self.n_cand, n_struct, 3, dtype=torch.float64, device=device)
         return out
 
     @staticmethod
@@ -451,7 +453,7 @@ class QNEPBatch:
                 return None
             return t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data
         return _lib.BatchOutputsC(ptr("energy"), ptr("forces"), ptr("charges"), ptr("virial"), ptr("bec"),
-                                  ptr("total_charge"))
+                                  ptr("total_charge"), ptr("polarization"))
 
     def _args(self, positions, types, offsets, boxes, out, stream):
         assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
@@ -469,7 +471,7 @@ class QNEPBatch:
 
     def compute_into(self, positions, types, offsets, boxes, out: dict, stream=None):
         """Enqueue one batched call writing into ``out`` (from ``outputs``); no synchronisation."""
-        if "virial" in out or "bec" in out or "total_charge" in out:
+        if any(k in out for k in ("virial", "bec", "total_charge", "polarization")):
             args = self._args(positions, types, offsets, boxes, out, stream)
             oc = self._outputs_c(out)
             _lib.check(self.lib.qnep_batch_compute_outputs(*args[:7], ctypes.byref(oc)), batch=self.handle)
@@ -481,7 +483,7 @@ class QNEPBatch:
         """End-to-end call on host buffers: positions [N, 3] float32 and types [N] int32 (numpy
         arrays or pinned CPU tensors) in, every array of ``out`` (host energy [C, S] float64,
         optional forces [C, N, 3], charges [C, N], virial [C, S, 3, 3], bec [C, N, 3, 3] float32,
-        total_charge [C, S] float64) filled, synchronised."""
+        total_charge [C, S], polarization [C, S, 3] float64) filled, synchronised."""
         off, bx = self._describe(offsets, boxes)
 
         def hptr(a):
@@ -503,10 +505,11 @@ class QNEPBatch:
         return self.lib.qnep_batch_sync_status(self.handle)
 
     def compute(self, positions, types, offsets, boxes, retries: int = 3, forces=True, charges=True,
-                virial=False, bec=False, total_charge=False) -> dict:
+                virial=False, bec=False, total_charge=False, polarization=False) -> dict:
         """Batched call with a status check; grows the neighbour lists and retries on overflow."""
         n_struct = len(offsets) - 1
-        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges, virial, bec, total_charge)
+        out = self.outputs(n_struct, positions.shape[0], positions.device, forces, charges, virial, bec, total_charge,
+                           polarization)
         for _ in range(retries + 1):
             self.compute_into(positions, types, offsets, boxes, out)
             st = self.sync_status()

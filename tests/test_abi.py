@@ -56,7 +56,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.ElecC) == 56
     assert ctypes.sizeof(_lib.HParamsC) == 40
     assert ctypes.sizeof(_lib.OutputsC) == 72
-    assert ctypes.sizeof(_lib.BatchOutputsC) == 48      # six pointers
+    assert ctypes.sizeof(_lib.BatchOutputsC) == 56      # seven pointers
     assert ctypes.sizeof(_lib.LossInputsC) == 40        # five pointers
     assert ctypes.sizeof(_lib.LossWeightsFullC) == 56   # seven doubles
 

@@ -6,6 +6,7 @@ the full training loss of Sec. II.E built on them.
   contractions, Ewald modes 1 and 2 and charged targets; the acoustic sum rule
   sum_i Z_i = Q I (every entry term is added to one atom and subtracted from another) on every
   pair; energies, forces and charges of the call unchanged by asking for BEC.
+* polarization P = sum q~^c_i r_i per pair against the oracle (1e-5 e A per atom).
 * total charge before the correction (the D_Q input) against the oracle's sum of q~ per pair:
   FP32 network charges summed in FP64, within N x 2e-6 e x sqrt(eps_inf) (the per-atom charge
   tolerance summed over the structure's atoms).
@@ -58,6 +59,9 @@ def _check_bec(res, off, systems, s, c, hp, params, elec):
     seps = float(params[c, -1])
     dq = abs(res["total_charge"][c, s] - ref["total_charge_raw"])
     assert dq <= 2e-6 * sysm.n_atoms * seps, (s, c, dq, ref["total_charge_raw"])
+    if "polarization" in res:   # P = sum q~^c r over the positions as given, 1e-5 e A per atom
+        dp = np.abs(res["polarization"][c, s] - ref["polarization"]).max() / sysm.n_atoms
+        assert dp <= 1e-5, (s, c, dp)
     return ref
 
 
@@ -78,7 +82,7 @@ def test_batched_bec_and_total_charge_against_oracle(dev, contract):
     hp = wl.HParams(n_species=4)
     params = wl.random_params(hp, np.random.default_rng(64), n_candidates=33)
     elec = wl.Elec(mode=1, kind="ewald", q_total=0.3)
-    res, off = _run(systems, hp, params, elec, dev, contract, bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, contract, bec=True, total_charge=True, polarization=True)
     plain, _ = _run(systems, hp, params, elec, dev, contract)
     n = np.diff(off)
     assert np.abs(res["energy"] - plain["energy"]).max() / n.min() <= 1e-9
@@ -99,7 +103,7 @@ def test_batched_bec_mode2_water_perovskite_and_edge_cases(dev):
             ([wl.batio3_supercell(2, seed=68), wl.batio3_supercell(3, seed=69)], wl.HParams(n_species=3),
              wl.Elec(mode=1, kind="ewald", q_total=-0.4), 70, 2)):
         params = wl.random_params(hp, np.random.default_rng(seed), n_candidates=c_n)
-        res, off = _run(systems, hp, params, elec, dev, "bf16x3", bec=True, total_charge=True)
+        res, off = _run(systems, hp, params, elec, dev, "bf16x3", bec=True, total_charge=True, polarization=True)
         for s in range(len(systems)):
             _check_bec(res, off, systems, s, s % c_n, hp, params, elec)
         _sum_rule(res, off, elec.q_total)
@@ -111,7 +115,7 @@ def test_batched_bec_mode2_water_perovskite_and_edge_cases(dev):
     empty = wl.System(np.zeros((0, 3), np.float32), np.zeros(0, np.int32), np.diag([10.0, 10.0, 10.0]),
                       wl.LLZO_SPECIES)
     systems = [one, _llzo((1, 1, 1), 72), empty]
-    res, off = _run(systems, hp, params, elec, dev, "fp32", bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, "fp32", bec=True, total_charge=True, polarization=True)
     for s in (0, 1):
         _check_bec(res, off, systems, s, 0, hp, params, elec)
     assert res["total_charge"][0, 2] == 0.0
@@ -121,7 +125,7 @@ def test_full_llzo_batch_bec_sum_rule_and_sampled_pairs(dev):
     """The 512 x 64 batch with BEC and total charges (tensor-core contraction): the sum rule on every
     pair, the largest and smallest cells' pairs against the oracle."""
     systems, hp, params, elec = wl.config_llzo_batch()
-    res, off = _run(systems, hp, params, elec, dev, "bf16x3", bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, "bf16x3", bec=True, total_charge=True, polarization=True)
     assert np.isfinite(res["bec"]).all() and np.isfinite(res["total_charge"]).all()
     _sum_rule(res, off, elec.q_total)
     sizes = np.diff(off)
@@ -140,7 +144,8 @@ def test_full_loss_matches_oracle(dev):
     hp = wl.HParams(n_species=4)
     params = wl.random_params(hp, np.random.default_rng(84), n_candidates=5)
     elec = wl.Elec(mode=1, kind="ewald")
-    res, off = _run(systems, hp, params, elec, dev, "bf16x3", virial=True, bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, "bf16x3", virial=True, bec=True, total_charge=True,
+                    polarization=True)
     rng = np.random.default_rng(85)
     n, s = int(off[-1]), len(systems)
     refs = {"energy": res["energy"][0] + rng.normal(size=s) * 3.0,

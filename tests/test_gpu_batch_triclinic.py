@@ -54,7 +54,8 @@ def test_sheared_llzo_and_orthorhombic_cells_against_oracle(dev, contract):
     hp = wl.HParams(n_species=4)
     params = wl.random_params(hp, np.random.default_rng(108), n_candidates=33)
     elec = wl.Elec(mode=1, kind="ewald", q_total=0.2)
-    res, off = _run(systems, hp, params, elec, dev, contract, virial=True, bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, contract, virial=True, bec=True, total_charge=True,
+                    polarization=True)
     for s, c in ((0, 0), (1, 3), (2, 32), (3, 17), (0, 31)):
         _check_pair(res, off, systems, s, c, hp, params, elec)
         _check_virial(res, off, systems, s, c, hp, params, elec)
@@ -68,7 +69,8 @@ def test_sheared_perovskite_mode2(dev):
     hp = wl.HParams(n_species=3)
     params = wl.random_params(hp, np.random.default_rng(115), n_candidates=3)
     elec = wl.Elec(mode=2, kind="ewald", q_total=-0.3)
-    res, off = _run(systems, hp, params, elec, dev, "bf16x3", virial=True, bec=True, total_charge=True)
+    res, off = _run(systems, hp, params, elec, dev, "bf16x3", virial=True, bec=True, total_charge=True,
+                    polarization=True)
     for s in range(2):
         for c in range(3):
             _check_pair(res, off, systems, s, c, hp, params, elec)
