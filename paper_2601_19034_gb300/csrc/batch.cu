@@ -18,8 +18,14 @@
 //   4 fields     lanes over atoms: phi^k_i and the k-space field (Sec. II.C);
 //                lanes over candidates: real-space phi^r_i and F^r_i
 //   5 backward   per species block: lambda = dU/dD + (phi_i - mean phi) dq/dD; radial
-//                and angular partial forces per pair (Sec. II.C), float4 atomics
-//   6 outputs    forces, corrected charges (input order), energy per candidate
+//                and angular partial forces per pair (Sec. II.C), float4 atomics; on request
+//                the virial, and a second pass with kappa = sqrt(eps_inf) dq/dD for the BEC
+//                terms of Eq. bec_2
+//   6 outputs    forces, corrected charges, BEC (input order), energy, virial, uncorrected
+//                total charge and polarization per candidate
+// General cells (restricted form, a along x and b in the xy plane) change the pre-pass only:
+// wrapping by lattice translations, cells along the fractional axes, phases of the fractional
+// coordinates; the item kernel reads Cartesian wave vectors from the tables either way.
 #include <algorithm>
 #include <cstdint>
 

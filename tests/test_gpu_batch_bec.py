@@ -174,3 +174,32 @@ def test_full_loss_matches_oracle(dev):
     t0 = terms0.cpu().numpy()
     assert (t0[:, 3] == 0).all() and (t0[:, 4] == 0).all()
     np.testing.assert_allclose(t0[:, [0, 1, 2, 5, 6]], terms[:, [0, 1, 2, 5, 6]], rtol=1e-12)
+
+
+def test_host_buffer_call_with_every_output(dev):
+    """qnep_batch_compute_host with BEC, total charges, polarization and virial requested: every
+    output copied back to (pinned) host memory equals the device-buffer call's."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    systems = [_llzo((1, 1, 1), 91), _llzo((2, 1, 1), 92)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(93), n_candidates=3)
+    elec = wl.Elec(mode=1, kind="ewald", q_total=0.1)
+    pos, typ, off, boxes = stack_structures(systems)
+    b = QNEPBatch(hp, params, elec)
+    b.set_contraction("bf16x3")
+    ref = b.compute(torch.tensor(pos, device=dev), torch.tensor(typ, device=dev), off, boxes, virial=True, bec=True,
+                    total_charge=True, polarization=True)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    c, s_, n = 3, len(systems), int(off[-1])
+    out = {"energy": torch.zeros(c, s_, dtype=torch.float64).pin_memory(),
+           "forces": torch.zeros(c, n, 3).pin_memory(), "charges": torch.zeros(c, n).pin_memory(),
+           "virial": torch.zeros(c, s_, 3, 3, dtype=torch.float64).pin_memory(),
+           "bec": torch.zeros(c, n, 3, 3).pin_memory(),
+           "total_charge": torch.zeros(c, s_, dtype=torch.float64).pin_memory(),
+           "polarization": torch.zeros(c, s_, 3, dtype=torch.float64).pin_memory()}
+    b.compute_host(torch.tensor(pos).pin_memory(), torch.tensor(typ).pin_memory(), off, boxes, out)
+    b.close()
+    for k, v in out.items():
+        tol = 1e-9 if v.dtype == torch.float64 else 1e-5
+        assert np.abs(v.numpy() - ref[k]).max() <= tol * max(1.0, float(np.abs(ref[k]).max())), k
