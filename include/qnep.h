@@ -420,6 +420,20 @@ qnep_status qnep_batch_capacity(const qnep_batch* b, int* cap_list, int* cap_ang
  * in which blocks take the (structure, candidate-group) items. */
 qnep_status qnep_batch_set_config(qnep_batch* b, int warps, int order);
 qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
+/* Static geometry, for training on fixed structures (Sec. II.E: every generation of the population
+ * is scored on the same training structures, so only the candidates change between calls).  With
+ * enable = 1, the candidate-independent pre-pass (wrapping, cell and species order, neighbour
+ * lists, pair geometry rows, basis sums, phase factors, operand images) runs in the first call
+ * after this one and is reused by later calls while the batch description, the positions and
+ * types pointers and the contraction's needs are unchanged; the caller promises that the memory
+ * behind positions and types does not change meanwhile, or calls qnep_batch_geometry_changed
+ * (the next call then rebuilds); with qnep_batch_compute_host the promise covers the host
+ * positions and types.  A change between the FP32 and the tensor-core contraction rebuilds.
+ * Neighbour overflow and species errors are reported by the call that built the geometry.  A call captured in a CUDA graph while the geometry is kept contains
+ * no pre-pass.  enable = 0 (the default) runs the pre-pass in every call.  QNEP_ERR_ARG for a NULL
+ * batch or an enable outside {0, 1}.  No GPU work. */
+qnep_status qnep_batch_set_static_geometry(qnep_batch* b, int enable);
+qnep_status qnep_batch_geometry_changed(qnep_batch* b);
 /* Descriptor contraction of the batched call: the angular expansion coefficients
  * A_{n,lm} = sum_{s,k} c^A[t_i][s][n][k] B^A[s][k][lm] of every atom and candidate (Sec. II.A)
  * in FP32 on the FP32 pipes (QNEP_BATCH_CONTRACT_FP32, the default), or on the tensor cores

@@ -159,6 +159,10 @@ def _declare(lib):
     lib.qnep_batch_loss_full.argtypes = [i, i, p, i, ctypes.POINTER(LossInputsC), ctypes.POINTER(LossInputsC), p, p,
                                          i, ctypes.POINTER(LossWeightsFullC), p, p, p]
     lib.qnep_batch_loss_full.restype = i
+    lib.qnep_batch_set_static_geometry.argtypes = [p, i]
+    lib.qnep_batch_set_static_geometry.restype = i
+    lib.qnep_batch_geometry_changed.argtypes = [p]
+    lib.qnep_batch_geometry_changed.restype = i
     lib.qnep_batch_set_contraction.argtypes = [p, i]
     lib.qnep_batch_set_contraction.restype = i
     lib.qnep_batch_get_contraction.argtypes = [p, ctypes.POINTER(i)]

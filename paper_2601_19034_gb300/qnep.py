@@ -535,6 +535,14 @@ class QNEPBatch:
                 "structure": _lib.QNEP_BATCH_ORDER_STRUCTURE}[order]
         _lib.check(self.lib.qnep_batch_set_config(self.handle, int(warps), code), batch=self.handle)
 
+    def set_static_geometry(self, enable: bool = True):
+        """Keep the candidate-independent pre-pass between calls on unchanged structures (training)."""
+        _lib.check(self.lib.qnep_batch_set_static_geometry(self.handle, 1 if enable else 0), batch=self.handle)
+
+    def geometry_changed(self):
+        """The positions or types behind the same pointers changed: the next call rebuilds the geometry."""
+        _lib.check(self.lib.qnep_batch_geometry_changed(self.handle), batch=self.handle)
+
     def set_contraction(self, contract: str = "fp32"):
         """Descriptor contraction: "fp32" (FP32 FMAs), "bf16x3" (tensor cores, BF16 hi/lo split, FP32-path
         accuracy) or "bf16" (tensor cores, one BF16 product: the reduced-precision form)."""

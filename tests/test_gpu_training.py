@@ -222,3 +222,59 @@ def test_loss_with_virial_matches_oracle(dev, sizes):
                                  _t(z, dev), weights)
     assert np.all(terms0.cpu().numpy()[:, 2] == 0.0)
     np.testing.assert_allclose(terms0.cpu().numpy()[:, [0, 1, 3, 4]], terms[:, [0, 1, 3, 4]], rtol=1e-12)
+
+
+def test_static_geometry_keeps_the_prepass_and_follows_changes(dev):
+    """qnep_batch_set_static_geometry: calls after the first reuse its pre-pass and give the outputs
+    of full calls, new candidates included (the training loop's case); a captured call replays
+    without the pre-pass; after an in-place move of the positions and qnep_batch_geometry_changed
+    the next call equals a full call on the moved structures; a contraction change rebuilds."""
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    from tests.test_gpu_batch import _llzo
+    systems = [_llzo((1, 1, 1), 141), _llzo((2, 1, 1), 142)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(143), n_candidates=5)
+    params2 = wl.random_params(hp, np.random.default_rng(144), n_candidates=5)
+    elec = wl.Elec(mode=1, kind="ewald")
+    pos, typ, off, boxes = stack_structures(systems)
+    pd, td = _t(pos, dev), _t(typ, dev)
+
+    def full(prm, positions, contract="bf16x3"):
+        f = QNEPBatch(hp, prm, elec)
+        f.set_contraction(contract)
+        o = {k: v.clone() for k, v in f.compute(positions, td, off, boxes).items()}
+        f.close()
+        return o
+
+    def same(a, b_):
+        n = np.diff(off)
+        assert ((a["energy"] - b_["energy"]).abs().cpu().numpy() / n[None]).max() <= 1e-9
+        assert (a["forces"] - b_["forces"]).abs().max().item() <= 1e-5
+        assert (a["charges"] - b_["charges"]).abs().max().item() <= 1e-6
+
+    b = QNEPBatch(hp, params, elec)
+    b.set_contraction("bf16x3")
+    b.set_static_geometry(True)
+    same(b.compute(pd, td, off, boxes), full(params, pd))          # builds the geometry
+    b.set_params(_t(params2, dev))
+    same(b.compute(pd, td, off, boxes), full(params2, pd))         # reuses it, new candidates
+    out = b.outputs(len(off) - 1, pos.shape[0], dev)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.compute_into(pd, td, off, boxes, out, stream=stream.cuda_stream)
+    for v in out.values():
+        v.zero_()
+    with torch.cuda.stream(stream):
+        g.replay()
+    torch.cuda.synchronize()
+    same(out, full(params2, pd))
+    del g
+    pd.add_(0.05)                                                   # the structures move in place
+    b.geometry_changed()
+    same(b.compute(pd, td, off, boxes), full(params2, pd))
+    b.set_contraction("fp32")                                       # FP32 B^A sums are built anew
+    same(b.compute(pd, td, off, boxes), full(params2, pd, "fp32"))
+    b.close()
