@@ -87,3 +87,30 @@ def test_autograd_large_system_gradient_consistency(dev):
     f = model.compute(pos, typ, sysm.box)["forces"]
     g = model.vjp(pos, typ, sysm.box, 1.0)
     assert (g + f).abs().max().item() < 2e-5
+
+
+@pytest.mark.parametrize("kind", ["ewald", "pppm"])
+def test_autograd_in_a_general_cell(dev, kind):
+    """The differentiation form in a sheared perovskite cell (every off-diagonal element non-zero):
+    the gradient of a U + sum c q^c + d . P against the oracle's, Ewald and PPPM."""
+    from paper_2601_19034_gb300.qnep import QNEP, qnep_energy
+    s0 = wl.batio3_supercell(3, seed=33)
+    box = s0.box + np.array([[0.0, 0.4, -0.3], [0.9, 0.0, 0.5], [-0.7, 1.1, 0.0]])
+    pos0 = (s0.positions.astype(np.float64) @ np.linalg.inv(s0.box)) @ box
+    s = wl.System(pos0.astype(np.float32), s0.types, box, s0.species)
+    hp = wl.HParams(n_species=3)
+    params = wl.random_params(hp, np.random.default_rng(34))[0]
+    elec = wl.Elec(mode=1, kind=kind, q_total=0.2, mesh=(16, 16, 16), order=5)
+    model = QNEP(hp, params, elec)
+    rng = np.random.default_rng(35)
+    a, c, d = 0.7, rng.normal(size=s.n_atoms), np.array([0.3, -0.5, 0.2])
+    pos = torch.tensor(s.positions, device=dev, requires_grad=True)
+    typ = torch.tensor(s.types, device=dev)
+    e, q, p = qnep_energy(model, pos, typ, s.box)
+    loss = a * e + (torch.as_tensor(c, device=dev) * q).sum() + (torch.as_tensor(d, device=dev) * p).sum()
+    loss.backward()
+    ref_grad, ref = _oracle_grad(s, hp, params, elec, a, c, d)
+    assert abs(e.item() - ref["energy"]) / s.n_atoms < 1e-6
+    err = np.abs(pos.grad.cpu().numpy() - ref_grad).max()
+    assert err < 1e-4, err
+    model.close()
