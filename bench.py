@@ -914,6 +914,19 @@ def run_batch(args):
     for prec in ("bf16", "tf32"):
         mixed[f"speedup_{prec}_vs_fp32"] = mixed[prec]["value"] / mixed["fp32"]["value"]
     mixed["errors_vs_oracle"] = "per-output bounds against the FP64 oracle in tests/test_gpu_precision.py"
+    # and on the ~1.0 M-atom Mg-water interface (PPPM 256 x 256 x 384), the configuration that names
+    # the mixed-precision network: the MD force call (forces and charges), FP32 vs BF16 network
+    sy_m, hp_m, par_m, el_m = workloads.config_mg_water()
+    large = {"workload": WORKLOADS["mgwater_nve"], "atoms": sy_m.n_atoms, "outputs": "forces, charges"}
+    for prec in ("fp32", "bf16"):
+        mm = QNEP(hp_m, par_m, el_m, precision=prec)
+        ms_m, _ = _time_single(mm, sy_m, dev, min(args.steps, 10), 3, flush, want=dict(bec=False, virial=False))
+        large[prec] = {"ms_per_call": ms_m, "value": sy_m.n_atoms / (ms_m * 1e-3), "unit": UNIT}
+        mm.close()
+    large["speedup_bf16_vs_fp32"] = large["bf16"]["value"] / large["fp32"]["value"]
+    large["errors_vs_oracle"] = ("BF16 network against the FP32 path at this size: force RMSE <= 5e-3 eV/A "
+                                 "(tests/test_gpu_nve.py); per-output bounds in tests/test_gpu_precision.py")
+    mixed["mgwater_1m"] = large
 
     # plain FP32 single-structure path on the same structures (candidate 0; one call per structure):
     # every call captured in its own CUDA graph (one model per box shape, so no call rebuilds its
