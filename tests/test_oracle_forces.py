@@ -247,3 +247,35 @@ def test_polarization_moves_by_q_total_under_translation(q_total):
     p0 = fc.force_call(pos, box, types, hp, blob, elec, want_bec=False)["polarization"]
     p1 = fc.force_call(pos + d, box, types, hp, blob, elec, want_bec=False)["polarization"]
     np.testing.assert_allclose(p1 - p0, q_total * d, atol=1e-11)
+
+
+def test_network_with_zero_input_weights_is_a_closed_form(batio3_subcell):
+    """Every first-layer weight W0 = 0: the hidden layer is tanh(-b0) of the central atom's species
+    (Eq. U_i with the bias subtracted), so U_i = sum_mu w1E tanh(-b0) - b1E and q_i likewise are
+    constants per species, whatever the descriptor.  Then the charges do not move with the atoms:
+    the forces are the static electrostatic forces of those fixed charges, the BEC are q~^c times
+    the identity, and the NEP energy is the sum of the per-species constants (numpy's tanh)."""
+    from oracle import ewald
+    pos, box, types, hp, blob, elec = batio3_subcell
+    blob = np.array(blob, dtype=np.float32)
+    s, nn, nd = hp.n_species, hp.n_neurons, hp.n_des
+    o = s * s * (hp.n_radial * hp.basis_radial + hp.n_angular * hp.basis_angular) + nd
+    u_t, q_t = [], []
+    for _ in range(s):
+        blob[o:o + nn * nd] = 0.0                      # W0
+        o += nn * nd
+        b0 = blob[o:o + nn].astype(np.float64)
+        w1e = blob[o + nn:o + 2 * nn].astype(np.float64)
+        w1q = blob[o + 2 * nn:o + 3 * nn].astype(np.float64)
+        b1e, b1q = float(blob[o + 3 * nn]), float(blob[o + 3 * nn + 1])
+        u_t.append(float((w1e * np.tanh(-b0)).sum()) - b1e)
+        q_t.append(float((w1q * np.tanh(-b0)).sum()) - b1q)
+        o += 3 * nn + 2
+    out = fc.force_call(pos, box, types, hp, blob, elec)
+    np.testing.assert_allclose(out["site_energy"], np.asarray(u_t)[types], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out["q_raw"], np.asarray(q_t)[types], rtol=0, atol=1e-12)
+    assert abs(out["e_nep"] - float(np.asarray(u_t)[types].sum())) < 1e-10
+    ent_real = geometry.neighbor_entries(pos, box, elec.rc_real)
+    static = ewald.ewald_static(pos, box, out["charges"], ent_real, elec)
+    np.testing.assert_allclose(out["forces"], static["force"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out["bec"], out["qtilde"][:, None, None] * np.eye(3)[None], rtol=0, atol=1e-12)

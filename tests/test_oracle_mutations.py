@@ -328,3 +328,26 @@ def test_general_cell_pppm_gradient_with_h_inverse_transposed(monkeypatch):
     pppm_general_orig = pppm.pppm_general
     monkeypatch.setattr(pppm, "pppm_general", general)
     _fails(t_tri.test_pppm_in_a_general_cell_converges_to_ewald)
+
+
+def test_network_slips_fail_the_zero_weight_closed_form(monkeypatch, batio3_subcell):  # noqa: F811
+    """The closed form with W0 = 0 catches, without restating Eq. U_i, the hidden bias added and
+    the output layer taken from the first species for every atom."""
+    from oracle import network
+
+    def bias_added(d, types, model):
+        t = torch.as_tensor(types, dtype=torch.long)
+        h = torch.tanh(torch.einsum("imn,in->im", model.w0[t], d) + model.b0[t])
+        return (model.w1e[t] * h).sum(1) - model.b1e[t], (model.w1q[t] * h).sum(1) - model.b1q[t]
+
+    def first_species_output(d, types, model):
+        t = torch.as_tensor(types, dtype=torch.long)
+        h = torch.tanh(torch.einsum("imn,in->im", model.w0[t], d) - model.b0[t])
+        z = torch.zeros_like(t)
+        return (model.w1e[z] * h).sum(1) - model.b1e[z], (model.w1q[z] * h).sum(1) - model.b1q[z]
+
+    for wrong in (bias_added, first_species_output):
+        monkeypatch.setattr(network, "site_energy_and_charge", wrong)
+        _fails(t_forces.test_network_with_zero_input_weights_is_a_closed_form, batio3_subcell)
+    monkeypatch.undo()
+    t_forces.test_network_with_zero_input_weights_is_a_closed_form(batio3_subcell)
