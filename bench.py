@@ -162,9 +162,9 @@ def _ewald_kcount(box, kmax):
 
 # DRAM bytes (read + write) of the batched item kernel per atom-evaluation, from one ncu
 # capture of the current kernel (tensor-core form) on the first 160 structures x 64
-# candidates (10.299 GB read + 7.348 GB written for 6,709,248 atom-evaluations; the traffic grows
+# candidates (10.330 GB read + 7.348 GB written for 6,709,248 atom-evaluations; the traffic grows
 # with the atom-evaluations).  Set to None when the item kernel changes until it is captured again.
-ITEM_DRAM_BYTES_PER_EVAL = (10.298995e9 + 7.348247e9) / 6709248
+ITEM_DRAM_BYTES_PER_EVAL = (10.329806e9 + 7.348257e9) / 6709248
 ITEM_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_batch_items launch on the "
                     "first 160 structures x 64 candidates, scaled by atom-evaluations")
 

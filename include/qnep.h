@@ -340,12 +340,14 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  *   atom_offsets: host [n_struct + 1], atom_offsets[0] = 0, non-decreasing;
  *                 structure s holds atoms atom_offsets[s] .. atom_offsets[s+1]-1
  *   positions:    device [N_total][3] float32 (A), types: device [N_total] int32
- *   boxes:        host [n_struct][9] doubles, rows = lattice vectors: orthorhombic, or a general
- *                 cell in the restricted form a = (a_x, 0, 0), b = (b_x, b_y, 0),
- *                 c = (c_x, c_y, c_z), a_x, b_y, c_z > 0 (every cell can be rotated into it;
- *                 QNEP_ERR_UNSUPPORTED for other general cells, QNEP_ERR_ARG for a left-handed
- *                 one); every perpendicular width >= the neighbour-list cutoff; at most 32768
- *                 atoms per structure
+ *   boxes:        host [n_struct][9] doubles, rows = lattice vectors: orthorhombic or a general
+ *                 right-handed cell (QNEP_ERR_ARG for a left-handed or degenerate one).  The
+ *                 kernels run general cells in the restricted form a = (a_x, 0, 0),
+ *                 b = (b_x, b_y, 0), c = (c_x, c_y, c_z); a cell given otherwise is rotated into it
+ *                 (rows of R: a / |a|, (a x b) x a / |..|, a x b / |a x b|), its positions rotated
+ *                 as they are read, and forces, virial and BEC rotated back (R^T F, R^T W R,
+ *                 R^T Z R): every output is in the input frame.  Every perpendicular width >= the
+ *                 neighbour-list cutoff; at most 32768 atoms per structure
  *   energy:       device [n_candidates][n_struct] doubles (eV)
  *   forces:       device [n_candidates][N_total][3] float32 (eV/A), or NULL
  *   charges:      device [n_candidates][N_total] float32 (e), or NULL

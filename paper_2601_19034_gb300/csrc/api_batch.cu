@@ -49,6 +49,7 @@ struct qnep_batch {
     BatchStruct* d_st = nullptr;
     BatchKTab* d_kt = nullptr;
     BatchKTri* d_ktri = nullptr;          // general-cell phase data per k-table (pre-pass)
+    float* d_rot = nullptr;               // per structure: rotation into the restricted cell form, flag
     int4* d_chunk = nullptr;
     float4* d_kvec = nullptr;
     int* d_kreal = nullptr;
@@ -159,18 +160,44 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     int cell_total = 0, nmax = 0, nph_max = 0, nk_max = 0;
     double dens_max = 0.0;
     const double two_pi = 6.283185307179586, ke = 14.3996454784;
+    std::vector<float> rot((size_t)n_struct * 12, 0.f);   // per structure: R (row-major), flag, pad
     for (int s = 0; s < n_struct; ++s) {
-        const double* bx = boxes + 9 * (size_t)s;
+        const double* bx0 = boxes + 9 * (size_t)s;
         for (int k = 0; k < 9; ++k)
-            if (!std::isfinite(bx[k])) return failb(b, QNEP_ERR_ARG, "box has a non-finite entry");
+            if (!std::isfinite(bx0[k])) return failb(b, QNEP_ERR_ARG, "box has a non-finite entry");
         // orthorhombic, or a general cell in the restricted form a = (a_x, 0, 0), b = (b_x, b_y, 0),
-        // c = (c_x, c_y, c_z) with a_x, b_y, c_z > 0 (every cell can be rotated into it): its H and
-        // H^-1 are lower triangular, so the x and y components of k = 2 pi H^-1 n depend on (n1, n2)
-        // only, as the k-space field pass assumes for a column of wave vectors
+        // c = (c_x, c_y, c_z) with a_x, b_y, c_z > 0: its H and H^-1 are lower triangular, so the x and
+        // y components of k = 2 pi H^-1 n depend on (n1, n2) only, as the k-space field pass assumes
+        // for a column of wave vectors.  Any other general cell is rotated into that form (rows of R:
+        // e1 = a / |a|, e3 = a x b / |a x b|, e2 = e3 x e1; the pre-pass rotates the positions, the
+        // outputs are rotated back)
+        double bx[9];
+        for (int k = 0; k < 9; ++k) bx[k] = bx0[k];
+        float* rs = rot.data() + 12 * (size_t)s;
+        rs[0] = rs[4] = rs[8] = 1.f;
+        if (bx[1] != 0 || bx[2] != 0 || bx[5] != 0) {
+            const double* av = bx0;
+            const double* bv = bx0 + 3;
+            const double la = std::sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+            const double n3[3] = {av[1] * bv[2] - av[2] * bv[1], av[2] * bv[0] - av[0] * bv[2], av[0] * bv[1] - av[1] * bv[0]};
+            const double ln = std::sqrt(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2]);
+            if (!(la > 0) || !(ln > 0)) return failb(b, QNEP_ERR_ARG, "the cell vectors must be independent");
+            double R[9];
+            for (int d = 0; d < 3; ++d) {
+                R[d] = av[d] / la;
+                R[6 + d] = n3[d] / ln;
+            }
+            R[3] = R[7] * R[2] - R[8] * R[1];   // e2 = e3 x e1
+            R[4] = R[8] * R[0] - R[6] * R[2];
+            R[5] = R[6] * R[1] - R[7] * R[0];
+            for (int r = 0; r < 3; ++r)          // rows of the rotated cell: R a_r
+                for (int d = 0; d < 3; ++d)
+                    bx[3 * r + d] = R[3 * d] * bx0[3 * r] + R[3 * d + 1] * bx0[3 * r + 1] + R[3 * d + 2] * bx0[3 * r + 2];
+            bx[1] = bx[2] = bx[5] = 0.0;         // zero by construction (rounding only)
+            for (int k = 0; k < 9; ++k) rs[k] = (float)R[k];
+            rs[9] = 1.f;
+        }
         const bool tri = bx[3] != 0 || bx[6] != 0 || bx[7] != 0 || bx[1] != 0 || bx[2] != 0 || bx[5] != 0;
-        if (tri && (bx[1] != 0 || bx[2] != 0 || bx[5] != 0))
-            return failb(b, QNEP_ERR_UNSUPPORTED,
-                         "general cells must have a along x and b in the xy plane (rotate the cell)");
         if (tri && !(bx[0] > 0 && bx[4] > 0 && bx[8] > 0))
             return failb(b, QNEP_ERR_ARG, "the cell vectors must be right-handed (a_x, b_y, c_z > 0)");
         double hinv[9];
@@ -310,6 +337,7 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
     CKB(upload(&b->d_st, sts));
     CKB(upload(&b->d_kt, kts));
     CKB(upload(&b->d_ktri, ktris));
+    CKB(upload(&b->d_rot, rot));
     CKB(upload(&b->d_chunk, chunks));
     CKB(upload(&b->d_kvec, kvec));
     CKB(upload(&b->d_kreal, kreal));
@@ -622,7 +650,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
                           b->cell_start, b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list,
                           b->cnt_list, b->nbr_ang, b->cnt_ang, b->phase, batch_phase_stride(b->nph_max), b->geo_rad,
                           b->geo_ang, b->bsum, batch_bstride(b->hp.n_species), tc ? b->bimg : nullptr,
-                          (float)b->es.alpha, b->d_status, st);
+                          (float)b->es.alpha, b->d_rot, b->d_status, st);
         b->geom_valid = true;
         b->geom_pos = positions;
         b->geom_types = types;
@@ -669,6 +697,7 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     a.bec = out->bec;
     a.total_charge = out->total_charge;
     a.polarization = out->polarization;
+    a.rot = b->d_rot;
     a.pos_in = positions;
     a.n_struct = n_struct;
     a.n_total = b->n_total;
@@ -879,7 +908,7 @@ qnep_status qnep_batch_set_params(qnep_batch* b, const float* params, void* stre
 void qnep_batch_destroy(qnep_batch* b) {
     if (!b) return;
     if (b->last_stream) cudaStreamSynchronize(b->last_stream);
-    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_ktri,   b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
+    void* ptrs[] = {b->d_pt,      b->d_st,     b->d_kt,       b->d_ktri,   b->d_rot,    b->d_chunk,  b->d_kvec,  b->d_kreal,     b->d_items_lpt,
                     b->d_items_nat, b->spos4,  b->sidx,       b->order,    b->spec_off,   b->cell_start,
                     b->nbr_list,  b->cnt_list, b->nbr_ang,    b->cnt_ang,  b->phase,      b->scratch,
                     b->geo_rad,   b->geo_ang,  b->bsum,     b->bimg,

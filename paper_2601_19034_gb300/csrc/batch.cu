@@ -120,12 +120,47 @@ __device__ __forceinline__ float wrap_coord(float x, float L, float invL) {
 
 // ---------------------------------------------------------------------------------
 // pre-pass 1: cells, stable cell order, species order
+// Position of input atom i of a structure as the pre-pass uses it: rotated by R (rows e1, e2, e3)
+// when the structure's general cell was rotated into the restricted form (rot: [S][12], R then a
+// flag), as given otherwise.
+__device__ __forceinline__ void prep_position(const float* __restrict__ pos, const float* __restrict__ rot, int s,
+                                              size_t i, float x[3]) {
+    const float p0 = pos[3 * i], p1 = pos[3 * i + 1], p2 = pos[3 * i + 2];
+    if (rot && rot[12 * s + 9] != 0.f) {
+        const float* R = rot + 12 * s;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = fmaf(R[3 * a + 2], p2, fmaf(R[3 * a + 1], p1, R[3 * a] * p0));
+        return;
+    }
+    x[0] = p0;
+    x[1] = p1;
+    x[2] = p2;
+}
+
+// Back to the input frame: v = R^T v' and Z = R^T Z' R (row-major 3 x 3)
+__device__ __forceinline__ float4 rot_back_vec(const float* __restrict__ R, float4 v) {
+    return make_float4(fmaf(R[6], v.z, fmaf(R[3], v.y, R[0] * v.x)), fmaf(R[7], v.z, fmaf(R[4], v.y, R[1] * v.x)),
+                       fmaf(R[8], v.z, fmaf(R[5], v.y, R[2] * v.x)), v.w);
+}
+__device__ __forceinline__ void rot_back_tensor(const float* __restrict__ R, float z[9]) {
+    float t[9];
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) t[3 * x + d] = fmaf(R[6 + x], z[6 + d], fmaf(R[3 + x], z[3 + d], R[x] * z[d]));
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) z[3 * x + y] = fmaf(t[3 * x + 2], R[6 + y], fmaf(t[3 * x + 1], R[3 + y], t[3 * x] * R[y]));
+}
+
 __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __restrict__ pos,
                                                              const int* __restrict__ types, int nmax, int n_species,
                                                              const BatchStruct* __restrict__ sts,
                                                              int* __restrict__ cell_start_all,
                                                              float4* __restrict__ spos4, int* __restrict__ sidx,
                                                              int* __restrict__ order, int* __restrict__ spec_off,
+                                                             const float* __restrict__ rot,
                                                              unsigned int* __restrict__ status) {
     extern __shared__ int psm[];
     const BatchStruct bs = sts[blockIdx.x];
@@ -142,8 +177,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __rest
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int cc[3];
         if (g.tri) {   // cells along the fractional axes; the position wrapped by lattice translations
-            const float x[3] = {pos[3 * (size_t)(off + i)], pos[3 * (size_t)(off + i) + 1],
-                                pos[3 * (size_t)(off + i) + 2]};
+            float x[3];
+            prep_position(pos, rot, blockIdx.x, (size_t)(off + i), x);
             float w[3];
             wrap_and_cell(g, x, w, cc);
         } else {
@@ -190,8 +225,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_batch_sort(const float* __rest
                 const int slot = base + __popc(mk & below);
                 float w[3];
                 if (g.tri) {
-                    const float x[3] = {pos[3 * (size_t)(off + i)], pos[3 * (size_t)(off + i) + 1],
-                                        pos[3 * (size_t)(off + i) + 2]};
+                    float x[3];
+                    prep_position(pos, rot, blockIdx.x, (size_t)(off + i), x);
                     int cd[3];
                     wrap_and_cell(g, x, w, cd);
                 } else {
@@ -2236,13 +2271,16 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
         // 6 outputs in input order, candidate-major: lanes over consecutive input atoms (through the
         // inverse of the sort permutation), so each warp writes contiguous rows of the outputs
         const bool zout = BEC && a.bec;
+        // a general cell rotated into the restricted form: forces and BEC back to the input frame
+        const float* Rot = (a.rot && a.rot[12 * item.x + 9] != 0.f) ? a.rot + 12 * item.x : nullptr;
         if ((a.forces || a.charges || zout) && n > a.inv_cap) {   // a structure too large for the permutation
             for (int i = threadIdx.x; i < n * CG; i += NW * 32) {
                 const int m = i >> 5, c = grp * CG + (i & 31);
                 if (c >= a.n_cand) continue;
                 const size_t gi = (size_t)off + __ldg(&a.sidx[off + m]);
                 if (a.forces) {
-                    const float4 F = fsum[i];
+                    float4 F = fsum[i];
+                    if (Rot) F = rot_back_vec(Rot, F);
                     float* fo = a.forces + ((size_t)c * a.n_total + gi) * 3;
                     fo[0] = F.x;
                     fo[1] = F.y;
@@ -2253,8 +2291,10 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                     const float4 z0 = zsum[(size_t)(3 * m) * CG + (i & 31)], z1 = zsum[(size_t)(3 * m + 1) * CG + (i & 31)];
                     const float z8 = zsum[(size_t)(3 * m + 2) * CG + (i & 31)].x;
                     float* zo = a.bec + ((size_t)c * a.n_total + gi) * 9;
-                    zo[0] = z0.x; zo[1] = z0.y; zo[2] = z0.z; zo[3] = z0.w;
-                    zo[4] = z1.x; zo[5] = z1.y; zo[6] = z1.z; zo[7] = z1.w; zo[8] = z8;
+                    float zz[9] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w, z8};
+                    if (Rot) rot_back_tensor(Rot, zz);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) zo[q] = zz[q];
                 }
             }
         } else if (a.forces || a.charges || zout) {
@@ -2270,7 +2310,8 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                 for (int g = lane; g < n; g += 32) {
                     const int i = inv[g] * CG + cl;
                     if (fo) {
-                        const float4 F = fsum[i];
+                        float4 F = fsum[i];
+                        if (Rot) F = rot_back_vec(Rot, F);
                         fo[3 * g] = F.x;
                         fo[3 * g + 1] = F.y;
                         fo[3 * g + 2] = F.z;
@@ -2281,21 +2322,43 @@ __global__ void __launch_bounds__(NW * 32, 8 / NW) k_batch_items(BatchArgs a) {
                         const float4 z0 = zsum[zm], z1 = zsum[zm + CG];
                         const float z8 = zsum[zm + 2 * CG].x;
                         float* zr = zo + 9 * (size_t)g;
-                        zr[0] = z0.x; zr[1] = z0.y; zr[2] = z0.z; zr[3] = z0.w;
-                        zr[4] = z1.x; zr[5] = z1.y; zr[6] = z1.z; zr[7] = z1.w; zr[8] = z8;
+                        float zz[9] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w, z8};
+                        if (Rot) rot_back_tensor(Rot, zz);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) zr[q] = zz[q];
                     }
                 }
             }
         }
         if (VIR && a.virial && warp == 1 && cand < a.n_cand) {
-            // W = sum over the warps' FP64 slots (entries, real space, k space), per candidate
+            // W = sum over the warps' FP64 slots (entries, real space, k space), per candidate;
+            // R^T W R back in the input frame for a rotated cell
+            double wt[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 double t = 0.0;
 #pragma unroll
                 for (int w = 0; w < NW; ++w) t += vacc[((size_t)w * 9 + q) * CG + lane];
-                a.virial[((size_t)cand * a.n_struct + item.x) * 9 + q] = t;
+                wt[q] = t;
             }
+            if (Rot) {
+                double o9[9];
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y) {
+                        double t = 0.0;
+#pragma unroll
+                        for (int u = 0; u < 3; ++u)
+#pragma unroll
+                            for (int v = 0; v < 3; ++v) t += (double)Rot[3 * u + x] * wt[3 * u + v] * (double)Rot[3 * v + y];
+                        o9[3 * x + y] = t;
+                    }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) wt[q] = o9[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a.virial[((size_t)cand * a.n_struct + item.x) * 9 + q] = wt[q];
         }
         if (warp == 0 && cand < a.n_cand) {
             double e = sums[lane] + sums[CG + lane];
@@ -2375,7 +2438,8 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
                        const BatchStruct* st, const BatchKTab* kt, const BatchKTri* ktri, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
-                       int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_) {
+                       int bstride, unsigned char* bimg, float alpha, const float* rot, unsigned int* status,
+                       cudaStream_t st_) {
     if (n_struct <= 0) return;
     const size_t sm1 = sizeof(int) * ((size_t)nmax + BATCH_MAX_CELLS + 1 + MAX_SPECIES + 1);
     const size_t sm2 = sizeof(int) * (size_t)(PREP_THREADS / 32) * (2 * cap_l + 2 * cap_a + 32 * TAB_P + 16);
@@ -2383,7 +2447,7 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
     if (sm1 > 48 * 1024) ensure_smem_attr(k_batch_sort, attr1, (int)sm1);
     if (sm2 > 48 * 1024) ensure_smem_attr(k_batch_lists, attr2, (int)sm2);
     k_batch_sort<<<n_struct, PREP_THREADS, sm1, st_>>>(pos, types, nmax, n_species, st, cell_start, spos4, sidx,
-                                                        order, spec_off, status);
+                                                        order, spec_off, rot, status);
     // about one warp per 32 atoms of the largest structure
     const int ysplit = std::max(1, std::min(64, (nmax + 32 * (PREP_THREADS / 32) - 1) / (32 * (PREP_THREADS / 32)) * 4));
     k_batch_lists<<<dim3(n_struct, ysplit), PREP_THREADS, sm2, st_>>>(n_species, st, kt, ktri, cell_start, spos4, cap_l, cap_a, nbr_list,

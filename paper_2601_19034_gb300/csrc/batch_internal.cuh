@@ -135,6 +135,7 @@ struct BatchArgs {
     double* total_charge;    // [n_cand][n_struct] or NULL (sum of q~ before the correction)
     double* polarization;    // [n_cand][n_struct][3] or NULL (P = sum q~^c_i r_i, positions as given)
     const float* pos_in;     // [N_total][3] the call's positions (for the polarization)
+    const float* rot;        // [n_struct][12]: R into the restricted cell form, then a flag (1: rotated)
     int n_struct;
     int n_total;
     int inv_cap;             // ints of shared memory for the outputs' inverse permutation (set at launch)
@@ -145,7 +146,8 @@ void launch_batch_prep(const float* pos, const int* types, int n_struct, int nma
                        const BatchStruct* st, const BatchKTab* kt, const BatchKTri* ktri, int* cell_start, float4* spos4, int* sidx,
                        int* order, int* spec_off, int cap_l, int cap_a, int* nbr_list, int* cnt_list, int* nbr_ang,
                        int* cnt_ang, float2* phase, int nph_stride, float* geo_rad, float* geo_ang, float* bsum,
-                       int bstride, unsigned char* bimg, float alpha, unsigned int* status, cudaStream_t st_);
+                       int bstride, unsigned char* bimg, float alpha, const float* rot, unsigned int* status,
+                       cudaStream_t st_);
 // Floats per atom of the basis sums: B^R padded to MAX_SPECIES species, then B^A of n_species.
 inline int batch_bstride(int n_species) { return MAX_SPECIES * KR + n_species * KA * NLM; }
 // Dynamic shared memory of the item kernel and its resident blocks per SM (0: does not fit).
