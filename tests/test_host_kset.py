@@ -94,3 +94,72 @@ def test_half_space_kset_matches_the_oracle(harness, lengths):
     for c in range(ncol):
         col = real[real[:, 0] == c][:, 3]
         assert len(col) and np.array_equal(col, np.arange(col.min(), col.max() + 1))
+
+
+HARNESS_BOX = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "kset_host.h"
+int main(int argc, char** argv) {
+    double box[9];
+    for (int k = 0; k < 9; ++k) box[k] = atof(argv[1 + k]);
+    qnep::KSet ks = qnep::build_kset_box(box, atof(argv[10]), atof(argv[11]));
+    int ncol = (int)ks.cols.size() - 1;
+    printf("%d %d %d %zu %zu\n", ncol, (int)ks.chunk_col.size(), (int)ks.cols[ncol].w, ks.kg.size(), ks.chunk_col.size());
+    for (int c = 0; c < ncol; ++c) {
+        int4 col = ks.cols[c];
+        int len = ks.cols[c + 1].w - col.w;
+        for (int t = 0; t < len; ++t) printf("%d %d %d %d %.9e\n", c, col.x, col.y, col.z + t, ks.kg[col.w + t]);
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness_box(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are not available")
+    d = tmp_path_factory.mktemp("kset_box")
+    src = d / "kset_box.cpp"
+    src.write_text(HARNESS_BOX)
+    exe = d / "kset_box"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2601_19034_gb300", "csrc"),
+                    "-I", CUDA_INC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    return str(exe)
+
+
+@pytest.mark.parametrize("box", [
+    [[12.42, 0.62, -0.5], [2.48, 12.42, 0.75], [-1.24, 1.86, 12.42]],     # every off-diagonal non-zero
+    [[12.97, 0.0, 0.0], [1.556, 12.97, 0.0], [-1.038, 1.297, 12.97]],     # the restricted form
+    [[0.0, 2.82, 2.82], [2.82, 0.0, 2.82], [2.82, 2.82, 0.0]],           # fcc primitive cell
+])
+def test_half_space_kset_of_a_general_cell_matches_the_oracle(harness_box, box):
+    """The k-set of a general cell (k = 2 pi H^-1 n, the tables of the sheared-cell Ewald paths)
+    against the oracle's full-sphere enumeration: one of each +-k pair, G(k) with V = |det H| to
+    FP32 rounding, padding with G = 0, contiguous n3 runs per column."""
+    box = np.asarray(box, dtype=np.float64)
+    alpha = 0.3
+    kmax = 2.0 * alpha * math.sqrt(math.log(1e6))
+    out = subprocess.run([harness_box, *[repr(float(x)) for x in box.ravel()], repr(kmax), repr(alpha)], check=True,
+                         capture_output=True, text=True).stdout.split("\n")
+    head = [int(x) for x in out[0].split()]
+    rows = np.array([[float(x) for x in ln.split()] for ln in out[1:] if ln.strip()])
+    ncol, nchunk, nk_padded = head[0], head[1], head[2]
+    assert nk_padded == 8 * nchunk and len(rows) == nk_padded
+    real = rows[rows[:, 4] > 0]
+    n = real[:, 1:4].astype(np.int64)
+    full = ewald.kspace_integers(box, kmax)
+    assert 2 * len(n) == len(full)
+    half = {tuple(v) for v in n}
+    assert len(half) == len(n)
+    for v in map(tuple, full):
+        assert (v in half) != (tuple(-x for x in v) in half)
+    k = 2 * math.pi * n @ np.linalg.inv(box).T
+    k2 = (k * k).sum(1)
+    g = (2 * math.pi / abs(np.linalg.det(box))) * np.exp(-k2 / (4 * alpha * alpha)) / k2
+    np.testing.assert_allclose(real[:, 4], g, rtol=2e-7)
+    for c in range(ncol):
+        col = real[real[:, 0] == c][:, 3]
+        assert len(col) and np.array_equal(col, np.arange(col.min(), col.max() + 1))
