@@ -176,24 +176,8 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         float* rs = rot.data() + 12 * (size_t)s;
         rs[0] = rs[4] = rs[8] = 1.f;
         if (bx[1] != 0 || bx[2] != 0 || bx[5] != 0) {
-            const double* av = bx0;
-            const double* bv = bx0 + 3;
-            const double la = std::sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
-            const double n3[3] = {av[1] * bv[2] - av[2] * bv[1], av[2] * bv[0] - av[0] * bv[2], av[0] * bv[1] - av[1] * bv[0]};
-            const double ln = std::sqrt(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2]);
-            if (!(la > 0) || !(ln > 0)) return failb(b, QNEP_ERR_ARG, "the cell vectors must be independent");
             double R[9];
-            for (int d = 0; d < 3; ++d) {
-                R[d] = av[d] / la;
-                R[6 + d] = n3[d] / ln;
-            }
-            R[3] = R[7] * R[2] - R[8] * R[1];   // e2 = e3 x e1
-            R[4] = R[8] * R[0] - R[6] * R[2];
-            R[5] = R[6] * R[1] - R[7] * R[0];
-            for (int r = 0; r < 3; ++r)          // rows of the rotated cell: R a_r
-                for (int d = 0; d < 3; ++d)
-                    bx[3 * r + d] = R[3 * d] * bx0[3 * r] + R[3 * d + 1] * bx0[3 * r + 1] + R[3 * d + 2] * bx0[3 * r + 2];
-            bx[1] = bx[2] = bx[5] = 0.0;         // zero by construction (rounding only)
+            if (!rotate_to_restricted(bx0, R, bx)) return failb(b, QNEP_ERR_ARG, "the cell vectors must be independent");
             for (int k = 0; k < 9; ++k) rs[k] = (float)R[k];
             rs[9] = 1.f;
         }

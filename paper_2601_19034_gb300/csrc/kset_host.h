@@ -21,6 +21,32 @@ struct KSet {
     std::vector<float> kg;        // G(k) = (2 pi / V) exp(-k^2 / 4 alpha^2) / k^2, 0 on padding
 };
 
+// A general cell (rows a, b, c) turned into the restricted form a' = (a_x, 0, 0),
+// b' = (b_x, b_y, 0), c' = (c_x, c_y, c_z): R has the rows e1 = a / |a|, e2 = e3 x e1,
+// e3 = a x b / |a x b| (a rotation: orthonormal rows, det +1), and the rows of the turned cell
+// are R a, R b, R c, with the entries zero by construction set to zero.  Returns false for a
+// degenerate cell (a = 0 or a parallel to b); a left-handed cell comes out with c'_z < 0.
+inline bool rotate_to_restricted(const double box[9], double R[9], double out[9]) {
+    const double* av = box;
+    const double* bv = box + 3;
+    const double la = std::sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+    const double n3[3] = {av[1] * bv[2] - av[2] * bv[1], av[2] * bv[0] - av[0] * bv[2], av[0] * bv[1] - av[1] * bv[0]};
+    const double ln = std::sqrt(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2]);
+    if (!(la > 0) || !(ln > 0)) return false;
+    for (int d = 0; d < 3; ++d) {
+        R[d] = av[d] / la;
+        R[6 + d] = n3[d] / ln;
+    }
+    R[3] = R[7] * R[2] - R[8] * R[1];   // e2 = e3 x e1
+    R[4] = R[8] * R[0] - R[6] * R[2];
+    R[5] = R[6] * R[1] - R[7] * R[0];
+    for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d)
+            out[3 * r + d] = R[3 * d] * box[3 * r] + R[3 * d + 1] * box[3 * r + 1] + R[3 * d + 2] * box[3 * r + 2];
+    out[1] = out[2] = out[5] = 0.0;
+    return true;
+}
+
 inline KSet build_kset(const double L[3], double kmax, double alpha) {
     const double two_pi = 6.283185307179586;
     const double vol = L[0] * L[1] * L[2];

@@ -163,3 +163,68 @@ def test_half_space_kset_of_a_general_cell_matches_the_oracle(harness_box, box):
     for c in range(ncol):
         col = real[real[:, 0] == c][:, 3]
         assert len(col) and np.array_equal(col, np.arange(col.min(), col.max() + 1))
+
+
+HARNESS_ROT = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "kset_host.h"
+int main(int argc, char** argv) {
+    double box[9], R[9], out[9];
+    for (int k = 0; k < 9; ++k) box[k] = atof(argv[1 + k]);
+    if (!qnep::rotate_to_restricted(box, R, out)) { printf("degenerate\n"); return 0; }
+    for (int k = 0; k < 9; ++k) printf("%.17g ", R[k]);
+    printf("\n");
+    for (int k = 0; k < 9; ++k) printf("%.17g ", out[k]);
+    printf("\n");
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness_rot(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are not available")
+    d = tmp_path_factory.mktemp("rot")
+    src = d / "rot.cpp"
+    src.write_text(HARNESS_ROT)
+    exe = d / "rot"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2601_19034_gb300", "csrc"),
+                    "-I", CUDA_INC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    return str(exe)
+
+
+def _rotate(exe, box):
+    out = subprocess.run([exe, *[repr(float(x)) for x in np.asarray(box).ravel()]], check=True,
+                         capture_output=True, text=True).stdout.split("\n")
+    if out[0].strip() == "degenerate":
+        return None, None
+    return (np.array([float(x) for x in out[0].split()]).reshape(3, 3),
+            np.array([float(x) for x in out[1].split()]).reshape(3, 3))
+
+
+def test_general_cell_rotation_into_the_restricted_form(harness_rot):
+    """The batched call's turn of a general cell into the restricted form: R is a rotation
+    (orthonormal, det +1), the turned rows are R a, R b, R c with a' along x and b' in the xy plane,
+    so lengths, angles and the volume are kept; a left-handed cell comes out with c'_z < 0, and a
+    cell with a parallel to b is reported as degenerate."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        box = np.diag(rng.uniform(8.0, 30.0, 3)) + rng.normal(0.0, 2.0, (3, 3))
+        if np.linalg.det(box) < 0:
+            box[2] = -box[2]
+        r, turned = _rotate(harness_rot, box)
+        np.testing.assert_allclose(r @ r.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(r) - 1.0) < 1e-13
+        np.testing.assert_allclose(turned, box @ r.T, atol=1e-12 * np.abs(box).max())
+        assert turned[0, 1] == 0.0 and turned[0, 2] == 0.0 and turned[1, 2] == 0.0
+        assert turned[0, 0] > 0 and turned[1, 1] > 0 and turned[2, 2] > 0
+        np.testing.assert_allclose(turned @ turned.T, box @ box.T, rtol=1e-12, atol=1e-10)
+        assert abs(np.linalg.det(turned) - np.linalg.det(box)) < 1e-10 * abs(np.linalg.det(box))
+    left = np.array([[20.0, 0.3, 0.2], [1.0, 20.0, 0.5], [0.4, 2.0, -20.0]])
+    _, turned = _rotate(harness_rot, left)
+    assert turned[2, 2] < 0
+    r, turned = _rotate(harness_rot, np.array([[10.0, 1.0, 0.0], [20.0, 2.0, 0.0], [0.0, 0.0, 10.0]]))
+    assert r is None
