@@ -81,6 +81,13 @@ def test_full_loss_rejects_unpaired_buffers_before_any_gpu_work(lib):
     assert fn(2, 1, dummy, 4, None, full, dummy, None, 0, w, dummy, dummy, None) == _lib.QNEP_ERR_ARG
 
 
+def test_static_geometry_switch_rejects_bad_arguments(lib):
+    """qnep_batch_set_static_geometry / qnep_batch_geometry_changed refuse a NULL batch (host-only
+    checks, no CUDA call; the enable flag's range needs a batch, so a device)."""
+    assert lib.qnep_batch_set_static_geometry(None, 1) == _lib.QNEP_ERR_ARG
+    assert lib.qnep_batch_geometry_changed(None) == _lib.QNEP_ERR_ARG
+
+
 def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
     """Host-side checks of the field-response and training entry points (no CUDA call is reached)."""
     dummy = ctypes.c_void_p(0x1000)       # never dereferenced: every call below returns before using it
