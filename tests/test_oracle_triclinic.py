@@ -11,6 +11,7 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 from oracle import ewald, forcecall, geometry
 from paper_2601_19034_gb300 import workloads as wl
@@ -112,3 +113,38 @@ def test_pppm_in_a_general_cell_energy_identity_and_mesh_virial():
         assert abs(fd - out["phi"][i]) < 1e-6
     w = virial.kspace_static_pppm(pos, box, q, mesh, 5, 0.3)
     np.testing.assert_allclose(w.sum(0), out["virial"], rtol=1e-10, atol=1e-10 * np.abs(out["virial"]).max())
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_virial_and_forces_in_a_general_cell_match_finite_differences(mode):
+    """In a fully sheared cell the force call's virial is -dU/d eps under the homogeneous strain of
+    positions and cell (central differences, +-1e-6) and its forces are -dU/dr (central
+    differences, 1e-4 A), Ewald modes 1 and 2: the general-cell images, k = 2 pi H^-1 n and the
+    volume enter both."""
+    s0 = wl.batio3_supercell(2, seed=41)
+    box = s0.box + np.array([[0.0, 0.4, -0.3], [0.7, 0.0, 0.5], [-0.6, 0.8, 0.0]])
+    pos = (s0.positions.astype(np.float64) @ np.linalg.inv(s0.box)) @ box
+    hp = wl.HParams(n_species=3)
+    blob = wl.random_params(hp, np.random.default_rng(42))[0]
+    elec = wl.Elec(mode=mode, kind="ewald", q_total=0.2)
+    out = forcecall.force_call(pos, box, s0.types, hp, blob, elec, want_bec=False)
+
+    def energy(p, b):
+        with torch.no_grad():
+            e, _, _ = forcecall.total_energy_autograd(p, b, s0.types, hp, blob, elec)
+        return float(e)
+
+    h = 1e-6
+    for a, b in ((0, 0), (2, 2), (0, 1), (1, 2), (2, 0)):
+        eps = np.zeros((3, 3))
+        eps[a, b] = h
+        dp, dm = np.eye(3) + eps, np.eye(3) - eps
+        w = -(energy(pos @ dp.T, box @ dp.T) - energy(pos @ dm.T, box @ dm.T)) / (2 * h)
+        assert abs(w - out["virial"][b, a]) < 1e-4 * max(1.0, abs(out["virial"][b, a])), (a, b)
+    hr = 1e-4
+    for i, d in ((0, 0), (7, 1), (23, 2)):
+        pp, pm = pos.copy(), pos.copy()
+        pp[i, d] += hr
+        pm[i, d] -= hr
+        f = -(energy(pp, box) - energy(pm, box)) / (2 * hr)
+        assert abs(f - out["forces"][i, d]) < 1e-5 * max(1.0, abs(f)), (i, d)
