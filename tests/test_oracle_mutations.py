@@ -351,3 +351,24 @@ def test_network_slips_fail_the_zero_weight_closed_form(monkeypatch, batio3_subc
         _fails(t_forces.test_network_with_zero_input_weights_is_a_closed_form, batio3_subcell)
     monkeypatch.undo()
     t_forces.test_network_with_zero_input_weights_is_a_closed_form(batio3_subcell)
+
+
+def test_general_cell_wave_vectors_with_h_inverse_transposed(monkeypatch):
+    """k = 2 pi n H^-1 (transposed) instead of 2 pi H^-1 n: the forces-and-virial differences in a
+    sheared cell cannot see it (energy and derivatives share it), the unimodular change of cell
+    and PPPM -> Ewald in a sheared box do."""
+    from tests import test_oracle_triclinic as t_tri
+
+    def wrong(pos, box, q, alpha, nvec):
+        inv = torch.linalg.inv(box)
+        kv = 2.0 * math.pi * torch.as_tensor(nvec, dtype=torch.float64) @ inv
+        k2 = (kv * kv).sum(1)
+        omega = torch.abs(torch.linalg.det(box))
+        g = (2.0 * math.pi / omega) * torch.exp(-k2 / (4.0 * alpha * alpha)) / k2
+        phase = pos @ kv.T
+        s_re = (q[:, None] * torch.cos(phase)).sum(0)
+        s_im = -(q[:, None] * torch.sin(phase)).sum(0)
+        return ewald.KE * (g * (s_re * s_re + s_im * s_im)).sum()
+    monkeypatch.setattr(ewald, "reciprocal_energy", wrong)
+    _fails(t_tri.test_unimodular_change_of_cell_leaves_the_force_call_unchanged, 1)
+    _fails(t_tri.test_pppm_in_a_general_cell_converges_to_ewald)
