@@ -150,12 +150,13 @@ def _batch_seed(rank: int) -> int:
 
 
 def _ewald_kcount(box, kmax):
-    """Half-space k vectors with |k| < kmax (for the algorithmic operation count)."""
-    lengths = np.diag(box)
-    nmax = [int(math.floor(kmax * ln / (2 * math.pi))) for ln in lengths]
+    """Half-space k vectors with |k| < kmax (for the algorithmic operation count), k = 2 pi H^-1 n
+    for the cell with rows H (any cell; |n_d| <= kmax |a_d| / 2 pi)."""
+    box = np.asarray(box, dtype=np.float64)
+    nmax = [int(math.floor(kmax * np.linalg.norm(box[d]) / (2 * math.pi))) for d in range(3)]
     g = np.meshgrid(*[np.arange(-m, m + 1) for m in nmax], indexing="ij")
     n = np.stack([x.ravel() for x in g], 1)
-    k = 2 * math.pi * n / lengths
+    k = 2 * math.pi * n @ np.linalg.inv(box).T
     k2 = (k * k).sum(1)
     return int(((k2 > 0) & (k2 < kmax * kmax)).sum()) // 2
 
@@ -483,7 +484,7 @@ def _batch_flop(systems, hp, elec, n_cand):
     S = hp.n_species
     total = 0.0
     for sy in systems:
-        vol = float(np.prod(np.diag(sy.box)))
+        vol = abs(float(np.linalg.det(np.asarray(sy.box, dtype=np.float64))))
         rho = sy.n_atoms / vol
         n_r = 4.0 / 3.0 * math.pi * hp.rc_radial ** 3 * rho
         n_a = 4.0 / 3.0 * math.pi * hp.rc_angular ** 3 * rho
