@@ -325,7 +325,8 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * Many structures of uneven size, each under many candidate parameter vectors:
  * the shape of a separable natural-evolution-strategy fitness evaluation, where
  * every candidate of the population is scored on every training structure
- * (Sec. II.E; the training loss weighs energies, forces and charges).  One call
+ * (Sec. II.E; the training loss weighs energies, forces, virials, BEC and total
+ * charges).  One call
  * returns, for every (candidate c, structure s), the total energy U^tot
  * (Eq. U_i, Eq. U_ES with the charges of Sec. II.D), the forces including the
  * charge-derivative terms (Sec. II.C) and the corrected charges q^c.
@@ -356,8 +357,8 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * launch.  A graph captured from a call keeps that call's workspaces: re-capture it
  * after a call that reallocated them (a new description, a capacity change, a
  * launch shape with more resident blocks).  Asking for BEC allocates its accumulators
- * in a buffer of their own, so it does not move the workspaces of calls without BEC.  Errors in the arguments return before any GPU work; device-side
- * conditions (list overflow, a species index out of range) are reported by
+ * in a buffer of their own, so it does not move the workspaces of calls without BEC.
+ * Errors in the arguments return before any GPU work; device-side conditions (list overflow, a species index out of range) are reported by
  * qnep_batch_sync_status (QNEP_ERR_NBR_OVERFLOW: raise the capacity with
  * qnep_batch_set_capacity and call again; outputs of that call are invalid).
  * Caller owns every buffer; the batch owns its device copies and workspaces. */
