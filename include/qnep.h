@@ -358,8 +358,9 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  * after a call that reallocated them (a new description, a capacity change, a
  * launch shape with more resident blocks).  Asking for BEC allocates its accumulators
  * in a buffer of their own, so it does not move the workspaces of calls without BEC.
- * Errors in the arguments return before any GPU work; device-side conditions (list overflow, a species index out of range) are reported by
- * qnep_batch_sync_status (QNEP_ERR_NBR_OVERFLOW: raise the capacity with
+ * Errors in the arguments return before any GPU work; device-side conditions (list
+ * overflow, a species index out of range) are reported by qnep_batch_sync_status
+ * (QNEP_ERR_NBR_OVERFLOW: raise the capacity with
  * qnep_batch_set_capacity and call again; outputs of that call are invalid).
  * Caller owns every buffer; the batch owns its device copies and workspaces. */
 typedef struct qnep_batch qnep_batch;
