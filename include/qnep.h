@@ -434,8 +434,9 @@ qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
  * (the next call then rebuilds); with qnep_batch_compute_host the promise covers the host
  * positions and types.  A change between the FP32 and the tensor-core contraction rebuilds.
  * Neighbour overflow and species errors are reported by the call that built the geometry.
- * A call captured in a CUDA graph while the geometry is kept contains no pre-pass.  enable = 0 (the default) runs the pre-pass in every call.  QNEP_ERR_ARG for a NULL
- * batch or an enable outside {0, 1}.  No GPU work. */
+ * A call captured in a CUDA graph while the geometry is kept contains no pre-pass.  enable = 0
+ * (the default) runs the pre-pass in every call.  QNEP_ERR_ARG for a NULL batch or an enable
+ * outside {0, 1}.  No GPU work. */
 qnep_status qnep_batch_set_static_geometry(qnep_batch* b, int enable);
 qnep_status qnep_batch_geometry_changed(qnep_batch* b);
 /* Descriptor contraction of the batched call: the angular expansion coefficients
