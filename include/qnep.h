@@ -147,6 +147,9 @@ qnep_status qnep_reserve(qnep_model* m, int n_atoms, const double box[9]);
  *              k = 2 pi H^-1 n (Sec. II.B); PPPM puts its mesh along the lattice vectors (an
  *              atom's mesh coordinates N_d (r H^-1)_d) and takes the three field components as
  *              fractional gradients mapped to Cartesian ones by H^-1 at the interpolation.
+ *              Ewald: at most 159 phase factors per atom, (n1 + 1) + (2 n2 + 1) + (2 n3 + 8)
+ *              rounded up to odd with n_d = floor(kmax |a_d| / 2 pi); a larger k-set returns
+ *              QNEP_ERR_UNSUPPORTED before it is enumerated.
  *   stream:    cudaStream_t (NULL = legacy default stream)
  * Asynchronous: returns after enqueueing.  Device-side errors (neighbour
  * overflow) are recorded in scalars[QNEP_S_STATUS] and returned by the next
@@ -348,7 +351,9 @@ qnep_status qnep_ewald_kspace_noalloc(int n_atoms, const float* positions, const
  *                 (rows of R: a / |a|, (a x b) x a / |..|, a x b / |a x b|), its positions rotated
  *                 as they are read, and forces, virial and BEC rotated back (R^T F, R^T W R,
  *                 R^T Z R): every output is in the input frame.  Every perpendicular width >= the
- *                 neighbour-list cutoff; at most 32768 atoms per structure
+ *                 neighbour-list cutoff; at most 32768 atoms per structure; at most 94 Ewald phase
+ *                 factors per atom, (n1 + 1) + (2 n2 + 1) + (2 n3 + 8) with
+ *                 n_d = floor(kmax |a_d| / 2 pi) (QNEP_ERR_UNSUPPORTED before any work otherwise)
  *   energy:       device [n_candidates][n_struct] doubles (eV)
  *   forces:       device [n_candidates][N_total][3] float32 (eV/A), or NULL
  *   charges:      device [n_candidates][N_total] float32 (e), or NULL

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -325,9 +326,14 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
         if (!(L[d] > 0)) return fail(m, QNEP_ERR_ARG, "box edge must be positive");
         if (width[d] < rcl) return fail(m, QNEP_ERR_UNSUPPORTED, "cell width shorter than the list cutoff");
     }
+    // the Ewald phase-factor count (rounded up to odd) is known from n_max alone: refuse before
+    // enumerating the k-set and before any state of the previous box is touched
+    if (m->es.mode != 0 && m->es.kind == QNEP_EWALD && kset_phase_count(L, m->es.kmax) > EWALD_MAX_NPH)
+        return fail(m, QNEP_ERR_UNSUPPORTED, "k_max * box edge too large for the Ewald phase tables");
     bool box_changed = !m->have_box || std::memcmp(m->box, box, sizeof(double) * 9) != 0;
     if (box_changed) {
         if (m->have_box) CK(cudaStreamSynchronize(st));   // in-flight kernels may read the old tables
+        m->have_box = false;   // until every table of the new box is built (a failure below rebuilds next call)
         Geom& g = m->geom;
         g.ncells = 1;
         g.tri = tri ? 1 : 0;
@@ -355,7 +361,12 @@ qnep_status prepare(qnep_model* m, int n, const double* box, cudaStream_t st) {
             m->ncell_alloc = g.ncells + 1;
         }
         if (m->es.mode != 0 && m->es.kind == QNEP_EWALD) {
-            qnep_status s = build_ewald_table(m, L, box, tri);
+            qnep_status s;
+            try {
+                s = build_ewald_table(m, L, box, tri);
+            } catch (const std::bad_alloc&) {   // host tables: no exception crosses the C ABI
+                s = fail(m, QNEP_ERR_OOM, "host memory for the k-set could not be obtained");
+            }
             if (s != QNEP_OK) return s;
             int groups = (m->tab.nchunk + 31) / 32 + 1;
             if (groups > m->sk_done_alloc) {
@@ -515,9 +526,9 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
     if (n_params != per * (size_t)n_candidates) return QNEP_ERR_ARG;
     if (es->mode < 0 || es->mode > 2) return QNEP_ERR_ARG;
     if (es->mode != 0) {
-        if (!(es->alpha > 0)) return QNEP_ERR_ARG;
+        if (!(es->alpha > 0) || !std::isfinite(es->alpha)) return QNEP_ERR_ARG;
         if (es->kind != QNEP_EWALD && es->kind != QNEP_PPPM) return QNEP_ERR_ARG;
-        if (es->kind == QNEP_EWALD && !(es->kmax > 0)) return QNEP_ERR_ARG;
+        if (es->kind == QNEP_EWALD && (!(es->kmax > 0) || !std::isfinite(es->kmax))) return QNEP_ERR_ARG;
         if (es->kind == QNEP_PPPM) {
             if (es->order != 5) return QNEP_ERR_UNSUPPORTED;
             for (int d = 0; d < 3; ++d)

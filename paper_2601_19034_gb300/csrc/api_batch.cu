@@ -6,6 +6,7 @@
 #include <cstring>
 #include <array>
 #include <map>
+#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -230,6 +231,9 @@ qnep_status describe(qnep_batch* b, int n_struct, const int* off, const double* 
         for (int k = 0; k < 9; ++k) key[k] = bx[k];
         auto it = tab_of.find(key);
         if (it == tab_of.end()) {
+            // the phase-factor count is known from n_max alone: refuse before enumerating the k-set
+            if (kset_phase_count(L, b->es.kmax) > BATCH_MAX_NPH)
+                return failb(b, QNEP_ERR_UNSUPPORTED, "box too large for the batched k-space tables");
             KSet ks = tri ? build_kset_box(bx, b->es.kmax, b->es.alpha) : build_kset(L, b->es.kmax, b->es.alpha);
             BatchKTab kt{};
             kt.n1max = ks.nmax[0];
@@ -460,7 +464,8 @@ qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const fl
     if (n_params != per * (size_t)n_candidates) return QNEP_ERR_ARG;
     if (es->mode != 1 && es->mode != 2) return QNEP_ERR_UNSUPPORTED;
     if (es->kind != QNEP_EWALD) return QNEP_ERR_UNSUPPORTED;
-    if (!(es->alpha > 0) || !(es->kmax > 0)) return QNEP_ERR_ARG;
+    if (!(es->alpha > 0) || !(es->kmax > 0) || !std::isfinite(es->alpha) || !std::isfinite(es->kmax))
+        return QNEP_ERR_ARG;
     if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
     for (size_t k = 0; k < n_params; ++k)
         if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
@@ -579,7 +584,12 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
         return failb(b, QNEP_ERR_ARG, "positions and types are required");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!same_desc(b, n_struct, atom_offsets, boxes)) {
-        qnep_status s = describe(b, n_struct, atom_offsets, boxes, st);
+        qnep_status s;
+        try {
+            s = describe(b, n_struct, atom_offsets, boxes, st);
+        } catch (const std::bad_alloc&) {   // host tables: no exception crosses the C ABI
+            s = failb(b, QNEP_ERR_OOM, "host memory for the batch description could not be obtained");
+        }
         if (s != QNEP_OK) {
             b->have_desc = false;
             return s;

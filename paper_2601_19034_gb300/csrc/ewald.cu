@@ -92,6 +92,8 @@ constexpr int SK_WARPS = 8;
 constexpr int SK_T = 4;       // atoms per warp tile (one bulk copy of their phase rows)
 constexpr int SK_NB = 4;      // tile buffers in each warp's copy ring
 constexpr int SK_SPAN = 512;  // at most this many atoms per block (FP32 partial sums)
+static_assert(sizeof(float2) * SK_T * SK_NB * SK_WARPS * EWALD_MAX_NPH <= 160 * 1024,
+              "the largest accepted phase rows fit the structure-factor kernel's copy rings");
 
 // One thread = one 8-wide chunk of a column.  A block takes at most 512 atoms; they are
 // cut into tiles of 4 whose phase rows are contiguous in global memory, and warp w

@@ -47,6 +47,21 @@ inline bool rotate_to_restricted(const double box[9], double R[9], double out[9]
     return true;
 }
 
+// Phase factors per atom of the k-set whose axes have the lengths len[3] (the edges of an
+// orthorhombic cell, the row lengths |a_d| of a general one): (n1max + 1) + (2 n2max + 1) +
+// (2 n3max + 8), with n_d max = floor(k_max len_d / 2 pi) formed as the builders below form it, but
+// in double and before any enumeration, so that a huge k_max * length is refused without an int
+// overflow or a long host loop.  +inf when a product is not finite.
+inline double kset_phase_count(const double len[3], double kmax) {
+    const double two_pi = 6.283185307179586;
+    double nm[3];
+    for (int d = 0; d < 3; ++d) {
+        nm[d] = std::floor(kmax * len[d] / two_pi);
+        if (!std::isfinite(nm[d])) return HUGE_VAL;
+    }
+    return (nm[0] + 1) + (2 * nm[1] + 1) + (2 * nm[2] + 8);
+}
+
 inline KSet build_kset(const double L[3], double kmax, double alpha) {
     const double two_pi = 6.283185307179586;
     const double vol = L[0] * L[1] * L[2];

@@ -125,6 +125,11 @@ struct FieldIn {
     const int* sidx;        // input index of each sorted atom (for gq)
 };
 
+// Phase factors per atom (the odd row length nph below) that the single-structure Ewald kernels
+// hold in shared memory: the structure-factor kernel's copy rings take 1 KB per phase factor
+// within its 160 KB opt-in.  A k-set with more is refused on the host before it is enumerated.
+constexpr int EWALD_MAX_NPH = 159;
+
 // Ewald k-space description (host-built, uploaded when the box changes).
 //  Half space of wave vectors k = 2 pi (n1/Lx, n2/Ly, n3/Lz), |k| < kmax, grouped
 //  in columns (n1, n2) holding the contiguous run n3 in [lo, hi].  Each column is

@@ -10,7 +10,8 @@
   the sheared BaTiO3 cell and a sheared 64-water box against the oracle's general-cell PPPM,
   every output including the per-atom virial's mesh term, both kernel families.
 * Boxes the library does not take are refused: a left-handed cell, a cell narrower than the
-  cutoff.
+  cutoff, a cell whose Ewald k-set needs more phase factors per atom than the kernels hold; the
+  model keeps computing the cell it had.
 """
 import numpy as np
 import pytest
@@ -112,12 +113,13 @@ def test_unimodular_change_of_cell_on_the_gpu(dev):
 
 def test_boxes_that_are_refused(dev):
     from paper_2601_19034_gb300 import _lib
-    from paper_2601_19034_gb300.qnep import QNEP
+    from paper_2601_19034_gb300.qnep import QNEP, parse_scalars
     sysm = _sheared_batio3()
     hp = wl.HParams(n_species=3)
     params = wl.random_params(hp, np.random.default_rng(67))[0]
     pos, typ = torch.tensor(sysm.positions, device=dev), torch.tensor(sysm.types, device=dev)
     m = QNEP(hp, params, wl.Elec(mode=1, kind="ewald"))
+    before = parse_scalars(m.compute(pos, typ, sysm.box)["scalars"])["energy"]
     left = sysm.box[[1, 0, 2]]                     # rows swapped: left-handed
     with pytest.raises(_lib.QnepError) as e:
         m.compute(pos, typ, left)
@@ -127,6 +129,13 @@ def test_boxes_that_are_refused(dev):
     with pytest.raises(_lib.QnepError) as e:
         m.compute(pos, typ, thin)
     assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    big = 12.0 * sysm.box                          # k_max |a_d| / 2 pi ~ 50: over 159 phase factors per atom
+    with pytest.raises(_lib.QnepError) as e:
+        m.compute(pos, typ, big)
+    assert e.value.status == _lib.QNEP_ERR_UNSUPPORTED
+    # the refusals leave the model's tables alone: the cell it had still computes the same energy
+    after = parse_scalars(m.compute(pos, typ, sysm.box)["scalars"])["energy"]
+    assert abs(after - before) / sysm.n_atoms <= 1e-6
     m.close()
 
 

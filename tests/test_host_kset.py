@@ -8,6 +8,7 @@ FP32 rounding, the padding entries carry G = 0, and the columns hold contiguous 
 """
 import math
 import os
+import re
 import shutil
 import subprocess
 
@@ -228,3 +229,90 @@ def test_general_cell_rotation_into_the_restricted_form(harness_rot):
     assert turned[2, 2] < 0
     r, turned = _rotate(harness_rot, np.array([[10.0, 1.0, 0.0], [20.0, 2.0, 0.0], [0.0, 0.0, 10.0]]))
     assert r is None
+
+
+HARNESS_COUNT = r"""
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include "kset_host.h"
+// argv: 9 box entries, k_max, alpha, build (1: also enumerate the set and count from its n_max)
+int main(int argc, char** argv) {
+    double box[9];
+    for (int k = 0; k < 9; ++k) box[k] = atof(argv[1 + k]);
+    const double kmax = atof(argv[10]), alpha = atof(argv[11]);
+    const bool tri = box[1] != 0 || box[2] != 0 || box[3] != 0 || box[5] != 0 || box[6] != 0 || box[7] != 0;
+    double len[3];
+    for (int d = 0; d < 3; ++d) {
+        const double* a = box + 3 * d;
+        len[d] = tri ? std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) : box[4 * d];
+    }
+    const double pre = qnep::kset_phase_count(len, kmax);
+    printf("%.17g\n", pre);
+    if (atoi(argv[12])) {
+        qnep::KSet ks = tri ? qnep::build_kset_box(box, kmax, alpha) : qnep::build_kset(len, kmax, alpha);
+        printf("%d\n", (ks.nmax[0] + 1) + (2 * ks.nmax[1] + 1) + (2 * ks.nmax[2] + 8));
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness_count(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are not available")
+    d = tmp_path_factory.mktemp("kset_count")
+    src = d / "kset_count.cpp"
+    src.write_text(HARNESS_COUNT)
+    exe = d / "kset_count"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2601_19034_gb300", "csrc"),
+                    "-I", CUDA_INC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    return str(exe)
+
+
+def _count(exe, box, kmax, build):
+    out = subprocess.run([exe, *[repr(float(x)) for x in np.asarray(box, dtype=np.float64).ravel()], repr(kmax),
+                          "0.3", "1" if build else "0"], check=True, capture_output=True, text=True,
+                         timeout=30).stdout.split()
+    return float(out[0]), (int(out[1]) if build else None)
+
+
+def test_phase_count_is_known_before_the_enumeration(harness_count):
+    """The phase-factor count per atom that both force calls check against their shared-memory
+    limits before they enumerate a k-set: equal to the count from the n_max the builders find, for
+    orthorhombic and general cells, and over every limit (without an int overflow or a long loop)
+    when k_max times an edge is huge or not finite."""
+    alpha = 0.3
+    kmax = 2.0 * alpha * math.sqrt(math.log(1e6))
+    boxes = [np.diag([12.42, 12.42, 12.42]), np.diag([12.97, 25.94, 40.0]),
+             [[12.42, 0.62, -0.5], [2.48, 12.42, 0.75], [-1.24, 1.86, 12.42]],
+             [[12.97, 0.0, 0.0], [1.556, 12.97, 0.0], [-1.038, 1.297, 12.97]],
+             [[0.0, 2.82, 2.82], [2.82, 0.0, 2.82], [2.82, 2.82, 0.0]]]
+    for box in boxes:
+        pre, built = _count(harness_count, box, kmax, True)
+        assert pre == built
+        # by hand: n_d = floor(k_max |a_d| / 2 pi)
+        nd = [math.floor(kmax * np.linalg.norm(row) / (2 * math.pi)) for row in np.asarray(box, dtype=np.float64)]
+        assert built == (nd[0] + 1) + (2 * nd[1] + 1) + (2 * nd[2] + 8)
+    for kbig in (1e3, 1e12, 1e300, float("inf")):
+        pre, _ = _count(harness_count, np.diag([10.0, 10.0, 10.0]), kbig, False)
+        assert pre > 1e3
+
+
+def test_documented_phase_limits_match_the_kernels():
+    """The limits the C header states for the two Ewald force calls are the constants the host code
+    checks against."""
+    with open(os.path.join(ROOT, "include", "qnep.h")) as f:
+        header = " ".join(" ".join(ln.strip().lstrip("*") for ln in f).split())   # comment text, one line
+    csrc = os.path.join(ROOT, "paper_2601_19034_gb300", "csrc")
+    with open(os.path.join(csrc, "batch_internal.cuh")) as f:
+        batch = f.read()
+    with open(os.path.join(csrc, "qnep_internal.cuh")) as f:
+        single = f.read()
+    nb = int(re.search(r"constexpr int BATCH_MAX_NPH = (\d+);", batch).group(1))
+    ns = int(re.search(r"constexpr int EWALD_MAX_NPH = (\d+);", single).group(1))
+    assert f"at most {nb} Ewald phase factors per atom" in header
+    assert f"Ewald: at most {ns} phase factors per atom" in header
+    assert ns % 2 == 1   # the single-structure rows are rounded up to an odd length
