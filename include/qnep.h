@@ -438,7 +438,9 @@ qnep_status qnep_batch_get_config(const qnep_batch* b, int* warps, int* order);
  * behind positions and types does not change meanwhile, or calls qnep_batch_geometry_changed
  * (the next call then rebuilds); with qnep_batch_compute_host the promise covers the host
  * positions and types.  A change between the FP32 and the tensor-core contraction rebuilds.
- * Neighbour overflow and species errors are reported by the call that built the geometry.
+ * Neighbour overflow and species errors of the pre-pass are reported by the call that built the
+ * geometry and by every call that reuses it (the pre-pass keeps its own status word); a
+ * qnep_batch_sync_status that reports one ends the reuse, so the next call rebuilds.
  * A call captured in a CUDA graph while the geometry is kept contains no pre-pass.  enable = 0
  * (the default) runs the pre-pass in every call.  QNEP_ERR_ARG for a NULL batch or an enable
  * outside {0, 1}.  No GPU work. */

@@ -83,7 +83,8 @@ struct qnep_batch {
     BatchScratch sc{};
     float* scratch = nullptr;
     unsigned int* d_work = nullptr;
-    unsigned int* d_status = nullptr;
+    unsigned int* d_status = nullptr;       // [0] this call's kernels, [1] the pre-pass that built the
+                                            // lists in use (kept, with them, while static geometry is reused)
     cudaStream_t last_stream = nullptr;
     std::map<std::tuple<int, int, int, int>, int> per_sm_cache;   // (warps, nph_max, contract, 0 | virial 1 | BEC 2) -> blocks per SM
     // host-buffer entry point: device copies of the inputs and outputs (grown on demand)
@@ -490,7 +491,8 @@ qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const fl
     if (cudaMalloc((void**)&b->d_pt, sizeof(float) * pt.size()) != cudaSuccess ||
         cudaMemcpy(b->d_pt, pt.data(), sizeof(float) * pt.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMalloc((void**)&b->d_work, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_status, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc((void**)&b->d_status, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(b->d_status, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
         qnep_batch_destroy(b);
         return QNEP_ERR_CUDA;
     }
@@ -613,8 +615,14 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
     const int slots = per_sm * b->num_sms;
     qnep_status s = ensure_scratch(b, slots, bec, st);
     if (s != QNEP_OK) return s;
+    // (the tensor-core form's pre-pass writes the B^A operand images instead of the FP32 B^A sums:
+    // a change of contraction family rebuilds)
+    const bool reuse = b->static_geom && b->geom_valid && b->geom_pos == positions && b->geom_types == types &&
+                       b->geom_tc == tc;
     CKB(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned int), st));
-    CKB(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned int), st));
+    // a reused pre-pass keeps its status word: an overflow it recorded is reported by every call
+    // that reads its lists
+    CKB(cudaMemsetAsync(b->d_status, 0, (reuse ? 1 : 2) * sizeof(unsigned int), st));
     if (b->has_empty) {   // structures without atoms have no item: their energies (and virials) are zero
         CKB(cudaMemsetAsync(energy, 0, sizeof(double) * (size_t)b->n_cand * n_struct, st));
         if (virial) CKB(cudaMemsetAsync(virial, 0, sizeof(double) * 9 * (size_t)b->n_cand * n_struct, st));
@@ -635,16 +643,12 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
         }
         CKB(cudaEventRecord(b->ev[0], st));
     }
-    // (the tensor-core form's pre-pass writes the B^A operand images instead of the FP32 B^A sums:
-    // a change of contraction family rebuilds)
-    const bool reuse = b->static_geom && b->geom_valid && b->geom_pos == positions && b->geom_types == types &&
-                       b->geom_tc == tc;
     if (!reuse) {
         launch_batch_prep(positions, types, n_struct, b->nmax, b->hp.n_species, b->d_st, b->d_kt, b->d_ktri,
                           b->cell_start, b->spos4, b->sidx, b->order, b->spec_off, b->cap_l, b->cap_a, b->nbr_list,
                           b->cnt_list, b->nbr_ang, b->cnt_ang, b->phase, batch_phase_stride(b->nph_max), b->geo_rad,
                           b->geo_ang, b->bsum, batch_bstride(b->hp.n_species), tc ? b->bimg : nullptr,
-                          (float)b->es.alpha, b->d_rot, b->d_status, st);
+                          (float)b->es.alpha, b->d_rot, b->d_status + 1, st);
         b->geom_valid = true;
         b->geom_pos = positions;
         b->geom_types = types;
@@ -710,9 +714,10 @@ qnep_status qnep_batch_compute_outputs(qnep_batch* b, int n_struct, const int* a
 qnep_status qnep_batch_sync_status(qnep_batch* b) {
     if (!b) return QNEP_ERR_ARG;
     CKB(cudaStreamSynchronize(b->last_stream));
-    unsigned int h = 0;
-    CKB(cudaMemcpy(&h, b->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost));
-    const qnep_status s = qnep_status_from_device_bits(h);
+    unsigned int w[2] = {0u, 0u};
+    CKB(cudaMemcpy(w, b->d_status, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    if (w[1]) b->geom_valid = false;   // kept geometry with an error: the next call rebuilds it
+    const qnep_status s = qnep_status_from_device_bits(w[0] | w[1]);
     if (s == QNEP_ERR_ARG) return failb(b, s, "a species index is outside [0, n_species)");
     if (s == QNEP_ERR_NBR_OVERFLOW) return failb(b, s, "neighbour list capacity exceeded");
     if (s == QNEP_ERR_TIMEOUT)

@@ -278,3 +278,37 @@ def test_static_geometry_keeps_the_prepass_and_follows_changes(dev):
     b.set_contraction("fp32")                                       # FP32 B^A sums are built anew
     same(b.compute(pd, td, off, boxes), full(params2, pd, "fp32"))
     b.close()
+
+
+def test_static_geometry_reports_the_kept_prepass_status(dev):
+    """A list overflow recorded by the pre-pass whose geometry is kept is reported by the calls
+    that reuse it, not only by the call that built it; the report ends the reuse (the next call
+    runs the pre-pass again), and with capacities from the density again the outputs are those of
+    a fresh batch."""
+    from paper_2601_19034_gb300 import _lib
+    from paper_2601_19034_gb300.qnep import QNEPBatch, stack_structures
+    from tests.test_gpu_batch import _llzo
+    systems = [_llzo((1, 1, 1), 151)]
+    hp = wl.HParams(n_species=4)
+    params = wl.random_params(hp, np.random.default_rng(152), n_candidates=2)
+    elec = wl.Elec(mode=1, kind="ewald")
+    pos, typ, off, boxes = stack_structures(systems)
+    pd, td = _t(pos, dev), _t(typ, dev)
+    b = QNEPBatch(hp, params, elec)
+    b.set_static_geometry(True)
+    b.set_capacity(32, 16)             # ~80 neighbours within 6 A and ~24 within 4 A in LLZO: both overflow
+    out = b.outputs(1, pos.shape[0], dev)
+    b.compute_into(pd, td, off, boxes, out)                         # builds the kept geometry, unchecked
+    b.compute_into(pd, td, off, boxes, out)                         # reuses it
+    assert b.sync_status() == _lib.QNEP_ERR_NBR_OVERFLOW
+    b.compute_into(pd, td, off, boxes, out)                         # the pre-pass runs again
+    assert b.sync_status() == _lib.QNEP_ERR_NBR_OVERFLOW
+    b.set_capacity(0, 0)                                            # capacities from the density
+    got = b.compute(pd, td, off, boxes)
+    fresh = QNEPBatch(hp, params, elec)
+    ref = fresh.compute(pd, td, off, boxes)
+    assert (got["energy"] - ref["energy"]).abs().max().item() / pos.shape[0] <= 1e-9
+    assert (got["forces"] - ref["forces"]).abs().max().item() <= 1e-5
+    assert (got["charges"] - ref["charges"]).abs().max().item() <= 1e-6
+    fresh.close()
+    b.close()
