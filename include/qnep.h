@@ -187,7 +187,8 @@ qnep_status qnep_compute_vjp(qnep_model* m, int n_atoms, const float* positions,
 
 /* NVE molecular dynamics (velocity Verlet) around the force call.  Runs n_steps steps of
  * dt_fs femtoseconds from the given state; the force call of this model (its
- * precision and electrostatics) is evaluated at every step, neighbour lists rebuilt.
+ * precision and electrostatics) is evaluated at every step, neighbour lists rebuilt at every
+ * step or, with qnep_set_skin, kept while no atom has moved more than half the skin.
  *   positions, velocities: device [N][3] float32 (A, A/fs), updated in place
  *   types: device [N] int32; masses: host [n_species] doubles (amu)
  *   forces: device [N][3] float32, left holding the forces of the final positions
@@ -250,7 +251,10 @@ qnep_status qnep_set_capacity(qnep_model* m, int cap_list, int cap_angular);
  * CUDA graph once the lists exist).  A new box, atom count or capacity forces a rebuild; atom
  * types must not change while a list is kept (call qnep_set_skin again to force a rebuild).
  * skin = 0 (the default) rebuilds the lists at every call.  QNEP_ERR_ARG for a negative,
- * non-finite or > 5 A skin.  List overflow is reported as for qnep_compute.
+ * non-finite or > 5 A skin.  List overflow is reported as for qnep_compute; an overflow of the
+ * kept candidate lists (capacity: the list capacity scaled by the volume ratio of the two
+ * cutoffs) is in the status of the call that rebuilt them only, so check the status after each
+ * call while a list is kept (the Python binding does, growing the capacity, which rebuilds).
  * qnep_skin_rebuilds: the number of rebuilds so far (synchronises the device). */
 qnep_status qnep_set_skin(qnep_model* m, double skin);
 qnep_status qnep_skin_rebuilds(qnep_model* m, unsigned int* count);
