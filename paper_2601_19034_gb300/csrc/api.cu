@@ -463,6 +463,30 @@ struct StageTimer {
     }
 };
 
+// Device state of a new model: parameters, accumulators, the mapped status word, the second stream
+// and its events.  On failure the caller destroys the model (every handle not yet made is null).
+qnep_status init_model(qnep_model* m, const float* params_host, size_t n_params) {
+    CK(cudaMalloc((void**)&m->d_params, sizeof(float) * n_params));
+    CK(cudaMemcpy(m->d_params, params_host, sizeof(float) * n_params, cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void**)&m->d_acc, sizeof(Accum)));
+    CK(cudaMemset(m->d_acc, 0, sizeof(Accum)));
+    CK(cudaHostAlloc((void**)&m->h_status, sizeof(unsigned int), cudaHostAllocMapped));
+    *m->h_status = 0;
+    CK(cudaHostGetDevicePointer((void**)&m->d_status, m->h_status, 0));
+    CK(cudaMalloc((void**)&m->fin_done, sizeof(unsigned int)));
+    CK(cudaMemset(m->fin_done, 0, sizeof(unsigned int)));
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            m->num_sms = sms;
+    }
+    CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+    return QNEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -540,31 +564,22 @@ qnep_status qnep_create(qnep_model** out, const qnep_hparams* hp, const float* p
         return QNEP_ERR_ARG;
     for (size_t k = 0; k < n_params; ++k)
         if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
-    m = new qnep_model();
+    try {   // host memory: no exception crosses the C ABI
+        m = new qnep_model();
+    } catch (const std::bad_alloc&) {
+        return QNEP_ERR_OOM;
+    }
     m->hp = *hp;
     m->es = *es;
     m->precision = precision;
     m->n_cand = n_candidates;
     m->lay = make_layout(hp->n_species);
     m->sqrt_eps = params_host[m->lay.sqrt_eps];
-    CK(cudaMalloc((void**)&m->d_params, sizeof(float) * n_params));
-    CK(cudaMemcpy(m->d_params, params_host, sizeof(float) * n_params, cudaMemcpyHostToDevice));
-    CK(cudaMalloc((void**)&m->d_acc, sizeof(Accum)));
-    CK(cudaMemset(m->d_acc, 0, sizeof(Accum)));
-    CK(cudaHostAlloc((void**)&m->h_status, sizeof(unsigned int), cudaHostAllocMapped));
-    *m->h_status = 0;
-    CK(cudaHostGetDevicePointer((void**)&m->d_status, m->h_status, 0));
-    CK(cudaMalloc((void**)&m->fin_done, sizeof(unsigned int)));
-    CK(cudaMemset(m->fin_done, 0, sizeof(unsigned int)));
-    {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            m->num_sms = sms;
+    const qnep_status s = init_model(m, params_host, n_params);
+    if (s != QNEP_OK) {   // nothing of a half-built model outlives the failed call
+        qnep_destroy(m);
+        return s;
     }
-    CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
     *out = m;
     return QNEP_OK;
 }

@@ -470,14 +470,20 @@ qnep_status qnep_batch_create(qnep_batch** out, const qnep_hparams* hp, const fl
     if (es->mode == 1 && (!(es->rc_real > 0) || es->rc_real > hp->rc_radial)) return QNEP_ERR_UNSUPPORTED;
     for (size_t k = 0; k < n_params; ++k)
         if (!std::isfinite(params_host[k])) return QNEP_ERR_ARG;
-    b = new qnep_batch();
-    b->hp = *hp;
-    b->es = *es;
-    b->lay = make_layout(hp->n_species);
-    b->n_cand = n_candidates;
-    b->n_groups = (n_candidates + CG - 1) / CG;
+    std::vector<float> pt;
+    try {   // host memory: no exception crosses the C ABI
+        b = new qnep_batch();
+        b->hp = *hp;
+        b->es = *es;
+        b->lay = make_layout(hp->n_species);
+        b->n_cand = n_candidates;
+        b->n_groups = (n_candidates + CG - 1) / CG;
+        pt.assign((size_t)b->n_groups * (size_t)b->lay.total * CG, 0.f);
+    } catch (const std::bad_alloc&) {
+        delete b;
+        return QNEP_ERR_OOM;
+    }
     const size_t P = (size_t)b->lay.total;
-    std::vector<float> pt((size_t)b->n_groups * P * CG, 0.f);
     for (int gi = 0; gi < b->n_groups; ++gi)
         for (int l = 0; l < CG; ++l) {
             const int c = gi * CG + l;
@@ -811,6 +817,12 @@ qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_off
                                 const int* types, const double* boxes, void* stream, double* energy, float* forces,
                                 float* charges, int reps, double* best_ms) {
     if (!b || reps < 1) return QNEP_ERR_ARG;
+    std::vector<float> t;   // the event times of one shape's repetitions
+    try {
+        t.resize((size_t)reps);
+    } catch (const std::bad_alloc&) {
+        return failb(b, QNEP_ERR_OOM, "host memory for the autotuner's timings could not be obtained");
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     CKB(cudaEventCreate(&e0));
@@ -832,7 +844,6 @@ qnep_status qnep_batch_autotune(qnep_batch* b, int n_struct, const int* atom_off
                 result = s;
                 break;
             }
-            std::vector<float> t(reps);
             for (int r = 0; r < reps && s == QNEP_OK; ++r) {
                 cudaEventRecord(e0, st);
                 s = qnep_batch_compute(b, n_struct, atom_offsets, positions, types, boxes, stream, energy, forces,
