@@ -148,3 +148,56 @@ def test_noalloc_refuses_oversized_k_set_before_any_gpu_work(lib):
               len(err)) == _lib.QNEP_ERR_UNSUPPORTED
     assert fn(16, dummy, dummy, box, 0.3, float("inf"), None, None, None, None, err, len(err)) == _lib.QNEP_ERR_ARG
     assert fn(8193, dummy, dummy, box, 0.3, 2.0, None, None, None, None, err, len(err)) == _lib.QNEP_ERR_UNSUPPORTED
+
+
+def _header_constants():
+    """Every integer constant the header defines: enum entries and #defines (comments removed)."""
+    text = open(os.path.join(ROOT, "include", "qnep.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"\b(QNEP_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+(QNEP_[A-Z0-9_]+)\s+(\d+)\s*$", text, flags=re.M)})
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The status codes, option codes and sizes the Python binding passes are the header's values, and
+    the named scalars it reads back sit at the header's indices."""
+    hc = _header_constants()
+    names = [n for n in dir(_lib) if n.startswith("QNEP_")]
+    assert len(names) >= 20
+    for n in names:
+        assert n in hc, n
+        assert getattr(_lib, n) == hc[n], n
+    s = _lib.SCALAR_NAMES
+    assert s["energy"] == hc["QNEP_S_ENERGY"] and s["e_nep"] == hc["QNEP_S_E_NEP"]
+    assert s["e_real"] == hc["QNEP_S_E_REAL"] and s["e_kspace"] == hc["QNEP_S_E_KSPACE"]
+    assert s["e_self"] == hc["QNEP_S_E_SELF"] and s["qtilde_sum"] == hc["QNEP_S_QTILDE_SUM"]
+    assert s["phi_mean"] == hc["QNEP_S_PHI_MEAN"] and s["status"] == hc["QNEP_S_STATUS"]
+    assert s["virial"] == slice(hc["QNEP_S_VIRIAL"], hc["QNEP_S_VIRIAL"] + 9)
+    assert s["polarization"] == slice(hc["QNEP_S_POLARIZATION"], hc["QNEP_S_POLARIZATION"] + 3)
+    assert hc["QNEP_NSCALARS"] == hc["QNEP_S_STATUS"] + 1
+
+
+def test_parse_scalars_and_stack_structures_on_the_host():
+    """Host helpers of the binding: the scalar vector split into named values (virial row-major),
+    and ragged structures (an empty one among them) stacked with their offsets and boxes."""
+    from paper_2601_19034_gb300.qnep import parse_scalars, stack_structures
+    v = np.arange(_lib.QNEP_NSCALARS, dtype=np.float64) * 0.5
+    sc = parse_scalars(v)
+    assert sc["energy"] == 0.0 and sc["e_kspace"] == 1.5 and sc["status"] == 9.5
+    np.testing.assert_array_equal(sc["virial"], (np.arange(5, 14) * 0.5).reshape(3, 3))
+    np.testing.assert_array_equal(sc["polarization"], np.arange(14, 17) * 0.5)
+    rng = np.random.default_rng(3)
+    systems = []
+    for n, edge in ((5, 9.0), (0, 10.0), (3, 11.0)):
+        box = np.diag([edge, edge + 1.0, edge + 2.0])
+        box[1, 0] = 0.5
+        systems.append(wl.System(rng.uniform(0, edge, (n, 3)).astype(np.float32),
+                                 rng.integers(0, 2, n).astype(np.int32), box, ("H", "O")))
+    pos, typ, off, boxes = stack_structures(systems)
+    assert off.tolist() == [0, 5, 5, 8] and off.dtype == np.int32
+    assert pos.shape == (8, 3) and pos.dtype == np.float32 and typ.dtype == np.int32
+    np.testing.assert_array_equal(pos[5:], systems[2].positions)
+    np.testing.assert_array_equal(typ[:5], systems[0].types)
+    assert boxes.shape == (3, 3, 3) and boxes.dtype == np.float64
+    np.testing.assert_array_equal(boxes[1], systems[1].box)
