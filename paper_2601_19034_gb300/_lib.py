@@ -144,6 +144,9 @@ def _declare(lib):
     lib.qnep_nve_run_field.restype = i
     lib.qnep_field_response.argtypes = [i, p, p, p, p, i, p, p]
     lib.qnep_field_response.restype = i
+    lib.qnep_ewald_kspace_noalloc.argtypes = [i, p, p, p, ctypes.c_double, ctypes.c_double, p, p, p, p,
+                                              ctypes.c_char_p, ctypes.c_size_t]
+    lib.qnep_ewald_kspace_noalloc.restype = i
     # batched evaluation
     lib.qnep_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(HParamsC), p, ctypes.c_size_t, i,
                                       ctypes.POINTER(ElecC)]

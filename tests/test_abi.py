@@ -201,3 +201,50 @@ def test_parse_scalars_and_stack_structures_on_the_host():
     np.testing.assert_array_equal(typ[:5], systems[0].types)
     assert boxes.shape == (3, 3, 3) and boxes.dtype == np.float64
     np.testing.assert_array_equal(boxes[1], systems[1].box)
+
+
+def _prototypes():
+    """name -> (return type, [parameter declarations]) of every function the header declares."""
+    text = open(os.path.join(ROOT, "include", "qnep.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"#[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(qnep_[a-z_]+)\s*\(([^()]*)\)\s*;", text):
+        ret, name, params = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+        plist = [] if params in ("", "void") else [x.strip() for x in params.split(",")]
+        out[name] = (ret.split("}")[-1].strip(), plist)
+    return out
+
+
+def _kind_of_c(decl):
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    words = decl.replace("const ", "").split()
+    t = " ".join(words[:-1]) if len(words) > 1 else words[0]
+    return {"int": "int", "unsigned int": "uint", "size_t": "size", "double": "double", "float": "float",
+            "qnep_status": "int"}[t]
+
+
+def _kind_of_ctypes(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_uint: "uint", ctypes.c_size_t: "size", ctypes.c_double: "double",
+            ctypes.c_float: "float"}[t]
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every entry point the header declares has ctypes argument types in the binding (without them a
+    device pointer would be passed as a 32-bit int), with the header's count of arguments, and each
+    argument and the result of the header's kind: pointer, int, unsigned, size_t, double or float."""
+    protos = _prototypes()
+    assert set(protos) == set(_declared_symbols())
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, f"{name}: no argtypes"
+        assert len(fn.argtypes) == len(params), name
+        for k, (decl, t) in enumerate(zip(params, fn.argtypes)):
+            assert _kind_of_ctypes(t) == _kind_of_c(decl), f"{name} argument {k}: {decl}"
+        want = "void" if ret == "void" else ("ptr" if "*" in ret else _kind_of_c(ret + " r"))
+        assert _kind_of_ctypes(fn.restype) == want, f"{name} result: {ret}"

@@ -24,12 +24,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _entry(lib):
-    f = lib.qnep_ewald_kspace_noalloc
-    p = ctypes.c_void_p
-    f.argtypes = [ctypes.c_int, p, p, p, ctypes.c_double, ctypes.c_double, p, p, p, p, ctypes.c_char_p,
-                  ctypes.c_size_t]
-    f.restype = ctypes.c_int
-    return f
+    return lib.qnep_ewald_kspace_noalloc   # argument types declared by the binding
 
 
 def test_noalloc_matches_qnep_compute_twice():
