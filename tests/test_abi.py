@@ -248,3 +248,48 @@ def test_binding_signatures_match_the_header(lib):
             assert _kind_of_ctypes(t) == _kind_of_c(decl), f"{name} argument {k}: {decl}"
         want = "void" if ret == "void" else ("ptr" if "*" in ret else _kind_of_c(ret + " r"))
         assert _kind_of_ctypes(fn.restype) == want, f"{name} result: {ret}"
+
+
+STRUCTS = {"qnep_hparams": "HParamsC", "qnep_elec": "ElecC", "qnep_outputs": "OutputsC", "qnep_vjp": "VjpC",
+           "qnep_batch_outputs": "BatchOutputsC", "qnep_loss_weights": "LossWeightsC",
+           "qnep_loss_weights_v": "LossWeightsVC", "qnep_loss_inputs": "LossInputsC",
+           "qnep_loss_weights_full": "LossWeightsFullC"}
+
+
+def test_struct_fields_match_the_compiled_header(tmp_path):
+    """Every struct the header declares, compiled by the C compiler: the binding's ctypes structure
+    has the same fields (a missing name does not compile) at the same offsets with the same sizes,
+    and the same total size."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    text = open(os.path.join(ROOT, "include", "qnep.h")).read()
+    assert set(re.findall(r"\}\s*(qnep_[a-z_]+)\s*;", text)) - {"qnep_status"} == set(STRUCTS)
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qnep.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in getattr(_lib, pyname)._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname}*)0)->{fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    rows = [ln.split() for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                text=True).stdout.splitlines()]
+    c = {}
+    for r in rows:
+        if r[1] == "size":
+            c[(r[0], None)] = (int(r[2]),)
+        else:
+            c[(r[0], r[1])] = (int(r[2]), int(r[3]))
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(_lib, pyname)
+        assert ctypes.sizeof(cls) == c[(cname, None)][0], cname
+        for fname, _ in cls._fields_:
+            f = getattr(cls, fname)
+            assert (f.offset, f.size) == c[(cname, fname)], f"{cname}.{fname}"
