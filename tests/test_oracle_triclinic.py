@@ -148,3 +148,35 @@ def test_virial_and_forces_in_a_general_cell_match_finite_differences(mode):
         pm[i, d] -= hr
         f = -(energy(pp, box) - energy(pm, box)) / (2 * hr)
         assert abs(f - out["forces"][i, d]) < 1e-5 * max(1.0, abs(f)), (i, d)
+
+
+@pytest.mark.parametrize("kind,mode", [("ewald", 1), ("ewald", 2), ("pppm", 1)])
+def test_turning_the_structure_with_its_cell_turns_every_output(kind, mode):
+    """Rotation covariance of the whole force call, a fact of the physics rather than of any code:
+    turning the atoms and the cell's rows by one rotation R leaves the energy and the charges as
+    they were and turns the forces (R F_i), the virial (R W R^T), the Born effective charges
+    (R Z_i R^T) and the polarization (R P).  The turned cell has no zero entry, so the general-cell
+    k-set (Ewald) and the mesh along the lattice vectors (PPPM) run in full; Q != 0 keeps the
+    charge correction in play."""
+    s = wl.batio3_supercell(2, seed=35)
+    hp = wl.HParams(n_species=3)
+    blob = wl.random_params(hp, np.random.default_rng(36))[0]
+    extra = {"mesh": (12, 12, 12)} if kind == "pppm" else {}
+    elec = wl.Elec(mode=mode, kind=kind, q_total=0.3, **extra)
+    box = s.box.copy()
+    box[1, 0], box[2, 0], box[2, 1] = 0.9, -0.6, 0.7          # a sheared cell in the restricted form
+    pos = (s.positions.astype(np.float64) / s.box[0, 0]) @ box
+    rng = np.random.default_rng(37)
+    r, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(r) < 0:
+        r[:, 0] = -r[:, 0]                                     # a proper rotation
+    a = forcecall.force_call(pos, box, s.types, hp, blob, elec)
+    b = forcecall.force_call(pos @ r.T, box @ r.T, s.types, hp, blob, elec)
+    assert np.abs(box @ r.T).min() > 1e-3                      # every entry of the turned cell non-zero
+    assert abs(b["energy"] - a["energy"]) < 1e-9 * max(1.0, abs(a["energy"]))
+    np.testing.assert_allclose(b["charges"], a["charges"], atol=1e-12)
+    scale = lambda x: max(1.0, np.abs(x).max())               # noqa: E731
+    np.testing.assert_allclose(b["forces"], a["forces"] @ r.T, atol=1e-9 * scale(a["forces"]))
+    np.testing.assert_allclose(b["virial"], r @ a["virial"] @ r.T, atol=1e-9 * scale(a["virial"]))
+    np.testing.assert_allclose(b["bec"], np.einsum("ab,ibc,dc->iad", r, a["bec"], r), atol=1e-9 * scale(a["bec"]))
+    np.testing.assert_allclose(b["polarization"], r @ a["polarization"], atol=1e-9 * scale(a["polarization"]))
