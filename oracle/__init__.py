@@ -22,6 +22,7 @@ Modules
   field       external-field force and polarization current from the BEC (Sec. II.D)
   training    population loss terms of Sec. II.E and the SNES update it drives
   virial      per-atom virial of Eq. per-atom_virial (Ewald and PPPM)
+  md          velocity-Verlet NVE steps around a force call (the 0.5 fs runs of Sec. III)
   params      unpacking of the documented parameter blob
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against

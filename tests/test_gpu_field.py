@@ -22,7 +22,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import field, forcecall  # noqa: E402
+from oracle import field, forcecall, md  # noqa: E402
 from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -155,9 +155,6 @@ def test_argument_errors(dev):
     torch.cuda.synchronize()
 
 
-ACC_UNIT = 9.6485332e-3   # (eV/A)/amu in A/fs^2
-
-
 def _batio3_md():
     s = wl.batio3_supercell(4, seed=91)
     hp = wl.HParams(n_species=3)
@@ -186,15 +183,14 @@ def test_nve_in_field_step_against_oracle(dev):
     x0 = s.positions.astype(np.float64)
     r0 = forcecall.force_call(x0, s.box, s.types, hp, params, elec)
     ft0 = r0["forces"] + field.electric_force(r0["bec"], e)
-    a0 = ft0 * ACC_UNIT / m_atom[:, None]
-    x1 = x0 + dt * (v0 + 0.5 * dt * a0)
+    x1 = md.positions_after_step(x0, v0, ft0, m_atom, dt)
     x1_gpu = pos.cpu().numpy()
     np.testing.assert_allclose(x1_gpu, x1, atol=2e-5)
     r1 = forcecall.force_call(x1_gpu.astype(np.float64), s.box, s.types, hp, params, elec)
     ft1 = r1["forces"] + field.electric_force(r1["bec"], e)
     np.testing.assert_allclose(f1.cpu().numpy(), ft1, atol=1e-4 + 1e-4 * np.abs(e).sum())
     np.testing.assert_allclose(z1.cpu().numpy(), r1["bec"], atol=1e-4)
-    v1 = v0 + 0.5 * dt * (a0 + ft1 * ACC_UNIT / m_atom[:, None])
+    v1 = md.velocities_after_step(v0, ft0, ft1, m_atom, dt)
     v1_gpu = vel.cpu().numpy()
     np.testing.assert_allclose(v1_gpu, v1, atol=1e-6)
     p = pdot.cpu().numpy()

@@ -2,7 +2,7 @@
 
 * a 3297-atom Mg-water slab (same construction as the 1 M-atom system) against the FP64
   oracle, FP32 and BF16 network;
-* one velocity-Verlet step against the update written out in numpy;
+* one velocity-Verlet step against the oracle's update (oracle/md.py) with the GPU's forces;
 * energy conservation of a short NVE run;
 * the full ~1.0 M-atom system (PPPM 256 x 256 x 384): BF16 against the FP32 path
   (force RMSE <= 5e-3 eV/A), the charge constraint, and an NVE segment.
@@ -12,13 +12,11 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import forcecall  # noqa: E402
+from oracle import forcecall, md  # noqa: E402
 from paper_2601_19034_gb300 import workloads as wl  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-ACC_UNIT = 9.6485332e-3   # (eV/A)/amu in A/fs^2
-KE_UNIT = 103.6427        # amu A^2/fs^2 in eV
 
 
 @pytest.fixture(scope="module")
@@ -79,15 +77,13 @@ def test_velocity_verlet_step_is_the_textbook_update(dev):
     dt = 0.5
     f1, en = nve(model, pos, vel, typ, masses, sysm.box, dt, 1)
     torch.cuda.synchronize()
-    a0 = f0 * ACC_UNIT / m_atom[:, None]
-    x1 = sysm.positions.astype(np.float64) + dt * (v0 + 0.5 * dt * a0)
+    # the oracle's velocity-Verlet update, with the GPU's forces at both ends of the step
+    x1 = md.positions_after_step(sysm.positions, v0, f0, m_atom, dt)
     np.testing.assert_allclose(pos.cpu().numpy(), x1, atol=2e-5)
-    a1 = f1.cpu().numpy().astype(np.float64) * ACC_UNIT / m_atom[:, None]
-    v1 = v0 + 0.5 * dt * (a0 + a1)
+    v1 = md.velocities_after_step(v0, f0, f1.cpu().numpy(), m_atom, dt)
     np.testing.assert_allclose(vel.cpu().numpy(), v1, atol=1e-6)
     e = en.cpu().numpy()
-    k0 = 0.5 * (m_atom[:, None] * v0.astype(np.float64) ** 2).sum() * KE_UNIT
-    k1 = 0.5 * (m_atom[:, None] * v1 ** 2).sum() * KE_UNIT
+    k0, k1 = md.kinetic_energy(v0, m_atom), md.kinetic_energy(v1, m_atom)
     assert abs(e[0, 1] - k0) <= 1e-5 * k0 and abs(e[1, 1] - k1) <= 1e-5 * k1
     model.close()
 

@@ -13,10 +13,11 @@ import pytest
 import torch
 
 from oracle import descriptor as dm
-from oracle import ewald, field, forcecall, pppm, training, virial
+from oracle import ewald, field, forcecall, md, pppm, training, virial
 from tests import test_oracle_descriptor as t_desc
 from tests import test_oracle_electrostatics as t_es
 from tests import test_oracle_forces as t_forces
+from tests import test_oracle_md as t_md
 from tests import test_oracle_training as t_tr
 from tests import test_oracle_virial as t_vir
 from tests.test_oracle_field import cluster  # noqa: F401  (fixture for the field pins)
@@ -372,3 +373,26 @@ def test_general_cell_wave_vectors_with_h_inverse_transposed(monkeypatch):
     monkeypatch.setattr(ewald, "reciprocal_energy", wrong)
     _fails(t_tri.test_unimodular_change_of_cell_leaves_the_force_call_unchanged, 1)
     _fails(t_tri.test_pppm_in_a_general_cell_converges_to_ewald)
+
+
+def test_drift_without_the_half(monkeypatch):
+    def wrong(x, v, f, masses, h):
+        x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+        v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
+        return x + h * v + h * h * md.acceleration(f, masses)
+    monkeypatch.setattr(md, "positions_after_step", wrong)
+    _fails(t_md.test_harmonic_well_follows_the_closed_form_of_the_map, 1.2)
+    _fails(t_md.test_energy_error_is_second_order_in_the_step)
+
+
+def test_velocity_half_step_with_the_old_forces_only(monkeypatch):
+    def wrong(v, f_old, f_new, masses, h):
+        return np.asarray(v, dtype=np.float64).reshape(-1, 3) + h * md.acceleration(f_old, masses)
+    monkeypatch.setattr(md, "velocities_after_step", wrong)
+    _fails(t_md.test_harmonic_well_follows_the_closed_form_of_the_map, 1.2)
+    _fails(t_md.test_reversing_the_velocities_retraces_the_trajectory)
+
+
+def test_kinetic_energy_conversion_mistyped(monkeypatch):
+    monkeypatch.setattr(md, "KE_UNIT", md.DALTON / md.E_CHARGE * 1e10 * 1.0001)
+    _fails(t_md.test_unit_conversions)
