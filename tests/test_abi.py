@@ -133,10 +133,7 @@ def test_device_status_bits_decode(lib):
 
 def test_noalloc_refuses_oversized_k_set_before_any_gpu_work(lib):
     """A huge k_max * L is refused from the arguments alone (no enumeration, no CUDA call)."""
-    fn = lib.qnep_ewald_kspace_noalloc
-    p = ctypes.c_void_p
-    fn.argtypes = [ctypes.c_int, p, p, p, ctypes.c_double, ctypes.c_double, p, p, p, p, ctypes.c_char_p,
-                   ctypes.c_size_t]
+    fn = lib.qnep_ewald_kspace_noalloc    # argument types declared by the binding
     dummy = ctypes.c_void_p(0x1000)       # never dereferenced: every call below returns before using it
     box = (ctypes.c_double * 9)(10.0, 0, 0, 0, 10.0, 0, 0, 0, 10.0)
     err = ctypes.create_string_buffer(256)
