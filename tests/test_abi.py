@@ -120,8 +120,7 @@ def test_new_entry_points_reject_bad_arguments_before_any_gpu_work(lib):
 
 def test_device_status_bits_decode(lib):
     """The status word the kernels write maps to the documented codes (bit 1: a bounded wait gave up)."""
-    f = lib.qnep_status_from_device_bits
-    f.argtypes = [ctypes.c_uint]
+    f = lib.qnep_status_from_device_bits        # argument types declared by the binding
     assert f(0) == _lib.QNEP_OK
     assert f(1) == _lib.QNEP_ERR_NBR_OVERFLOW
     assert f(2) == _lib.QNEP_ERR_TIMEOUT
