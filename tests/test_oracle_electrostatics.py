@@ -223,3 +223,21 @@ def test_pppm_converges_to_ewald():
     np.testing.assert_allclose(out["virial"], ref["virial"] - ewald.ewald_static(
         pos, s.box, q, ent, wl.Elec(mode=1, alpha=alpha), with_kspace=False)["virial"],
         atol=2e-3 * np.abs(ref["virial"]).max())
+
+
+def test_coulomb_constant_from_the_si_definitions():
+    """k_e = e^2 / (4 pi eps_0) in eV A per e^2 follows from e = 1.602176634e-19 C (exact) and
+    eps_0 = 8.8541878128e-12 F/m (CODATA 2018): k_e [eV A] = e / (4 pi eps_0) [V m] x 1e10.  The
+    oracle's constant, and the CUDA path's own literals (written separately: FP64 to 1e-11, FP32 to
+    its rounding), are that value.  The Madelung pin above divides by k_e and cannot see it."""
+    import re
+    ke = 1.602176634e-19 / (4.0 * math.pi * 8.8541878128e-12) * 1e10
+    assert ewald.KE == pytest.approx(ke, rel=1e-11)
+    assert pppm.KE == pytest.approx(ke, rel=1e-11)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2601_19034_gb300", "csrc")
+    internal = open(os.path.join(csrc, "qnep_internal.cuh")).read()
+    assert float(re.search(r"constexpr double KE_D = ([0-9.]+);", internal).group(1)) == pytest.approx(ke, rel=1e-11)
+    assert float(re.search(r"constexpr float KE = ([0-9.]+)f;", internal).group(1)) == pytest.approx(ke, rel=6e-8)
+    batch = open(os.path.join(csrc, "api_batch.cu")).read()
+    assert float(re.search(r"\bke = ([0-9.]+);", batch).group(1)) == pytest.approx(ke, rel=1e-11)
