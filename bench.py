@@ -749,6 +749,116 @@ def _time_other_contraction(hp, params, elec, pos_d, typ_d, off, boxes, stream, 
 _CHUNKS = {}
 
 
+def _time_atom_virial(dev, flush, steps):
+    """Cost of the per-atom virial (the entry scatter, the static pair terms and the per-atom k-space
+    term; with PPPM its six more inverse FFTs): the single-structure call on BaTiO3 5000 (Ewald) and
+    on 8000 waters (PPPM 64^3), with and without W_i, graph replay, L2 flushed.  Never raises: a
+    failure is reported in the leg."""
+    from paper_2601_19034_gb300.qnep import QNEP
+    res = {"what": "single-structure force call (forces, virial, BEC, P) with and without the per-atom virial"}
+    for name in ("batio3", "water_pppm"):
+        m = None
+        try:
+            sysm, hp, par, el = _config(name)
+            m = QNEP(hp, par, el)
+            base, _ = _time_single(m, sysm, dev, steps, 3, flush)
+            av, _ = _time_single(m, sysm, dev, steps, 3, flush, want=dict(atom_virial=True))
+            res[name] = {"atoms": sysm.n_atoms, "ms_per_call": base, "ms_per_call_with_atom_virial": av,
+                         "cost": av / base - 1.0, "value_with_atom_virial": sysm.n_atoms / (av * 1e-3),
+                         "unit": UNIT}
+        except Exception as exc:   # noqa: BLE001  (a side measurement never ends the bench line)
+            res[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        finally:
+            if m is not None:
+                m.close()
+    return res
+
+
+def _general_cells(systems, seed=11):
+    """The structures with their cells sheared into the restricted form (every entry below the
+    diagonal non-zero) and then turned by one random rotation: fully general cells with the same
+    fractional coordinates."""
+    from paper_2601_19034_gb300 import workloads
+    rng = np.random.default_rng(seed)
+    r, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(r) < 0:
+        r[:, 0] = -r[:, 0]
+    shear = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0], [-0.05, 0.07, 0.0]])
+    out = []
+    for s_ in systems:
+        box = np.asarray(s_.box, dtype=np.float64)
+        cell = box + shear * np.diag(box)[:, None]
+        frac = np.asarray(s_.positions, dtype=np.float64) @ np.linalg.inv(box)
+        out.append(workloads.System(((frac @ cell) @ r.T).astype(np.float32), s_.types, cell @ r.T, s_.species))
+    return out
+
+
+def _time_general_cells(hp, params, elec, systems, dev, stream, flush, steps, evals, contract, config,
+                        ortho_ms):
+    """General (triclinic) cells: the batched call on the same structures in fully general cells
+    (the restricted form inside the call, outputs turned back), and the single-structure call on
+    BaTiO3 5000 in a sheared cell, each against its orthorhombic form.  Never raises."""
+    import torch
+
+    from paper_2601_19034_gb300.qnep import QNEP, QNEPBatch, stack_structures
+    res = {"what": "cells sheared (b_x = 0.1 b_y, c_x = -0.05 c_z, c_y = 0.07 c_z) and turned by one random "
+                   "rotation, same fractional coordinates"}
+    g = None
+    try:
+        turned = _general_cells(systems)
+        pos, typ, off, boxes = stack_structures(turned)
+        pos_d, typ_d = torch.tensor(pos, device=dev), torch.tensor(typ, device=dev)
+        g = QNEPBatch(hp, params, elec)
+        g.set_contraction(contract)
+        g.set_config(*config)
+        out = g.compute(pos_d, typ_d, off, boxes)
+        with torch.cuda.stream(stream):
+            g.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            g.compute_into(pos_d, typ_d, off, boxes, out, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(3 + steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                graph.replay()
+                b_.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(a.elapsed_time(b_))
+        status = g.sync_status()
+        del graph
+        med = float(np.median(ms))
+        res["batched"] = {"ms_per_step": med, "value": evals / (med * 1e-3), "unit": UNIT,
+                          "vs_orthorhombic": ortho_ms / med, "device_status": status}
+    except Exception as exc:   # noqa: BLE001  (a side measurement never ends the bench line)
+        res["batched"] = {"error": f"{type(exc).__name__}: {exc}"}
+    finally:
+        if g is not None:
+            g.close()
+    m = None
+    try:
+        sysm, hp_b, par_b, el_b = _config("batio3")
+        m = QNEP(hp_b, par_b, el_b)
+        ortho, _ = _time_single(m, sysm, dev, steps, 3, flush)
+        m.close()
+        m = QNEP(hp_b, par_b, el_b)
+        sheared = _general_cells([sysm])[0]
+        general, _ = _time_single(m, sheared, dev, steps, 3, flush)
+        res["single_batio3_5000"] = {"ms_per_call_orthorhombic": ortho, "ms_per_call_general": general,
+                                     "vs_orthorhombic": ortho / general}
+    except Exception as exc:   # noqa: BLE001
+        res["single_batio3_5000"] = {"error": f"{type(exc).__name__}: {exc}"}
+    finally:
+        if m is not None:
+            m.close()
+    return res
+
+
 def _ewald_chunks(box, kmax):
     """Chunks of 8 wave vectors of the half-space k-set (orthorhombic box): per (n1, n2) column
     the contiguous n3 range with 0 < |k| < kmax, split into chunks of 8 (cached per box shape)."""
@@ -975,6 +1085,10 @@ def run_batch(args):
                            "kernel alone")
     b.set_static_geometry(False)
     del g_static
+    # side measurements of the scope table's further rows, last so that nothing above depends on them
+    atom_virial = _time_atom_virial(dev, flush, min(args.steps, 20))
+    general = _time_general_cells(hp, params, elec, systems, dev, stream, flush, min(args.steps, 10), evals,
+                                  args.contract, (warps, order), ms_per_step)
     line = None
     if rank == 0:
         achieved = flop / (ms_per_step * 1e-3) / 1e12
@@ -1009,6 +1123,8 @@ def run_batch(args):
             "plain_fp32": dict(plain, speedup_batched_vs_plain=value / plain["value"]),
             "with_virial": with_virial,
             "with_bec": with_bec,
+            "atom_virial": atom_virial,
+            "general_cells": general,
             "e2e": {"value": evals / (statistics.median(e2e_ms) * 1e-3) * world, "unit": UNIT,
                     "h2d_bytes_per_step": n_total * 16, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.median(e2e_ms),
