@@ -289,3 +289,24 @@ def test_struct_fields_match_the_compiled_header(tmp_path):
         for fname, _ in cls._fields_:
             f = getattr(cls, fname)
             assert (f.offset, f.size) == c[(cname, fname)], f"{cname}.{fname}"
+
+
+def test_missing_library_fails_loudly_and_the_package_never_imports_the_oracle():
+    """The product path has no fallback: opening a library that is not there raises (in a fresh
+    interpreter, as the binding caches the open library), and no module of the package imports the
+    FP64 oracle."""
+    import subprocess
+    import sys
+    code = ("from paper_2601_19034_gb300 import _lib\n"
+            "try:\n"
+            "    _lib.load('/nonexistent/libqnep.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "raised: libqnep.so not built" in r.stdout, r.stdout + r.stderr
+    pkg = os.path.join(ROOT, "paper_2601_19034_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, name)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), name
